@@ -1,0 +1,147 @@
+"""Seeded synthetic inputs for the quasi-linear elliptic model problem.
+
+This module is shared by the CUDA path's tests and benchmark and by the FP64
+oracle's tests. It holds none of the quasi-Newton method's arithmetic
+(no residual, no eigen-decomposition, no mode products, no beta rule): it only
+draws random coefficients and evaluates the problem data of the model problem
+(Sec. 2, eq. main-pde, with lambda u + b u^3 as the nonlinearity) from
+closed-form sine series.
+
+Grid (Sec. 3.2, Dirichlet case): n interior points per axis on (0,1),
+h = 1/(n+1), x_i = i*h for i = 1..n. Arrays are C-ordered with the x index
+fastest: a 2-D field is U[y, x], a 3-D field is U[z, y, x], which is the
+column-major vec() ordering the paper uses with vec(A X B^T) = (B kron A) vec(X).
+
+Random numbers come from SplitMix64 (Steele, Lea, Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) mapped to (0,1) with 53-bit
+resolution and to N(0,1) by the Box-Muller transform (cosine branch).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_MASK64 = (1 << 64) - 1
+_GOLDEN = 0x9E3779B97F4A7C15
+
+
+class SplitMix64:
+    """SplitMix64 stream: state += golden gamma, then the 64-bit finaliser."""
+
+    def __init__(self, seed: int):
+        self.state = int(seed) & _MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + _GOLDEN) & _MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+        return z ^ (z >> 31)
+
+    def next_unit(self) -> float:
+        """Uniform on the open interval (0, 1): ((u >> 11) + 0.5) * 2^-53."""
+        return ((self.next_u64() >> 11) + 0.5) * (1.0 / 9007199254740992.0)
+
+    def next_uniform(self, lo: float, hi: float) -> float:
+        return lo + (hi - lo) * self.next_unit()
+
+    def next_normal(self) -> float:
+        """Standard normal from two uniforms (Box-Muller, cosine branch only)."""
+        u1 = self.next_unit()
+        u2 = self.next_unit()
+        return math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
+
+    def normals(self, count: int) -> np.ndarray:
+        return np.array([self.next_normal() for _ in range(count)], dtype=np.float64)
+
+
+def grid_h(n: int) -> float:
+    """Mesh width for n interior points on (0,1) with Dirichlet ends."""
+    return 1.0 / (n + 1)
+
+
+def grid_points(n: int) -> np.ndarray:
+    """Interior nodes x_i = i*h, i = 1..n."""
+    return np.arange(1, n + 1, dtype=np.float64) * grid_h(n)
+
+
+def sine_basis(n: int, kmax: int) -> np.ndarray:
+    """B[k-1, i] = sin(k*pi*x_i) for k = 1..kmax, i over interior nodes."""
+    k = np.arange(1, kmax + 1, dtype=np.float64)[:, None]
+    return np.sin(k * math.pi * grid_points(n)[None, :])
+
+
+def manufactured_coeffs(seed: int, dim: int, kmax: int) -> np.ndarray:
+    """c[k_z, k_y, k_x] ~ N(0,1) (dim=3) or c[k_y, k_x] (dim=2).
+
+    Drawn in C order, i.e. lexicographic with the x mode index fastest.
+    """
+    rng = SplitMix64(seed)
+    return rng.normals(kmax ** dim).reshape((kmax,) * dim)
+
+
+def sine_series(coef: np.ndarray, n: int) -> np.ndarray:
+    """Evaluate sum_k coef[k] * prod_a sin(k_a pi x_a) on the n^dim interior grid.
+
+    The sum is separable, so it is evaluated one axis at a time; the result
+    is exact up to rounding (no truncation).
+    """
+    dim = coef.ndim
+    kmax = coef.shape[0]
+    B = sine_basis(n, kmax)                      # (kmax, n)
+    if dim == 2:
+        return B.T @ coef @ B                    # [y, x]
+    if dim == 3:
+        t = np.tensordot(coef, B, axes=([2], [0]))           # [kz, ky, x]
+        t = np.tensordot(t, B, axes=([1], [0]))              # [kz, x, y]
+        t = np.ascontiguousarray(t.transpose(0, 2, 1))       # [kz, y, x]
+        out = B.T @ t.reshape(kmax, n * n)                   # [z, y*x]
+        return out.reshape(n, n, n)
+    raise ValueError("dim must be 2 or 3")
+
+
+def mode_wavenumber_sq(kmax: int, dim: int) -> np.ndarray:
+    """|k|^2 = sum_a k_a^2 for the mode index tensor (1-based modes)."""
+    k = np.arange(1, kmax + 1, dtype=np.float64)
+    if dim == 2:
+        return k[:, None] ** 2 + k[None, :] ** 2
+    return k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2
+
+
+def manufactured_problem(n: int, dim: int, seed: int, kmax: int | None = None,
+                         amp: float = 0.1, lam: float = 0.0, b: float = 1.0):
+    """Manufactured solution and source for -Lap u + lam u + b u^3 = f on (0,1)^dim.
+
+    u* = prod_a sin(pi x_a) + amp * sum_{k in {1..kmax}^dim} c_k prod_a sin(k_a pi x_a),
+    c_k ~ N(0,1) from SplitMix64(seed). f is the continuous source
+    -Lap u* + lam u* + b u*^3 sampled at the interior nodes; -Lap of a sine
+    mode is pi^2 |k|^2 times the mode. kmax defaults to 4 in 2-D and 6 in 3-D.
+
+    Returns (u_star, f), float64 arrays of shape (n,)*dim, x fastest.
+    """
+    if kmax is None:
+        kmax = 4 if dim == 2 else 6
+    coef = amp * manufactured_coeffs(seed, dim, kmax)
+    coef[(0,) * dim] += 1.0
+    u = sine_series(coef, n)
+    lap = sine_series(coef * (math.pi ** 2) * mode_wavenumber_sq(kmax, dim), n)
+    f = lap + lam * u + b * u ** 3
+    return u, f
+
+
+def random_field(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """Uniform random array (for operator tests), drawn in C order.
+
+    Vectorised SplitMix64: element i uses the stream state seed + (i+1)*gamma,
+    which is exactly the i-th output of SplitMix64(seed).
+    """
+    count = int(np.prod(shape))
+    with np.errstate(over="ignore"):
+        idx = np.arange(1, count + 1, dtype=np.uint64)
+        z = np.uint64(seed & _MASK64) + idx * np.uint64(_GOLDEN)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    unit = ((z >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+    return (lo + (hi - lo) * unit).reshape(shape)
