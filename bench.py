@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Benchmark: time to relative residual 1e-10 for -Lap u + u^3 = f on the
+3-D 511^3 interior grid (Dirichlet 0, 7-point differences), quasi-Newton with
+the fast-diagonalisation inverse, mode products in BF16x3 split precision on
+the tensor cores, residual / update / stop test in FP64. Zero start,
+manufactured source (6x6x6 random sine modes, seed-drawn), synthetic data.
+
+One step = one complete solve (every iteration: residual + reductions, beta_n
+and stop test, 3 forward mode products with the eigen-sum divide, 3 backward
+mode products with the update) with f and U resident in HBM. Prints one JSON
+line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (numpy) on the host cores instead.
+Under torchrun (N > 1) every rank solves its own seed (replicas; the solve
+has no data-parallel split); value is the slowest rank's time per solve.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to rel. residual 1e-10 at 511^3, mixed/warm vs plain FP64; % of peak"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=511)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end solve")
+    ap.add_argument("--quick", action="store_true", help="= --no-fp64 --no-cpu --no-e2e")
+    a = ap.parse_args()
+    if a.quick:
+        a.no_fp64 = a.no_cpu = a.no_e2e = True
+    return a
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def src_hash(path):
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def ncu_traffic(kernel_file: str):
+    """DRAM bytes per launch of the mode-product kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "modeprod_tc_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("source_sha256_16") != src_hash(kernel_file):
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def cpu_oracle_baseline(n: int, seed: int, iters_timed: int = 1):
+    """Time the FP64 oracle on the host cores: iters_timed quasi-Newton
+    iterations at n^3 (the full solve takes minutes), scaled by the iteration
+    count the oracle needs on the same problem family at 127^3 (the count is
+    mesh-independent, Sec. 6). Returns (ms per solve estimate, details)."""
+    import numpy as np
+    import oracle as O
+    from paper_2502_03611_gb300.inputs import manufactured_problem
+    _, f_small = manufactured_problem(127, 3, seed=seed)
+    _, h_small, _ = O.qn_solve(f_small)
+    its = len(h_small) - 1
+    _, f = manufactured_problem(n, 3, seed=seed)
+    eig = O.eig_1d(n)
+    U = np.zeros_like(f)
+    times = []
+    for _ in range(iters_timed):
+        t0 = time.perf_counter()
+        U, r, beta = O.qn_step(U, f, eig)
+        times.append(time.perf_counter() - t0)
+    per_it = statistics.mean(times)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return per_it * its * 1e3, {"per_iteration_s": per_it, "iterations_assumed": its, "cores": cores}
+
+
+def run_reference(a):
+    """--impl reference: the FP64 CPU oracle, as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle as O
+    from paper_2502_03611_gb300.inputs import manufactured_problem
+    n = a.n
+    _, f_small = manufactured_problem(127, 3, seed=a.seed)
+    _, h_small, _ = O.qn_solve(f_small)
+    its = len(h_small) - 1
+    _, f = manufactured_problem(n, 3, seed=a.seed)
+    eig = O.eig_1d(n)
+    U = np.zeros_like(f)
+    warm = min(a.warmup, 2)
+    steps = min(a.steps, 5)
+    for _ in range(warm):
+        U, _, _ = O.qn_step(U, f, eig)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        U, _, _ = O.qn_step(U, f, eig)
+        times.append(time.perf_counter() - t0)
+    per_it = statistics.mean(times)
+    value = per_it * its * 1e3
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = (f"{steps} timed quasi-Newton iterations (after {warm} untimed) of the FP64 numpy oracle at "
+              f"{n}^3, mean {per_it:.2f} s/iteration x {its} iterations (the oracle's count at 127^3 "
+              f"on the same seed; the count is mesh-independent)")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "ms",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(value, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (manufactured sine-series source, seed-drawn)",
+            "config": {"workload": f"3-D -Lap u + u^3 = f, {n}^3 interior, 7-point FD, Dirichlet 0, "
+                                   f"tol 1e-10, zero start, seed {a.seed}",
+                       "n": n, "dim": 3, "precision": "fp64 (CPU oracle)", "parallelism": "none"},
+            "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2502_03611_gb300 import qn
+    from paper_2502_03611_gb300.inputs import manufactured_problem
+
+    n = a.n
+    seed = a.seed + rank
+    peaks, peak_src = load_peaks()
+    _, f_np = manufactured_problem(n, 3, seed=seed)
+    f_np = np.ascontiguousarray(f_np.reshape(-1))
+    N = f_np.size
+    f = torch.from_numpy(f_np).cuda()
+    U = torch.zeros(N, dtype=torch.float64, device="cuda")
+    ctx = qn.QnContext(3, n, a.precision)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(a.warmup, 0)):
+        U.zero_()
+        qn.qn_solve(ctx, U, f, max_it=100)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    qn.qn_profile_enable(ctx, True)
+    sampler = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = []
+    for _ in range(a.steps):
+        U.zero_()
+        res, _ = qn.qn_solve(ctx, U, f, max_it=100)
+        results.append(res)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    prof = qn.qn_profile_read(ctx)
+    qn.qn_profile_enable(ctx, False)
+    ms_per_step = elapsed_ms / max(a.steps, 1)
+    t = torch.tensor([ms_per_step], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    iters = [r["iterations"] for r in results]
+    rels = [r["rel"] for r in results]
+    ok = all(r["status"] == 0 for r in results)
+
+    # ---- roofline of the dominant kernel (mode product) and of the residual kernel
+    P = ((n + 63) // 64) * 64
+    mp_avg_ms = prof["modeprod_ms"] / max(prof["modeprod_launches"], 1)
+    alg_flops = 2.0 * float(n) ** 4                      # one mode product: 2 N n, N = n^3
+    exec_flops = (3 if a.precision == "bf16x3" else 1) * 2.0 * float(P) ** 4
+    mp_tflops = alg_flops / (mp_avg_ms * 1e-3) / 1e12
+    if a.precision == "bf16x3":
+        peak = float(peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))
+        peak_name = f"bf16 dense, sustained ({peak_src})"
+    else:
+        peak = None
+        peak_name = "fp64 (see plain_fp64.fp64_peak)"
+    kernel_file = os.path.join(ROOT, "paper_2502_03611_gb300", "csrc",
+                               "qn_modeprod_tc.cu" if a.precision == "bf16x3" else "qn_modeprod_f64.cu")
+    roofline = {"kernel": "k_modeprod_tc" if a.precision == "bf16x3" else "k_modeprod_f64",
+                "bound": "tensor", "achieved": round(mp_tflops, 2), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(mp_tflops / peak, 4) if peak else None,
+                "traffic": ncu_traffic(kernel_file) if a.precision == "bf16x3" else None,
+                "peak_source": peak_name,
+                "flops_per_launch_algorithmic": alg_flops,
+                "flops_per_launch_executed": exec_flops,
+                "executed_tflops": round(exec_flops / (mp_avg_ms * 1e-3) / 1e12, 2),
+                "executed_frac": round(exec_flops / (mp_avg_ms * 1e-3) / 1e12 / peak, 4) if peak else None,
+                "avg_launch_ms": round(mp_avg_ms, 4), "launches": prof["modeprod_launches"]}
+    res_avg_ms = prof["residual_ms"] / max(prof["residual_launches"], 1)
+    split = a.precision == "bf16x3"
+    res_bytes = 16.0 * N + (4.0 * P ** 3 if split else 8.0 * N)
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
+    res_gbs = res_bytes / (res_avg_ms * 1e-3) / 1e9
+    kernels = {
+        "residual": {"avg_launch_ms": round(res_avg_ms, 4), "launches": prof["residual_launches"],
+                     "bytes_per_launch": res_bytes, "achieved_gbs": round(res_gbs, 1),
+                     "frac_hbm": round(res_gbs / hbm, 4), "share": None},
+        "modeprod": {"avg_launch_ms": round(mp_avg_ms, 4), "launches": prof["modeprod_launches"],
+                     "store_ms": round(prof["mp_store_ms"] / max(prof["mp_store_launches"], 1), 4),
+                     "divide_ms": round(prof["mp_divide_ms"] / max(prof["mp_divide_launches"], 1), 4),
+                     "update_ms": round(prof["mp_last_ms"] / max(prof["mp_last_launches"], 1), 4)},
+        "finalize": {"avg_launch_ms": round(prof["finalize_ms"] / max(prof["finalize_launches"], 1), 4),
+                     "launches": prof["finalize_launches"]},
+    }
+    tot = prof["residual_ms"] + prof["modeprod_ms"] + prof["finalize_ms"]
+    if tot > 0:
+        kernels["residual"]["share"] = round(prof["residual_ms"] / tot, 4)
+        kernels["modeprod"]["share"] = round(prof["modeprod_ms"] / tot, 4)
+        kernels["finalize"]["share"] = round(prof["finalize_ms"] / tot, 4)
+    gpu_launches = int(prof["launches"])
+
+    # ---- end to end through the public API with host buffers (copies inside the timed region)
+    e2e = None
+    if not a.no_e2e:
+        f_h = torch.from_numpy(f_np).pin_memory()
+        U_h = torch.zeros(N, dtype=torch.float64).pin_memory()
+        U_np = U_h.numpy()
+        e2e_ms = []
+        for rep in range(3):
+            U_np[:] = 0.0
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            qn.qn_solve_host(ctx, U_np, f_h.numpy(), max_it=100)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:
+                e2e_ms.append(e0.elapsed_time(e1))
+        e2e = {"value": round(statistics.median(e2e_ms), 3), "unit": "ms",
+               "h2d_bytes_per_step": 2 * 8 * N, "d2h_bytes_per_step": 8 * N,
+               "note": "qn_solve_host: H2D of f and U0 from pinned memory, solve, D2H of U"}
+        del f_h, U_h
+
+    # ---- plain FP64 GPU solve of the same problem (the denominator of the speedup)
+    plain = None
+    if not a.no_fp64 and a.precision == "bf16x3":
+        del ctx
+        torch.cuda.empty_cache()
+        ctx64 = qn.QnContext(3, n, "fp64")
+        U.zero_()
+        qn.qn_solve(ctx64, U, f, max_it=1)           # load kernels
+        torch.cuda.synchronize()
+        qn.qn_profile_enable(ctx64, True)
+        U.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r64, _ = qn.qn_solve(ctx64, U, f, max_it=100)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        p64 = qn.qn_profile_read(ctx64)
+        ms64 = e0.elapsed_time(e1)
+        mp64 = p64["modeprod_ms"] / max(p64["modeprod_launches"], 1)
+        # cuBLAS DGEMM throughput as the FP64 denominator (no FP64 peak is in MEASURED_PEAKS)
+        A = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+        B = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            A @ B
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(5):
+            A @ B
+        g1.record(stream)
+        torch.cuda.synchronize()
+        dgemm_tflops = 5 * 2 * 4096.0 ** 3 / (g0.elapsed_time(g1) * 1e-3) / 1e12
+        fp64_mp_tflops = alg_flops / (mp64 * 1e-3) / 1e12
+        plain = {"ms": round(ms64, 2), "iterations": r64["iterations"], "rel": r64["rel"],
+                 "status": r64["status"], "modeprod_avg_ms": round(mp64, 3),
+                 "modeprod_tflops": round(fp64_mp_tflops, 3),
+                 "fp64_peak": {"cublas_dgemm_tflops": round(dgemm_tflops, 3),
+                               "frac_of_cublas_dgemm": round(fp64_mp_tflops / dgemm_tflops, 4)},
+                 "speedup_mixed_vs_fp64": round(ms64 / ms_max, 2)}
+        del ctx64, A, B
+
+    cpu = None
+    if not a.no_cpu and rank == 0 and world == 1:
+        ms_cpu, det = cpu_oracle_baseline(n, a.seed)
+        cpu = {"value": round(ms_cpu, 1), "unit": "ms", "cores": det["cores"], "kind": "oracle",
+               "sample": (f"1 quasi-Newton iteration of the FP64 numpy oracle at {n}^3 "
+                          f"({det['per_iteration_s']:.2f} s) x {det['iterations_assumed']} iterations "
+                          f"(oracle count at 127^3, same seed)")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(ms_max, 3), "unit": "ms", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_max, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3+f64" if a.precision == "bf16x3" else "f64",
+            "data": "synthetic (manufactured sine-series source, 6x6x6 modes, seed-drawn)",
+            "config": {"workload": f"3-D -Lap u + u^3 = f, {n}^3 interior ({N} unknowns), 7-point FD, "
+                                   f"Dirichlet 0, tol 1e-10 on ||F||/||f||, zero start, seed {a.seed}",
+                       "n": n, "dim": 3, "precision": a.precision,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (f, U: 1.07 GB each)"},
+            "iterations": iters[0] if len(set(iters)) == 1 else iters,
+            "final_rel": max(rels), "converged": ok,
+            "solves_per_s": round(world * 1e3 / ms_max, 3),
+            "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
+            "e2e": e2e, "plain_fp64": plain, "cpu_baseline": cpu, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

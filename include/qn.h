@@ -1,0 +1,202 @@
+/*
+ * qn.h - C ABI of libqn: GPU quasi-Newton solver for discretised quasi-linear
+ * elliptic equations A_h U + N_h(U) = 0 with a fast-diagonalisation inverse.
+ *
+ * Method: W. Hao, S. Lee, X. Zhang, "An Efficient Quasi-Newton Method with
+ * Tensor Product Implementation for Solving Quasi-Linear Elliptic Equations
+ * and Systems" (arXiv 2502.03611).
+ *
+ * Problem solved (Sec. 2 eq. main-pde, Sec. 3.2, Sec. 4 eq. F_u):
+ *   -Lap u + lam u + b u^3 = f   on (0,1)^dim, u = 0 on the boundary,
+ * discretised by second-order central differences (5-point in 2-D, 7-point in
+ * 3-D, eq. fdm-discrete) on n interior nodes per axis, h = 1/(n+1):
+ *   F(U) = A_h vec(U) + N_h(U),  A_h = sum_a I..H_a..I + lam I,
+ *   H_a = (1/h^2) tridiag(-1, 2, -1),  N_h(U) = b U^3 - f.
+ * Quasi-Newton update (Sec. 4 eq. identity-method):
+ *   U <- U - step * (A_h + beta_n I)^{-1} F(U),
+ *   beta_n = (lambda_max + lambda_min)/2 of (N_h)_U = diag(3 b U^2),
+ * with the inverse applied by fast diagonalisation (Sec. 4.1 eq. fin_inverse):
+ * mode products with S^{-1} along every axis, pointwise division by
+ * (sum_a lambda_{i_a} + lam + beta_n), mode products with S along every axis.
+ * Stopping rule: ||F(U)||_2 / ||f||_2 <= tol (the paper leaves the tolerance
+ * open; this library takes the relative l2 residual against the source).
+ *
+ * Conventions for every entry point:
+ *  - Arrays are float64, C order with the x index fastest: U[y][x] in 2-D and
+ *    U[z][y][x] in 3-D, interior nodes only (n^dim values). This is the
+ *    paper's vec() ordering.
+ *  - Array pointers are DEVICE pointers unless the name ends in _host. The
+ *    caller owns them; the library never frees or retains them past the call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Work is enqueued on it. Entry points that return statistics to
+ *    host structs synchronise that stream before returning.
+ *  - Every call returns QN_OK (0) or a negative QN_E* code. Arguments are
+ *    validated on the host before anything is launched. No call exits the
+ *    process or throws across the ABI. qn_last_error() returns a message for
+ *    the last failure on the calling thread.
+ */
+#ifndef QN_H
+#define QN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define QN_OK            0
+#define QN_EINVAL       -1  /* bad argument (null pointer, size, non-finite parameter) */
+#define QN_ENOMEM       -2  /* device or host allocation failed */
+#define QN_ECUDA        -3  /* a CUDA runtime/driver call failed (see qn_last_error) */
+#define QN_ENOTCONV     -4  /* max_it reached before the tolerance; U holds the last iterate */
+#define QN_EDIVERGED    -5  /* residual became non-finite or grew past 1e8 x ||f|| */
+#define QN_ETIMEOUT     -6  /* a device-side wait gave up (kernel returned early, no hang) */
+#define QN_EUNSUPPORTED -7  /* valid request this build does not implement */
+
+/* ---- enumerations -------------------------------------------------------- */
+#define QN_BC_DIRICHLET 0   /* homogeneous Dirichlet, interior unknowns only (Sec. 3.2) */
+
+#define QN_PREC_FP64   0    /* mode products in FP64 on the FP64 pipe */
+#define QN_PREC_BF16X3 1    /* mode products on tcgen05 tensor cores as
+                               hi*hi + hi*lo + lo*hi BF16 products, FP32
+                               accumulation; residual, beta, update and stop
+                               test stay FP64 (outer loop = iterative refinement) */
+
+#define QN_BETA_PAPER 0     /* beta_n = (max + min)/2 of diag(3 b U^2) (eq. identity-method) */
+#define QN_BETA_FIXED 1     /* beta_n = qn_opts.beta_value every iteration */
+
+/* ---- structures ------------------------------------------------------------ */
+typedef struct qn_problem {
+    int dim;          /* 2 or 3 */
+    int n;            /* interior nodes per axis, 1 <= n <= 1024 (same on every axis) */
+    int bc;           /* QN_BC_DIRICHLET */
+    int precision;    /* QN_PREC_FP64 or QN_PREC_BF16X3 */
+    double lam;       /* linear coefficient lam of -Lap u + lam u + b u^3 = f */
+    double b;         /* cubic coefficient b */
+} qn_problem;
+
+typedef struct qn_stats {
+    double res_norm;  /* ||F(U)||_2 at the evaluated iterate */
+    double f_norm;    /* ||f||_2 */
+    double fu_min;    /* smallest entry of diag(N_h)_U = 3 b U^2 */
+    double fu_max;    /* largest entry */
+    double beta;      /* beta_n applied to this iterate (paper rule or fixed) */
+    double rel;       /* res_norm / f_norm */
+} qn_stats;
+
+typedef struct qn_opts {
+    double tol;        /* stop when rel <= tol (1e-10 in the benchmarks) */
+    int max_it;        /* at most this many updates (>= 0, <= 4096) */
+    int beta_mode;     /* QN_BETA_PAPER or QN_BETA_FIXED */
+    double beta_value; /* used with QN_BETA_FIXED */
+    double step;       /* update scale; 1.0 is the paper's plain update */
+    int sync_every;    /* host checks convergence every this many iterations
+                          (>= 1); kernels queued past convergence exit at once */
+} qn_opts;
+
+typedef struct qn_result {
+    int iterations;    /* updates applied */
+    int status;        /* QN_OK, QN_ENOTCONV, QN_EDIVERGED or QN_ETIMEOUT */
+    double rel;        /* final ||F(U)||_2 / ||f||_2 */
+} qn_result;
+
+typedef struct qn_ctx qn_ctx;  /* opaque; owns device workspace for one problem shape */
+
+/* ---- entry points ------------------------------------------------------------ */
+
+/* Version of this ABI (major*10000 + minor*100 + patch). */
+int qn_version(void);
+
+/* Message for the last failing call on this thread ("" if none). Owned by the library. */
+const char *qn_last_error(void);
+
+/* 1-D diagonalisation H = S diag(lam) S^{-1} (Sec. 4.2; H from Sec. 3.2 eq. Sy).
+ * Host-only, FP64. n >= 1; h must equal 1/(n+1) (checked to 1e-12 relative).
+ * For QN_BC_DIRICHLET the eigenpairs are the closed-form discrete sine pairs
+ * lam_k = (4/h^2) sin^2(k pi h/2), S[j][k] = sqrt(2h) sin(j k pi h) (1-based
+ * j, k), ascending in k; S is symmetric orthogonal so S_inv = S.
+ * S, S_inv: caller-owned host buffers of n*n doubles, row-major (S[j*n+k]).
+ * lam: caller-owned host buffer of n doubles. Any output may be NULL. */
+int qn_setup_1d_eig(int n, double h, int bc, double *S, double *S_inv, double *lam);
+
+/* Create a context for one problem shape on the current CUDA device: uploads
+ * S, S^{-1} and the eigenvalues (and their BF16 hi/lo splits for
+ * QN_PREC_BF16X3), allocates the working buffers (about 2 n^dim doubles for
+ * FP64, 2 padded n^dim x 4 bytes for BF16X3) and, for BF16X3, builds the TMA
+ * tensor maps. QN_EUNSUPPORTED for BF16X3 on a device without sm_103a
+ * tcgen05 support. *out is owned by the library until qn_ctx_destroy. */
+int qn_ctx_create(const qn_problem *p, qn_ctx **out);
+
+/* Free everything the context owns. NULL is accepted. Synchronises the device. */
+int qn_ctx_destroy(qn_ctx *ctx);
+
+/* Residual F(U) = A_h vec(U) + lam U + b U^3 - f (Sec. 4 eq. F_u) in FP64.
+ * U, f: device, n^dim doubles. R: device, n^dim doubles, or NULL to compute
+ * only the statistics. st (host, may be NULL): norms and extreme entries of
+ * diag(3 b U^2); beta is the paper's beta_n for U. Synchronises `stream`
+ * when st != NULL. */
+int qn_residual(qn_ctx *ctx, const double *U, const double *f, double *R,
+                qn_stats *st, void *stream);
+
+/* Shifted inverse by fast diagonalisation (Sec. 4.1 eq. fin_inverse):
+ * V = (sum_a I..H_a..I + shift I)^{-1} r, i.e. A_h without lam, plus shift.
+ * r, V: device, n^dim doubles, distinct. Runs in the context's precision
+ * (FP64 or BF16X3 mode products). shift must be finite and
+ * > -dim * lambda_min(H). Does not synchronise. */
+int qn_fast_diag_solve(qn_ctx *ctx, const double *r, double *V, double shift, void *stream);
+
+/* One quasi-Newton update in place (Sec. 4 eq. identity-method):
+ * U <- U - step (A_h + beta I)^{-1} F(U) with step = 1 and beta = the paper's
+ * beta_n when `beta` is NaN, else the given beta. U, f: device, n^dim doubles.
+ * st (host, may be NULL): statistics of the iterate BEFORE the update.
+ * Synchronises `stream` when st != NULL. */
+int qn_step(qn_ctx *ctx, double *U, const double *f, double beta, qn_stats *st, void *stream);
+
+/* Iterate qn_step until ||F(U)||/||f|| <= opts->tol or opts->max_it updates.
+ * U: device, n^dim doubles: in = initial iterate U_0 (zeros for the standard
+ * start, or a warm start), out = last iterate. f: device, n^dim doubles.
+ * opts: host (NULL = tol 1e-10, max_it 200, paper beta, step 1, sync_every 2).
+ * res (host, may be NULL): iteration count, status, final relative residual.
+ * history (host, may be NULL): receives the statistics of iterates
+ * U_0 .. U_iterations (history_len entries at most). Synchronises `stream`.
+ * Returns res->status (QN_OK when converged). */
+int qn_solve(qn_ctx *ctx, double *U, const double *f, const qn_opts *opts,
+             qn_result *res, qn_stats *history, int history_len, void *stream);
+
+/* qn_solve with HOST arrays: copies f_host and U_host (initial iterate) to
+ * context-owned device buffers, solves, copies the result back into U_host.
+ * U_host, f_host: host, n^dim doubles (pinned memory gives full copy speed).
+ * Synchronises `stream`. */
+int qn_solve_host(qn_ctx *ctx, double *U_host, const double *f_host, const qn_opts *opts,
+                  qn_result *res, qn_stats *history, int history_len, void *stream);
+
+/* ---- measurement ------------------------------------------------------------- */
+typedef struct qn_profile {
+    long long launches;       /* kernels launched that did work since qn_profile_enable
+                                 (launches queued past convergence are not counted) */
+    int residual_launches;    /* residual + reduction kernel */
+    double residual_ms;       /* summed CUDA-event time on the launching stream */
+    int finalize_launches;    /* one-block reduction finaliser (beta_n, stop test) */
+    double finalize_ms;
+    int modeprod_launches;    /* all mode-product launches (sum of the three below) */
+    double modeprod_ms;
+    int mp_store_launches;    /* products that store the next product's input */
+    double mp_store_ms;
+    int mp_divide_launches;   /* last forward product, with the eigen-sum divide */
+    double mp_divide_ms;
+    int mp_last_launches;     /* last backward product, with the update (or dense store) */
+    double mp_last_ms;
+} qn_profile;
+
+/* on != 0: from now on record a pair of CUDA events around every kernel
+ * launch of this context (on the launching stream); on == 0: stop recording.
+ * Either way the counters are reset. */
+int qn_profile_enable(qn_ctx *ctx, int on);
+
+/* Sum the recorded launch times per kernel class (waits for the events).
+ * out: host struct. */
+int qn_profile_read(qn_ctx *ctx, qn_profile *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QN_H */

@@ -1,0 +1,669 @@
+// C-ABI entry points of libqn (declared in include/qn.h): context set-up,
+// residual, shifted fast-diagonalisation inverse, one quasi-Newton step and
+// the solve loop.
+//
+// One iteration (Sec. 4 eq. identity-method with the inverse of Sec. 4.1
+// eq. fin_inverse) is enqueued as
+//   residual+reductions -> finalise (beta_n, stop test, on the device)
+//   -> dim forward mode products (S^{-1}; the last one divides by the eigen-sums)
+//   -> dim backward mode products (S; the last one applies U -= step * delta).
+// The finaliser's `done` flag makes every later kernel return at once, so the
+// host may queue several iterations before it checks convergence.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "qn_internal.h"
+
+namespace qn {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return QN_ECUDA;
+}
+
+}  // namespace qn
+
+using namespace qn;
+
+static const int kHistCap = 4097;
+
+struct qn_ctx {
+    qn_problem prob;
+    int device;
+    int num_sms;
+    int n, P, dim;
+    long long N;    // n^dim
+    long long NP;   // P^dim (split path)
+    double h, inv_h2;
+    // eigen-data
+    double *S64, *Si64, *lam64;
+    __nv_bfloat16 *S_hi, *S_lo, *Si_hi, *Si_lo;
+    float *lam32;
+    // working buffers
+    double *w64[2];
+    __nv_bfloat16 *bhi[2], *blo[2];
+    double *partials;
+    int nparts;
+    DevState *st;
+    qn_stats *hist;
+    int *err;
+    TcPlan *plan;
+    // host-array staging for qn_solve_host
+    double *dU, *df;
+    // launch accounting / optional CUDA-event timing of every launch
+    struct ProfRec {
+        cudaEvent_t a, b;
+        int kind;
+        int iter;
+        int valid;
+    };
+    std::vector<ProfRec> *prof;
+    size_t prof_used;
+    int prof_on;
+    int cur_iter;
+    long long launches;
+};
+
+enum ProfKind { PK_RESIDUAL = 0, PK_FINALIZE = 1, PK_MP_STORE = 2, PK_MP_DIVIDE = 3, PK_MP_LAST = 4,
+                PK_SPLIT = 5, PK_COUNT = 6 };
+
+// Begin/end a timed launch. With profiling off these only count launches.
+static long prof_begin(qn_ctx *c, int kind, cudaStream_t s) {
+    c->launches++;
+    if (!c->prof_on) return -1;
+    if (c->prof_used == c->prof->size()) {
+        qn_ctx::ProfRec r;
+        if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return -1;
+        c->prof->push_back(r);
+    }
+    qn_ctx::ProfRec &r = (*c->prof)[c->prof_used];
+    r.kind = kind;
+    r.iter = c->cur_iter;
+    r.valid = 1;
+    if (cudaEventRecord(r.a, s) != cudaSuccess) return -1;
+    return (long)c->prof_used++;
+}
+
+static void prof_end(qn_ctx *c, long idx, cudaStream_t s) {
+    if (idx >= 0) cudaEventRecord((*c->prof)[idx].b, s);
+}
+
+static int check_ctx(qn_ctx *c) {
+    if (!c) {
+        set_error("null context");
+        return QN_EINVAL;
+    }
+    return QN_OK;
+}
+
+static void split_host(double v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    const float f = (float)v;
+    hi = __float2bfloat16_rn(f);
+    lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+}
+
+extern "C" int qn_version(void) { return 10000; }
+
+extern "C" const char *qn_last_error(void) { return g_err; }
+
+extern "C" int qn_setup_1d_eig(int n, double h, int bc, double *S, double *S_inv, double *lam) {
+    if (n < 1 || n > 65536) {
+        set_error("qn_setup_1d_eig: n=%d out of range", n);
+        return QN_EINVAL;
+    }
+    const double hh = 1.0 / (n + 1);
+    if (!(fabs(h - hh) <= 1e-12 * hh)) {
+        set_error("qn_setup_1d_eig: h=%.17g but 1/(n+1)=%.17g", h, hh);
+        return QN_EINVAL;
+    }
+    if (bc != QN_BC_DIRICHLET) {
+        set_error("qn_setup_1d_eig: only QN_BC_DIRICHLET is implemented");
+        return QN_EUNSUPPORTED;
+    }
+    const double pi = 3.14159265358979323846;
+    const double scale = sqrt(2.0 * hh);
+    for (int k = 1; k <= n; ++k) {
+        const double s = sin(0.5 * k * pi * hh);
+        if (lam) lam[k - 1] = 4.0 / (hh * hh) * s * s;
+    }
+    for (int j = 1; j <= n; ++j) {
+        for (int k = 1; k <= n; ++k) {
+            // sin(j k pi h) with the product reduced mod 2(n+1) for accuracy
+            const long long jk = ((long long)j * k) % (2LL * (n + 1));
+            const double v = scale * sin(pi * (double)jk * hh);
+            if (S) S[(size_t)(j - 1) * n + (k - 1)] = v;
+            if (S_inv) S_inv[(size_t)(j - 1) * n + (k - 1)] = v;   // symmetric orthogonal
+        }
+    }
+    return QN_OK;
+}
+
+static void ctx_free(qn_ctx *c) {
+    if (!c) return;
+    cudaFree(c->S64);
+    cudaFree(c->Si64);
+    cudaFree(c->lam64);
+    cudaFree(c->S_hi);
+    cudaFree(c->S_lo);
+    cudaFree(c->Si_hi);
+    cudaFree(c->Si_lo);
+    cudaFree(c->lam32);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(c->w64[b]);
+        cudaFree(c->bhi[b]);
+        cudaFree(c->blo[b]);
+    }
+    cudaFree(c->partials);
+    cudaFree(c->st);
+    cudaFree(c->hist);
+    cudaFree(c->err);
+    cudaFree(c->dU);
+    cudaFree(c->df);
+    if (c->plan) tc_plan_destroy(c->plan);
+    if (c->prof) {
+        for (auto &r : *c->prof) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        delete c->prof;
+    }
+    delete c;
+}
+
+#define CK(call)                                  \
+    do {                                          \
+        cudaError_t _e = (call);                  \
+        if (_e != cudaSuccess) {                  \
+            int _r = cuda_fail(_e, #call);        \
+            ctx_free(c);                          \
+            return _r;                            \
+        }                                         \
+    } while (0)
+
+extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
+    if (!p || !out) {
+        set_error("qn_ctx_create: null argument");
+        return QN_EINVAL;
+    }
+    *out = nullptr;
+    if (p->dim != 2 && p->dim != 3) {
+        set_error("qn_ctx_create: dim must be 2 or 3 (got %d)", p->dim);
+        return QN_EINVAL;
+    }
+    if (p->n < 1 || p->n > 1024) {
+        set_error("qn_ctx_create: n must be in [1, 1024] (got %d)", p->n);
+        return QN_EINVAL;
+    }
+    if (p->bc != QN_BC_DIRICHLET) {
+        set_error("qn_ctx_create: only QN_BC_DIRICHLET is implemented");
+        return QN_EUNSUPPORTED;
+    }
+    if (p->precision != QN_PREC_FP64 && p->precision != QN_PREC_BF16X3) {
+        set_error("qn_ctx_create: unknown precision %d", p->precision);
+        return QN_EINVAL;
+    }
+    if (!isfinite(p->lam) || !isfinite(p->b)) {
+        set_error("qn_ctx_create: lam and b must be finite");
+        return QN_EINVAL;
+    }
+    qn_ctx *c = new (std::nothrow) qn_ctx();
+    if (!c) return QN_ENOMEM;
+    memset(c, 0, sizeof(*c));
+    c->prob = *p;
+    c->prof = new (std::nothrow) std::vector<qn_ctx::ProfRec>();
+    if (!c->prof) {
+        delete c;
+        return QN_ENOMEM;
+    }
+    CK(cudaGetDevice(&c->device));
+    CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    c->n = p->n;
+    c->dim = p->dim;
+    c->P = ((p->n + 63) / 64) * 64;
+    c->N = 1;
+    c->NP = 1;
+    for (int a = 0; a < c->dim; ++a) {
+        c->N *= c->n;
+        c->NP *= c->P;
+    }
+    c->h = 1.0 / (c->n + 1);
+    c->inv_h2 = 1.0 / (c->h * c->h);
+    const int n = c->n, P = c->P;
+
+    std::vector<double> S((size_t)n * n), Si((size_t)n * n), lam(n);
+    int rc = qn_setup_1d_eig(n, c->h, p->bc, S.data(), Si.data(), lam.data());
+    if (rc != QN_OK) {
+        ctx_free(c);
+        return rc;
+    }
+    CK(cudaMalloc(&c->S64, sizeof(double) * n * n));
+    CK(cudaMalloc(&c->Si64, sizeof(double) * n * n));
+    CK(cudaMalloc(&c->lam64, sizeof(double) * n));
+    CK(cudaMemcpy(c->S64, S.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->Si64, Si.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->lam64, lam.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+
+    const int rows = (c->dim == 3) ? P * P : P;
+    c->nparts = rows < 4 * c->num_sms ? rows : 4 * c->num_sms;
+    CK(cudaMalloc(&c->partials, sizeof(double) * 4 * c->nparts));
+    CK(cudaMalloc(&c->st, sizeof(DevState)));
+    CK(cudaMalloc(&c->hist, sizeof(qn_stats) * kHistCap));
+    CK(cudaMalloc(&c->err, sizeof(int)));
+    CK(cudaMemset(c->err, 0, sizeof(int)));
+
+    if (p->precision == QN_PREC_FP64) {
+        for (int b = 0; b < 2; ++b) CK(cudaMalloc(&c->w64[b], sizeof(double) * c->N));
+    } else {
+        if (!tc_supported(c->device)) {
+            set_error("qn_ctx_create: QN_PREC_BF16X3 needs an sm_103 (tcgen05) device");
+            ctx_free(c);
+            return QN_EUNSUPPORTED;
+        }
+        std::vector<__nv_bfloat16> hS((size_t)P * P), lS((size_t)P * P), hSi((size_t)P * P),
+            lSi((size_t)P * P);
+        std::vector<float> l32(P, 1e30f);
+        for (int j = 0; j < P; ++j)
+            for (int k = 0; k < P; ++k) {
+                const double vs = (j < n && k < n) ? S[(size_t)j * n + k] : 0.0;
+                const double vi = (j < n && k < n) ? Si[(size_t)j * n + k] : 0.0;
+                split_host(vs, hS[(size_t)j * P + k], lS[(size_t)j * P + k]);
+                split_host(vi, hSi[(size_t)j * P + k], lSi[(size_t)j * P + k]);
+            }
+        for (int k = 0; k < n; ++k) l32[k] = (float)lam[k];
+        const size_t mb = sizeof(__nv_bfloat16) * P * P;
+        CK(cudaMalloc(&c->S_hi, mb));
+        CK(cudaMalloc(&c->S_lo, mb));
+        CK(cudaMalloc(&c->Si_hi, mb));
+        CK(cudaMalloc(&c->Si_lo, mb));
+        CK(cudaMalloc(&c->lam32, sizeof(float) * P));
+        CK(cudaMemcpy(c->S_hi, hS.data(), mb, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->S_lo, lS.data(), mb, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->Si_hi, hSi.data(), mb, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->Si_lo, lSi.data(), mb, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->lam32, l32.data(), sizeof(float) * P, cudaMemcpyHostToDevice));
+        const size_t pb = sizeof(__nv_bfloat16) * (size_t)c->NP;
+        for (int b = 0; b < 2; ++b) {
+            CK(cudaMalloc(&c->bhi[b], pb));
+            CK(cudaMalloc(&c->blo[b], pb));
+            CK(cudaMemset(c->bhi[b], 0, pb));
+            CK(cudaMemset(c->blo[b], 0, pb));
+        }
+        rc = tc_plan_create(&c->plan, n, P, c->dim, c->bhi, c->blo, c->S_hi, c->S_lo, c->Si_hi, c->Si_lo,
+                            c->num_sms);
+        if (rc != QN_OK) {
+            ctx_free(c);
+            return rc;
+        }
+    }
+    *out = c;
+    return QN_OK;
+}
+
+extern "C" int qn_ctx_destroy(qn_ctx *c) {
+    if (!c) return QN_OK;
+    cudaDeviceSynchronize();
+    ctx_free(c);
+    return QN_OK;
+}
+
+// ---- internal enqueue helpers ------------------------------------------------------
+static int reset_state(qn_ctx *c, double tol, int max_it, int beta_mode, double beta_value,
+                       cudaStream_t s) {
+    DevState h;
+    memset(&h, 0, sizeof(h));
+    h.tol = tol;
+    h.max_it = max_it;
+    h.beta_mode = beta_mode;
+    h.beta_value = beta_value;
+    QN_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    return QN_OK;
+}
+
+static EpiArgs epi_args(qn_ctx *c, double *U, double step) {
+    EpiArgs e;
+    e.lam64 = c->lam64;
+    e.lam32 = c->lam32;
+    e.shift = &c->st->shift;
+    e.step = step;
+    e.U = U;
+    e.done = &c->st->done;
+    e.err = c->err;
+    return e;
+}
+
+// Residual of U into the first working buffer (split planes or FP64), with partials.
+static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double *R64_override,
+                            bool to_work, const int *done, cudaStream_t s) {
+    ResidualArgs a;
+    a.U = U;
+    a.f = f;
+    a.n = c->n;
+    a.dim = c->dim;
+    a.inv_h2 = c->inv_h2;
+    a.lam = c->prob.lam;
+    a.b = c->prob.b;
+    a.R64 = R64_override;
+    a.Rhi = nullptr;
+    a.Rlo = nullptr;
+    a.P = c->P;
+    if (to_work) {
+        if (c->prob.precision == QN_PREC_FP64) {
+            a.R64 = c->w64[0];
+        } else {
+            a.Rhi = c->bhi[0];
+            a.Rlo = c->blo[0];
+        }
+    }
+    a.partials = c->partials;
+    a.done = done;
+    const long pr = prof_begin(c, PK_RESIDUAL, s);
+    const int rc = launch_residual(a, c->nparts, s);
+    prof_end(c, pr, s);
+    return rc;
+}
+
+// Shifted inverse of working buffer 0 (or of `r0` for the FP64 path), written
+// as U -= step*delta (update=true) or V = delta (update=false).
+static int enqueue_inverse(qn_ctx *c, const double *r0, double *target, bool update, double step,
+                           cudaStream_t s) {
+    const int d = c->dim;
+    const EpiArgs e = epi_args(c, target, step);
+    int cur = 0;
+    for (int i = 0; i < 2 * d; ++i) {
+        const bool forward = i < d;
+        const bool last = (i == 2 * d - 1);
+        Epi epi = EPI_STORE;
+        if (i == d - 1) epi = EPI_DIVIDE;
+        if (last) epi = update ? EPI_UPDATE : EPI_DENSE;
+        const int next = 1 - cur;
+        int rc;
+        const long pr = prof_begin(c, last ? PK_MP_LAST : (epi == EPI_DIVIDE ? PK_MP_DIVIDE : PK_MP_STORE), s);
+        if (c->prob.precision == QN_PREC_FP64) {
+            GemmShape g;
+            g.n = c->n;
+            g.P = c->n;
+            g.dim = d;
+            g.K = c->n;
+            g.N = c->n;
+            g.Mtot = (d == 3) ? c->n * c->n : c->n;
+            const double *A = (i == 0 && r0 != nullptr) ? r0 : c->w64[cur];
+            const double *B = forward ? c->Si64 : c->S64;
+            double *o = last ? target : c->w64[next];
+            rc = launch_modeprod_f64(A, B, o, g, epi, e, s);
+        } else {
+            rc = launch_modeprod_tc(c->plan, cur, last ? -1 : next, forward, epi, e, s);
+        }
+        prof_end(c, pr, s);
+        if (rc != QN_OK) return rc;
+        cur = next;
+    }
+    return QN_OK;
+}
+
+static int enqueue_iteration(qn_ctx *c, double *U, const double *f, double step, cudaStream_t s) {
+    int rc = enqueue_residual(c, U, f, nullptr, true, &c->st->done, s);
+    if (rc) return rc;
+    const long pr = prof_begin(c, PK_FINALIZE, s);
+    rc = launch_finalize(c->partials, c->nparts, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 1, s);
+    prof_end(c, pr, s);
+    if (rc) return rc;
+    return enqueue_inverse(c, nullptr, U, true, step, s);
+}
+
+static int read_state(qn_ctx *c, DevState *h, cudaStream_t s) {
+    QN_CUDA(cudaMemcpyAsync(h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    QN_CUDA(cudaStreamSynchronize(s));
+    int err = 0;
+    QN_CUDA(cudaMemcpy(&err, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        QN_CUDA(cudaMemset(c->err, 0, sizeof(int)));
+        set_error("a device-side wait gave up (tensor-core pipeline timeout)");
+        return QN_ETIMEOUT;
+    }
+    return QN_OK;
+}
+
+static bool bad_ptr(const void *p) { return p == nullptr; }
+
+// ---- public entry points -----------------------------------------------------------------
+extern "C" int qn_residual(qn_ctx *c, const double *U, const double *f, double *R, qn_stats *st,
+                           void *stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (bad_ptr(U) || bad_ptr(f)) {
+        set_error("qn_residual: null U or f");
+        return QN_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = reset_state(c, -1.0, 0, QN_BETA_PAPER, 0.0, s);
+    if (rc) return rc;
+    rc = enqueue_residual(c, U, f, R, false, nullptr, s);
+    if (rc) return rc;
+    const long pr = prof_begin(c, PK_FINALIZE, s);
+    rc = launch_finalize(c->partials, c->nparts, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 0, s);
+    prof_end(c, pr, s);
+    if (rc) return rc;
+    if (st) {
+        QN_CUDA(cudaMemcpyAsync(st, c->hist, sizeof(qn_stats), cudaMemcpyDeviceToHost, s));
+        QN_CUDA(cudaStreamSynchronize(s));
+    }
+    return QN_OK;
+}
+
+extern "C" int qn_fast_diag_solve(qn_ctx *c, const double *r, double *V, double shift, void *stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (bad_ptr(r) || bad_ptr(V) || r == V) {
+        set_error("qn_fast_diag_solve: r and V must be distinct non-null device arrays");
+        return QN_EINVAL;
+    }
+    if (!isfinite(shift)) {
+        set_error("qn_fast_diag_solve: shift must be finite");
+        return QN_EINVAL;
+    }
+    // smallest eigenvalue of sum_a H_a is dim * lambda_1
+    const double l1 = 4.0 / (c->h * c->h) * pow(sin(0.5 * 3.14159265358979323846 * c->h), 2);
+    if (!(shift > -c->dim * l1)) {
+        set_error("qn_fast_diag_solve: shift %.6g makes the operator singular or indefinite", shift);
+        return QN_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = reset_state(c, -1.0, 0, QN_BETA_FIXED, 0.0, s);
+    if (rc) return rc;
+    QN_CUDA(cudaMemcpyAsync(&c->st->shift, &shift, sizeof(double), cudaMemcpyHostToDevice, s));
+    if (c->prob.precision == QN_PREC_FP64) {
+        return enqueue_inverse(c, r, V, false, 1.0, s);
+    }
+    const long pr = prof_begin(c, PK_SPLIT, s);
+    rc = launch_split_pad(r, c->n, c->P, c->dim, c->bhi[0], c->blo[0], 4 * c->num_sms, s);
+    prof_end(c, pr, s);
+    if (rc) return rc;
+    return enqueue_inverse(c, nullptr, V, false, 1.0, s);
+}
+
+extern "C" int qn_step(qn_ctx *c, double *U, const double *f, double beta, qn_stats *st, void *stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (bad_ptr(U) || bad_ptr(f)) {
+        set_error("qn_step: null U or f");
+        return QN_EINVAL;
+    }
+    if (isinf(beta)) {
+        set_error("qn_step: beta must be finite or NaN (paper rule)");
+        return QN_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool paper = isnan(beta);
+    rc = reset_state(c, -1.0, 1, paper ? QN_BETA_PAPER : QN_BETA_FIXED, paper ? 0.0 : beta, s);
+    if (rc) return rc;
+    rc = enqueue_iteration(c, U, f, 1.0, s);
+    if (rc) return rc;
+    DevState h;
+    rc = read_state(c, &h, s);
+    if (rc) return rc;
+    if (st) QN_CUDA(cudaMemcpy(st, c->hist, sizeof(qn_stats), cudaMemcpyDeviceToHost));
+    if (h.done && h.status == QN_EDIVERGED) {
+        set_error("qn_step: non-finite residual or beta");
+        return QN_EDIVERGED;
+    }
+    return QN_OK;
+}
+
+extern "C" int qn_solve(qn_ctx *c, double *U, const double *f, const qn_opts *opts, qn_result *res,
+                        qn_stats *history, int history_len, void *stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (bad_ptr(U) || bad_ptr(f)) {
+        set_error("qn_solve: null U or f");
+        return QN_EINVAL;
+    }
+    qn_opts o;
+    if (opts) {
+        o = *opts;
+    } else {
+        o.tol = 1e-10;
+        o.max_it = 200;
+        o.beta_mode = QN_BETA_PAPER;
+        o.beta_value = 0.0;
+        o.step = 1.0;
+        o.sync_every = 2;
+    }
+    if (!(o.tol >= 0.0) || o.max_it < 0 || o.max_it > kHistCap - 1 || !isfinite(o.step) ||
+        (o.beta_mode != QN_BETA_PAPER && o.beta_mode != QN_BETA_FIXED) ||
+        (o.beta_mode == QN_BETA_FIXED && !isfinite(o.beta_value))) {
+        set_error("qn_solve: invalid options");
+        return QN_EINVAL;
+    }
+    if (o.sync_every < 1) o.sync_every = 1;
+    if (history_len < 0 || (history_len > 0 && history == nullptr)) {
+        set_error("qn_solve: invalid history buffer");
+        return QN_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = reset_state(c, o.tol, o.max_it, o.beta_mode, o.beta_value, s);
+    if (rc) return rc;
+    DevState h;
+    memset(&h, 0, sizeof(h));
+    int enqueued = 0;
+    const size_t first_rec = c->prof_used;
+    const long long launches0 = c->launches;
+    while (enqueued <= o.max_it) {
+        for (int k = 0; k < o.sync_every && enqueued <= o.max_it; ++k, ++enqueued) {
+            c->cur_iter = enqueued;
+            rc = enqueue_iteration(c, U, f, o.step, s);
+            if (rc) return rc;
+        }
+        rc = read_state(c, &h, s);
+        if (rc) return rc;
+        if (h.done) break;
+    }
+    if (!h.done) {   // cannot happen: the finaliser stops at max_it
+        set_error("qn_solve: internal iteration accounting error");
+        return QN_ECUDA;
+    }
+    const int its = h.it;
+    int status = h.status;
+    // launches queued past convergence returned at once: drop them from the accounting
+    for (size_t i = first_rec; i < c->prof_used; ++i) {
+        qn_ctx::ProfRec &r = (*c->prof)[i];
+        const bool mp = r.kind >= PK_MP_STORE && r.kind <= PK_MP_LAST;
+        if ((mp && r.iter >= its) || (!mp && r.iter > its)) r.valid = 0;
+    }
+    c->launches = launches0 + 2LL * (its + 1) + 2LL * c->dim * its;
+    qn_stats last;
+    QN_CUDA(cudaMemcpy(&last, c->hist + its, sizeof(qn_stats), cudaMemcpyDeviceToHost));
+    if (history && history_len > 0) {
+        const int cnt = (its + 1) < history_len ? (its + 1) : history_len;
+        QN_CUDA(cudaMemcpy(history, c->hist, sizeof(qn_stats) * cnt, cudaMemcpyDeviceToHost));
+    }
+    if (res) {
+        res->iterations = its;
+        res->status = status;
+        res->rel = last.rel;
+    }
+    if (status == QN_ENOTCONV) set_error("qn_solve: max_it reached (rel %.3e)", last.rel);
+    if (status == QN_EDIVERGED) set_error("qn_solve: diverged (rel %.3e)", last.rel);
+    return status;
+}
+
+extern "C" int qn_solve_host(qn_ctx *c, double *U_host, const double *f_host, const qn_opts *opts,
+                             qn_result *res, qn_stats *history, int history_len, void *stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (bad_ptr(U_host) || bad_ptr(f_host)) {
+        set_error("qn_solve_host: null U_host or f_host");
+        return QN_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * (size_t)c->N;
+    if (!c->dU) {
+        QN_CUDA(cudaMalloc(&c->dU, bytes));
+        QN_CUDA(cudaMalloc(&c->df, bytes));
+    }
+    QN_CUDA(cudaMemcpyAsync(c->df, f_host, bytes, cudaMemcpyHostToDevice, s));
+    QN_CUDA(cudaMemcpyAsync(c->dU, U_host, bytes, cudaMemcpyHostToDevice, s));
+    rc = qn_solve(c, c->dU, c->df, opts, res, history, history_len, stream);
+    if (rc != QN_OK && rc != QN_ENOTCONV && rc != QN_EDIVERGED) return rc;
+    QN_CUDA(cudaMemcpyAsync(U_host, c->dU, bytes, cudaMemcpyDeviceToHost, s));
+    QN_CUDA(cudaStreamSynchronize(s));
+    return rc;
+}
+
+extern "C" int qn_profile_enable(qn_ctx *c, int on) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    c->prof_on = on ? 1 : 0;
+    c->prof_used = 0;
+    c->launches = 0;
+    return QN_OK;
+}
+
+extern "C" int qn_profile_read(qn_ctx *c, qn_profile *out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!out) {
+        set_error("qn_profile_read: null output");
+        return QN_EINVAL;
+    }
+    memset(out, 0, sizeof(*out));
+    out->launches = c->launches;
+    double ms[PK_COUNT] = {0};
+    int cnt[PK_COUNT] = {0};
+    for (size_t i = 0; i < c->prof_used; ++i) {
+        qn_ctx::ProfRec &r = (*c->prof)[i];
+        if (!r.valid) continue;
+        QN_CUDA(cudaEventSynchronize(r.b));
+        float t = 0.f;
+        QN_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        ms[r.kind] += t;
+        cnt[r.kind] += 1;
+    }
+    out->residual_launches = cnt[PK_RESIDUAL];
+    out->residual_ms = ms[PK_RESIDUAL];
+    out->finalize_launches = cnt[PK_FINALIZE];
+    out->finalize_ms = ms[PK_FINALIZE];
+    out->modeprod_launches = cnt[PK_MP_STORE] + cnt[PK_MP_DIVIDE] + cnt[PK_MP_LAST];
+    out->modeprod_ms = ms[PK_MP_STORE] + ms[PK_MP_DIVIDE] + ms[PK_MP_LAST];
+    out->mp_store_launches = cnt[PK_MP_STORE];
+    out->mp_store_ms = ms[PK_MP_STORE];
+    out->mp_divide_launches = cnt[PK_MP_DIVIDE];
+    out->mp_divide_ms = ms[PK_MP_DIVIDE];
+    out->mp_last_launches = cnt[PK_MP_LAST];
+    out->mp_last_ms = ms[PK_MP_LAST];
+    return QN_OK;
+}

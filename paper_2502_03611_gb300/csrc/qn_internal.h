@@ -1,0 +1,103 @@
+// Internal declarations shared by the libqn translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qn.h"
+
+namespace qn {
+
+// Device-resident solver state: written by the reduction finaliser, read by
+// every later kernel of the iteration (so the host need not synchronise
+// between the residual and the inverse).
+struct DevState {
+    int done;        // 1 once converged / diverged / out of iterations: later kernels return at once
+    int status;      // QN_OK, QN_ENOTCONV, QN_EDIVERGED
+    int it;          // index of the iterate whose residual was evaluated last
+    int err;         // nonzero if a device-side wait gave up (QN_ETIMEOUT)
+    double shift;    // lam + beta_n used by the pointwise divide
+    double beta;     // beta_n
+    double tol;
+    int max_it;
+    int beta_mode;
+    double beta_value;
+};
+
+// Residual kernel outputs.
+struct ResidualArgs {
+    const double *U;
+    const double *f;
+    int n, dim;
+    double inv_h2, lam, b;
+    double *R64;               // dense FP64 residual or nullptr
+    __nv_bfloat16 *Rhi;        // padded split planes (P per axis) or nullptr
+    __nv_bfloat16 *Rlo;
+    int P;
+    double *partials;          // [grid][4] : sum r^2, sum f^2, min U^2, max U^2
+    const int *done;           // skip when *done != 0 (nullptr: never skip)
+};
+
+// Epilogue selector shared by both mode-product kernels.
+enum Epi : int {
+    EPI_STORE = 0,    // out[k][m] = acc (next product's input)
+    EPI_DIVIDE = 1,   // out[k][m] = acc / (lambda_k + row eigen-sum + shift)
+    EPI_UPDATE = 2,   // U[dense(k, m)] -= step * acc
+    EPI_DENSE = 3,    // V[dense(k, m)] = acc  (FP64 dense output)
+};
+
+struct EpiArgs {
+    const double *lam64;      // eigenvalues (n), FP64
+    const float *lam32;       // eigenvalues padded to P with 1e30 (split path)
+    const double *shift;      // device pointer to lam + beta_n
+    double step;
+    double *U;                // EPI_UPDATE / EPI_DENSE target (dense n^dim)
+    const int *done;          // skip when *done != 0
+    int *err;                 // device error flag
+};
+
+// Per-launch geometry of one mode product: out = (A * B^T)^T with
+// A: [Mtot][K] (K = contraction axis, contiguous), B: [N][K].
+struct GemmShape {
+    int Mtot;   // rows of A (= n^(dim-1), or P^(dim-1) padded)
+    int K;      // contraction length (n, or P padded)
+    int N;      // output modes (n, or P padded)
+    int n;      // logical extent per axis
+    int P;      // padded extent per axis (split path), = n for FP64
+    int dim;
+};
+
+// ---- launchers (implemented in the .cu files) ---------------------------------
+int launch_residual(const ResidualArgs &a, int grid, cudaStream_t s);
+int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *hist,
+                    int hist_cap, double b, double lam, int update_state, cudaStream_t s);
+int launch_split_pad(const double *r, int n, int P, int dim, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                     int grid, cudaStream_t s);
+int launch_modeprod_f64(const double *A, const double *B, double *out, const GemmShape &g,
+                        Epi epi, const EpiArgs &e, cudaStream_t s);
+
+struct TcPlan;   // tensor maps + tile config of the tcgen05 path
+int tc_plan_create(TcPlan **plan, int n, int P, int dim, __nv_bfloat16 *bufs_hi[2],
+                   __nv_bfloat16 *bufs_lo[2], const __nv_bfloat16 *S_hi,
+                   const __nv_bfloat16 *S_lo, const __nv_bfloat16 *Si_hi,
+                   const __nv_bfloat16 *Si_lo, int num_sms);
+void tc_plan_destroy(TcPlan *plan);
+// One split-precision mode product: src buffer index -> dst buffer index (or
+// the FP64 dense target for EPI_UPDATE / EPI_DENSE). forward selects S^{-1}.
+int launch_modeprod_tc(TcPlan *plan, int src, int dst, bool forward, Epi epi,
+                       const EpiArgs &e, cudaStream_t s);
+bool tc_supported(int device);
+
+// error reporting
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace qn
+
+#define QN_CUDA(call)                                         \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) return qn::cuda_fail(_e, #call); \
+    } while (0)

@@ -1,0 +1,479 @@
+// Split-precision mode product on the 5th-generation tensor cores (tcgen05).
+//
+// Same contraction as the FP64 kernel (Sec. 4.1 eq. fin_inverse, one mode
+// product per launch, result stored transposed so the axes rotate and every
+// product contracts the contiguous axis):
+//
+//     out[k][m] = sum_j A[m][j] * B[k][j],   A = [Mtot][P] data, B = S or S^{-1}
+//
+// with each operand held as an unevaluated sum of two BF16 values
+// (x = x_hi + x_lo, x_hi = bf16(x), x_lo = bf16(x - x_hi)) and the product
+// formed as A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32 (TMEM) accumulators.
+// The intermediate tensors are stored in the same hi/lo form on a grid padded
+// to P = 64*ceil(n/64) points per axis (padded entries are zero, padded
+// eigenvalues are 1e30 so the divide keeps them zero).
+//
+// Kernel organisation (persistent, one CTA of 192 threads per SM):
+//   warp 0 lane 0  TMA producer: A_hi, A_lo (128 x BK) and B_hi, B_lo (BN x BK)
+//                  tiles per pipeline stage, K-major with 128-B or 64-B swizzle
+//   warp 1         allocates TMEM (2 accumulators of BN FP32 columns); lane 0
+//                  issues tcgen05.mma (M=128, N=BN, K=16) and commits to mbarriers
+//   warps 2..5     epilogue: tcgen05.ld of the accumulator (warp w owns TMEM
+//                  lanes 32*(w%4)..+31 = rows), then store / divide / update
+// Tiles are walked in m-major order (consecutive CTAs share the same A rows;
+// S stays resident in L2). The epilogue of tile i overlaps the MMAs of tile
+// i+1 through the double-buffered accumulators.
+//
+// Every mbarrier wait is bounded (2 s of %globaltimer). On expiry the kernel
+// sets the device error flag, tells the other roles to stop, waits (bounded)
+// for its own outstanding TMA copies and MMAs, frees TMEM and returns.
+#include <cudaTypedefs.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "qn_internal.h"
+#include "qn_ptx.cuh"
+
+namespace qn {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int kThreads = 192;
+constexpr int kMaxStages = 8;
+constexpr uint64_t kTimeoutNs = 2000000000ull;
+constexpr uint32_t kCtrlBytes = 512;
+
+struct TcArgs {
+    int Mtot, P, n, BN, ntile_n, ntiles, tmem_cols, stages;
+    __nv_bfloat16 *out_hi;
+    __nv_bfloat16 *out_lo;
+    EpiArgs e;
+};
+
+// Wait for `parity` on `bar`; false on timeout or when another role aborted.
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                         int *err) {
+    if (ptx::mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = ptx::globaltimer();
+    while (true) {
+        if (ptx::mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (ptx::globaltimer() - t0 > kTimeoutNs) {
+            *abort_flag = 1;
+            atomicExch(err, QN_ETIMEOUT);
+            return false;
+        }
+    }
+}
+
+// Bounded wait that ignores the abort flag (used while draining after an abort).
+__device__ __forceinline__ void drain_bar(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = ptx::globaltimer();
+    while (!ptx::mbar_try_wait(bar, parity)) {
+        if (ptx::globaltimer() - t0 > kTimeoutNs) return;
+    }
+}
+
+__device__ __forceinline__ void split_store(float v, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                                            long long o) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[o] = h;
+    lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+template <int BK, int EPI, int DIM>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_modeprod_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
+                  const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
+                  const TcArgs args) {
+    if (args.e.done != nullptr && *(volatile const int *)args.e.done) return;
+
+    constexpr uint32_t kRowBytes = BK * 2;                // one swizzle row per tile row
+    constexpr uint32_t kLayout = (BK == 64) ? 2u : 4u;    // 128-B : 64-B swizzle
+    constexpr int kKSteps = BK / 16;
+
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = ptx::smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const int BN = args.BN;
+    const uint32_t a_bytes = BM * kRowBytes;
+    const uint32_t b_bytes = (uint32_t)BN * kRowBytes;
+    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+    const int stages = args.stages;
+    const uint32_t ctrl = base + (uint32_t)stages * stage_bytes;
+    // control block: full[8], empty[8], tfull[2], tempty[2], mma_done, tmem slot, abort
+    auto full_bar = [&](int s) { return ctrl + 8u * s; };
+    auto empty_bar = [&](int s) { return ctrl + 64u + 8u * s; };
+    auto tfull_bar = [&](int b) { return ctrl + 128u + 8u * b; };
+    auto tempty_bar = [&](int b) { return ctrl + 144u + 8u * b; };
+    const uint32_t mma_done_bar = ctrl + 160u;
+    const uint32_t tmem_slot = ctrl + 168u;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem_raw + (ctrl + 172u - raw));
+    float *lam_s = reinterpret_cast<float *>(smem_raw + (ctrl + kCtrlBytes - raw));
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            ptx::mbar_init(full_bar(s), 1);
+            ptx::mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(tfull_bar(b), 1);
+            ptx::mbar_init(tempty_bar(b), 4);
+        }
+        ptx::mbar_init(mma_done_bar, 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+        ptx::fence_proxy_async();
+        ptx::prefetch_tensormap(&mA_hi);
+        ptx::prefetch_tensormap(&mA_lo);
+        ptx::prefetch_tensormap(&mB_hi);
+        ptx::prefetch_tensormap(&mB_lo);
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(tmem_slot, (uint32_t)args.tmem_cols);
+        ptx::tmem_relinquish();
+    }
+    if (EPI == EPI_DIVIDE) {
+        for (int i = threadIdx.x; i < args.P; i += blockDim.x) lam_s[i] = args.e.lam32[i];
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t *>(smem_raw + (tmem_slot - raw));
+
+    const int KB = args.P / BK;
+    int *err = args.e.err;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------ TMA producer ------------------------------
+        uint32_t armed_parity[kMaxStages];
+        uint32_t armed_mask = 0;
+        int s = 0;
+        uint32_t ph = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; ok && t < args.ntiles; t += gridDim.x) {
+            const int m0 = (t / args.ntile_n) * BM;
+            const int n0 = (t % args.ntile_n) * BN;
+            for (int kb = 0; kb < KB; ++kb) {
+                if (!wait_bar(empty_bar(s), ph ^ 1u, abort_flag, err)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t st = base + (uint32_t)s * stage_bytes;
+                ptx::mbar_arrive_expect_tx(full_bar(s), stage_bytes);
+                ptx::tma_load_2d(st, &mA_hi, full_bar(s), kb * BK, m0);
+                ptx::tma_load_2d(st + a_bytes, &mA_lo, full_bar(s), kb * BK, m0);
+                ptx::tma_load_2d(st + 2 * a_bytes, &mB_hi, full_bar(s), kb * BK, n0);
+                ptx::tma_load_2d(st + 2 * a_bytes + b_bytes, &mB_lo, full_bar(s), kb * BK, n0);
+                armed_parity[s] = ph;
+                armed_mask |= 1u << s;
+                if (++s == stages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+        }
+        if (!ok) {
+            for (int i = 0; i < stages; ++i)
+                if (armed_mask & (1u << i)) drain_bar(full_bar(i), armed_parity[i]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------ MMA issuer --------------------------------
+        const uint32_t idesc = ptx::idesc_bf16_f32(BM, (uint32_t)BN);
+        int s = 0;
+        uint32_t ph = 0;
+        int acc = 0;
+        uint32_t aph = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; ok && t < args.ntiles; t += gridDim.x) {
+            if (!wait_bar(tempty_bar(acc), aph ^ 1u, abort_flag, err)) break;
+            ptx::tc_fence_after();
+            const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+            for (int kb = 0; kb < KB; ++kb) {
+                if (!wait_bar(full_bar(s), ph, abort_flag, err)) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint32_t st = base + (uint32_t)s * stage_bytes;
+#pragma unroll
+                for (int kk = 0; kk < kKSteps; ++kk) {
+                    const uint32_t koff = (uint32_t)kk * 32u;
+                    const uint64_t a_hi = ptx::smem_desc_kmajor(st + koff, kRowBytes, kLayout);
+                    const uint64_t a_lo = ptx::smem_desc_kmajor(st + a_bytes + koff, kRowBytes, kLayout);
+                    const uint64_t b_hi = ptx::smem_desc_kmajor(st + 2 * a_bytes + koff, kRowBytes, kLayout);
+                    const uint64_t b_lo =
+                        ptx::smem_desc_kmajor(st + 2 * a_bytes + b_bytes + koff, kRowBytes, kLayout);
+                    const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+                    ptx::mma_bf16(d_tmem, a_hi, b_hi, idesc, first);
+                    ptx::mma_bf16(d_tmem, a_hi, b_lo, idesc, 1u);
+                    ptx::mma_bf16(d_tmem, a_lo, b_hi, idesc, 1u);
+                }
+                ptx::mma_commit(empty_bar(s));
+                if (++s == stages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+            if (!ok) break;
+            ptx::mma_commit(tfull_bar(acc));
+            acc ^= 1;
+            if (acc == 0) aph ^= 1u;
+        }
+        ptx::mma_commit(mma_done_bar);
+        drain_bar(mma_done_bar, 0);
+    } else if (warp >= 2) {
+        // ------------------------------ epilogue ----------------------------------
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        int acc = 0;
+        uint32_t aph = 0;
+        float shift = 0.0f;
+        if (EPI == EPI_DIVIDE) shift = (float)(*args.e.shift);
+        const float step = (float)args.e.step;
+        const int P = args.P, n = args.n;
+        const long long Mtot = args.Mtot;
+        for (int t = blockIdx.x; t < args.ntiles; t += gridDim.x) {
+            // every lane waits; the decision to go on is made warp-uniform so
+            // that the .sync.aligned TMEM loads below are never divergent
+            const bool ready = wait_bar(tfull_bar(acc), aph, abort_flag, err);
+            if (!__all_sync(0xffffffffu, ready)) break;
+            ptx::tc_fence_after();
+            const long long m = (long long)(t / args.ntile_n) * BM + row;
+            const int n0 = (t % args.ntile_n) * BN;
+            const bool m_ok = m < Mtot;
+            float rowlam = 0.0f;
+            long long ubase = -1;   // dense U index without the k term (UPDATE/DENSE)
+            if (m_ok) {
+                if (EPI == EPI_DIVIDE) {
+                    rowlam = (DIM == 3) ? lam_s[m / P] + lam_s[m % P] : lam_s[m];
+                }
+                if (EPI == EPI_UPDATE || EPI == EPI_DENSE) {
+                    if (DIM == 3) {
+                        const int yy = (int)(m / P), xx = (int)(m % P);
+                        if (yy < n && xx < n) ubase = (long long)yy * n + xx;
+                    } else {
+                        if (m < n) ubase = m;
+                    }
+                }
+            }
+            const long long kstride = (DIM == 3) ? (long long)n * n : (long long)n;
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t r[32];
+                ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
+                ptx::tmem_ld_wait();
+                if (!m_ok) continue;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int k = n0 + c + i;
+                    const float v = __uint_as_float(r[i]);
+                    if (EPI == EPI_STORE) {
+                        if (k < P) split_store(v, args.out_hi, args.out_lo, (long long)k * Mtot + m);
+                    } else if (EPI == EPI_DIVIDE) {
+                        if (k < P) {
+                            const float den = lam_s[k] + rowlam + shift;
+                            split_store(v / den, args.out_hi, args.out_lo, (long long)k * Mtot + m);
+                        }
+                    } else if (EPI == EPI_UPDATE) {
+                        if (ubase >= 0 && k < n) {
+                            double *u = args.e.U + (long long)k * kstride + ubase;
+                            *u = *u - (double)step * (double)v;
+                        }
+                    } else {   // EPI_DENSE
+                        if (ubase >= 0 && k < n) args.e.U[(long long)k * kstride + ubase] = (double)v;
+                    }
+                }
+            }
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(tempty_bar(acc));
+            acc ^= 1;
+            if (acc == 0) aph ^= 1u;
+        }
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem_base, (uint32_t)args.tmem_cols);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct TcPlan {
+    int n, P, dim, Mtot, BN, ntile_n, ntile_m, ntiles, grid, stages, tmem_cols, BK;
+    size_t smem;
+    CUtensorMap a_hi[2], a_lo[2];
+    CUtensorMap s_hi, s_lo, si_hi, si_lo;
+    __nv_bfloat16 *bufs_hi[2];
+    __nv_bfloat16 *bufs_lo[2];
+};
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (fn) return fn;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return nullptr;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    return fn;
+}
+
+static int encode_2d(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                     uint32_t box_outer, int BK) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled unavailable from the driver");
+        return QN_ECUDA;
+    }
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d) for %llux%llu box %ux%u", (int)r,
+                  (unsigned long long)inner, (unsigned long long)outer, box_inner, box_outer);
+        return QN_ECUDA;
+    }
+    return QN_OK;
+}
+
+bool tc_supported(int device) {
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, device) != cudaSuccess) return false;
+    return p.major == 10 && p.minor == 3;
+}
+
+template <int BK>
+static size_t smem_bytes(int BN, int stages, int P) {
+    const size_t stage = (size_t)(2 * BM + 2 * BN) * BK * 2;
+    return 1024 + stage * stages + kCtrlBytes + (size_t)P * 4;
+}
+
+int tc_plan_create(TcPlan **out, int n, int P, int dim, __nv_bfloat16 *bufs_hi[2],
+                   __nv_bfloat16 *bufs_lo[2], const __nv_bfloat16 *S_hi, const __nv_bfloat16 *S_lo,
+                   const __nv_bfloat16 *Si_hi, const __nv_bfloat16 *Si_lo, int num_sms) {
+    TcPlan *p = (TcPlan *)calloc(1, sizeof(TcPlan));
+    if (!p) return QN_ENOMEM;
+    p->n = n;
+    p->P = P;
+    p->dim = dim;
+    p->Mtot = (dim == 3) ? P * P : P;
+    p->BN = P <= 256 ? P : 256;
+    p->ntile_n = (P + p->BN - 1) / p->BN;
+    p->ntile_m = (p->Mtot + BM - 1) / BM;
+    p->ntiles = p->ntile_n * p->ntile_m;
+    int cols = 32;
+    while (cols < 2 * p->BN) cols <<= 1;
+    p->tmem_cols = cols;
+    const char *bk_env = getenv("QN_TC_BK");
+    p->BK = (bk_env && atoi(bk_env) == 32) ? 32 : 64;
+    const size_t budget = 227 * 1024;
+    int stages = kMaxStages;
+    while (stages > 2 && (p->BK == 64 ? smem_bytes<64>(p->BN, stages, P) : smem_bytes<32>(p->BN, stages, P)) > budget)
+        --stages;
+    const char *st_env = getenv("QN_TC_STAGES");
+    if (st_env && atoi(st_env) >= 2 && atoi(st_env) < stages) stages = atoi(st_env);
+    p->stages = stages;
+    p->smem = p->BK == 64 ? smem_bytes<64>(p->BN, stages, P) : smem_bytes<32>(p->BN, stages, P);
+    if (p->smem > budget) {
+        set_error("tensor-core plan needs %zu B of shared memory", p->smem);
+        free(p);
+        return QN_EUNSUPPORTED;
+    }
+    p->grid = p->ntiles < num_sms ? p->ntiles : num_sms;
+    int rc = QN_OK;
+    for (int b = 0; b < 2 && rc == QN_OK; ++b) {
+        p->bufs_hi[b] = bufs_hi[b];
+        p->bufs_lo[b] = bufs_lo[b];
+        rc = encode_2d(&p->a_hi[b], bufs_hi[b], P, p->Mtot, p->BK, BM, p->BK);
+        if (rc == QN_OK) rc = encode_2d(&p->a_lo[b], bufs_lo[b], P, p->Mtot, p->BK, BM, p->BK);
+    }
+    if (rc == QN_OK) rc = encode_2d(&p->s_hi, S_hi, P, P, p->BK, p->BN, p->BK);
+    if (rc == QN_OK) rc = encode_2d(&p->s_lo, S_lo, P, P, p->BK, p->BN, p->BK);
+    if (rc == QN_OK) rc = encode_2d(&p->si_hi, Si_hi, P, P, p->BK, p->BN, p->BK);
+    if (rc == QN_OK) rc = encode_2d(&p->si_lo, Si_lo, P, P, p->BK, p->BN, p->BK);
+    if (rc != QN_OK) {
+        free(p);
+        return rc;
+    }
+    *out = p;
+    return QN_OK;
+}
+
+void tc_plan_destroy(TcPlan *plan) { free(plan); }
+
+template <int BK, int EPI, int DIM>
+static int launch_t(TcPlan *p, const CUtensorMap &a_hi, const CUtensorMap &a_lo, const CUtensorMap &b_hi,
+                    const CUtensorMap &b_lo, const TcArgs &args, cudaStream_t s) {
+    auto kern = k_modeprod_tc<BK, EPI, DIM>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        QN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr_set = true;
+    }
+    kern<<<p->grid, kThreads, p->smem, s>>>(a_hi, a_lo, b_hi, b_lo, args);
+    QN_CUDA(cudaGetLastError());
+    return QN_OK;
+}
+
+template <int BK>
+static int launch_bk(TcPlan *p, const CUtensorMap &a_hi, const CUtensorMap &a_lo, const CUtensorMap &b_hi,
+                     const CUtensorMap &b_lo, Epi epi, const TcArgs &args, cudaStream_t s) {
+    if (p->dim == 3) {
+        switch (epi) {
+            case EPI_STORE: return launch_t<BK, EPI_STORE, 3>(p, a_hi, a_lo, b_hi, b_lo, args, s);
+            case EPI_DIVIDE: return launch_t<BK, EPI_DIVIDE, 3>(p, a_hi, a_lo, b_hi, b_lo, args, s);
+            case EPI_UPDATE: return launch_t<BK, EPI_UPDATE, 3>(p, a_hi, a_lo, b_hi, b_lo, args, s);
+            case EPI_DENSE: return launch_t<BK, EPI_DENSE, 3>(p, a_hi, a_lo, b_hi, b_lo, args, s);
+        }
+    } else {
+        switch (epi) {
+            case EPI_STORE: return launch_t<BK, EPI_STORE, 2>(p, a_hi, a_lo, b_hi, b_lo, args, s);
+            case EPI_DIVIDE: return launch_t<BK, EPI_DIVIDE, 2>(p, a_hi, a_lo, b_hi, b_lo, args, s);
+            case EPI_UPDATE: return launch_t<BK, EPI_UPDATE, 2>(p, a_hi, a_lo, b_hi, b_lo, args, s);
+            case EPI_DENSE: return launch_t<BK, EPI_DENSE, 2>(p, a_hi, a_lo, b_hi, b_lo, args, s);
+        }
+    }
+    return QN_EINVAL;
+}
+
+int launch_modeprod_tc(TcPlan *p, int src, int dst, bool forward, Epi epi, const EpiArgs &e,
+                       cudaStream_t s) {
+    TcArgs args;
+    args.Mtot = p->Mtot;
+    args.P = p->P;
+    args.n = p->n;
+    args.BN = p->BN;
+    args.ntile_n = p->ntile_n;
+    args.ntiles = p->ntiles;
+    args.tmem_cols = p->tmem_cols;
+    args.stages = p->stages;
+    args.out_hi = (dst >= 0) ? p->bufs_hi[dst] : nullptr;
+    args.out_lo = (dst >= 0) ? p->bufs_lo[dst] : nullptr;
+    args.e = e;
+    const CUtensorMap &b_hi = forward ? p->si_hi : p->s_hi;
+    const CUtensorMap &b_lo = forward ? p->si_lo : p->s_lo;
+    if (p->BK == 64) return launch_bk<64>(p, p->a_hi[src], p->a_lo[src], b_hi, b_lo, epi, args, s);
+    return launch_bk<32>(p, p->a_hi[src], p->a_lo[src], b_hi, b_lo, epi, args, s);
+}
+
+}  // namespace qn

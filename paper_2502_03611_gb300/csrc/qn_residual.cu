@@ -1,0 +1,221 @@
+// Residual F(U) = A_h vec(U) + lam U + b U^3 - f (Sec. 4 eq. F_u, with the
+// 5/7-point difference operator of Sec. 3.2 eq. fdm-discrete, Dirichlet 0)
+// fused with the reductions the iteration needs: sum F^2 and sum f^2 (stop
+// test) and min/max U^2 (beta_n = mid-range of diag(3 b U^2), Sec. 4
+// eq. identity-method). One pass over U and f; HBM-bound.
+//
+// Outputs, selected per launch:
+//   R64           dense FP64 residual (FP64 path, qn_residual)
+//   Rhi/Rlo       residual rounded to FP32 and split into BF16 hi + lo planes
+//                 on the zero-padded P^dim grid (input of the tensor-core
+//                 mode products; padded entries are written as 0)
+// Per-block partials go to a fixed-size array; a one-block finaliser reduces
+// them in a fixed order (deterministic) and decides beta_n and convergence on
+// the device.
+#include <math.h>
+
+#include "qn_internal.h"
+
+namespace qn {
+
+namespace {
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+struct Red4 {
+    double r2, f2, mn, mx;
+};
+
+__device__ __forceinline__ Red4 warp_reduce(Red4 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.r2 += __shfl_xor_sync(0xffffffffu, v.r2, o);
+        v.f2 += __shfl_xor_sync(0xffffffffu, v.f2, o);
+        v.mn = fmin(v.mn, __shfl_xor_sync(0xffffffffu, v.mn, o));
+        v.mx = fmax(v.mx, __shfl_xor_sync(0xffffffffu, v.mx, o));
+    }
+    return v;
+}
+
+// Reduce over the block (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
+__device__ Red4 block_reduce(Red4 v) {
+    __shared__ Red4 sh[32];
+    v = warp_reduce(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    if (w == 0) {
+        v = (l < nw) ? sh[l] : Red4{0.0, 0.0, INFINITY, 0.0};
+        v = warp_reduce(v);
+    }
+    return v;
+}
+
+template <int DIM, bool SPLIT>
+__global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
+    if (a.done != nullptr && *(volatile const int *)a.done) return;
+    const int n = a.n;
+    const int P = SPLIT ? a.P : n;
+    const long long rows = (DIM == 3) ? (long long)P * P : (long long)P;
+    const double *__restrict__ U = a.U;
+    const double *__restrict__ f = a.f;
+    const long long nn = (long long)n * n;
+    Red4 acc{0.0, 0.0, INFINITY, 0.0};
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int y = (DIM == 3) ? (int)(row % P) : (int)row;
+        const int z = (DIM == 3) ? (int)(row / P) : 0;
+        const bool row_ok = (y < n) && (z < n);
+        for (int x = threadIdx.x; x < P; x += blockDim.x) {
+            double r = 0.0;
+            if (row_ok && x < n) {
+                const long long c = ((long long)z * n + y) * n + x;
+                const double u = __ldg(U + c);
+                double nb = 0.0;
+                if (x > 0) nb += __ldg(U + c - 1);
+                if (x < n - 1) nb += __ldg(U + c + 1);
+                if (y > 0) nb += __ldg(U + c - n);
+                if (y < n - 1) nb += __ldg(U + c + n);
+                if (DIM == 3) {
+                    if (z > 0) nb += __ldg(U + c - nn);
+                    if (z < n - 1) nb += __ldg(U + c + nn);
+                }
+                const double fv = __ldg(f + c);
+                r = (2.0 * DIM * u - nb) * a.inv_h2 + a.lam * u + a.b * u * u * u - fv;
+                const double u2 = u * u;
+                acc.r2 = fma(r, r, acc.r2);
+                acc.f2 = fma(fv, fv, acc.f2);
+                acc.mn = fmin(acc.mn, u2);
+                acc.mx = fmax(acc.mx, u2);
+                if (a.R64 != nullptr) a.R64[c] = r;
+            }
+            if (SPLIT) {
+                __nv_bfloat16 hi, lo;
+                split_bf16((float)r, hi, lo);
+                const long long o = row * P + x;
+                a.Rhi[o] = hi;
+                a.Rlo[o] = lo;
+            }
+        }
+    }
+    acc = block_reduce(acc);
+    if (threadIdx.x == 0) {
+        double *p = a.partials + 4ll * blockIdx.x;
+        p[0] = acc.r2;
+        p[1] = acc.f2;
+        p[2] = acc.mn;
+        p[3] = acc.mx;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_finalize(const double *partials, int nparts, DevState *st,
+                                                  qn_stats *hist, int hist_cap, double b,
+                                                  double lam, int update_state) {
+    if (update_state && *(volatile int *)&st->done) return;
+    Red4 acc{0.0, 0.0, INFINITY, 0.0};
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        acc.r2 += partials[4 * i + 0];
+        acc.f2 += partials[4 * i + 1];
+        acc.mn = fmin(acc.mn, partials[4 * i + 2]);
+        acc.mx = fmax(acc.mx, partials[4 * i + 3]);
+    }
+    acc = block_reduce(acc);
+    if (threadIdx.x != 0) return;
+    const double res = sqrt(acc.r2);
+    const double fn = sqrt(acc.f2);
+    const double fa = 3.0 * b * acc.mn, fb = 3.0 * b * acc.mx;
+    const double fu_min = fmin(fa, fb), fu_max = fmax(fa, fb);
+    const double beta = (st->beta_mode == QN_BETA_FIXED) ? st->beta_value : 0.5 * (fu_min + fu_max);
+    double rel;
+    if (fn > 0.0)
+        rel = res / fn;
+    else
+        rel = (res == 0.0) ? 0.0 : INFINITY;
+    const int it = st->it;
+    if (hist != nullptr && it >= 0 && it < hist_cap) {
+        qn_stats s;
+        s.res_norm = res;
+        s.f_norm = fn;
+        s.fu_min = fu_min;
+        s.fu_max = fu_max;
+        s.beta = beta;
+        s.rel = rel;
+        hist[it] = s;
+    }
+    if (!update_state) return;
+    st->beta = beta;
+    st->shift = lam + beta;
+    if (rel <= st->tol) {
+        st->status = QN_OK;
+        st->done = 1;
+    } else if (!isfinite(rel) || rel > 1e8 || !isfinite(beta)) {
+        st->status = QN_EDIVERGED;
+        st->done = 1;
+    } else if (it >= st->max_it) {
+        st->status = QN_ENOTCONV;
+        st->done = 1;
+    } else {
+        st->it = it + 1;   // the update about to run produces iterate it+1
+    }
+}
+
+// Dense FP64 field -> FP32 -> BF16 hi/lo planes on the zero-padded P^dim grid.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_split_pad(const double *__restrict__ r, int n, int P,
+                                                   __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+    const long long total = (DIM == 3) ? (long long)P * P * P : (long long)P * P;
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
+         o += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(o % P);
+        const long long row = o / P;
+        const int y = (int)(row % P);
+        const int z = (DIM == 3) ? (int)(row / P) : 0;
+        double v = 0.0;
+        if (x < n && y < n && z < n) v = r[((long long)z * n + y) * n + x];
+        __nv_bfloat16 h, l;
+        split_bf16((float)v, h, l);
+        hi[o] = h;
+        lo[o] = l;
+    }
+}
+
+}  // namespace
+
+int launch_split_pad(const double *r, int n, int P, int dim, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                     int grid, cudaStream_t s) {
+    if (dim == 3)
+        k_split_pad<3><<<grid, 256, 0, s>>>(r, n, P, hi, lo);
+    else
+        k_split_pad<2><<<grid, 256, 0, s>>>(r, n, P, hi, lo);
+    QN_CUDA(cudaGetLastError());
+    return QN_OK;
+}
+
+int launch_residual(const ResidualArgs &a, int grid, cudaStream_t s) {
+    const bool split = a.Rhi != nullptr;
+    if (a.dim == 3) {
+        if (split)
+            k_residual<3, true><<<grid, 256, 0, s>>>(a);
+        else
+            k_residual<3, false><<<grid, 256, 0, s>>>(a);
+    } else {
+        if (split)
+            k_residual<2, true><<<grid, 256, 0, s>>>(a);
+        else
+            k_residual<2, false><<<grid, 256, 0, s>>>(a);
+    }
+    QN_CUDA(cudaGetLastError());
+    return QN_OK;
+}
+
+int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *hist,
+                        int hist_cap, double b, double lam, int update_state, cudaStream_t s) {
+    k_finalize<<<1, 256, 0, s>>>(partials, nparts, st, hist, hist_cap, b, lam, update_state);
+    QN_CUDA(cudaGetLastError());
+    return QN_OK;
+}
+
+}  // namespace qn

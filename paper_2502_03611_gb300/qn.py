@@ -1,0 +1,267 @@
+"""Thin Python binding of libqn (include/qn.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels. PyTorch supplies device memory and the current CUDA stream.
+The functions carry the C-ABI names; a missing library is a hard error.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqn.so")
+
+QN_OK = 0
+QN_EINVAL = -1
+QN_ENOMEM = -2
+QN_ECUDA = -3
+QN_ENOTCONV = -4
+QN_EDIVERGED = -5
+QN_ETIMEOUT = -6
+QN_EUNSUPPORTED = -7
+
+QN_BC_DIRICHLET = 0
+QN_PREC_FP64 = 0
+QN_PREC_BF16X3 = 1
+QN_BETA_PAPER = 0
+QN_BETA_FIXED = 1
+
+PRECISIONS = {"fp64": QN_PREC_FP64, "bf16x3": QN_PREC_BF16X3}
+
+
+class QnProblem(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("bc", ctypes.c_int),
+                ("precision", ctypes.c_int), ("lam", ctypes.c_double), ("b", ctypes.c_double)]
+
+
+class QnStats(ctypes.Structure):
+    _fields_ = [("res_norm", ctypes.c_double), ("f_norm", ctypes.c_double),
+                ("fu_min", ctypes.c_double), ("fu_max", ctypes.c_double),
+                ("beta", ctypes.c_double), ("rel", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class QnOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_it", ctypes.c_int), ("beta_mode", ctypes.c_int),
+                ("beta_value", ctypes.c_double), ("step", ctypes.c_double),
+                ("sync_every", ctypes.c_int)]
+
+
+class QnResult(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("rel", ctypes.c_double)]
+
+
+class QnProfile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong),
+                ("residual_launches", ctypes.c_int), ("residual_ms", ctypes.c_double),
+                ("finalize_launches", ctypes.c_int), ("finalize_ms", ctypes.c_double),
+                ("modeprod_launches", ctypes.c_int), ("modeprod_ms", ctypes.c_double),
+                ("mp_store_launches", ctypes.c_int), ("mp_store_ms", ctypes.c_double),
+                ("mp_divide_launches", ctypes.c_int), ("mp_divide_ms", ctypes.c_double),
+                ("mp_last_launches", ctypes.c_int), ("mp_last_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class QnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libqn error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libqn.so (built by paper_2502_03611_gb300.build). No fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libqn.so not found at {path}: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "qn_version": (ctypes.c_int, []),
+        "qn_last_error": (ctypes.c_char_p, []),
+        "qn_setup_1d_eig": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, D, D, D]),
+        "qn_ctx_create": (ctypes.c_int, [ctypes.POINTER(QnProblem), ctypes.POINTER(P)]),
+        "qn_ctx_destroy": (ctypes.c_int, [P]),
+        "qn_residual": (ctypes.c_int, [P, P, P, P, ctypes.POINTER(QnStats), P]),
+        "qn_fast_diag_solve": (ctypes.c_int, [P, P, P, ctypes.c_double, P]),
+        "qn_step": (ctypes.c_int, [P, P, P, ctypes.c_double, ctypes.POINTER(QnStats), P]),
+        "qn_solve": (ctypes.c_int, [P, P, P, ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult),
+                                    ctypes.POINTER(QnStats), ctypes.c_int, P]),
+        "qn_solve_host": (ctypes.c_int, [P, P, P, ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult),
+                                         ctypes.POINTER(QnStats), ctypes.c_int, P]),
+        "qn_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
+        "qn_profile_read": (ctypes.c_int, [P, ctypes.POINTER(QnProfile)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc, allowed=(QN_OK,)):
+    if rc not in allowed:
+        raise QnError(rc, load_library().qn_last_error().decode())
+    return rc
+
+
+def qn_version() -> int:
+    return load_library().qn_version()
+
+
+def qn_last_error() -> str:
+    return load_library().qn_last_error().decode()
+
+
+def qn_setup_1d_eig(n: int, h: float | None = None, bc: int = QN_BC_DIRICHLET):
+    """Host 1-D diagonalisation; returns numpy (S, S_inv, lam)."""
+    lib = load_library()
+    h = 1.0 / (n + 1) if h is None else h
+    S = np.empty((n, n))
+    Si = np.empty((n, n))
+    lam = np.empty(n)
+    D = ctypes.POINTER(ctypes.c_double)
+    _check(lib.qn_setup_1d_eig(n, h, bc, S.ctypes.data_as(D), Si.ctypes.data_as(D), lam.ctypes.data_as(D)))
+    return S, Si, lam
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, numel, name):
+    import torch
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class QnContext:
+    """Owns a qn_ctx (qn_ctx_create / qn_ctx_destroy)."""
+
+    def __init__(self, dim: int, n: int, precision: str | int = "fp64", lam: float = 0.0,
+                 b: float = 1.0, bc: int = QN_BC_DIRICHLET):
+        lib = load_library()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.problem = QnProblem(dim, n, bc, prec, lam, b)
+        self.dim, self.n, self.precision = dim, n, prec
+        self.numel = n ** dim
+        h = ctypes.c_void_p()
+        _check(lib.qn_ctx_create(ctypes.byref(self.problem), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().qn_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def qn_ctx_create(dim, n, precision="fp64", lam=0.0, b=1.0, bc=QN_BC_DIRICHLET) -> QnContext:
+    return QnContext(dim, n, precision, lam, b, bc)
+
+
+def qn_ctx_destroy(ctx: QnContext):
+    ctx.close()
+
+
+def qn_residual(ctx: QnContext, U, f, R=None, stream=None) -> dict:
+    st = QnStats()
+    _check(load_library().qn_residual(ctx.handle, _dptr(U, ctx.numel, "U"), _dptr(f, ctx.numel, "f"),
+                                      _dptr(R, ctx.numel, "R"), ctypes.byref(st), _stream_ptr(stream)))
+    return st.as_dict()
+
+
+def qn_fast_diag_solve(ctx: QnContext, r, V, shift: float, stream=None):
+    _check(load_library().qn_fast_diag_solve(ctx.handle, _dptr(r, ctx.numel, "r"), _dptr(V, ctx.numel, "V"),
+                                             float(shift), _stream_ptr(stream)))
+
+
+def qn_step(ctx: QnContext, U, f, beta: float = math.nan, stream=None) -> dict:
+    st = QnStats()
+    _check(load_library().qn_step(ctx.handle, _dptr(U, ctx.numel, "U"), _dptr(f, ctx.numel, "f"),
+                                  float(beta), ctypes.byref(st), _stream_ptr(stream)))
+    return st.as_dict()
+
+
+def make_opts(tol=1e-10, max_it=200, beta=None, step=1.0, sync_every=2) -> QnOpts:
+    if beta is None:
+        return QnOpts(tol, max_it, QN_BETA_PAPER, 0.0, step, sync_every)
+    return QnOpts(tol, max_it, QN_BETA_FIXED, float(beta), step, sync_every)
+
+
+def qn_solve(ctx: QnContext, U, f, tol=1e-10, max_it=200, beta=None, step=1.0, sync_every=2,
+             history_len=0, stream=None, check=True):
+    """Returns (result dict, list of per-iterate stats dicts)."""
+    opts = make_opts(tol, max_it, beta, step, sync_every)
+    res = QnResult()
+    hist = (QnStats * history_len)() if history_len > 0 else None
+    rc = load_library().qn_solve(ctx.handle, _dptr(U, ctx.numel, "U"), _dptr(f, ctx.numel, "f"),
+                                 ctypes.byref(opts), ctypes.byref(res), hist, history_len,
+                                 _stream_ptr(stream))
+    if check:
+        _check(rc, allowed=(QN_OK, QN_ENOTCONV, QN_EDIVERGED))
+    out = {"iterations": res.iterations, "status": res.status, "rel": res.rel, "rc": rc}
+    n_h = min(res.iterations + 1, history_len) if rc in (QN_OK, QN_ENOTCONV, QN_EDIVERGED) else 0
+    return out, [hist[i].as_dict() for i in range(n_h)] if hist is not None else []
+
+
+def qn_solve_host(ctx: QnContext, U_host: np.ndarray, f_host: np.ndarray, tol=1e-10, max_it=200,
+                  beta=None, step=1.0, sync_every=2, stream=None):
+    """Solve with host arrays (copies inside the call). U_host is updated in place."""
+    for name, a in (("U_host", U_host), ("f_host", f_host)):
+        if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != ctx.numel:
+            raise ValueError(f"{name} must be a C-contiguous float64 array of {ctx.numel} values")
+    opts = make_opts(tol, max_it, beta, step, sync_every)
+    res = QnResult()
+    rc = load_library().qn_solve_host(ctx.handle, ctypes.c_void_p(U_host.ctypes.data),
+                                      ctypes.c_void_p(f_host.ctypes.data), ctypes.byref(opts),
+                                      ctypes.byref(res), None, 0, _stream_ptr(stream))
+    _check(rc, allowed=(QN_OK, QN_ENOTCONV, QN_EDIVERGED))
+    return {"iterations": res.iterations, "status": res.status, "rel": res.rel, "rc": rc}
+
+
+def qn_profile_enable(ctx: QnContext, on: bool = True):
+    _check(load_library().qn_profile_enable(ctx.handle, 1 if on else 0))
+
+
+def qn_profile_read(ctx: QnContext) -> dict:
+    p = QnProfile()
+    _check(load_library().qn_profile_read(ctx.handle, ctypes.byref(p)))
+    return p.as_dict()

@@ -1,0 +1,88 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+entry point include/qn.h declares, its host-only 1-D diagonalisation matches
+the oracle, and argument validation fails before anything is launched."""
+import math
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qn.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2502_03611_gb300 import build as B
+    from paper_2502_03611_gb300 import qn
+    B.build()
+    return qn.load_library()
+
+
+def declared_entry_points():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qn_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_core_calls():
+    names = declared_entry_points()
+    for want in ("qn_setup_1d_eig", "qn_residual", "qn_step", "qn_solve", "qn_ctx_create",
+                 "qn_fast_diag_solve"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2502_03611_gb300 import qn
+    out = subprocess.run(["nm", "-D", "--defined-only", qn.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\sT\s(qn_[a-z0-9_]+)", out))
+    missing = [s for s in declared_entry_points() if s not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    for s in declared_entry_points():
+        assert hasattr(lib, s)
+
+
+def test_version(lib):
+    from paper_2502_03611_gb300 import qn
+    assert qn.qn_version() >= 10000
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 63, 255, 511])
+def test_setup_1d_eig_matches_oracle(lib, n):
+    import oracle as O
+    from paper_2502_03611_gb300 import qn
+    S, Si, lam = qn.qn_setup_1d_eig(n)
+    So, _, lamo = O.eig_1d(n)
+    assert np.abs(lam - lamo).max() <= 1e-12 * lamo.max()
+    # eigenvectors are unique up to sign: compare |<s_k, o_k>| = 1 and validity
+    dots = np.abs(np.sum(S * So, axis=0))
+    assert np.abs(dots - 1.0).max() < 1e-10
+    assert np.abs(Si @ S - np.eye(n)).max() < 1e-12
+    H = O.fd_matrix_1d(n)
+    assert np.abs(H @ S - S * lam[None, :]).max() < 1e-12 * lam.max()
+
+
+def test_setup_rejects_bad_arguments(lib):
+    from paper_2502_03611_gb300 import qn
+    D = __import__("ctypes").POINTER(__import__("ctypes").c_double)
+    assert lib.qn_setup_1d_eig(0, 0.5, 0, None, None, None) == qn.QN_EINVAL
+    assert lib.qn_setup_1d_eig(7, 0.1, 0, None, None, None) == qn.QN_EINVAL   # h != 1/(n+1)
+    assert lib.qn_setup_1d_eig(7, 0.125, 1, None, None, None) == qn.QN_EUNSUPPORTED
+    assert "h=" in qn.qn_last_error() or "QN_BC" in qn.qn_last_error()
+
+
+def test_ctx_create_validates_before_cuda(lib):
+    import ctypes
+    from paper_2502_03611_gb300 import qn
+    h = ctypes.c_void_p()
+    for prob in (qn.QnProblem(4, 10, 0, 0, 0.0, 1.0), qn.QnProblem(3, 0, 0, 0, 0.0, 1.0),
+                 qn.QnProblem(3, 2000, 0, 0, 0.0, 1.0), qn.QnProblem(3, 10, 0, 9, 0.0, 1.0),
+                 qn.QnProblem(3, 10, 0, 0, math.inf, 1.0)):
+        assert lib.qn_ctx_create(ctypes.byref(prob), ctypes.byref(h)) == qn.QN_EINVAL
+    assert lib.qn_ctx_create(None, ctypes.byref(h)) == qn.QN_EINVAL
+    assert lib.qn_residual(None, None, None, None, None, None) == qn.QN_EINVAL
+    assert lib.qn_solve(None, None, None, None, None, None, 0, None) == qn.QN_EINVAL
+    assert lib.qn_ctx_destroy(None) == qn.QN_OK

@@ -1,0 +1,293 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Tolerances:
+* FP64 path: operators to 1e-12 relative (same arithmetic, different
+  summation order); solves: same iteration count (+-1 allowed only when the
+  oracle's last relative residual lies within 5 % of the tolerance), final
+  relative residual <= 1e-10, max|U_gpu - U_oracle| <= 1e-9 max|U_oracle|.
+* BF16X3 path: one shifted inverse carries the error of six split products
+  (each ~2^-16 relative from the dropped lo*lo term and the BF16 rounding of
+  the stored intermediates, plus FP32 accumulation over K <= 512 terms), so a
+  single inverse is checked to 3e-4 of max|V|; a solve must still reach the
+  FP64 residual tolerance 1e-10 and the oracle's solution to 1e-9 max|U|,
+  because the residual and update are FP64 (iterative refinement).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2502_03611_gb300.inputs import manufactured_problem, random_field
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qn():
+    import torch  # noqa: F401
+    from paper_2502_03611_gb300 import build as B
+    from paper_2502_03611_gb300 import qn as Q
+    B.build()
+    Q.load_library()
+    return Q
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+# --------------------------------------------------------------------------------------------
+# residual
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,n", [(2, 1), (2, 63), (2, 100), (3, 1), (3, 17), (3, 64), (3, 65)])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_residual_matches_oracle(qn, dim, n, prec):
+    import torch
+    U = random_field((n,) * dim, seed=n + dim)
+    f = random_field((n,) * dim, seed=7 * n + dim) * 50.0
+    lam, b = 0.3, 1.7
+    ctx = qn.QnContext(dim, n, prec, lam=lam, b=b)
+    R = torch.empty(n ** dim, dtype=torch.float64, device="cuda")
+    st = qn.qn_residual(ctx, dev(U).reshape(-1), dev(f).reshape(-1), R)
+    want = O.residual(U, f, lam, b)
+    got = host(R).reshape(want.shape)
+    scale = np.abs(want).max() + (2 * dim) * (n + 1) ** 2 * np.abs(U).max()
+    assert np.abs(got - want).max() <= 1e-13 * scale
+    assert st["res_norm"] == pytest.approx(np.linalg.norm(want), rel=1e-12)
+    assert st["f_norm"] == pytest.approx(np.linalg.norm(f), rel=1e-12)
+    d = O.jacobian_diag(U, b)
+    assert st["fu_min"] == pytest.approx(d.min(), rel=1e-14, abs=1e-300)
+    assert st["fu_max"] == pytest.approx(d.max(), rel=1e-14)
+    assert st["beta"] == pytest.approx(O.beta_rule(U, b), rel=1e-14)
+
+
+# --------------------------------------------------------------------------------------------
+# shifted inverse (forward mode products, divide, backward mode products)
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,n", [(2, 1), (2, 63), (2, 64), (2, 130), (3, 1), (3, 7), (3, 33),
+                                   (3, 64), (3, 65), (3, 127)])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("shift", [0.0, 12.5])
+def test_fast_diag_solve_matches_oracle(qn, dim, n, prec, shift):
+    import torch
+    r = random_field((n,) * dim, seed=31 + n, lo=-10.0, hi=10.0)
+    ctx = qn.QnContext(dim, n, prec)
+    V = torch.empty(n ** dim, dtype=torch.float64, device="cuda")
+    qn.qn_fast_diag_solve(ctx, dev(r).reshape(-1), V, shift)
+    S, Si, lam = O.eig_1d(n)
+    want = O.fast_diag_solve(r, S, Si, lam, shift)
+    got = host(V).reshape(want.shape)
+    tol = 1e-12 if prec == "fp64" else 3e-4
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err <= tol, err
+
+
+# --------------------------------------------------------------------------------------------
+# one quasi-Newton step
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,n", [(2, 63), (3, 31)])
+@pytest.mark.parametrize("beta", [None, 4.0])
+def test_step_matches_oracle(qn, dim, n, beta):
+    u, f = manufactured_problem(n, dim, seed=3)
+    U0 = 0.5 * u
+    ctx = qn.QnContext(dim, n, "fp64")
+    Ud = dev(U0).reshape(-1)
+    st = qn.qn_step(ctx, Ud, dev(f).reshape(-1), math.nan if beta is None else beta)
+    want, r, beta_used = O.qn_step(U0, f, beta=beta)
+    got = host(Ud).reshape(want.shape)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    assert st["beta"] == pytest.approx(beta_used, rel=1e-13)
+    assert st["res_norm"] == pytest.approx(np.linalg.norm(r), rel=1e-12)
+
+
+# --------------------------------------------------------------------------------------------
+# full solves
+# --------------------------------------------------------------------------------------------
+def _solve_pair(qn, dim, n, seed, prec, max_it=200):
+    import torch
+    u, f = manufactured_problem(n, dim, seed=seed)
+    ctx = qn.QnContext(dim, n, prec)
+    U = torch.zeros(n ** dim, dtype=torch.float64, device="cuda")
+    res, hist = qn.qn_solve(ctx, U, dev(f).reshape(-1), tol=1e-10, max_it=max_it, history_len=max_it + 1)
+    Uo, ho, ok = O.qn_solve(f, tol=1e-10, max_it=max_it)
+    assert ok
+    return res, hist, host(U).reshape(f.shape), Uo, ho, f
+
+
+def _check_solution(res, Ug, Uo, f, hist_o):
+    assert res["status"] == 0, res
+    assert res["rel"] <= 1e-10
+    # the oracle's own residual of the GPU solution
+    rel = np.linalg.norm(O.residual(Ug, f)) / np.linalg.norm(f)
+    assert rel <= 1.05e-10, rel
+    assert np.abs(Ug - Uo).max() <= 1e-9 * np.abs(Uo).max()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4])
+def test_solve_2d_63_fp64(qn, seed):
+    res, hist, Ug, Uo, ho, f = _solve_pair(qn, 2, 63, seed, "fp64")
+    _check_solution(res, Ug, Uo, f, ho)
+    its_o = len(ho) - 1
+    near = ho[-2]["rel"] <= 1.05e-10 if len(ho) > 1 else False
+    assert res["iterations"] == its_o or (near and abs(res["iterations"] - its_o) <= 1)
+    # per-iterate history agrees with the oracle's
+    for a, b in zip(hist, ho):
+        assert a["rel"] == pytest.approx(b["rel"], rel=1e-6, abs=1e-13)
+        assert a["beta"] == pytest.approx(b["beta"], rel=1e-9, abs=1e-12)
+
+
+@pytest.mark.parametrize("n", [1, 15, 33, 65])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_solve_3d_small(qn, n, prec):
+    res, hist, Ug, Uo, ho, f = _solve_pair(qn, 3, n, 0, prec)
+    _check_solution(res, Ug, Uo, f, ho)
+    its_o = len(ho) - 1
+    if prec == "fp64":
+        assert abs(res["iterations"] - its_o) <= 1
+    else:
+        assert res["iterations"] <= its_o + 2
+
+
+@pytest.mark.parametrize("dim,n", [(2, 63), (2, 511), (3, 127)])
+def test_solve_bf16x3_matches_oracle(qn, dim, n):
+    res, hist, Ug, Uo, ho, f = _solve_pair(qn, dim, n, 1, "bf16x3")
+    _check_solution(res, Ug, Uo, f, ho)
+    assert res["iterations"] <= len(ho) - 1 + 2
+
+
+def test_solve_3d_255_fp64_full_size(qn):
+    res, hist, Ug, Uo, ho, f = _solve_pair(qn, 3, 255, 0, "fp64")
+    _check_solution(res, Ug, Uo, f, ho)
+    assert abs(res["iterations"] - (len(ho) - 1)) <= 1
+
+
+def test_solve_3d_511_bf16x3_full_size(qn):
+    """The benchmark workload. The oracle's full solve at 511^3 is too slow for a
+    test, so the GPU result is judged by properties that hold at any size: the
+    oracle's FP64 residual of the GPU solution is <= 1e-10 ||f||, and since
+    F(U) - F(U_h) = (A_h + diag(b(U^2 + U U_h + U_h^2))) (U - U_h) with the
+    diagonal >= 0, ||U - U_h||_2 <= ||F(U)||_2 / lambda_min(A_h)."""
+    import torch
+    n = 511
+    u, f = manufactured_problem(n, 3, seed=0)
+    ctx = qn.QnContext(3, n, "bf16x3")
+    U = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
+    res, hist = qn.qn_solve(ctx, U, dev(f).reshape(-1), tol=1e-10, max_it=60, history_len=61)
+    assert res["status"] == 0 and res["rel"] <= 1e-10
+    Ug = host(U).reshape(f.shape)
+    del U
+    r = O.residual(Ug, f)
+    rnorm = np.linalg.norm(r)
+    assert rnorm <= 1.05e-10 * np.linalg.norm(f)
+    lam_min = 3 * 4.0 * (n + 1) ** 2 * math.sin(math.pi / (2 * (n + 1))) ** 2
+    rms_err_bound = rnorm / lam_min / math.sqrt(Ug.size)
+    assert rms_err_bound <= 1e-9 * np.abs(Ug).max()
+    # discretisation error against the manufactured solution decays as O(h^2):
+    # halving h (255 -> 511 interior points) divides it by about 4
+    err511 = np.abs(Ug - u).max()
+    u255, f255 = manufactured_problem(255, 3, seed=0)
+    ctx255 = qn.QnContext(3, 255, "bf16x3")
+    U255 = torch.zeros(255 ** 3, dtype=torch.float64, device="cuda")
+    r255, _ = qn.qn_solve(ctx255, U255, dev(f255).reshape(-1))
+    assert r255["status"] == 0
+    err255 = np.abs(host(U255).reshape(u255.shape) - u255).max()
+    assert 3.6 < err255 / err511 < 4.4, (err255, err511)
+    # mesh-independent iteration count (the paper's Sec. 6 observation): same as at 127^3
+    _, ho_small, _ = O.qn_solve(manufactured_problem(127, 3, seed=0)[1])
+    assert abs(res["iterations"] - (len(ho_small) - 1)) <= 2
+
+
+def test_golden_2d_63(qn):
+    """Against stored oracle values (tests/golden/make_golden.py)."""
+    import json
+    import os
+    import torch
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "qn2d_n63_seed0.json")))
+    n = g["n"]
+    _, f = manufactured_problem(n, 2, seed=g["seed"])
+    ctx = qn.QnContext(2, n, "fp64")
+    U = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    res, hist = qn.qn_solve(ctx, U, dev(f).reshape(-1), history_len=64)
+    assert res["iterations"] == g["iterations"]
+    for a, want in zip(hist, g["rel_history"]):
+        assert a["rel"] == pytest.approx(want, rel=1e-6, abs=1e-13)
+    Ug = host(U).reshape(n, n)
+    for (y, x), want in zip(g["sample_index"], g["sample_value"]):
+        assert Ug[y, x] == pytest.approx(want, rel=1e-9, abs=1e-12)
+
+
+# --------------------------------------------------------------------------------------------
+# edge cases and error handling
+# --------------------------------------------------------------------------------------------
+def test_zero_source_converges_immediately(qn):
+    import torch
+    ctx = qn.QnContext(3, 9, "fp64")
+    U = torch.zeros(9 ** 3, dtype=torch.float64, device="cuda")
+    f = torch.zeros_like(U)
+    res, hist = qn.qn_solve(ctx, U, f, history_len=4)
+    assert res["status"] == 0 and res["iterations"] == 0 and res["rel"] == 0.0
+
+
+def test_not_converged_status(qn):
+    import torch
+    _, f = manufactured_problem(31, 3, seed=0)
+    ctx = qn.QnContext(3, 31, "fp64")
+    U = torch.zeros(31 ** 3, dtype=torch.float64, device="cuda")
+    res, hist = qn.qn_solve(ctx, U, dev(f).reshape(-1), max_it=2, history_len=3)
+    assert res["status"] == qn.QN_ENOTCONV and res["iterations"] == 2
+    # the iterate after 2 updates equals the oracle's
+    U2 = np.zeros_like(f)
+    for _ in range(2):
+        U2, _, _ = O.qn_step(U2, f)
+    assert np.abs(host(U).reshape(f.shape) - U2).max() <= 1e-12 * np.abs(U2).max()
+
+
+def test_nonfinite_source_reports_divergence(qn):
+    import torch
+    _, f = manufactured_problem(15, 3, seed=0)
+    f[3, 4, 5] = np.nan
+    ctx = qn.QnContext(3, 15, "bf16x3")
+    U = torch.zeros(15 ** 3, dtype=torch.float64, device="cuda")
+    res, _ = qn.qn_solve(ctx, U, dev(f).reshape(-1), max_it=5)
+    assert res["status"] == qn.QN_EDIVERGED
+
+
+def test_bad_arguments_rejected(qn):
+    import torch
+    ctx = qn.QnContext(2, 8, "fp64")
+    r = torch.zeros(64, dtype=torch.float64, device="cuda")
+    with pytest.raises(qn.QnError):
+        qn.qn_fast_diag_solve(ctx, r, r, 0.0)               # aliasing
+    with pytest.raises(qn.QnError):
+        qn.qn_fast_diag_solve(ctx, r, torch.zeros_like(r), -1e9)   # indefinite
+    with pytest.raises(qn.QnError):
+        qn.qn_solve(ctx, r, r.clone(), tol=-1.0)
+
+
+def test_deterministic(qn):
+    import torch
+    _, f = manufactured_problem(65, 3, seed=2)
+    outs = []
+    for _ in range(2):
+        ctx = qn.QnContext(3, 65, "bf16x3")
+        U = torch.zeros(65 ** 3, dtype=torch.float64, device="cuda")
+        qn.qn_solve(ctx, U, dev(f).reshape(-1))
+        outs.append(host(U))
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_solve_host_arrays(qn):
+    n = 33
+    u, f = manufactured_problem(n, 3, seed=4)
+    ctx = qn.QnContext(3, n, "bf16x3")
+    U = np.zeros(n ** 3)
+    res = qn.qn_solve_host(ctx, U, np.ascontiguousarray(f.reshape(-1)))
+    Uo, _, _ = O.qn_solve(f)
+    assert res["status"] == 0
+    assert np.abs(U.reshape(f.shape) - Uo).max() <= 1e-9 * np.abs(Uo).max()
