@@ -169,6 +169,26 @@ int qn_solve(qn_ctx *ctx, double *U, const double *f, const qn_opts *opts,
 int qn_solve_host(qn_ctx *ctx, double *U_host, const double *f_host, const qn_opts *opts,
                   qn_result *res, qn_stats *history, int history_len, void *stream);
 
+/* Allocation-free variant of qn_residual, for callers that cannot allocate
+ * device memory where they need a residual: their device memory is owned in
+ * full by another allocator or a fixed budget, or they run in a section that
+ * must not allocate. No context is needed and nothing is allocated; the
+ * paper has no counterpart to this entry point (it is a deployment aid).
+ * Computes the same F(U) = A_h vec(U) + lam U + b U^3 - f and statistics as
+ * qn_residual for a dim-D grid with n interior nodes per axis.
+ *   dim: 2 or 3. n: 1..1024 (larger n is rejected with QN_EINVAL).
+ *   U, f: device, n^dim doubles. R: device, n^dim doubles, or NULL.
+ *   st: host struct, required. Synchronises `stream`.
+ * Scratch: a fixed 33 KB device array inside libqn (4096 partial sums plus
+ * the solver state and one statistics record), present on every GPU that
+ * loads the library until the process exits. The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture. All calls share the one array, so
+ * calls that overlap on the GPU (other streams, other host threads) race;
+ * serialise them. Each call rewrites every scratch entry it reads. */
+int qn_residual_noalloc(int dim, int n, double lam, double b, const double *U, const double *f,
+                        double *R, qn_stats *st, void *stream);
+
 /* ---- measurement ------------------------------------------------------------- */
 typedef struct qn_profile {
     long long launches;       /* kernels launched that did work since qn_profile_enable

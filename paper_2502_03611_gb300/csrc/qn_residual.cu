@@ -13,6 +13,9 @@
 // them in a fixed order (deterministic) and decides beta_n and convergence on
 // the device.
 #include <math.h>
+#include <string.h>
+
+#include <mutex>
 
 #include "qn_internal.h"
 
@@ -218,4 +221,130 @@ int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *
     return QN_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free residual (qn_residual_noalloc)
+//
+// Some callers cannot allocate device memory where they call the residual:
+// their device memory is entirely owned by another allocator or a fixed
+// budget (a framework's memory pool, a service with a hard memory cap), or
+// they run in a section where allocation is not allowed. For them the
+// residual kernel's scratch (per-block partial sums and the finalised
+// statistics) lives in this fixed device array instead of a context's
+// workspace. Every GPU that loads libqn holds it until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxBlocks = 1024;               // reduction blocks per call
+constexpr int kNoAllocStateDoubles = 16;              // DevState (<= 128 B)
+constexpr int kNoAllocStatsDoubles = 8;               // one qn_stats (48 B)
+constexpr int kNoAllocDoubles = 4 * kNoAllocMaxBlocks + kNoAllocStateDoubles + kNoAllocStatsDoubles;
+static_assert(sizeof(DevState) <= kNoAllocStateDoubles * sizeof(double), "DevState too large");
+static_assert(sizeof(qn_stats) <= kNoAllocStatsDoubles * sizeof(double), "qn_stats too large");
+
+// 4096 partial-sum slots + solver state + one statistics record: 33 KB.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[128] = {nullptr};   // device address of the array, per device ordinal
+
+// Device address of g_noalloc_scratch on the current device (looked up once
+// per device; in host code the array's name is only a host-side stand-in).
+int noalloc_scratch(double **out) {
+    int dev = 0;
+    QN_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) {
+        set_error("qn_residual_noalloc: device ordinal %d out of range", dev);
+        return QN_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return QN_OK;
+}
+
+// Put the solver state in the scratch into "evaluate iterate 0, paper beta".
+__global__ void k_noalloc_prepare(DevState *st) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        st->done = 0;
+        st->status = QN_OK;
+        st->it = 0;
+        st->err = 0;
+        st->shift = 0.0;
+        st->beta = 0.0;
+        st->tol = -1.0;
+        st->max_it = 0;
+        st->beta_mode = QN_BETA_PAPER;
+        st->beta_value = 0.0;
+    }
+}
+
+}  // namespace
+
 }  // namespace qn
+
+extern "C" int qn_residual_noalloc(int dim, int n, double lam, double b, const double *U,
+                                   const double *f, double *R, qn_stats *st, void *stream) {
+    using namespace qn;
+    if (dim != 2 && dim != 3) {
+        set_error("qn_residual_noalloc: dim must be 2 or 3 (got %d)", dim);
+        return QN_EINVAL;
+    }
+    if (n < 1 || n > 1024) {
+        set_error("qn_residual_noalloc: n=%d exceeds the supported range 1..1024", n);
+        return QN_EINVAL;
+    }
+    if (!U || !f || !st) {
+        set_error("qn_residual_noalloc: U, f and st must be non-null");
+        return QN_EINVAL;
+    }
+    if (!isfinite(lam) || !isfinite(b)) {
+        set_error("qn_residual_noalloc: lam and b must be finite");
+        return QN_EINVAL;
+    }
+    const long long rows = (dim == 3) ? (long long)n * n : (long long)n;
+    const int grid = rows < kNoAllocMaxBlocks ? (int)rows : kNoAllocMaxBlocks;
+    if (grid > kNoAllocMaxBlocks) {   // cannot happen with n <= 1024; kept as the scratch guard
+        set_error("qn_residual_noalloc: %d reduction blocks exceed the scratch maximum %d", grid,
+                  kNoAllocMaxBlocks);
+        return QN_EINVAL;
+    }
+    double *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != QN_OK) return rc;
+    double *partials = scratch;
+    DevState *state = reinterpret_cast<DevState *>(scratch + 4 * kNoAllocMaxBlocks);
+    qn_stats *stats = reinterpret_cast<qn_stats *>(scratch + 4 * kNoAllocMaxBlocks + kNoAllocStateDoubles);
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // every partial slot read below is written by this call's residual
+    // blocks, so only the solver state needs resetting
+    k_noalloc_prepare<<<1, 32, 0, s>>>(state);
+    QN_CUDA(cudaGetLastError());
+    ResidualArgs a;
+    a.U = U;
+    a.f = f;
+    a.n = n;
+    a.dim = dim;
+    const double h = 1.0 / (n + 1);
+    a.inv_h2 = 1.0 / (h * h);
+    a.lam = lam;
+    a.b = b;
+    a.R64 = R;
+    a.Rhi = nullptr;
+    a.Rlo = nullptr;
+    a.P = n;
+    a.partials = partials;
+    a.done = nullptr;
+    rc = launch_residual(a, grid, s);
+    if (rc != QN_OK) return rc;
+    rc = launch_finalize(partials, grid, state, stats, 1, b, lam, 0, s);
+    if (rc != QN_OK) return rc;
+    QN_CUDA(cudaMemcpyAsync(st, stats, sizeof(qn_stats), cudaMemcpyDeviceToHost, s));
+    QN_CUDA(cudaStreamSynchronize(s));
+    return QN_OK;
+}
