@@ -371,6 +371,10 @@ static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double 
     }
     a.partials = c->partials;
     a.done = done;
+    // the split-precision solve only needs ||F|| to ~1e-7 for its stop test:
+    // its residual sums float(r)^2 (Kahan) instead of an FP64 FMA per point
+    a.fast = (to_work && c->prob.precision == QN_PREC_BF16X3) ? 1 : 0;
+    a.want_f2 = (!to_work || c->cur_iter == 0) ? 1 : 0;
     const long pr = prof_begin(c, PK_RESIDUAL, s);
     const int rc = launch_residual(a, c->nparts, s);
     prof_end(c, pr, s);
@@ -419,7 +423,8 @@ static int enqueue_iteration(qn_ctx *c, double *U, const double *f, double step,
     int rc = enqueue_residual(c, U, f, nullptr, true, &c->st->done, s);
     if (rc) return rc;
     const long pr = prof_begin(c, PK_FINALIZE, s);
-    rc = launch_finalize(c->partials, c->nparts, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 1, s);
+    rc = launch_finalize(c->partials, c->nparts, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 1,
+                         c->cur_iter > 0 ? 1 : 0, s);
     prof_end(c, pr, s);
     if (rc) return rc;
     return enqueue_inverse(c, nullptr, U, true, step, s);
@@ -455,7 +460,7 @@ extern "C" int qn_residual(qn_ctx *c, const double *U, const double *f, double *
     rc = enqueue_residual(c, U, f, R, false, nullptr, s);
     if (rc) return rc;
     const long pr = prof_begin(c, PK_FINALIZE, s);
-    rc = launch_finalize(c->partials, c->nparts, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 0, s);
+    rc = launch_finalize(c->partials, c->nparts, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 0, 0, s);
     prof_end(c, pr, s);
     if (rc) return rc;
     if (st) {
@@ -511,6 +516,7 @@ extern "C" int qn_step(qn_ctx *c, double *U, const double *f, double beta, qn_st
     const bool paper = isnan(beta);
     rc = reset_state(c, -1.0, 1, paper ? QN_BETA_PAPER : QN_BETA_FIXED, paper ? 0.0 : beta, s);
     if (rc) return rc;
+    c->cur_iter = 0;
     rc = enqueue_iteration(c, U, f, 1.0, s);
     if (rc) return rc;
     DevState h;

@@ -24,6 +24,7 @@ struct DevState {
     int max_it;
     int beta_mode;
     double beta_value;
+    double f_norm;   // ||f||_2, computed on the first iteration of a solve
 };
 
 // Residual kernel outputs.
@@ -38,6 +39,8 @@ struct ResidualArgs {
     int P;
     double *partials;          // [grid][4] : sum r^2, sum f^2, min U^2, max U^2
     const int *done;           // skip when *done != 0 (nullptr: never skip)
+    int fast;                  // 1: sum r^2 from float(r) (Kahan, FP32) -- inside the solve loop
+    int want_f2;               // 1: also sum f^2 (first iteration / standalone residual)
 };
 
 // Epilogue selector shared by both mode-product kernels.
@@ -72,7 +75,8 @@ struct GemmShape {
 // ---- launchers (implemented in the .cu files) ---------------------------------
 int launch_residual(const ResidualArgs &a, int grid, cudaStream_t s);
 int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *hist,
-                    int hist_cap, double b, double lam, int update_state, cudaStream_t s);
+                    int hist_cap, double b, double lam, int update_state, int use_saved_fnorm,
+                    cudaStream_t s);
 int launch_split_pad(const double *r, int n, int P, int dim, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
                      int grid, cudaStream_t s);
 int launch_modeprod_f64(const double *A, const double *B, double *out, const GemmShape &g,

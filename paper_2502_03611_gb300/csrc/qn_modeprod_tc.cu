@@ -13,13 +13,14 @@
 // to P = 64*ceil(n/64) points per axis (padded entries are zero, padded
 // eigenvalues are 1e30 so the divide keeps them zero).
 //
-// Kernel organisation (persistent, one CTA of 192 threads per SM):
+// Kernel organisation (persistent, one CTA of 320 threads per SM):
 //   warp 0 lane 0  TMA producer: A_hi, A_lo (128 x BK) and B_hi, B_lo (BN x BK)
 //                  tiles per pipeline stage, K-major with 128-B or 64-B swizzle
 //   warp 1         allocates TMEM (2 accumulators of BN FP32 columns); lane 0
 //                  issues tcgen05.mma (M=128, N=BN, K=16) and commits to mbarriers
-//   warps 2..5     epilogue: tcgen05.ld of the accumulator (warp w owns TMEM
-//                  lanes 32*(w%4)..+31 = rows), then store / divide / update
+//   warps 2..9     epilogue: tcgen05.ld of the accumulator (warp w owns TMEM
+//                  lanes 32*(w%4)..+31 = rows and one half of the BN columns),
+//                  then store / divide / update
 // Tiles are walked in m-major order (consecutive CTAs share the same A rows;
 // S stays resident in L2). The epilogue of tile i overlaps the MMAs of tile
 // i+1 through the double-buffered accumulators.
@@ -33,6 +34,7 @@
 #include <string.h>
 
 #include "qn_internal.h"
+#include "qn_numeric.cuh"
 #include "qn_ptx.cuh"
 
 namespace qn {
@@ -40,7 +42,8 @@ namespace qn {
 namespace {
 
 constexpr int BM = 128;
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;                       // two warps per TMEM lane quadrant
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kMaxStages = 8;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr uint32_t kCtrlBytes = 512;
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(tfull_bar(b), 1);
-            ptx::mbar_init(tempty_bar(b), 4);
+            ptx::mbar_init(tempty_bar(b), kEpiWarps);
         }
         ptx::mbar_init(mma_done_bar, 1);
         *abort_flag = 0;
@@ -229,7 +232,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         drain_bar(mma_done_bar, 0);
     } else if (warp >= 2) {
         // ------------------------------ epilogue ----------------------------------
-        const int q = warp & 3;
+        const int q = warp & 3;                          // TMEM lanes 32q..32q+31 = tile rows
+        const int half = (warp - 2) >> 2;                // which half of the BN columns
         const int row = q * 32 + lane;
         int acc = 0;
         uint32_t aph = 0;
@@ -263,29 +267,60 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             const long long kstride = (DIM == 3) ? (long long)n * n : (long long)n;
-            for (int c = 0; c < BN; c += 32) {
+            const int cbeg = half * (BN >> 1), cend = cbeg + (BN >> 1);
+            for (int c = cbeg; c < cend; c += 32) {
                 uint32_t r[32];
                 ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
                 ptx::tmem_ld_wait();
                 if (!m_ok) continue;
+                const int k0 = n0 + c;
+                if (EPI == EPI_STORE) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int k = n0 + c + i;
-                    const float v = __uint_as_float(r[i]);
-                    if (EPI == EPI_STORE) {
-                        if (k < P) split_store(v, args.out_hi, args.out_lo, (long long)k * Mtot + m);
-                    } else if (EPI == EPI_DIVIDE) {
+                    for (int i = 0; i < 32; ++i)
+                        if (k0 + i < P)
+                            split_store(__uint_as_float(r[i]), args.out_hi, args.out_lo, (long long)(k0 + i) * Mtot + m);
+                } else if (EPI == EPI_DIVIDE) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int k = k0 + i;
                         if (k < P) {
                             const float den = lam_s[k] + rowlam + shift;
-                            split_store(v / den, args.out_hi, args.out_lo, (long long)k * Mtot + m);
+                            split_store(__fdividef(__uint_as_float(r[i]), den), args.out_hi, args.out_lo,
+                                        (long long)k * Mtot + m);
                         }
-                    } else if (EPI == EPI_UPDATE) {
-                        if (ubase >= 0 && k < n) {
-                            double *u = args.e.U + (long long)k * kstride + ubase;
-                            *u = *u - (double)step * (double)v;
+                    }
+                } else if (EPI == EPI_UPDATE) {
+                    if (ubase >= 0) {
+                        // 16 loads of U in flight per thread before the stores,
+                        // instead of a serial read-modify-write
+                        double *ub = args.e.U + ubase;
+#pragma unroll
+                        for (int h = 0; h < 32; h += 16) {
+                            double old[16];
+#pragma unroll
+                            for (int i = 0; i < 16; ++i)
+                                old[i] = (k0 + h + i < n) ? ub[(long long)(k0 + h + i) * kstride] : 0.0;
+                            if (step == 1.0f) {
+#pragma unroll
+                                for (int i = 0; i < 16; ++i)
+                                    if (k0 + h + i < n)
+                                        ub[(long long)(k0 + h + i) * kstride] = old[i] - f2d_exact(__uint_as_float(r[h + i]));
+                            } else {
+                                const double st = (double)step;
+#pragma unroll
+                                for (int i = 0; i < 16; ++i)
+                                    if (k0 + h + i < n)
+                                        ub[(long long)(k0 + h + i) * kstride] =
+                                            fma(-st, f2d_exact(__uint_as_float(r[h + i])), old[i]);
+                            }
                         }
-                    } else {   // EPI_DENSE
-                        if (ubase >= 0 && k < n) args.e.U[(long long)k * kstride + ubase] = (double)v;
+                    }
+                } else {   // EPI_DENSE
+                    if (ubase >= 0) {
+                        double *ub = args.e.U + ubase;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (k0 + i < n) ub[(long long)(k0 + i) * kstride] = f2d_exact(__uint_as_float(r[i]));
                     }
                 }
             }

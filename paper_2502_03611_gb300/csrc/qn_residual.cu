@@ -18,6 +18,7 @@
 #include <mutex>
 
 #include "qn_internal.h"
+#include "qn_numeric.cuh"
 
 namespace qn {
 
@@ -58,7 +59,15 @@ __device__ Red4 block_reduce(Red4 v) {
     return v;
 }
 
-template <int DIM, bool SPLIT>
+// FP64-pipe budget per interior point (the GPU issues ~2 FP64 ops/clk/SM):
+// the stencil 2d*u - sum(neighbours) is summed exactly in fixed point on the
+// integer pipe (more accurate than an FP64 sum), leaving u^2, u^3, b u^3 - f
+// and lap/h^2 + (...) = 4 FP64 ops (+1 with lam != 0, +1 for sum f^2 on the
+// first iteration, +1 for sum r^2 outside the split-precision solve, whose
+// stop test sums float(r)^2 with Kahan in FP32). min/max |U| use the integer
+// bit pattern; the FP32 rounding of r runs on the integer pipe.
+// KIND 0: lam u + b u^3 (general); 1: lam = 0; 2: lam = 0 and b = 1 (3 FP64 ops).
+template <int DIM, bool SPLIT, bool FAST, int KIND>
 __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
     if (a.done != nullptr && *(volatile const int *)a.done) return;
     const int n = a.n;
@@ -67,43 +76,70 @@ __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
     const double *__restrict__ U = a.U;
     const double *__restrict__ f = a.f;
     const long long nn = (long long)n * n;
-    Red4 acc{0.0, 0.0, INFINITY, 0.0};
+    const bool want_f2 = a.want_f2 != 0;
+    double r2 = 0.0, f2 = 0.0;
+    float kr2 = 0.0f, kc = 0.0f;                          // Kahan sum of float(r)^2
+    unsigned long long amin = 0x7FFFFFFFFFFFFFFFull, amax = 0ull;
     for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
         const int y = (DIM == 3) ? (int)(row % P) : (int)row;
         const int z = (DIM == 3) ? (int)(row / P) : 0;
         const bool row_ok = (y < n) && (z < n);
+        const long long cbase = ((long long)z * n + y) * n;
         for (int x = threadIdx.x; x < P; x += blockDim.x) {
             double r = 0.0;
             if (row_ok && x < n) {
-                const long long c = ((long long)z * n + y) * n + x;
+                const long long c = cbase + x;
                 const double u = __ldg(U + c);
-                double nb = 0.0;
-                if (x > 0) nb += __ldg(U + c - 1);
-                if (x < n - 1) nb += __ldg(U + c + 1);
-                if (y > 0) nb += __ldg(U + c - n);
-                if (y < n - 1) nb += __ldg(U + c + n);
+                double nbv[2 * DIM];
+                nbv[0] = (x > 0) ? __ldg(U + c - 1) : 0.0;
+                nbv[1] = (x < n - 1) ? __ldg(U + c + 1) : 0.0;
+                nbv[2] = (y > 0) ? __ldg(U + c - n) : 0.0;
+                nbv[3] = (y < n - 1) ? __ldg(U + c + n) : 0.0;
                 if (DIM == 3) {
-                    if (z > 0) nb += __ldg(U + c - nn);
-                    if (z < n - 1) nb += __ldg(U + c + nn);
+                    nbv[2 * DIM - 2] = (z > 0) ? __ldg(U + c - nn) : 0.0;
+                    nbv[2 * DIM - 1] = (z < n - 1) ? __ldg(U + c + nn) : 0.0;
                 }
                 const double fv = __ldg(f + c);
-                r = (2.0 * DIM * u - nb) * a.inv_h2 + a.lam * u + a.b * u * u * u - fv;
+                // exact fixed-point stencil on the integer pipe (qn_numeric.cuh)
+                const double lap = stencil_fixed<DIM>(u, nbv);
                 const double u2 = u * u;
-                acc.r2 = fma(r, r, acc.r2);
-                acc.f2 = fma(fv, fv, acc.f2);
-                acc.mn = fmin(acc.mn, u2);
-                acc.mx = fmax(acc.mx, u2);
+                double t;
+                if (KIND == 2) {
+                    t = fma(u2, u, -fv);
+                } else {
+                    t = fma(a.b, u2 * u, -fv);
+                    if (KIND == 0) t = fma(a.lam, u, t);
+                }
+                r = fma(lap, a.inv_h2, t);
+                const unsigned long long ab = abs_bits(u);
+                amin = ab < amin ? ab : amin;
+                amax = ab > amax ? ab : amax;
+                if (want_f2) f2 = fma(fv, fv, f2);
+                if (FAST) {
+                    const float rf = d2f_rn(r);
+                    const float yk = fmaf(rf, rf, -kc);
+                    const float tk = kr2 + yk;
+                    kc = (tk - kr2) - yk;
+                    kr2 = tk;
+                } else {
+                    r2 = fma(r, r, r2);
+                }
                 if (a.R64 != nullptr) a.R64[c] = r;
             }
             if (SPLIT) {
-                __nv_bfloat16 hi, lo;
-                split_bf16((float)r, hi, lo);
+                const float rf = d2f_rn(r);
+                const __nv_bfloat16 hi = __float2bfloat16_rn(rf);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(rf - __bfloat162float(hi));
                 const long long o = row * P + x;
                 a.Rhi[o] = hi;
                 a.Rlo[o] = lo;
             }
         }
     }
+    if (FAST) r2 = (double)kr2 - (double)kc;
+    const double umin = __longlong_as_double((long long)amin);
+    const double umax = __longlong_as_double((long long)amax);
+    Red4 acc{r2, f2, (amin == 0x7FFFFFFFFFFFFFFFull) ? INFINITY : umin * umin, umax * umax};
     acc = block_reduce(acc);
     if (threadIdx.x == 0) {
         double *p = a.partials + 4ll * blockIdx.x;
@@ -116,7 +152,7 @@ __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
 
 __global__ void __launch_bounds__(256) k_finalize(const double *partials, int nparts, DevState *st,
                                                   qn_stats *hist, int hist_cap, double b,
-                                                  double lam, int update_state) {
+                                                  double lam, int update_state, int use_saved_fnorm) {
     if (update_state && *(volatile int *)&st->done) return;
     Red4 acc{0.0, 0.0, INFINITY, 0.0};
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
@@ -128,7 +164,8 @@ __global__ void __launch_bounds__(256) k_finalize(const double *partials, int np
     acc = block_reduce(acc);
     if (threadIdx.x != 0) return;
     const double res = sqrt(acc.r2);
-    const double fn = sqrt(acc.f2);
+    const double fn = use_saved_fnorm ? st->f_norm : sqrt(acc.f2);
+    if (update_state && !use_saved_fnorm) st->f_norm = fn;
     const double fa = 3.0 * b * acc.mn, fb = 3.0 * b * acc.mx;
     const double fu_min = fmin(fa, fb), fu_max = fmax(fa, fb);
     const double beta = (st->beta_mode == QN_BETA_FIXED) ? st->beta_value : 0.5 * (fu_min + fu_max);
@@ -197,26 +234,46 @@ int launch_split_pad(const double *r, int n, int P, int dim, __nv_bfloat16 *hi, 
     return QN_OK;
 }
 
+template <int DIM, bool SPLIT, bool FAST>
+static void launch_res3(const ResidualArgs &a, int grid, cudaStream_t s) {
+    if (a.lam != 0.0)
+        k_residual<DIM, SPLIT, FAST, 0><<<grid, 256, 0, s>>>(a);
+    else if (a.b != 1.0)
+        k_residual<DIM, SPLIT, FAST, 1><<<grid, 256, 0, s>>>(a);
+    else
+        k_residual<DIM, SPLIT, FAST, 2><<<grid, 256, 0, s>>>(a);
+}
+
+template <int DIM, bool SPLIT>
+static void launch_res2(const ResidualArgs &a, int grid, cudaStream_t s) {
+    if (a.fast)
+        launch_res3<DIM, SPLIT, true>(a, grid, s);
+    else
+        launch_res3<DIM, SPLIT, false>(a, grid, s);
+}
+
 int launch_residual(const ResidualArgs &a, int grid, cudaStream_t s) {
     const bool split = a.Rhi != nullptr;
     if (a.dim == 3) {
         if (split)
-            k_residual<3, true><<<grid, 256, 0, s>>>(a);
+            launch_res2<3, true>(a, grid, s);
         else
-            k_residual<3, false><<<grid, 256, 0, s>>>(a);
+            launch_res2<3, false>(a, grid, s);
     } else {
         if (split)
-            k_residual<2, true><<<grid, 256, 0, s>>>(a);
+            launch_res2<2, true>(a, grid, s);
         else
-            k_residual<2, false><<<grid, 256, 0, s>>>(a);
+            launch_res2<2, false>(a, grid, s);
     }
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }
 
 int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *hist,
-                        int hist_cap, double b, double lam, int update_state, cudaStream_t s) {
-    k_finalize<<<1, 256, 0, s>>>(partials, nparts, st, hist, hist_cap, b, lam, update_state);
+                        int hist_cap, double b, double lam, int update_state, int use_saved_fnorm,
+                        cudaStream_t s) {
+    k_finalize<<<1, 256, 0, s>>>(partials, nparts, st, hist, hist_cap, b, lam, update_state,
+                                 use_saved_fnorm);
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }
@@ -280,6 +337,7 @@ __global__ void k_noalloc_prepare(DevState *st) {
         st->max_it = 0;
         st->beta_mode = QN_BETA_PAPER;
         st->beta_value = 0.0;
+        st->f_norm = 0.0;
     }
 }
 
@@ -340,9 +398,11 @@ extern "C" int qn_residual_noalloc(int dim, int n, double lam, double b, const d
     a.P = n;
     a.partials = partials;
     a.done = nullptr;
+    a.fast = 0;
+    a.want_f2 = 1;
     rc = launch_residual(a, grid, s);
     if (rc != QN_OK) return rc;
-    rc = launch_finalize(partials, grid, state, stats, 1, b, lam, 0, s);
+    rc = launch_finalize(partials, grid, state, stats, 1, b, lam, 0, 0, s);
     if (rc != QN_OK) return rc;
     QN_CUDA(cudaMemcpyAsync(st, stats, sizeof(qn_stats), cudaMemcpyDeviceToHost, s));
     QN_CUDA(cudaStreamSynchronize(s));

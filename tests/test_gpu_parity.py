@@ -93,17 +93,25 @@ def test_fast_diag_solve_matches_oracle(qn, dim, n, prec, shift):
 # --------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("dim,n", [(2, 63), (3, 31)])
 @pytest.mark.parametrize("beta", [None, 4.0])
-def test_step_matches_oracle(qn, dim, n, beta):
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_step_matches_oracle(qn, dim, n, beta, prec):
     u, f = manufactured_problem(n, dim, seed=3)
     U0 = 0.5 * u
-    ctx = qn.QnContext(dim, n, "fp64")
+    ctx = qn.QnContext(dim, n, prec)
     Ud = dev(U0).reshape(-1)
     st = qn.qn_step(ctx, Ud, dev(f).reshape(-1), math.nan if beta is None else beta)
     want, r, beta_used = O.qn_step(U0, f, beta=beta)
     got = host(Ud).reshape(want.shape)
-    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    delta = np.abs(want - U0).max()
+    if prec == "fp64":
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+        assert st["res_norm"] == pytest.approx(np.linalg.norm(r), rel=1e-12)
+    else:
+        # the update delta carries the split products' error; the FP64 U does not
+        assert np.abs(got - want).max() <= 3e-4 * delta
+        # ||F|| from float(r)^2 summed in FP32 (Kahan): ~1e-7 relative
+        assert st["res_norm"] == pytest.approx(np.linalg.norm(r), rel=1e-6)
     assert st["beta"] == pytest.approx(beta_used, rel=1e-13)
-    assert st["res_norm"] == pytest.approx(np.linalg.norm(r), rel=1e-12)
 
 
 # --------------------------------------------------------------------------------------------
