@@ -189,6 +189,57 @@ int qn_solve_host(qn_ctx *ctx, double *U_host, const double *f_host, const qn_op
 int qn_residual_noalloc(int dim, int n, double lam, double b, const double *U, const double *f,
                         double *R, qn_stats *st, void *stream);
 
+/* ---- batched coupled two-component systems (Sec. 4.3) ---------------------------
+ * Many independent 2-D instances of
+ *   -Lap u + u^3 + alpha v = f1,   -D Lap v + v^3 - alpha u = f2   (Dirichlet 0)
+ * with uneven grid sizes, solved together. Each iteration evaluates both
+ * residuals (FP64), takes one beta per instance as the midpoint of the extreme
+ * eigenvalues of the 2x2 blocks [[3u^2, alpha], [-alpha, 3v^2]] over all nodes
+ * (Sec. 4.3 eqs. eigen_quad, eigenvalues; real parts when the pair is complex),
+ * and updates u -= (A_h + beta I)^{-1} F_u, v -= (D A_h + beta I)^{-1} F_v by
+ * fast diagonalisation with BF16x3 tensor-core mode products. Each of the four
+ * mode-product phases is one grouped persistent launch over every instance
+ * and component; an iteration (six launches) is captured into a CUDA graph. */
+typedef struct qn_sys_instance {
+    int n;                  /* interior nodes per axis (n x n grid), 1..1024 */
+    double alpha;           /* coupling coefficient (finite) */
+    double D;               /* diffusion of the second component, > 0 */
+    double *U, *V;          /* device, n*n doubles each: initial iterates in, solutions out */
+    const double *f1, *f2;  /* device, n*n doubles each */
+} qn_sys_instance;
+
+typedef struct qn_sys_result {
+    int iterations;         /* updates applied to this instance */
+    int status;             /* QN_OK, QN_ENOTCONV or QN_EDIVERGED */
+    double rel;             /* final sqrt(|F_u|^2 + |F_v|^2) / sqrt(|f1|^2 + |f2|^2) */
+    double time_ms;         /* device time from the start of the batch solve to this
+                               instance's convergence (-1 if it never stopped) */
+} qn_sys_result;
+
+typedef struct qn_batch qn_batch;   /* opaque; owns workspace, tensor maps, tile tables, graph */
+
+/* Create a batch over `count` instances (host array; the device arrays it
+ * points to must stay valid until qn_batch_destroy). bk: K-tile of the mode
+ * products, 0 (= 64), 32 or 64. bn: NULL, or one N-tile width per instance
+ * (multiple of 16 in 16..256, 0 = default min(P, 256)), e.g. from
+ * qn_autotune_tile. */
+int qn_batch_create(const qn_sys_instance *inst, int count, int bk, const int *bn, qn_batch **out);
+
+/* Solve every instance from its current U, V. opts: tol, max_it and
+ * sync_every (iterations per captured graph launch, the host checks between
+ * launches); beta_mode must be QN_BETA_PAPER and step 1. res: host array of
+ * `count` results (may be NULL). Returns QN_OK if every instance converged,
+ * else the first non-OK instance status. Synchronises `stream`. */
+int qn_batch_solve(qn_batch *b, const qn_opts *opts, qn_sys_result *res, void *stream);
+
+int qn_batch_destroy(qn_batch *b);
+
+/* Project autotuner for the batched mode products: times the grouped
+ * split-precision product over `copies` synthetic instances of size n for
+ * each candidate (bk in {32, 64}) x (bn in {64, 128, 256}, bn <= P) and
+ * returns the fastest. best_ms: mean time of one grouped launch (host). */
+int qn_autotune_tile(int n, int copies, int *best_bk, int *best_bn, double *best_ms);
+
 /* ---- measurement ------------------------------------------------------------- */
 typedef struct qn_profile {
     long long launches;       /* kernels launched that did work since qn_profile_enable

@@ -1,0 +1,724 @@
+// Batched coupled two-component systems (Sec. 4.3, eq. system; beta from the
+// eigenvalues of the 2x2 blocks of DN_h, eqs. eigen_quad and eigenvalues).
+//
+// Each instance i is a 2-D problem on n_i x n_i interior nodes:
+//   F_u = A_h u + u^3 + alpha v - f1,   F_v = D A_h v + v^3 - alpha u - f2,
+// solved by the quasi-Newton iteration with the block-diagonal approximate
+// Jacobian diag(A_h + beta I, D A_h + beta I); both blocks share the
+// eigenvectors of A_h, the second divides by D * (lambda_i + lambda_j) + beta.
+// One beta per instance: the midpoint of the extreme (real parts of the)
+// eigenvalues of [[3u^2, alpha], [-alpha, 3v^2]] over all nodes.
+//
+// One iteration of ALL instances is six launches:
+//   k_sys_residual   work items (instance, 8 rows) of every active instance:
+//                    both residuals (FP64, fixed-point stencil), their BF16
+//                    hi/lo planes, and partial sums / eigenvalue extremes
+//   k_sys_finalize   one block per instance: norms, beta, stop test, and the
+//                    device time at which the instance converged
+//   4 x k_modeprod_tc one grouped persistent launch per mode product over the
+//                    tiles of every instance and component (forward x, forward
+//                    y + divide, backward x, backward y + update)
+// and is captured once into a CUDA graph that the solve replays; instances
+// that have converged make every later launch skip their work.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "qn_internal.h"
+#include "qn_numeric.cuh"
+#include "qn_ptx.cuh"
+
+namespace qn {
+namespace {
+
+constexpr int kRowsPerItem = 8;
+
+struct SysInst {
+    double *U, *V;
+    const double *f1, *f2;
+    __nv_bfloat16 *ru_hi, *ru_lo, *rv_hi, *rv_lo;   // buffer 0 planes of both components
+    double alpha, D, inv_h2;
+    int n, P, item_begin, item_count;
+};
+
+struct SysState {
+    int done, status, it, pad;
+    double beta, f_norm, rel, res;
+    unsigned long long t_done;
+};
+
+struct SysItem {
+    int inst, row0, row1, pad;
+};
+
+struct SysCtl {
+    double tol;
+    int max_it;
+    int ndone;
+    unsigned long long t0;
+};
+
+struct Red4 {
+    double r2, f2, mx, mn;
+};
+
+__device__ __forceinline__ Red4 warp_red(Red4 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.r2 += __shfl_xor_sync(0xffffffffu, v.r2, o);
+        v.f2 += __shfl_xor_sync(0xffffffffu, v.f2, o);
+        v.mx = fmax(v.mx, __shfl_xor_sync(0xffffffffu, v.mx, o));
+        v.mn = fmin(v.mn, __shfl_xor_sync(0xffffffffu, v.mn, o));
+    }
+    return v;
+}
+
+__device__ Red4 block_red(Red4 v) {
+    __shared__ Red4 sh[32];
+    v = warp_red(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    if (w == 0) {
+        v = (l < nw) ? sh[l] : Red4{0.0, 0.0, -INFINITY, INFINITY};
+        v = warp_red(v);
+    }
+    return v;
+}
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+__global__ void k_sys_init(SysState *st, int count, SysCtl *ctl, double tol, int max_it) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) {
+        SysState s;
+        memset(&s, 0, sizeof(s));
+        st[i] = s;
+    }
+    if (i == 0) {
+        ctl->tol = tol;
+        ctl->max_it = max_it;
+        ctl->ndone = 0;
+        ctl->t0 = ptx::globaltimer();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sys_residual(const SysInst *__restrict__ inst,
+                                                      const SysItem *__restrict__ items,
+                                                      const SysState *__restrict__ st,
+                                                      double *__restrict__ partials) {
+    const SysItem it = items[blockIdx.x];
+    const SysState S = st[it.inst];
+    if (S.done) return;
+    const SysInst I = inst[it.inst];
+    const int n = I.n, P = I.P;
+    const bool want_f2 = S.it == 0;
+    const double alpha = I.alpha, Dh2 = I.D * I.inv_h2;
+    const float alpha_f = (float)alpha;
+    float kr2 = 0.0f, kc = 0.0f;
+    double f2 = 0.0;
+    float mxp = -INFINITY, mnm = INFINITY;
+    for (int y = it.row0; y < it.row1; ++y) {
+        for (int x = threadIdx.x; x < P; x += blockDim.x) {
+            double Fu = 0.0, Fv = 0.0;
+            if (y < n && x < n) {
+                const int c = y * n + x;
+                const double u = __ldg(I.U + c), v = __ldg(I.V + c);
+                double nu[4], nv[4];
+                nu[0] = x > 0 ? __ldg(I.U + c - 1) : 0.0;
+                nu[1] = x < n - 1 ? __ldg(I.U + c + 1) : 0.0;
+                nu[2] = y > 0 ? __ldg(I.U + c - n) : 0.0;
+                nu[3] = y < n - 1 ? __ldg(I.U + c + n) : 0.0;
+                nv[0] = x > 0 ? __ldg(I.V + c - 1) : 0.0;
+                nv[1] = x < n - 1 ? __ldg(I.V + c + 1) : 0.0;
+                nv[2] = y > 0 ? __ldg(I.V + c - n) : 0.0;
+                nv[3] = y < n - 1 ? __ldg(I.V + c + n) : 0.0;
+                const double g1 = __ldg(I.f1 + c), g2 = __ldg(I.f2 + c);
+                const double lu = stencil_fixed<2>(u, nu);
+                const double lv = stencil_fixed<2>(v, nv);
+                Fu = fma(lu, I.inv_h2, fma(u * u, u, fma(alpha, v, -g1)));
+                Fv = fma(lv, Dh2, fma(v * v, v, fma(-alpha, u, -g2)));
+                // eigenvalues of [[3u^2, alpha], [-alpha, 3v^2]] (real parts), FP32
+                const float uf = d2f_rn(u), vf = d2f_rn(v);
+                const float a = 3.0f * uf * uf, d = 3.0f * vf * vf;
+                const float disc = (a - d) * (a - d) - 4.0f * alpha_f * alpha_f;
+                const float sq = disc > 0.0f ? sqrtf(disc) : 0.0f;
+                mxp = fmaxf(mxp, 0.5f * (a + d + sq));
+                mnm = fminf(mnm, 0.5f * (a + d - sq));
+                if (want_f2) f2 = fma(g1, g1, fma(g2, g2, f2));
+                const float fu = d2f_rn(Fu), fv = d2f_rn(Fv);
+                const float yk = fmaf(fu, fu, fmaf(fv, fv, -kc));
+                const float tk = kr2 + yk;
+                kc = (tk - kr2) - yk;
+                kr2 = tk;
+            }
+            const int o = y * P + x;
+            __nv_bfloat16 h, l;
+            split_bf16(d2f_rn(Fu), h, l);
+            I.ru_hi[o] = h;
+            I.ru_lo[o] = l;
+            split_bf16(d2f_rn(Fv), h, l);
+            I.rv_hi[o] = h;
+            I.rv_lo[o] = l;
+        }
+    }
+    Red4 acc{(double)kr2 - (double)kc, f2, (double)mxp, (double)mnm};
+    acc = block_red(acc);
+    if (threadIdx.x == 0) {
+        double *p = partials + 4ll * blockIdx.x;
+        p[0] = acc.r2;
+        p[1] = acc.f2;
+        p[2] = acc.mx;
+        p[3] = acc.mn;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_sys_finalize(const SysInst *__restrict__ inst, SysState *st,
+                                                      const double *__restrict__ partials, SysCtl *ctl) {
+    const int i = blockIdx.x;
+    if (*(volatile int *)&st[i].done) return;
+    const SysInst I = inst[i];
+    Red4 acc{0.0, 0.0, -INFINITY, INFINITY};
+    for (int k = threadIdx.x; k < I.item_count; k += blockDim.x) {
+        const double *p = partials + 4ll * (I.item_begin + k);
+        acc.r2 += p[0];
+        acc.f2 += p[1];
+        acc.mx = fmax(acc.mx, p[2]);
+        acc.mn = fmin(acc.mn, p[3]);
+    }
+    acc = block_red(acc);
+    if (threadIdx.x != 0) return;
+    SysState s = st[i];
+    if (s.it == 0) s.f_norm = sqrt(acc.f2);
+    const double res = sqrt(acc.r2);
+    double rel = s.f_norm > 0.0 ? res / s.f_norm : (res == 0.0 ? 0.0 : INFINITY);
+    const double beta = 0.5 * (acc.mx + acc.mn);
+    s.rel = rel;
+    s.res = res;
+    s.beta = beta;
+    bool fin = false;
+    if (rel <= ctl->tol) {
+        s.status = QN_OK;
+        fin = true;
+    } else if (!isfinite(rel) || rel > 1e8 || !isfinite(beta)) {
+        s.status = QN_EDIVERGED;
+        fin = true;
+    } else if (s.it >= ctl->max_it) {
+        s.status = QN_ENOTCONV;
+        fin = true;
+    } else {
+        s.it += 1;
+    }
+    if (fin) {
+        s.done = 1;
+        s.t_done = ptx::globaltimer();
+        atomicAdd(&ctl->ndone, 1);
+    }
+    st[i] = s;
+}
+
+}  // namespace
+}  // namespace qn
+
+using namespace qn;
+
+struct qn_batch {
+    int count, device, num_sms, BK;
+    std::vector<qn_sys_instance> inst;
+    std::vector<int> P, BN;
+    // per distinct (P, BN): eigen-data
+    struct SizeData {
+        int P, n, BN;
+        __nv_bfloat16 *S_hi, *S_lo, *Si_hi, *Si_lo;
+        float *lam32;
+        int map_index;   // 4 maps: s_hi, s_lo, si_hi, si_lo
+    };
+    std::vector<SizeData> sizes;
+    std::vector<int> size_of;          // instance -> sizes index
+    __nv_bfloat16 *planes;             // all instance planes
+    CUtensorMap *maps;                 // device tensor maps
+    TcGroup *groups;                   // [4 steps][2 * count]
+    TcTile *tiles;
+    int ntiles, grid_mp;
+    SysInst *d_inst;
+    SysItem *d_items;
+    int nitems;
+    double *partials;
+    SysState *d_state;
+    SysCtl *d_ctl;
+    int *err;
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
+    int graph_iters;
+    cudaStream_t graph_stream;
+};
+
+static void batch_free(qn_batch *b) {
+    if (!b) return;
+    for (auto &z : b->sizes) {
+        cudaFree(z.S_hi);
+        cudaFree(z.S_lo);
+        cudaFree(z.Si_hi);
+        cudaFree(z.Si_lo);
+        cudaFree(z.lam32);
+    }
+    cudaFree(b->planes);
+    cudaFree(b->maps);
+    cudaFree(b->groups);
+    cudaFree(b->tiles);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_items);
+    cudaFree(b->partials);
+    cudaFree(b->d_state);
+    cudaFree(b->d_ctl);
+    cudaFree(b->err);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+}
+
+#define BCK(call)                                  \
+    do {                                           \
+        cudaError_t _e = (call);                   \
+        if (_e != cudaSuccess) {                   \
+            int _r = cuda_fail(_e, #call);         \
+            batch_free(b);                         \
+            return _r;                             \
+        }                                          \
+    } while (0)
+
+static void split_host(double v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    const float f = (float)v;
+    hi = __float2bfloat16_rn(f);
+    lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+}
+
+extern "C" int qn_batch_create(const qn_sys_instance *inst, int count, int bk, const int *bn,
+                               qn_batch **out) {
+    if (!inst || !out || count < 1 || count > 65536) {
+        set_error("qn_batch_create: need 1..65536 instances and an output pointer");
+        return QN_EINVAL;
+    }
+    *out = nullptr;
+    if (bk != 0 && bk != 32 && bk != 64) {
+        set_error("qn_batch_create: bk must be 0 (default), 32 or 64");
+        return QN_EINVAL;
+    }
+    for (int i = 0; i < count; ++i) {
+        const qn_sys_instance &q = inst[i];
+        if (q.n < 1 || q.n > 1024 || !q.U || !q.V || !q.f1 || !q.f2 || !isfinite(q.alpha) ||
+            !(q.D > 0.0) || !isfinite(q.D)) {
+            set_error("qn_batch_create: instance %d invalid (n in 1..1024, D > 0, non-null arrays)", i);
+            return QN_EINVAL;
+        }
+        if (bn && bn[i] != 0 && (bn[i] < 16 || bn[i] > 256 || bn[i] % 16)) {
+            set_error("qn_batch_create: bn[%d]=%d must be a multiple of 16 in 16..256", i, bn[i]);
+            return QN_EINVAL;
+        }
+    }
+    qn_batch *b = new (std::nothrow) qn_batch();
+    if (!b) return QN_ENOMEM;
+    b->count = count;
+    b->inst.assign(inst, inst + count);
+    BCK(cudaGetDevice(&b->device));
+    BCK(cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device));
+    if (!tc_supported(b->device)) {
+        set_error("qn_batch_create: needs an sm_103 (tcgen05) device");
+        batch_free(b);
+        return QN_EUNSUPPORTED;
+    }
+    if (tc_set_attributes() != QN_OK) {
+        batch_free(b);
+        return QN_ECUDA;
+    }
+    b->BK = bk ? bk : 64;
+    b->P.resize(count);
+    b->BN.resize(count);
+    b->size_of.resize(count);
+    for (int i = 0; i < count; ++i) {
+        b->P[i] = ((inst[i].n + 63) / 64) * 64;
+        int want = (bn && bn[i]) ? bn[i] : (b->P[i] <= 256 ? b->P[i] : 256);
+        if (want > b->P[i]) want = b->P[i];
+        b->BN[i] = want;
+    }
+    // eigen-data per distinct (n, BN)
+    for (int i = 0; i < count; ++i) {
+        int found = -1;
+        for (size_t z = 0; z < b->sizes.size(); ++z)
+            if (b->sizes[z].n == inst[i].n && b->sizes[z].BN == b->BN[i]) found = (int)z;
+        if (found < 0) {
+            qn_batch::SizeData z;
+            memset(&z, 0, sizeof(z));
+            z.n = inst[i].n;
+            z.P = b->P[i];
+            z.BN = b->BN[i];
+            b->sizes.push_back(z);
+            found = (int)b->sizes.size() - 1;
+        }
+        b->size_of[i] = found;
+    }
+    const int nsz = (int)b->sizes.size();
+    std::vector<CUtensorMap> hmaps(4 * nsz + 8 * count);
+    for (int z = 0; z < nsz; ++z) {
+        qn_batch::SizeData &d = b->sizes[z];
+        const int n = d.n, P = d.P;
+        std::vector<double> S((size_t)n * n), Si((size_t)n * n), lam(n);
+        int rc = qn_setup_1d_eig(n, 1.0 / (n + 1), QN_BC_DIRICHLET, S.data(), Si.data(), lam.data());
+        if (rc != QN_OK) {
+            batch_free(b);
+            return rc;
+        }
+        std::vector<__nv_bfloat16> hS((size_t)P * P), lS((size_t)P * P), hSi((size_t)P * P), lSi((size_t)P * P);
+        std::vector<float> l32(P, 1e30f);
+        for (int j = 0; j < P; ++j)
+            for (int k = 0; k < P; ++k) {
+                const double vs = (j < n && k < n) ? S[(size_t)j * n + k] : 0.0;
+                const double vi = (j < n && k < n) ? Si[(size_t)j * n + k] : 0.0;
+                split_host(vs, hS[(size_t)j * P + k], lS[(size_t)j * P + k]);
+                split_host(vi, hSi[(size_t)j * P + k], lSi[(size_t)j * P + k]);
+            }
+        for (int k = 0; k < n; ++k) l32[k] = (float)lam[k];
+        const size_t mb = sizeof(__nv_bfloat16) * P * P;
+        BCK(cudaMalloc(&d.S_hi, mb));
+        BCK(cudaMalloc(&d.S_lo, mb));
+        BCK(cudaMalloc(&d.Si_hi, mb));
+        BCK(cudaMalloc(&d.Si_lo, mb));
+        BCK(cudaMalloc(&d.lam32, sizeof(float) * P));
+        BCK(cudaMemcpy(d.S_hi, hS.data(), mb, cudaMemcpyHostToDevice));
+        BCK(cudaMemcpy(d.S_lo, lS.data(), mb, cudaMemcpyHostToDevice));
+        BCK(cudaMemcpy(d.Si_hi, hSi.data(), mb, cudaMemcpyHostToDevice));
+        BCK(cudaMemcpy(d.Si_lo, lSi.data(), mb, cudaMemcpyHostToDevice));
+        BCK(cudaMemcpy(d.lam32, l32.data(), sizeof(float) * P, cudaMemcpyHostToDevice));
+        d.map_index = 4 * z;
+        int rc2 = tc_encode_2d(&hmaps[4 * z + 0], d.S_hi, P, P, b->BK, d.BN, b->BK);
+        if (!rc2) rc2 = tc_encode_2d(&hmaps[4 * z + 1], d.S_lo, P, P, b->BK, d.BN, b->BK);
+        if (!rc2) rc2 = tc_encode_2d(&hmaps[4 * z + 2], d.Si_hi, P, P, b->BK, d.BN, b->BK);
+        if (!rc2) rc2 = tc_encode_2d(&hmaps[4 * z + 3], d.Si_lo, P, P, b->BK, d.BN, b->BK);
+        if (rc2) {
+            batch_free(b);
+            return rc2;
+        }
+    }
+    // planes: per instance, per component, per buffer: hi, lo (P^2 each)
+    std::vector<size_t> plane_off(count);
+    size_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        plane_off[i] = total;
+        total += (size_t)8 * b->P[i] * b->P[i];
+    }
+    BCK(cudaMalloc(&b->planes, sizeof(__nv_bfloat16) * total));
+    BCK(cudaMemset(b->planes, 0, sizeof(__nv_bfloat16) * total));
+    auto plane = [&](int i, int comp, int buf, int lo) {
+        const size_t PP = (size_t)b->P[i] * b->P[i];
+        return b->planes + plane_off[i] + PP * (size_t)(comp * 4 + buf * 2 + lo);
+    };
+    const int mapbase = 4 * nsz;
+    for (int i = 0; i < count; ++i) {
+        const int P = b->P[i];
+        for (int comp = 0; comp < 2; ++comp)
+            for (int buf = 0; buf < 2; ++buf)
+                for (int lo = 0; lo < 2; ++lo) {
+                    int rc = tc_encode_2d(&hmaps[mapbase + 8 * i + comp * 4 + buf * 2 + lo], plane(i, comp, buf, lo),
+                                          P, P, b->BK, 128, b->BK);
+                    if (rc) {
+                        batch_free(b);
+                        return rc;
+                    }
+                }
+    }
+    BCK(cudaMalloc(&b->maps, sizeof(CUtensorMap) * hmaps.size()));
+    BCK(cudaMemcpy(b->maps, hmaps.data(), sizeof(CUtensorMap) * hmaps.size(), cudaMemcpyHostToDevice));
+
+    // state, control, items
+    BCK(cudaMalloc(&b->d_state, sizeof(SysState) * count));
+    BCK(cudaMalloc(&b->d_ctl, sizeof(SysCtl)));
+    BCK(cudaMalloc(&b->err, sizeof(int)));
+    BCK(cudaMemset(b->err, 0, sizeof(int)));
+    std::vector<SysInst> hinst(count);
+    std::vector<SysItem> hitems;
+    for (int i = 0; i < count; ++i) {
+        SysInst &s = hinst[i];
+        s.U = inst[i].U;
+        s.V = inst[i].V;
+        s.f1 = inst[i].f1;
+        s.f2 = inst[i].f2;
+        s.ru_hi = plane(i, 0, 0, 0);
+        s.ru_lo = plane(i, 0, 0, 1);
+        s.rv_hi = plane(i, 1, 0, 0);
+        s.rv_lo = plane(i, 1, 0, 1);
+        s.alpha = inst[i].alpha;
+        s.D = inst[i].D;
+        const double h = 1.0 / (inst[i].n + 1);
+        s.inv_h2 = 1.0 / (h * h);
+        s.n = inst[i].n;
+        s.P = b->P[i];
+        s.item_begin = (int)hitems.size();
+        for (int r = 0; r < b->P[i]; r += kRowsPerItem) {
+            SysItem it;
+            it.inst = i;
+            it.row0 = r;
+            it.row1 = std::min(r + kRowsPerItem, b->P[i]);
+            it.pad = 0;
+            hitems.push_back(it);
+        }
+        s.item_count = (int)hitems.size() - s.item_begin;
+    }
+    b->nitems = (int)hitems.size();
+    BCK(cudaMalloc(&b->d_inst, sizeof(SysInst) * count));
+    BCK(cudaMemcpy(b->d_inst, hinst.data(), sizeof(SysInst) * count, cudaMemcpyHostToDevice));
+    BCK(cudaMalloc(&b->d_items, sizeof(SysItem) * b->nitems));
+    BCK(cudaMemcpy(b->d_items, hitems.data(), sizeof(SysItem) * b->nitems, cudaMemcpyHostToDevice));
+    BCK(cudaMalloc(&b->partials, sizeof(double) * 4 * b->nitems));
+
+    // groups: 4 product steps x (instance, component); step s reads buffer (s & 1)
+    // and writes buffer 1 - (s & 1); steps 0, 1 forward (S^{-1}), 2, 3 backward (S)
+    std::vector<TcGroup> hg((size_t)4 * 2 * count);
+    for (int step = 0; step < 4; ++step)
+        for (int i = 0; i < count; ++i)
+            for (int comp = 0; comp < 2; ++comp) {
+                TcGroup &g = hg[(size_t)step * 2 * count + 2 * i + comp];
+                const qn_batch::SizeData &z = b->sizes[b->size_of[i]];
+                const int src = step & 1, dst = 1 - src;
+                const bool fwd = step < 2;
+                const CUtensorMap *mb = b->maps;
+                g.a_hi = mb + mapbase + 8 * i + comp * 4 + src * 2 + 0;
+                g.a_lo = mb + mapbase + 8 * i + comp * 4 + src * 2 + 1;
+                g.b_hi = mb + z.map_index + (fwd ? 2 : 0);
+                g.b_lo = mb + z.map_index + (fwd ? 3 : 1);
+                g.out_hi = step < 3 ? plane(i, comp, dst, 0) : nullptr;
+                g.out_lo = step < 3 ? plane(i, comp, dst, 1) : nullptr;
+                g.U = comp == 0 ? inst[i].U : inst[i].V;
+                g.lam32 = z.lam32;
+                g.shift = &b->d_state[i].beta;
+                g.done = &b->d_state[i].done;
+                g.dscale = comp == 0 ? 1.0f : (float)inst[i].D;
+                g.step = 1.0f;
+                g.Mtot = b->P[i];
+                g.P = b->P[i];
+                g.n = inst[i].n;
+                g.BN = b->BN[i];
+                g.ntile_n = (b->P[i] + b->BN[i] - 1) / b->BN[i];
+                g.ntiles = g.ntile_n * ((b->P[i] + 127) / 128);
+            }
+    BCK(cudaMalloc(&b->groups, sizeof(TcGroup) * hg.size()));
+    BCK(cudaMemcpy(b->groups, hg.data(), sizeof(TcGroup) * hg.size(), cudaMemcpyHostToDevice));
+    // tiles: largest instances first (longest processing time first)
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->P[x] > b->P[y]; });
+    std::vector<TcTile> ht;
+    for (int i : order)
+        for (int comp = 0; comp < 2; ++comp) {
+            const TcGroup &g = hg[2 * i + comp];
+            for (int mt = 0; mt < (b->P[i] + 127) / 128; ++mt)
+                for (int nt = 0; nt < g.ntile_n; ++nt) {
+                    TcTile t;
+                    t.group = 2 * i + comp;
+                    t.m0 = mt * 128;
+                    t.n0 = nt * g.BN;
+                    t.pad = 0;
+                    ht.push_back(t);
+                }
+        }
+    b->ntiles = (int)ht.size();
+    b->grid_mp = b->ntiles < b->num_sms ? b->ntiles : b->num_sms;
+    BCK(cudaMalloc(&b->tiles, sizeof(TcTile) * b->ntiles));
+    BCK(cudaMemcpy(b->tiles, ht.data(), sizeof(TcTile) * b->ntiles, cudaMemcpyHostToDevice));
+    *out = b;
+    return QN_OK;
+}
+
+extern "C" int qn_batch_destroy(qn_batch *b) {
+    if (!b) return QN_OK;
+    cudaDeviceSynchronize();
+    batch_free(b);
+    return QN_OK;
+}
+
+static int enqueue_batch_iteration(qn_batch *b, cudaStream_t s) {
+    k_sys_residual<<<b->nitems, 256, 0, s>>>(b->d_inst, b->d_items, b->d_state, b->partials);
+    QN_CUDA(cudaGetLastError());
+    k_sys_finalize<<<b->count, 128, 0, s>>>(b->d_inst, b->d_state, b->partials, b->d_ctl);
+    QN_CUDA(cudaGetLastError());
+    const Epi epis[4] = {EPI_STORE, EPI_DIVIDE, EPI_STORE, EPI_UPDATE};
+    for (int step = 0; step < 4; ++step) {
+        int rc = launch_modeprod_tc_grouped(b->groups + (size_t)step * 2 * b->count, b->tiles, b->ntiles, 2, b->BK,
+                                            epis[step], b->err, b->grid_mp, s);
+        if (rc) return rc;
+    }
+    return QN_OK;
+}
+
+extern "C" int qn_batch_solve(qn_batch *b, const qn_opts *opts, qn_sys_result *res, void *stream) {
+    if (!b) {
+        set_error("qn_batch_solve: null batch");
+        return QN_EINVAL;
+    }
+    double tol = 1e-10;
+    int max_it = 200;
+    int chunk = 4;
+    if (opts) {
+        tol = opts->tol;
+        max_it = opts->max_it;
+        if (opts->sync_every >= 1) chunk = opts->sync_every;
+        if (opts->beta_mode != QN_BETA_PAPER || opts->step != 1.0) {
+            set_error("qn_batch_solve: only the paper's beta rule and step 1 are supported");
+            return QN_EUNSUPPORTED;
+        }
+    }
+    if (!(tol >= 0.0) || max_it < 0 || max_it > 4096) {
+        set_error("qn_batch_solve: invalid options");
+        return QN_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // capture `chunk` iterations once per (batch, stream, chunk)
+    if (!b->gexec || b->graph_iters != chunk || b->graph_stream != s) {
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        if (b->graph) {
+            cudaGraphDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        cudaStream_t cap;
+        QN_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return cuda_fail(e, "cudaStreamBeginCapture");
+        }
+        int rc = QN_OK;
+        for (int k = 0; k < chunk && rc == QN_OK; ++k) rc = enqueue_batch_iteration(b, cap);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        b->graph = g;
+        QN_CUDA(cudaGraphInstantiate(&b->gexec, g, 0));
+        b->graph_iters = chunk;
+        b->graph_stream = s;
+    }
+    k_sys_init<<<(b->count + 255) / 256, 256, 0, s>>>(b->d_state, b->count, b->d_ctl, tol, max_it);
+    QN_CUDA(cudaGetLastError());
+    int launched = 0;
+    SysCtl hctl;
+    while (true) {
+        QN_CUDA(cudaGraphLaunch(b->gexec, s));
+        launched += chunk;
+        QN_CUDA(cudaMemcpyAsync(&hctl, b->d_ctl, sizeof(SysCtl), cudaMemcpyDeviceToHost, s));
+        QN_CUDA(cudaStreamSynchronize(s));
+        if (hctl.ndone >= b->count || launched > max_it + chunk) break;
+    }
+    int err = 0;
+    QN_CUDA(cudaMemcpy(&err, b->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        QN_CUDA(cudaMemset(b->err, 0, sizeof(int)));
+        set_error("qn_batch_solve: a device-side wait gave up (tensor-core pipeline timeout)");
+        return QN_ETIMEOUT;
+    }
+    std::vector<SysState> hs(b->count);
+    QN_CUDA(cudaMemcpy(hs.data(), b->d_state, sizeof(SysState) * b->count, cudaMemcpyDeviceToHost));
+    int worst = QN_OK;
+    for (int i = 0; i < b->count; ++i) {
+        const int st = hs[i].done ? hs[i].status : QN_ENOTCONV;
+        if (res) {
+            res[i].iterations = hs[i].it;
+            res[i].status = st;
+            res[i].rel = hs[i].rel;
+            res[i].time_ms = hs[i].done ? (double)(hs[i].t_done - hctl.t0) * 1e-6 : -1.0;
+        }
+        if (st != QN_OK && worst == QN_OK) worst = st;
+    }
+    return worst;
+}
+
+extern "C" int qn_autotune_tile(int n, int copies, int *best_bk, int *best_bn, double *best_ms) {
+    if (n < 1 || n > 1024 || copies < 1 || copies > 4096 || !best_bk || !best_bn) {
+        set_error("qn_autotune_tile: n in 1..1024, copies in 1..4096, non-null outputs");
+        return QN_EINVAL;
+    }
+    const int P = ((n + 63) / 64) * 64;
+    double *zero = nullptr;
+    const size_t nn = (size_t)n * n;
+    QN_CUDA(cudaMalloc(&zero, sizeof(double) * nn));
+    cudaMemset(zero, 0, sizeof(double) * nn);
+    std::vector<qn_sys_instance> inst(copies);
+    for (int i = 0; i < copies; ++i) {
+        inst[i].n = n;
+        inst[i].alpha = 0.5;
+        inst[i].D = 1.0;
+        inst[i].U = zero;
+        inst[i].V = zero;
+        inst[i].f1 = zero;
+        inst[i].f2 = zero;
+    }
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(zero);
+        set_error("qn_autotune_tile: stream creation failed");
+        return QN_ECUDA;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    int bbk = 64, bbn = P < 256 ? P : 256;
+    const int bks[2] = {64, 32};
+    const int bns[3] = {64, 128, 256};
+    int rc = QN_OK;
+    for (int a = 0; a < 2 && rc == QN_OK; ++a)
+        for (int c = 0; c < 3 && rc == QN_OK; ++c) {
+            const int bn = bns[c];
+            if (bn > P) continue;
+            std::vector<int> bnv(copies, bn);
+            qn_batch *b = nullptr;
+            rc = qn_batch_create(inst.data(), copies, bks[a], bnv.data(), &b);
+            if (rc) break;
+            // states all "not done" so that every tile runs
+            k_sys_init<<<(copies + 255) / 256, 256, 0, s>>>(b->d_state, copies, b->d_ctl, 0.0, 1);
+            const int reps = 10;
+            for (int w = 0; w < 2 && rc == QN_OK; ++w)
+                rc = launch_modeprod_tc_grouped(b->groups, b->tiles, b->ntiles, 2, b->BK, EPI_STORE, b->err,
+                                                b->grid_mp, s);
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && rc == QN_OK; ++r)
+                rc = launch_modeprod_tc_grouped(b->groups, b->tiles, b->ntiles, 2, b->BK, EPI_STORE, b->err,
+                                                b->grid_mp, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = QN_ECUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            int err = 0;
+            cudaMemcpy(&err, b->err, sizeof(int), cudaMemcpyDeviceToHost);
+            if (err) rc = QN_ETIMEOUT;
+            qn_batch_destroy(b);
+            if (rc == QN_OK && ms / reps < best) {
+                best = ms / reps;
+                bbk = bks[a];
+                bbn = bn;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    cudaFree(zero);
+    if (rc) return rc;
+    *best_bk = bbk;
+    *best_bn = bbn;
+    if (best_ms) *best_ms = best;
+    return QN_OK;
+}

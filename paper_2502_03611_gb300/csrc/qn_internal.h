@@ -82,7 +82,27 @@ int launch_split_pad(const double *r, int n, int P, int dim, __nv_bfloat16 *hi, 
 int launch_modeprod_f64(const double *A, const double *B, double *out, const GemmShape &g,
                         Epi epi, const EpiArgs &e, cudaStream_t s);
 
-struct TcPlan;   // tensor maps + tile config of the tcgen05 path
+// ---- tcgen05 split-precision mode products ------------------------------------------
+// One group = one GEMM out[k][m] = sum_j A[m][j] B[k][j] (one mode product of
+// one tensor). A launch processes the tiles of one group (single-instance
+// solve) or of many groups (batched solve: every instance and component).
+struct TcGroup {
+    const CUtensorMap *a_hi, *a_lo, *b_hi, *b_lo;   // tensor maps in global memory (64-B aligned)
+    __nv_bfloat16 *out_hi, *out_lo;                   // EPI_STORE / EPI_DIVIDE destination planes
+    double *U;                                        // EPI_UPDATE / EPI_DENSE target (dense n^dim)
+    const float *lam32;                               // padded eigenvalues (P entries, 1e30 past n)
+    const double *shift;                              // lam + beta_n of the group's instance
+    const int *done;                                  // the instance's stop flag (nullptr: never)
+    float dscale;                                     // divisor = dscale * eigen-sum + shift
+    float step;                                       // update scale
+    int Mtot, P, n, BN, ntile_n, ntiles;
+};
+
+struct TcTile {
+    int group, m0, n0, pad;
+};
+
+struct TcPlan;   // tensor maps + tile config of the single-instance tcgen05 path
 int tc_plan_create(TcPlan **plan, int n, int P, int dim, __nv_bfloat16 *bufs_hi[2],
                    __nv_bfloat16 *bufs_lo[2], const __nv_bfloat16 *S_hi,
                    const __nv_bfloat16 *S_lo, const __nv_bfloat16 *Si_hi,
@@ -92,6 +112,15 @@ void tc_plan_destroy(TcPlan *plan);
 // the FP64 dense target for EPI_UPDATE / EPI_DENSE). forward selects S^{-1}.
 int launch_modeprod_tc(TcPlan *plan, int src, int dst, bool forward, Epi epi,
                        const EpiArgs &e, cudaStream_t s);
+// Grouped launch over a device tile table (batched solves).
+int launch_modeprod_tc_grouped(const TcGroup *groups, const TcTile *tiles, int ntiles, int dim, int BK,
+                               Epi epi, int *err, int grid, cudaStream_t s);
+// Encode a 2-D BF16 tensor map [outer][inner] with a (box_inner x box_outer) box.
+int tc_encode_2d(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                 uint32_t box_outer, int BK);
+size_t tc_smem_bytes(int BK, int stages);
+int tc_set_attributes();
+int tc_stages(int BK);
 bool tc_supported(int device);
 
 // error reporting

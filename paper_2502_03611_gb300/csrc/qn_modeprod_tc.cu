@@ -42,18 +42,13 @@ namespace qn {
 namespace {
 
 constexpr int BM = 128;
+constexpr int BN_MAX = 256;
 constexpr int kEpiWarps = 8;                       // two warps per TMEM lane quadrant
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kMaxStages = 8;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr uint32_t kCtrlBytes = 512;
-
-struct TcArgs {
-    int Mtot, P, n, BN, ntile_n, ntiles, tmem_cols, stages;
-    __nv_bfloat16 *out_hi;
-    __nv_bfloat16 *out_lo;
-    EpiArgs e;
-};
+constexpr uint32_t kTmemCols = 2 * BN_MAX;         // two accumulators of BN_MAX FP32 columns
 
 // Wait for `parity` on `bar`; false on timeout or when another role aborted.
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort_flag,
@@ -79,32 +74,48 @@ __device__ __forceinline__ void drain_bar(uint32_t bar, uint32_t parity) {
     }
 }
 
-__device__ __forceinline__ void split_store(float v, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                                            long long o) {
+__device__ __forceinline__ void split_store(float v, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int o) {
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     hi[o] = h;
     lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
+// Group and tile origin of tile t: single-group launches enumerate the tiles
+// of `g0` (m-major); grouped launches read the tile table.
+__device__ __forceinline__ void tile_info(int t, const TcGroup &g0, const TcGroup *groups,
+                                          const TcTile *tiles, TcGroup &G, int &m0, int &n0) {
+    if (groups == nullptr) {
+        G = g0;
+        m0 = (t / g0.ntile_n) * BM;
+        n0 = (t % g0.ntile_n) * g0.BN;
+    } else {
+        const TcTile T = tiles[t];
+        G = groups[T.group];
+        m0 = T.m0;
+        n0 = T.n0;
+    }
+}
+
+__device__ __forceinline__ bool group_done(const TcGroup &G) {
+    return G.done != nullptr && *(volatile const int *)G.done;
+}
+
 template <int BK, int EPI, int DIM>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_modeprod_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
-                  const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
-                  const TcArgs args) {
-    if (args.e.done != nullptr && *(volatile const int *)args.e.done) return;
+    k_modeprod_tc(const TcGroup g0, const TcGroup *__restrict__ groups, const TcTile *__restrict__ tiles,
+                  const int ntiles, const int stages, int *err) {
+    if (groups == nullptr && group_done(g0)) return;
 
     constexpr uint32_t kRowBytes = BK * 2;                // one swizzle row per tile row
     constexpr uint32_t kLayout = (BK == 64) ? 2u : 4u;    // 128-B : 64-B swizzle
     constexpr int kKSteps = BK / 16;
+    constexpr uint32_t a_bytes = BM * kRowBytes;
+    constexpr uint32_t b_bytes_max = BN_MAX * kRowBytes;
+    constexpr uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes_max;
 
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = ptx::smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    const int BN = args.BN;
-    const uint32_t a_bytes = BM * kRowBytes;
-    const uint32_t b_bytes = (uint32_t)BN * kRowBytes;
-    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
-    const int stages = args.stages;
     const uint32_t ctrl = base + (uint32_t)stages * stage_bytes;
     // control block: full[8], empty[8], tfull[2], tempty[2], mma_done, tmem slot, abort
     auto full_bar = [&](int s) { return ctrl + 8u * s; };
@@ -114,7 +125,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t mma_done_bar = ctrl + 160u;
     const uint32_t tmem_slot = ctrl + 168u;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem_raw + (ctrl + 172u - raw));
-    float *lam_s = reinterpret_cast<float *>(smem_raw + (ctrl + kCtrlBytes - raw));
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -132,25 +142,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         *abort_flag = 0;
         ptx::fence_mbar_init();
         ptx::fence_proxy_async();
-        ptx::prefetch_tensormap(&mA_hi);
-        ptx::prefetch_tensormap(&mA_lo);
-        ptx::prefetch_tensormap(&mB_hi);
-        ptx::prefetch_tensormap(&mB_lo);
+        if (groups == nullptr) {
+            ptx::prefetch_tensormap(g0.a_hi);
+            ptx::prefetch_tensormap(g0.a_lo);
+            ptx::prefetch_tensormap(g0.b_hi);
+            ptx::prefetch_tensormap(g0.b_lo);
+        }
     }
     if (warp == 1) {
-        ptx::tmem_alloc(tmem_slot, (uint32_t)args.tmem_cols);
+        ptx::tmem_alloc(tmem_slot, kTmemCols);
         ptx::tmem_relinquish();
-    }
-    if (EPI == EPI_DIVIDE) {
-        for (int i = threadIdx.x; i < args.P; i += blockDim.x) lam_s[i] = args.e.lam32[i];
     }
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t *>(smem_raw + (tmem_slot - raw));
-
-    const int KB = args.P / BK;
-    int *err = args.e.err;
 
     if (warp == 0 && lane == 0) {
         // ------------------------------ TMA producer ------------------------------
@@ -159,20 +165,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         int s = 0;
         uint32_t ph = 0;
         bool ok = true;
-        for (int t = blockIdx.x; ok && t < args.ntiles; t += gridDim.x) {
-            const int m0 = (t / args.ntile_n) * BM;
-            const int n0 = (t % args.ntile_n) * BN;
+        for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+            TcGroup G;
+            int m0, n0;
+            tile_info(t, g0, groups, tiles, G, m0, n0);
+            if (group_done(G)) continue;
+            const uint32_t tx_bytes = 2 * a_bytes + 2u * (uint32_t)G.BN * kRowBytes;
+            const int KB = G.P / BK;
             for (int kb = 0; kb < KB; ++kb) {
                 if (!wait_bar(empty_bar(s), ph ^ 1u, abort_flag, err)) {
                     ok = false;
                     break;
                 }
                 const uint32_t st = base + (uint32_t)s * stage_bytes;
-                ptx::mbar_arrive_expect_tx(full_bar(s), stage_bytes);
-                ptx::tma_load_2d(st, &mA_hi, full_bar(s), kb * BK, m0);
-                ptx::tma_load_2d(st + a_bytes, &mA_lo, full_bar(s), kb * BK, m0);
-                ptx::tma_load_2d(st + 2 * a_bytes, &mB_hi, full_bar(s), kb * BK, n0);
-                ptx::tma_load_2d(st + 2 * a_bytes + b_bytes, &mB_lo, full_bar(s), kb * BK, n0);
+                ptx::mbar_arrive_expect_tx(full_bar(s), tx_bytes);
+                ptx::tma_load_2d(st, G.a_hi, full_bar(s), kb * BK, m0);
+                ptx::tma_load_2d(st + a_bytes, G.a_lo, full_bar(s), kb * BK, m0);
+                ptx::tma_load_2d(st + 2 * a_bytes, G.b_hi, full_bar(s), kb * BK, n0);
+                ptx::tma_load_2d(st + 2 * a_bytes + b_bytes_max, G.b_lo, full_bar(s), kb * BK, n0);
                 armed_parity[s] = ph;
                 armed_mask |= 1u << s;
                 if (++s == stages) {
@@ -187,16 +197,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == 1 && lane == 0) {
         // ------------------------------ MMA issuer --------------------------------
-        const uint32_t idesc = ptx::idesc_bf16_f32(BM, (uint32_t)BN);
         int s = 0;
         uint32_t ph = 0;
         int acc = 0;
         uint32_t aph = 0;
         bool ok = true;
-        for (int t = blockIdx.x; ok && t < args.ntiles; t += gridDim.x) {
+        for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+            TcGroup G;
+            int m0, n0;
+            tile_info(t, g0, groups, tiles, G, m0, n0);
+            if (group_done(G)) continue;
+            const uint32_t idesc = ptx::idesc_bf16_f32(BM, (uint32_t)G.BN);
+            const int KB = G.P / BK;
             if (!wait_bar(tempty_bar(acc), aph ^ 1u, abort_flag, err)) break;
             ptx::tc_fence_after();
-            const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+            const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN_MAX);
             for (int kb = 0; kb < KB; ++kb) {
                 if (!wait_bar(full_bar(s), ph, abort_flag, err)) {
                     ok = false;
@@ -211,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint64_t a_lo = ptx::smem_desc_kmajor(st + a_bytes + koff, kRowBytes, kLayout);
                     const uint64_t b_hi = ptx::smem_desc_kmajor(st + 2 * a_bytes + koff, kRowBytes, kLayout);
                     const uint64_t b_lo =
-                        ptx::smem_desc_kmajor(st + 2 * a_bytes + b_bytes + koff, kRowBytes, kLayout);
+                        ptx::smem_desc_kmajor(st + 2 * a_bytes + b_bytes_max + koff, kRowBytes, kLayout);
                     const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
                     ptx::mma_bf16(d_tmem, a_hi, b_hi, idesc, first);
                     ptx::mma_bf16(d_tmem, a_hi, b_lo, idesc, 1u);
@@ -237,90 +252,89 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int row = q * 32 + lane;
         int acc = 0;
         uint32_t aph = 0;
-        float shift = 0.0f;
-        if (EPI == EPI_DIVIDE) shift = (float)(*args.e.shift);
-        const float step = (float)args.e.step;
-        const int P = args.P, n = args.n;
-        const long long Mtot = args.Mtot;
-        for (int t = blockIdx.x; t < args.ntiles; t += gridDim.x) {
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            TcGroup G;
+            int m0, n0;
+            tile_info(t, g0, groups, tiles, G, m0, n0);
+            if (group_done(G)) continue;
             // every lane waits; the decision to go on is made warp-uniform so
             // that the .sync.aligned TMEM loads below are never divergent
             const bool ready = wait_bar(tfull_bar(acc), aph, abort_flag, err);
             if (!__all_sync(0xffffffffu, ready)) break;
             ptx::tc_fence_after();
-            const long long m = (long long)(t / args.ntile_n) * BM + row;
-            const int n0 = (t % args.ntile_n) * BN;
+            const int P = G.P, n = G.n, BN = G.BN;
+            const int Mtot = G.Mtot;
+            const int m = m0 + row;
             const bool m_ok = m < Mtot;
-            float rowlam = 0.0f;
-            long long ubase = -1;   // dense U index without the k term (UPDATE/DENSE)
+            float rowlam = 0.0f, shift = 0.0f;
+            int ubase = -1;   // dense U index without the k term (UPDATE/DENSE)
             if (m_ok) {
                 if (EPI == EPI_DIVIDE) {
-                    rowlam = (DIM == 3) ? lam_s[m / P] + lam_s[m % P] : lam_s[m];
+                    rowlam = (DIM == 3) ? __ldg(G.lam32 + m / P) + __ldg(G.lam32 + m % P) : __ldg(G.lam32 + m);
+                    shift = (float)(*G.shift);
                 }
                 if (EPI == EPI_UPDATE || EPI == EPI_DENSE) {
                     if (DIM == 3) {
-                        const int yy = (int)(m / P), xx = (int)(m % P);
-                        if (yy < n && xx < n) ubase = (long long)yy * n + xx;
+                        const int yy = m / P, xx = m % P;
+                        if (yy < n && xx < n) ubase = yy * n + xx;
                     } else {
                         if (m < n) ubase = m;
                     }
                 }
             }
-            const long long kstride = (DIM == 3) ? (long long)n * n : (long long)n;
+            const int kstride = (DIM == 3) ? n * n : n;
+            const float dscale = G.dscale;
+            const float step = G.step;
             const int cbeg = half * (BN >> 1), cend = cbeg + (BN >> 1);
             for (int c = cbeg; c < cend; c += 32) {
                 uint32_t r[32];
-                ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
+                ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN_MAX + c), r);
                 ptx::tmem_ld_wait();
                 if (!m_ok) continue;
                 const int k0 = n0 + c;
                 if (EPI == EPI_STORE) {
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
-                        if (k0 + i < P)
-                            split_store(__uint_as_float(r[i]), args.out_hi, args.out_lo, (long long)(k0 + i) * Mtot + m);
+                        if (k0 + i < P) split_store(__uint_as_float(r[i]), G.out_hi, G.out_lo, (k0 + i) * Mtot + m);
                 } else if (EPI == EPI_DIVIDE) {
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const int k = k0 + i;
                         if (k < P) {
-                            const float den = lam_s[k] + rowlam + shift;
-                            split_store(__fdividef(__uint_as_float(r[i]), den), args.out_hi, args.out_lo,
-                                        (long long)k * Mtot + m);
+                            const float den = dscale * (__ldg(G.lam32 + k) + rowlam) + shift;
+                            split_store(__fdividef(__uint_as_float(r[i]), den), G.out_hi, G.out_lo, k * Mtot + m);
                         }
                     }
                 } else if (EPI == EPI_UPDATE) {
                     if (ubase >= 0) {
                         // 16 loads of U in flight per thread before the stores,
                         // instead of a serial read-modify-write
-                        double *ub = args.e.U + ubase;
+                        double *ub = G.U + ubase;
 #pragma unroll
                         for (int h = 0; h < 32; h += 16) {
                             double old[16];
 #pragma unroll
-                            for (int i = 0; i < 16; ++i)
-                                old[i] = (k0 + h + i < n) ? ub[(long long)(k0 + h + i) * kstride] : 0.0;
+                            for (int i = 0; i < 16; ++i) old[i] = (k0 + h + i < n) ? ub[(k0 + h + i) * kstride] : 0.0;
                             if (step == 1.0f) {
 #pragma unroll
                                 for (int i = 0; i < 16; ++i)
                                     if (k0 + h + i < n)
-                                        ub[(long long)(k0 + h + i) * kstride] = old[i] - f2d_exact(__uint_as_float(r[h + i]));
+                                        ub[(k0 + h + i) * kstride] = old[i] - f2d_exact(__uint_as_float(r[h + i]));
                             } else {
                                 const double st = (double)step;
 #pragma unroll
                                 for (int i = 0; i < 16; ++i)
                                     if (k0 + h + i < n)
-                                        ub[(long long)(k0 + h + i) * kstride] =
-                                            fma(-st, f2d_exact(__uint_as_float(r[h + i])), old[i]);
+                                        ub[(k0 + h + i) * kstride] = fma(-st, f2d_exact(__uint_as_float(r[h + i])), old[i]);
                             }
                         }
                     }
                 } else {   // EPI_DENSE
                     if (ubase >= 0) {
-                        double *ub = args.e.U + ubase;
+                        double *ub = G.U + ubase;
 #pragma unroll
                         for (int i = 0; i < 32; ++i)
-                            if (k0 + i < n) ub[(long long)(k0 + i) * kstride] = f2d_exact(__uint_as_float(r[i]));
+                            if (k0 + i < n) ub[(k0 + i) * kstride] = f2d_exact(__uint_as_float(r[i]));
                     }
                 }
             }
@@ -337,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 1) {
         __syncwarp();
         ptx::tc_fence_after();
-        ptx::tmem_dealloc(tmem_base, (uint32_t)args.tmem_cols);
+        ptx::tmem_dealloc(tmem_base, kTmemCols);
     }
 }
 
@@ -347,10 +361,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 // host side
 // ---------------------------------------------------------------------------
 struct TcPlan {
-    int n, P, dim, Mtot, BN, ntile_n, ntile_m, ntiles, grid, stages, tmem_cols, BK;
+    int n, P, dim, Mtot, BN, ntile_n, ntiles, grid, stages, BK;
     size_t smem;
-    CUtensorMap a_hi[2], a_lo[2];
-    CUtensorMap s_hi, s_lo, si_hi, si_lo;
+    CUtensorMap *maps;   // device: a_hi[2], a_lo[2], s_hi, s_lo, si_hi, si_lo
     __nv_bfloat16 *bufs_hi[2];
     __nv_bfloat16 *bufs_lo[2];
 };
@@ -368,8 +381,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-static int encode_2d(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t outer, uint32_t box_inner,
-                     uint32_t box_outer, int BK) {
+int tc_encode_2d(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                 uint32_t box_outer, int BK) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
     if (!enc) {
         set_error("cuTensorMapEncodeTiled unavailable from the driver");
@@ -397,10 +410,18 @@ bool tc_supported(int device) {
     return p.major == 10 && p.minor == 3;
 }
 
-template <int BK>
-static size_t smem_bytes(int BN, int stages, int P) {
-    const size_t stage = (size_t)(2 * BM + 2 * BN) * BK * 2;
-    return 1024 + stage * stages + kCtrlBytes + (size_t)P * 4;
+size_t tc_smem_bytes(int BK, int stages) {
+    const size_t stage = (size_t)(2 * BM + 2 * BN_MAX) * BK * 2;
+    return 1024 + stage * stages + kCtrlBytes;
+}
+
+int tc_stages(int BK) {
+    const size_t budget = 227 * 1024;
+    int stages = kMaxStages;
+    while (stages > 2 && tc_smem_bytes(BK, stages) > budget) --stages;
+    const char *st_env = getenv("QN_TC_STAGES");
+    if (st_env && atoi(st_env) >= 2 && atoi(st_env) < stages) stages = atoi(st_env);
+    return stages;
 }
 
 int tc_plan_create(TcPlan **out, int n, int P, int dim, __nv_bfloat16 *bufs_hi[2],
@@ -412,41 +433,34 @@ int tc_plan_create(TcPlan **out, int n, int P, int dim, __nv_bfloat16 *bufs_hi[2
     p->P = P;
     p->dim = dim;
     p->Mtot = (dim == 3) ? P * P : P;
-    p->BN = P <= 256 ? P : 256;
+    p->BN = P <= BN_MAX ? P : BN_MAX;
     p->ntile_n = (P + p->BN - 1) / p->BN;
-    p->ntile_m = (p->Mtot + BM - 1) / BM;
-    p->ntiles = p->ntile_n * p->ntile_m;
-    int cols = 32;
-    while (cols < 2 * p->BN) cols <<= 1;
-    p->tmem_cols = cols;
+    p->ntiles = p->ntile_n * ((p->Mtot + BM - 1) / BM);
     const char *bk_env = getenv("QN_TC_BK");
     p->BK = (bk_env && atoi(bk_env) == 32) ? 32 : 64;
-    const size_t budget = 227 * 1024;
-    int stages = kMaxStages;
-    while (stages > 2 && (p->BK == 64 ? smem_bytes<64>(p->BN, stages, P) : smem_bytes<32>(p->BN, stages, P)) > budget)
-        --stages;
-    const char *st_env = getenv("QN_TC_STAGES");
-    if (st_env && atoi(st_env) >= 2 && atoi(st_env) < stages) stages = atoi(st_env);
-    p->stages = stages;
-    p->smem = p->BK == 64 ? smem_bytes<64>(p->BN, stages, P) : smem_bytes<32>(p->BN, stages, P);
-    if (p->smem > budget) {
-        set_error("tensor-core plan needs %zu B of shared memory", p->smem);
-        free(p);
-        return QN_EUNSUPPORTED;
-    }
+    p->stages = tc_stages(p->BK);
+    p->smem = tc_smem_bytes(p->BK, p->stages);
     p->grid = p->ntiles < num_sms ? p->ntiles : num_sms;
+    if (tc_set_attributes() != QN_OK) {
+        free(p);
+        return QN_ECUDA;
+    }
+    CUtensorMap h[8];
     int rc = QN_OK;
     for (int b = 0; b < 2 && rc == QN_OK; ++b) {
         p->bufs_hi[b] = bufs_hi[b];
         p->bufs_lo[b] = bufs_lo[b];
-        rc = encode_2d(&p->a_hi[b], bufs_hi[b], P, p->Mtot, p->BK, BM, p->BK);
-        if (rc == QN_OK) rc = encode_2d(&p->a_lo[b], bufs_lo[b], P, p->Mtot, p->BK, BM, p->BK);
+        rc = tc_encode_2d(&h[b], bufs_hi[b], P, p->Mtot, p->BK, BM, p->BK);
+        if (rc == QN_OK) rc = tc_encode_2d(&h[2 + b], bufs_lo[b], P, p->Mtot, p->BK, BM, p->BK);
     }
-    if (rc == QN_OK) rc = encode_2d(&p->s_hi, S_hi, P, P, p->BK, p->BN, p->BK);
-    if (rc == QN_OK) rc = encode_2d(&p->s_lo, S_lo, P, P, p->BK, p->BN, p->BK);
-    if (rc == QN_OK) rc = encode_2d(&p->si_hi, Si_hi, P, P, p->BK, p->BN, p->BK);
-    if (rc == QN_OK) rc = encode_2d(&p->si_lo, Si_lo, P, P, p->BK, p->BN, p->BK);
+    if (rc == QN_OK) rc = tc_encode_2d(&h[4], S_hi, P, P, p->BK, p->BN, p->BK);
+    if (rc == QN_OK) rc = tc_encode_2d(&h[5], S_lo, P, P, p->BK, p->BN, p->BK);
+    if (rc == QN_OK) rc = tc_encode_2d(&h[6], Si_hi, P, P, p->BK, p->BN, p->BK);
+    if (rc == QN_OK) rc = tc_encode_2d(&h[7], Si_lo, P, P, p->BK, p->BN, p->BK);
+    if (rc == QN_OK && cudaMalloc(&p->maps, sizeof(h)) != cudaSuccess) rc = QN_ENOMEM;
+    if (rc == QN_OK && cudaMemcpy(p->maps, h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) rc = QN_ECUDA;
     if (rc != QN_OK) {
+        if (p->maps) cudaFree(p->maps);
         free(p);
         return rc;
     }
@@ -454,61 +468,89 @@ int tc_plan_create(TcPlan **out, int n, int P, int dim, __nv_bfloat16 *bufs_hi[2
     return QN_OK;
 }
 
-void tc_plan_destroy(TcPlan *plan) { free(plan); }
+void tc_plan_destroy(TcPlan *plan) {
+    if (!plan) return;
+    cudaFree(plan->maps);
+    free(plan);
+}
 
 template <int BK, int EPI, int DIM>
-static int launch_t(TcPlan *p, const CUtensorMap &a_hi, const CUtensorMap &a_lo, const CUtensorMap &b_hi,
-                    const CUtensorMap &b_lo, const TcArgs &args, cudaStream_t s) {
+static int launch_t(const TcGroup &g0, const TcGroup *groups, const TcTile *tiles, int ntiles, int stages,
+                    int *err, int grid, cudaStream_t s) {
     auto kern = k_modeprod_tc<BK, EPI, DIM>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        QN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr_set = true;
-    }
-    kern<<<p->grid, kThreads, p->smem, s>>>(a_hi, a_lo, b_hi, b_lo, args);
+    kern<<<grid, kThreads, tc_smem_bytes(BK, stages), s>>>(g0, groups, tiles, ntiles, stages, err);
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }
 
-template <int BK>
-static int launch_bk(TcPlan *p, const CUtensorMap &a_hi, const CUtensorMap &a_lo, const CUtensorMap &b_hi,
-                     const CUtensorMap &b_lo, Epi epi, const TcArgs &args, cudaStream_t s) {
-    if (p->dim == 3) {
-        switch (epi) {
-            case EPI_STORE: return launch_t<BK, EPI_STORE, 3>(p, a_hi, a_lo, b_hi, b_lo, args, s);
-            case EPI_DIVIDE: return launch_t<BK, EPI_DIVIDE, 3>(p, a_hi, a_lo, b_hi, b_lo, args, s);
-            case EPI_UPDATE: return launch_t<BK, EPI_UPDATE, 3>(p, a_hi, a_lo, b_hi, b_lo, args, s);
-            case EPI_DENSE: return launch_t<BK, EPI_DENSE, 3>(p, a_hi, a_lo, b_hi, b_lo, args, s);
-        }
-    } else {
-        switch (epi) {
-            case EPI_STORE: return launch_t<BK, EPI_STORE, 2>(p, a_hi, a_lo, b_hi, b_lo, args, s);
-            case EPI_DIVIDE: return launch_t<BK, EPI_DIVIDE, 2>(p, a_hi, a_lo, b_hi, b_lo, args, s);
-            case EPI_UPDATE: return launch_t<BK, EPI_UPDATE, 2>(p, a_hi, a_lo, b_hi, b_lo, args, s);
-            case EPI_DENSE: return launch_t<BK, EPI_DENSE, 2>(p, a_hi, a_lo, b_hi, b_lo, args, s);
-        }
+template <int BK, int DIM>
+static int launch_epi(Epi epi, const TcGroup &g0, const TcGroup *groups, const TcTile *tiles, int ntiles,
+                      int stages, int *err, int grid, cudaStream_t s) {
+    switch (epi) {
+        case EPI_STORE: return launch_t<BK, EPI_STORE, DIM>(g0, groups, tiles, ntiles, stages, err, grid, s);
+        case EPI_DIVIDE: return launch_t<BK, EPI_DIVIDE, DIM>(g0, groups, tiles, ntiles, stages, err, grid, s);
+        case EPI_UPDATE: return launch_t<BK, EPI_UPDATE, DIM>(g0, groups, tiles, ntiles, stages, err, grid, s);
+        case EPI_DENSE: return launch_t<BK, EPI_DENSE, DIM>(g0, groups, tiles, ntiles, stages, err, grid, s);
     }
     return QN_EINVAL;
 }
 
-int launch_modeprod_tc(TcPlan *p, int src, int dst, bool forward, Epi epi, const EpiArgs &e,
-                       cudaStream_t s) {
-    TcArgs args;
-    args.Mtot = p->Mtot;
-    args.P = p->P;
-    args.n = p->n;
-    args.BN = p->BN;
-    args.ntile_n = p->ntile_n;
-    args.ntiles = p->ntiles;
-    args.tmem_cols = p->tmem_cols;
-    args.stages = p->stages;
-    args.out_hi = (dst >= 0) ? p->bufs_hi[dst] : nullptr;
-    args.out_lo = (dst >= 0) ? p->bufs_lo[dst] : nullptr;
-    args.e = e;
-    const CUtensorMap &b_hi = forward ? p->si_hi : p->s_hi;
-    const CUtensorMap &b_lo = forward ? p->si_lo : p->s_lo;
-    if (p->BK == 64) return launch_bk<64>(p, p->a_hi[src], p->a_lo[src], b_hi, b_lo, epi, args, s);
-    return launch_bk<32>(p, p->a_hi[src], p->a_lo[src], b_hi, b_lo, epi, args, s);
+static int launch_any(int BK, int dim, Epi epi, const TcGroup &g0, const TcGroup *groups, const TcTile *tiles,
+                      int ntiles, int stages, int *err, int grid, cudaStream_t s) {
+    if (BK == 64)
+        return dim == 3 ? launch_epi<64, 3>(epi, g0, groups, tiles, ntiles, stages, err, grid, s)
+                        : launch_epi<64, 2>(epi, g0, groups, tiles, ntiles, stages, err, grid, s);
+    return dim == 3 ? launch_epi<32, 3>(epi, g0, groups, tiles, ntiles, stages, err, grid, s)
+                    : launch_epi<32, 2>(epi, g0, groups, tiles, ntiles, stages, err, grid, s);
+}
+
+template <int BK, int DIM>
+static int set_attr_dim() {
+    QN_CUDA(cudaFuncSetAttribute(k_modeprod_tc<BK, EPI_STORE, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    QN_CUDA(cudaFuncSetAttribute(k_modeprod_tc<BK, EPI_DIVIDE, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    QN_CUDA(cudaFuncSetAttribute(k_modeprod_tc<BK, EPI_UPDATE, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    QN_CUDA(cudaFuncSetAttribute(k_modeprod_tc<BK, EPI_DENSE, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    return QN_OK;
+}
+
+// Opt every instantiation in to the large dynamic shared memory once (before
+// any launch, so that launches can be captured into CUDA graphs).
+int tc_set_attributes() {
+    int rc = set_attr_dim<64, 2>();
+    if (rc == QN_OK) rc = set_attr_dim<64, 3>();
+    if (rc == QN_OK) rc = set_attr_dim<32, 2>();
+    if (rc == QN_OK) rc = set_attr_dim<32, 3>();
+    return rc;
+}
+
+int launch_modeprod_tc(TcPlan *p, int src, int dst, bool forward, Epi epi, const EpiArgs &e, cudaStream_t s) {
+    TcGroup g;
+    g.a_hi = p->maps + src;
+    g.a_lo = p->maps + 2 + src;
+    g.b_hi = p->maps + (forward ? 6 : 4);
+    g.b_lo = p->maps + (forward ? 7 : 5);
+    g.out_hi = (dst >= 0) ? p->bufs_hi[dst] : nullptr;
+    g.out_lo = (dst >= 0) ? p->bufs_lo[dst] : nullptr;
+    g.U = e.U;
+    g.lam32 = e.lam32;
+    g.shift = e.shift;
+    g.done = e.done;
+    g.dscale = 1.0f;
+    g.step = (float)e.step;
+    g.Mtot = p->Mtot;
+    g.P = p->P;
+    g.n = p->n;
+    g.BN = p->BN;
+    g.ntile_n = p->ntile_n;
+    g.ntiles = p->ntiles;
+    return launch_any(p->BK, p->dim, epi, g, nullptr, nullptr, p->ntiles, p->stages, e.err, p->grid, s);
+}
+
+int launch_modeprod_tc_grouped(const TcGroup *groups, const TcTile *tiles, int ntiles, int dim, int BK, Epi epi,
+                               int *err, int grid, cudaStream_t s) {
+    TcGroup dummy;
+    memset(&dummy, 0, sizeof(dummy));
+    return launch_any(BK, dim, epi, dummy, groups, tiles, ntiles, tc_stages(BK), err, grid, s);
 }
 
 }  // namespace qn

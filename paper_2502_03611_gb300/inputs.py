@@ -145,3 +145,38 @@ def random_field(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndar
         z = z ^ (z >> np.uint64(31))
     unit = ((z >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
     return (lo + (hi - lo) * unit).reshape(shape)
+
+
+# ---------------------------------------------------------------------------
+# coupled two-component systems (batched workload)
+# ---------------------------------------------------------------------------
+COUPLED_SIZES = (63, 127, 255, 511)
+
+
+def coupled_params(seed: int, i: int, sizes=COUPLED_SIZES):
+    """(n, alpha, D) of instance i of batch `seed`: SplitMix64(seed*1000 + i)
+    draws n uniformly from `sizes`, alpha ~ U[0,1], D ~ U[0.1, 10]."""
+    rng = SplitMix64(seed * 1000 + i)
+    k = min(int(rng.next_unit() * len(sizes)), len(sizes) - 1)
+    alpha = rng.next_uniform(0.0, 1.0)
+    D = rng.next_uniform(0.1, 10.0)
+    return sizes[k], alpha, D
+
+
+def coupled_problem(n: int, alpha: float, D: float, seed_i: int, kmax: int = 4, amp: float = 0.1,
+                    b: float = 1.0):
+    """Manufactured pair for -Lap u + b u^3 + alpha v = f1, -D Lap v + b v^3 - alpha u = f2
+    on the n x n interior grid: u*, v* are independent 2-D manufactured solutions
+    (coefficient seeds 2*seed_i and 2*seed_i + 1), and f1, f2 are evaluated
+    analytically. Returns (u*, v*, f1, f2)."""
+    out = []
+    laps = []
+    for s in (2 * seed_i, 2 * seed_i + 1):
+        coef = amp * manufactured_coeffs(s, 2, kmax)
+        coef[0, 0] += 1.0
+        out.append(sine_series(coef, n))
+        laps.append(sine_series(coef * (math.pi ** 2) * mode_wavenumber_sq(kmax, 2), n))
+    u, v = out
+    f1 = laps[0] + b * u ** 3 + alpha * v
+    f2 = D * laps[1] + b * v ** 3 - alpha * u
+    return u, v, f1, f2

@@ -70,6 +70,20 @@ class QnProfile(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class QnSysInstance(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("alpha", ctypes.c_double), ("D", ctypes.c_double),
+                ("U", ctypes.c_void_p), ("V", ctypes.c_void_p), ("f1", ctypes.c_void_p),
+                ("f2", ctypes.c_void_p)]
+
+
+class QnSysResult(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("rel", ctypes.c_double),
+                ("time_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class QnError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"libqn error {code}: {msg}")
@@ -103,6 +117,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "qn_solve_host": (ctypes.c_int, [P, P, P, ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult),
                                          ctypes.POINTER(QnStats), ctypes.c_int, P]),
         "qn_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
+        "qn_residual_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                               P, P, P, ctypes.POINTER(QnStats), P]),
+        "qn_batch_create": (ctypes.c_int, [ctypes.POINTER(QnSysInstance), ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(P)]),
+        "qn_batch_solve": (ctypes.c_int, [P, ctypes.POINTER(QnOpts), ctypes.POINTER(QnSysResult), P]),
+        "qn_batch_destroy": (ctypes.c_int, [P]),
+        "qn_autotune_tile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
         "qn_profile_read": (ctypes.c_int, [P, ctypes.POINTER(QnProfile)]),
     }
     for name, (res, args) in sig.items():
@@ -265,3 +287,50 @@ def qn_profile_read(ctx: QnContext) -> dict:
     p = QnProfile()
     _check(load_library().qn_profile_read(ctx.handle, ctypes.byref(p)))
     return p.as_dict()
+
+
+def qn_autotune_tile(n: int, copies: int = 16):
+    """Project autotuner: fastest (bk, bn) for the grouped mode product at size n."""
+    bk, bn, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(load_library().qn_autotune_tile(n, copies, ctypes.byref(bk), ctypes.byref(bn), ctypes.byref(ms)))
+    return bk.value, bn.value, ms.value
+
+
+class QnBatch:
+    """Owns a qn_batch over coupled 2-D instances. `instances` is a list of
+    dicts with n, alpha, D and float64 CUDA tensors U, V, f1, f2 (n*n each);
+    the tensors must outlive the batch (the object keeps references)."""
+
+    def __init__(self, instances, bk: int = 0, bn=None):
+        lib = load_library()
+        self._keep = instances
+        arr = (QnSysInstance * len(instances))()
+        for i, d in enumerate(instances):
+            nn = d["n"] * d["n"]
+            arr[i] = QnSysInstance(d["n"], d["alpha"], d["D"], _dptr(d["U"], nn, "U"), _dptr(d["V"], nn, "V"),
+                                   _dptr(d["f1"], nn, "f1"), _dptr(d["f2"], nn, "f2"))
+        bnarr = None
+        if bn is not None:
+            bnarr = (ctypes.c_int * len(instances))(*[int(x) for x in bn])
+        h = ctypes.c_void_p()
+        _check(lib.qn_batch_create(arr, len(instances), int(bk), bnarr, ctypes.byref(h)))
+        self._h = h
+        self.count = len(instances)
+
+    def solve(self, tol=1e-10, max_it=200, sync_every=4, stream=None):
+        opts = make_opts(tol, max_it, None, 1.0, sync_every)
+        res = (QnSysResult * self.count)()
+        rc = load_library().qn_batch_solve(self._h, ctypes.byref(opts), res, _stream_ptr(stream))
+        _check(rc, allowed=(QN_OK, QN_ENOTCONV, QN_EDIVERGED))
+        return rc, [r.as_dict() for r in res]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().qn_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
