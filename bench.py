@@ -47,10 +47,11 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end solve")
-    ap.add_argument("--quick", action="store_true", help="= --no-fp64 --no-cpu --no-e2e")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched coupled-systems measurement")
+    ap.add_argument("--quick", action="store_true", help="= --no-fp64 --no-cpu --no-e2e --no-batched")
     a = ap.parse_args()
     if a.quick:
-        a.no_fp64 = a.no_cpu = a.no_e2e = True
+        a.no_fp64 = a.no_cpu = a.no_e2e = a.no_batched = True
     return a
 
 
@@ -155,6 +156,58 @@ def cpu_oracle_baseline(n: int, seed: int, iters_timed: int = 1):
     per_it = statistics.mean(times)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return per_it * its * 1e3, {"per_iteration_s": per_it, "iterations_assumed": its, "cores": cores}
+
+
+def run_batched(qn, seed=0, count=256, reps=3):
+    """Batched coupled 2-D systems: 256 instances, n uniform on {63,127,255,511},
+    alpha ~ U[0,1], D ~ U[0.1,10]; tiles from the project autotuner per size.
+    Returns instances/s and p50/p99 of the per-instance device time to convergence."""
+    import numpy as np
+    import torch
+    from paper_2502_03611_gb300.inputs import coupled_params, coupled_problem
+    specs = [coupled_params(seed, i) + (seed * 1000 + i,) for i in range(count)]
+    tuned = {}
+    for n in sorted({s[0] for s in specs}):
+        tuned[n] = qn.qn_autotune_tile(n, copies=16)
+    # one K-tile per launch: the one tuned for the largest (costliest) size;
+    # other sizes keep their tuned N-tile when it was tuned with that K-tile
+    bk = tuned[max(tuned)][0]
+    insts = []
+    for (n, alpha, D, seed_i) in specs:
+        _, _, f1, f2 = coupled_problem(n, alpha, D, seed_i)
+        insts.append({"n": n, "alpha": alpha, "D": D,
+                      "U": torch.zeros(n * n, dtype=torch.float64, device="cuda"),
+                      "V": torch.zeros(n * n, dtype=torch.float64, device="cuda"),
+                      "f1": torch.from_numpy(f1.reshape(-1)).cuda(), "f2": torch.from_numpy(f2.reshape(-1)).cuda()})
+    bn = [tuned[i["n"]][1] if tuned[i["n"]][0] == bk else 0 for i in insts]
+    batch = qn.QnBatch(insts, bk=bk, bn=bn)
+    stream = torch.cuda.current_stream()
+    times, per_inst, its = [], [], []
+    for rep in range(reps + 2):
+        for i in insts:
+            i["U"].zero_()
+            i["V"].zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, res = batch.solve(sync_every=4)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep >= 2:
+            times.append(e0.elapsed_time(e1))
+            per_inst += [r["time_ms"] for r in res]
+            its += [r["iterations"] for r in res]
+        ok = rc == 0 and all(r["status"] == 0 for r in res)
+    ms = statistics.median(times)
+    return {"workload": f"{count} coupled 2-D systems, n uniform on {{63,127,255,511}}, alpha~U[0,1], "
+                        f"D~U[0.1,10], tol 1e-10, seed {seed}",
+            "instances_per_s": round(count / (ms * 1e-3), 1), "ms_per_batch": round(ms, 3),
+            "p50_instance_ms": round(float(np.percentile(per_inst, 50)), 3),
+            "p99_instance_ms": round(float(np.percentile(per_inst, 99)), 3),
+            "iterations_mean": round(float(np.mean(its)), 2), "iterations_max": int(max(its)),
+            "converged": ok, "tiles": {str(n): {"bk": v[0], "bn": v[1], "ms": round(v[2], 4)} for n, v in tuned.items()},
+            "bk_used": bk, "steps": reps}
 
 
 def run_reference(a):
@@ -384,6 +437,10 @@ def main():
                  "speedup_mixed_vs_fp64": round(ms64 / ms_max, 2)}
         del ctx64, A, B
 
+    batched = None
+    if not a.no_batched and a.precision == "bf16x3":
+        batched = run_batched(qn)
+
     cpu = None
     if not a.no_cpu and rank == 0 and world == 1:
         ms_cpu, det = cpu_oracle_baseline(n, a.seed)
@@ -408,7 +465,7 @@ def main():
             "final_rel": max(rels), "converged": ok,
             "solves_per_s": round(world * 1e3 / ms_max, 3),
             "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
-            "e2e": e2e, "plain_fp64": plain, "cpu_baseline": cpu, "clocks": clocks,
+            "e2e": e2e, "plain_fp64": plain, "batched": batched, "cpu_baseline": cpu, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
