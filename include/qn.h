@@ -240,6 +240,70 @@ int qn_batch_destroy(qn_batch *b);
  * returns the fastest. best_ms: mean time of one grouped launch (host). */
 int qn_autotune_tile(int n, int copies, int *best_bk, int *best_bn, double *best_ms);
 
+/* ---- learned warm start ---------------------------------------------------------
+ * A small neural operator maps the source f, restricted to a coarse G^3 grid,
+ * to a coarse initial iterate, which is prolonged to the fine grid as U_0.
+ * Network: lift 1 -> 32 channels; `blocks` blocks of
+ *   z = synthesis(R_k . analysis(h)) + h W + b,  h <- gelu(z) (not after the last),
+ * with analysis / synthesis in the first `modes` sine modes per axis
+ * (orthonormal Dirichlet sine basis) and per-mode 32x32 mixing R_k; then a
+ * projection 32 -> 1. Activations are stored in BF16; arithmetic,
+ * accumulation, master weights, gradients and AdamW moments are FP32.
+ * Flat parameter order: wl(32), bl(32), per block R(modes^3*32*32, index
+ * [kz][ky][kx][i][o]), W(32*32, [i][o]), b(32); then wp(32), bp(1).
+ * The paper has no learned component (this extends the solver's start). */
+typedef struct qn_net qn_net;
+
+/* Number of parameters for channels (must be 32), modes, blocks. */
+long long qn_net_param_count(int channels, int modes, int blocks);
+
+/* Create a network on the current device. G: coarse grid nodes per axis
+ * (2..256), channels == 32, modes in 1..min(G, 16), blocks 1..16,
+ * max_batch 1..64 (activation buffers are sized for it). Parameters start at
+ * zero: set them with qn_net_set_params. */
+int qn_net_create(int G, int channels, int modes, int blocks, int max_batch, qn_net **out);
+int qn_net_destroy(qn_net *net);
+
+/* Copy all parameters from / to a host float array of qn_net_param_count
+ * entries. Setting parameters resets the AdamW moments and step count. */
+int qn_net_set_params(qn_net *net, const float *host_params, long long count);
+int qn_net_get_params(qn_net *net, float *host_params, long long count);
+
+/* Inference on B coarse inputs: f_coarse, out: device float arrays [B][G^3]. */
+int qn_net_forward(qn_net *net, const float *f_coarse, float *out, int B, void *stream);
+
+/* Mean-squared loss against target [B][G^3] and its gradient (forward +
+ * backward). grads_out: device float array of qn_net_param_count entries, or
+ * NULL. loss: host, or NULL (then the call does not synchronise). */
+int qn_net_gradients(qn_net *net, const float *f_coarse, const float *target, int B, float *grads_out,
+                     double *loss, void *stream);
+
+/* One AdamW step (beta1 0.9, beta2 0.999, eps 1e-8, decoupled weight decay)
+ * on the loss of qn_net_gradients. loss: host, or NULL. */
+int qn_net_train_step(qn_net *net, const float *f_coarse, const float *target, int B, float lr,
+                      float weight_decay, double *loss, void *stream);
+
+/* U0 (device, n^3 doubles) = out_scale * prolong(net(in_scale * restrict(f))),
+ * f: device, n^3 doubles. */
+int qn_net_predict(qn_net *net, const double *f_fine, int n, double in_scale, double out_scale,
+                   double *U0, void *stream);
+
+/* Trilinear transfer of B fields from the m_from^3 to the m_to^3 interior grid
+ * of (0,1)^3 (nodes j/(m+1), zero boundary), times scale. src, dst: device. */
+int qn_interp3d(const double *src, int m_from, double *dst, int m_to, int B, double scale, void *stream);
+int qn_interp3d_f32(const double *src, int m_from, float *dst, int m_to, int B, double scale, void *stream);
+
+/* Warm-started solve. U0 from qn_net_predict, then one quasi-Newton step
+ * U1 = U0 - delta. The correction delta estimates the error of U0, so if
+ * ||delta|| < ||U0|| / 2 the solve continues from U1 (the step counts as an
+ * iteration, *used_warm = 1); otherwise, or if U0 is not finite, it restarts
+ * from the zero start (*used_warm = 0). ||F(U0)|| is not the criterion: the
+ * trilinear prolongation leaves high-frequency error that A_h amplifies in
+ * the residual while the first correction removes it. ctx: 3-D context with
+ * the same n. U, f: device, n^3. Uses stream-ordered temporary memory. */
+int qn_solve_warm(qn_ctx *ctx, qn_net *net, double *U, const double *f, int n, double in_scale,
+                  double out_scale, const qn_opts *opts, qn_result *res, int *used_warm, void *stream);
+
 /* ---- measurement ------------------------------------------------------------- */
 typedef struct qn_profile {
     long long launches;       /* kernels launched that did work since qn_profile_enable

@@ -180,3 +180,45 @@ def coupled_problem(n: int, alpha: float, D: float, seed_i: int, kmax: int = 4, 
     f1 = laps[0] + b * u ** 3 + alpha * v
     f2 = D * laps[1] + b * v ** 3 - alpha * u
     return u, v, f1, f2
+
+
+# ---------------------------------------------------------------------------
+# Gaussian random field sources (learned warm-start workload)
+# ---------------------------------------------------------------------------
+GRF_KMAX = 32
+
+
+def normals_vec(seed: int, count: int) -> np.ndarray:
+    """count standard normals from SplitMix64(seed), vectorised: normal i uses
+    the stream outputs 2i and 2i+1 as (u1, u2) of the Box-Muller cosine branch."""
+    u = random_field((2 * count,), seed, 0.0, 1.0)
+    u1, u2 = u[0::2], u[1::2]
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+def grf_coeffs(seed: int, kmax: int = GRF_KMAX) -> np.ndarray:
+    """Sine-series coefficients xi_k / (1 + |k|^2), k in {1..kmax}^3, xi ~ N(0,1).
+
+    Power spectrum (1 + |k|^2)^-2 (amplitude = its square root); modes above
+    kmax per axis are dropped (they carry a small fraction of the variance)."""
+    xi = normals_vec(seed, kmax ** 3).reshape(kmax, kmax, kmax)
+    return xi / (1.0 + mode_wavenumber_sq(kmax, 3))
+
+
+def grf_source(n: int, seed: int, kmax: int = GRF_KMAX, scale: float = 1.0) -> np.ndarray:
+    """Dirichlet-consistent GRF on the n^3 interior grid, rescaled to RMS `scale`
+    (unit empirical variance for scale 1; the field has zero mean in law)."""
+    f = sine_series(grf_coeffs(seed, kmax), n)
+    return f * (scale / math.sqrt(float(np.mean(f * f))))
+
+
+def grf_source_torch(n: int, seed: int, device="cuda", kmax: int = GRF_KMAX, scale: float = 1.0):
+    """grf_source with the separable synthesis done by torch on `device`
+    (FP64; the same coefficients, the same sums, for fast data generation)."""
+    import torch
+    c = torch.from_numpy(grf_coeffs(seed, kmax)).to(device)
+    B = torch.from_numpy(sine_basis(n, kmax)).to(device)            # (kmax, n)
+    t = torch.einsum("abk,kx->abx", c, B)                           # [kz, ky, x]
+    t = torch.einsum("ky,akx->ayx", B, t)                           # [kz, y, x]
+    f = torch.einsum("kz,kyx->zyx", B, t)                           # [z, y, x]
+    return f * (scale / torch.sqrt(torch.mean(f * f)))

@@ -125,6 +125,21 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "qn_batch_destroy": (ctypes.c_int, [P]),
         "qn_autotune_tile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+        "qn_net_param_count": (ctypes.c_longlong, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "qn_net_create": (ctypes.c_int, [ctypes.c_int] * 5 + [ctypes.POINTER(P)]),
+        "qn_net_destroy": (ctypes.c_int, [P]),
+        "qn_net_set_params": (ctypes.c_int, [P, P, ctypes.c_longlong]),
+        "qn_net_get_params": (ctypes.c_int, [P, P, ctypes.c_longlong]),
+        "qn_net_forward": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
+        "qn_net_gradients": (ctypes.c_int, [P, P, P, ctypes.c_int, P, ctypes.POINTER(ctypes.c_double), P]),
+        "qn_net_train_step": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                             ctypes.POINTER(ctypes.c_double), P]),
+        "qn_net_predict": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, P]),
+        "qn_interp3d": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_double, P]),
+        "qn_interp3d_f32": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_double, P]),
+        "qn_solve_warm": (ctypes.c_int, [P, P, P, P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult),
+                                         ctypes.POINTER(ctypes.c_int), P]),
         "qn_profile_read": (ctypes.c_int, [P, ctypes.POINTER(QnProfile)]),
     }
     for name, (res, args) in sig.items():
@@ -334,3 +349,100 @@ class QnBatch:
             self.close()
         except Exception:
             pass
+
+
+def _fptr(t, numel, name, dtype="float32"):
+    import torch
+    want = torch.float32 if dtype == "float32" else torch.float64
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == want and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def qn_interp3d(src, m_from: int, dst, m_to: int, batch: int = 1, scale: float = 1.0, stream=None):
+    """Trilinear transfer of `batch` fields between interior grids (device tensors)."""
+    lib = load_library()
+    if dst.dtype.is_floating_point and dst.element_size() == 4:
+        _check(lib.qn_interp3d_f32(_fptr(src, batch * m_from ** 3, "src", "float64"), m_from,
+                                   _fptr(dst, batch * m_to ** 3, "dst", "float32"), m_to, batch, scale,
+                                   _stream_ptr(stream)))
+    else:
+        _check(lib.qn_interp3d(_fptr(src, batch * m_from ** 3, "src", "float64"), m_from,
+                               _fptr(dst, batch * m_to ** 3, "dst", "float64"), m_to, batch, scale,
+                               _stream_ptr(stream)))
+
+
+class QnNet:
+    """Owns a qn_net (learned warm start)."""
+
+    def __init__(self, G: int, modes: int = 6, blocks: int = 4, max_batch: int = 8, channels: int = 32):
+        lib = load_library()
+        self.G, self.M, self.L, self.C, self.max_batch = G, modes, blocks, channels, max_batch
+        self.nparams = lib.qn_net_param_count(channels, modes, blocks)
+        h = ctypes.c_void_p()
+        _check(lib.qn_net_create(G, channels, modes, blocks, max_batch, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(load_library().qn_net_set_params(self._h, ctypes.c_void_p(p.ctypes.data), p.size))
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.nparams, dtype=np.float32)
+        _check(load_library().qn_net_get_params(self._h, ctypes.c_void_p(p.ctypes.data), p.size))
+        return p
+
+    def forward(self, f_coarse, out, batch: int, stream=None):
+        n = batch * self.G ** 3
+        _check(load_library().qn_net_forward(self._h, _fptr(f_coarse, n, "f"), _fptr(out, n, "out"), batch,
+                                             _stream_ptr(stream)))
+
+    def gradients(self, f_coarse, target, batch: int, grads, stream=None) -> float:
+        n = batch * self.G ** 3
+        loss = ctypes.c_double()
+        _check(load_library().qn_net_gradients(self._h, _fptr(f_coarse, n, "f"), _fptr(target, n, "target"), batch,
+                                               _fptr(grads, self.nparams, "grads"), ctypes.byref(loss),
+                                               _stream_ptr(stream)))
+        return loss.value
+
+    def train_step(self, f_coarse, target, batch: int, lr: float, weight_decay: float = 0.0, stream=None,
+                   want_loss: bool = True):
+        n = batch * self.G ** 3
+        loss = ctypes.c_double()
+        _check(load_library().qn_net_train_step(self._h, _fptr(f_coarse, n, "f"), _fptr(target, n, "target"), batch,
+                                                ctypes.c_float(lr), ctypes.c_float(weight_decay),
+                                                ctypes.byref(loss) if want_loss else None, _stream_ptr(stream)))
+        return loss.value if want_loss else None
+
+    def predict(self, f_fine, n: int, U0, in_scale: float = 1.0, out_scale: float = 1.0, stream=None):
+        _check(load_library().qn_net_predict(self._h, _fptr(f_fine, n ** 3, "f", "float64"), n, in_scale, out_scale,
+                                             _fptr(U0, n ** 3, "U0", "float64"), _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().qn_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qn_solve_warm(ctx: QnContext, net: QnNet, U, f, in_scale=1.0, out_scale=1.0, tol=1e-10, max_it=200,
+                  sync_every=2, stream=None):
+    opts = make_opts(tol, max_it, None, 1.0, sync_every)
+    res = QnResult()
+    used = ctypes.c_int()
+    rc = load_library().qn_solve_warm(ctx.handle, net.handle, _dptr(U, ctx.numel, "U"), _dptr(f, ctx.numel, "f"),
+                                      ctx.n, in_scale, out_scale, ctypes.byref(opts), ctypes.byref(res),
+                                      ctypes.byref(used), _stream_ptr(stream))
+    _check(rc, allowed=(QN_OK, QN_ENOTCONV, QN_EDIVERGED))
+    return {"iterations": res.iterations, "status": res.status, "rel": res.rel, "used_warm": bool(used.value)}
