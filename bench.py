@@ -369,6 +369,15 @@ def main():
         kernels["residual"]["share"] = round(prof["residual_ms"] / tot, 4)
         kernels["modeprod"]["share"] = round(prof["modeprod_ms"] / tot, 4)
         kernels["finalize"]["share"] = round(prof["finalize_ms"] / tot, 4)
+    kernels["modeprod"]["roofline"] = roofline
+    # the JSON line's roofline is that of the kernel with the largest time share
+    if prof["residual_ms"] > prof["modeprod_ms"]:
+        roofline = {"kernel": "k_residual", "bound": "hbm", "achieved": round(res_gbs, 1), "peak": hbm,
+                    "unit": "GB/s", "frac": round(res_gbs / hbm, 4), "traffic": None,
+                    "peak_source": f"HBM copy bandwidth ({peak_src})",
+                    "bytes_per_launch_algorithmic": res_bytes, "avg_launch_ms": round(res_avg_ms, 4),
+                    "launches": prof["residual_launches"],
+                    "note": "issue-bound (integer stencil + FP64 pipe), see profiles/residual_383.md"}
     gpu_launches = int(prof["launches"])
 
     # ---- end to end through the public API with host buffers (copies inside the timed region)
