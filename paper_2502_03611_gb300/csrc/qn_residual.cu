@@ -67,7 +67,7 @@ __device__ Red4 block_reduce(Red4 v) {
 // stop test sums float(r)^2 with Kahan in FP32). min/max |U| use the integer
 // bit pattern; the FP32 rounding of r runs on the integer pipe.
 // KIND 0: lam u + b u^3 (general); 1: lam = 0; 2: lam = 0 and b = 1 (3 FP64 ops).
-template <int DIM, bool SPLIT, bool FAST, int KIND>
+template <int DIM, bool SPLIT, bool FAST, int KIND, bool WANT_F2>
 __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
     if (a.done != nullptr && *(volatile const int *)a.done) return;
     const int n = a.n;
@@ -76,7 +76,6 @@ __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
     const double *__restrict__ U = a.U;
     const double *__restrict__ f = a.f;
     const long long nn = (long long)n * n;
-    const bool want_f2 = a.want_f2 != 0;
     double r2 = 0.0, f2 = 0.0;
     float kr2 = 0.0f, kc = 0.0f;                          // Kahan sum of float(r)^2
     unsigned long long amin = 0x7FFFFFFFFFFFFFFFull, amax = 0ull;
@@ -114,7 +113,7 @@ __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
                 const unsigned long long ab = abs_bits(u);
                 amin = ab < amin ? ab : amin;
                 amax = ab > amax ? ab : amax;
-                if (want_f2) f2 = fma(fv, fv, f2);
+                if (WANT_F2) f2 = fma(fv, fv, f2);
                 if (FAST) {
                     const float rf = d2f_rn(r);
                     const float yk = fmaf(rf, rf, -kc);
@@ -234,14 +233,22 @@ int launch_split_pad(const double *r, int n, int P, int dim, __nv_bfloat16 *hi, 
     return QN_OK;
 }
 
+template <int DIM, bool SPLIT, bool FAST, bool WF2>
+static void launch_res4(const ResidualArgs &a, int grid, cudaStream_t s) {
+    if (a.lam != 0.0)
+        k_residual<DIM, SPLIT, FAST, 0, WF2><<<grid, 256, 0, s>>>(a);
+    else if (a.b != 1.0)
+        k_residual<DIM, SPLIT, FAST, 1, WF2><<<grid, 256, 0, s>>>(a);
+    else
+        k_residual<DIM, SPLIT, FAST, 2, WF2><<<grid, 256, 0, s>>>(a);
+}
+
 template <int DIM, bool SPLIT, bool FAST>
 static void launch_res3(const ResidualArgs &a, int grid, cudaStream_t s) {
-    if (a.lam != 0.0)
-        k_residual<DIM, SPLIT, FAST, 0><<<grid, 256, 0, s>>>(a);
-    else if (a.b != 1.0)
-        k_residual<DIM, SPLIT, FAST, 1><<<grid, 256, 0, s>>>(a);
+    if (a.want_f2)
+        launch_res4<DIM, SPLIT, FAST, true>(a, grid, s);
     else
-        k_residual<DIM, SPLIT, FAST, 2><<<grid, 256, 0, s>>>(a);
+        launch_res4<DIM, SPLIT, FAST, false>(a, grid, s);
 }
 
 template <int DIM, bool SPLIT>
