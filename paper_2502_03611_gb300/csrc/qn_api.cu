@@ -77,6 +77,7 @@ struct qn_ctx {
     int prof_on;
     int cur_iter;
     long long launches;
+    int res_fp64_warps;   // residual inside the split solve: FP64-stencil warps per block (of 8)
 };
 
 enum ProfKind { PK_RESIDUAL = 0, PK_FINALIZE = 1, PK_MP_STORE = 2, PK_MP_DIVIDE = 3, PK_MP_LAST = 4,
@@ -234,6 +235,11 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
     CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
     c->n = p->n;
     c->dim = p->dim;
+    {
+        const char *env = getenv("QN_RES_FP64_WARPS");
+        const int w = env ? atoi(env) : 3;
+        c->res_fp64_warps = (w >= 0 && w <= 8) ? w : 3;
+    }
     c->P = ((p->n + 63) / 64) * 64;
     c->N = 1;
     c->NP = 1;
@@ -374,6 +380,7 @@ static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double 
     // the split-precision solve only needs ||F|| to ~1e-7 for its stop test:
     // its residual sums float(r)^2 (Kahan) instead of an FP64 FMA per point
     a.fast = (to_work && c->prob.precision == QN_PREC_BF16X3) ? 1 : 0;
+    a.fp64_warps = a.fast ? c->res_fp64_warps : 0;
     a.want_f2 = (!to_work || c->cur_iter == 0) ? 1 : 0;
     const long pr = prof_begin(c, PK_RESIDUAL, s);
     const int rc = launch_residual(a, c->nparts, s);

@@ -41,6 +41,8 @@ struct ResidualArgs {
     const int *done;           // skip when *done != 0 (nullptr: never skip)
     int fast;                  // 1: sum r^2 from float(r) (Kahan, FP32) -- inside the solve loop
     int want_f2;               // 1: also sum f^2 (first iteration / standalone residual)
+    int fp64_warps;            // warps (of 8) per block that sum the stencil on the FP64 pipe;
+                               // the others use the exact fixed-point sum on the integer pipe
 };
 
 // Epilogue selector shared by both mode-product kernels.

@@ -59,26 +59,35 @@ __device__ Red4 block_reduce(Red4 v) {
     return v;
 }
 
-// FP64-pipe budget per interior point (the GPU issues ~2 FP64 ops/clk/SM):
-// the stencil 2d*u - sum(neighbours) is summed exactly in fixed point on the
-// integer pipe (more accurate than an FP64 sum), leaving u^2, u^3, b u^3 - f
-// and lap/h^2 + (...) = 4 FP64 ops (+1 with lam != 0, +1 for sum f^2 on the
-// first iteration, +1 for sum r^2 outside the split-precision solve, whose
-// stop test sums float(r)^2 with Kahan in FP32). min/max |U| use the integer
-// bit pattern; the FP32 rounding of r runs on the integer pipe.
-// KIND 0: lam u + b u^3 (general); 1: lam = 0; 2: lam = 0 and b = 1 (3 FP64 ops).
-template <int DIM, bool SPLIT, bool FAST, int KIND, bool WANT_F2>
-__global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
-    if (a.done != nullptr && *(volatile const int *)a.done) return;
+// FP64-pipe budget per interior point (the GPU issues ~2 FP64 ops/clk/SM).
+// Two implementations of the stencil 2d*u - sum(neighbours), run by different
+// warps of the same block so that the FP64 pipe and the integer pipe work at
+// the same time:
+//   INT_STENCIL  exact fixed-point sum on the integer pipe (qn_numeric.cuh),
+//                ~20x more instructions but no FP64 operation;
+//   FP64         five adds and one FMA on the FP64 pipe.
+// The rest costs u^2, b u^3 - f and lap/h^2 + (...): 3 FP64 ops (+1 with
+// lam != 0, +1 with b != 1, +1 for sum f^2 on the first iteration, +1 for
+// sum r^2 outside the split-precision solve, whose stop test sums float(r)^2
+// with Kahan in FP32). min/max |U| use the integer bit pattern; the FP32
+// rounding of r runs on the integer pipe. Each warp sweeps its own columns
+// with one of the two loops (a warp-uniform branch around the whole loop, so
+// neither variant is predicated into the other).
+// KIND 0: lam u + b u^3 (general); 1: lam = 0; 2: lam = 0 and b = 1.
+struct ResAcc {
+    double r2, f2;
+    float kr2, kc;
+    unsigned long long amin, amax;
+};
+
+template <int DIM, bool SPLIT, bool FAST, int KIND, bool WANT_F2, bool INT_STENCIL>
+__device__ __forceinline__ void residual_sweep(const ResidualArgs &a, ResAcc &s) {
     const int n = a.n;
     const int P = SPLIT ? a.P : n;
     const long long rows = (DIM == 3) ? (long long)P * P : (long long)P;
     const double *__restrict__ U = a.U;
     const double *__restrict__ f = a.f;
     const long long nn = (long long)n * n;
-    double r2 = 0.0, f2 = 0.0;
-    float kr2 = 0.0f, kc = 0.0f;                          // Kahan sum of float(r)^2
-    unsigned long long amin = 0x7FFFFFFFFFFFFFFFull, amax = 0ull;
     for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
         const int y = (DIM == 3) ? (int)(row % P) : (int)row;
         const int z = (DIM == 3) ? (int)(row / P) : 0;
@@ -99,8 +108,14 @@ __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
                     nbv[2 * DIM - 1] = (z < n - 1) ? __ldg(U + c + nn) : 0.0;
                 }
                 const double fv = __ldg(f + c);
-                // exact fixed-point stencil on the integer pipe (qn_numeric.cuh)
-                const double lap = stencil_fixed<DIM>(u, nbv);
+                double lap;
+                if (INT_STENCIL) {
+                    lap = stencil_fixed<DIM>(u, nbv);
+                } else {
+                    double sum = (nbv[0] + nbv[1]) + (nbv[2] + nbv[3]);
+                    if (DIM == 3) sum += nbv[4] + nbv[5];
+                    lap = fma(2.0 * DIM, u, -sum);
+                }
                 const double u2 = u * u;
                 double t;
                 if (KIND == 2) {
@@ -111,17 +126,17 @@ __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
                 }
                 r = fma(lap, a.inv_h2, t);
                 const unsigned long long ab = abs_bits(u);
-                amin = ab < amin ? ab : amin;
-                amax = ab > amax ? ab : amax;
-                if (WANT_F2) f2 = fma(fv, fv, f2);
+                s.amin = ab < s.amin ? ab : s.amin;
+                s.amax = ab > s.amax ? ab : s.amax;
+                if (WANT_F2) s.f2 = fma(fv, fv, s.f2);
                 if (FAST) {
                     const float rf = d2f_rn(r);
-                    const float yk = fmaf(rf, rf, -kc);
-                    const float tk = kr2 + yk;
-                    kc = (tk - kr2) - yk;
-                    kr2 = tk;
+                    const float yk = fmaf(rf, rf, -s.kc);
+                    const float tk = s.kr2 + yk;
+                    s.kc = (tk - s.kr2) - yk;
+                    s.kr2 = tk;
                 } else {
-                    r2 = fma(r, r, r2);
+                    s.r2 = fma(r, r, s.r2);
                 }
                 if (a.R64 != nullptr) a.R64[c] = r;
             }
@@ -135,10 +150,20 @@ __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
             }
         }
     }
-    if (FAST) r2 = (double)kr2 - (double)kc;
-    const double umin = __longlong_as_double((long long)amin);
-    const double umax = __longlong_as_double((long long)amax);
-    Red4 acc{r2, f2, (amin == 0x7FFFFFFFFFFFFFFFull) ? INFINITY : umin * umin, umax * umax};
+}
+
+template <int DIM, bool SPLIT, bool FAST, int KIND, bool WANT_F2>
+__global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
+    if (a.done != nullptr && *(volatile const int *)a.done) return;
+    ResAcc s{0.0, 0.0, 0.0f, 0.0f, 0x7FFFFFFFFFFFFFFFull, 0ull};
+    if ((int)(threadIdx.x >> 5) < a.fp64_warps)
+        residual_sweep<DIM, SPLIT, FAST, KIND, WANT_F2, false>(a, s);
+    else
+        residual_sweep<DIM, SPLIT, FAST, KIND, WANT_F2, true>(a, s);
+    if (FAST) s.r2 = (double)s.kr2 - (double)s.kc;
+    const double umin = __longlong_as_double((long long)s.amin);
+    const double umax = __longlong_as_double((long long)s.amax);
+    Red4 acc{s.r2, s.f2, (s.amin == 0x7FFFFFFFFFFFFFFFull) ? INFINITY : umin * umin, umax * umax};
     acc = block_reduce(acc);
     if (threadIdx.x == 0) {
         double *p = a.partials + 4ll * blockIdx.x;
@@ -407,6 +432,7 @@ extern "C" int qn_residual_noalloc(int dim, int n, double lam, double b, const d
     a.done = nullptr;
     a.fast = 0;
     a.want_f2 = 1;
+    a.fp64_warps = 0;
     rc = launch_residual(a, grid, s);
     if (rc != QN_OK) return rc;
     rc = launch_finalize(partials, grid, state, stats, 1, b, lam, 0, 0, s);
