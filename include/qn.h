@@ -320,6 +320,9 @@ typedef struct qn_profile {
     double mp_divide_ms;
     int mp_last_launches;     /* last backward product, with the update (or dense store) */
     double mp_last_ms;
+    int residual_tiled_launches;   /* of residual_launches: the residuals of a 3-D split solve
+                                      from its third iteration on (no FP64 arithmetic) */
+    double residual_tiled_ms;
 } qn_profile;
 
 /* on != 0: from now on record a pair of CUDA events around every kernel

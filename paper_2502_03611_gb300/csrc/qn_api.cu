@@ -78,10 +78,15 @@ struct qn_ctx {
     int cur_iter;
     long long launches;
     int res_fp64_warps;   // residual inside the split solve: FP64-stencil warps per block (of 8)
+    float2 *fdf;          // 3-D split solve: padded FP32-pair copy of f (k_residual_tiled)
+    int res_tiled;        // 1: iterations >= 2 of a 3-D split solve use k_residual_tiled
+    int res_zc;           // planes per work item of k_residual_tiled
+    int res_parts;        // partial-sum records written by the last residual launch
+    int res_fx_headroom;  // DevState::fx_headroom for the solves of this context
 };
 
 enum ProfKind { PK_RESIDUAL = 0, PK_FINALIZE = 1, PK_MP_STORE = 2, PK_MP_DIVIDE = 3, PK_MP_LAST = 4,
-                PK_SPLIT = 5, PK_COUNT = 6 };
+                PK_SPLIT = 5, PK_RESIDUAL_TILED = 6, PK_COUNT = 7 };
 
 // Begin/end a timed launch. With profiling off these only count launches.
 static long prof_begin(qn_ctx *c, int kind, cudaStream_t s) {
@@ -170,6 +175,7 @@ static void ctx_free(qn_ctx *c) {
         cudaFree(c->blo[b]);
     }
     cudaFree(c->partials);
+    cudaFree(c->fdf);
     cudaFree(c->st);
     cudaFree(c->hist);
     cudaFree(c->err);
@@ -239,6 +245,16 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
         const char *env = getenv("QN_RES_FP64_WARPS");
         const int w = env ? atoi(env) : 3;
         c->res_fp64_warps = (w >= 0 && w <= 8) ? w : 3;
+        const char *et = getenv("QN_RES_TILED");
+        c->res_tiled = et ? (atoi(et) != 0) : 1;
+        const char *ez = getenv("QN_RES_ZC");
+        const int zc = ez ? atoi(ez) : 32;
+        c->res_zc = (zc >= 1 && zc <= 4096) ? zc : 32;
+        // exponent headroom of the fixed-point stencil (2 = room for 4x growth of
+        // max|U|); smaller values route more planes through the exact path
+        const char *eh = getenv("QN_RES_FX_HEADROOM");
+        const int hr = eh ? atoi(eh) : 2;
+        c->res_fx_headroom = (hr >= -16 && hr <= 2) ? hr : 2;
     }
     c->P = ((p->n + 63) / 64) * 64;
     c->N = 1;
@@ -309,6 +325,13 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
             CK(cudaMemset(c->bhi[b], 0, pb));
             CK(cudaMemset(c->blo[b], 0, pb));
         }
+        // the float-pair residual needs lam, b and 1/h^2 well inside the FP32 range
+        const bool pair_ok = fabs(p->lam) < 0x1p40 && fabs(p->b) < 0x1p20 && c->inv_h2 < 0x1p24;
+        if (c->dim == 3 && pair_ok) {
+            CK(cudaMalloc(&c->fdf, sizeof(float2) * (size_t)c->NP));
+        } else {
+            c->res_tiled = 0;
+        }
         rc = tc_plan_create(&c->plan, n, P, c->dim, c->bhi, c->blo, c->S_hi, c->S_lo, c->Si_hi, c->Si_lo,
                             c->num_sms);
         if (rc != QN_OK) {
@@ -336,6 +359,8 @@ static int reset_state(qn_ctx *c, double tol, int max_it, int beta_mode, double 
     h.max_it = max_it;
     h.beta_mode = beta_mode;
     h.beta_value = beta_value;
+    h.fx_headroom = c->res_fx_headroom;
+    h.npts = (double)c->N;
     QN_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     return QN_OK;
 }
@@ -355,7 +380,7 @@ static EpiArgs epi_args(qn_ctx *c, double *U, double step) {
 // Residual of U into the first working buffer (split planes or FP64), with partials.
 static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double *R64_override,
                             bool to_work, const int *done, cudaStream_t s) {
-    ResidualArgs a;
+    ResidualArgs a{};
     a.U = U;
     a.f = f;
     a.n = c->n;
@@ -378,12 +403,28 @@ static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double 
     a.partials = c->partials;
     a.done = done;
     // the split-precision solve only needs ||F|| to ~1e-7 for its stop test:
-    // its residual sums float(r)^2 (Kahan) instead of an FP64 FMA per point
-    a.fast = (to_work && c->prob.precision == QN_PREC_BF16X3) ? 1 : 0;
-    a.fp64_warps = a.fast ? c->res_fp64_warps : 0;
+    // from its second iteration on (RMS(f) known, which scales the sum) its
+    // residual sums float(r)^2 (Kahan) instead of an FP64 FMA per point
+    const bool split_solve = to_work && c->prob.precision == QN_PREC_BF16X3;
     a.want_f2 = (!to_work || c->cur_iter == 0) ? 1 : 0;
-    const long pr = prof_begin(c, PK_RESIDUAL, s);
-    const int rc = launch_residual(a, c->nparts, s);
+    a.fast = (split_solve && !a.want_f2) ? 1 : 0;
+    a.fp64_warps = split_solve ? c->res_fp64_warps : 0;
+    a.r2_exp = &c->st->r2_exp;
+    // the first residual of a 3-D split solve also writes the FP32-pair copy
+    // of f; from the third iteration on (max|U| of the previous iterate known)
+    // the residual runs without FP64 arithmetic
+    a.fdf = split_solve ? c->fdf : nullptr;
+    a.fx_fbad = &c->st->fx_fbad;
+    a.fx_e = &c->st->fx_e;
+    const bool tiled = a.fast && c->fdf != nullptr && c->res_tiled && c->cur_iter >= 2;
+    const long pr = prof_begin(c, tiled ? PK_RESIDUAL_TILED : PK_RESIDUAL, s);
+    int rc;
+    if (tiled) {
+        rc = launch_residual_tiled(a, c->nparts, c->res_zc, &c->res_parts, s);
+    } else {
+        rc = launch_residual(a, c->nparts, s);
+        c->res_parts = c->nparts;
+    }
     prof_end(c, pr, s);
     return rc;
 }
@@ -430,7 +471,7 @@ static int enqueue_iteration(qn_ctx *c, double *U, const double *f, double step,
     int rc = enqueue_residual(c, U, f, nullptr, true, &c->st->done, s);
     if (rc) return rc;
     const long pr = prof_begin(c, PK_FINALIZE, s);
-    rc = launch_finalize(c->partials, c->nparts, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 1,
+    rc = launch_finalize(c->partials, c->res_parts, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 1,
                          c->cur_iter > 0 ? 1 : 0, s);
     prof_end(c, pr, s);
     if (rc) return rc;
@@ -467,7 +508,7 @@ extern "C" int qn_residual(qn_ctx *c, const double *U, const double *f, double *
     rc = enqueue_residual(c, U, f, R, false, nullptr, s);
     if (rc) return rc;
     const long pr = prof_begin(c, PK_FINALIZE, s);
-    rc = launch_finalize(c->partials, c->nparts, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 0, 0, s);
+    rc = launch_finalize(c->partials, c->res_parts, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 0, 0, s);
     prof_end(c, pr, s);
     if (rc) return rc;
     if (st) {
@@ -666,8 +707,10 @@ extern "C" int qn_profile_read(qn_ctx *c, qn_profile *out) {
         ms[r.kind] += t;
         cnt[r.kind] += 1;
     }
-    out->residual_launches = cnt[PK_RESIDUAL];
-    out->residual_ms = ms[PK_RESIDUAL];
+    out->residual_launches = cnt[PK_RESIDUAL] + cnt[PK_RESIDUAL_TILED];
+    out->residual_ms = ms[PK_RESIDUAL] + ms[PK_RESIDUAL_TILED];
+    out->residual_tiled_launches = cnt[PK_RESIDUAL_TILED];
+    out->residual_tiled_ms = ms[PK_RESIDUAL_TILED];
     out->finalize_launches = cnt[PK_FINALIZE];
     out->finalize_ms = ms[PK_FINALIZE];
     out->modeprod_launches = cnt[PK_MP_STORE] + cnt[PK_MP_DIVIDE] + cnt[PK_MP_LAST];

@@ -47,7 +47,8 @@ struct SysInst {
 };
 
 struct SysState {
-    int done, status, it, pad;
+    int done, status, it;
+    int r2_exp;   // k: from the second iteration on, sum r^2 adds (float(r) 2^-k)^2 in FP32 (2^k ~ RMS(f))
     double beta, f_norm, rel, res;
     unsigned long long t_done;
 };
@@ -112,6 +113,13 @@ __global__ void k_sys_init(SysState *st, int count, SysCtl *ctl, double tol, int
     }
 }
 
+// sum f^2 and r^2 in FP64 (first iteration only; out of line so that the FP64
+// operations are not predicated into every later iteration's loop)
+static __device__ __noinline__ double2 first_iteration_sums(double2 acc, double g1, double g2, double Fu,
+                                                          double Fv) {
+    return make_double2(fma(g1, g1, fma(g2, g2, acc.x)), fma(Fu, Fu, fma(Fv, Fv, acc.y)));
+}
+
 __global__ void __launch_bounds__(256) k_sys_residual(const SysInst *__restrict__ inst,
                                                       const SysItem *__restrict__ items,
                                                       const SysState *__restrict__ st,
@@ -121,11 +129,12 @@ __global__ void __launch_bounds__(256) k_sys_residual(const SysInst *__restrict_
     if (S.done) return;
     const SysInst I = inst[it.inst];
     const int n = I.n, P = I.P;
-    const bool want_f2 = S.it == 0;
+    const bool want_f2 = S.it == 0;   // first iteration: sum f^2 and r^2 in FP64
     const double alpha = I.alpha, Dh2 = I.D * I.inv_h2;
     const float alpha_f = (float)alpha;
+    const float r2s = __int_as_float((127 - S.r2_exp) << 23);   // 2^-k
     float kr2 = 0.0f, kc = 0.0f;
-    double f2 = 0.0;
+    double f2 = 0.0, r2 = 0.0;
     float mxp = -INFINITY, mnm = INFINITY;
     for (int y = it.row0; y < it.row1; ++y) {
         for (int x = threadIdx.x; x < P; x += blockDim.x) {
@@ -154,12 +163,17 @@ __global__ void __launch_bounds__(256) k_sys_residual(const SysInst *__restrict_
                 const float sq = disc > 0.0f ? sqrtf(disc) : 0.0f;
                 mxp = fmaxf(mxp, 0.5f * (a + d + sq));
                 mnm = fminf(mnm, 0.5f * (a + d - sq));
-                if (want_f2) f2 = fma(g1, g1, fma(g2, g2, f2));
-                const float fu = d2f_rn(Fu), fv = d2f_rn(Fv);
-                const float yk = fmaf(fu, fu, fmaf(fv, fv, -kc));
-                const float tk = kr2 + yk;
-                kc = (tk - kr2) - yk;
-                kr2 = tk;
+                if (want_f2) {
+                    const double2 s2 = first_iteration_sums(make_double2(f2, r2), g1, g2, Fu, Fv);
+                    f2 = s2.x;
+                    r2 = s2.y;
+                } else {
+                    const float fu = __fmul_rn(d2f_rn(Fu), r2s), fv = __fmul_rn(d2f_rn(Fv), r2s);
+                    const float yk = fmaf(fu, fu, fmaf(fv, fv, -kc));
+                    const float tk = kr2 + yk;
+                    kc = (tk - kr2) - yk;
+                    kr2 = tk;
+                }
             }
             const int o = y * P + x;
             __nv_bfloat16 h, l;
@@ -171,7 +185,8 @@ __global__ void __launch_bounds__(256) k_sys_residual(const SysInst *__restrict_
             I.rv_lo[o] = l;
         }
     }
-    Red4 acc{(double)kr2 - (double)kc, f2, (double)mxp, (double)mnm};
+    if (!want_f2) r2 = ldexp((double)kr2 - (double)kc, 2 * S.r2_exp);
+    Red4 acc{r2, f2, (double)mxp, (double)mnm};
     acc = block_red(acc);
     if (threadIdx.x == 0) {
         double *p = partials + 4ll * blockIdx.x;
@@ -198,7 +213,12 @@ __global__ void __launch_bounds__(128) k_sys_finalize(const SysInst *__restrict_
     acc = block_red(acc);
     if (threadIdx.x != 0) return;
     SysState s = st[i];
-    if (s.it == 0) s.f_norm = sqrt(acc.f2);
+    if (s.it == 0) {
+        s.f_norm = sqrt(acc.f2);
+        const double rms = s.f_norm / sqrt(2.0 * I.n * I.n);
+        int k = (rms > 0.0 && rms < INFINITY) ? ilogb(rms) : 0;
+        s.r2_exp = k < -120 ? -120 : (k > 120 ? 120 : k);
+    }
     const double res = sqrt(acc.r2);
     double rel = s.f_norm > 0.0 ? res / s.f_norm : (res == 0.0 ? 0.0 : INFINITY);
     const double beta = 0.5 * (acc.mx + acc.mn);

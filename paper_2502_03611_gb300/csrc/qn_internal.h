@@ -25,6 +25,15 @@ struct DevState {
     int beta_mode;
     double beta_value;
     double f_norm;   // ||f||_2, computed on the first iteration of a solve
+    int fx_e;        // fixed-point exponent for the next residual of the split solve
+                     // (biased exponent of max|U| + 2; 0: not usable, see k_residual_tiled)
+    int fx_fbad;     // 1: some |f| is too large for the FP32-pair copy of f
+    int fx_headroom; // fx_e = biased exponent of max|U| + fx_headroom (2: U may grow 4x
+                     // before a plane takes the exact path; smaller values send more there)
+    int r2_exp;      // k: the FP32 sum of r^2 inside the split solve adds (r 2^-k)^2,
+                     // 2^k ~ RMS(f) (set on the first iteration), so it neither
+                     // overflows nor underflows for any scale of f
+    double npts;     // number of unknowns (for RMS(f))
 };
 
 // Residual kernel outputs.
@@ -43,6 +52,11 @@ struct ResidualArgs {
     int want_f2;               // 1: also sum f^2 (first iteration / standalone residual)
     int fp64_warps;            // warps (of 8) per block that sum the stencil on the FP64 pipe;
                                // the others use the exact fixed-point sum on the integer pipe
+    float2 *fdf;               // padded P^3 copy of f as FP32 pairs (hi, lo): written by the
+                               // first residual of a split 3-D solve, read by k_residual_tiled
+    int *fx_fbad;              // set when some |f| does not fit the FP32-pair copy
+    const int *fx_e;           // DevState::fx_e (k_residual_tiled)
+    const int *r2_exp;         // DevState::r2_exp (fast == 1)
 };
 
 // Epilogue selector shared by both mode-product kernels.
@@ -76,6 +90,9 @@ struct GemmShape {
 
 // ---- launchers (implemented in the .cu files) ---------------------------------
 int launch_residual(const ResidualArgs &a, int grid, cudaStream_t s);
+// 3-D split solve, iterations >= 2: no FP64 arithmetic per point (k_residual_tiled).
+// Uses at most max_grid blocks; the number of partial records written goes to *grid_used.
+int launch_residual_tiled(const ResidualArgs &a, int max_grid, int zchunk, int *grid_used, cudaStream_t s);
 int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *hist,
                     int hist_cap, double b, double lam, int update_state, int use_saved_fnorm,
                     cudaStream_t s);

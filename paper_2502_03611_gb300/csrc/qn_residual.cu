@@ -74,10 +74,24 @@ __device__ Red4 block_reduce(Red4 v) {
 // with one of the two loops (a warp-uniform branch around the whole loop, so
 // neither variant is predicated into the other).
 // KIND 0: lam u + b u^3 (general); 1: lam = 0; 2: lam = 0 and b = 1.
+// f as an unevaluated pair of floats hi + lo (48 significant bits), the form
+// k_residual_tiled reads; |f| >= 2^100 (or inf/nan) marks the copy unusable.
+static __device__ __noinline__ void flag_fbad(int *flag) {
+    if (flag != nullptr) atomicOr(flag, 1);
+}
+
+__device__ __forceinline__ float2 f_pair(double fv, int *flag) {
+    const unsigned int hw = (unsigned int)((unsigned long long)__double_as_longlong(fv) >> 32);
+    if ((int)((hw >> 20) & 0x7FFu) >= 1023 + 100) flag_fbad(flag);
+    const float fh = d2f_rn(fv);
+    return make_float2(fh, d2f_rn(fv - f2d_exact(fh)));
+}
+
 struct ResAcc {
     double r2, f2;
     float kr2, kc;
     unsigned long long amin, amax;
+    float r2s;   // 2^-r2_exp: r is scaled before its FP32 square
 };
 
 template <int DIM, bool SPLIT, bool FAST, int KIND, bool WANT_F2, bool INT_STENCIL>
@@ -95,6 +109,7 @@ __device__ __forceinline__ void residual_sweep(const ResidualArgs &a, ResAcc &s)
         const long long cbase = ((long long)z * n + y) * n;
         for (int x = threadIdx.x; x < P; x += blockDim.x) {
             double r = 0.0;
+            float2 fpair = make_float2(0.0f, 0.0f);
             if (row_ok && x < n) {
                 const long long c = cbase + x;
                 const double u = __ldg(U + c);
@@ -130,7 +145,7 @@ __device__ __forceinline__ void residual_sweep(const ResidualArgs &a, ResAcc &s)
                 s.amax = ab > s.amax ? ab : s.amax;
                 if (WANT_F2) s.f2 = fma(fv, fv, s.f2);
                 if (FAST) {
-                    const float rf = d2f_rn(r);
+                    const float rf = __fmul_rn(d2f_rn(r), s.r2s);
                     const float yk = fmaf(rf, rf, -s.kc);
                     const float tk = s.kr2 + yk;
                     s.kc = (tk - s.kr2) - yk;
@@ -139,6 +154,7 @@ __device__ __forceinline__ void residual_sweep(const ResidualArgs &a, ResAcc &s)
                     s.r2 = fma(r, r, s.r2);
                 }
                 if (a.R64 != nullptr) a.R64[c] = r;
+                if (SPLIT && WANT_F2) fpair = f_pair(fv, a.fx_fbad);
             }
             if (SPLIT) {
                 const float rf = d2f_rn(r);
@@ -147,6 +163,7 @@ __device__ __forceinline__ void residual_sweep(const ResidualArgs &a, ResAcc &s)
                 const long long o = row * P + x;
                 a.Rhi[o] = hi;
                 a.Rlo[o] = lo;
+                if (WANT_F2 && a.fdf != nullptr) a.fdf[o] = fpair;
             }
         }
     }
@@ -155,12 +172,13 @@ __device__ __forceinline__ void residual_sweep(const ResidualArgs &a, ResAcc &s)
 template <int DIM, bool SPLIT, bool FAST, int KIND, bool WANT_F2>
 __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
     if (a.done != nullptr && *(volatile const int *)a.done) return;
-    ResAcc s{0.0, 0.0, 0.0f, 0.0f, 0x7FFFFFFFFFFFFFFFull, 0ull};
+    const int r2k = FAST ? *a.r2_exp : 0;
+    ResAcc s{0.0, 0.0, 0.0f, 0.0f, 0x7FFFFFFFFFFFFFFFull, 0ull, __int_as_float((127 - r2k) << 23)};
     if ((int)(threadIdx.x >> 5) < a.fp64_warps)
         residual_sweep<DIM, SPLIT, FAST, KIND, WANT_F2, false>(a, s);
     else
         residual_sweep<DIM, SPLIT, FAST, KIND, WANT_F2, true>(a, s);
-    if (FAST) s.r2 = (double)s.kr2 - (double)s.kc;
+    if (FAST) s.r2 = ldexp((double)s.kr2 - (double)s.kc, 2 * r2k);
     const double umin = __longlong_as_double((long long)s.amin);
     const double umax = __longlong_as_double((long long)s.amax);
     Red4 acc{s.r2, s.f2, (s.amin == 0x7FFFFFFFFFFFFFFFull) ? INFINITY : umin * umin, umax * umax};
@@ -189,7 +207,13 @@ __global__ void __launch_bounds__(256) k_finalize(const double *partials, int np
     if (threadIdx.x != 0) return;
     const double res = sqrt(acc.r2);
     const double fn = use_saved_fnorm ? st->f_norm : sqrt(acc.f2);
-    if (update_state && !use_saved_fnorm) st->f_norm = fn;
+    if (update_state && !use_saved_fnorm) {
+        st->f_norm = fn;
+        // scale of the FP32 sum of r^2 in the later iterations: 2^k ~ RMS(f)
+        const double rms = (st->npts > 0.0) ? fn / sqrt(st->npts) : 0.0;
+        int k = (rms > 0.0 && rms < INFINITY) ? ilogb(rms) : 0;
+        st->r2_exp = k < -120 ? -120 : (k > 120 ? 120 : k);
+    }
     const double fa = 3.0 * b * acc.mn, fb = 3.0 * b * acc.mx;
     const double fu_min = fmin(fa, fb), fu_max = fmax(fa, fb);
     const double beta = (st->beta_mode == QN_BETA_FIXED) ? st->beta_value : 0.5 * (fu_min + fu_max);
@@ -210,6 +234,17 @@ __global__ void __launch_bounds__(256) k_finalize(const double *partials, int np
         hist[it] = s;
     }
     if (!update_state) return;
+    // exponent for the fixed-point stencil of the next residual: max|U| of
+    // this iterate with 2^fx_headroom of room (2: U may grow 4x; values
+    // beyond it take the exact per-point path)
+    int fxe = 0;
+    if (!st->fx_fbad && fn >= 0x1p-40 && acc.mx > 0.0 && acc.mx < INFINITY) {
+        const double um = sqrt(acc.mx);   // >= max|U| in exponent (u^2 rounds up at most)
+        const int ex = (int)(((unsigned long long)__double_as_longlong(um) >> 52) & 0x7FF);
+        const int E = ex + st->fx_headroom;
+        if (E - 1023 >= -60 && E - 1023 <= 36) fxe = E;
+    }
+    st->fx_e = fxe;
     st->beta = beta;
     st->shift = lam + beta;
     if (rel <= st->tol) {
@@ -223,6 +258,362 @@ __global__ void __launch_bounds__(256) k_finalize(const double *partials, int np
         st->done = 1;
     } else {
         st->it = it + 1;   // the update about to run produces iterate it+1
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_residual_tiled: the residual of the split-precision 3-D solve with no FP64
+// arithmetic per point (used from the third iteration of a solve on).
+//
+// Every U value is converted once to a signed fixed-point integer in units of
+// 2^(E - 1075 - kFxG), E = DevState::fx_e (the biased exponent of max|U| of
+// the previous iterate plus 2, i.e. room for U to grow 4x). The 7-point
+// stencil 6u - sum(nb) is then an exact int64 sum. The remaining terms,
+// lap/h^2 + lam u + b u^3 - f, are evaluated in unevaluated pairs of floats
+// (hi + lo, ~48 significant bits) on the FP32 pipe, f being read from its
+// FP32-pair copy written by the first residual of the solve.
+// Accuracy: each stencil input is truncated toward zero at the unit
+// 2^(E-1075-kFxG) (1/8 ulp of max|U|), so 6u - sum(nb) is off by at most 12
+// units, 1.5 ulp of max|U| - less than rounding the same sum in FP64; the float-
+// pair arithmetic adds ~2^-46 of the largest term (|lap/h^2|, |b u^3|, |f|),
+// about 1e-14 ||f||, far below the 1e-10 stop tolerance; the result is
+// rounded once to FP32, the precision of the split planes it feeds.
+//
+// Layout: a block owns a 64 x 16 (x, y) tile of the padded grid and a chunk
+// of planes, marching in z. Each thread holds 2 x 2 points (an x pair in two
+// consecutive rows) of three consecutive planes in registers; the current
+// plane with a one-point halo sits in shared memory (two buffers, one barrier
+// per plane) for the x/y neighbours. The loads of plane z+2 and of f on plane
+// z+1 are issued before the stencil of plane z.
+//
+// A plane holding a value whose exponent exceeds E (U grew more than 4x, or a
+// non-finite value) is flagged through the barrier's OR; the points whose
+// stencil touches it are evaluated by the exact per-point path of k_residual
+// instead. E = 0 (not usable) sends every point there.
+// ---------------------------------------------------------------------------
+constexpr int kTX = 64, kTY = 16, kTThreads = 256;
+constexpr int kSRow = 68;                                 // int64 per shared row; x = -1..64 at columns 1..66
+constexpr int kSRows = kTY + 2;
+constexpr int kHaloPerWarp = (2 * kTX + 2 * kTY) / 8;    // 160 halo points, 20 per warp
+constexpr int kFxG = 5;                                   // guard bits below the ulp of exponent E
+static_assert(kTThreads == 8 * 32 && kTY == 2 * 8 && kTX == 2 * 32, "tile / thread mapping");
+
+// Signed fixed-point value of the double with bit pattern b, in units of
+// 2^(E - 1075 - kFxG); `bad` is set when its exponent exceeds E.
+__device__ __forceinline__ long long fx_of(unsigned long long b, int E, unsigned &bad) {
+    const int ex = (int)((unsigned int)(b >> 52) & 0x7FFu);
+    bad |= (unsigned)(ex > E);
+    int sh = E - ex;
+    sh = sh < 0 ? 0 : (sh > 63 ? 63 : sh);
+    const unsigned long long m = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << kFxG;
+    const unsigned long long v = (ex == 0) ? 0ull : (m >> sh);
+    const unsigned long long sg = (unsigned long long)((long long)b >> 63);   // 0 or all ones
+    return (long long)((v ^ sg) - sg);
+}
+
+// Exact int -> float for |c| < 2^22 (the FP32 add of 1.5 * 2^23 trick, read backwards).
+__device__ __forceinline__ float small_i2f(int c) {
+    return __fsub_rn(__int_as_float(0x4B400000 + c), 12582912.0f);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Fixed-point value v (|v| < 2^62) times the power of two `scale`, as a float pair.
+__device__ __forceinline__ void fx_to_pair(long long v, float scale, float &hi, float &lo) {
+    const int c2 = (int)(v >> 42);                                   // signed, |c2| <= 2^20
+    const int c1 = (int)((unsigned long long)v >> 21) & 0x1FFFFF;
+    const int c0 = (int)v & 0x1FFFFF;
+    const float f2 = __fmaf_rn(__int_as_float(0x4B400000 + c2), 0x1p42f, -0x1.8p65f);   // c2 * 2^42, exact
+    const float f1 = __fmaf_rn(__int_as_float(0x4B400000 + c1), 0x1p21f, -0x1.8p44f);   // c1 * 2^21, exact
+    const float f0 = small_i2f(c0);
+    float s, e;
+    two_sum(f2, f1, s, e);
+    hi = __fmul_rn(s, scale);
+    lo = __fmul_rn(__fadd_rn(e, f0), scale);
+}
+
+// r = lap/h^2 + lam u + b u^3 - f in float pairs, rounded to FP32.
+template <int KIND>
+__device__ __forceinline__ float residual_pair(long long ufx, long long lapfx, float fh, float fl, float scale,
+                                               float ih, float il, float bh, float bl, float lh, float ll) {
+    float uh, ul, Lh, Ll;
+    fx_to_pair(ufx, scale, uh, ul);
+    fx_to_pair(lapfx, scale, Lh, Ll);
+    const float p = __fmul_rn(uh, uh);                         // u^2 = p + pe
+    float pe = __fmaf_rn(uh, uh, -p);
+    pe = __fmaf_rn(__fadd_rn(uh, uh), ul, pe);
+    float w = __fmul_rn(p, uh);                                // u^3 = w + we
+    float we = __fmaf_rn(p, uh, -w);
+    we = __fmaf_rn(p, ul, we);
+    we = __fmaf_rn(pe, uh, we);
+    if (KIND != 2) {                                           // b u^3
+        const float w2 = __fmul_rn(bh, w);
+        float e2 = __fmaf_rn(bh, w, -w2);
+        e2 = __fmaf_rn(bh, we, e2);
+        e2 = __fmaf_rn(bl, w, e2);
+        w = w2;
+        we = e2;
+    }
+    if (KIND == 0) {                                           // + lam u
+        const float v = __fmul_rn(lh, uh);
+        float ve = __fmaf_rn(lh, uh, -v);
+        ve = __fmaf_rn(lh, ul, ve);
+        ve = __fmaf_rn(ll, uh, ve);
+        float s2, e2;
+        two_sum(w, v, s2, e2);
+        we = __fadd_rn(__fadd_rn(we, ve), e2);
+        w = s2;
+    }
+    float t, te;                                               // N(u) - f
+    two_sum(w, -fh, t, te);
+    te = __fadd_rn(te, __fsub_rn(we, fl));
+    const float L = __fmul_rn(Lh, ih);                         // lap / h^2
+    float Le = __fmaf_rn(Lh, ih, -L);
+    Le = __fmaf_rn(Ll, ih, Le);
+    Le = __fmaf_rn(Lh, il, Le);
+    float r, re;
+    two_sum(L, t, r, re);
+    re = __fadd_rn(re, __fadd_rn(Le, te));
+    return __fadd_rn(r, re);
+}
+
+// The exact per-point path (as k_residual), for points next to a flagged plane.
+static __device__ __noinline__ float residual_point_exact(const double *U, const double *f, int n, int x, int y,
+                                                          int z, double inv_h2, double lam, double b) {
+    const long long nn = (long long)n * n;
+    const long long c = ((long long)z * n + y) * n + x;
+    const double u = U[c];
+    double nb[6];
+    nb[0] = (x > 0) ? U[c - 1] : 0.0;
+    nb[1] = (x < n - 1) ? U[c + 1] : 0.0;
+    nb[2] = (y > 0) ? U[c - n] : 0.0;
+    nb[3] = (y < n - 1) ? U[c + n] : 0.0;
+    nb[4] = (z > 0) ? U[c - nn] : 0.0;
+    nb[5] = (z < n - 1) ? U[c + nn] : 0.0;
+    const double lap = stencil_fixed<3>(u, nb);
+    double t = fma(b, (u * u) * u, -f[c]);
+    t = fma(lam, u, t);
+    return d2f_rn(fma(lap, inv_h2, t));
+}
+
+__device__ __forceinline__ void store_split2(__nv_bfloat162 *hi2, __nv_bfloat162 *lo2, long long i2, float r0,
+                                             float r1) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(r0, r1);
+    const float2 hf = __bfloat1622float2(h);
+    hi2[i2] = h;
+    lo2[i2] = __floats2bfloat162_rn(__fsub_rn(r0, hf.x), __fsub_rn(r1, hf.y));
+}
+
+__device__ __forceinline__ void minmax_bits(unsigned long long v, bool valid, unsigned long long &mn,
+                                            unsigned long long &mx) {
+    const unsigned long long ab = v & 0x7FFFFFFFFFFFFFFFull;
+    mn = (valid && ab < mn) ? ab : mn;
+    mx = (valid && ab > mx) ? ab : mx;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kTThreads, 2) k_residual_tiled(ResidualArgs a, int zchunk) {
+    if (a.done != nullptr && *(volatile const int *)a.done) return;
+    __shared__ __align__(16) long long spl[2][kSRows * kSRow];
+    const int n = a.n, P = a.P;
+    const int E = *a.fx_e;
+    const bool fx_ok = (E != 0);
+    const float scale = __int_as_float(fx_ok ? ((E - 1075 - kFxG + 127) << 23) : 0);
+    const float ih = __double2float_rn(a.inv_h2);
+    const float il = __double2float_rn(a.inv_h2 - (double)ih);
+    float bh = 1.0f, bl = 0.0f, lh = 0.0f, ll = 0.0f;
+    if (KIND != 2) {
+        bh = __double2float_rn(a.b);
+        bl = __double2float_rn(a.b - (double)bh);
+    }
+    if (KIND == 0) {
+        lh = __double2float_rn(a.lam);
+        ll = __double2float_rn(a.lam - (double)lh);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tiles_x = P / kTX, tiles_y = P / kTY;
+    const int nzc = (P + zchunk - 1) / zchunk;
+    const long long items = (long long)tiles_x * tiles_y * nzc;
+    const long long nn = (long long)n * n;
+    const unsigned long long *Ub = reinterpret_cast<const unsigned long long *>(a.U);
+    const float4 *fdf4 = reinterpret_cast<const float4 *>(a.fdf);
+    __nv_bfloat162 *Rhi2 = reinterpret_cast<__nv_bfloat162 *>(a.Rhi);
+    __nv_bfloat162 *Rlo2 = reinterpret_cast<__nv_bfloat162 *>(a.Rlo);
+    const int s0 = (2 * warp + 1) * kSRow + 2 * lane + 2;   // shared slot of own point (xo, yo)
+    const bool hlane = lane < kHaloPerWarp;
+    const int hidx = warp * kHaloPerWarp + lane;
+    float kr2 = 0.0f, kc = 0.0f;
+    unsigned long long amin = 0x7FFFFFFFFFFFFFFFull, amax = 0ull;
+    const int r2k = *a.r2_exp;
+    const float r2s = __int_as_float((127 - r2k) << 23);   // 2^-r2k
+
+    for (long long item = blockIdx.x; item < items; item += gridDim.x) {
+        const int tx = (int)(item % tiles_x);
+        const long long q = item / tiles_x;
+        const int ty = (int)(q % tiles_y);
+        const int z0 = (int)(q / tiles_y) * zchunk;
+        const int z1 = min(z0 + zchunk, P);
+        const int X0 = tx * kTX, Y0 = ty * kTY;
+        const int xo = X0 + 2 * lane, yo = Y0 + 2 * warp;
+        // zero planes of the padding (z >= n)
+        for (int z = max(z0, n); z < z1; ++z) {
+            const long long o = ((long long)z * P + yo) * P + xo;
+            const __nv_bfloat162 zz = __floats2bfloat162_rn(0.0f, 0.0f);
+            Rhi2[o >> 1] = zz;
+            Rlo2[o >> 1] = zz;
+            Rhi2[(o + P) >> 1] = zz;
+            Rlo2[(o + P) >> 1] = zz;
+        }
+        const int zl = min(z1, n);
+        if (z0 >= zl) continue;   // block-uniform
+
+        const bool v00 = xo < n && yo < n, v10 = xo + 1 < n && yo < n;
+        const bool v01 = xo < n && yo + 1 < n, v11 = xo + 1 < n && yo + 1 < n;
+        const long long own = (long long)yo * n + xo;
+        int hx, hy, hslot;
+        if (hidx < kTX) {
+            hx = X0 + hidx;
+            hy = Y0 - 1;
+            hslot = hidx + 2;
+        } else if (hidx < 2 * kTX) {
+            hx = X0 + hidx - kTX;
+            hy = Y0 + kTY;
+            hslot = (kTY + 1) * kSRow + hidx - kTX + 2;
+        } else if (hidx < 2 * kTX + kTY) {
+            hx = X0 - 1;
+            hy = Y0 + hidx - 2 * kTX;
+            hslot = (hidx - 2 * kTX + 1) * kSRow + 1;
+        } else {
+            hx = X0 + kTX;
+            hy = Y0 + hidx - 2 * kTX - kTY;
+            hslot = (hidx - 2 * kTX - kTY + 1) * kSRow + kTX + 2;
+        }
+        const bool hval = hlane && hx >= 0 && hx < n && hy >= 0 && hy < n;
+        const long long hoff = hval ? (long long)hy * n + hx : 0;
+
+        unsigned long long R[4], RH;
+        auto load_plane = [&](int z) {
+            const bool zin = z >= 0 && z < n;
+            const unsigned long long *p = Ub + (long long)(zin ? z : 0) * nn;
+            R[0] = (zin && v00) ? __ldg(p + own) : 0ull;
+            R[1] = (zin && v10) ? __ldg(p + own + 1) : 0ull;
+            R[2] = (zin && v01) ? __ldg(p + own + n) : 0ull;
+            R[3] = (zin && v11) ? __ldg(p + own + n + 1) : 0ull;
+            RH = (zin && hval) ? __ldg(p + hoff) : 0ull;
+        };
+        auto minmax_own = [&]() {
+            minmax_bits(R[0], v00, amin, amax);
+            minmax_bits(R[1], v10, amin, amax);
+            minmax_bits(R[2], v01, amin, amax);
+            minmax_bits(R[3], v11, amin, amax);
+        };
+        auto f_at = [&](int z, int row) -> float4 {
+            return __ldg(fdf4 + ((((long long)z * P + row) * P + xo) >> 1));
+        };
+
+        long long Fm[4], Fc[4], Fp[4];
+        unsigned bm = 0, bc = 0, bh0 = 0;
+        load_plane(z0 - 1);
+        for (int i = 0; i < 4; ++i) Fm[i] = fx_of(R[i], E, bm);
+        load_plane(z0);
+        minmax_own();
+        for (int i = 0; i < 4; ++i) Fc[i] = fx_of(R[i], E, bc);
+        {
+            long long *S = spl[z0 & 1];
+            const long long H = fx_of(RH, E, bh0);
+            *reinterpret_cast<longlong2 *>(S + s0) = make_longlong2(Fc[0], Fc[1]);
+            *reinterpret_cast<longlong2 *>(S + s0 + kSRow) = make_longlong2(Fc[2], Fc[3]);
+            if (hlane) S[hslot] = H;
+        }
+        load_plane(z0 + 1);
+        float4 fa = f_at(z0, yo), fb = f_at(z0, yo + 1);
+        int blk = __syncthreads_or((int)(bc | bh0));
+
+        for (int z = z0; z < zl; ++z) {
+            unsigned bp = 0, bhp = 0;
+            for (int i = 0; i < 4; ++i) Fp[i] = fx_of(R[i], E, bp);
+            const long long Hp = fx_of(RH, E, bhp);
+            if (z + 1 < zl) minmax_own();
+            {
+                long long *S = spl[(z + 1) & 1];
+                *reinterpret_cast<longlong2 *>(S + s0) = make_longlong2(Fp[0], Fp[1]);
+                *reinterpret_cast<longlong2 *>(S + s0 + kSRow) = make_longlong2(Fp[2], Fp[3]);
+                if (hlane) S[hslot] = Hp;
+            }
+            load_plane(z + 2);
+            float4 fa_n = make_float4(0.f, 0.f, 0.f, 0.f), fb_n = fa_n;
+            if (z + 1 < zl) {
+                fa_n = f_at(z + 1, yo);
+                fb_n = f_at(z + 1, yo + 1);
+            }
+
+            float rf[4];
+            if (fx_ok && !(blk | bm | bp)) {
+                const long long *S = spl[z & 1];
+                const longlong2 up = *reinterpret_cast<const longlong2 *>(S + s0 - kSRow);
+                const longlong2 dn = *reinterpret_cast<const longlong2 *>(S + s0 + 2 * kSRow);
+                const unsigned long long l0 = S[s0 - 1], r0 = S[s0 + 2];
+                const unsigned long long l1 = S[s0 + kSRow - 1], r1 = S[s0 + kSRow + 2];
+                typedef unsigned long long u64;
+                const u64 c0 = Fc[0], c1 = Fc[1], c2 = Fc[2], c3 = Fc[3];
+                // 6u - (x- + x+ + y- + y+ + z- + z+), exact (wrap-free: |sum| < 2^62)
+                const long long lap0 = (long long)(6ull * c0 - (((l0 + c1) + ((u64)up.x + c2)) + ((u64)Fm[0] + (u64)Fp[0])));
+                const long long lap1 = (long long)(6ull * c1 - (((c0 + r0) + ((u64)up.y + c3)) + ((u64)Fm[1] + (u64)Fp[1])));
+                const long long lap2 = (long long)(6ull * c2 - (((l1 + c3) + (c0 + (u64)dn.x)) + ((u64)Fm[2] + (u64)Fp[2])));
+                const long long lap3 = (long long)(6ull * c3 - (((c2 + r1) + (c1 + (u64)dn.y)) + ((u64)Fm[3] + (u64)Fp[3])));
+                rf[0] = residual_pair<KIND>(Fc[0], lap0, fa.x, fa.y, scale, ih, il, bh, bl, lh, ll);
+                rf[1] = residual_pair<KIND>(Fc[1], lap1, fa.z, fa.w, scale, ih, il, bh, bl, lh, ll);
+                rf[2] = residual_pair<KIND>(Fc[2], lap2, fb.x, fb.y, scale, ih, il, bh, bl, lh, ll);
+                rf[3] = residual_pair<KIND>(Fc[3], lap3, fb.z, fb.w, scale, ih, il, bh, bl, lh, ll);
+            } else {
+                rf[0] = v00 ? residual_point_exact(a.U, a.f, n, xo, yo, z, a.inv_h2, a.lam, a.b) : 0.0f;
+                rf[1] = v10 ? residual_point_exact(a.U, a.f, n, xo + 1, yo, z, a.inv_h2, a.lam, a.b) : 0.0f;
+                rf[2] = v01 ? residual_point_exact(a.U, a.f, n, xo, yo + 1, z, a.inv_h2, a.lam, a.b) : 0.0f;
+                rf[3] = v11 ? residual_point_exact(a.U, a.f, n, xo + 1, yo + 1, z, a.inv_h2, a.lam, a.b) : 0.0f;
+            }
+            rf[0] = v00 ? rf[0] : 0.0f;
+            rf[1] = v10 ? rf[1] : 0.0f;
+            rf[2] = v01 ? rf[2] : 0.0f;
+            rf[3] = v11 ? rf[3] : 0.0f;
+            // sum (r 2^-k)^2 (FP32, Kahan over planes)
+            const float q0 = __fmul_rn(rf[0], r2s), q1 = __fmul_rn(rf[1], r2s);
+            const float q2 = __fmul_rn(rf[2], r2s), q3 = __fmul_rn(rf[3], r2s);
+            const float sq = __fadd_rn(__fmaf_rn(q0, q0, __fmul_rn(q1, q1)), __fmaf_rn(q2, q2, __fmul_rn(q3, q3)));
+            const float yk = __fsub_rn(sq, kc);
+            const float tk = __fadd_rn(kr2, yk);
+            kc = __fsub_rn(__fsub_rn(tk, kr2), yk);
+            kr2 = tk;
+            const long long o = ((long long)z * P + yo) * P + xo;
+            store_split2(Rhi2, Rlo2, o >> 1, rf[0], rf[1]);
+            store_split2(Rhi2, Rlo2, (o + P) >> 1, rf[2], rf[3]);
+
+            blk = __syncthreads_or((int)(bp | bhp));
+            for (int i = 0; i < 4; ++i) {
+                Fm[i] = Fc[i];
+                Fc[i] = Fp[i];
+            }
+            bm = bc;
+            bc = bp;
+            fa = fa_n;
+            fb = fb_n;
+        }
+    }
+
+    const double umin = __longlong_as_double((long long)amin);
+    const double umax = __longlong_as_double((long long)amax);
+    Red4 acc{ldexp((double)kr2 - (double)kc, 2 * r2k), 0.0,
+             (amin == 0x7FFFFFFFFFFFFFFFull) ? INFINITY : umin * umin, umax * umax};
+    acc = block_reduce(acc);
+    if (threadIdx.x == 0) {
+        double *p = a.partials + 4ll * blockIdx.x;
+        p[0] = acc.r2;
+        p[1] = acc.f2;
+        p[2] = acc.mn;
+        p[3] = acc.mx;
     }
 }
 
@@ -270,8 +661,10 @@ static void launch_res4(const ResidualArgs &a, int grid, cudaStream_t s) {
 
 template <int DIM, bool SPLIT, bool FAST>
 static void launch_res3(const ResidualArgs &a, int grid, cudaStream_t s) {
-    if (a.want_f2)
-        launch_res4<DIM, SPLIT, FAST, true>(a, grid, s);
+    // the scaled FP32 norm needs RMS(f), known once sum f^2 has been taken:
+    // the fast form never sums f^2
+    if (!FAST && a.want_f2)
+        launch_res4<DIM, SPLIT, false, true>(a, grid, s);
     else
         launch_res4<DIM, SPLIT, FAST, false>(a, grid, s);
 }
@@ -299,6 +692,46 @@ int launch_residual(const ResidualArgs &a, int grid, cudaStream_t s) {
     }
     QN_CUDA(cudaGetLastError());
     return QN_OK;
+}
+
+template <int KIND>
+static int tiled_blocks_per_sm() {
+    static int cached = 0;   // per process: every device it runs on is a GB300
+    if (cached == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_residual_tiled<KIND>, kTThreads, 0) != cudaSuccess ||
+            nb < 1)
+            nb = 1;
+        cached = nb;
+    }
+    return cached;
+}
+
+template <int KIND>
+static int launch_tiled_kind(const ResidualArgs &a, int max_grid, int zchunk, int *grid_used, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    QN_CUDA(cudaGetDevice(&dev));
+    QN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long items = (long long)(a.P / kTX) * (a.P / kTY) * ((a.P + zchunk - 1) / zchunk);
+    long long g = (long long)tiled_blocks_per_sm<KIND>() * sms;
+    if (g > max_grid) g = max_grid;
+    if (g > items) g = items;
+    if (g < 1) g = 1;
+    k_residual_tiled<KIND><<<(int)g, kTThreads, 0, s>>>(a, zchunk);
+    QN_CUDA(cudaGetLastError());
+    *grid_used = (int)g;
+    return QN_OK;
+}
+
+int launch_residual_tiled(const ResidualArgs &a, int max_grid, int zchunk, int *grid_used, cudaStream_t s) {
+    if (a.dim != 3 || a.Rhi == nullptr || a.fdf == nullptr || a.fx_e == nullptr || a.P % kTX != 0 ||
+        zchunk < 1) {
+        set_error("launch_residual_tiled: needs a 3-D split residual with the FP32-pair copy of f");
+        return QN_EINVAL;
+    }
+    if (a.lam != 0.0) return launch_tiled_kind<0>(a, max_grid, zchunk, grid_used, s);
+    if (a.b != 1.0) return launch_tiled_kind<1>(a, max_grid, zchunk, grid_used, s);
+    return launch_tiled_kind<2>(a, max_grid, zchunk, grid_used, s);
 }
 
 int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *hist,
@@ -415,7 +848,7 @@ extern "C" int qn_residual_noalloc(int dim, int n, double lam, double b, const d
     // blocks, so only the solver state needs resetting
     k_noalloc_prepare<<<1, 32, 0, s>>>(state);
     QN_CUDA(cudaGetLastError());
-    ResidualArgs a;
+    ResidualArgs a{};
     a.U = U;
     a.f = f;
     a.n = n;

@@ -120,3 +120,22 @@ def test_batch_256_uneven_config(qn):
         assert np.array_equal(solo[0]["U"].cpu().numpy(), inst["U"].cpu().numpy())
         assert np.array_equal(solo[0]["V"].cpu().numpy(), inst["V"].cpu().numpy())
     assert seen == {63, 127, 255, 511}
+
+
+def test_batch_tiny_source_scale(qn):
+    """Sources scaled by 2^-80: the FP32 sum of r^2 is taken on r 2^-k with
+    2^k ~ RMS(f), so it neither underflows (a false 'converged') nor loses
+    the stop test."""
+    specs = [(63, 0.4, 1.5, 31), (100, 0.8, 0.3, 32)]
+    insts, truth = make_instances(specs)
+    s = 2.0 ** -80
+    for inst in insts:
+        inst["f1"] *= s
+        inst["f2"] *= s
+    truth = [(f1 * s, f2 * s) for (f1, f2) in truth]
+    batch = qn.QnBatch(insts)
+    rc, res = batch.solve()
+    assert rc == 0
+    for inst, (f1, f2), r in zip(insts, truth, res):
+        assert r["iterations"] >= 1
+        check_against_oracle(inst, f1, f2, r)

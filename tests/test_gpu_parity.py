@@ -299,3 +299,118 @@ def test_solve_host_arrays(qn):
     Uo, _, _ = O.qn_solve(f)
     assert res["status"] == 0
     assert np.abs(U.reshape(f.shape) - Uo).max() <= 1e-9 * np.abs(Uo).max()
+
+
+# --------------------------------------------------------------------------------------------
+# the residual of the split 3-D solve from its third iteration on: exact fixed-point
+# stencil + float-pair arithmetic, no FP64 per point (k_residual_tiled)
+# --------------------------------------------------------------------------------------------
+def _solve_3d_bf16x3(qn, n, f, lam=0.0, b=1.0, max_it=200):
+    import torch
+    ctx = qn.QnContext(3, n, "bf16x3", lam=lam, b=b)
+    U = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
+    qn.qn_profile_enable(ctx, True)
+    res, hist = qn.qn_solve(ctx, U, dev(f).reshape(-1), tol=1e-10, max_it=max_it, history_len=max_it + 1)
+    prof = qn.qn_profile_read(ctx)
+    return res, hist, host(U).reshape(f.shape), prof
+
+
+@pytest.mark.parametrize("n", [17, 70, 130])
+def test_tiled_residual_solve_matches_oracle(qn, n):
+    """Ragged tiles (n = 70, 130: P = 128, 192 -> several 64 x 16 tiles and z chunks
+    with a partial last one), and a single tile (n = 17)."""
+    u, f = manufactured_problem(n, 3, seed=3)
+    res, hist, Ug, prof = _solve_3d_bf16x3(qn, n, f)
+    Uo, ho, ok = O.qn_solve(f, tol=1e-10)
+    assert ok
+    assert prof["residual_tiled_launches"] >= 1, prof
+    _check_solution(res, Ug, Uo, f, ho)
+    assert res["iterations"] <= len(ho) - 1 + 2
+
+
+@pytest.mark.parametrize("lam,b", [(0.0, 0.5), (2.5, 0.5), (-3.0, 2.0), (40.0, 1.0)])
+def test_tiled_residual_general_coefficients(qn, lam, b):
+    n = 47
+    u, f = manufactured_problem(n, 3, seed=5, lam=lam, b=b)
+    res, hist, Ug, prof = _solve_3d_bf16x3(qn, n, f, lam=lam, b=b)
+    Uo, ho, ok = O.qn_solve(f, tol=1e-10, lam=lam, b=b)
+    assert ok and prof["residual_tiled_launches"] >= 1
+    assert res["status"] == 0 and res["rel"] <= 1e-10
+    rel = np.linalg.norm(O.residual(Ug, f, lam=lam, b=b)) / np.linalg.norm(f)
+    assert rel <= 1.05e-10, rel
+    assert np.abs(Ug - Uo).max() <= 1e-9 * np.abs(Uo).max()
+
+
+def test_tiled_residual_agrees_with_per_point_residual(qn, monkeypatch):
+    """Same solve with the per-point residual kernel throughout (QN_RES_TILED=0):
+    same iteration count, solutions equal to the solver tolerance."""
+    n = 65
+    u, f = manufactured_problem(n, 3, seed=1)
+    res_t, hist_t, Ut, prof_t = _solve_3d_bf16x3(qn, n, f)
+    monkeypatch.setenv("QN_RES_TILED", "0")
+    res_p, hist_p, Up, prof_p = _solve_3d_bf16x3(qn, n, f)
+    assert prof_t["residual_tiled_launches"] >= 1 and prof_p["residual_tiled_launches"] == 0
+    assert res_t["iterations"] == res_p["iterations"]
+    assert np.abs(Ut - Up).max() <= 1e-9 * np.abs(Up).max()
+    # the two residual kernels round r to FP32 from different (both accurate)
+    # evaluations, so the iterates agree to far below the split products' error
+    for a, c in zip(hist_t, hist_p):
+        assert a["beta"] == pytest.approx(c["beta"], rel=1e-6)
+        assert a["rel"] == pytest.approx(c["rel"], rel=1e-4, abs=1e-14)
+
+
+@pytest.mark.parametrize("headroom", [0, -6])
+def test_tiled_residual_flagged_planes_take_exact_path(qn, monkeypatch, headroom):
+    """With less exponent headroom the planes holding values above the
+    fixed-point range are flagged and their points evaluated by the exact
+    per-point path (-6: most planes); the solve is unchanged to tolerance."""
+    n = 70
+    u, f = manufactured_problem(n, 3, seed=2)
+    Uo, ho, ok = O.qn_solve(f, tol=1e-10)
+    monkeypatch.setenv("QN_RES_FX_HEADROOM", str(headroom))
+    res, hist, Ug, prof = _solve_3d_bf16x3(qn, n, f)
+    assert prof["residual_tiled_launches"] >= 1
+    _check_solution(res, Ug, Uo, f, ho)
+    assert res["iterations"] <= len(ho) - 1 + 2
+
+
+@pytest.mark.parametrize("scale,b", [(2.0 ** 101, 0.0), (2.0 ** -70, 1.0)])
+def test_tiled_residual_out_of_range_uses_exact_path(qn, scale, b):
+    """|f| >= 2^100 (beyond the FP32-pair copy) or max|U| < 2^-60 (fixed-point
+    units below the FP32 range) leave no usable fixed-point exponent: every
+    point of the tiled kernel takes the exact per-point path. Nearly linear
+    problems, four iterations against the oracle's four."""
+    import torch
+    n = 33
+    u, f = manufactured_problem(n, 3, seed=0)
+    f = f * scale
+    ctx = qn.QnContext(3, n, "bf16x3", b=b)
+    qn.qn_profile_enable(ctx, True)
+    U = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
+    res, _ = qn.qn_solve(ctx, U, dev(f).reshape(-1), tol=1e-30, max_it=4)
+    assert res["status"] == qn.QN_ENOTCONV and res["iterations"] == 4
+    assert qn.qn_profile_read(ctx)["residual_tiled_launches"] >= 2
+    Uo = np.zeros_like(f)
+    for _ in range(4):
+        Uo, _, _ = O.qn_step(Uo, f, b=b)
+    assert np.abs(host(U).reshape(f.shape) - Uo).max() <= 1e-9 * np.abs(Uo).max()
+
+
+@pytest.mark.parametrize("dim,n,scale,b", [(3, 40, 2.0 ** 80, 0.0), (3, 40, 2.0 ** -80, 1.0),
+                                           (2, 63, 2.0 ** 90, 0.0), (2, 63, 2.0 ** -90, 1.0)])
+def test_split_solve_any_source_scale(qn, dim, n, scale, b):
+    """The split solve's FP32 sum of r^2 is taken on r 2^-k, 2^k ~ RMS(f): a
+    source of any scale neither overflows it (a false 'diverged') nor
+    underflows it (a false 'converged' at U = 0)."""
+    import torch
+    u, f = manufactured_problem(n, dim, seed=6)
+    f = f * scale
+    ctx = qn.QnContext(dim, n, "bf16x3", b=b)
+    U = torch.zeros(n ** dim, dtype=torch.float64, device="cuda")
+    res, hist = qn.qn_solve(ctx, U, dev(f).reshape(-1), tol=1e-10, history_len=50)
+    Uo, ho, ok = O.qn_solve(f, tol=1e-10, b=b)
+    assert ok and res["status"] == 0 and res["iterations"] >= 1
+    Ug = host(U).reshape(f.shape)
+    rel = np.linalg.norm(O.residual(Ug, f, b=b)) / np.linalg.norm(f)
+    assert rel <= 1.05e-10
+    assert np.abs(Ug - Uo).max() <= 1e-9 * np.abs(Uo).max()
