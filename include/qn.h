@@ -308,7 +308,8 @@ int qn_solve_warm(qn_ctx *ctx, qn_net *net, double *U, const double *f, int n, d
 typedef struct qn_profile {
     long long launches;       /* kernels launched that did work since qn_profile_enable
                                  (launches queued past convergence are not counted) */
-    int residual_launches;    /* residual + reduction kernel */
+    int residual_launches;    /* residual + reduction kernel (and, in a 3-D split solve, the
+                                 preparation passes of its first two iterations) */
     double residual_ms;       /* summed CUDA-event time on the launching stream */
     int finalize_launches;    /* one-block reduction finaliser (beta_n, stop test) */
     double finalize_ms;

@@ -83,6 +83,7 @@ struct qn_ctx {
     int res_zc;           // planes per work item of k_residual_tiled
     int res_parts;        // partial-sum records written by the last residual launch
     int res_fx_headroom;  // DevState::fx_headroom for the solves of this context
+    int res_saved_fnorm;  // 1: the last residual's finaliser takes ||f|| from DevState::f_norm
 };
 
 enum ProfKind { PK_RESIDUAL = 0, PK_FINALIZE = 1, PK_MP_STORE = 2, PK_MP_DIVIDE = 3, PK_MP_LAST = 4,
@@ -416,9 +417,29 @@ static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double 
     a.fdf = split_solve ? c->fdf : nullptr;
     a.fx_fbad = &c->st->fx_fbad;
     a.fx_e = &c->st->fx_e;
-    const bool tiled = a.fast && c->fdf != nullptr && c->res_tiled && c->cur_iter >= 2;
+    // 3-D split solve: the residual without FP64 arithmetic (k_residual_tiled)
+    // in every iteration. It needs the FP32-pair copy of f and a fixed-point
+    // exponent from max|U|: iteration 0 prepares both in one pass over f and
+    // U_0 (and takes ||f|| there), iteration 1 scans max|U_1|, later ones take
+    // max|U| from the previous residual.
+    const bool tiled = split_solve && c->fdf != nullptr && c->res_tiled;
+    c->res_saved_fnorm = (c->cur_iter > 0 || tiled) ? 1 : 0;
+    int rc = QN_OK;
+    if (tiled && c->cur_iter <= 1) {
+        const long pp = prof_begin(c, PK_RESIDUAL, s);
+        if (c->cur_iter == 0)
+            rc = launch_prep_split(U, f, c->n, c->P, c->fdf, c->partials, c->nparts, c->st, s);
+        else
+            rc = launch_umax(U, c->N, c->st, 2 * c->num_sms, s);
+        prof_end(c, pp, s);
+        if (rc) return rc;
+        c->launches += 1;   // two kernels per preparation step
+    }
+    if (tiled) {
+        a.fast = 1;
+        a.want_f2 = 0;
+    }
     const long pr = prof_begin(c, tiled ? PK_RESIDUAL_TILED : PK_RESIDUAL, s);
-    int rc;
     if (tiled) {
         rc = launch_residual_tiled(a, c->nparts, c->res_zc, &c->res_parts, s);
     } else {
@@ -472,7 +493,7 @@ static int enqueue_iteration(qn_ctx *c, double *U, const double *f, double step,
     if (rc) return rc;
     const long pr = prof_begin(c, PK_FINALIZE, s);
     rc = launch_finalize(c->partials, c->res_parts, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 1,
-                         c->cur_iter > 0 ? 1 : 0, s);
+                         c->res_saved_fnorm, s);
     prof_end(c, pr, s);
     if (rc) return rc;
     return enqueue_inverse(c, nullptr, U, true, step, s);
@@ -639,6 +660,8 @@ extern "C" int qn_solve(qn_ctx *c, double *U, const double *f, const qn_opts *op
         if ((mp && r.iter >= its) || (!mp && r.iter > its)) r.valid = 0;
     }
     c->launches = launches0 + 2LL * (its + 1) + 2LL * c->dim * its;
+    if (c->prob.precision == QN_PREC_BF16X3 && c->fdf != nullptr && c->res_tiled)
+        c->launches += 2 + (its >= 1 ? 2 : 0);   // preparation kernels of iterations 0 and 1
     qn_stats last;
     QN_CUDA(cudaMemcpy(&last, c->hist + its, sizeof(qn_stats), cudaMemcpyDeviceToHost));
     if (history && history_len > 0) {

@@ -34,6 +34,7 @@ struct DevState {
                      // 2^k ~ RMS(f) (set on the first iteration), so it neither
                      // overflows nor underflows for any scale of f
     double npts;     // number of unknowns (for RMS(f))
+    unsigned long long umax_scan;   // max|U| bit pattern from a scan pass (k_prep_split, k_umax)
 };
 
 // Residual kernel outputs.
@@ -93,6 +94,13 @@ int launch_residual(const ResidualArgs &a, int grid, cudaStream_t s);
 // 3-D split solve, iterations >= 2: no FP64 arithmetic per point (k_residual_tiled).
 // Uses at most max_grid blocks; the number of partial records written goes to *grid_used.
 int launch_residual_tiled(const ResidualArgs &a, int max_grid, int zchunk, int *grid_used, cudaStream_t s);
+// Before the first two tiled residuals of a solve (no previous iterate to take
+// the fixed-point exponent from): iteration 0 -> the FP32-pair copy of f, sum
+// f^2 (DevState::f_norm, r2_exp) and max|U_0|; iteration 1 -> max|U_1|. Both
+// end by setting DevState::fx_e from the scanned max|U|.
+int launch_prep_split(const double *U, const double *f, int n, int P, float2 *fdf, double *partials,
+                      int nparts, DevState *st, cudaStream_t s);
+int launch_umax(const double *U, long long N, DevState *st, int grid, cudaStream_t s);
 int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *hist,
                     int hist_cap, double b, double lam, int update_state, int use_saved_fnorm,
                     cudaStream_t s);

@@ -109,7 +109,6 @@ __device__ __forceinline__ void residual_sweep(const ResidualArgs &a, ResAcc &s)
         const long long cbase = ((long long)z * n + y) * n;
         for (int x = threadIdx.x; x < P; x += blockDim.x) {
             double r = 0.0;
-            float2 fpair = make_float2(0.0f, 0.0f);
             if (row_ok && x < n) {
                 const long long c = cbase + x;
                 const double u = __ldg(U + c);
@@ -154,7 +153,6 @@ __device__ __forceinline__ void residual_sweep(const ResidualArgs &a, ResAcc &s)
                     s.r2 = fma(r, r, s.r2);
                 }
                 if (a.R64 != nullptr) a.R64[c] = r;
-                if (SPLIT && WANT_F2) fpair = f_pair(fv, a.fx_fbad);
             }
             if (SPLIT) {
                 const float rf = d2f_rn(r);
@@ -163,7 +161,6 @@ __device__ __forceinline__ void residual_sweep(const ResidualArgs &a, ResAcc &s)
                 const long long o = row * P + x;
                 a.Rhi[o] = hi;
                 a.Rlo[o] = lo;
-                if (WANT_F2 && a.fdf != nullptr) a.fdf[o] = fpair;
             }
         }
     }
@@ -190,6 +187,126 @@ __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
         p[2] = acc.mn;
         p[3] = acc.mx;
     }
+}
+
+// Exponent E of the fixed-point stencil of k_residual_tiled for an iterate
+// whose max|U| has bit pattern umax: its exponent plus DevState::fx_headroom
+// (2: room for U to grow 4x before planes take the exact path). 0 (not
+// usable) for a subnormal, non-finite or out-of-range max|U| (outside
+// 2^[-60, 36], where the float-pair arithmetic could leave the FP32 range),
+// for a source beyond the FP32-pair copy, or for ||f|| < 2^-40.
+__device__ __forceinline__ int fx_exponent(unsigned long long umax, const DevState *st) {
+    if (st->fx_fbad || !(st->f_norm >= 0x1p-40)) return 0;
+    if (umax == 0ull) return 1023;   // U = 0: every fixed-point value is 0, any exponent serves
+    const int ex = (int)((umax >> 52) & 0x7FF);
+    if (ex == 0 || ex == 0x7FF) return 0;
+    const int E = ex + st->fx_headroom;
+    return (E - 1023 >= -60 && E - 1023 <= 36) ? E : 0;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// Block-wide max (blockDim.x a multiple of 32, <= 1024); result valid in thread 0.
+__device__ unsigned long long block_max_u64(unsigned long long v) {
+    __shared__ unsigned long long sh[32];
+    v = warp_max_u64(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0ull;
+        v = warp_max_u64(v);
+    }
+    return v;
+}
+
+// Iteration 0 of a 3-D split solve, one pass over f and U_0: the padded
+// FP32-pair copy of f (zeros in the padding), per-block sums of f^2 (FP64),
+// the |f| range check and the max|U_0| bit pattern.
+__global__ void __launch_bounds__(256) k_prep_split(const double *__restrict__ U, const double *__restrict__ f,
+                                                    int n, int P, float2 *__restrict__ fdf,
+                                                    double *__restrict__ partials, DevState *st) {
+    const long long rows = (long long)P * P;
+    double f2 = 0.0;
+    unsigned long long umax = 0ull;
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int y = (int)(row % P), z = (int)(row / P);
+        const bool row_ok = (y < n) && (z < n);
+        const long long cbase = ((long long)z * n + y) * n;
+        for (int x = threadIdx.x; x < P; x += blockDim.x) {
+            float2 fp = make_float2(0.0f, 0.0f);
+            if (row_ok && x < n) {
+                const double fv = __ldg(f + cbase + x);
+                f2 = fma(fv, fv, f2);
+                fp = f_pair(fv, &st->fx_fbad);
+                const unsigned long long ab = abs_bits(__ldg(U + cbase + x));
+                umax = ab > umax ? ab : umax;
+            }
+            fdf[row * P + x] = fp;
+        }
+    }
+    const unsigned long long bm = block_max_u64(umax);
+    Red4 acc{0.0, f2, 0.0, 0.0};
+    acc = block_reduce(acc);
+    if (threadIdx.x == 0) {
+        partials[4ll * blockIdx.x + 1] = acc.f2;
+        atomicMax(&st->umax_scan, bm);
+    }
+}
+
+// ||f|| (fixed-order sum of the partials), the scale of the FP32 norm sums
+// and the fixed-point exponent for the first residual.
+__global__ void __launch_bounds__(256) k_prep_split_finish(const double *partials, int nparts, DevState *st) {
+    Red4 acc{0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc.f2 += partials[4 * i + 1];
+    acc = block_reduce(acc);
+    if (threadIdx.x != 0) return;
+    const double fn = sqrt(acc.f2);
+    st->f_norm = fn;
+    const double rms = (st->npts > 0.0) ? fn / sqrt(st->npts) : 0.0;
+    const int k = (rms > 0.0 && rms < INFINITY) ? ilogb(rms) : 0;
+    st->r2_exp = k < -120 ? -120 : (k > 120 ? 120 : k);
+    st->fx_e = fx_exponent(st->umax_scan, st);
+    st->umax_scan = 0ull;
+}
+
+// max|U| bit pattern of a dense array (iteration 1: the first update's result).
+__global__ void __launch_bounds__(256) k_umax(const double *__restrict__ U, long long N, int vec16, DevState *st) {
+    if (*(volatile const int *)&st->done) return;
+    const unsigned long long *b = reinterpret_cast<const unsigned long long *>(U);
+    unsigned long long m = 0ull;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long tail = 0;
+    if (vec16) {   // U 16-B aligned: two values per load
+        const long long N2 = N >> 1;
+        const ulonglong2 *b2 = reinterpret_cast<const ulonglong2 *>(b);
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N2; i += stride) {
+            const ulonglong2 v = __ldg(b2 + i);
+            const unsigned long long a0 = v.x & 0x7FFFFFFFFFFFFFFFull, a1 = v.y & 0x7FFFFFFFFFFFFFFFull;
+            m = a0 > m ? a0 : m;
+            m = a1 > m ? a1 : m;
+        }
+        tail = 2 * N2;
+    }
+    for (long long i = tail + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride) {
+        const unsigned long long a = __ldg(b + i) & 0x7FFFFFFFFFFFFFFFull;
+        m = a > m ? a : m;
+    }
+    const unsigned long long bm = block_max_u64(m);
+    if (threadIdx.x == 0) atomicMax(&st->umax_scan, bm);
+}
+
+__global__ void k_umax_finish(DevState *st) {
+    if (threadIdx.x != 0 || *(volatile const int *)&st->done) return;
+    st->fx_e = fx_exponent(st->umax_scan, st);
+    st->umax_scan = 0ull;
 }
 
 __global__ void __launch_bounds__(256) k_finalize(const double *partials, int nparts, DevState *st,
@@ -234,17 +351,10 @@ __global__ void __launch_bounds__(256) k_finalize(const double *partials, int np
         hist[it] = s;
     }
     if (!update_state) return;
-    // exponent for the fixed-point stencil of the next residual: max|U| of
-    // this iterate with 2^fx_headroom of room (2: U may grow 4x; values
-    // beyond it take the exact per-point path)
-    int fxe = 0;
-    if (!st->fx_fbad && fn >= 0x1p-40 && acc.mx > 0.0 && acc.mx < INFINITY) {
-        const double um = sqrt(acc.mx);   // >= max|U| in exponent (u^2 rounds up at most)
-        const int ex = (int)(((unsigned long long)__double_as_longlong(um) >> 52) & 0x7FF);
-        const int E = ex + st->fx_headroom;
-        if (E - 1023 >= -60 && E - 1023 <= 36) fxe = E;
-    }
-    st->fx_e = fxe;
+    // exponent for the fixed-point stencil of the next residual, from max|U|
+    // of this iterate (sqrt of max U^2 has at least max|U|'s exponent: the
+    // rounding of u^2 can only carry it up)
+    st->fx_e = (acc.mx < INFINITY) ? fx_exponent((unsigned long long)__double_as_longlong(sqrt(acc.mx)), st) : 0;
     st->beta = beta;
     st->shift = lam + beta;
     if (rel <= st->tol) {
@@ -732,6 +842,24 @@ int launch_residual_tiled(const ResidualArgs &a, int max_grid, int zchunk, int *
     if (a.lam != 0.0) return launch_tiled_kind<0>(a, max_grid, zchunk, grid_used, s);
     if (a.b != 1.0) return launch_tiled_kind<1>(a, max_grid, zchunk, grid_used, s);
     return launch_tiled_kind<2>(a, max_grid, zchunk, grid_used, s);
+}
+
+int launch_prep_split(const double *U, const double *f, int n, int P, float2 *fdf, double *partials,
+                      int nparts, DevState *st, cudaStream_t s) {
+    k_prep_split<<<nparts, 256, 0, s>>>(U, f, n, P, fdf, partials, st);
+    QN_CUDA(cudaGetLastError());
+    k_prep_split_finish<<<1, 256, 0, s>>>(partials, nparts, st);
+    QN_CUDA(cudaGetLastError());
+    return QN_OK;
+}
+
+int launch_umax(const double *U, long long N, DevState *st, int grid, cudaStream_t s) {
+    const int vec16 = ((reinterpret_cast<uintptr_t>(U) & 15u) == 0) ? 1 : 0;
+    k_umax<<<grid, 256, 0, s>>>(U, N, vec16, st);
+    QN_CUDA(cudaGetLastError());
+    k_umax_finish<<<1, 32, 0, s>>>(st);
+    QN_CUDA(cudaGetLastError());
+    return QN_OK;
 }
 
 int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *hist,

@@ -414,3 +414,40 @@ def test_split_solve_any_source_scale(qn, dim, n, scale, b):
     rel = np.linalg.norm(O.residual(Ug, f, b=b)) / np.linalg.norm(f)
     assert rel <= 1.05e-10
     assert np.abs(Ug - Uo).max() <= 1e-9 * np.abs(Uo).max()
+
+
+@pytest.mark.parametrize("max_it", [1, 2, 3, 4])
+def test_tiled_path_iterates_match_per_point_path(qn, monkeypatch, max_it):
+    """The first iterations of a 3-D split solve: iteration 0 prepares the
+    FP32-pair copy of f and ||f|| in one pass, iteration 1 scans max|U_1| for
+    the fixed-point exponent. Stopped after max_it iterations, U must equal the
+    iterate of the per-point residual path (QN_RES_TILED=0) to the FP32
+    rounding of the residual."""
+    import torch
+    n = 45
+    u, f = manufactured_problem(n, 3, seed=8)
+    outs = []
+    for tiled in ("1", "0"):
+        monkeypatch.setenv("QN_RES_TILED", tiled)
+        ctx = qn.QnContext(3, n, "bf16x3")
+        U = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
+        res, _ = qn.qn_solve(ctx, U, dev(f).reshape(-1), tol=1e-30, max_it=max_it)
+        assert res["status"] == qn.QN_ENOTCONV and res["iterations"] == max_it
+        outs.append(host(U))
+    assert np.abs(outs[0] - outs[1]).max() <= 1e-6 * np.abs(outs[1]).max()
+
+
+@pytest.mark.parametrize("step", [0.7, 1.3])
+def test_split_solve_damped_step(qn, step):
+    """U_k = U_{k-1} - step * delta with step != 1: same fixed point as the oracle's damped iteration."""
+    import torch
+    n = 33
+    u, f = manufactured_problem(n, 3, seed=9)
+    ctx = qn.QnContext(3, n, "bf16x3")
+    U = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
+    res, _ = qn.qn_solve(ctx, U, dev(f).reshape(-1), tol=1e-10, step=step, max_it=300)
+    Uo, ho, ok = O.qn_solve(f, tol=1e-10, step=step, max_it=300)
+    assert ok and res["status"] == 0
+    Ug = host(U).reshape(f.shape)
+    assert np.linalg.norm(O.residual(Ug, f)) / np.linalg.norm(f) <= 1.05e-10
+    assert np.abs(Ug - Uo).max() <= 1e-9 * np.abs(Uo).max()
