@@ -43,7 +43,9 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BN_MAX = 256;
-constexpr int kEpiWarps = 8;                       // two warps per TMEM lane quadrant
+constexpr int kEpiWarps = 16;                      // four warps per TMEM lane quadrant
+constexpr int kEpiParts = kEpiWarps / 4;            // column ranges per quadrant
+constexpr int kChunk = 16;                          // accumulator columns per TMEM load
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kMaxStages = 8;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp >= 2) {
         // ------------------------------ epilogue ----------------------------------
         const int q = warp & 3;                          // TMEM lanes 32q..32q+31 = tile rows
-        const int half = (warp - 2) >> 2;                // which half of the BN columns
+        const int part = (warp - 2) >> 2;                // which of the kEpiParts column ranges
         const int row = q * 32 + lane;
         int acc = 0;
         uint32_t aph = 0;
@@ -285,20 +287,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int kstride = (DIM == 3) ? n * n : n;
             const float dscale = G.dscale;
             const float step = G.step;
-            const int cbeg = half * (BN >> 1), cend = cbeg + (BN >> 1);
-            for (int c = cbeg; c < cend; c += 32) {
-                uint32_t r[32];
-                ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN_MAX + c), r);
+            const int cols = BN / kEpiParts;   // >= 16: BN is 64, 128 or 256
+            const int cbeg = part * cols, cend = cbeg + cols;
+            for (int c = cbeg; c < cend; c += kChunk) {
+                uint32_t r[kChunk];
+                ptx::tmem_ld_32x32b_x16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN_MAX + c), r);
                 ptx::tmem_ld_wait();
                 if (!m_ok) continue;
                 const int k0 = n0 + c;
                 if (EPI == EPI_STORE) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
+                    for (int i = 0; i < kChunk; ++i)
                         if (k0 + i < P) split_store(__uint_as_float(r[i]), G.out_hi, G.out_lo, (k0 + i) * Mtot + m);
                 } else if (EPI == EPI_DIVIDE) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
+                    for (int i = 0; i < kChunk; ++i) {
                         const int k = k0 + i;
                         if (k < P) {
                             const float den = dscale * (__ldg(G.lam32 + k) + rowlam) + shift;
@@ -307,33 +310,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 } else if (EPI == EPI_UPDATE) {
                     if (ubase >= 0) {
-                        // 16 loads of U in flight per thread before the stores,
+                        // the chunk's 16 loads of U in flight before its stores,
                         // instead of a serial read-modify-write
                         double *ub = G.U + ubase;
+                        double old[kChunk];
 #pragma unroll
-                        for (int h = 0; h < 32; h += 16) {
-                            double old[16];
+                        for (int i = 0; i < kChunk; ++i) old[i] = (k0 + i < n) ? ub[(k0 + i) * kstride] : 0.0;
+                        if (step == 1.0f) {
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) old[i] = (k0 + h + i < n) ? ub[(k0 + h + i) * kstride] : 0.0;
-                            if (step == 1.0f) {
+                            for (int i = 0; i < kChunk; ++i)
+                                if (k0 + i < n) ub[(k0 + i) * kstride] = old[i] - f2d_exact(__uint_as_float(r[i]));
+                        } else {
+                            const double st = (double)step;
 #pragma unroll
-                                for (int i = 0; i < 16; ++i)
-                                    if (k0 + h + i < n)
-                                        ub[(k0 + h + i) * kstride] = old[i] - f2d_exact(__uint_as_float(r[h + i]));
-                            } else {
-                                const double st = (double)step;
-#pragma unroll
-                                for (int i = 0; i < 16; ++i)
-                                    if (k0 + h + i < n)
-                                        ub[(k0 + h + i) * kstride] = fma(-st, f2d_exact(__uint_as_float(r[h + i])), old[i]);
-                            }
+                            for (int i = 0; i < kChunk; ++i)
+                                if (k0 + i < n)
+                                    ub[(k0 + i) * kstride] = fma(-st, f2d_exact(__uint_as_float(r[i])), old[i]);
                         }
                     }
                 } else {   // EPI_DENSE
                     if (ubase >= 0) {
                         double *ub = G.U + ubase;
 #pragma unroll
-                        for (int i = 0; i < 32; ++i)
+                        for (int i = 0; i < kChunk; ++i)
                             if (k0 + i < n) ub[(k0 + i) * kstride] = f2d_exact(__uint_as_float(r[i]));
                     }
                 }
