@@ -102,8 +102,11 @@ __device__ __forceinline__ bool group_done(const TcGroup &G) {
     return G.done != nullptr && *(volatile const int *)G.done;
 }
 
+// 576 threads x 104 registers (one CTA per SM; 112 exceeds the launch limit)
+static_assert(kThreads * 104 <= 65536, "register file");
+
 template <int BK, int EPI, int DIM>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__(104)
     k_modeprod_tc(const TcGroup g0, const TcGroup *__restrict__ groups, const TcTile *__restrict__ tiles,
                   const int ntiles, const int stages, int *err) {
     if (groups == nullptr && group_done(g0)) return;
@@ -313,6 +316,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                         // the chunk's 16 loads of U in flight before its stores,
                         // instead of a serial read-modify-write
                         double *ub = G.U + ubase;
+                        // the next chunk's U lines are requested into L2 now
+                        // (no registers), its loads then hit L2
+                        if (c + kChunk < cend) {
+#pragma unroll
+                            for (int i = 0; i < kChunk; ++i)
+                                if (k0 + kChunk + i < n) ptx::prefetch_l2(ub + (k0 + kChunk + i) * kstride);
+                        }
                         double old[kChunk];
 #pragma unroll
                         for (int i = 0; i < kChunk; ++i) old[i] = (k0 + i < n) ? ub[(k0 + i) * kstride] : 0.0;
