@@ -84,6 +84,11 @@ struct qn_ctx {
     int res_parts;        // partial-sum records written by the last residual launch
     int res_fx_headroom;  // DevState::fx_headroom for the solves of this context
     int res_saved_fnorm;  // 1: the last residual's finaliser takes ||f|| from DevState::f_norm
+    // reflection-split mode products (3-D split solve, P a multiple of 128)
+    int split;            // 1: the plan holds the split matrices and the solve loop uses them
+    int split_layout;     // 1: the last residual wrote its planes in split / folded order
+    __nv_bfloat16 *bf_hi, *bf_lo, *bb_hi, *bb_lo;   // [P][P/2] forward / backward matrices
+    float *lam32_split;   // eigenvalues in split mode order (even modes, then odd), 1e30 padding
 };
 
 enum ProfKind { PK_RESIDUAL = 0, PK_FINALIZE = 1, PK_MP_STORE = 2, PK_MP_DIVIDE = 3, PK_MP_LAST = 4,
@@ -170,6 +175,11 @@ static void ctx_free(qn_ctx *c) {
     cudaFree(c->Si_hi);
     cudaFree(c->Si_lo);
     cudaFree(c->lam32);
+    cudaFree(c->bf_hi);
+    cudaFree(c->bf_lo);
+    cudaFree(c->bb_hi);
+    cudaFree(c->bb_lo);
+    cudaFree(c->lam32_split);
     for (int b = 0; b < 2; ++b) {
         cudaFree(c->w64[b]);
         cudaFree(c->bhi[b]);
@@ -339,6 +349,55 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
             ctx_free(c);
             return rc;
         }
+        // Reflection-split matrices (qn_modeprod_tc.cu): with H = P/2,
+        //   forward  Bf[p][j]: p < H -> S[j][2p] for j < ceil(n/2) (the middle
+        //            column of an odd n included); p >= H -> S[j][2(p-H)+1], j < n/2
+        //   backward Bb[r][i]: r < H -> S[r][2i] (r < ceil(n/2));
+        //            r >= H -> S[r-H][2i+1] (r-H < n/2)
+        // (S symmetric), and the eigenvalues in the same mode order.
+        const char *es = getenv("QN_SPLIT");
+        const bool want_split = es ? (atoi(es) != 0) : true;
+        if (want_split && c->dim == 3 && P % 128 == 0 && c->fdf != nullptr) {
+            const int H = P / 2, nsym = (n + 1) / 2, nanti = n / 2;
+            std::vector<__nv_bfloat16> fh((size_t)P * H), fl((size_t)P * H), bh((size_t)P * H), blo((size_t)P * H);
+            std::vector<float> ls(P, 1e30f);
+            for (int p = 0; p < P; ++p) {
+                const int k = (p < H) ? 2 * p : 2 * (p - H) + 1;
+                const int jmax = (p < H) ? nsym : nanti;
+                if (k < n) ls[p] = (float)lam[k];
+                for (int j = 0; j < H; ++j) {
+                    const double v = (k < n && j < jmax) ? S[(size_t)j * n + k] : 0.0;
+                    split_host(v, fh[(size_t)p * H + j], fl[(size_t)p * H + j]);
+                }
+            }
+            for (int r = 0; r < P; ++r) {
+                const int j = (r < H) ? r : r - H;
+                const int jmax = (r < H) ? nsym : nanti;
+                for (int i = 0; i < H; ++i) {
+                    const int k = (r < H) ? 2 * i : 2 * i + 1;
+                    const double v = (j < jmax && k < n) ? S[(size_t)j * n + k] : 0.0;
+                    split_host(v, bh[(size_t)r * H + i], blo[(size_t)r * H + i]);
+                }
+            }
+            const size_t bb = sizeof(__nv_bfloat16) * (size_t)P * H;
+            CK(cudaMalloc(&c->bf_hi, bb));
+            CK(cudaMalloc(&c->bf_lo, bb));
+            CK(cudaMalloc(&c->bb_hi, bb));
+            CK(cudaMalloc(&c->bb_lo, bb));
+            CK(cudaMalloc(&c->lam32_split, sizeof(float) * P));
+            CK(cudaMemcpy(c->bf_hi, fh.data(), bb, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->bf_lo, fl.data(), bb, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->bb_hi, bh.data(), bb, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->bb_lo, blo.data(), bb, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->lam32_split, ls.data(), sizeof(float) * P, cudaMemcpyHostToDevice));
+            rc = tc_plan_enable_split(c->plan, c->bf_hi, c->bf_lo, c->bb_hi, c->bb_lo);
+            if (rc == QN_OK) {
+                c->split = 1;
+            } else if (rc != QN_EUNSUPPORTED) {
+                ctx_free(c);
+                return rc;
+            }
+        }
     }
     *out = c;
     return QN_OK;
@@ -425,10 +484,13 @@ static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double 
     const bool tiled = split_solve && c->fdf != nullptr && c->res_tiled;
     c->res_saved_fnorm = (c->cur_iter > 0 || tiled) ? 1 : 0;
     int rc = QN_OK;
+    // reflection-split layout of the planes (read by the split mode products)
+    const bool mirror = tiled && c->split;
+    c->split_layout = mirror ? 1 : 0;
     if (tiled && c->cur_iter <= 1) {
         const long pp = prof_begin(c, PK_RESIDUAL, s);
         if (c->cur_iter == 0)
-            rc = launch_prep_split(U, f, c->n, c->P, c->fdf, c->partials, c->nparts, c->st, s);
+            rc = launch_prep_split(U, f, c->n, c->P, c->fdf, c->partials, c->nparts, c->st, mirror, s);
         else
             rc = launch_umax(U, c->N, c->st, 2 * c->num_sms, s);
         prof_end(c, pp, s);
@@ -440,7 +502,9 @@ static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double 
         a.want_f2 = 0;
     }
     const long pr = prof_begin(c, tiled ? PK_RESIDUAL_TILED : PK_RESIDUAL, s);
-    if (tiled) {
+    if (mirror) {
+        rc = launch_residual_mirror(a, c->nparts, c->res_zc, &c->res_parts, s);
+    } else if (tiled) {
         rc = launch_residual_tiled(a, c->nparts, c->res_zc, &c->res_parts, s);
     } else {
         rc = launch_residual(a, c->nparts, s);
@@ -453,9 +517,25 @@ static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double 
 // Shifted inverse of working buffer 0 (or of `r0` for the FP64 path), written
 // as U -= step*delta (update=true) or V = delta (update=false).
 static int enqueue_inverse(qn_ctx *c, const double *r0, double *target, bool update, double step,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool split = false) {
     const int d = c->dim;
-    const EpiArgs e = epi_args(c, target, step);
+    EpiArgs e = epi_args(c, target, step);
+    if (split && update) {
+        // reflection-split products on the split / folded planes of the residual
+        e.lam32 = c->lam32_split;
+        const Epi seq[6] = {EPI_STORE_BFLY, EPI_STORE_BFLY, EPI_DIVIDE, EPI_STORE_PQ, EPI_STORE_PQ, EPI_UPDATE_PQ};
+        int cur = 0;
+        for (int i = 0; i < 6; ++i) {
+            const bool last = (i == 5);
+            const int next = 1 - cur;
+            const long pr = prof_begin(c, last ? PK_MP_LAST : (i == 2 ? PK_MP_DIVIDE : PK_MP_STORE), s);
+            const int rc = launch_modeprod_tc_split(c->plan, cur, last ? -1 : next, seq[i], e, s);
+            prof_end(c, pr, s);
+            if (rc != QN_OK) return rc;
+            cur = next;
+        }
+        return QN_OK;
+    }
     int cur = 0;
     for (int i = 0; i < 2 * d; ++i) {
         const bool forward = i < d;
@@ -496,7 +576,7 @@ static int enqueue_iteration(qn_ctx *c, double *U, const double *f, double step,
                          c->res_saved_fnorm, s);
     prof_end(c, pr, s);
     if (rc) return rc;
-    return enqueue_inverse(c, nullptr, U, true, step, s);
+    return enqueue_inverse(c, nullptr, U, true, step, s, c->split_layout != 0);
 }
 
 static int read_state(qn_ctx *c, DevState *h, cudaStream_t s) {

@@ -66,6 +66,10 @@ enum Epi : int {
     EPI_DIVIDE = 1,   // out[k][m] = acc / (lambda_k + row eigen-sum + shift)
     EPI_UPDATE = 2,   // U[dense(k, m)] -= step * acc
     EPI_DENSE = 3,    // V[dense(k, m)] = acc  (FP64 dense output)
+    // reflection-split products (3-D split solve, see k_modeprod_tc):
+    EPI_STORE_BFLY = 4,   // forward: sums / differences of reflection partners along the next axis
+    EPI_STORE_PQ = 5,     // backward: rows j and n-1-j from the even- and odd-mode partial sums
+    EPI_UPDATE_PQ = 6,    // backward, last product: U -= step * (the same two rows)
 };
 
 struct EpiArgs {
@@ -99,7 +103,10 @@ int launch_residual_tiled(const ResidualArgs &a, int max_grid, int zchunk, int *
 // f^2 (DevState::f_norm, r2_exp) and max|U_0|; iteration 1 -> max|U_1|. Both
 // end by setting DevState::fx_e from the scanned max|U|.
 int launch_prep_split(const double *U, const double *f, int n, int P, float2 *fdf, double *partials,
-                      int nparts, DevState *st, cudaStream_t s);
+                      int nparts, DevState *st, bool mirror, cudaStream_t s);
+// The same residual written in split order along x and folded order along y
+// and z, the input layout of the reflection-split mode products.
+int launch_residual_mirror(const ResidualArgs &a, int max_grid, int zchunk, int *grid_used, cudaStream_t s);
 int launch_umax(const double *U, long long N, DevState *st, int grid, cudaStream_t s);
 int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *hist,
                     int hist_cap, double b, double lam, int update_state, int use_saved_fnorm,
@@ -139,6 +146,15 @@ void tc_plan_destroy(TcPlan *plan);
 // the FP64 dense target for EPI_UPDATE / EPI_DENSE). forward selects S^{-1}.
 int launch_modeprod_tc(TcPlan *plan, int src, int dst, bool forward, Epi epi,
                        const EpiArgs &e, cudaStream_t s);
+// Reflection-split products (3-D, P a multiple of 128): B_fwd, B_bwd are the
+// [P][P/2] split-precision matrices described in qn_modeprod_tc.cu. Returns
+// QN_EUNSUPPORTED when the sizes do not allow it (the plan keeps the dense path).
+int tc_plan_enable_split(TcPlan *plan, const __nv_bfloat16 *bf_hi, const __nv_bfloat16 *bf_lo,
+                         const __nv_bfloat16 *bb_hi, const __nv_bfloat16 *bb_lo);
+bool tc_plan_has_split(const TcPlan *plan);
+// One reflection-split product: EPI_STORE_BFLY / EPI_DIVIDE (forward) or
+// EPI_STORE_PQ / EPI_UPDATE_PQ (backward).
+int launch_modeprod_tc_split(TcPlan *plan, int src, int dst, Epi epi, const EpiArgs &e, cudaStream_t s);
 // Grouped launch over a device tile table (batched solves).
 int launch_modeprod_tc_grouped(const TcGroup *groups, const TcTile *tiles, int ntiles, int dim, int BK,
                                Epi epi, int *err, int grid, cudaStream_t s);

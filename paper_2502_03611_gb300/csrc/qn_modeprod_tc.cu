@@ -25,6 +25,26 @@
 // S stays resident in L2). The epilogue of tile i overlaps the MMAs of tile
 // i+1 through the double-buffered accumulators.
 //
+// Reflection-split products (MODE 1 and 2; 3-D split solve with P a multiple
+// of 128, H = P/2). The sine basis satisfies S[n-1-j][k] = (-1)^k S[j][k], so
+// along one axis
+//   forward:  Xhat[2i]   = sum_j S[j][2i]   a_j,  a_j = x_j + x_{n-1-j} (+ the middle x of odd n)
+//             Xhat[2i+1] = sum_j S[j][2i+1] b_j,  b_j = x_j - x_{n-1-j}
+//   backward: x_j = p_j + q_j, x_{n-1-j} = p_j - q_j with p_j = sum_i S[j][2i] Y_{2i},
+//             q_j = sum_i S[j][2i+1] Y_{2i+1}
+// - two GEMMs of half the contraction length instead of one: half the tensor
+// work. Tensors in this form keep the contracted axis in split order (a or
+// even modes in [0, H), b or odd modes in [H, P)).
+//   MODE 1 (forward): output rows k < H take the A columns [0, H), rows >= H the
+//   columns [H, P); B = [P][H] (even-mode rows, then odd-mode rows).
+//   MODE 2 (backward): a tile of BN <= 128 output rows j < H accumulates p over
+//   the A columns [0, H) and q over [H, P) in two TMEM accumulators; B = [P][H]
+//   (rows j of the even-mode half, then of the odd-mode half). The epilogue
+//   writes rows j and n-1-j.
+// The butterflies that form a and b ride in the epilogues: the axis that the
+// next product contracts is the fast part of m, stored in folded order (j at
+// 2j, its mirror at 2j+1), so partners sit in adjacent TMEM lanes (one shuffle).
+//
 // Every mbarrier wait is bounded (2 s of %globaltimer). On expiry the kernel
 // sets the device error flag, tells the other roles to stop, waits (bounded)
 // for its own outstanding TMA copies and MMAs, frees TMEM and returns.
@@ -105,7 +125,7 @@ __device__ __forceinline__ bool group_done(const TcGroup &G) {
 // 576 threads x 104 registers (one CTA per SM; 112 exceeds the launch limit)
 static_assert(kThreads * 104 <= 65536, "register file");
 
-template <int BK, int EPI, int DIM>
+template <int BK, int EPI, int DIM, int MODE>
 __global__ void __maxnreg__(104)
     k_modeprod_tc(const TcGroup g0, const TcGroup *__restrict__ groups, const TcTile *__restrict__ tiles,
                   const int ntiles, const int stages, int *err) {
@@ -176,18 +196,28 @@ __global__ void __maxnreg__(104)
             tile_info(t, g0, groups, tiles, G, m0, n0);
             if (group_done(G)) continue;
             const uint32_t tx_bytes = 2 * a_bytes + 2u * (uint32_t)G.BN * kRowBytes;
-            const int KB = G.P / BK;
+            const int Hh = G.P >> 1, KBh = Hh / BK;
+            const int KB = (MODE == 0) ? G.P / BK : (MODE == 1 ? KBh : 2 * KBh);
             for (int kb = 0; kb < KB; ++kb) {
                 if (!wait_bar(empty_bar(s), ph ^ 1u, abort_flag, err)) {
                     ok = false;
                     break;
                 }
+                // A column (contraction) and B row coordinates of this K step
+                int ax = kb * BK, bx = kb * BK, by = n0;
+                if (MODE == 1) ax = (n0 >= Hh ? Hh : 0) + kb * BK;
+                if (MODE == 2) {
+                    const bool second = kb >= KBh;
+                    bx = (second ? kb - KBh : kb) * BK;
+                    ax = (second ? Hh : 0) + bx;
+                    by = (second ? Hh : 0) + n0;
+                }
                 const uint32_t st = base + (uint32_t)s * stage_bytes;
                 ptx::mbar_arrive_expect_tx(full_bar(s), tx_bytes);
-                ptx::tma_load_2d(st, G.a_hi, full_bar(s), kb * BK, m0);
-                ptx::tma_load_2d(st + a_bytes, G.a_lo, full_bar(s), kb * BK, m0);
-                ptx::tma_load_2d(st + 2 * a_bytes, G.b_hi, full_bar(s), kb * BK, n0);
-                ptx::tma_load_2d(st + 2 * a_bytes + b_bytes_max, G.b_lo, full_bar(s), kb * BK, n0);
+                ptx::tma_load_2d(st, G.a_hi, full_bar(s), ax, m0);
+                ptx::tma_load_2d(st + a_bytes, G.a_lo, full_bar(s), ax, m0);
+                ptx::tma_load_2d(st + 2 * a_bytes, G.b_hi, full_bar(s), bx, by);
+                ptx::tma_load_2d(st + 2 * a_bytes + b_bytes_max, G.b_lo, full_bar(s), bx, by);
                 armed_parity[s] = ph;
                 armed_mask |= 1u << s;
                 if (++s == stages) {
@@ -213,11 +243,15 @@ __global__ void __maxnreg__(104)
             tile_info(t, g0, groups, tiles, G, m0, n0);
             if (group_done(G)) continue;
             const uint32_t idesc = ptx::idesc_bf16_f32(BM, (uint32_t)G.BN);
-            const int KB = G.P / BK;
+            const int KBh = (G.P >> 1) / BK;
+            const int KB = (MODE == 0) ? G.P / BK : (MODE == 1 ? KBh : 2 * KBh);
             if (!wait_bar(tempty_bar(acc), aph ^ 1u, abort_flag, err)) break;
             ptx::tc_fence_after();
-            const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN_MAX);
             for (int kb = 0; kb < KB; ++kb) {
+                // MODE 2: the second half of the K steps accumulates q, BN columns further on
+                const bool second = (MODE == 2) && kb >= KBh;
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN_MAX + (second ? G.BN : 0));
+                const int kb0 = second ? kb - KBh : kb;
                 if (!wait_bar(full_bar(s), ph, abort_flag, err)) {
                     ok = false;
                     break;
@@ -232,7 +266,7 @@ __global__ void __maxnreg__(104)
                     const uint64_t b_hi = ptx::smem_desc_kmajor(st + 2 * a_bytes + koff, kRowBytes, kLayout);
                     const uint64_t b_lo =
                         ptx::smem_desc_kmajor(st + 2 * a_bytes + b_bytes_max + koff, kRowBytes, kLayout);
-                    const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+                    const uint32_t first = (kb0 == 0 && kk == 0) ? 0u : 1u;
                     ptx::mma_bf16(d_tmem, a_hi, b_hi, idesc, first);
                     ptx::mma_bf16(d_tmem, a_hi, b_lo, idesc, 1u);
                     ptx::mma_bf16(d_tmem, a_lo, b_hi, idesc, 1u);
@@ -278,7 +312,7 @@ __global__ void __maxnreg__(104)
                     rowlam = (DIM == 3) ? __ldg(G.lam32 + m / P) + __ldg(G.lam32 + m % P) : __ldg(G.lam32 + m);
                     shift = (float)(*G.shift);
                 }
-                if (EPI == EPI_UPDATE || EPI == EPI_DENSE) {
+                if (EPI == EPI_UPDATE || EPI == EPI_DENSE || EPI == EPI_UPDATE_PQ) {
                     if (DIM == 3) {
                         const int yy = m / P, xx = m % P;
                         if (yy < n && xx < n) ubase = yy * n + xx;
@@ -292,7 +326,79 @@ __global__ void __maxnreg__(104)
             const float step = G.step;
             const int cols = BN / kEpiParts;   // >= 16: BN is 64, 128 or 256
             const int cbeg = part * cols, cend = cbeg + cols;
-            for (int c = cbeg; c < cend; c += kChunk) {
+            const int Hh = P >> 1;
+            const int nsym = (n + 1) >> 1, nanti = n >> 1;
+            const uint32_t tacc = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN_MAX);
+            if (EPI == EPI_STORE_BFLY) {
+                // row m = (slow, F): F = 2i holds spatial i, F = 2i+1 its mirror n-1-i
+                // (adjacent lanes); the even lane writes a_i at position i, the odd
+                // lane b_i at H + i of the next product's split-order axis (zeros in
+                // the padding of either half)
+                const int F = m % P, slow = m / P, i2 = F >> 1;
+                const bool odd = (F & 1) != 0;
+                const bool valid = odd ? (i2 < nanti) : (i2 < nsym);
+                const int obase = slow * P + (odd ? Hh + i2 : i2);
+                for (int c = cbeg; c < cend; c += kChunk) {
+                    uint32_t r[kChunk];
+                    ptx::tmem_ld_32x32b_x16(tacc + (uint32_t)c, r);
+                    ptx::tmem_ld_wait();
+                    const int k0 = n0 + c;
+#pragma unroll
+                    for (int i = 0; i < kChunk; ++i) {
+                        const float v = __uint_as_float(r[i]);
+                        const float pv = __shfl_xor_sync(0xffffffffu, v, 1);
+                        const float o = valid ? (odd ? pv - v : v + pv) : 0.0f;
+                        if (k0 + i < P) split_store(o, G.out_hi, G.out_lo, (k0 + i) * Mtot + obase);
+                    }
+                }
+            }
+            if (EPI == EPI_STORE_PQ || EPI == EPI_UPDATE_PQ) {
+                // p in columns [0, BN), q in [BN, 2 BN) of the accumulator; output
+                // rows j (< H) and n-1-j; the middle row of an odd n takes p alone
+                for (int c = cbeg; c < cend; c += 8) {
+                    uint32_t rp[8], rq[8];
+                    ptx::tmem_ld_32x32b_x8(tacc + (uint32_t)c, rp);
+                    ptx::tmem_ld_32x32b_x8(tacc + (uint32_t)(BN + c), rq);
+                    ptx::tmem_ld_wait();
+                    if (!m_ok) continue;
+                    const int j0 = n0 + c;
+                    if (EPI == EPI_STORE_PQ) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int j = j0 + i;
+                            const float p = __uint_as_float(rp[i]), qv = __uint_as_float(rq[i]);
+                            if (j < nanti) {
+                                split_store(p + qv, G.out_hi, G.out_lo, j * Mtot + m);
+                                split_store(p - qv, G.out_hi, G.out_lo, (n - 1 - j) * Mtot + m);
+                            } else if (j < nsym) {
+                                split_store(p, G.out_hi, G.out_lo, j * Mtot + m);
+                            }
+                        }
+                    } else if (ubase >= 0) {
+                        double *ub = G.U + ubase;
+                        double oa[8], ob[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int j = j0 + i;
+                            oa[i] = (j < nsym) ? ub[j * kstride] : 0.0;
+                            ob[i] = (j < nanti) ? ub[(n - 1 - j) * kstride] : 0.0;
+                        }
+                        const double st = (double)step;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int j = j0 + i;
+                            const float p = __uint_as_float(rp[i]), qv = __uint_as_float(rq[i]);
+                            const float xa = (j < nanti) ? p + qv : p, xb = p - qv;
+                            if (j < nsym)
+                                ub[j * kstride] = (step == 1.0f) ? oa[i] - f2d_exact(xa) : fma(-st, f2d_exact(xa), oa[i]);
+                            if (j < nanti)
+                                ub[(n - 1 - j) * kstride] =
+                                    (step == 1.0f) ? ob[i] - f2d_exact(xb) : fma(-st, f2d_exact(xb), ob[i]);
+                        }
+                    }
+                }
+            }
+            for (int c = cbeg; EPI <= EPI_DENSE && c < cend; c += kChunk) {
                 uint32_t r[kChunk];
                 ptx::tmem_ld_32x32b_x16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN_MAX + c), r);
                 ptx::tmem_ld_wait();
@@ -371,8 +477,9 @@ __global__ void __maxnreg__(104)
 // ---------------------------------------------------------------------------
 struct TcPlan {
     int n, P, dim, Mtot, BN, ntile_n, ntiles, grid, stages, BK;
+    int split, BN1, BN2, num_sms;   // reflection-split products: forward / backward tile widths
     size_t smem;
-    CUtensorMap *maps;   // device: a_hi[2], a_lo[2], s_hi, s_lo, si_hi, si_lo
+    CUtensorMap *maps;   // device: a_hi[2], a_lo[2], s_hi, s_lo, si_hi, si_lo, bf_hi, bf_lo, bb_hi, bb_lo
     __nv_bfloat16 *bufs_hi[2];
     __nv_bfloat16 *bufs_lo[2];
 };
@@ -450,11 +557,13 @@ int tc_plan_create(TcPlan **out, int n, int P, int dim, __nv_bfloat16 *bufs_hi[2
     p->stages = tc_stages(p->BK);
     p->smem = tc_smem_bytes(p->BK, p->stages);
     p->grid = p->ntiles < num_sms ? p->ntiles : num_sms;
+    p->num_sms = num_sms;
     if (tc_set_attributes() != QN_OK) {
         free(p);
         return QN_ECUDA;
     }
-    CUtensorMap h[8];
+    CUtensorMap h[12];
+    memset(h, 0, sizeof(h));
     int rc = QN_OK;
     for (int b = 0; b < 2 && rc == QN_OK; ++b) {
         p->bufs_hi[b] = bufs_hi[b];
@@ -477,16 +586,35 @@ int tc_plan_create(TcPlan **out, int n, int P, int dim, __nv_bfloat16 *bufs_hi[2
     return QN_OK;
 }
 
+int tc_plan_enable_split(TcPlan *p, const __nv_bfloat16 *bf_hi, const __nv_bfloat16 *bf_lo,
+                         const __nv_bfloat16 *bb_hi, const __nv_bfloat16 *bb_lo) {
+    const int H = p->P / 2;
+    if (p->dim != 3 || p->BK != 64 || p->P % 128 != 0) return QN_EUNSUPPORTED;
+    p->BN1 = H < BN_MAX ? H : BN_MAX;   // forward tiles must not straddle the halves
+    p->BN2 = H < 128 ? H : 128;         // backward: two accumulators of BN2 columns per tile
+    CUtensorMap h[4];
+    int rc = tc_encode_2d(&h[0], bf_hi, H, p->P, p->BK, p->BN1, p->BK);
+    if (rc == QN_OK) rc = tc_encode_2d(&h[1], bf_lo, H, p->P, p->BK, p->BN1, p->BK);
+    if (rc == QN_OK) rc = tc_encode_2d(&h[2], bb_hi, H, p->P, p->BK, p->BN2, p->BK);
+    if (rc == QN_OK) rc = tc_encode_2d(&h[3], bb_lo, H, p->P, p->BK, p->BN2, p->BK);
+    if (rc != QN_OK) return rc;
+    QN_CUDA(cudaMemcpy(p->maps + 8, h, sizeof(h), cudaMemcpyHostToDevice));
+    p->split = 1;
+    return QN_OK;
+}
+
+bool tc_plan_has_split(const TcPlan *p) { return p != nullptr && p->split; }
+
 void tc_plan_destroy(TcPlan *plan) {
     if (!plan) return;
     cudaFree(plan->maps);
     free(plan);
 }
 
-template <int BK, int EPI, int DIM>
+template <int BK, int EPI, int DIM, int MODE = 0>
 static int launch_t(const TcGroup &g0, const TcGroup *groups, const TcTile *tiles, int ntiles, int stages,
                     int *err, int grid, cudaStream_t s) {
-    auto kern = k_modeprod_tc<BK, EPI, DIM>;
+    auto kern = k_modeprod_tc<BK, EPI, DIM, MODE>;
     kern<<<grid, kThreads, tc_smem_bytes(BK, stages), s>>>(g0, groups, tiles, ntiles, stages, err);
     QN_CUDA(cudaGetLastError());
     return QN_OK;
@@ -513,13 +641,20 @@ static int launch_any(int BK, int dim, Epi epi, const TcGroup &g0, const TcGroup
                     : launch_epi<32, 2>(epi, g0, groups, tiles, ntiles, stages, err, grid, s);
 }
 
+template <int BK, int EPI, int DIM, int MODE = 0>
+static int set_attr_one() {
+    QN_CUDA(cudaFuncSetAttribute(k_modeprod_tc<BK, EPI, DIM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 227 * 1024));
+    return QN_OK;
+}
+
 template <int BK, int DIM>
 static int set_attr_dim() {
-    QN_CUDA(cudaFuncSetAttribute(k_modeprod_tc<BK, EPI_STORE, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    QN_CUDA(cudaFuncSetAttribute(k_modeprod_tc<BK, EPI_DIVIDE, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    QN_CUDA(cudaFuncSetAttribute(k_modeprod_tc<BK, EPI_UPDATE, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    QN_CUDA(cudaFuncSetAttribute(k_modeprod_tc<BK, EPI_DENSE, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    return QN_OK;
+    int rc = set_attr_one<BK, EPI_STORE, DIM>();
+    if (rc == QN_OK) rc = set_attr_one<BK, EPI_DIVIDE, DIM>();
+    if (rc == QN_OK) rc = set_attr_one<BK, EPI_UPDATE, DIM>();
+    if (rc == QN_OK) rc = set_attr_one<BK, EPI_DENSE, DIM>();
+    return rc;
 }
 
 // Opt every instantiation in to the large dynamic shared memory once (before
@@ -529,7 +664,54 @@ int tc_set_attributes() {
     if (rc == QN_OK) rc = set_attr_dim<64, 3>();
     if (rc == QN_OK) rc = set_attr_dim<32, 2>();
     if (rc == QN_OK) rc = set_attr_dim<32, 3>();
+    if (rc == QN_OK) rc = set_attr_one<64, EPI_STORE_BFLY, 3, 1>();
+    if (rc == QN_OK) rc = set_attr_one<64, EPI_DIVIDE, 3, 1>();
+    if (rc == QN_OK) rc = set_attr_one<64, EPI_STORE_PQ, 3, 2>();
+    if (rc == QN_OK) rc = set_attr_one<64, EPI_UPDATE_PQ, 3, 2>();
     return rc;
+}
+
+int launch_modeprod_tc_split(TcPlan *p, int src, int dst, Epi epi, const EpiArgs &e, cudaStream_t s) {
+    if (!p->split) {
+        set_error("launch_modeprod_tc_split: the plan has no reflection-split matrices");
+        return QN_EINVAL;
+    }
+    const bool fwd = (epi == EPI_STORE_BFLY || epi == EPI_DIVIDE);
+    if (!fwd && epi != EPI_STORE_PQ && epi != EPI_UPDATE_PQ) {
+        set_error("launch_modeprod_tc_split: epilogue %d is not a reflection-split one", (int)epi);
+        return QN_EINVAL;
+    }
+    TcGroup g;
+    memset(&g, 0, sizeof(g));
+    g.a_hi = p->maps + src;
+    g.a_lo = p->maps + 2 + src;
+    g.b_hi = p->maps + (fwd ? 8 : 10);
+    g.b_lo = p->maps + (fwd ? 9 : 11);
+    g.out_hi = (dst >= 0) ? p->bufs_hi[dst] : nullptr;
+    g.out_lo = (dst >= 0) ? p->bufs_lo[dst] : nullptr;
+    g.U = e.U;
+    g.lam32 = e.lam32;
+    g.shift = e.shift;
+    g.done = e.done;
+    g.dscale = 1.0f;
+    g.step = (float)e.step;
+    g.Mtot = p->Mtot;
+    g.P = p->P;
+    g.n = p->n;
+    g.BN = fwd ? p->BN1 : p->BN2;
+    g.ntile_n = fwd ? p->P / p->BN1 : (p->P / 2) / p->BN2;
+    g.ntiles = g.ntile_n * (p->Mtot / BM);
+    const int grid = g.ntiles < p->num_sms ? g.ntiles : p->num_sms;
+    switch (epi) {
+        case EPI_STORE_BFLY:
+            return launch_t<64, EPI_STORE_BFLY, 3, 1>(g, nullptr, nullptr, g.ntiles, p->stages, e.err, grid, s);
+        case EPI_DIVIDE:
+            return launch_t<64, EPI_DIVIDE, 3, 1>(g, nullptr, nullptr, g.ntiles, p->stages, e.err, grid, s);
+        case EPI_STORE_PQ:
+            return launch_t<64, EPI_STORE_PQ, 3, 2>(g, nullptr, nullptr, g.ntiles, p->stages, e.err, grid, s);
+        default:
+            return launch_t<64, EPI_UPDATE_PQ, 3, 2>(g, nullptr, nullptr, g.ntiles, p->stages, e.err, grid, s);
+    }
 }
 
 int launch_modeprod_tc(TcPlan *p, int src, int dst, bool forward, Epi epi, const EpiArgs &e, cudaStream_t s) {

@@ -229,27 +229,53 @@ __device__ unsigned long long block_max_u64(unsigned long long v) {
 
 // Iteration 0 of a 3-D split solve, one pass over f and U_0: the padded
 // FP32-pair copy of f (zeros in the padding), per-block sums of f^2 (FP64),
-// the |f| range check and the max|U_0| bit pattern.
+// the |f| range check and the max|U_0| bit pattern. MIRROR: the copy is laid
+// out for k_residual_mirror, entry (z, y, i < P/2) = (f(i), f(n-1-i)) as two
+// FP32 pairs (the second zero where n-1-i <= i); else (z, y, x) = f(x).
+template <bool MIRROR>
 __global__ void __launch_bounds__(256) k_prep_split(const double *__restrict__ U, const double *__restrict__ f,
                                                     int n, int P, float2 *__restrict__ fdf,
                                                     double *__restrict__ partials, DevState *st) {
     const long long rows = (long long)P * P;
+    const int H = P / 2, nsym = (n + 1) / 2, nanti = n / 2;
     double f2 = 0.0;
     unsigned long long umax = 0ull;
     for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
         const int y = (int)(row % P), z = (int)(row / P);
         const bool row_ok = (y < n) && (z < n);
         const long long cbase = ((long long)z * n + y) * n;
-        for (int x = threadIdx.x; x < P; x += blockDim.x) {
-            float2 fp = make_float2(0.0f, 0.0f);
-            if (row_ok && x < n) {
-                const double fv = __ldg(f + cbase + x);
-                f2 = fma(fv, fv, f2);
-                fp = f_pair(fv, &st->fx_fbad);
-                const unsigned long long ab = abs_bits(__ldg(U + cbase + x));
-                umax = ab > umax ? ab : umax;
+        if (MIRROR) {
+            float4 *f4 = reinterpret_cast<float4 *>(fdf);
+            for (int i = threadIdx.x; i < H; i += blockDim.x) {
+                float2 a = make_float2(0.0f, 0.0f), b = a;
+                if (row_ok && i < nsym) {
+                    const double fv = __ldg(f + cbase + i);
+                    f2 = fma(fv, fv, f2);
+                    a = f_pair(fv, &st->fx_fbad);
+                    const unsigned long long ab = abs_bits(__ldg(U + cbase + i));
+                    umax = ab > umax ? ab : umax;
+                }
+                if (row_ok && i < nanti) {
+                    const double fv = __ldg(f + cbase + (n - 1 - i));
+                    f2 = fma(fv, fv, f2);
+                    b = f_pair(fv, &st->fx_fbad);
+                    const unsigned long long ab = abs_bits(__ldg(U + cbase + (n - 1 - i)));
+                    umax = ab > umax ? ab : umax;
+                }
+                f4[row * H + i] = make_float4(a.x, a.y, b.x, b.y);
             }
-            fdf[row * P + x] = fp;
+        } else {
+            for (int x = threadIdx.x; x < P; x += blockDim.x) {
+                float2 fp = make_float2(0.0f, 0.0f);
+                if (row_ok && x < n) {
+                    const double fv = __ldg(f + cbase + x);
+                    f2 = fma(fv, fv, f2);
+                    fp = f_pair(fv, &st->fx_fbad);
+                    const unsigned long long ab = abs_bits(__ldg(U + cbase + x));
+                    umax = ab > umax ? ab : umax;
+                }
+                fdf[row * P + x] = fp;
+            }
         }
     }
     const unsigned long long bm = block_max_u64(umax);
@@ -727,6 +753,253 @@ __global__ void __launch_bounds__(kTThreads, 2) k_residual_tiled(ResidualArgs a,
     }
 }
 
+// ---------------------------------------------------------------------------
+// k_residual_mirror: k_residual_tiled for the reflection-split mode products.
+//
+// The inverse then contracts every axis through the reflection symmetry of the
+// sine basis, S[n-1-j][k] = (-1)^k S[j][k]: the forward products take the
+// sums a_j = r_j + r_{n-1-j} and differences b_j = r_j - r_{n-1-j} (j < n/2,
+// the middle point of an odd n joining the sums), so this kernel writes the
+// residual with
+//   x   in split order: a_j at position j, b_j at position P/2 + j (zeros in
+//       the padding of either half),
+//   y,z in folded order: y < ceil(n/2) at row 2y, y >= ceil(n/2) at row
+//       2(n-1-y)+1 (rows >= n are padding), so that the products' epilogues
+//       find reflection partners in adjacent TMEM lanes.
+// Same arithmetic as k_residual_tiled (fixed-point stencil with exponent E,
+// float-pair nonlinear term, exact per-point path for flagged planes); the
+// tile is two mirrored strips: lane l of a warp owns x = X0 + l (left strip)
+// and its mirror n-1-X0-l (right strip), so both members of each pair are in
+// one thread's registers. Shared rows hold the left strip (x = X0-1..X0+32 at
+// columns 0..33) and the right strip in lane order (l' = -1..32 at columns
+// 34..67, x = n-1-X0-l'). f is read as float pairs of the two strips
+// (f_hi(x), f_lo(x), f_hi(x'), f_lo(x')) written by k_prep_split.
+// ---------------------------------------------------------------------------
+constexpr int kMHaloPerWarp = (4 * 32 + 4 * kTY) / 8;   // 192 halo values, 24 per warp
+
+__device__ __forceinline__ int fold_index(int i, int n, int nsym) {
+    return (i >= n) ? i : (i < nsym ? 2 * i : 2 * (n - 1 - i) + 1);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kTThreads, 2) k_residual_mirror(ResidualArgs a, int zchunk) {
+    if (a.done != nullptr && *(volatile const int *)a.done) return;
+    __shared__ __align__(16) long long spl[2][kSRows * kSRow];
+    const int n = a.n, P = a.P, H = a.P / 2;
+    const int nsym = (n + 1) / 2, nanti = n / 2;
+    const int E = *a.fx_e;
+    const bool fx_ok = (E != 0);
+    const float scale = __int_as_float(fx_ok ? ((E - 1075 - kFxG + 127) << 23) : 0);
+    const float ih = __double2float_rn(a.inv_h2);
+    const float il = __double2float_rn(a.inv_h2 - (double)ih);
+    float bh = 1.0f, bl = 0.0f, lh = 0.0f, ll = 0.0f;
+    if (KIND != 2) {
+        bh = __double2float_rn(a.b);
+        bl = __double2float_rn(a.b - (double)bh);
+    }
+    if (KIND == 0) {
+        lh = __double2float_rn(a.lam);
+        ll = __double2float_rn(a.lam - (double)lh);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tiles_x = H / 32, tiles_y = P / kTY;
+    const int nzc = (P + zchunk - 1) / zchunk;
+    const long long items = (long long)tiles_x * tiles_y * nzc;
+    const long long nn = (long long)n * n;
+    const unsigned long long *Ub = reinterpret_cast<const unsigned long long *>(a.U);
+    const float4 *fdf4 = reinterpret_cast<const float4 *>(a.fdf);
+    const int r0s = (2 * warp + 1) * kSRow, r1s = r0s + kSRow;   // shared rows of the own points
+    const bool hlane = lane < kMHaloPerWarp;
+    const int hidx = warp * kMHaloPerWarp + lane;
+    float kr2 = 0.0f, kc = 0.0f;
+    unsigned long long amin = 0x7FFFFFFFFFFFFFFFull, amax = 0ull;
+    const int r2k = *a.r2_exp;
+    const float r2s = __int_as_float((127 - r2k) << 23);   // 2^-r2k
+
+    for (long long item = blockIdx.x; item < items; item += gridDim.x) {
+        const int tx = (int)(item % tiles_x);
+        const long long q = item / tiles_x;
+        const int ty = (int)(q % tiles_y);
+        const int z0 = (int)(q / tiles_y) * zchunk;
+        const int z1 = min(z0 + zchunk, P);
+        const int X0 = tx * 32, Y0 = ty * kTY;
+        const int xL = X0 + lane, xR = n - 1 - X0 - lane;
+        const int y0 = Y0 + 2 * warp, y1 = y0 + 1;
+        const int Fy0 = fold_index(y0, n, nsym), Fy1 = fold_index(y1, n, nsym);
+        // zero planes of the padding (z >= n), both halves of both rows
+        for (int z = max(z0, n); z < z1; ++z) {
+            const long long o0 = ((long long)z * P + Fy0) * P, o1 = ((long long)z * P + Fy1) * P;
+            const __nv_bfloat16 zb = __float2bfloat16_rn(0.0f);
+            a.Rhi[o0 + xL] = zb;
+            a.Rlo[o0 + xL] = zb;
+            a.Rhi[o0 + H + xL] = zb;
+            a.Rlo[o0 + H + xL] = zb;
+            a.Rhi[o1 + xL] = zb;
+            a.Rlo[o1 + xL] = zb;
+            a.Rhi[o1 + H + xL] = zb;
+            a.Rlo[o1 + H + xL] = zb;
+        }
+        const int zl = min(z1, n);
+        if (z0 >= zl) continue;   // block-uniform
+
+        // present: the value exists on the grid (else Dirichlet 0); own: this
+        // thread evaluates the point (left: x <= middle; right: x > middle)
+        const bool pL = xL < n, pR = xR >= 0, py0 = y0 < n, py1 = y1 < n;
+        const bool oL = xL < nsym, oR = xL < nanti;
+        const bool v0 = oL && py0, v1 = oR && py0, v2 = oL && py1, v3 = oR && py1;   // own points
+        int hx, hy, hslot;
+        {
+            const int h = hidx;
+            if (h < 128) {
+                const int rr = (h < 64) ? 0 : (kTY + 1);
+                const int g = h & 63;
+                hy = (h < 64) ? Y0 - 1 : Y0 + kTY;
+                if (g < 32) {
+                    hx = X0 + g;
+                    hslot = rr * kSRow + 1 + g;
+                } else {
+                    hx = n - 1 - X0 - (g - 32);
+                    hslot = rr * kSRow + 35 + (g - 32);
+                }
+            } else {
+                const int g = h - 128;
+                const int rr = 1 + (g >> 2);
+                hy = Y0 + rr - 1;
+                const int w = g & 3;
+                hx = (w == 0) ? X0 - 1 : (w == 1) ? X0 + 32 : (w == 2) ? n - X0 : n - 1 - X0 - 32;
+                hslot = rr * kSRow + ((w == 0) ? 0 : (w == 1) ? 33 : (w == 2) ? 34 : 67);
+            }
+        }
+        const bool hval = hlane && hx >= 0 && hx < n && hy >= 0 && hy < n;
+        const long long hoff = hval ? (long long)hy * n + hx : 0;
+
+        unsigned long long R[4], RH;
+        auto load_plane = [&](int z) {
+            const bool zin = z >= 0 && z < n;
+            const unsigned long long *p = Ub + (long long)(zin ? z : 0) * nn;
+            R[0] = (zin && pL && py0) ? __ldg(p + (long long)y0 * n + xL) : 0ull;
+            R[1] = (zin && pR && py0) ? __ldg(p + (long long)y0 * n + xR) : 0ull;
+            R[2] = (zin && pL && py1) ? __ldg(p + (long long)y1 * n + xL) : 0ull;
+            R[3] = (zin && pR && py1) ? __ldg(p + (long long)y1 * n + xR) : 0ull;
+            RH = (zin && hval) ? __ldg(p + hoff) : 0ull;
+        };
+        auto minmax_own = [&]() {
+            minmax_bits(R[0], v0, amin, amax);
+            minmax_bits(R[1], v1, amin, amax);
+            minmax_bits(R[2], v2, amin, amax);
+            minmax_bits(R[3], v3, amin, amax);
+        };
+        auto f_at = [&](int z, int y) -> float4 {
+            return __ldg(fdf4 + (((long long)z * P + y) * H + xL));
+        };
+        auto store_plane = [&](long long *S, const long long (&F)[4], long long Hv) {
+            S[r0s + 1 + lane] = F[0];
+            S[r0s + 35 + lane] = F[1];
+            S[r1s + 1 + lane] = F[2];
+            S[r1s + 35 + lane] = F[3];
+            if (hlane) S[hslot] = Hv;
+        };
+
+        long long Fm[4], Fc[4], Fp[4];
+        unsigned bm = 0, bc = 0, bh0 = 0;
+        load_plane(z0 - 1);
+        for (int i = 0; i < 4; ++i) Fm[i] = fx_of(R[i], E, bm);
+        load_plane(z0);
+        minmax_own();
+        for (int i = 0; i < 4; ++i) Fc[i] = fx_of(R[i], E, bc);
+        store_plane(spl[z0 & 1], Fc, fx_of(RH, E, bh0));
+        load_plane(z0 + 1);
+        float4 fa = f_at(z0, y0), fb = f_at(z0, y1);
+        int blk = __syncthreads_or((int)(bc | bh0));
+
+        for (int z = z0; z < zl; ++z) {
+            unsigned bp = 0, bhp = 0;
+            for (int i = 0; i < 4; ++i) Fp[i] = fx_of(R[i], E, bp);
+            const long long Hp = fx_of(RH, E, bhp);
+            if (z + 1 < zl) minmax_own();
+            store_plane(spl[(z + 1) & 1], Fp, Hp);
+            load_plane(z + 2);
+            float4 fa_n = make_float4(0.f, 0.f, 0.f, 0.f), fb_n = fa_n;
+            if (z + 1 < zl) {
+                fa_n = f_at(z + 1, y0);
+                fb_n = f_at(z + 1, y1);
+            }
+
+            float rf[4];
+            if (fx_ok && !(blk | bm | bp)) {
+                const long long *S = spl[z & 1];
+                typedef unsigned long long u64;
+                const u64 c0 = Fc[0], c1 = Fc[1], c2 = Fc[2], c3 = Fc[3];
+                // left (x: cols l, l+2) and right (x-1: col 36+l, x+1: col 34+l) neighbours,
+                // y-1 / y+1 from the rows above / below (own rows pair up)
+                const u64 sl0 = (u64)S[r0s + lane] + (u64)S[r0s + lane + 2];
+                const u64 sr0 = (u64)S[r0s + 36 + lane] + (u64)S[r0s + 34 + lane];
+                const u64 sl1 = (u64)S[r1s + lane] + (u64)S[r1s + lane + 2];
+                const u64 sr1 = (u64)S[r1s + 36 + lane] + (u64)S[r1s + 34 + lane];
+                const u64 uL = (u64)S[r0s - kSRow + 1 + lane], uR = (u64)S[r0s - kSRow + 35 + lane];
+                const u64 dL = (u64)S[r1s + kSRow + 1 + lane], dR = (u64)S[r1s + kSRow + 35 + lane];
+                const long long lap0 = (long long)(6ull * c0 - ((sl0 + (uL + c2)) + ((u64)Fm[0] + (u64)Fp[0])));
+                const long long lap1 = (long long)(6ull * c1 - ((sr0 + (uR + c3)) + ((u64)Fm[1] + (u64)Fp[1])));
+                const long long lap2 = (long long)(6ull * c2 - ((sl1 + (c0 + dL)) + ((u64)Fm[2] + (u64)Fp[2])));
+                const long long lap3 = (long long)(6ull * c3 - ((sr1 + (c1 + dR)) + ((u64)Fm[3] + (u64)Fp[3])));
+                rf[0] = residual_pair<KIND>(Fc[0], lap0, fa.x, fa.y, scale, ih, il, bh, bl, lh, ll);
+                rf[1] = residual_pair<KIND>(Fc[1], lap1, fa.z, fa.w, scale, ih, il, bh, bl, lh, ll);
+                rf[2] = residual_pair<KIND>(Fc[2], lap2, fb.x, fb.y, scale, ih, il, bh, bl, lh, ll);
+                rf[3] = residual_pair<KIND>(Fc[3], lap3, fb.z, fb.w, scale, ih, il, bh, bl, lh, ll);
+            } else {
+                rf[0] = v0 ? residual_point_exact(a.U, a.f, n, xL, y0, z, a.inv_h2, a.lam, a.b) : 0.0f;
+                rf[1] = v1 ? residual_point_exact(a.U, a.f, n, xR, y0, z, a.inv_h2, a.lam, a.b) : 0.0f;
+                rf[2] = v2 ? residual_point_exact(a.U, a.f, n, xL, y1, z, a.inv_h2, a.lam, a.b) : 0.0f;
+                rf[3] = v3 ? residual_point_exact(a.U, a.f, n, xR, y1, z, a.inv_h2, a.lam, a.b) : 0.0f;
+            }
+            rf[0] = v0 ? rf[0] : 0.0f;
+            rf[1] = v1 ? rf[1] : 0.0f;
+            rf[2] = v2 ? rf[2] : 0.0f;
+            rf[3] = v3 ? rf[3] : 0.0f;
+            // sum (r 2^-k)^2 (FP32, Kahan over planes)
+            const float q0 = __fmul_rn(rf[0], r2s), q1 = __fmul_rn(rf[1], r2s);
+            const float q2 = __fmul_rn(rf[2], r2s), q3 = __fmul_rn(rf[3], r2s);
+            const float sq = __fadd_rn(__fmaf_rn(q0, q0, __fmul_rn(q1, q1)), __fmaf_rn(q2, q2, __fmul_rn(q3, q3)));
+            const float yk = __fsub_rn(sq, kc);
+            const float tk = __fadd_rn(kr2, yk);
+            kc = __fsub_rn(__fsub_rn(tk, kr2), yk);
+            kr2 = tk;
+            // split-order output: sums at x, differences at P/2 + x, folded rows and plane
+            const int Fz = fold_index(z, n, nsym);
+            const long long o0 = ((long long)Fz * P + Fy0) * P, o1 = ((long long)Fz * P + Fy1) * P;
+            // (rf of a point this thread does not own is 0; the middle point of an
+            // odd n has no difference: its slot P/2 + n/2 stays 0)
+            split_bf16(__fadd_rn(rf[0], rf[1]), a.Rhi[o0 + xL], a.Rlo[o0 + xL]);
+            split_bf16(v1 ? __fsub_rn(rf[0], rf[1]) : 0.0f, a.Rhi[o0 + H + xL], a.Rlo[o0 + H + xL]);
+            split_bf16(__fadd_rn(rf[2], rf[3]), a.Rhi[o1 + xL], a.Rlo[o1 + xL]);
+            split_bf16(v3 ? __fsub_rn(rf[2], rf[3]) : 0.0f, a.Rhi[o1 + H + xL], a.Rlo[o1 + H + xL]);
+
+            blk = __syncthreads_or((int)(bp | bhp));
+            for (int i = 0; i < 4; ++i) {
+                Fm[i] = Fc[i];
+                Fc[i] = Fp[i];
+            }
+            bm = bc;
+            bc = bp;
+            fa = fa_n;
+            fb = fb_n;
+        }
+    }
+
+    const double umin = __longlong_as_double((long long)amin);
+    const double umax = __longlong_as_double((long long)amax);
+    Red4 acc{ldexp((double)kr2 - (double)kc, 2 * r2k), 0.0,
+             (amin == 0x7FFFFFFFFFFFFFFFull) ? INFINITY : umin * umin, umax * umax};
+    acc = block_reduce(acc);
+    if (threadIdx.x == 0) {
+        double *p = a.partials + 4ll * blockIdx.x;
+        p[0] = acc.r2;
+        p[1] = acc.f2;
+        p[2] = acc.mn;
+        p[3] = acc.mx;
+    }
+}
+
 // Dense FP64 field -> FP32 -> BF16 hi/lo planes on the zero-padded P^dim grid.
 template <int DIM>
 __global__ void __launch_bounds__(256) k_split_pad(const double *__restrict__ r, int n, int P,
@@ -833,6 +1106,46 @@ static int launch_tiled_kind(const ResidualArgs &a, int max_grid, int zchunk, in
     return QN_OK;
 }
 
+template <int KIND>
+static int mirror_blocks_per_sm() {
+    static int cached = 0;
+    if (cached == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_residual_mirror<KIND>, kTThreads, 0) != cudaSuccess ||
+            nb < 1)
+            nb = 1;
+        cached = nb;
+    }
+    return cached;
+}
+
+template <int KIND>
+static int launch_mirror_kind(const ResidualArgs &a, int max_grid, int zchunk, int *grid_used, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    QN_CUDA(cudaGetDevice(&dev));
+    QN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long items = (long long)(a.P / 64) * (a.P / kTY) * ((a.P + zchunk - 1) / zchunk);
+    long long g = (long long)mirror_blocks_per_sm<KIND>() * sms;
+    if (g > max_grid) g = max_grid;
+    if (g > items) g = items;
+    if (g < 1) g = 1;
+    k_residual_mirror<KIND><<<(int)g, kTThreads, 0, s>>>(a, zchunk);
+    QN_CUDA(cudaGetLastError());
+    *grid_used = (int)g;
+    return QN_OK;
+}
+
+int launch_residual_mirror(const ResidualArgs &a, int max_grid, int zchunk, int *grid_used, cudaStream_t s) {
+    if (a.dim != 3 || a.Rhi == nullptr || a.fdf == nullptr || a.fx_e == nullptr || a.P % 128 != 0 ||
+        zchunk < 1) {
+        set_error("launch_residual_mirror: needs a 3-D split residual, P a multiple of 128, the f copy");
+        return QN_EINVAL;
+    }
+    if (a.lam != 0.0) return launch_mirror_kind<0>(a, max_grid, zchunk, grid_used, s);
+    if (a.b != 1.0) return launch_mirror_kind<1>(a, max_grid, zchunk, grid_used, s);
+    return launch_mirror_kind<2>(a, max_grid, zchunk, grid_used, s);
+}
+
 int launch_residual_tiled(const ResidualArgs &a, int max_grid, int zchunk, int *grid_used, cudaStream_t s) {
     if (a.dim != 3 || a.Rhi == nullptr || a.fdf == nullptr || a.fx_e == nullptr || a.P % kTX != 0 ||
         zchunk < 1) {
@@ -845,8 +1158,11 @@ int launch_residual_tiled(const ResidualArgs &a, int max_grid, int zchunk, int *
 }
 
 int launch_prep_split(const double *U, const double *f, int n, int P, float2 *fdf, double *partials,
-                      int nparts, DevState *st, cudaStream_t s) {
-    k_prep_split<<<nparts, 256, 0, s>>>(U, f, n, P, fdf, partials, st);
+                      int nparts, DevState *st, bool mirror, cudaStream_t s) {
+    if (mirror)
+        k_prep_split<true><<<nparts, 256, 0, s>>>(U, f, n, P, fdf, partials, st);
+    else
+        k_prep_split<false><<<nparts, 256, 0, s>>>(U, f, n, P, fdf, partials, st);
     QN_CUDA(cudaGetLastError());
     k_prep_split_finish<<<1, 256, 0, s>>>(partials, nparts, st);
     QN_CUDA(cudaGetLastError());

@@ -343,7 +343,9 @@ def test_tiled_residual_general_coefficients(qn, lam, b):
 
 def test_tiled_residual_agrees_with_per_point_residual(qn, monkeypatch):
     """Same solve with the per-point residual kernel throughout (QN_RES_TILED=0):
-    same iteration count, solutions equal to the solver tolerance."""
+    same iteration count, solutions equal to the solver tolerance. Both runs use
+    the dense mode products (QN_SPLIT=0), so only the residual kernels differ."""
+    monkeypatch.setenv("QN_SPLIT", "0")
     n = 65
     u, f = manufactured_problem(n, 3, seed=1)
     res_t, hist_t, Ut, prof_t = _solve_3d_bf16x3(qn, n, f)
@@ -422,8 +424,9 @@ def test_tiled_path_iterates_match_per_point_path(qn, monkeypatch, max_it):
     FP32-pair copy of f and ||f|| in one pass, iteration 1 scans max|U_1| for
     the fixed-point exponent. Stopped after max_it iterations, U must equal the
     iterate of the per-point residual path (QN_RES_TILED=0) to the FP32
-    rounding of the residual."""
+    rounding of the residual (dense mode products in both runs)."""
     import torch
+    monkeypatch.setenv("QN_SPLIT", "0")
     n = 45
     u, f = manufactured_problem(n, 3, seed=8)
     outs = []
@@ -451,3 +454,21 @@ def test_split_solve_damped_step(qn, step):
     Ug = host(U).reshape(f.shape)
     assert np.linalg.norm(O.residual(Ug, f)) / np.linalg.norm(f) <= 1.05e-10
     assert np.abs(Ug - Uo).max() <= 1e-9 * np.abs(Uo).max()
+
+
+@pytest.mark.parametrize("n", [65, 127, 200])
+def test_reflection_split_products_match_dense(qn, monkeypatch, n):
+    """The reflection-split mode products (sums / differences of mirror points,
+    even / odd modes; P a multiple of 128) against the dense products: same
+    iteration count within 1, both solutions at the oracle's to 1e-9."""
+    import torch
+    u, f = manufactured_problem(n, 3, seed=11)
+    Uo, ho, ok = O.qn_solve(f, tol=1e-10)
+    assert ok
+    outs = []
+    for split in ("1", "0"):
+        monkeypatch.setenv("QN_SPLIT", split)
+        res, hist, Ug, prof = _solve_3d_bf16x3(qn, n, f)
+        _check_solution(res, Ug, Uo, f, ho)
+        outs.append(res["iterations"])
+    assert abs(outs[0] - outs[1]) <= 1
