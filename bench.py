@@ -326,10 +326,18 @@ def main():
 
     # ---- roofline of the dominant kernel (mode product) and of the residual kernel
     P = ((n + 63) // 64) * 64
+    split = bool(prof.get("split_products", 0))
     mp_avg_ms = prof["modeprod_ms"] / max(prof["modeprod_launches"], 1)
-    alg_flops = 2.0 * float(n) ** 4                      # one mode product: 2 N n, N = n^3
-    exec_flops = (3 if a.precision == "bf16x3" else 1) * 2.0 * float(P) ** 4
+    st_avg_ms = prof["mp_store_ms"] / max(prof["mp_store_launches"], 1)
+    # one mode product of an n^3 tensor: 2 n^4 flops as a dense contraction; the
+    # reflection-split form does half (two contractions of length n/2): n^4
+    alg_flops = (1.0 if split else 2.0) * float(n) ** 4
+    # executed on the tensor cores: 3 BF16 products over the padded grid
+    exec_flops = (3 if a.precision == "bf16x3" else 1) * (1.0 if split else 2.0) * float(P) ** 4
+    # HBM bytes of a store launch: the hi/lo planes read (4 B) and written (4 B) per padded point
+    st_bytes = 8.0 * float(P) ** 3
     mp_tflops = alg_flops / (mp_avg_ms * 1e-3) / 1e12
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
     if a.precision == "bf16x3":
         peak = float(peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))
         peak_name = f"bf16 dense, sustained ({peak_src})"
@@ -338,16 +346,24 @@ def main():
         peak_name = "fp64 (see plain_fp64.fp64_peak)"
     kernel_file = os.path.join(ROOT, "paper_2502_03611_gb300", "csrc",
                                "qn_modeprod_tc.cu" if a.precision == "bf16x3" else "qn_modeprod_f64.cu")
-    roofline = {"kernel": "k_modeprod_tc" if a.precision == "bf16x3" else "k_modeprod_f64",
-                "bound": "tensor", "achieved": round(mp_tflops, 2), "peak": peak, "unit": "TFLOP/s",
-                "frac": round(mp_tflops / peak, 4) if peak else None,
-                "traffic": ncu_traffic(kernel_file) if a.precision == "bf16x3" else None,
-                "peak_source": peak_name,
-                "flops_per_launch_algorithmic": alg_flops,
-                "flops_per_launch_executed": exec_flops,
-                "executed_tflops": round(exec_flops / (mp_avg_ms * 1e-3) / 1e12, 2),
-                "executed_frac": round(exec_flops / (mp_avg_ms * 1e-3) / 1e12 / peak, 4) if peak else None,
-                "avg_launch_ms": round(mp_avg_ms, 4), "launches": prof["modeprod_launches"]}
+    traffic = ncu_traffic(kernel_file) if a.precision == "bf16x3" else None
+    tensor_roofline = {"kernel": "k_modeprod_tc" if a.precision == "bf16x3" else "k_modeprod_f64",
+                       "bound": "tensor", "achieved": round(mp_tflops, 2), "peak": peak, "unit": "TFLOP/s",
+                       "frac": round(mp_tflops / peak, 4) if peak else None,
+                       "peak_source": peak_name, "split_products": split,
+                       "flops_per_launch_algorithmic": alg_flops,
+                       "flops_per_launch_executed": exec_flops,
+                       "executed_tflops": round(exec_flops / (mp_avg_ms * 1e-3) / 1e12, 2),
+                       "executed_frac": round(exec_flops / (mp_avg_ms * 1e-3) / 1e12 / peak, 4) if peak else None,
+                       "avg_launch_ms": round(mp_avg_ms, 4), "launches": prof["modeprod_launches"]}
+    st_gbs = st_bytes / (st_avg_ms * 1e-3) / 1e9
+    hbm_roofline = {"kernel": "k_modeprod_tc (store launches)", "bound": "hbm", "achieved": round(st_gbs, 1),
+                    "peak": hbm, "unit": "GB/s", "frac": round(st_gbs / hbm, 4), "traffic": traffic,
+                    "peak_source": f"HBM copy bandwidth ({peak_src})",
+                    "bytes_per_launch_algorithmic": st_bytes, "avg_launch_ms": round(st_avg_ms, 4),
+                    "launches": prof["mp_store_launches"]}
+    # split products are bound by HBM (half the tensor work, the same bytes); dense ones by the tensor pipe
+    roofline = hbm_roofline if split else dict(tensor_roofline, traffic=traffic)
     res_avg_ms = prof["residual_ms"] / max(prof["residual_launches"], 1)
     split = a.precision == "bf16x3"
     # algorithmic bytes per residual launch: U 8 + f 8 read per unknown, the
@@ -385,6 +401,7 @@ def main():
         kernels["modeprod"]["share"] = round(prof["modeprod_ms"] / tot, 4)
         kernels["finalize"]["share"] = round(prof["finalize_ms"] / tot, 4)
     kernels["modeprod"]["roofline"] = roofline
+    kernels["modeprod"]["tensor"] = tensor_roofline
     # the JSON line's roofline is that of the kernel with the largest time share
     if prof["residual_ms"] > prof["modeprod_ms"]:
         roofline = {"kernel": "k_residual_tiled" if til_n else "k_residual", "bound": "hbm",

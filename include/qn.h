@@ -324,6 +324,9 @@ typedef struct qn_profile {
     int residual_tiled_launches;   /* of residual_launches: the residuals of a 3-D split solve
                                       from its third iteration on (no FP64 arithmetic) */
     double residual_tiled_ms;
+    int split_products;       /* 1: the last shifted inverse used the reflection-split mode
+                                 products (3-D split solve, n+ padding a multiple of 128):
+                                 half the tensor work of the dense products */
 } qn_profile;
 
 /* on != 0: from now on record a pair of CUDA events around every kernel

@@ -87,6 +87,7 @@ struct qn_ctx {
     // reflection-split mode products (3-D split solve, P a multiple of 128)
     int split;            // 1: the plan holds the split matrices and the solve loop uses them
     int split_layout;     // 1: the last residual wrote its planes in split / folded order
+    int last_split;       // 1: the last shifted inverse used the split products
     __nv_bfloat16 *bf_hi, *bf_lo, *bb_hi, *bb_lo;   // [P][P/2] forward / backward matrices
     float *lam32_split;   // eigenvalues in split mode order (even modes, then odd), 1e30 padding
 };
@@ -520,6 +521,7 @@ static int enqueue_inverse(qn_ctx *c, const double *r0, double *target, bool upd
                            cudaStream_t s, bool split = false) {
     const int d = c->dim;
     EpiArgs e = epi_args(c, target, step);
+    c->last_split = (split && update) ? 1 : 0;
     if (split && update) {
         // reflection-split products on the split / folded planes of the residual
         e.lam32 = c->lam32_split;
@@ -814,6 +816,7 @@ extern "C" int qn_profile_read(qn_ctx *c, qn_profile *out) {
     out->residual_ms = ms[PK_RESIDUAL] + ms[PK_RESIDUAL_TILED];
     out->residual_tiled_launches = cnt[PK_RESIDUAL_TILED];
     out->residual_tiled_ms = ms[PK_RESIDUAL_TILED];
+    out->split_products = c->last_split;
     out->finalize_launches = cnt[PK_FINALIZE];
     out->finalize_ms = ms[PK_FINALIZE];
     out->modeprod_launches = cnt[PK_MP_STORE] + cnt[PK_MP_DIVIDE] + cnt[PK_MP_LAST];

@@ -590,8 +590,23 @@ int tc_plan_enable_split(TcPlan *p, const __nv_bfloat16 *bf_hi, const __nv_bfloa
                          const __nv_bfloat16 *bb_hi, const __nv_bfloat16 *bb_lo) {
     const int H = p->P / 2;
     if (p->dim != 3 || p->BK != 64 || p->P % 128 != 0) return QN_EUNSUPPORTED;
-    p->BN1 = H < BN_MAX ? H : BN_MAX;   // forward tiles must not straddle the halves
-    p->BN2 = H < 128 ? H : 128;         // backward: two accumulators of BN2 columns per tile
+    // tile widths must divide H (a forward tile stays inside one half; the
+    // backward tiles cover the H rows exactly) and give every epilogue warp a
+    // whole number of TMEM chunks: BN1/kEpiParts a multiple of kChunk (16),
+    // BN2/kEpiParts a multiple of 8; BN2 <= 128 (two accumulators per tile)
+    p->BN1 = 0;
+    for (int bn = BN_MAX; bn >= 16 * kEpiParts; bn -= 16 * kEpiParts)
+        if (H % bn == 0) {
+            p->BN1 = bn;
+            break;
+        }
+    p->BN2 = 0;
+    for (int bn = 128; bn >= 8 * kEpiParts; bn -= 8 * kEpiParts)
+        if (H % bn == 0) {
+            p->BN2 = bn;
+            break;
+        }
+    if (p->BN1 == 0 || p->BN2 == 0) return QN_EUNSUPPORTED;
     CUtensorMap h[4];
     int rc = tc_encode_2d(&h[0], bf_hi, H, p->P, p->BK, p->BN1, p->BK);
     if (rc == QN_OK) rc = tc_encode_2d(&h[1], bf_lo, H, p->P, p->BK, p->BN1, p->BK);

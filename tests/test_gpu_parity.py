@@ -472,3 +472,22 @@ def test_reflection_split_products_match_dense(qn, monkeypatch, n):
         _check_solution(res, Ug, Uo, f, ho)
         outs.append(res["iterations"])
     assert abs(outs[0] - outs[1]) <= 1
+
+
+def test_reflection_split_products_p384(qn, monkeypatch):
+    """P = 384 (H = 192): the split tiles are 192 (forward) and 96 (backward)
+    wide. Judged by the oracle's residual of the GPU solution and agreement
+    with the dense products (the oracle's own solve at 330^3 is slow)."""
+    import torch
+    n = 330
+    u, f = manufactured_problem(n, 3, seed=12)
+    sols = []
+    for split in ("1", "0"):
+        monkeypatch.setenv("QN_SPLIT", split)
+        res, hist, Ug, prof = _solve_3d_bf16x3(qn, n, f, max_it=60)
+        assert res["status"] == 0 and res["rel"] <= 1e-10
+        assert prof["split_products"] == (1 if split == "1" else 0)
+        sols.append(Ug)
+    rel = np.linalg.norm(O.residual(sols[0], f)) / np.linalg.norm(f)
+    assert rel <= 1.05e-10, rel
+    assert np.abs(sols[0] - sols[1]).max() <= 1e-9 * np.abs(sols[1]).max()
