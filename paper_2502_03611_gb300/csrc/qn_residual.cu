@@ -80,11 +80,28 @@ static __device__ __noinline__ void flag_fbad(int *flag) {
     if (flag != nullptr) atomicOr(flag, 1);
 }
 
+static __device__ __noinline__ float2 f_pair_slow(double fv) {
+    const float fh = __double2float_rn(fv);
+    return make_float2(fh, __double2float_rn(fv - (double)fh));
+}
+
+// hi = f rounded to FP32, lo = (f - hi) rounded to FP32. The difference is
+// taken exactly on the integer significands (|f| - |hi| has at most 29
+// significant bits), so no FP64 operation is spent; tiny, huge and
+// non-finite f take the FP64 route.
 __device__ __forceinline__ float2 f_pair(double fv, int *flag) {
-    const unsigned int hw = (unsigned int)((unsigned long long)__double_as_longlong(fv) >> 32);
-    if ((int)((hw >> 20) & 0x7FFu) >= 1023 + 100) flag_fbad(flag);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(fv);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (ex >= 1023 + 100) flag_fbad(flag);
+    if (ex < 1075 - 126 || ex >= 1023 + 100) return f_pair_slow(fv);
     const float fh = d2f_rn(fv);
-    return make_float2(fh, d2f_rn(fv - f2d_exact(fh)));
+    const unsigned int fb = __float_as_uint(fh);
+    const int ef = (int)((fb >> 23) & 0xFFu);
+    const long long hu = (long long)((fb & 0x7FFFFFu) | 0x800000u) << (ef - ex + 925);   // 29, or 30 after a carry
+    const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+    float lo = __fmul_rn(__int2float_rn((int)(m - hu)), __int_as_float((ex - 1075 + 127) << 23));
+    if (b >> 63) lo = -lo;
+    return make_float2(fh, lo);
 }
 
 struct ResAcc {
