@@ -352,9 +352,33 @@ __global__ void __maxnreg__(104)
                     }
                 }
             }
-            if (EPI == EPI_STORE_PQ || EPI == EPI_UPDATE_PQ) {
+            if (EPI == EPI_STORE_PQ) {
                 // p in columns [0, BN), q in [BN, 2 BN) of the accumulator; output
                 // rows j (< H) and n-1-j; the middle row of an odd n takes p alone
+                for (int c = cbeg; c < cend; c += kChunk) {
+                    uint32_t rp[kChunk], rq[kChunk];
+                    ptx::tmem_ld_32x32b_x16(tacc + (uint32_t)c, rp);
+                    ptx::tmem_ld_32x32b_x16(tacc + (uint32_t)(BN + c), rq);
+                    ptx::tmem_ld_wait();
+                    if (!m_ok) continue;
+                    const int j0 = n0 + c;
+#pragma unroll
+                    for (int i = 0; i < kChunk; ++i) {
+                        if (c + i >= cend) break;   // BN2/kEpiParts may be 24 (P = 384): half a chunk
+                        const int j = j0 + i;
+                        const float p = __uint_as_float(rp[i]), qv = __uint_as_float(rq[i]);
+                        if (j < nanti) {
+                            split_store(p + qv, G.out_hi, G.out_lo, j * Mtot + m);
+                            split_store(p - qv, G.out_hi, G.out_lo, (n - 1 - j) * Mtot + m);
+                        } else if (j < nsym) {
+                            split_store(p, G.out_hi, G.out_lo, j * Mtot + m);
+                        }
+                    }
+                }
+            }
+            if (EPI == EPI_UPDATE_PQ) {
+                // as EPI_STORE_PQ, the two rows subtracted from U (8 columns at a
+                // time: two FP64 rows of old values per chunk)
                 for (int c = cbeg; c < cend; c += 8) {
                     uint32_t rp[8], rq[8];
                     ptx::tmem_ld_32x32b_x8(tacc + (uint32_t)c, rp);
@@ -362,19 +386,7 @@ __global__ void __maxnreg__(104)
                     ptx::tmem_ld_wait();
                     if (!m_ok) continue;
                     const int j0 = n0 + c;
-                    if (EPI == EPI_STORE_PQ) {
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int j = j0 + i;
-                            const float p = __uint_as_float(rp[i]), qv = __uint_as_float(rq[i]);
-                            if (j < nanti) {
-                                split_store(p + qv, G.out_hi, G.out_lo, j * Mtot + m);
-                                split_store(p - qv, G.out_hi, G.out_lo, (n - 1 - j) * Mtot + m);
-                            } else if (j < nsym) {
-                                split_store(p, G.out_hi, G.out_lo, j * Mtot + m);
-                            }
-                        }
-                    } else if (ubase >= 0) {
+                    if (ubase >= 0) {
                         double *ub = G.U + ubase;
                         double oa[8], ob[8];
 #pragma unroll
