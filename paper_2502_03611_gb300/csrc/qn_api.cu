@@ -10,6 +10,8 @@
 // The finaliser's `done` flag makes every later kernel return at once, so the
 // host may queue several iterations before it checks convergence.
 #include <math.h>
+
+#include <cmath>
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -84,6 +86,8 @@ struct qn_ctx {
     int res_parts;        // partial-sum records written by the last residual launch
     int res_fx_headroom;  // DevState::fx_headroom for the solves of this context
     int res_saved_fnorm;  // 1: the last residual's finaliser takes ||f|| from DevState::f_norm
+    float *warm_dsq;      // device: ||U_1 - U_0||^2 of a warm-started solve's first iteration
+    int warm_dsq_on;      // 1 while that iteration's products are enqueued
     // reflection-split mode products (3-D split solve, P a multiple of 128)
     int split;            // 1: the plan holds the split matrices and the solve loop uses them
     int split_layout;     // 1: the last residual wrote its planes in split / folded order
@@ -187,6 +191,7 @@ static void ctx_free(qn_ctx *c) {
         cudaFree(c->blo[b]);
     }
     cudaFree(c->partials);
+    cudaFree(c->warm_dsq);
     cudaFree(c->fdf);
     cudaFree(c->st);
     cudaFree(c->hist);
@@ -433,6 +438,7 @@ static EpiArgs epi_args(qn_ctx *c, double *U, double step) {
     e.shift = &c->st->shift;
     e.step = step;
     e.U = U;
+    e.dsq = c->warm_dsq_on ? c->warm_dsq : nullptr;
     e.done = &c->st->done;
     e.err = c->err;
     return e;
@@ -681,8 +687,15 @@ extern "C" int qn_step(qn_ctx *c, double *U, const double *f, double beta, qn_st
     return QN_OK;
 }
 
+bool qn::ctx_split_precision(const qn_ctx *c) { return c != nullptr && c->prob.precision == QN_PREC_BF16X3; }
+
 extern "C" int qn_solve(qn_ctx *c, double *U, const double *f, const qn_opts *opts, qn_result *res,
                         qn_stats *history, int history_len, void *stream) {
+    return solve_internal(c, U, f, opts, res, history, history_len, stream, nullptr, nullptr);
+}
+
+int qn::solve_internal(qn_ctx *c, double *U, const double *f, const qn_opts *opts, qn_result *res,
+                       qn_stats *history, int history_len, void *stream, const double *u0_sq, int *used_warm) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (bad_ptr(U) || bad_ptr(f)) {
@@ -717,9 +730,45 @@ extern "C" int qn_solve(qn_ctx *c, double *U, const double *f, const qn_opts *op
     DevState h;
     memset(&h, 0, sizeof(h));
     int enqueued = 0;
-    const size_t first_rec = c->prof_used;
-    const long long launches0 = c->launches;
-    while (enqueued <= o.max_it) {
+    size_t first_rec = c->prof_used;
+    long long launches0 = c->launches;
+    if (u0_sq != nullptr && c->prob.precision == QN_PREC_BF16X3) {
+        // warm start: the first iteration from U_0 also sums ||U_1 - U_0||^2 =
+        // ||step * delta||^2 in its last mode product. delta estimates the
+        // error of U_0: keep going from U_1 if it is below ||U_0|| / 2, else
+        // restart from the zero start
+        if (!c->warm_dsq) QN_CUDA(cudaMalloc(&c->warm_dsq, sizeof(float)));
+        QN_CUDA(cudaMemsetAsync(c->warm_dsq, 0, sizeof(float), s));
+        c->cur_iter = 0;
+        c->warm_dsq_on = 1;
+        rc = enqueue_iteration(c, U, f, o.step, s);
+        c->warm_dsq_on = 0;
+        if (rc) return rc;
+        enqueued = 1;
+        rc = read_state(c, &h, s);
+        if (rc) return rc;
+        float dsq = 0.0f;
+        double u2 = 0.0;
+        QN_CUDA(cudaMemcpy(&dsq, c->warm_dsq, sizeof(float), cudaMemcpyDeviceToHost));
+        QN_CUDA(cudaMemcpy(&u2, u0_sq, sizeof(double), cudaMemcpyDeviceToHost));
+        const bool converged0 = h.done && h.status == QN_OK && h.it == 0;
+        const bool keep = converged0 || (std::isfinite(dsq) && std::isfinite(u2) && u2 > 0.0 &&
+                                         (double)dsq < 0.25 * u2 && !(h.done && h.status != QN_OK));
+        if (used_warm) *used_warm = keep ? 1 : 0;
+        if (!keep) {
+            // restart from U = 0: the launches so far stay in the accounting
+            QN_CUDA(cudaMemsetAsync(U, 0, sizeof(double) * (size_t)c->N, s));
+            rc = reset_state(c, o.tol, o.max_it, o.beta_mode, o.beta_value, s);
+            if (rc) return rc;
+            memset(&h, 0, sizeof(h));
+            enqueued = 0;
+            first_rec = c->prof_used;
+            launches0 = c->launches;
+        }
+    } else if (used_warm) {
+        *used_warm = 0;
+    }
+    while (!h.done && enqueued <= o.max_it) {
         for (int k = 0; k < o.sync_every && enqueued <= o.max_it; ++k, ++enqueued) {
             c->cur_iter = enqueued;
             rc = enqueue_iteration(c, U, f, o.step, s);

@@ -78,6 +78,7 @@ struct EpiArgs {
     const double *shift;      // device pointer to lam + beta_n
     double step;
     double *U;                // EPI_UPDATE / EPI_DENSE target (dense n^dim)
+    float *dsq;               // update epilogues: += sum (step * delta)^2 (nullptr: off)
     const int *done;          // skip when *done != 0
     int *err;                 // device error flag
 };
@@ -124,6 +125,7 @@ struct TcGroup {
     const CUtensorMap *a_hi, *a_lo, *b_hi, *b_lo;   // tensor maps in global memory (64-B aligned)
     __nv_bfloat16 *out_hi, *out_lo;                   // EPI_STORE / EPI_DIVIDE destination planes
     double *U;                                        // EPI_UPDATE / EPI_DENSE target (dense n^dim)
+    float *dsq;                                       // update epilogues: += sum (step * delta)^2 (nullptr: off)
     const float *lam32;                               // padded eigenvalues (P entries, 1e30 past n)
     const double *shift;                              // lam + beta_n of the group's instance
     const int *done;                                  // the instance's stop flag (nullptr: never)
@@ -165,6 +167,15 @@ size_t tc_smem_bytes(int BK, int stages);
 int tc_set_attributes();
 int tc_stages(int BK);
 bool tc_supported(int device);
+
+// qn_solve with an optional check of the first correction (warm-started
+// solves, split precision): with u0_sq (device, ||U_0||^2) non-null, the
+// first iteration also sums ||U_1 - U_0||^2 in its last mode product; if it
+// is not below ||U_0||^2 / 4 (or anything is not finite), U restarts from 0.
+// *used_warm tells which happened. Other arguments as qn_solve.
+int solve_internal(::qn_ctx *c, double *U, const double *f, const qn_opts *opts, qn_result *res,
+                   qn_stats *history, int history_len, void *stream, const double *u0_sq, int *used_warm);
+bool ctx_split_precision(const ::qn_ctx *c);
 
 // error reporting
 void set_error(const char *fmt, ...);

@@ -326,6 +326,7 @@ __global__ void __maxnreg__(104)
             const float step = G.step;
             const int cols = BN / kEpiParts;   // >= 16: BN is 64, 128 or 256
             const int cbeg = part * cols, cend = cbeg + cols;
+            float dsq_acc = 0.0f;   // sum of squared updates (G.dsq)
             const int Hh = P >> 1;
             const int nsym = (n + 1) >> 1, nanti = n >> 1;
             const uint32_t tacc = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN_MAX);
@@ -401,6 +402,8 @@ __global__ void __maxnreg__(104)
                             const int j = j0 + i;
                             const float p = __uint_as_float(rp[i]), qv = __uint_as_float(rq[i]);
                             const float xa = (j < nanti) ? p + qv : p, xb = p - qv;
+                            if (j < nsym) dsq_acc = fmaf(xa, xa, dsq_acc);
+                            if (j < nanti) dsq_acc = fmaf(xb, xb, dsq_acc);
                             if (j < nsym)
                                 ub[j * kstride] = (step == 1.0f) ? oa[i] - f2d_exact(xa) : fma(-st, f2d_exact(xa), oa[i]);
                             if (j < nanti)
@@ -444,6 +447,11 @@ __global__ void __maxnreg__(104)
                         double old[kChunk];
 #pragma unroll
                         for (int i = 0; i < kChunk; ++i) old[i] = (k0 + i < n) ? ub[(k0 + i) * kstride] : 0.0;
+#pragma unroll
+                        for (int i = 0; i < kChunk; ++i) {
+                            const float x = __uint_as_float(r[i]);
+                            if (k0 + i < n) dsq_acc = fmaf(x, x, dsq_acc);
+                        }
                         if (step == 1.0f) {
 #pragma unroll
                             for (int i = 0; i < kChunk; ++i)
@@ -464,6 +472,11 @@ __global__ void __maxnreg__(104)
                             if (k0 + i < n) ub[(k0 + i) * kstride] = f2d_exact(__uint_as_float(r[i]));
                     }
                 }
+            }
+            if ((EPI == EPI_UPDATE || EPI == EPI_UPDATE_PQ) && G.dsq != nullptr) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) dsq_acc += __shfl_xor_sync(0xffffffffu, dsq_acc, o);
+                if (lane == 0) atomicAdd(G.dsq, dsq_acc * step * step);
             }
             ptx::tc_fence_before();
             __syncwarp();
@@ -717,6 +730,7 @@ int launch_modeprod_tc_split(TcPlan *p, int src, int dst, Epi epi, const EpiArgs
     g.out_hi = (dst >= 0) ? p->bufs_hi[dst] : nullptr;
     g.out_lo = (dst >= 0) ? p->bufs_lo[dst] : nullptr;
     g.U = e.U;
+    g.dsq = e.dsq;
     g.lam32 = e.lam32;
     g.shift = e.shift;
     g.done = e.done;
@@ -750,6 +764,7 @@ int launch_modeprod_tc(TcPlan *p, int src, int dst, bool forward, Epi epi, const
     g.out_hi = (dst >= 0) ? p->bufs_hi[dst] : nullptr;
     g.out_lo = (dst >= 0) ? p->bufs_lo[dst] : nullptr;
     g.U = e.U;
+    g.dsq = e.dsq;
     g.lam32 = e.lam32;
     g.shift = e.shift;
     g.done = e.done;

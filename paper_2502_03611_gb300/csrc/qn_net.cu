@@ -26,6 +26,7 @@
 #include <string.h>
 
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "qn_internal.h"
@@ -70,29 +71,51 @@ __device__ __forceinline__ void block_atomic_lanes(float v, float *dst, float *s
 }
 
 // out[o][k][i][c] (+)= sum_j Mt[k][j] in[o][j][i][c]
+// The lanes of a warp take the channels c (coalesced loads of the C
+// contiguous values at every j); a warp walks a run of `run` consecutive
+// (o, k, i) rows, decomposing the first row index once and stepping the
+// others (every tensor here has < 2^31 elements); the j loop is unrolled so
+// that several loads are in flight. Large tensors take runs of up to 8 rows,
+// small ones (latency-bound) one row per warp.
+constexpr int kAxisRunMax = 8;
 template <typename Tin>
 __global__ void __launch_bounds__(256) k_axis(const Tin *__restrict__ in, float *__restrict__ out,
                                               const float *__restrict__ Mt, long long outer, int Kin, int Kout,
-                                              int inner, int C, int accumulate) {
+                                              int inner, int C, int accumulate, int run) {
     __shared__ float sM[64 * 64];
     for (int t = threadIdx.x; t < Kin * Kout; t += blockDim.x) sM[t] = Mt[t];
     __syncthreads();
-    const long long total = outer * Kout * inner * C;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(idx % C);
-        long long r = idx / C;
-        const int i = (int)(r % inner);
-        r /= inner;
-        const int k = (int)(r % Kout);
-        const long long o = r / Kout;
-        const long long ibase = (o * Kin * inner + i) * C + c;
-        float s = 0.0f;
-        for (int j = 0; j < Kin; ++j) s = fmaf(sM[k * Kin + j], ld(in, ibase + (long long)j * inner * C), s);
-        if (accumulate)
-            out[idx] += s;
-        else
-            out[idx] = s;
+    const int lane = threadIdx.x & 31;
+    const int rows = (int)(outer * Kout * inner);
+    const int jstride = inner * C;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int r0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * run; r0 < rows; r0 += nwarps * run) {
+        int i = r0 % inner;
+        const int rr = r0 / inner;
+        int k = rr % Kout;
+        int o = rr / Kout;
+        const int rend = min(r0 + run, rows);
+        for (int row = r0; row < rend; ++row) {
+            const Tin *ib = in + ((long long)o * Kin * inner + i) * C;
+            const float *mk = sM + k * Kin;
+            float *ob = out + (long long)row * C;
+            for (int c = lane; c < C; c += 32) {
+                float sacc = 0.0f;
+#pragma unroll 8
+                for (int j = 0; j < Kin; ++j) sacc = fmaf(mk[j], ld(ib, (long long)j * jstride + c), sacc);
+                if (accumulate)
+                    ob[c] += sacc;
+                else
+                    ob[c] = sacc;
+            }
+            if (++i == inner) {
+                i = 0;
+                if (++k == Kout) {
+                    k = 0;
+                    ++o;
+                }
+            }
+        }
     }
 }
 
@@ -156,22 +179,34 @@ __global__ void k_modemix_bwd_w(const float *__restrict__ hh, const float *__res
     }
 }
 
-// z = s + h W + b ; h_next = gelu(z) (or z). One warp per node, lane = output channel (C == 32).
+// z = s + h W + b ; h_next = gelu(z) (or z). One warp per node, lane = output
+// channel (C == 32): each lane keeps its column of W in registers; the node's
+// 32 input channels are broadcast from shared memory (eight 16-byte reads).
 __global__ void __launch_bounds__(256) k_pointwise(const float *__restrict__ sp, const __nv_bfloat16 *__restrict__ h,
                                                    const float *__restrict__ W, const float *__restrict__ bvec,
                                                    __nv_bfloat16 *__restrict__ z, __nv_bfloat16 *__restrict__ hnext,
                                                    long long pts, int act) {
-    __shared__ float sW[32 * 32];
-    for (int t = threadIdx.x; t < 1024; t += blockDim.x) sW[t] = W[t];
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
+    __shared__ __align__(16) float sh[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float w[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) w[i] = __ldg(W + i * 32 + lane);
     const float bo = bvec[lane];
+    const float4 *h4 = reinterpret_cast<const float4 *>(sh[warp]);
     for (long long p = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; p < pts;
          p += ((long long)gridDim.x * blockDim.x) >> 5) {
-        const float hin = __bfloat162float(h[p * 32 + lane]);
+        sh[warp][lane] = __bfloat162float(h[p * 32 + lane]);
+        __syncwarp();
         float s = sp[p * 32 + lane] + bo;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) s = fmaf(__shfl_sync(0xffffffffu, hin, i), sW[i * 32 + lane], s);
+        for (int q = 0; q < 8; ++q) {
+            const float4 v = h4[q];
+            s = fmaf(v.x, w[4 * q], s);
+            s = fmaf(v.y, w[4 * q + 1], s);
+            s = fmaf(v.z, w[4 * q + 2], s);
+            s = fmaf(v.w, w[4 * q + 3], s);
+        }
+        __syncwarp();
         z[p * 32 + lane] = __float2bfloat16_rn(s);
         hnext[p * 32 + lane] = __float2bfloat16_rn(act ? gelu_f(s) : s);
     }
@@ -301,48 +336,59 @@ __global__ void k_adamw(float *__restrict__ p, const float *__restrict__ g, floa
 
 // Trilinear transfer: dst (m_to^3) = interpolation of src (m_from^3) at nodes
 // i/(m_to+1), with zero values on the boundary of (0,1)^3. Batched over B.
+// The 1-D corner indices and weights (the same table for every axis) are
+// computed once per block into shared memory; the interpolation runs in FP64
+// only when both source and destination are FP64 (the exactly tested
+// transfer), else in FP32 - the precision of the FP32 end (the network's
+// input or output), without spending the FP64 pipe.
+constexpr int kInterpMax = 2048;
 template <typename Tin, typename Tout>
-__global__ void k_interp3d(const Tin *__restrict__ src, int m_from, Tout *__restrict__ dst, int m_to, int B,
-                           float scale) {
-    const long long per = (long long)m_to * m_to * m_to;
-    const long long total = per * B;
+__global__ void __launch_bounds__(256) k_interp3d(const Tin *__restrict__ src, int m_from, Tout *__restrict__ dst,
+                                                  int m_to, int B, double scale) {
+    typedef typename std::conditional<(sizeof(Tin) == 8 && sizeof(Tout) == 8), double, float>::type Tc;
+    __shared__ int sj[kInterpMax];
+    __shared__ Tc sw[kInterpMax];
+    for (int i = threadIdx.x; i < m_to; i += blockDim.x) {
+        const double t = (double)(i + 1) * (m_from + 1) / (m_to + 1);
+        const int j = (int)floor(t);   // 1-based left node; 0 and m_from+1 are the zero boundary
+        sj[i] = j;
+        sw[i] = (Tc)(t - j);
+    }
+    __syncthreads();
+    const Tc sc = (Tc)scale;
+    const long long rows = (long long)B * m_to * m_to;
     const long long sper = (long long)m_from * m_from * m_from;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long b = idx / per;
-        long long r = idx % per;
-        const int ix = (int)(r % m_to);
-        r /= m_to;
-        const int iy = (int)(r % m_to);
-        const int iz = (int)(r / m_to);
-        int j0[3];
-        double w[3];
-        const int ii[3] = {ix, iy, iz};
-        for (int a = 0; a < 3; ++a) {
-            const double t = (double)(ii[a] + 1) * (m_from + 1) / (m_to + 1);
-            int j = (int)floor(t);
-            w[a] = t - j;
-            j0[a] = j;   // 1-based left node; 0 and m_from+1 are the zero boundary
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int iy = (int)(row % m_to);
+        const long long r2 = row / m_to;
+        const int iz = (int)(r2 % m_to);
+        const long long b = r2 / m_to;
+        const Tin *sb = src + b * sper;
+        const int jz = sj[iz], jy = sj[iy];
+        const Tc wz = sw[iz], wy = sw[iy];
+        // weights and row offsets of the four (z, y) corner rows (0 outside the grid)
+        Tc wr[4];
+        long long ro[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int zz = jz + (c >> 1), yy = jy + (c & 1);
+            const bool ok = zz >= 1 && zz <= m_from && yy >= 1 && yy <= m_from;
+            wr[c] = ok ? ((c >> 1) ? wz : (Tc)1 - wz) * ((c & 1) ? wy : (Tc)1 - wy) : (Tc)0;
+            ro[c] = ok ? ((long long)(zz - 1) * m_from + (yy - 1)) * m_from : 0;
         }
-        double s = 0.0;
-        for (int dz = 0; dz < 2; ++dz) {
-            const int jz = j0[2] + dz;
-            if (jz < 1 || jz > m_from) continue;
-            const double wz = dz ? w[2] : 1.0 - w[2];
-            for (int dy = 0; dy < 2; ++dy) {
-                const int jy = j0[1] + dy;
-                if (jy < 1 || jy > m_from) continue;
-                const double wy = dy ? w[1] : 1.0 - w[1];
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int jx = j0[0] + dx;
-                    if (jx < 1 || jx > m_from) continue;
-                    const double wx = dx ? w[0] : 1.0 - w[0];
-                    s += wz * wy * wx *
-                         (double)src[b * sper + ((long long)(jz - 1) * m_from + (jy - 1)) * m_from + (jx - 1)];
-                }
+        for (int ix = threadIdx.x; ix < m_to; ix += blockDim.x) {
+            const int jx = sj[ix];
+            const Tc wx = sw[ix];
+            const bool okl = jx >= 1, okr = jx + 1 <= m_from;
+            Tc acc = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const Tc vl = okl ? (Tc)sb[ro[c] + jx - 1] : (Tc)0;
+                const Tc vr = okr ? (Tc)sb[ro[c] + jx] : (Tc)0;
+                acc += wr[c] * (((Tc)1 - wx) * vl + wx * vr);
             }
+            dst[row * m_to + ix] = (Tout)(acc * sc);
         }
-        dst[idx] = (Tout)(s * scale);
     }
 }
 
@@ -360,6 +406,14 @@ inline int grid_for(long long n, int block = 256) {
     if (g < 1) g = 1;
     return (int)g;
 }
+
+// k_axis: rows of C (= 32) channels per warp so that ~10k warps share the work
+inline int axis_run(long long elements) {
+    const long long rows = elements / 32;
+    long long r = rows / (152 * 64);
+    return (int)(r < 1 ? 1 : (r > kAxisRunMax ? kAxisRunMax : r));
+}
+inline int grid_axis(long long elements) { return grid_for((elements + axis_run(elements) - 1) / axis_run(elements)); }
 
 }  // namespace
 }  // namespace qn
@@ -540,20 +594,20 @@ static int net_forward(qn_net *n, int B, cudaStream_t s) {
     k_lift<<<grid_for(pts * C), 256, 0, s>>>(n->fin, P_wl(n), P_bl(n), n->h[0], pts, C);
     for (int l = 0; l < n->L; ++l) {
         // analysis x, y, z
-        k_axis<__nv_bfloat16><<<grid_for((long long)B * G * G * M * C), 256, 0, s>>>(
-            n->h[l], n->t1, n->basis_a, (long long)B * G * G, G, M, 1, C, 0);
-        k_axis<float><<<grid_for((long long)B * G * M * M * C), 256, 0, s>>>(n->t1, n->t2, n->basis_a,
-                                                                             (long long)B * G, G, M, M, C, 0);
-        k_axis<float><<<grid_for((long long)B * K * C), 256, 0, s>>>(n->t2, n->hh[l], n->basis_a, (long long)B, G, M,
-                                                                     M * M, C, 0);
+        k_axis<__nv_bfloat16><<<grid_axis((long long)B * G * G * M * C), 256, 0, s>>>(
+            n->h[l], n->t1, n->basis_a, (long long)B * G * G, G, M, 1, C, 0, axis_run((long long)B * G * G * M * C));
+        k_axis<float><<<grid_axis((long long)B * G * M * M * C), 256, 0, s>>>(n->t1, n->t2, n->basis_a,
+                                                                             (long long)B * G, G, M, M, C, 0, axis_run((long long)B * G * M * M * C));
+        k_axis<float><<<grid_axis((long long)B * K * C), 256, 0, s>>>(n->t2, n->hh[l], n->basis_a, (long long)B, G, M,
+                                                                     M * M, C, 0, axis_run((long long)B * K * C));
         k_modemix<<<grid_for((long long)B * K * C), 256, 0, s>>>(n->hh[l], n->params + off_R(n, l), n->g, B, K, C);
         // synthesis z, y, x
-        k_axis<float><<<grid_for((long long)B * G * M * M * C), 256, 0, s>>>(n->g, n->t2, n->basis_s, (long long)B, M,
-                                                                             G, M * M, C, 0);
-        k_axis<float><<<grid_for((long long)B * G * G * M * C), 256, 0, s>>>(n->t2, n->t1, n->basis_s,
-                                                                             (long long)B * G, M, G, M, C, 0);
-        k_axis<float><<<grid_for(pts * C), 256, 0, s>>>(n->t1, n->sp, n->basis_s, (long long)B * G * G, M, G, 1, C,
-                                                        0);
+        k_axis<float><<<grid_axis((long long)B * G * M * M * C), 256, 0, s>>>(n->g, n->t2, n->basis_s, (long long)B, M,
+                                                                             G, M * M, C, 0, axis_run((long long)B * G * M * M * C));
+        k_axis<float><<<grid_axis((long long)B * G * G * M * C), 256, 0, s>>>(n->t2, n->t1, n->basis_s,
+                                                                             (long long)B * G, M, G, M, C, 0, axis_run((long long)B * G * G * M * C));
+        k_axis<float><<<grid_axis(pts * C), 256, 0, s>>>(n->t1, n->sp, n->basis_s, (long long)B * G * G, M, G, 1, C,
+                                                        0, axis_run(pts * C));
         k_pointwise<<<grid_for(pts * 32), 256, 0, s>>>(n->sp, n->h[l], n->params + off_W(n, l),
                                                        n->params + off_b(n, l), n->z[l], n->h[l + 1], pts,
                                                        l < n->L - 1 ? 1 : 0);
@@ -578,22 +632,22 @@ static int net_backward(qn_net *n, int B, cudaStream_t s) {
                                                            n->dh2, n->grads + off_W(n, l), n->grads + off_b(n, l), pts,
                                                            l < n->L - 1 ? 1 : 0);
         // spectral path: dg = analysis(dz); dR; dhh = dg R^T; dh_prev += synthesis(dhh)
-        k_axis<float><<<grid_for((long long)B * G * G * M * C), 256, 0, s>>>(n->dz, n->t1, n->basis_a,
-                                                                             (long long)B * G * G, G, M, 1, C, 0);
-        k_axis<float><<<grid_for((long long)B * G * M * M * C), 256, 0, s>>>(n->t1, n->t2, n->basis_a,
-                                                                             (long long)B * G, G, M, M, C, 0);
-        k_axis<float><<<grid_for((long long)B * K * C), 256, 0, s>>>(n->t2, n->dg, n->basis_a, (long long)B, G, M,
-                                                                     M * M, C, 0);
+        k_axis<float><<<grid_axis((long long)B * G * G * M * C), 256, 0, s>>>(n->dz, n->t1, n->basis_a,
+                                                                             (long long)B * G * G, G, M, 1, C, 0, axis_run((long long)B * G * G * M * C));
+        k_axis<float><<<grid_axis((long long)B * G * M * M * C), 256, 0, s>>>(n->t1, n->t2, n->basis_a,
+                                                                             (long long)B * G, G, M, M, C, 0, axis_run((long long)B * G * M * M * C));
+        k_axis<float><<<grid_axis((long long)B * K * C), 256, 0, s>>>(n->t2, n->dg, n->basis_a, (long long)B, G, M,
+                                                                     M * M, C, 0, axis_run((long long)B * K * C));
         k_modemix_bwd_w<<<grid_for((long long)K * C * C), 256, 0, s>>>(n->hh[l], n->dg, n->grads + off_R(n, l), B, K,
                                                                         C);
         k_modemix_bwd_in<<<grid_for((long long)B * K * C), 256, 0, s>>>(n->dg, n->params + off_R(n, l), n->dhh, B, K,
                                                                          C);
-        k_axis<float><<<grid_for((long long)B * G * M * M * C), 256, 0, s>>>(n->dhh, n->t2, n->basis_s, (long long)B,
-                                                                             M, G, M * M, C, 0);
-        k_axis<float><<<grid_for((long long)B * G * G * M * C), 256, 0, s>>>(n->t2, n->t1, n->basis_s,
-                                                                             (long long)B * G, M, G, M, C, 0);
-        k_axis<float><<<grid_for(pts * C), 256, 0, s>>>(n->t1, n->dh2, n->basis_s, (long long)B * G * G, M, G, 1, C,
-                                                        1);
+        k_axis<float><<<grid_axis((long long)B * G * M * M * C), 256, 0, s>>>(n->dhh, n->t2, n->basis_s, (long long)B,
+                                                                             M, G, M * M, C, 0, axis_run((long long)B * G * M * M * C));
+        k_axis<float><<<grid_axis((long long)B * G * G * M * C), 256, 0, s>>>(n->t2, n->t1, n->basis_s,
+                                                                             (long long)B * G, M, G, M, C, 0, axis_run((long long)B * G * G * M * C));
+        k_axis<float><<<grid_axis(pts * C), 256, 0, s>>>(n->t1, n->dh2, n->basis_s, (long long)B * G * G, M, G, 1, C,
+                                                        1, axis_run(pts * C));
         float *tmp = n->dh;
         n->dh = n->dh2;
         n->dh2 = tmp;
@@ -672,26 +726,26 @@ extern "C" int qn_net_train_step(qn_net *n, const float *f_coarse, const float *
 }
 
 extern "C" int qn_interp3d(const double *src, int m_from, double *dst, int m_to, int B, double scale, void *stream) {
-    if (!src || !dst || m_from < 1 || m_to < 1 || m_from > 2048 || m_to > 2048 || B < 1) {
+    if (!src || !dst || m_from < 1 || m_to < 1 || m_from > kInterpMax || m_to > kInterpMax || B < 1) {
         set_error("qn_interp3d: invalid arguments");
         return QN_EINVAL;
     }
-    const long long total = (long long)m_to * m_to * m_to * B;
-    k_interp3d<double, double><<<grid_for(total), 256, 0, (cudaStream_t)stream>>>(src, m_from, dst, m_to, B,
-                                                                                  (float)scale);
+    const long long rows = (long long)m_to * m_to * B;
+    k_interp3d<double, double><<<grid_for(rows * 256), 256, 0, (cudaStream_t)stream>>>(src, m_from, dst, m_to, B,
+                                                                                      scale);
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }
 
 extern "C" int qn_interp3d_f32(const double *src, int m_from, float *dst, int m_to, int B, double scale,
                                void *stream) {
-    if (!src || !dst || m_from < 1 || m_to < 1 || m_from > 2048 || m_to > 2048 || B < 1) {
+    if (!src || !dst || m_from < 1 || m_to < 1 || m_from > kInterpMax || m_to > kInterpMax || B < 1) {
         set_error("qn_interp3d_f32: invalid arguments");
         return QN_EINVAL;
     }
-    const long long total = (long long)m_to * m_to * m_to * B;
-    k_interp3d<double, float><<<grid_for(total), 256, 0, (cudaStream_t)stream>>>(src, m_from, dst, m_to, B,
-                                                                                 (float)scale);
+    const long long rows = (long long)m_to * m_to * B;
+    k_interp3d<double, float><<<grid_for(rows * 256), 256, 0, (cudaStream_t)stream>>>(src, m_from, dst, m_to, B,
+                                                                                     scale);
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }
@@ -706,12 +760,10 @@ extern "C" int qn_net_predict(qn_net *n, const double *f_fine, int nf, double in
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int G = n->G;
-    k_interp3d<double, float><<<grid_for((long long)G * G * G), 256, 0, s>>>(f_fine, nf, n->fin, G, 1,
-                                                                           (float)in_scale);
+    k_interp3d<double, float><<<grid_for((long long)G * G * 256), 256, 0, s>>>(f_fine, nf, n->fin, G, 1, in_scale);
     int rc = net_forward(n, 1, s);
     if (rc) return rc;
-    k_interp3d<float, double><<<grid_for((long long)nf * nf * nf), 256, 0, s>>>(n->out, G, U0, nf, 1,
-                                                                              (float)out_scale);
+    k_interp3d<float, double><<<grid_for((long long)nf * nf * 256), 256, 0, s>>>(n->out, G, U0, nf, 1, out_scale);
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }
@@ -752,15 +804,28 @@ extern "C" int qn_solve_warm(qn_ctx *ctx, qn_net *net, double *U, const double *
     const long long N = (long long)n * n * n;
     int rc = qn_net_predict(net, f, n, in_scale, out_scale, U, stream);
     if (rc) return rc;
-    double *U0 = nullptr, *sums = nullptr;
-    QN_CUDA(cudaMallocAsync(&U0, sizeof(double) * N, s));
+    double *sums = nullptr;
     QN_CUDA(cudaMallocAsync(&sums, 2 * sizeof(double), s));
+    QN_CUDA(cudaMemsetAsync(sums, 0, 2 * sizeof(double), s));
+    if (ctx_split_precision(ctx)) {
+        // one solve from U_0; its first iteration measures ||U_1 - U_0|| and
+        // falls back to the zero start by itself (solve_internal)
+        k_diff_norms<<<grid_for(N), 256, 0, s>>>(U, U, N, sums);   // sums[1] = ||U_0||^2
+        QN_CUDA(cudaGetLastError());
+        int used = 0;
+        rc = solve_internal(ctx, U, f, opts, res, nullptr, 0, stream, sums + 1, &used);
+        cudaFreeAsync(sums, s);
+        if (used_warm) *used_warm = used;
+        return rc;
+    }
+    // FP64 path: a separate first step, then the solve
+    double *U0 = nullptr;
+    QN_CUDA(cudaMallocAsync(&U0, sizeof(double) * N, s));
     QN_CUDA(cudaMemcpyAsync(U0, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
     qn_stats st0;
     rc = qn_step(ctx, U, f, NAN, &st0, stream);          // U1 = U0 - delta
     bool warm = (rc == QN_OK) && isfinite(st0.res_norm);
     if (warm) {
-        QN_CUDA(cudaMemsetAsync(sums, 0, 2 * sizeof(double), s));
         k_diff_norms<<<grid_for(N), 256, 0, s>>>(U, U0, N, sums);
         double h[2] = {0.0, 0.0};
         QN_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
