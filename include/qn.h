@@ -91,6 +91,10 @@ typedef struct qn_opts {
     double step;       /* update scale; 1.0 is the paper's plain update */
     int sync_every;    /* host checks convergence every this many iterations
                           (>= 1); kernels queued past convergence exit at once */
+    int graph;         /* 1: from the third iteration on, each group of sync_every
+                          iterations is replayed from a CUDA graph captured once per
+                          context (re-captured when U, f, step or sync_every change);
+                          ignored while launch profiling is on. 0: plain launches */
 } qn_opts;
 
 typedef struct qn_result {

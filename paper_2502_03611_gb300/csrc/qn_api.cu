@@ -86,6 +86,14 @@ struct qn_ctx {
     int res_parts;        // partial-sum records written by the last residual launch
     int res_fx_headroom;  // DevState::fx_headroom for the solves of this context
     int res_saved_fnorm;  // 1: the last residual's finaliser takes ||f|| from DevState::f_norm
+    // CUDA graph of sync_every steady-state iterations (qn_opts.graph)
+    cudaStream_t cap_stream;
+    cudaGraphExec_t gexec;
+    double *g_U;
+    const double *g_f;
+    double g_step;
+    int g_chunk;
+    long long g_launches; // kernels per replay
     float *warm_dsq;      // device: ||U_1 - U_0||^2 of a warm-started solve's first iteration
     int warm_dsq_on;      // 1 while that iteration's products are enqueued
     // reflection-split mode products (3-D split solve, P a multiple of 128)
@@ -192,6 +200,8 @@ static void ctx_free(qn_ctx *c) {
     }
     cudaFree(c->partials);
     cudaFree(c->warm_dsq);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     cudaFree(c->fdf);
     cudaFree(c->st);
     cudaFree(c->hist);
@@ -587,6 +597,47 @@ static int enqueue_iteration(qn_ctx *c, double *U, const double *f, double step,
     return enqueue_inverse(c, nullptr, U, true, step, s, c->split_layout != 0);
 }
 
+// Capture `chunk` steady-state iterations (third iteration on: the residual
+// takes its fixed-point exponent from the previous iterate, no preparation
+// passes) into a CUDA graph on a private stream, once per (U, f, step, chunk).
+static int ensure_iteration_graph(qn_ctx *c, double *U, const double *f, double step, int chunk) {
+    if (c->gexec && c->g_U == U && c->g_f == f && c->g_step == step && c->g_chunk == chunk) return QN_OK;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (!c->cap_stream) QN_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const long long l0 = c->launches;
+    const int it0 = c->cur_iter;
+    QN_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = QN_OK;
+    for (int k = 0; k < chunk && rc == QN_OK; ++k) {
+        c->cur_iter = 2 + k;
+        rc = enqueue_iteration(c, U, f, step, c->cap_stream);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    c->cur_iter = it0;
+    c->g_launches = c->launches - l0;
+    c->launches = l0;
+    if (rc != QN_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture (solve iterations)");
+    const cudaError_t ei = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        c->gexec = nullptr;
+        return cuda_fail(ei, "cudaGraphInstantiate (solve iterations)");
+    }
+    c->g_U = U;
+    c->g_f = f;
+    c->g_step = step;
+    c->g_chunk = chunk;
+    return QN_OK;
+}
+
 static int read_state(qn_ctx *c, DevState *h, cudaStream_t s) {
     QN_CUDA(cudaMemcpyAsync(h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     QN_CUDA(cudaStreamSynchronize(s));
@@ -712,6 +763,7 @@ int qn::solve_internal(qn_ctx *c, double *U, const double *f, const qn_opts *opt
         o.beta_value = 0.0;
         o.step = 1.0;
         o.sync_every = 2;
+        o.graph = 0;
     }
     if (!(o.tol >= 0.0) || o.max_it < 0 || o.max_it > kHistCap - 1 || !isfinite(o.step) ||
         (o.beta_mode != QN_BETA_PAPER && o.beta_mode != QN_BETA_FIXED) ||
@@ -768,11 +820,21 @@ int qn::solve_internal(qn_ctx *c, double *U, const double *f, const qn_opts *opt
     } else if (used_warm) {
         *used_warm = 0;
     }
+    const bool use_graph = o.graph != 0 && !c->prof_on;
     while (!h.done && enqueued <= o.max_it) {
-        for (int k = 0; k < o.sync_every && enqueued <= o.max_it; ++k, ++enqueued) {
-            c->cur_iter = enqueued;
-            rc = enqueue_iteration(c, U, f, o.step, s);
+        if (use_graph && enqueued >= 2 && enqueued + o.sync_every <= o.max_it + 1) {
+            // steady-state iterations (the same launches every time): replay
+            rc = ensure_iteration_graph(c, U, f, o.step, o.sync_every);
             if (rc) return rc;
+            QN_CUDA(cudaGraphLaunch(c->gexec, s));
+            c->launches += c->g_launches;
+            enqueued += o.sync_every;
+        } else {
+            for (int k = 0; k < o.sync_every && enqueued <= o.max_it; ++k, ++enqueued) {
+                c->cur_iter = enqueued;
+                rc = enqueue_iteration(c, U, f, o.step, s);
+                if (rc) return rc;
+            }
         }
         rc = read_state(c, &h, s);
         if (rc) return rc;

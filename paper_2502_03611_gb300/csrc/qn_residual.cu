@@ -257,31 +257,55 @@ __global__ void __launch_bounds__(256) k_prep_split(const double *__restrict__ U
     const int H = P / 2, nsym = (n + 1) / 2, nanti = n / 2;
     double f2 = 0.0;
     unsigned long long umax = 0ull;
-    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    if (MIRROR) {
+        // four rows per step, their loads issued together (the pass is
+        // latency-bound with one row per step)
+        constexpr int kRows = 4;
+        float4 *f4 = reinterpret_cast<float4 *>(fdf);
+        for (long long row0 = blockIdx.x; row0 < rows; row0 += (long long)kRows * gridDim.x) {
+            for (int i = threadIdx.x; i < H; i += blockDim.x) {
+                double fa[kRows], fb[kRows], ua[kRows], ub[kRows];
+                bool oka[kRows], okb[kRows];
+#pragma unroll
+                for (int g = 0; g < kRows; ++g) {
+                    const long long row = row0 + (long long)g * gridDim.x;
+                    const int y = (int)(row % P), z = (int)(row / P);
+                    const bool row_ok = row < rows && (y < n) && (z < n);
+                    const long long cbase = ((long long)z * n + y) * n;
+                    oka[g] = row_ok && i < nsym;
+                    okb[g] = row_ok && i < nanti;
+                    fa[g] = oka[g] ? __ldg(f + cbase + i) : 0.0;
+                    ua[g] = oka[g] ? __ldg(U + cbase + i) : 0.0;
+                    fb[g] = okb[g] ? __ldg(f + cbase + (n - 1 - i)) : 0.0;
+                    ub[g] = okb[g] ? __ldg(U + cbase + (n - 1 - i)) : 0.0;
+                }
+#pragma unroll
+                for (int g = 0; g < kRows; ++g) {
+                    const long long row = row0 + (long long)g * gridDim.x;
+                    if (row >= rows) break;
+                    float2 a = make_float2(0.0f, 0.0f), b = a;
+                    if (oka[g]) {
+                        f2 = fma(fa[g], fa[g], f2);
+                        a = f_pair(fa[g], &st->fx_fbad);
+                        const unsigned long long ab = abs_bits(ua[g]);
+                        umax = ab > umax ? ab : umax;
+                    }
+                    if (okb[g]) {
+                        f2 = fma(fb[g], fb[g], f2);
+                        b = f_pair(fb[g], &st->fx_fbad);
+                        const unsigned long long ab = abs_bits(ub[g]);
+                        umax = ab > umax ? ab : umax;
+                    }
+                    f4[row * H + i] = make_float4(a.x, a.y, b.x, b.y);
+                }
+            }
+        }
+    }
+    for (long long row = blockIdx.x; !MIRROR && row < rows; row += gridDim.x) {
         const int y = (int)(row % P), z = (int)(row / P);
         const bool row_ok = (y < n) && (z < n);
         const long long cbase = ((long long)z * n + y) * n;
-        if (MIRROR) {
-            float4 *f4 = reinterpret_cast<float4 *>(fdf);
-            for (int i = threadIdx.x; i < H; i += blockDim.x) {
-                float2 a = make_float2(0.0f, 0.0f), b = a;
-                if (row_ok && i < nsym) {
-                    const double fv = __ldg(f + cbase + i);
-                    f2 = fma(fv, fv, f2);
-                    a = f_pair(fv, &st->fx_fbad);
-                    const unsigned long long ab = abs_bits(__ldg(U + cbase + i));
-                    umax = ab > umax ? ab : umax;
-                }
-                if (row_ok && i < nanti) {
-                    const double fv = __ldg(f + cbase + (n - 1 - i));
-                    f2 = fma(fv, fv, f2);
-                    b = f_pair(fv, &st->fx_fbad);
-                    const unsigned long long ab = abs_bits(__ldg(U + cbase + (n - 1 - i)));
-                    umax = ab > umax ? ab : umax;
-                }
-                f4[row * H + i] = make_float4(a.x, a.y, b.x, b.y);
-            }
-        } else {
+        {
             for (int x = threadIdx.x; x < P; x += blockDim.x) {
                 float2 fp = make_float2(0.0f, 0.0f);
                 if (row_ok && x < n) {

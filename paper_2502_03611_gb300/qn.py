@@ -50,7 +50,7 @@ class QnStats(ctypes.Structure):
 class QnOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_it", ctypes.c_int), ("beta_mode", ctypes.c_int),
                 ("beta_value", ctypes.c_double), ("step", ctypes.c_double),
-                ("sync_every", ctypes.c_int)]
+                ("sync_every", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class QnResult(ctypes.Structure):
@@ -259,16 +259,16 @@ def qn_step(ctx: QnContext, U, f, beta: float = math.nan, stream=None) -> dict:
     return st.as_dict()
 
 
-def make_opts(tol=1e-10, max_it=200, beta=None, step=1.0, sync_every=2) -> QnOpts:
+def make_opts(tol=1e-10, max_it=200, beta=None, step=1.0, sync_every=2, graph=False) -> QnOpts:
     if beta is None:
-        return QnOpts(tol, max_it, QN_BETA_PAPER, 0.0, step, sync_every)
-    return QnOpts(tol, max_it, QN_BETA_FIXED, float(beta), step, sync_every)
+        return QnOpts(tol, max_it, QN_BETA_PAPER, 0.0, step, sync_every, 1 if graph else 0)
+    return QnOpts(tol, max_it, QN_BETA_FIXED, float(beta), step, sync_every, 1 if graph else 0)
 
 
 def qn_solve(ctx: QnContext, U, f, tol=1e-10, max_it=200, beta=None, step=1.0, sync_every=2,
-             history_len=0, stream=None, check=True):
+             history_len=0, stream=None, check=True, graph=False):
     """Returns (result dict, list of per-iterate stats dicts)."""
-    opts = make_opts(tol, max_it, beta, step, sync_every)
+    opts = make_opts(tol, max_it, beta, step, sync_every, graph)
     res = QnResult()
     hist = (QnStats * history_len)() if history_len > 0 else None
     rc = load_library().qn_solve(ctx.handle, _dptr(U, ctx.numel, "U"), _dptr(f, ctx.numel, "f"),
@@ -282,12 +282,12 @@ def qn_solve(ctx: QnContext, U, f, tol=1e-10, max_it=200, beta=None, step=1.0, s
 
 
 def qn_solve_host(ctx: QnContext, U_host: np.ndarray, f_host: np.ndarray, tol=1e-10, max_it=200,
-                  beta=None, step=1.0, sync_every=2, stream=None):
+                  beta=None, step=1.0, sync_every=2, stream=None, graph=False):
     """Solve with host arrays (copies inside the call). U_host is updated in place."""
     for name, a in (("U_host", U_host), ("f_host", f_host)):
         if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != ctx.numel:
             raise ValueError(f"{name} must be a C-contiguous float64 array of {ctx.numel} values")
-    opts = make_opts(tol, max_it, beta, step, sync_every)
+    opts = make_opts(tol, max_it, beta, step, sync_every, graph)
     res = QnResult()
     rc = load_library().qn_solve_host(ctx.handle, ctypes.c_void_p(U_host.ctypes.data),
                                       ctypes.c_void_p(f_host.ctypes.data), ctypes.byref(opts),

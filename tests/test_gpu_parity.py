@@ -491,3 +491,24 @@ def test_reflection_split_products_p384(qn, monkeypatch):
     rel = np.linalg.norm(O.residual(sols[0], f)) / np.linalg.norm(f)
     assert rel <= 1.05e-10, rel
     assert np.abs(sols[0] - sols[1]).max() <= 1e-9 * np.abs(sols[1]).max()
+
+
+@pytest.mark.parametrize("dim,n,prec", [(3, 127, "bf16x3"), (3, 65, "bf16x3"), (3, 33, "fp64"), (2, 63, "bf16x3")])
+def test_graph_replay_matches_plain_launches(qn, dim, n, prec):
+    """qn_opts.graph: the steady-state iterations replayed from a CUDA graph
+    run the same kernels in the same order as plain launches - bitwise the
+    same U. A second solve with another source re-captures the graph."""
+    import torch
+    ctx = qn.QnContext(dim, n, prec)
+    for seed in (0, 1):
+        u, f = manufactured_problem(n, dim, seed=seed)
+        fd = dev(f).reshape(-1)
+        outs = []
+        for graph in (False, True):
+            U = torch.zeros(n ** dim, dtype=torch.float64, device="cuda")
+            res, hist = qn.qn_solve(ctx, U, fd, tol=1e-10, graph=graph, sync_every=2, history_len=40)
+            assert res["status"] == 0
+            outs.append((res["iterations"], host(U), [h["rel"] for h in hist]))
+        assert outs[0][0] == outs[1][0]
+        assert np.array_equal(outs[0][1], outs[1][1])
+        assert outs[0][2] == outs[1][2]
