@@ -65,7 +65,9 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+    """nvidia-smi clock / throttle-reason samples every 50 ms while running;
+    start() returns once the first sample is in (nvidia-smi takes a while to
+    come up), so that the samples cover the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -81,8 +83,17 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.index)], stdout=self.fh,
+                                          "-lms", "50", "-i", str(self.index)], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 3.0 and self.proc.poll() is None:
+                self.fh.flush()
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.02)
+            self.skip = 0
+            with open(self.path) as fh:
+                self.skip = sum(1 for _ in fh)   # samples taken before the timed region
         except Exception:
             self.proc = None
 
@@ -95,23 +106,25 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         with open(self.path) as fh:
             for line in fh:
                 parts = [p.strip() for p in line.split(",")]
                 if len(parts) < 9:
                     continue
                 try:
-                    sm.append(float(parts[1]))
-                    mx.append(float(parts[2]))
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
                 except ValueError:
                     continue
-                for nm, v in zip(names, parts[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(nm)
-        if not sm:
+        # the samples of the timed region; the last earlier one if it was shorter than a period
+        skip = getattr(self, "skip", 0)
+        rows = rows[skip:] if len(rows) > skip else rows[-1:]
+        if not rows:
             return None
+        sm = [r[0] for r in rows]
+        mx = [r[1] for r in rows]
+        reasons = {nm for r in rows for nm, v in zip(names, r[2]) if v.lower().startswith("active")}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
                 "reasons": sorted(reasons)}
 
@@ -412,6 +425,13 @@ def main():
         kernels["finalize"]["share"] = round(prof["finalize_ms"] / tot, 4)
     kernels["modeprod"]["roofline"] = roofline
     kernels["modeprod"]["tensor"] = tensor_roofline
+    # the pass marks of the measurement plan: 70 % of HBM for bandwidth-bound
+    # kernels, 60 % of the tensor peak for tensor-bound ones
+    kernels["residual"]["pass_70pct_hbm"] = bool(til_gbs and til_gbs / hbm >= 0.70)
+    if split:
+        kernels["modeprod"]["pass_70pct_hbm"] = bool(st_gbs / hbm >= 0.70)
+    elif peak:
+        kernels["modeprod"]["pass_60pct_tensor"] = bool(exec_flops / (mp_avg_ms * 1e-3) / 1e12 / peak >= 0.60)
     # the JSON line's roofline is that of the kernel with the largest time share
     if prof["residual_ms"] > prof["modeprod_ms"]:
         roofline = {"kernel": "k_residual_tiled" if til_n else "k_residual", "bound": "hbm",
