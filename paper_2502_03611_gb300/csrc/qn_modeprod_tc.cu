@@ -72,6 +72,10 @@ constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr uint32_t kCtrlBytes = 512;
 constexpr uint32_t kTmemCols = 2 * BN_MAX;         // two accumulators of BN_MAX FP32 columns
 
+// B rows per pipeline stage: backward split tiles (MODE 2) are at most 128
+// rows wide, so their stages are 64 KB and three fit in shared memory
+__host__ __device__ constexpr int bn_slot(int mode) { return mode == 2 ? 128 : BN_MAX; }
+
 // Wait for `parity` on `bar`; false on timeout or when another role aborted.
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort_flag,
                                          int *err) {
@@ -135,7 +139,7 @@ __global__ void __maxnreg__(104)
     constexpr uint32_t kLayout = (BK == 64) ? 2u : 4u;    // 128-B : 64-B swizzle
     constexpr int kKSteps = BK / 16;
     constexpr uint32_t a_bytes = BM * kRowBytes;
-    constexpr uint32_t b_bytes_max = BN_MAX * kRowBytes;
+    constexpr uint32_t b_bytes_max = bn_slot(MODE) * kRowBytes;
     constexpr uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes_max;
 
     extern __shared__ uint8_t smem_raw[];
@@ -551,9 +555,18 @@ bool tc_supported(int device) {
     return p.major == 10 && p.minor == 3;
 }
 
-size_t tc_smem_bytes(int BK, int stages) {
-    const size_t stage = (size_t)(2 * BM + 2 * BN_MAX) * BK * 2;
+static size_t smem_bytes_mode(int BK, int stages, int mode) {
+    const size_t stage = (size_t)(2 * BM + 2 * bn_slot(mode)) * BK * 2;
     return 1024 + stage * stages + kCtrlBytes;
+}
+
+size_t tc_smem_bytes(int BK, int stages) { return smem_bytes_mode(BK, stages, 0); }
+
+static int stages_mode(int BK, int mode) {
+    const size_t budget = 227 * 1024;
+    int stages = kMaxStages;
+    while (stages > 2 && smem_bytes_mode(BK, stages, mode) > budget) --stages;
+    return stages;
 }
 
 int tc_stages(int BK) {
@@ -655,7 +668,7 @@ template <int BK, int EPI, int DIM, int MODE = 0>
 static int launch_t(const TcGroup &g0, const TcGroup *groups, const TcTile *tiles, int ntiles, int stages,
                     int *err, int grid, cudaStream_t s) {
     auto kern = k_modeprod_tc<BK, EPI, DIM, MODE>;
-    kern<<<grid, kThreads, tc_smem_bytes(BK, stages), s>>>(g0, groups, tiles, ntiles, stages, err);
+    kern<<<grid, kThreads, smem_bytes_mode(BK, stages, MODE), s>>>(g0, groups, tiles, ntiles, stages, err);
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }
@@ -749,9 +762,10 @@ int launch_modeprod_tc_split(TcPlan *p, int src, int dst, Epi epi, const EpiArgs
         case EPI_DIVIDE:
             return launch_t<64, EPI_DIVIDE, 3, 1>(g, nullptr, nullptr, g.ntiles, p->stages, e.err, grid, s);
         case EPI_STORE_PQ:
-            return launch_t<64, EPI_STORE_PQ, 3, 2>(g, nullptr, nullptr, g.ntiles, p->stages, e.err, grid, s);
+            return launch_t<64, EPI_STORE_PQ, 3, 2>(g, nullptr, nullptr, g.ntiles, stages_mode(64, 2), e.err, grid, s);
         default:
-            return launch_t<64, EPI_UPDATE_PQ, 3, 2>(g, nullptr, nullptr, g.ntiles, p->stages, e.err, grid, s);
+            return launch_t<64, EPI_UPDATE_PQ, 3, 2>(g, nullptr, nullptr, g.ntiles, stages_mode(64, 2), e.err, grid,
+                                                      s);
     }
 }
 
