@@ -222,3 +222,52 @@ def grf_source_torch(n: int, seed: int, device="cuda", kmax: int = GRF_KMAX, sca
     t = torch.einsum("ky,akx->ayx", B, t)                           # [kz, y, x]
     f = torch.einsum("kz,kyx->zyx", B, t)                           # [z, y, x]
     return f * (scale / torch.sqrt(torch.mean(f * f)))
+
+
+# ---------------------------------------------------------------------------
+# Neumann workload: the three-dimensional Example 1 of Sec. 6.3
+# ---------------------------------------------------------------------------
+EX1_A = 10.0
+EX1_B = 10.0
+
+
+def neumann_nodes(n: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """n nodes x_i = lo + i h, i = 0..n-1, both ends included, h = (hi - lo)/(n - 1)
+    (the node set of the ghost-point Neumann discretisation, Sec. 3.2)."""
+    return lo + np.arange(n, dtype=np.float64) * ((hi - lo) / (n - 1))
+
+
+def ex1_potential_1d(x: np.ndarray) -> np.ndarray:
+    """One axis term of V = v(x) + v(y) + v(z), v(t) = 100 sin^2(pi t / 4) + t^2 (Sec. 6.3, Example 1)."""
+    return 100.0 * np.sin(0.25 * math.pi * x) ** 2 + x * x
+
+
+def ex1_problem(n: int, a: float = EX1_A, b: float = EX1_B):
+    """Data of -Lap u + a u + b u^3 + V u = f on (-1,1)^3 with zero normal derivative
+    (Sec. 6.3, Example 1), on n nodes per axis.
+
+    u* = cos(pi x) + cos(pi y) + cos(pi z) (zero normal derivative on the faces);
+    f is the continuous source -Lap u* + a u* + b u*^3 + V u* at the nodes, with
+    -Lap u* = pi^2 u*. Returns (u_star, f, v, h): 3-D arrays [z, y, x], the 1-D
+    potential table v (the same on every axis) and the mesh width h = 2/(n-1).
+    """
+    x = neumann_nodes(n)
+    c = np.cos(math.pi * x)
+    v = ex1_potential_1d(x)
+    u = c[None, None, :] + c[:, None, None] + c[None, :, None]
+    V = v[None, None, :] + v[None, :, None] + v[:, None, None]
+    f = (math.pi ** 2 + a) * u + b * u ** 3 + V * u
+    return u, f, v, 2.0 / (n - 1)
+
+
+def ex1_perturbation(n: int, seed: int, eps: float, degree: int = 4) -> np.ndarray:
+    """eps * p on the n^3 nodes of (-1,1)^3 (Sec. 6.3): p = q / max|q| with
+    q = sum_{i,j,k <= degree} c[k, j, i] x^i y^j z^k, c ~ U(-1, 1) drawn from
+    SplitMix64(seed) in C order (x power fastest); the maximum is taken over
+    the nodes, which include the corners of the cube."""
+    m = degree + 1
+    c = random_field((m, m, m), seed, -1.0, 1.0)
+    x = neumann_nodes(n)
+    Vp = np.vander(x, m, increasing=True)                     # Vp[node, power]
+    q = np.einsum("kji,zk,yj,xi->zyx", c, Vp, Vp, Vp, optimize=True)
+    return eps * q / float(np.max(np.abs(q)))

@@ -1,0 +1,159 @@
+"""Pins of the boundary / potential oracle (oracle.qn_oracle_bc) to facts that do not
+come from the oracle itself: closed-form eigenvalues, a general eigenvalue
+routine on the matrix of Sec. 3.2, Taylor consistency at the faces, the discrete
+divergence identity of the ghost-point scheme, dense linear algebra, the
+spectral radius that Sec. 5 says governs the linear iteration, and second-order
+convergence to the exact solution of the three-dimensional Example 1 (Sec. 6.3).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import qn_oracle as qo
+from oracle import qn_oracle_bc as ob
+from paper_2502_03611_gb300 import inputs as I
+
+
+@pytest.mark.parametrize("n", [2, 3, 8, 33])
+def test_neumann_eigenvalues_closed_form(n):
+    """DCT-I spectrum of the ghost-point matrix: (4/h^2) sin^2(k pi / (2(n-1))), k = 0..n-1."""
+    h = ob.mesh_width(n, "neumann", 2.0)
+    _, _, lam = ob.eig_1d(n, h, "neumann")
+    k = np.arange(n)
+    ref = 4.0 / h ** 2 * np.sin(k * math.pi / (2.0 * (n - 1))) ** 2
+    np.testing.assert_allclose(lam, ref, rtol=1e-12, atol=1e-12 / h ** 2)
+
+
+@pytest.mark.parametrize("n", [6, 21])
+def test_neumann_eigenvalues_general_routine(n):
+    """The non-symmetric matrix itself through a general (non-symmetric) eigenvalue routine."""
+    h = 0.3
+    H = ob.fd_matrix_1d(n, h, "neumann")
+    ev = np.linalg.eigvals(H)
+    assert np.max(np.abs(ev.imag)) < 1e-8 / h ** 2
+    _, _, lam = ob.eig_1d(n, h, "neumann")
+    np.testing.assert_allclose(np.sort(ev.real), lam, rtol=1e-10, atol=1e-10 / h ** 2)
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+def test_eig_factorisation(bc):
+    n = 11
+    h = ob.mesh_width(n, bc, 2.0)
+    H = ob.fd_matrix_1d(n, h, bc)
+    S, Si, lam = ob.eig_1d(n, h, bc)
+    np.testing.assert_allclose(H @ S, S * lam[None, :], atol=1e-10 / h ** 2)
+    np.testing.assert_allclose(Si @ S, np.eye(n), atol=1e-13)
+    if bc == "neumann":
+        assert np.max(np.abs(S - S.T)) > 1e-3      # not orthogonal: S^{-1} != S^T
+
+
+def test_neumann_rows_second_order_at_faces():
+    """u = cos(pi x) on [-1, 1] has zero slope at both faces and -u'' = pi^2 u. The
+    ghost-point matrix reproduces it to O(h^2) at every node, faces included (a
+    wrong face row leaves an O(1) error there)."""
+    errs = []
+    for n in (17, 33):
+        x = I.neumann_nodes(n)
+        h = ob.mesh_width(n, "neumann", 2.0)
+        u = np.cos(math.pi * x)
+        e = ob.fd_matrix_1d(n, h, "neumann") @ u - math.pi ** 2 * u
+        errs.append(np.max(np.abs(e)))
+        assert abs(e[0]) > 0.3 * errs[-1] and abs(e[-1]) > 0.3 * errs[-1]   # faces are not exempt
+    assert 3.6 < errs[0] / errs[1] < 4.4
+
+
+@pytest.mark.parametrize("bc,dim,n", [("neumann", 2, 6), ("neumann", 3, 4), ("dirichlet", 3, 4),
+                                      ("dirichlet", 2, 5)])
+def test_stencil_matches_kronecker(bc, dim, n):
+    """Stencil with ghost reflection (apply_operator) == Kronecker form (dense_operator)."""
+    h = ob.mesh_width(n, bc, 2.0)
+    U = I.random_field((n,) * dim, 7)
+    A = ob.dense_operator(n, dim, h, bc)
+    np.testing.assert_allclose(ob.apply_operator(U, h, bc).ravel(), A @ U.ravel(), atol=1e-11 / h ** 2)
+
+
+def test_neumann_discrete_divergence_and_constants():
+    """With zero flux the trapezoid-weighted sum of A_h U vanishes for every U (summation
+    by parts of the ghost-point scheme), and constants span the kernel of A_h."""
+    n = 7
+    h = ob.mesh_width(n, "neumann", 2.0)
+    U = I.random_field((n, n, n), 3)
+    w = ob.trapezoid_weights(n, "neumann")
+    W3 = w[:, None, None] * w[None, :, None] * w[None, None, :]
+    AU = ob.apply_operator(U, h, "neumann")
+    assert abs(float(np.sum(W3 * AU))) < 1e-12 * float(np.sum(np.abs(AU)))
+    assert np.max(np.abs(ob.apply_operator(np.full((n, n, n), 2.5), h, "neumann"))) < 1e-12
+
+
+@pytest.mark.parametrize("dim,n", [(2, 7), (3, 5)])
+def test_fast_diag_neumann_matches_dense_solve(dim, n):
+    h = ob.mesh_width(n, "neumann", 2.0)
+    r = I.random_field((n,) * dim, 11)
+    S, Si, lam = ob.eig_1d(n, h, "neumann")
+    shift = 3.7
+    v = qo.fast_diag_solve(r, S, Si, lam, shift)
+    ref = np.linalg.solve(ob.dense_operator(n, dim, h, "neumann", shift), r.ravel())
+    np.testing.assert_allclose(v.ravel(), ref, rtol=1e-11, atol=1e-13)
+
+
+def test_potential_axis_order():
+    n = 4
+    t = np.arange(n, dtype=np.float64)
+    V = ob.potential(np.stack([t, 10 * t, 100 * t]), 3, n)
+    assert V[3, 2, 1] == 1 + 20 + 300 and V[0, 1, 3] == 3 + 10
+    V2 = ob.potential(np.stack([t, 10 * t]), 2, n)
+    assert V2[2, 3] == 3 + 20
+
+
+def test_linear_iteration_rate_is_spectral_radius():
+    """b = 0: the iteration is linear, r_{k+1} = (I - (A_h + V)(A_h + (lam + beta) I)^{-1}) r_k
+    (Sec. 5, eq. error-update with R_n = 0). Its observed rate must equal the spectral
+    radius of that matrix with beta = mid-range of V; this pins V in both the residual
+    and the beta rule."""
+    n, lam = 5, 1.0
+    h = ob.mesh_width(n, "neumann", 2.0)
+    x = I.neumann_nodes(n)
+    v = np.stack([40 * x * x, 25 * (1 + x), 10 * np.cos(x)])
+    V = ob.potential(v, 3, n)
+    f = I.random_field((n, n, n), 5)
+    U, hist, ok = ob.qn_solve(f, h, "neumann", lam=lam, b=0.0, V=V, tol=1e-13, max_it=400)
+    assert ok
+    beta = 0.5 * (V.max() + V.min())
+    assert abs(hist[0]["beta"] - beta) < 1e-12 * beta
+    A = ob.dense_operator(n, 3, h, "neumann", lam)
+    M = np.eye(n ** 3) - (A + np.diag(V.ravel())) @ np.linalg.inv(A + beta * np.eye(n ** 3))
+    rho = float(np.max(np.abs(np.linalg.eigvals(M))))
+    rel = np.array([e["rel"] for e in hist])
+    k1 = len(rel) - 3
+    k0 = k1 - 15
+    rate = (rel[k1] / rel[k0]) ** (1.0 / (k1 - k0))
+    assert 0.5 < rho < 1.0
+    assert abs(rate - rho) < 0.03 * rho
+
+
+@pytest.mark.parametrize("bc", ["neumann", "dirichlet"])
+def test_qn_fixed_point_is_newton_solution(bc):
+    """The quasi-Newton limit solves F(U) = 0: it agrees with dense Newton (eq. newton)."""
+    n = 5
+    h = ob.mesh_width(n, bc, 2.0)
+    x = I.neumann_nodes(n) if bc == "neumann" else -1.0 + h * np.arange(1, n + 1)
+    V = ob.potential(I.ex1_potential_1d(x), 3, n)
+    f = 50.0 * I.random_field((n, n, n), 9)
+    U, _, ok = ob.qn_solve(f, h, bc, lam=10.0, b=10.0, V=V, tol=1e-13, max_it=2000)
+    assert ok
+    Un = ob.newton_dense(f, h, bc, lam=10.0, b=10.0, V=V, tol=1e-14)
+    np.testing.assert_allclose(U, Un, atol=1e-11 * np.max(np.abs(Un)))
+
+
+def test_ex1_converges_at_second_order():
+    """Example 1 of Sec. 6.3: the discrete solution tends to u* = cos(pi x) + cos(pi y) + cos(pi z)
+    as h^2 (error ratio ~4 when h halves)."""
+    errs = []
+    for n in (9, 17):
+        u, f, v, h = I.ex1_problem(n)
+        V = ob.potential(v, 3, n)
+        U, hist, ok = ob.qn_solve(f, h, "neumann", lam=I.EX1_A, b=I.EX1_B, V=V, tol=1e-12, max_it=1000)
+        assert ok
+        errs.append(float(np.max(np.abs(U - u))))
+    assert 3.3 < errs[0] / errs[1] < 4.7
