@@ -7,14 +7,20 @@
  * and Systems" (arXiv 2502.03611).
  *
  * Problem solved (Sec. 2 eq. main-pde, Sec. 3.2, Sec. 4 eq. F_u):
- *   -Lap u + lam u + b u^3 = f   on (0,1)^dim, u = 0 on the boundary,
- * discretised by second-order central differences (5-point in 2-D, 7-point in
- * 3-D, eq. fdm-discrete) on n interior nodes per axis, h = 1/(n+1):
+ *   -Lap u + lam u + b u^3 + V u = f   on a cube of side L (default (0,1)^dim),
+ * with u = 0 on the boundary (QN_BC_DIRICHLET) or a zero normal derivative
+ * (QN_BC_NEUMANN), and V an optional separable potential
+ * V(x, y, z) = v_x(x) + v_y(y) + v_z(z). Discretised by second-order central
+ * differences (5-point in 2-D, 7-point in 3-D, eq. fdm-discrete) on n nodes
+ * per axis: Dirichlet n interior nodes, h = L/(n+1); Neumann n nodes with
+ * both faces included, h = L/(n-1), the value past a face taken from the
+ * ghost point u_{-1} = u_1 (Sec. 3.2, Neumann rows):
  *   F(U) = A_h vec(U) + N_h(U),  A_h = sum_a I..H_a..I + lam I,
- *   H_a = (1/h^2) tridiag(-1, 2, -1),  N_h(U) = b U^3 - f.
+ *   H_a = (1/h^2) tridiag(-1, 2, -1) (Neumann: first row (2, -2), last
+ *   row (-2, 2)),  N_h(U) = b U^3 + V U - f.
  * Quasi-Newton update (Sec. 4 eq. identity-method):
  *   U <- U - step * (A_h + beta_n I)^{-1} F(U),
- *   beta_n = (lambda_max + lambda_min)/2 of (N_h)_U = diag(3 b U^2),
+ *   beta_n = (lambda_max + lambda_min)/2 of (N_h)_U = diag(3 b U^2 + V),
  * with the inverse applied by fast diagonalisation (Sec. 4.1 eq. fin_inverse):
  * mode products with S^{-1} along every axis, pointwise division by
  * (sum_a lambda_{i_a} + lam + beta_n), mode products with S along every axis.
@@ -54,6 +60,9 @@ extern "C" {
 
 /* ---- enumerations -------------------------------------------------------- */
 #define QN_BC_DIRICHLET 0   /* homogeneous Dirichlet, interior unknowns only (Sec. 3.2) */
+#define QN_BC_NEUMANN   1   /* zero normal derivative by ghost points, face nodes are unknowns
+                               (Sec. 3.2, Neumann rows with alpha_3 = 0; a nonzero flux only
+                               adds a constant to f at the face nodes, so pass it in f) */
 
 #define QN_PREC_FP64   0    /* mode products in FP64 on the FP64 pipe */
 #define QN_PREC_BF16X3 1    /* mode products on tcgen05 tensor cores as
@@ -61,23 +70,28 @@ extern "C" {
                                accumulation; residual, beta, update and stop
                                test stay FP64 (outer loop = iterative refinement) */
 
-#define QN_BETA_PAPER 0     /* beta_n = (max + min)/2 of diag(3 b U^2) (eq. identity-method) */
+#define QN_BETA_PAPER 0     /* beta_n = (max + min)/2 of diag(3 b U^2 + V) (eq. identity-method) */
 #define QN_BETA_FIXED 1     /* beta_n = qn_opts.beta_value every iteration */
 
 /* ---- structures ------------------------------------------------------------ */
 typedef struct qn_problem {
     int dim;          /* 2 or 3 */
-    int n;            /* interior nodes per axis, 1 <= n <= 1024 (same on every axis) */
-    int bc;           /* QN_BC_DIRICHLET */
+    int n;            /* unknowns per axis (same on every axis): Dirichlet 1..1024 interior
+                         nodes, Neumann 2..1024 nodes with both faces */
+    int bc;           /* QN_BC_DIRICHLET or QN_BC_NEUMANN */
     int precision;    /* QN_PREC_FP64 or QN_PREC_BF16X3 */
-    double lam;       /* linear coefficient lam of -Lap u + lam u + b u^3 = f */
+    double lam;       /* linear coefficient lam of -Lap u + lam u + b u^3 + V u = f */
     double b;         /* cubic coefficient b */
+    double length;    /* side L of the cubic domain; 0 selects 1 (the unit cube) */
+    const double *potential_host;   /* NULL (V = 0) or host array of dim*n doubles: the
+                         1-D tables v_x[n], v_y[n](, v_z[n]) of V = v_x + v_y (+ v_z) at the
+                         nodes, x first. Copied by qn_ctx_create; the caller keeps it. */
 } qn_problem;
 
 typedef struct qn_stats {
     double res_norm;  /* ||F(U)||_2 at the evaluated iterate */
     double f_norm;    /* ||f||_2 */
-    double fu_min;    /* smallest entry of diag(N_h)_U = 3 b U^2 */
+    double fu_min;    /* smallest entry of diag(N_h)_U = 3 b U^2 + V */
     double fu_max;    /* largest entry */
     double beta;      /* beta_n applied to this iterate (paper rule or fixed) */
     double rel;       /* res_norm / f_norm */
@@ -113,11 +127,18 @@ int qn_version(void);
 /* Message for the last failing call on this thread ("" if none). Owned by the library. */
 const char *qn_last_error(void);
 
-/* 1-D diagonalisation H = S diag(lam) S^{-1} (Sec. 4.2; H from Sec. 3.2 eq. Sy).
- * Host-only, FP64. n >= 1; h must equal 1/(n+1) (checked to 1e-12 relative).
- * For QN_BC_DIRICHLET the eigenpairs are the closed-form discrete sine pairs
- * lam_k = (4/h^2) sin^2(k pi h/2), S[j][k] = sqrt(2h) sin(j k pi h) (1-based
- * j, k), ascending in k; S is symmetric orthogonal so S_inv = S.
+/* 1-D diagonalisation H = S diag(lam) S^{-1} (Sec. 4.2; H from Sec. 3.2 eq. Sy
+ * and the Neumann rows). Host-only, FP64. h > 0 is the mesh width (it scales
+ * lam only); n >= 1 (Dirichlet) or n >= 2 (Neumann). Closed forms, ascending
+ * in k:
+ *  QN_BC_DIRICHLET (discrete sine pairs, 1-based j, k, t = 1/(n+1)):
+ *    lam_k = (4/h^2) sin^2(k pi t/2), S[j][k] = sqrt(2t) sin(j k pi t);
+ *    S is symmetric orthogonal, S_inv = S.
+ *  QN_BC_NEUMANN (discrete cosine pairs, 0-based j, k, t = 1/(n-1)):
+ *    lam_k = (4/h^2) sin^2(k pi t/2), S[j][k] = cos(j k pi t) / sqrt(c_k),
+ *    S_inv[k][j] = w_j cos(j k pi t) / sqrt(c_k), with w_j = 1/2 at the two
+ *    faces and 1 elsewhere, c_k = (n-1)/2, or n-1 for k = 0 and k = n-1.
+ *    S is not orthogonal (W^{1/2} S is), lam_0 = 0 (constants).
  * S, S_inv: caller-owned host buffers of n*n doubles, row-major (S[j*n+k]).
  * lam: caller-owned host buffer of n doubles. Any output may be NULL. */
 int qn_setup_1d_eig(int n, double h, int bc, double *S, double *S_inv, double *lam);
@@ -133,10 +154,10 @@ int qn_ctx_create(const qn_problem *p, qn_ctx **out);
 /* Free everything the context owns. NULL is accepted. Synchronises the device. */
 int qn_ctx_destroy(qn_ctx *ctx);
 
-/* Residual F(U) = A_h vec(U) + lam U + b U^3 - f (Sec. 4 eq. F_u) in FP64.
+/* Residual F(U) = A_h vec(U) + lam U + b U^3 + V U - f (Sec. 4 eq. F_u) in FP64.
  * U, f: device, n^dim doubles. R: device, n^dim doubles, or NULL to compute
  * only the statistics. st (host, may be NULL): norms and extreme entries of
- * diag(3 b U^2); beta is the paper's beta_n for U. Synchronises `stream`
+ * diag(3 b U^2 + V); beta is the paper's beta_n for U. Synchronises `stream`
  * when st != NULL. */
 int qn_residual(qn_ctx *ctx, const double *U, const double *f, double *R,
                 qn_stats *st, void *stream);
@@ -145,7 +166,8 @@ int qn_residual(qn_ctx *ctx, const double *U, const double *f, double *R,
  * V = (sum_a I..H_a..I + shift I)^{-1} r, i.e. A_h without lam, plus shift.
  * r, V: device, n^dim doubles, distinct. Runs in the context's precision
  * (FP64 or BF16X3 mode products). shift must be finite and
- * > -dim * lambda_min(H). Does not synchronise. */
+ * > -dim * lambda_min(H) (> 0 for Neumann data, where lambda_min = 0).
+ * Does not synchronise. */
 int qn_fast_diag_solve(qn_ctx *ctx, const double *r, double *V, double shift, void *stream);
 
 /* One quasi-Newton update in place (Sec. 4 eq. identity-method):
@@ -304,7 +326,9 @@ int qn_interp3d_f32(const double *src, int m_from, float *dst, int m_to, int B, 
  * from the zero start (*used_warm = 0). ||F(U0)|| is not the criterion: the
  * trilinear prolongation leaves high-frequency error that A_h amplifies in
  * the residual while the first correction removes it. ctx: 3-D context with
- * the same n. U, f: device, n^3. Uses stream-ordered temporary memory. */
+ * the same n, Dirichlet data on the unit cube and no potential (the network's
+ * basis; QN_EUNSUPPORTED otherwise). U, f: device, n^3. Uses stream-ordered
+ * temporary memory. */
 int qn_solve_warm(qn_ctx *ctx, qn_net *net, double *U, const double *f, int n, double in_scale,
                   double out_scale, const qn_opts *opts, qn_result *res, int *used_warm, void *stream);
 

@@ -102,6 +102,10 @@ struct qn_ctx {
     int last_split;       // 1: the last shifted inverse used the split products
     __nv_bfloat16 *bf_hi, *bf_lo, *bb_hi, *bb_lo;   // [P][P/2] forward / backward matrices
     float *lam32_split;   // eigenvalues in split mode order (even modes, then odd), 1e30 padding
+    // separable potential V = v_x + v_y (+ v_z): device tables [dim][n], FP64 and as FP32
+    // pairs with lam added to the last axis (k_residual_tiled / mirror); nullptr: V = 0
+    double *pot64;
+    float2 *pot2;
 };
 
 enum ProfKind { PK_RESIDUAL = 0, PK_FINALIZE = 1, PK_MP_STORE = 2, PK_MP_DIVIDE = 3, PK_MP_LAST = 4,
@@ -142,29 +146,52 @@ static void split_host(double v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
     lo = __float2bfloat16_rn(f - __bfloat162float(hi));
 }
 
-extern "C" int qn_version(void) { return 10000; }
+extern "C" int qn_version(void) { return 10100; }
 
 extern "C" const char *qn_last_error(void) { return g_err; }
 
 extern "C" int qn_setup_1d_eig(int n, double h, int bc, double *S, double *S_inv, double *lam) {
-    if (n < 1 || n > 65536) {
+    if (n < 1 || n > 65536 || (bc == QN_BC_NEUMANN && n < 2)) {
         set_error("qn_setup_1d_eig: n=%d out of range", n);
         return QN_EINVAL;
     }
-    const double hh = 1.0 / (n + 1);
-    if (!(fabs(h - hh) <= 1e-12 * hh)) {
-        set_error("qn_setup_1d_eig: h=%.17g but 1/(n+1)=%.17g", h, hh);
+    if (!(h > 0.0) || !isfinite(h)) {
+        set_error("qn_setup_1d_eig: h=%.17g must be positive and finite", h);
         return QN_EINVAL;
     }
-    if (bc != QN_BC_DIRICHLET) {
-        set_error("qn_setup_1d_eig: only QN_BC_DIRICHLET is implemented");
-        return QN_EUNSUPPORTED;
+    if (bc != QN_BC_DIRICHLET && bc != QN_BC_NEUMANN) {
+        set_error("qn_setup_1d_eig: unknown boundary condition %d", bc);
+        return QN_EINVAL;
     }
     const double pi = 3.14159265358979323846;
+    if (bc == QN_BC_NEUMANN) {
+        // discrete cosine pairs of the ghost-point matrix: H cos(j k pi t) =
+        // lam_k cos(j k pi t) in every row (the face rows because the ghost
+        // value equals the inner neighbour); the columns are orthogonal in the
+        // trapezoid weights w, with squared norms c_k
+        const double t = 1.0 / (n - 1);
+        for (int k = 0; k < n; ++k) {
+            const double sk = sin(0.5 * k * pi * t);
+            if (lam) lam[k] = 4.0 / (h * h) * sk * sk;
+        }
+        for (int j = 0; j < n; ++j) {
+            const double w = (j == 0 || j == n - 1) ? 0.5 : 1.0;
+            for (int k = 0; k < n; ++k) {
+                const double ck = (k == 0 || k == n - 1) ? (double)(n - 1) : 0.5 * (n - 1);
+                // cos(j k pi t) with the product reduced mod 2(n-1)
+                const long long jk = ((long long)j * k) % (2LL * (n - 1));
+                const double v = cos(pi * (double)jk * t) / sqrt(ck);
+                if (S) S[(size_t)j * n + k] = v;
+                if (S_inv) S_inv[(size_t)k * n + j] = w * v;
+            }
+        }
+        return QN_OK;
+    }
+    const double hh = 1.0 / (n + 1);
     const double scale = sqrt(2.0 * hh);
     for (int k = 1; k <= n; ++k) {
         const double s = sin(0.5 * k * pi * hh);
-        if (lam) lam[k - 1] = 4.0 / (hh * hh) * s * s;
+        if (lam) lam[k - 1] = 4.0 / (h * h) * s * s;
     }
     for (int j = 1; j <= n; ++j) {
         for (int k = 1; k <= n; ++k) {
@@ -193,6 +220,8 @@ static void ctx_free(qn_ctx *c) {
     cudaFree(c->bb_hi);
     cudaFree(c->bb_lo);
     cudaFree(c->lam32_split);
+    cudaFree(c->pot64);
+    cudaFree(c->pot2);
     for (int b = 0; b < 2; ++b) {
         cudaFree(c->w64[b]);
         cudaFree(c->bhi[b]);
@@ -239,13 +268,25 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
         set_error("qn_ctx_create: dim must be 2 or 3 (got %d)", p->dim);
         return QN_EINVAL;
     }
-    if (p->n < 1 || p->n > 1024) {
-        set_error("qn_ctx_create: n must be in [1, 1024] (got %d)", p->n);
+    if (p->bc != QN_BC_DIRICHLET && p->bc != QN_BC_NEUMANN) {
+        set_error("qn_ctx_create: unknown boundary condition %d", p->bc);
         return QN_EINVAL;
     }
-    if (p->bc != QN_BC_DIRICHLET) {
-        set_error("qn_ctx_create: only QN_BC_DIRICHLET is implemented");
-        return QN_EUNSUPPORTED;
+    const int nmin = (p->bc == QN_BC_NEUMANN) ? 2 : 1;
+    if (p->n < nmin || p->n > 1024) {
+        set_error("qn_ctx_create: n must be in [%d, 1024] (got %d)", nmin, p->n);
+        return QN_EINVAL;
+    }
+    if (!(p->length >= 0.0) || !isfinite(p->length)) {
+        set_error("qn_ctx_create: length must be finite and >= 0 (0 = unit cube)");
+        return QN_EINVAL;
+    }
+    if (p->potential_host) {
+        for (long long i = 0; i < (long long)p->dim * p->n; ++i)
+            if (!isfinite(p->potential_host[i])) {
+                set_error("qn_ctx_create: potential table entry %lld is not finite", i);
+                return QN_EINVAL;
+            }
     }
     if (p->precision != QN_PREC_FP64 && p->precision != QN_PREC_BF16X3) {
         set_error("qn_ctx_create: unknown precision %d", p->precision);
@@ -290,7 +331,11 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
         c->N *= c->n;
         c->NP *= c->P;
     }
-    c->h = 1.0 / (c->n + 1);
+    {
+        const double L = (p->length > 0.0) ? p->length : 1.0;
+        c->h = (p->bc == QN_BC_NEUMANN) ? L / (c->n - 1) : L / (c->n + 1);
+    }
+    c->prob.potential_host = nullptr;   // not retained
     c->inv_h2 = 1.0 / (c->h * c->h);
     const int n = c->n, P = c->P;
 
@@ -306,6 +351,27 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
     CK(cudaMemcpy(c->S64, S.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->Si64, Si.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->lam64, lam.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    double vmax = 0.0;   // bound on |lam + V| (range check of the float-pair residual)
+    if (p->potential_host) {
+        const int dn = c->dim * n;
+        std::vector<float2> v2(dn);
+        double vsum = fabs(p->lam);
+        for (int ax = 0; ax < c->dim; ++ax) {
+            double m = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const double v = p->potential_host[ax * n + i] + ((ax == 2) ? p->lam : 0.0);
+                const float hi = (float)v;
+                v2[ax * n + i] = make_float2(hi, (float)(v - (double)hi));
+                m = fmax(m, fabs(p->potential_host[ax * n + i]));
+            }
+            vsum += m;
+        }
+        vmax = vsum;
+        CK(cudaMalloc(&c->pot64, sizeof(double) * dn));
+        CK(cudaMalloc(&c->pot2, sizeof(float2) * dn));
+        CK(cudaMemcpy(c->pot64, p->potential_host, sizeof(double) * dn, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->pot2, v2.data(), sizeof(float2) * dn, cudaMemcpyHostToDevice));
+    }
 
     const int rows = (c->dim == 3) ? P * P : P;
     c->nparts = rows < 4 * c->num_sms ? rows : 4 * c->num_sms;
@@ -353,7 +419,8 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
             CK(cudaMemset(c->blo[b], 0, pb));
         }
         // the float-pair residual needs lam, b and 1/h^2 well inside the FP32 range
-        const bool pair_ok = fabs(p->lam) < 0x1p40 && fabs(p->b) < 0x1p20 && c->inv_h2 < 0x1p24;
+        const bool pair_ok = fabs(p->lam) < 0x1p40 && fabs(p->b) < 0x1p20 && c->inv_h2 < 0x1p24 &&
+                             vmax < 0x1p40;
         if (c->dim == 3 && pair_ok) {
             CK(cudaMalloc(&c->fdf, sizeof(float2) * (size_t)c->NP));
         } else {
@@ -366,11 +433,13 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
             return rc;
         }
         // Reflection-split matrices (qn_modeprod_tc.cu): with H = P/2,
-        //   forward  Bf[p][j]: p < H -> S[j][2p] for j < ceil(n/2) (the middle
-        //            column of an odd n included); p >= H -> S[j][2(p-H)+1], j < n/2
+        //   forward  Bf[p][j]: p < H -> S^{-1}[2p][j] for j < ceil(n/2) (the middle
+        //            column of an odd n included); p >= H -> S^{-1}[2(p-H)+1][j], j < n/2
         //   backward Bb[r][i]: r < H -> S[r][2i] (r < ceil(n/2));
         //            r >= H -> S[r-H][2i+1] (r-H < n/2)
-        // (S symmetric), and the eigenvalues in the same mode order.
+        // and the eigenvalues in the same mode order. Both the sine (Dirichlet)
+        // and the cosine (Neumann) pairs have S[n-1-j][k] = (-1)^k S[j][k] and
+        // S^{-1}[k][n-1-j] = (-1)^k S^{-1}[k][j].
         const char *es = getenv("QN_SPLIT");
         const bool want_split = es ? (atoi(es) != 0) : true;
         if (want_split && c->dim == 3 && P % 128 == 0 && c->fdf != nullptr) {
@@ -382,7 +451,7 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
                 const int jmax = (p < H) ? nsym : nanti;
                 if (k < n) ls[p] = (float)lam[k];
                 for (int j = 0; j < H; ++j) {
-                    const double v = (k < n && j < jmax) ? S[(size_t)j * n + k] : 0.0;
+                    const double v = (k < n && j < jmax) ? Si[(size_t)k * n + j] : 0.0;
                     split_host(v, fh[(size_t)p * H + j], fl[(size_t)p * H + j]);
                 }
             }
@@ -493,6 +562,10 @@ static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double 
     a.fdf = split_solve ? c->fdf : nullptr;
     a.fx_fbad = &c->st->fx_fbad;
     a.fx_e = &c->st->fx_e;
+    a.bc = c->prob.bc;
+    a.pot = c->pot64;
+    a.pot2 = c->pot2;
+    a.umax_scan = &c->st->umax_scan;
     // 3-D split solve: the residual without FP64 arithmetic (k_residual_tiled)
     // in every iteration. It needs the FP32-pair copy of f and a fixed-point
     // exponent from max|U|: iteration 0 prepares both in one pass over f and
@@ -591,7 +664,7 @@ static int enqueue_iteration(qn_ctx *c, double *U, const double *f, double step,
     if (rc) return rc;
     const long pr = prof_begin(c, PK_FINALIZE, s);
     rc = launch_finalize(c->partials, c->res_parts, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 1,
-                         c->res_saved_fnorm, s);
+                         c->res_saved_fnorm, c->pot64 != nullptr, s);
     prof_end(c, pr, s);
     if (rc) return rc;
     return enqueue_inverse(c, nullptr, U, true, step, s, c->split_layout != 0);
@@ -668,7 +741,8 @@ extern "C" int qn_residual(qn_ctx *c, const double *U, const double *f, double *
     rc = enqueue_residual(c, U, f, R, false, nullptr, s);
     if (rc) return rc;
     const long pr = prof_begin(c, PK_FINALIZE, s);
-    rc = launch_finalize(c->partials, c->res_parts, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 0, 0, s);
+    rc = launch_finalize(c->partials, c->res_parts, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 0, 0,
+                         c->pot64 != nullptr, s);
     prof_end(c, pr, s);
     if (rc) return rc;
     if (st) {
@@ -689,8 +763,10 @@ extern "C" int qn_fast_diag_solve(qn_ctx *c, const double *r, double *V, double 
         set_error("qn_fast_diag_solve: shift must be finite");
         return QN_EINVAL;
     }
-    // smallest eigenvalue of sum_a H_a is dim * lambda_1
-    const double l1 = 4.0 / (c->h * c->h) * pow(sin(0.5 * 3.14159265358979323846 * c->h), 2);
+    // smallest eigenvalue of sum_a H_a is dim * lambda_1 (0 for Neumann data: constants)
+    const double l1 = (c->prob.bc == QN_BC_NEUMANN)
+                          ? 0.0
+                          : 4.0 / (c->h * c->h) * pow(sin(0.5 * 3.14159265358979323846 / (c->n + 1)), 2);
     if (!(shift > -c->dim * l1)) {
         set_error("qn_fast_diag_solve: shift %.6g makes the operator singular or indefinite", shift);
         return QN_EINVAL;
@@ -739,6 +815,11 @@ extern "C" int qn_step(qn_ctx *c, double *U, const double *f, double beta, qn_st
 }
 
 bool qn::ctx_split_precision(const qn_ctx *c) { return c != nullptr && c->prob.precision == QN_PREC_BF16X3; }
+
+bool qn::ctx_unit_dirichlet(const qn_ctx *c) {
+    return c != nullptr && c->prob.bc == QN_BC_DIRICHLET && c->pot64 == nullptr &&
+           fabs(c->h * (c->n + 1) - 1.0) < 1e-12;
+}
 
 extern "C" int qn_solve(qn_ctx *c, double *U, const double *f, const qn_opts *opts, qn_result *res,
                         qn_stats *history, int history_len, void *stream) {

@@ -58,6 +58,14 @@ struct ResidualArgs {
     int *fx_fbad;              // set when some |f| does not fit the FP32-pair copy
     const int *fx_e;           // DevState::fx_e (k_residual_tiled)
     const int *r2_exp;         // DevState::r2_exp (fast == 1)
+    int bc;                    // QN_BC_DIRICHLET (0 past a face) or QN_BC_NEUMANN (the ghost
+                               // value past face node 0 is node 1, past node n-1 node n-2)
+    const double *pot;         // separable potential: 1-D tables [dim][n], x first (nullptr: V = 0).
+                               // With it the partial records hold min / max of 3 b U^2 + V in
+                               // their slots 2 and 3, and max|U| goes to *umax_scan
+    const float2 *pot2;        // the same tables as FP32 pairs (hi, lo), lam added to the last
+                               // axis' table: [dim][n] (k_residual_tiled / k_residual_mirror)
+    unsigned long long *umax_scan;   // DevState::umax_scan (atomicMax of |U| bit patterns)
 };
 
 // Epilogue selector shared by both mode-product kernels.
@@ -109,9 +117,11 @@ int launch_prep_split(const double *U, const double *f, int n, int P, float2 *fd
 // and z, the input layout of the reflection-split mode products.
 int launch_residual_mirror(const ResidualArgs &a, int max_grid, int zchunk, int *grid_used, cudaStream_t s);
 int launch_umax(const double *U, long long N, DevState *st, int grid, cudaStream_t s);
+// pot: the partial records hold min / max of 3 b U^2 + V (a potential is present) and the
+// fixed-point exponent comes from DevState::umax_scan; else they hold min / max U^2.
 int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *hist,
                     int hist_cap, double b, double lam, int update_state, int use_saved_fnorm,
-                    cudaStream_t s);
+                    int pot, cudaStream_t s);
 int launch_split_pad(const double *r, int n, int P, int dim, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
                      int grid, cudaStream_t s);
 int launch_modeprod_f64(const double *A, const double *B, double *out, const GemmShape &g,
@@ -176,6 +186,8 @@ bool tc_supported(int device);
 int solve_internal(::qn_ctx *c, double *U, const double *f, const qn_opts *opts, qn_result *res,
                    qn_stats *history, int history_len, void *stream, const double *u0_sq, int *used_warm);
 bool ctx_split_precision(const ::qn_ctx *c);
+// Dirichlet data on the unit cube and no potential (the learned warm start's setting)
+bool ctx_unit_dirichlet(const ::qn_ctx *c);
 
 // error reporting
 void set_error(const char *fmt, ...);

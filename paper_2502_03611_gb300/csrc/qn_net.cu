@@ -800,6 +800,10 @@ extern "C" int qn_solve_warm(qn_ctx *ctx, qn_net *net, double *U, const double *
         set_error("qn_solve_warm: invalid arguments");
         return QN_EINVAL;
     }
+    if (!ctx_unit_dirichlet(ctx)) {
+        set_error("qn_solve_warm: the network predicts Dirichlet solutions on the unit cube without a potential");
+        return QN_EUNSUPPORTED;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const long long N = (long long)n * n * n;
     int rc = qn_net_predict(net, f, n, in_scale, out_scale, U, stream);

@@ -1,8 +1,9 @@
-// Residual F(U) = A_h vec(U) + lam U + b U^3 - f (Sec. 4 eq. F_u, with the
-// 5/7-point difference operator of Sec. 3.2 eq. fdm-discrete, Dirichlet 0)
-// fused with the reductions the iteration needs: sum F^2 and sum f^2 (stop
-// test) and min/max U^2 (beta_n = mid-range of diag(3 b U^2), Sec. 4
-// eq. identity-method). One pass over U and f; HBM-bound.
+// Residual F(U) = A_h vec(U) + lam U + b U^3 + V U - f (Sec. 4 eq. F_u, with
+// the 5/7-point difference operator of Sec. 3.2 eq. fdm-discrete: Dirichlet 0
+// past a face, or the ghost-point reflection of the Neumann rows) fused with
+// the reductions the iteration needs: sum F^2 and sum f^2 (stop test) and
+// min/max U^2, or min/max of 3 b U^2 + V with a potential (beta_n = mid-range
+// of diag(N_h)_U, Sec. 4 eq. identity-method). One pass over U and f.
 //
 // Outputs, selected per launch:
 //   R64           dense FP64 residual (FP64 path, qn_residual)
@@ -59,6 +60,29 @@ __device__ Red4 block_reduce(Red4 v) {
     return v;
 }
 
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// Block-wide max (blockDim.x a multiple of 32, <= 1024); result valid in thread 0.
+__device__ unsigned long long block_max_u64(unsigned long long v) {
+    __shared__ unsigned long long sh[32];
+    v = warp_max_u64(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0ull;
+        v = warp_max_u64(v);
+    }
+    return v;
+}
+
 // FP64-pipe budget per interior point (the GPU issues ~2 FP64 ops/clk/SM).
 // Two implementations of the stencil 2d*u - sum(neighbours), run by different
 // warps of the same block so that the FP64 pipe and the integer pipe work at
@@ -73,7 +97,8 @@ __device__ Red4 block_reduce(Red4 v) {
 // rounding of r runs on the integer pipe. Each warp sweeps its own columns
 // with one of the two loops (a warp-uniform branch around the whole loop, so
 // neither variant is predicated into the other).
-// KIND 0: lam u + b u^3 (general); 1: lam = 0; 2: lam = 0 and b = 1.
+// KIND 0: lam u + b u^3 (general); 1: lam = 0; 2: lam = 0 and b = 1;
+// 3: (lam + V) u + b u^3 with the separable potential V.
 // f as an unevaluated pair of floats hi + lo (48 significant bits), the form
 // k_residual_tiled reads; |f| >= 2^100 (or inf/nan) marks the copy unusable.
 static __device__ __noinline__ void flag_fbad(int *flag) {
@@ -109,6 +134,7 @@ struct ResAcc {
     float kr2, kc;
     unsigned long long amin, amax;
     float r2s;   // 2^-r2_exp: r is scaled before its FP32 square
+    double dmn, dmx;   // KIND 3: extremes of 3 b u^2 + V
 };
 
 template <int DIM, bool SPLIT, bool FAST, int KIND, bool WANT_F2, bool INT_STENCIL>
@@ -119,24 +145,32 @@ __device__ __forceinline__ void residual_sweep(const ResidualArgs &a, ResAcc &s)
     const double *__restrict__ U = a.U;
     const double *__restrict__ f = a.f;
     const long long nn = (long long)n * n;
+    // Neumann faces: the missing neighbour is the ghost value, i.e. the
+    // neighbour on the other side (n >= 2 is guaranteed for Neumann data)
+    const bool neu = (a.bc == QN_BC_NEUMANN);
     for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
         const int y = (DIM == 3) ? (int)(row % P) : (int)row;
         const int z = (DIM == 3) ? (int)(row / P) : 0;
         const bool row_ok = (y < n) && (z < n);
         const long long cbase = ((long long)z * n + y) * n;
+        double vrow = 0.0;   // KIND 3: lam + v_y(y) + v_z(z)
+        if (KIND == 3 && row_ok) {
+            vrow = a.lam + __ldg(a.pot + n + y);
+            if (DIM == 3) vrow += __ldg(a.pot + 2 * n + z);
+        }
         for (int x = threadIdx.x; x < P; x += blockDim.x) {
             double r = 0.0;
             if (row_ok && x < n) {
                 const long long c = cbase + x;
                 const double u = __ldg(U + c);
                 double nbv[2 * DIM];
-                nbv[0] = (x > 0) ? __ldg(U + c - 1) : 0.0;
-                nbv[1] = (x < n - 1) ? __ldg(U + c + 1) : 0.0;
-                nbv[2] = (y > 0) ? __ldg(U + c - n) : 0.0;
-                nbv[3] = (y < n - 1) ? __ldg(U + c + n) : 0.0;
+                nbv[0] = (x > 0) ? __ldg(U + c - 1) : (neu ? __ldg(U + c + 1) : 0.0);
+                nbv[1] = (x < n - 1) ? __ldg(U + c + 1) : (neu ? __ldg(U + c - 1) : 0.0);
+                nbv[2] = (y > 0) ? __ldg(U + c - n) : (neu ? __ldg(U + c + n) : 0.0);
+                nbv[3] = (y < n - 1) ? __ldg(U + c + n) : (neu ? __ldg(U + c - n) : 0.0);
                 if (DIM == 3) {
-                    nbv[2 * DIM - 2] = (z > 0) ? __ldg(U + c - nn) : 0.0;
-                    nbv[2 * DIM - 1] = (z < n - 1) ? __ldg(U + c + nn) : 0.0;
+                    nbv[2 * DIM - 2] = (z > 0) ? __ldg(U + c - nn) : (neu ? __ldg(U + c + nn) : 0.0);
+                    nbv[2 * DIM - 1] = (z < n - 1) ? __ldg(U + c + nn) : (neu ? __ldg(U + c - nn) : 0.0);
                 }
                 const double fv = __ldg(f + c);
                 double lap;
@@ -154,6 +188,13 @@ __device__ __forceinline__ void residual_sweep(const ResidualArgs &a, ResAcc &s)
                 } else {
                     t = fma(a.b, u2 * u, -fv);
                     if (KIND == 0) t = fma(a.lam, u, t);
+                }
+                if (KIND == 3) {
+                    const double cv = vrow + __ldg(a.pot + x);        // lam + V
+                    t = fma(cv, u, t);
+                    const double d = fma(3.0 * a.b, u2, cv - a.lam);  // 3 b u^2 + V
+                    s.dmn = fmin(s.dmn, d);
+                    s.dmx = fmax(s.dmx, d);
                 }
                 r = fma(lap, a.inv_h2, t);
                 const unsigned long long ab = abs_bits(u);
@@ -187,7 +228,8 @@ template <int DIM, bool SPLIT, bool FAST, int KIND, bool WANT_F2>
 __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
     if (a.done != nullptr && *(volatile const int *)a.done) return;
     const int r2k = FAST ? *a.r2_exp : 0;
-    ResAcc s{0.0, 0.0, 0.0f, 0.0f, 0x7FFFFFFFFFFFFFFFull, 0ull, __int_as_float((127 - r2k) << 23)};
+    ResAcc s{0.0, 0.0, 0.0f, 0.0f, 0x7FFFFFFFFFFFFFFFull, 0ull, __int_as_float((127 - r2k) << 23),
+             INFINITY, -INFINITY};
     if ((int)(threadIdx.x >> 5) < a.fp64_warps)
         residual_sweep<DIM, SPLIT, FAST, KIND, WANT_F2, false>(a, s);
     else
@@ -196,6 +238,12 @@ __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
     const double umin = __longlong_as_double((long long)s.amin);
     const double umax = __longlong_as_double((long long)s.amax);
     Red4 acc{s.r2, s.f2, (s.amin == 0x7FFFFFFFFFFFFFFFull) ? INFINITY : umin * umin, umax * umax};
+    if (KIND == 3) {
+        acc.mn = s.dmn;
+        acc.mx = s.dmx;
+        const unsigned long long bm = block_max_u64(s.amax);
+        if (threadIdx.x == 0 && a.umax_scan != nullptr) atomicMax(a.umax_scan, bm);
+    }
     acc = block_reduce(acc);
     if (threadIdx.x == 0) {
         double *p = a.partials + 4ll * blockIdx.x;
@@ -219,29 +267,6 @@ __device__ __forceinline__ int fx_exponent(unsigned long long umax, const DevSta
     if (ex == 0 || ex == 0x7FF) return 0;
     const int E = ex + st->fx_headroom;
     return (E - 1023 >= -60 && E - 1023 <= 36) ? E : 0;
-}
-
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = w > v ? w : v;
-    }
-    return v;
-}
-
-// Block-wide max (blockDim.x a multiple of 32, <= 1024); result valid in thread 0.
-__device__ unsigned long long block_max_u64(unsigned long long v) {
-    __shared__ unsigned long long sh[32];
-    v = warp_max_u64(v);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        v = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0ull;
-        v = warp_max_u64(v);
-    }
-    return v;
 }
 
 // Iteration 0 of a 3-D split solve, one pass over f and U_0: the padded
@@ -378,7 +403,8 @@ __global__ void k_umax_finish(DevState *st) {
 
 __global__ void __launch_bounds__(256) k_finalize(const double *partials, int nparts, DevState *st,
                                                   qn_stats *hist, int hist_cap, double b,
-                                                  double lam, int update_state, int use_saved_fnorm) {
+                                                  double lam, int update_state, int use_saved_fnorm,
+                                                  int pot) {
     if (update_state && *(volatile int *)&st->done) return;
     Red4 acc{0.0, 0.0, INFINITY, 0.0};
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
@@ -398,7 +424,8 @@ __global__ void __launch_bounds__(256) k_finalize(const double *partials, int np
         int k = (rms > 0.0 && rms < INFINITY) ? ilogb(rms) : 0;
         st->r2_exp = k < -120 ? -120 : (k > 120 ? 120 : k);
     }
-    const double fa = 3.0 * b * acc.mn, fb = 3.0 * b * acc.mx;
+    // extremes of diag(N_h)_U: 3 b U^2 from those of U^2, or taken directly with a potential
+    const double fa = pot ? acc.mn : 3.0 * b * acc.mn, fb = pot ? acc.mx : 3.0 * b * acc.mx;
     const double fu_min = fmin(fa, fb), fu_max = fmax(fa, fb);
     const double beta = (st->beta_mode == QN_BETA_FIXED) ? st->beta_value : 0.5 * (fu_min + fu_max);
     double rel;
@@ -421,7 +448,12 @@ __global__ void __launch_bounds__(256) k_finalize(const double *partials, int np
     // exponent for the fixed-point stencil of the next residual, from max|U|
     // of this iterate (sqrt of max U^2 has at least max|U|'s exponent: the
     // rounding of u^2 can only carry it up)
-    st->fx_e = (acc.mx < INFINITY) ? fx_exponent((unsigned long long)__double_as_longlong(sqrt(acc.mx)), st) : 0;
+    if (pot) {
+        st->fx_e = fx_exponent(st->umax_scan, st);
+        st->umax_scan = 0ull;
+    } else {
+        st->fx_e = (acc.mx < INFINITY) ? fx_exponent((unsigned long long)__double_as_longlong(sqrt(acc.mx)), st) : 0;
+    }
     st->beta = beta;
     st->shift = lam + beta;
     if (rel <= st->tol) {
@@ -513,10 +545,21 @@ __device__ __forceinline__ void fx_to_pair(long long v, float scale, float &hi, 
     lo = __fmul_rn(__fadd_rn(e, f0), scale);
 }
 
-// r = lap/h^2 + lam u + b u^3 - f in float pairs, rounded to FP32.
+// (a + b) for two float pairs, renormalised.
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+    const float hi = __fadd_rn(s, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
+
+// r = lap/h^2 + lam u + b u^3 - f in float pairs, rounded to FP32. KIND 3:
+// (lh, ll) is the point's lam + V, and d receives 3 b u^2 + V (FP32, V = vf).
 template <int KIND>
 __device__ __forceinline__ float residual_pair(long long ufx, long long lapfx, float fh, float fl, float scale,
-                                               float ih, float il, float bh, float bl, float lh, float ll) {
+                                               float ih, float il, float bh, float bl, float lh, float ll,
+                                               float vf = 0.0f, float *d = nullptr) {
     float uh, ul, Lh, Ll;
     fx_to_pair(ufx, scale, uh, ul);
     fx_to_pair(lapfx, scale, Lh, Ll);
@@ -535,7 +578,8 @@ __device__ __forceinline__ float residual_pair(long long ufx, long long lapfx, f
         w = w2;
         we = e2;
     }
-    if (KIND == 0) {                                           // + lam u
+    if (KIND == 3) *d = __fmaf_rn(__fmul_rn(3.0f, bh), p, vf);
+    if (KIND == 0 || KIND == 3) {                              // + lam u  (KIND 3: + (lam + V) u)
         const float v = __fmul_rn(lh, uh);
         float ve = __fmaf_rn(lh, uh, -v);
         ve = __fmaf_rn(lh, ul, ve);
@@ -559,22 +603,38 @@ __device__ __forceinline__ float residual_pair(long long ufx, long long lapfx, f
 }
 
 // The exact per-point path (as k_residual), for points next to a flagged plane.
-static __device__ __noinline__ float residual_point_exact(const double *U, const double *f, int n, int x, int y,
-                                                          int z, double inv_h2, double lam, double b) {
+// Returns (r, 3 b u^2 + V); the second entry is 0 without a potential (pot == nullptr).
+static __device__ __noinline__ float2 residual_point_exact(const double *U, const double *f, int n, int x, int y,
+                                                           int z, double inv_h2, double lam, double b, int bc,
+                                                           const double *pot) {
     const long long nn = (long long)n * n;
     const long long c = ((long long)z * n + y) * n + x;
+    const bool neu = (bc == QN_BC_NEUMANN);
     const double u = U[c];
     double nb[6];
-    nb[0] = (x > 0) ? U[c - 1] : 0.0;
-    nb[1] = (x < n - 1) ? U[c + 1] : 0.0;
-    nb[2] = (y > 0) ? U[c - n] : 0.0;
-    nb[3] = (y < n - 1) ? U[c + n] : 0.0;
-    nb[4] = (z > 0) ? U[c - nn] : 0.0;
-    nb[5] = (z < n - 1) ? U[c + nn] : 0.0;
+    nb[0] = (x > 0) ? U[c - 1] : (neu ? U[c + 1] : 0.0);
+    nb[1] = (x < n - 1) ? U[c + 1] : (neu ? U[c - 1] : 0.0);
+    nb[2] = (y > 0) ? U[c - n] : (neu ? U[c + n] : 0.0);
+    nb[3] = (y < n - 1) ? U[c + n] : (neu ? U[c - n] : 0.0);
+    nb[4] = (z > 0) ? U[c - nn] : (neu ? U[c + nn] : 0.0);
+    nb[5] = (z < n - 1) ? U[c + nn] : (neu ? U[c - nn] : 0.0);
     const double lap = stencil_fixed<3>(u, nb);
     double t = fma(b, (u * u) * u, -f[c]);
-    t = fma(lam, u, t);
-    return d2f_rn(fma(lap, inv_h2, t));
+    double cv = lam;
+    float d = 0.0f;
+    if (pot != nullptr) {
+        cv += (pot[x] + pot[n + y]) + pot[2 * n + z];
+        d = d2f_rn(fma(3.0 * b, u * u, cv - lam));
+    }
+    t = fma(cv, u, t);
+    return make_float2(d2f_rn(fma(lap, inv_h2, t)), d);
+}
+
+// Grid index of the value a stencil reads at coordinate i (-1 <= i <= n):
+// itself, or for Neumann data the ghost reflection -1 -> 1, n -> n-2.
+// Indexes outside [0, n) after the mapping read as 0 (Dirichlet data, padding).
+__device__ __forceinline__ int ghost_index(int i, int n, bool neu) {
+    return neu ? (i == -1 ? 1 : (i == n ? n - 2 : i)) : i;
 }
 
 __device__ __forceinline__ void store_split2(__nv_bfloat162 *hi2, __nv_bfloat162 *lo2, long long i2, float r0,
@@ -592,6 +652,33 @@ __device__ __forceinline__ void minmax_bits(unsigned long long v, bool valid, un
     mx = (valid && ab > mx) ? ab : mx;
 }
 
+// Block partial record of the tiled residuals: sum r^2 (from the scaled FP32
+// Kahan sum) and min / max U^2, or with a potential (KIND 3) min / max of
+// 3 b U^2 + V, with max|U| sent to DevState::umax_scan.
+template <int KIND>
+__device__ __forceinline__ void tile_partials(const ResidualArgs &a, float kr2, float kc, int r2k,
+                                              unsigned long long amin, unsigned long long amax, float dmn,
+                                              float dmx) {
+    const double umin = __longlong_as_double((long long)amin);
+    const double umax = __longlong_as_double((long long)amax);
+    Red4 acc{ldexp((double)kr2 - (double)kc, 2 * r2k), 0.0,
+             (amin == 0x7FFFFFFFFFFFFFFFull) ? INFINITY : umin * umin, umax * umax};
+    if (KIND == 3) {
+        acc.mn = (double)dmn;
+        acc.mx = (double)dmx;
+        const unsigned long long bm = block_max_u64(amax);
+        if (threadIdx.x == 0) atomicMax(a.umax_scan, bm);
+    }
+    acc = block_reduce(acc);
+    if (threadIdx.x == 0) {
+        double *p = a.partials + 4ll * blockIdx.x;
+        p[0] = acc.r2;
+        p[1] = acc.f2;
+        p[2] = acc.mn;
+        p[3] = acc.mx;
+    }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kTThreads, 2) k_residual_tiled(ResidualArgs a, int zchunk) {
     if (a.done != nullptr && *(volatile const int *)a.done) return;
@@ -607,10 +694,12 @@ __global__ void __launch_bounds__(kTThreads, 2) k_residual_tiled(ResidualArgs a,
         bh = __double2float_rn(a.b);
         bl = __double2float_rn(a.b - (double)bh);
     }
-    if (KIND == 0) {
+    if (KIND == 0 || KIND == 3) {
         lh = __double2float_rn(a.lam);
         ll = __double2float_rn(a.lam - (double)lh);
     }
+    const bool neu = (a.bc == QN_BC_NEUMANN);
+    float dmn = INFINITY, dmx = -INFINITY;   // KIND 3: extremes of 3 b u^2 + V
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tiles_x = P / kTX, tiles_y = P / kTY;
     const int nzc = (P + zchunk - 1) / zchunk;
@@ -650,7 +739,21 @@ __global__ void __launch_bounds__(kTThreads, 2) k_residual_tiled(ResidualArgs a,
 
         const bool v00 = xo < n && yo < n, v10 = xo + 1 < n && yo < n;
         const bool v01 = xo < n && yo + 1 < n, v11 = xo + 1 < n && yo + 1 < n;
-        const long long own = (long long)yo * n + xo;
+        // loaded values: the own points, or at coordinate n the Neumann ghost
+        const int gx0 = ghost_index(xo, n, neu), gx1 = ghost_index(xo + 1, n, neu);
+        const int gy0 = ghost_index(yo, n, neu), gy1 = ghost_index(yo + 1, n, neu);
+        const bool l00 = gx0 < n && gy0 < n, l10 = gx1 < n && gy0 < n;
+        const bool l01 = gx0 < n && gy1 < n, l11 = gx1 < n && gy1 < n;
+        const int o00 = gy0 * n + gx0, o10 = gy0 * n + gx1, o01 = gy1 * n + gx0, o11 = gy1 * n + gx1;
+        float2 cxy[4];   // KIND 3: v_x + v_y of the own points
+        if (KIND == 3) {
+            const int xa = min(xo, n - 1), xb = min(xo + 1, n - 1);
+            const int ya = n + min(yo, n - 1), yb = n + min(yo + 1, n - 1);
+            cxy[0] = pair_add(__ldg(a.pot2 + xa), __ldg(a.pot2 + ya));
+            cxy[1] = pair_add(__ldg(a.pot2 + xb), __ldg(a.pot2 + ya));
+            cxy[2] = pair_add(__ldg(a.pot2 + xa), __ldg(a.pot2 + yb));
+            cxy[3] = pair_add(__ldg(a.pot2 + xb), __ldg(a.pot2 + yb));
+        }
         int hx, hy, hslot;
         if (hidx < kTX) {
             hx = X0 + hidx;
@@ -669,17 +772,20 @@ __global__ void __launch_bounds__(kTThreads, 2) k_residual_tiled(ResidualArgs a,
             hy = Y0 + hidx - 2 * kTX - kTY;
             hslot = (hidx - 2 * kTX - kTY + 1) * kSRow + kTX + 2;
         }
+        hx = ghost_index(hx, n, neu);
+        hy = ghost_index(hy, n, neu);
         const bool hval = hlane && hx >= 0 && hx < n && hy >= 0 && hy < n;
         const long long hoff = hval ? (long long)hy * n + hx : 0;
 
         unsigned long long R[4], RH;
         auto load_plane = [&](int z) {
-            const bool zin = z >= 0 && z < n;
-            const unsigned long long *p = Ub + (long long)(zin ? z : 0) * nn;
-            R[0] = (zin && v00) ? __ldg(p + own) : 0ull;
-            R[1] = (zin && v10) ? __ldg(p + own + 1) : 0ull;
-            R[2] = (zin && v01) ? __ldg(p + own + n) : 0ull;
-            R[3] = (zin && v11) ? __ldg(p + own + n + 1) : 0ull;
+            const int zg = ghost_index(z, n, neu);
+            const bool zin = zg >= 0 && zg < n;
+            const unsigned long long *p = Ub + (long long)(zin ? zg : 0) * nn;
+            R[0] = (zin && l00) ? __ldg(p + o00) : 0ull;
+            R[1] = (zin && l10) ? __ldg(p + o10) : 0ull;
+            R[2] = (zin && l01) ? __ldg(p + o01) : 0ull;
+            R[3] = (zin && l11) ? __ldg(p + o11) : 0ull;
             RH = (zin && hval) ? __ldg(p + hoff) : 0ull;
         };
         auto minmax_own = [&]() {
@@ -742,15 +848,59 @@ __global__ void __launch_bounds__(kTThreads, 2) k_residual_tiled(ResidualArgs a,
                 const long long lap1 = (long long)(6ull * c1 - (((c0 + r0) + ((u64)up.y + c3)) + ((u64)Fm[1] + (u64)Fp[1])));
                 const long long lap2 = (long long)(6ull * c2 - (((l1 + c3) + (c0 + (u64)dn.x)) + ((u64)Fm[2] + (u64)Fp[2])));
                 const long long lap3 = (long long)(6ull * c3 - (((c2 + r1) + (c1 + (u64)dn.y)) + ((u64)Fm[3] + (u64)Fp[3])));
-                rf[0] = residual_pair<KIND>(Fc[0], lap0, fa.x, fa.y, scale, ih, il, bh, bl, lh, ll);
-                rf[1] = residual_pair<KIND>(Fc[1], lap1, fa.z, fa.w, scale, ih, il, bh, bl, lh, ll);
-                rf[2] = residual_pair<KIND>(Fc[2], lap2, fb.x, fb.y, scale, ih, il, bh, bl, lh, ll);
-                rf[3] = residual_pair<KIND>(Fc[3], lap3, fb.z, fb.w, scale, ih, il, bh, bl, lh, ll);
+                if (KIND == 3) {
+                    // per point lam + V = (v_x + v_y) + (lam + v_z), V in FP32 for beta
+                    const float2 cz = __ldg(a.pot2 + 2 * n + z);
+                    float dd[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 cv = pair_add(cxy[i], cz);
+                        const long long lp = (i == 0) ? lap0 : (i == 1) ? lap1 : (i == 2) ? lap2 : lap3;
+                        const float fh = (i == 0) ? fa.x : (i == 1) ? fa.z : (i == 2) ? fb.x : fb.z;
+                        const float fl = (i == 0) ? fa.y : (i == 1) ? fa.w : (i == 2) ? fb.y : fb.w;
+                        rf[i] = residual_pair<KIND>(Fc[i], lp, fh, fl, scale, ih, il, bh, bl, cv.x, cv.y,
+                                                    __fsub_rn(cv.x, lh), &dd[i]);
+                    }
+                    if (v00) { dmn = fminf(dmn, dd[0]); dmx = fmaxf(dmx, dd[0]); }
+                    if (v10) { dmn = fminf(dmn, dd[1]); dmx = fmaxf(dmx, dd[1]); }
+                    if (v01) { dmn = fminf(dmn, dd[2]); dmx = fmaxf(dmx, dd[2]); }
+                    if (v11) { dmn = fminf(dmn, dd[3]); dmx = fmaxf(dmx, dd[3]); }
+                } else {
+                    rf[0] = residual_pair<KIND>(Fc[0], lap0, fa.x, fa.y, scale, ih, il, bh, bl, lh, ll);
+                    rf[1] = residual_pair<KIND>(Fc[1], lap1, fa.z, fa.w, scale, ih, il, bh, bl, lh, ll);
+                    rf[2] = residual_pair<KIND>(Fc[2], lap2, fb.x, fb.y, scale, ih, il, bh, bl, lh, ll);
+                    rf[3] = residual_pair<KIND>(Fc[3], lap3, fb.z, fb.w, scale, ih, il, bh, bl, lh, ll);
+                }
             } else {
-                rf[0] = v00 ? residual_point_exact(a.U, a.f, n, xo, yo, z, a.inv_h2, a.lam, a.b) : 0.0f;
-                rf[1] = v10 ? residual_point_exact(a.U, a.f, n, xo + 1, yo, z, a.inv_h2, a.lam, a.b) : 0.0f;
-                rf[2] = v01 ? residual_point_exact(a.U, a.f, n, xo, yo + 1, z, a.inv_h2, a.lam, a.b) : 0.0f;
-                rf[3] = v11 ? residual_point_exact(a.U, a.f, n, xo + 1, yo + 1, z, a.inv_h2, a.lam, a.b) : 0.0f;
+                const double *pot = (KIND == 3) ? a.pot : nullptr;
+                float dd[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                rf[0] = rf[1] = rf[2] = rf[3] = 0.0f;
+                if (v00) {
+                    const float2 e = residual_point_exact(a.U, a.f, n, xo, yo, z, a.inv_h2, a.lam, a.b, a.bc, pot);
+                    rf[0] = e.x;
+                    dd[0] = e.y;
+                }
+                if (v10) {
+                    const float2 e = residual_point_exact(a.U, a.f, n, xo + 1, yo, z, a.inv_h2, a.lam, a.b, a.bc, pot);
+                    rf[1] = e.x;
+                    dd[1] = e.y;
+                }
+                if (v01) {
+                    const float2 e = residual_point_exact(a.U, a.f, n, xo, yo + 1, z, a.inv_h2, a.lam, a.b, a.bc, pot);
+                    rf[2] = e.x;
+                    dd[2] = e.y;
+                }
+                if (v11) {
+                    const float2 e = residual_point_exact(a.U, a.f, n, xo + 1, yo + 1, z, a.inv_h2, a.lam, a.b, a.bc, pot);
+                    rf[3] = e.x;
+                    dd[3] = e.y;
+                }
+                if (KIND == 3) {
+                    if (v00) { dmn = fminf(dmn, dd[0]); dmx = fmaxf(dmx, dd[0]); }
+                    if (v10) { dmn = fminf(dmn, dd[1]); dmx = fmaxf(dmx, dd[1]); }
+                    if (v01) { dmn = fminf(dmn, dd[2]); dmx = fmaxf(dmx, dd[2]); }
+                    if (v11) { dmn = fminf(dmn, dd[3]); dmx = fmaxf(dmx, dd[3]); }
+                }
             }
             rf[0] = v00 ? rf[0] : 0.0f;
             rf[1] = v10 ? rf[1] : 0.0f;
@@ -780,18 +930,7 @@ __global__ void __launch_bounds__(kTThreads, 2) k_residual_tiled(ResidualArgs a,
         }
     }
 
-    const double umin = __longlong_as_double((long long)amin);
-    const double umax = __longlong_as_double((long long)amax);
-    Red4 acc{ldexp((double)kr2 - (double)kc, 2 * r2k), 0.0,
-             (amin == 0x7FFFFFFFFFFFFFFFull) ? INFINITY : umin * umin, umax * umax};
-    acc = block_reduce(acc);
-    if (threadIdx.x == 0) {
-        double *p = a.partials + 4ll * blockIdx.x;
-        p[0] = acc.r2;
-        p[1] = acc.f2;
-        p[2] = acc.mn;
-        p[3] = acc.mx;
-    }
+    tile_partials<KIND>(a, kr2, kc, r2k, amin, amax, dmn, dmx);
 }
 
 // ---------------------------------------------------------------------------
@@ -838,10 +977,12 @@ __global__ void __launch_bounds__(kTThreads, 2) k_residual_mirror(ResidualArgs a
         bh = __double2float_rn(a.b);
         bl = __double2float_rn(a.b - (double)bh);
     }
-    if (KIND == 0) {
+    if (KIND == 0 || KIND == 3) {
         lh = __double2float_rn(a.lam);
         ll = __double2float_rn(a.lam - (double)lh);
     }
+    const bool neu = (a.bc == QN_BC_NEUMANN);
+    float dmn = INFINITY, dmx = -INFINITY;   // KIND 3: extremes of 3 b u^2 + V
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tiles_x = H / 32, tiles_y = P / kTY;
     const int nzc = (P + zchunk - 1) / zchunk;
@@ -888,6 +1029,19 @@ __global__ void __launch_bounds__(kTThreads, 2) k_residual_mirror(ResidualArgs a
         const bool pL = xL < n, pR = xR >= 0, py0 = y0 < n, py1 = y1 < n;
         const bool oL = xL < nsym, oR = xL < nanti;
         const bool v0 = oL && py0, v1 = oR && py0, v2 = oL && py1, v3 = oR && py1;   // own points
+        // rows read: the own rows, or at y = n the Neumann ghost row n-2
+        // (x needs no ghost here: n > 64, so 0 < xR and xL < n)
+        const int gy0 = ghost_index(y0, n, neu), gy1 = ghost_index(y1, n, neu);
+        const bool ly0 = gy0 < n, ly1 = gy1 < n;
+        float2 cxy[4];   // KIND 3: v_x + v_y of the own points
+        if (KIND == 3) {
+            const int xa = min(max(xL, 0), n - 1), xb = min(max(xR, 0), n - 1);
+            const int ya = n + min(y0, n - 1), yb = n + min(y1, n - 1);
+            cxy[0] = pair_add(__ldg(a.pot2 + xa), __ldg(a.pot2 + ya));
+            cxy[1] = pair_add(__ldg(a.pot2 + xb), __ldg(a.pot2 + ya));
+            cxy[2] = pair_add(__ldg(a.pot2 + xa), __ldg(a.pot2 + yb));
+            cxy[3] = pair_add(__ldg(a.pot2 + xb), __ldg(a.pot2 + yb));
+        }
         int hx, hy, hslot;
         {
             const int h = hidx;
@@ -911,17 +1065,20 @@ __global__ void __launch_bounds__(kTThreads, 2) k_residual_mirror(ResidualArgs a
                 hslot = rr * kSRow + ((w == 0) ? 0 : (w == 1) ? 33 : (w == 2) ? 34 : 67);
             }
         }
+        hx = ghost_index(hx, n, neu);
+        hy = ghost_index(hy, n, neu);
         const bool hval = hlane && hx >= 0 && hx < n && hy >= 0 && hy < n;
         const long long hoff = hval ? (long long)hy * n + hx : 0;
 
         unsigned long long R[4], RH;
         auto load_plane = [&](int z) {
-            const bool zin = z >= 0 && z < n;
-            const unsigned long long *p = Ub + (long long)(zin ? z : 0) * nn;
-            R[0] = (zin && pL && py0) ? __ldg(p + (long long)y0 * n + xL) : 0ull;
-            R[1] = (zin && pR && py0) ? __ldg(p + (long long)y0 * n + xR) : 0ull;
-            R[2] = (zin && pL && py1) ? __ldg(p + (long long)y1 * n + xL) : 0ull;
-            R[3] = (zin && pR && py1) ? __ldg(p + (long long)y1 * n + xR) : 0ull;
+            const int zg = ghost_index(z, n, neu);
+            const bool zin = zg >= 0 && zg < n;
+            const unsigned long long *p = Ub + (long long)(zin ? zg : 0) * nn;
+            R[0] = (zin && pL && ly0) ? __ldg(p + (long long)gy0 * n + xL) : 0ull;
+            R[1] = (zin && pR && ly0) ? __ldg(p + (long long)gy0 * n + xR) : 0ull;
+            R[2] = (zin && pL && ly1) ? __ldg(p + (long long)gy1 * n + xL) : 0ull;
+            R[3] = (zin && pR && ly1) ? __ldg(p + (long long)gy1 * n + xR) : 0ull;
             RH = (zin && hval) ? __ldg(p + hoff) : 0ull;
         };
         auto minmax_own = [&]() {
@@ -983,15 +1140,59 @@ __global__ void __launch_bounds__(kTThreads, 2) k_residual_mirror(ResidualArgs a
                 const long long lap1 = (long long)(6ull * c1 - ((sr0 + (uR + c3)) + ((u64)Fm[1] + (u64)Fp[1])));
                 const long long lap2 = (long long)(6ull * c2 - ((sl1 + (c0 + dL)) + ((u64)Fm[2] + (u64)Fp[2])));
                 const long long lap3 = (long long)(6ull * c3 - ((sr1 + (c1 + dR)) + ((u64)Fm[3] + (u64)Fp[3])));
-                rf[0] = residual_pair<KIND>(Fc[0], lap0, fa.x, fa.y, scale, ih, il, bh, bl, lh, ll);
-                rf[1] = residual_pair<KIND>(Fc[1], lap1, fa.z, fa.w, scale, ih, il, bh, bl, lh, ll);
-                rf[2] = residual_pair<KIND>(Fc[2], lap2, fb.x, fb.y, scale, ih, il, bh, bl, lh, ll);
-                rf[3] = residual_pair<KIND>(Fc[3], lap3, fb.z, fb.w, scale, ih, il, bh, bl, lh, ll);
+                if (KIND == 3) {
+                    // per point lam + V = (v_x + v_y) + (lam + v_z), V in FP32 for beta
+                    const float2 cz = __ldg(a.pot2 + 2 * n + z);
+                    float dd[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 cv = pair_add(cxy[i], cz);
+                        const long long lp = (i == 0) ? lap0 : (i == 1) ? lap1 : (i == 2) ? lap2 : lap3;
+                        const float fh = (i == 0) ? fa.x : (i == 1) ? fa.z : (i == 2) ? fb.x : fb.z;
+                        const float fl = (i == 0) ? fa.y : (i == 1) ? fa.w : (i == 2) ? fb.y : fb.w;
+                        rf[i] = residual_pair<KIND>(Fc[i], lp, fh, fl, scale, ih, il, bh, bl, cv.x, cv.y,
+                                                    __fsub_rn(cv.x, lh), &dd[i]);
+                    }
+                    if (v0) { dmn = fminf(dmn, dd[0]); dmx = fmaxf(dmx, dd[0]); }
+                    if (v1) { dmn = fminf(dmn, dd[1]); dmx = fmaxf(dmx, dd[1]); }
+                    if (v2) { dmn = fminf(dmn, dd[2]); dmx = fmaxf(dmx, dd[2]); }
+                    if (v3) { dmn = fminf(dmn, dd[3]); dmx = fmaxf(dmx, dd[3]); }
+                } else {
+                    rf[0] = residual_pair<KIND>(Fc[0], lap0, fa.x, fa.y, scale, ih, il, bh, bl, lh, ll);
+                    rf[1] = residual_pair<KIND>(Fc[1], lap1, fa.z, fa.w, scale, ih, il, bh, bl, lh, ll);
+                    rf[2] = residual_pair<KIND>(Fc[2], lap2, fb.x, fb.y, scale, ih, il, bh, bl, lh, ll);
+                    rf[3] = residual_pair<KIND>(Fc[3], lap3, fb.z, fb.w, scale, ih, il, bh, bl, lh, ll);
+                }
             } else {
-                rf[0] = v0 ? residual_point_exact(a.U, a.f, n, xL, y0, z, a.inv_h2, a.lam, a.b) : 0.0f;
-                rf[1] = v1 ? residual_point_exact(a.U, a.f, n, xR, y0, z, a.inv_h2, a.lam, a.b) : 0.0f;
-                rf[2] = v2 ? residual_point_exact(a.U, a.f, n, xL, y1, z, a.inv_h2, a.lam, a.b) : 0.0f;
-                rf[3] = v3 ? residual_point_exact(a.U, a.f, n, xR, y1, z, a.inv_h2, a.lam, a.b) : 0.0f;
+                const double *pot = (KIND == 3) ? a.pot : nullptr;
+                float dd[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                rf[0] = rf[1] = rf[2] = rf[3] = 0.0f;
+                if (v0) {
+                    const float2 e = residual_point_exact(a.U, a.f, n, xL, y0, z, a.inv_h2, a.lam, a.b, a.bc, pot);
+                    rf[0] = e.x;
+                    dd[0] = e.y;
+                }
+                if (v1) {
+                    const float2 e = residual_point_exact(a.U, a.f, n, xR, y0, z, a.inv_h2, a.lam, a.b, a.bc, pot);
+                    rf[1] = e.x;
+                    dd[1] = e.y;
+                }
+                if (v2) {
+                    const float2 e = residual_point_exact(a.U, a.f, n, xL, y1, z, a.inv_h2, a.lam, a.b, a.bc, pot);
+                    rf[2] = e.x;
+                    dd[2] = e.y;
+                }
+                if (v3) {
+                    const float2 e = residual_point_exact(a.U, a.f, n, xR, y1, z, a.inv_h2, a.lam, a.b, a.bc, pot);
+                    rf[3] = e.x;
+                    dd[3] = e.y;
+                }
+                if (KIND == 3) {
+                    if (v0) { dmn = fminf(dmn, dd[0]); dmx = fmaxf(dmx, dd[0]); }
+                    if (v1) { dmn = fminf(dmn, dd[1]); dmx = fmaxf(dmx, dd[1]); }
+                    if (v2) { dmn = fminf(dmn, dd[2]); dmx = fmaxf(dmx, dd[2]); }
+                    if (v3) { dmn = fminf(dmn, dd[3]); dmx = fmaxf(dmx, dd[3]); }
+                }
             }
             rf[0] = v0 ? rf[0] : 0.0f;
             rf[1] = v1 ? rf[1] : 0.0f;
@@ -1027,18 +1228,7 @@ __global__ void __launch_bounds__(kTThreads, 2) k_residual_mirror(ResidualArgs a
         }
     }
 
-    const double umin = __longlong_as_double((long long)amin);
-    const double umax = __longlong_as_double((long long)amax);
-    Red4 acc{ldexp((double)kr2 - (double)kc, 2 * r2k), 0.0,
-             (amin == 0x7FFFFFFFFFFFFFFFull) ? INFINITY : umin * umin, umax * umax};
-    acc = block_reduce(acc);
-    if (threadIdx.x == 0) {
-        double *p = a.partials + 4ll * blockIdx.x;
-        p[0] = acc.r2;
-        p[1] = acc.f2;
-        p[2] = acc.mn;
-        p[3] = acc.mx;
-    }
+    tile_partials<KIND>(a, kr2, kc, r2k, amin, amax, dmn, dmx);
 }
 
 // Dense FP64 field -> FP32 -> BF16 hi/lo planes on the zero-padded P^dim grid.
@@ -1075,7 +1265,9 @@ int launch_split_pad(const double *r, int n, int P, int dim, __nv_bfloat16 *hi, 
 
 template <int DIM, bool SPLIT, bool FAST, bool WF2>
 static void launch_res4(const ResidualArgs &a, int grid, cudaStream_t s) {
-    if (a.lam != 0.0)
+    if (a.pot != nullptr)
+        k_residual<DIM, SPLIT, FAST, 3, WF2><<<grid, 256, 0, s>>>(a);
+    else if (a.lam != 0.0)
         k_residual<DIM, SPLIT, FAST, 0, WF2><<<grid, 256, 0, s>>>(a);
     else if (a.b != 1.0)
         k_residual<DIM, SPLIT, FAST, 1, WF2><<<grid, 256, 0, s>>>(a);
@@ -1182,6 +1374,13 @@ int launch_residual_mirror(const ResidualArgs &a, int max_grid, int zchunk, int 
         set_error("launch_residual_mirror: needs a 3-D split residual, P a multiple of 128, the f copy");
         return QN_EINVAL;
     }
+    if (a.pot != nullptr) {
+        if (a.pot2 == nullptr || a.umax_scan == nullptr) {
+            set_error("launch_residual_mirror: a potential needs its FP32-pair tables and the max|U| slot");
+            return QN_EINVAL;
+        }
+        return launch_mirror_kind<3>(a, max_grid, zchunk, grid_used, s);
+    }
     if (a.lam != 0.0) return launch_mirror_kind<0>(a, max_grid, zchunk, grid_used, s);
     if (a.b != 1.0) return launch_mirror_kind<1>(a, max_grid, zchunk, grid_used, s);
     return launch_mirror_kind<2>(a, max_grid, zchunk, grid_used, s);
@@ -1192,6 +1391,13 @@ int launch_residual_tiled(const ResidualArgs &a, int max_grid, int zchunk, int *
         zchunk < 1) {
         set_error("launch_residual_tiled: needs a 3-D split residual with the FP32-pair copy of f");
         return QN_EINVAL;
+    }
+    if (a.pot != nullptr) {
+        if (a.pot2 == nullptr || a.umax_scan == nullptr) {
+            set_error("launch_residual_tiled: a potential needs its FP32-pair tables and the max|U| slot");
+            return QN_EINVAL;
+        }
+        return launch_tiled_kind<3>(a, max_grid, zchunk, grid_used, s);
     }
     if (a.lam != 0.0) return launch_tiled_kind<0>(a, max_grid, zchunk, grid_used, s);
     if (a.b != 1.0) return launch_tiled_kind<1>(a, max_grid, zchunk, grid_used, s);
@@ -1221,9 +1427,9 @@ int launch_umax(const double *U, long long N, DevState *st, int grid, cudaStream
 
 int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *hist,
                         int hist_cap, double b, double lam, int update_state, int use_saved_fnorm,
-                        cudaStream_t s) {
+                        int pot, cudaStream_t s) {
     k_finalize<<<1, 256, 0, s>>>(partials, nparts, st, hist, hist_cap, b, lam, update_state,
-                                 use_saved_fnorm);
+                                 use_saved_fnorm, pot);
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }
@@ -1353,7 +1559,7 @@ extern "C" int qn_residual_noalloc(int dim, int n, double lam, double b, const d
     a.fp64_warps = 0;
     rc = launch_residual(a, grid, s);
     if (rc != QN_OK) return rc;
-    rc = launch_finalize(partials, grid, state, stats, 1, b, lam, 0, 0, s);
+    rc = launch_finalize(partials, grid, state, stats, 1, b, lam, 0, 0, 0, s);
     if (rc != QN_OK) return rc;
     QN_CUDA(cudaMemcpyAsync(st, stats, sizeof(qn_stats), cudaMemcpyDeviceToHost, s));
     QN_CUDA(cudaStreamSynchronize(s));

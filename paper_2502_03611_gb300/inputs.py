@@ -271,3 +271,13 @@ def ex1_perturbation(n: int, seed: int, eps: float, degree: int = 4) -> np.ndarr
     Vp = np.vander(x, m, increasing=True)                     # Vp[node, power]
     q = np.einsum("kji,zk,yj,xi->zyx", c, Vp, Vp, Vp, optimize=True)
     return eps * q / float(np.max(np.abs(q)))
+
+
+def ex2d1_problem(n: int):
+    """Data of -Lap u + u^3 + u = f on (-1,1)^2 with zero normal derivative (Sec. 6.2,
+    Example 1): u* = cos(pi x) cos(2 pi y), -Lap u* = 5 pi^2 u*, on n nodes per axis.
+    Returns (u_star [y, x], f, h) with h = 2/(n-1)."""
+    x = neumann_nodes(n)
+    u = np.cos(2.0 * math.pi * x)[:, None] * np.cos(math.pi * x)[None, :]
+    f = (5.0 * math.pi ** 2 + 1.0) * u + u ** 3
+    return u, f, 2.0 / (n - 1)

@@ -25,6 +25,8 @@ QN_ETIMEOUT = -6
 QN_EUNSUPPORTED = -7
 
 QN_BC_DIRICHLET = 0
+QN_BC_NEUMANN = 1
+BCS = {"dirichlet": QN_BC_DIRICHLET, "neumann": QN_BC_NEUMANN}
 QN_PREC_FP64 = 0
 QN_PREC_BF16X3 = 1
 QN_BETA_PAPER = 0
@@ -35,7 +37,8 @@ PRECISIONS = {"fp64": QN_PREC_FP64, "bf16x3": QN_PREC_BF16X3}
 
 class QnProblem(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("bc", ctypes.c_int),
-                ("precision", ctypes.c_int), ("lam", ctypes.c_double), ("b", ctypes.c_double)]
+                ("precision", ctypes.c_int), ("lam", ctypes.c_double), ("b", ctypes.c_double),
+                ("length", ctypes.c_double), ("potential_host", ctypes.POINTER(ctypes.c_double))]
 
 
 class QnStats(ctypes.Structure):
@@ -200,11 +203,21 @@ class QnContext:
     """Owns a qn_ctx (qn_ctx_create / qn_ctx_destroy)."""
 
     def __init__(self, dim: int, n: int, precision: str | int = "fp64", lam: float = 0.0,
-                 b: float = 1.0, bc: int = QN_BC_DIRICHLET):
+                 b: float = 1.0, bc: str | int = QN_BC_DIRICHLET, length: float = 0.0, potential=None):
+        """potential: None, or the 1-D tables of V = v_x + v_y (+ v_z) at the nodes, an array
+        of shape (n,) (the same table on every axis) or (dim, n) (x first)."""
         lib = load_library()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        self.problem = QnProblem(dim, n, bc, prec, lam, b)
-        self.dim, self.n, self.precision = dim, n, prec
+        bcv = BCS[bc] if isinstance(bc, str) else int(bc)
+        pot = None
+        if potential is not None:
+            v = np.asarray(potential, dtype=np.float64)
+            pot = np.ascontiguousarray(np.broadcast_to(v, (dim, n)) if v.ndim == 1 else v)
+            if pot.shape != (dim, n):
+                raise ValueError(f"potential tables must have shape ({n},) or ({dim}, {n})")
+        ptr = pot.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if pot is not None else None
+        self.problem = QnProblem(dim, n, bcv, prec, lam, b, length, ptr)
+        self.dim, self.n, self.precision, self.bc = dim, n, prec, bcv
         self.numel = n ** dim
         h = ctypes.c_void_p()
         _check(lib.qn_ctx_create(ctypes.byref(self.problem), ctypes.byref(h)))
@@ -232,8 +245,9 @@ class QnContext:
         self.close()
 
 
-def qn_ctx_create(dim, n, precision="fp64", lam=0.0, b=1.0, bc=QN_BC_DIRICHLET) -> QnContext:
-    return QnContext(dim, n, precision, lam, b, bc)
+def qn_ctx_create(dim, n, precision="fp64", lam=0.0, b=1.0, bc=QN_BC_DIRICHLET, length=0.0,
+                  potential=None) -> QnContext:
+    return QnContext(dim, n, precision, lam, b, bc, length, potential)
 
 
 def qn_ctx_destroy(ctx: QnContext):

@@ -65,13 +65,33 @@ def test_setup_1d_eig_matches_oracle(lib, n):
     assert np.abs(H @ S - S * lam[None, :]).max() < 1e-12 * lam.max()
 
 
+@pytest.mark.parametrize("n", [2, 3, 8, 201])
+def test_setup_1d_eig_neumann_matches_oracle(lib, n):
+    """Closed-form cosine pairs of the library against the oracle's diagonalisation
+    of the ghost-point matrix (Sec. 3.2 Neumann rows)."""
+    from oracle import qn_oracle_bc as ob
+    from paper_2502_03611_gb300 import qn
+    h = 2.0 / (n - 1)
+    S, Si, lam = qn.qn_setup_1d_eig(n, h, qn.QN_BC_NEUMANN)
+    So, Sio, lamo = ob.eig_1d(n, h, "neumann")
+    assert np.abs(lam - lamo).max() <= 1e-12 * lamo.max()
+    assert np.abs(Si @ S - np.eye(n)).max() < 1e-12
+    H = ob.fd_matrix_1d(n, h, "neumann")
+    assert np.abs(H @ S - S * lam[None, :]).max() < 1e-12 * lam.max()
+    # both normalise W^{1/2} S to orthonormal columns (W the trapezoid weights), so the
+    # columns agree up to sign: |sum_j w_j S_jk So_jk| = 1
+    w = ob.trapezoid_weights(n, "neumann")
+    assert np.abs(np.abs(np.sum(w[:, None] * S * So, axis=0)) - 1.0).max() < 1e-10
+
+
 def test_setup_rejects_bad_arguments(lib):
     from paper_2502_03611_gb300 import qn
-    D = __import__("ctypes").POINTER(__import__("ctypes").c_double)
     assert lib.qn_setup_1d_eig(0, 0.5, 0, None, None, None) == qn.QN_EINVAL
-    assert lib.qn_setup_1d_eig(7, 0.1, 0, None, None, None) == qn.QN_EINVAL   # h != 1/(n+1)
-    assert lib.qn_setup_1d_eig(7, 0.125, 1, None, None, None) == qn.QN_EUNSUPPORTED
-    assert "h=" in qn.qn_last_error() or "QN_BC" in qn.qn_last_error()
+    assert lib.qn_setup_1d_eig(7, 0.0, 0, None, None, None) == qn.QN_EINVAL    # h must be > 0
+    assert lib.qn_setup_1d_eig(7, -1.0, 1, None, None, None) == qn.QN_EINVAL
+    assert lib.qn_setup_1d_eig(1, 0.5, 1, None, None, None) == qn.QN_EINVAL    # Neumann needs n >= 2
+    assert lib.qn_setup_1d_eig(7, 0.125, 5, None, None, None) == qn.QN_EINVAL  # unknown bc
+    assert "boundary" in qn.qn_last_error()
 
 
 def test_ctx_create_validates_before_cuda(lib):
@@ -80,8 +100,15 @@ def test_ctx_create_validates_before_cuda(lib):
     h = ctypes.c_void_p()
     for prob in (qn.QnProblem(4, 10, 0, 0, 0.0, 1.0), qn.QnProblem(3, 0, 0, 0, 0.0, 1.0),
                  qn.QnProblem(3, 2000, 0, 0, 0.0, 1.0), qn.QnProblem(3, 10, 0, 9, 0.0, 1.0),
-                 qn.QnProblem(3, 10, 0, 0, math.inf, 1.0)):
+                 qn.QnProblem(3, 10, 0, 0, math.inf, 1.0), qn.QnProblem(3, 1, 1, 0, 0.0, 1.0),
+                 qn.QnProblem(3, 10, 7, 0, 0.0, 1.0), qn.QnProblem(3, 10, 1, 0, 0.0, 1.0, -2.0),
+                 qn.QnProblem(3, 10, 1, 0, 0.0, 1.0, math.nan)):
         assert lib.qn_ctx_create(ctypes.byref(prob), ctypes.byref(h)) == qn.QN_EINVAL
+    bad = np.zeros(30)
+    bad[17] = math.inf
+    prob = qn.QnProblem(3, 10, 1, 0, 0.0, 1.0, 2.0, bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    assert lib.qn_ctx_create(ctypes.byref(prob), ctypes.byref(h)) == qn.QN_EINVAL
+    assert "potential" in qn.qn_last_error()
     assert lib.qn_ctx_create(None, ctypes.byref(h)) == qn.QN_EINVAL
     assert lib.qn_residual(None, None, None, None, None, None) == qn.QN_EINVAL
     assert lib.qn_solve(None, None, None, None, None, None, 0, None) == qn.QN_EINVAL
