@@ -145,7 +145,8 @@ def test_step_ex1_matches_oracle(qn, n, prec):
         assert np.abs(got - Uo).max() <= 1e-12 * np.abs(Uo).max()
     else:
         assert np.abs(got - Uo).max() <= 3e-4 * delta
-    assert st["beta"] == pytest.approx(ho[0]["beta"], rel=1e-13)
+    # the split solve's tiled residual takes the extremes of 3 b U^2 + V in FP32
+    assert st["beta"] == pytest.approx(ho[0]["beta"], rel=1e-6 if prec == "bf16x3" else 1e-13)
     assert st["res_norm"] == pytest.approx(ho[0]["res"], rel=1e-6 if prec == "bf16x3" else 1e-12)
 
 
@@ -327,7 +328,7 @@ def test_ex1_200_full_size(qn):
 def test_warm_start_rejects_neumann(qn):
     import torch
     ctx = qn.QnContext(3, 33, "bf16x3", bc="neumann", length=2.0)
-    net = qn.QnNet(16, modes=4, blocks=1, max_batch=1, channels=8)
+    net = qn.QnNet(16, modes=4, blocks=1, max_batch=1)
     U = torch.zeros(33 ** 3, dtype=torch.float64, device="cuda")
     f = torch.ones(33 ** 3, dtype=torch.float64, device="cuda")
     with pytest.raises(qn.QnError) as e:
