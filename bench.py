@@ -11,6 +11,13 @@ mode products with the update) with f and U resident in HBM. Prints one JSON
 line on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload dirichlet|ex1] [--n N]
+
+--workload ex1 times the three-dimensional Example 1 of the paper's Sec. 6.3
+instead: -Lap u + 10 u + 10 u^3 + V u = f on (-1,1)^3 with zero normal
+derivative, V = sum of 100 sin^2(pi t/4) + t^2 over the axes, n = 200 nodes per
+axis by default (400, 800: the paper's other mesh sizes), started from the
+exact solution plus 0.1 times a random normalised polynomial.
 
 --impl reference times the FP64 CPU oracle (numpy) on the host cores instead.
 Under torchrun (N > 1) every rank solves its own seed (replicas; the solve
@@ -32,6 +39,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time to rel. residual 1e-10 at 511^3, mixed/warm vs plain FP64; % of peak"
+METRIC_EX1 = "time to rel. residual 1e-10, 3-D Example 1 (Neumann, potential) at n^3"
+# the paper's A100 80GB figures for Example 1, beta = (min+max)/2 (Table results3D_mesh);
+# the paper does not state its stopping tolerance, so these are context only
+PAPER_EX1 = {200: (62.9, 0.5), 400: (59.4, 3.5), 800: (55.5, 36.5)}
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -41,7 +52,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=511)
+    ap.add_argument("--workload", default="dirichlet", choices=["dirichlet", "ex1"])
+    ap.add_argument("--n", type=int, default=None, help="nodes per axis (default 511, ex1: 200)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison solve")
@@ -52,6 +64,8 @@ def parse():
     a = ap.parse_args()
     if a.quick:
         a.no_fp64 = a.no_cpu = a.no_e2e = a.no_batched = True
+    if a.n is None:
+        a.n = 200 if a.workload == "ex1" else 511
     return a
 
 
@@ -171,6 +185,30 @@ def cpu_oracle_baseline(n: int, seed: int, iters_timed: int = 1):
     return per_it * its * 1e3, {"per_iteration_s": per_it, "iterations_assumed": its, "cores": cores}
 
 
+def cpu_oracle_baseline_ex1(n: int, seed: int, iters_timed: int = 1):
+    """cpu_oracle_baseline for Example 1: iters_timed oracle iterations at n^3 times the
+    oracle's iteration count at 33^3 from the same kind of start (mesh-independent)."""
+    import numpy as np
+    from oracle import qn_oracle_bc as ob
+    from paper_2502_03611_gb300 import inputs as I
+    u, f, v, h = I.ex1_problem(33)
+    _, h_small, _ = ob.qn_solve(f, h, "neumann", U0=u + I.ex1_perturbation(33, seed, 0.1), lam=I.EX1_A,
+                                b=I.EX1_B, V=ob.potential(v, 3, 33))
+    its = len(h_small) - 1
+    u, f, v, h = I.ex1_problem(n)
+    V = ob.potential(v, 3, n)
+    eig = ob.eig_1d(n, h, "neumann")
+    U = u + I.ex1_perturbation(n, seed, 0.1)
+    times = []
+    for _ in range(iters_timed):
+        t0 = time.perf_counter()
+        U, _, _ = ob.qn_step(U, f, h, "neumann", eig, I.EX1_A, I.EX1_B, V)
+        times.append(time.perf_counter() - t0)
+    per_it = statistics.mean(times)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return per_it * its * 1e3, {"per_iteration_s": per_it, "iterations_assumed": its, "cores": cores}
+
+
 def run_batched(qn, seed=0, count=256, reps=3):
     """Batched coupled 2-D systems: 256 instances, n uniform on {63,127,255,511},
     alpha ~ U[0,1], D ~ U[0.1,10]; tiles from the project autotuner per size.
@@ -232,6 +270,9 @@ def run_reference(a):
     import oracle as O
     from paper_2502_03611_gb300.inputs import manufactured_problem
     n = a.n
+    if a.workload == "ex1":
+        run_reference_ex1(a)
+        return
     _, f_small = manufactured_problem(127, 3, seed=a.seed)
     _, h_small, _ = O.qn_solve(f_small)
     its = len(h_small) - 1
@@ -286,17 +327,36 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2502_03611_gb300 import qn
-    from paper_2502_03611_gb300.inputs import manufactured_problem
+    from paper_2502_03611_gb300 import inputs as I
 
     n = a.n
     seed = a.seed + rank
     peaks, peak_src = load_peaks()
-    _, f_np = manufactured_problem(n, 3, seed=seed)
+    ex1 = a.workload == "ex1"
+    if ex1:
+        # Sec. 6.3, Example 1: start = exact solution + 0.1 * normalised random polynomial
+        u_np, f_np, v_np, _ = I.ex1_problem(n)
+        U0_np = np.ascontiguousarray((u_np + I.ex1_perturbation(n, seed, 0.1)).reshape(-1))
+        ctx_kw = dict(lam=I.EX1_A, b=I.EX1_B, bc="neumann", length=2.0, potential=v_np)
+        max_it = 300
+        del u_np
+    else:
+        _, f_np = I.manufactured_problem(n, 3, seed=seed)
+        U0_np = None
+        ctx_kw = {}
+        max_it = 100
     f_np = np.ascontiguousarray(f_np.reshape(-1))
     N = f_np.size
     f = torch.from_numpy(f_np).cuda()
     U = torch.zeros(N, dtype=torch.float64, device="cuda")
-    ctx = qn.QnContext(3, n, a.precision)
+    U0 = torch.from_numpy(U0_np).cuda() if ex1 else None
+    ctx = qn.QnContext(3, n, a.precision, **ctx_kw)
+
+    def reset_start():
+        if U0 is None:
+            U.zero_()
+        else:
+            U.copy_(U0)
 
     def barrier():
         if world > 1:
@@ -305,8 +365,8 @@ def main():
     # steady-state iterations replay a CUDA graph (qn_opts.graph); the warm-up
     # solves capture it
     for _ in range(max(a.warmup, 0)):
-        U.zero_()
-        qn.qn_solve(ctx, U, f, max_it=100, graph=True)
+        reset_start()
+        qn.qn_solve(ctx, U, f, max_it=max_it, graph=True)
     torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
@@ -320,8 +380,8 @@ def main():
     ev0.record(stream)
     results = []
     for _ in range(a.steps):
-        U.zero_()
-        res, _ = qn.qn_solve(ctx, U, f, max_it=100, graph=True)
+        reset_start()
+        res, _ = qn.qn_solve(ctx, U, f, max_it=max_it, graph=True)
         results.append(res)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -333,8 +393,8 @@ def main():
     # launch (plain launches; outside the timed region)
     qn.qn_profile_enable(ctx, True)
     for _ in range(min(max(a.steps, 1), 3)):
-        U.zero_()
-        qn.qn_solve(ctx, U, f, max_it=100)
+        reset_start()
+        qn.qn_solve(ctx, U, f, max_it=max_it)
     torch.cuda.synchronize()
     prof = qn.qn_profile_read(ctx)
     qn.qn_profile_enable(ctx, False)
@@ -451,12 +511,12 @@ def main():
         U_np = U_h.numpy()
         e2e_ms = []
         for rep in range(3):
-            U_np[:] = 0.0
+            U_np[:] = 0.0 if U0_np is None else U0_np
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            qn.qn_solve_host(ctx, U_np, f_h.numpy(), max_it=100, graph=True)
+            qn.qn_solve_host(ctx, U_np, f_h.numpy(), max_it=max_it, graph=True)
             e1.record(stream)
             torch.cuda.synchronize()
             if rep > 0:
@@ -471,16 +531,16 @@ def main():
     if not a.no_fp64 and a.precision == "bf16x3":
         del ctx
         torch.cuda.empty_cache()
-        ctx64 = qn.QnContext(3, n, "fp64")
-        U.zero_()
+        ctx64 = qn.QnContext(3, n, "fp64", **ctx_kw)
+        reset_start()
         qn.qn_solve(ctx64, U, f, max_it=1)           # load kernels
         torch.cuda.synchronize()
         qn.qn_profile_enable(ctx64, True)
-        U.zero_()
+        reset_start()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        r64, _ = qn.qn_solve(ctx64, U, f, max_it=100)
+        r64, _ = qn.qn_solve(ctx64, U, f, max_it=max_it)
         e1.record(stream)
         torch.cuda.synchronize()
         p64 = qn.qn_profile_read(ctx64)
@@ -510,18 +570,49 @@ def main():
         del ctx64, A, B
 
     batched = None
-    if not a.no_batched and a.precision == "bf16x3":
+    if not a.no_batched and a.precision == "bf16x3" and not ex1:
         batched = run_batched(qn)
 
     cpu = None
     if not a.no_cpu and rank == 0 and world == 1:
-        ms_cpu, det = cpu_oracle_baseline(n, a.seed)
+        if ex1:
+            ms_cpu, det = cpu_oracle_baseline_ex1(n, a.seed)
+            small = "33^3, same kind of start"
+        else:
+            ms_cpu, det = cpu_oracle_baseline(n, a.seed)
+            small = "127^3, same seed"
         cpu = {"value": round(ms_cpu, 1), "unit": "ms", "cores": det["cores"], "kind": "oracle",
                "sample": (f"1 quasi-Newton iteration of the FP64 numpy oracle at {n}^3 "
                           f"({det['per_iteration_s']:.2f} s) x {det['iterations_assumed']} iterations "
-                          f"(oracle count at 127^3, same seed)")}
+                          f"(oracle count at {small})")}
 
-    if rank == 0:
+    if rank == 0 and ex1:
+        paper = PAPER_EX1.get(n)
+        line = {
+            "metric": METRIC_EX1, "value": round(ms_max, 3), "unit": "ms", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_max, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3+f64" if a.precision == "bf16x3" else "f64",
+            "data": "synthetic (closed-form source of u* = cos(pi x)+cos(pi y)+cos(pi z); seed-drawn "
+                    "start perturbation)",
+            "config": {"workload": f"3-D -Lap u + 10u + 10u^3 + Vu = f on (-1,1)^3, zero normal derivative "
+                                   f"(ghost points), {n}^3 nodes ({N} unknowns), tol 1e-10 on ||F||/||f||, "
+                                   f"start u* + 0.1 p (seed {a.seed})",
+                       "n": n, "dim": 3, "precision": a.precision,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": f"inputs {'larger' if 8 * N > 129e6 else 'smaller'} than L2 (f, U: "
+                             f"{8 * N / 1e9:.2f} GB each)",
+                       "launch": "iterations >= 2 replayed from a CUDA graph (qn_opts.graph)"},
+            "iterations": iters[0] if len(set(iters)) == 1 else iters,
+            "final_rel": max(rels), "converged": ok,
+            "paper_a100": ({"iterations": paper[0], "seconds": paper[1],
+                            "source": "Table results3D_mesh, beta=(min+max)/2, NVIDIA A100 80GB, MATLAB; "
+                                      "stopping tolerance not stated"} if paper else None),
+            "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
+            "e2e": e2e, "plain_fp64": plain, "cpu_baseline": cpu, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    elif rank == 0:
         line = {
             "metric": METRIC, "value": round(ms_max, 3), "unit": "ms", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_max, 3),
@@ -543,6 +634,45 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_reference_ex1(a):
+    """--impl reference --workload ex1: the FP64 CPU oracle timed on Example 1."""
+    from oracle import qn_oracle_bc as ob
+    from paper_2502_03611_gb300 import inputs as I
+    n = a.n
+    u, f, v, h = I.ex1_problem(33)
+    _, h_small, _ = ob.qn_solve(f, h, "neumann", U0=u + I.ex1_perturbation(33, a.seed, 0.1), lam=I.EX1_A,
+                                b=I.EX1_B, V=ob.potential(v, 3, 33))
+    its = len(h_small) - 1
+    u, f, v, h = I.ex1_problem(n)
+    V = ob.potential(v, 3, n)
+    eig = ob.eig_1d(n, h, "neumann")
+    U = u + I.ex1_perturbation(n, a.seed, 0.1)
+    warm = min(a.warmup, 2)
+    steps = min(a.steps, 5)
+    for _ in range(warm):
+        U, _, _ = ob.qn_step(U, f, h, "neumann", eig, I.EX1_A, I.EX1_B, V)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        U, _, _ = ob.qn_step(U, f, h, "neumann", eig, I.EX1_A, I.EX1_B, V)
+        times.append(time.perf_counter() - t0)
+    per_it = statistics.mean(times)
+    value = per_it * its * 1e3
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = (f"{steps} timed quasi-Newton iterations (after {warm} untimed) of the FP64 numpy oracle at "
+              f"{n}^3, mean {per_it:.2f} s/iteration x {its} iterations (the oracle's count at 33^3)")
+    line = {"impl": "reference", "metric": METRIC_EX1, "value": round(value, 3), "unit": "ms",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(value, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (closed-form source, seed-drawn start perturbation)",
+            "config": {"workload": f"3-D Example 1 (Sec. 6.3), {n}^3 nodes, Neumann, tol 1e-10",
+                       "n": n, "dim": 3, "precision": "fp64 (CPU oracle)", "parallelism": "none"},
+            "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -51,7 +51,7 @@ import numpy as np
 from .qn_oracle import fast_diag_solve
 
 __all__ = ["mesh_width", "fd_matrix_1d", "eig_1d", "apply_operator", "potential", "residual",
-           "jacobian_diag", "beta_rule", "qn_solve", "dense_operator", "newton_dense",
+           "jacobian_diag", "beta_rule", "qn_step", "qn_solve", "dense_operator", "newton_dense",
            "trapezoid_weights"]
 
 
@@ -149,6 +149,15 @@ def beta_rule(U, b: float = 1.0, V=None) -> float:
     """beta_n = (lambda_max + lambda_min)/2 of diag(3 b U^2 + V) (eq. identity-method)."""
     d = jacobian_diag(U, b, V)
     return 0.5 * (float(d.max()) + float(d.min()))
+
+
+def qn_step(U, f, h: float, bc: str, eig=None, lam: float = 0.0, b: float = 1.0, V=None,
+            beta=None, step: float = 1.0):
+    """One update of eq. identity-method. Returns (U_next, r, beta_used)."""
+    S, S_inv, lam1d = eig if eig is not None else eig_1d(f.shape[0], h, bc)
+    r = residual(U, f, h, bc, lam, b, V)
+    beta_n = beta_rule(U, b, V) if beta is None else float(beta)
+    return U - step * fast_diag_solve(r, S, S_inv, lam1d, lam + beta_n), r, beta_n
 
 
 def qn_solve(f, h: float, bc: str, U0=None, tol: float = 1e-10, max_it: int = 500,
