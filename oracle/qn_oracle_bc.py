@@ -34,6 +34,13 @@ systems):
 * Inverse, Sec. 4.1 eq. fin_inverse, with qn_oracle.fast_diag_solve (it takes
   S and S^{-1} separately, so a non-orthogonal S is fine).
 
+* Nonlinear eigenproblem, Sec. 4.4 (eqs. Eigenvalue_p, system_qusi,
+  system_normal): with f(U) = lam U + b U^3 + V U, each step takes the
+  Rayleigh quotient lambda_n = <A U + f(U), U> / <U, U>, the residual
+  F = A U + f(U) - lambda_n U, beta_n = mid-range of diag(3 b U^2 + V) - lambda_n
+  (the Jacobian of N_h = f - lambda_n U with lambda_n held fixed), the update
+  U~ = U - (A_h + beta_n I)^{-1} F and the normalisation U = U~ / ||U~||.
+
 Readings (also listed in the design notes):
 * The three-dimensional Example 1 of Sec. 6.3 has a u as a separate term; it
   is taken as the linear coefficient lam = a. beta_n then only sees
@@ -41,6 +48,11 @@ Readings (also listed in the design notes):
   spectrum by a and gives the same shift lam + beta_n.
 * "n^3 degrees of freedom" with Neumann data is read as n nodes per axis,
   boundary nodes included (they are unknowns of the ghost-point scheme).
+* Eigenproblem inner product: <U, W> = sum over nodes of m U W with the
+  lumped mass m = h^dim times the trapezoid weights (1/2 per face the node
+  lies on, Neumann data), the rectangle-rule L2 product the paper's M
+  matrices stand for; A_h is self-adjoint in it. The stopping rule is the
+  relative eigen-residual ||F|| / |lambda_n| <= tol (||U|| = 1).
 """
 from __future__ import annotations
 
@@ -52,7 +64,7 @@ from .qn_oracle import fast_diag_solve
 
 __all__ = ["mesh_width", "fd_matrix_1d", "eig_1d", "apply_operator", "potential", "residual",
            "jacobian_diag", "beta_rule", "qn_step", "qn_solve", "dense_operator", "newton_dense",
-           "trapezoid_weights"]
+           "trapezoid_weights", "mass_weights", "eig_residual", "qn_eig_solve", "newton_eig_dense"]
 
 
 def mesh_width(n: int, bc: str, length: float = 1.0) -> float:
@@ -217,3 +229,83 @@ def newton_dense(f, h: float, bc: str, U0=None, tol: float = 1e-12, max_it: int 
         J = A + np.diag(3.0 * b * u * u + Vv)
         u = u - np.linalg.solve(J, F)
     return u.reshape(f.shape)
+
+
+# ----------------------------------------------------------------------------
+# Nonlinear eigenproblem (Sec. 4.4)
+# ----------------------------------------------------------------------------
+def mass_weights(n: int, dim: int, h: float, bc: str) -> np.ndarray:
+    """Lumped mass per node: h^dim times the product of the 1-D trapezoid weights."""
+    w = trapezoid_weights(n, bc)
+    m = np.ones((n,) * dim) * h ** dim
+    for a in range(dim):
+        shape = [1] * dim
+        shape[a] = n
+        m = m * w.reshape(shape)
+    return m
+
+
+def eig_residual(U, h: float, bc: str, lam: float = 0.0, b: float = 1.0, V=None):
+    """(F, lambda_n): lambda_n = <A U + f(U), U> / <U, U> (Sec. 4.4), F = A U + f(U) - lambda_n U
+    with f(U) = lam U + b U^3 + V U and the mass-weighted product."""
+    m = mass_weights(U.shape[0], U.ndim, h, bc)
+    r0 = residual(U, np.zeros_like(U), h, bc, lam, b, V)
+    lam_n = float(np.sum(m * r0 * U)) / float(np.sum(m * U * U))
+    return r0 - lam_n * U, lam_n
+
+
+def qn_eig_solve(U0, h: float, bc: str, lam: float = 0.0, b: float = 1.0, V=None, tol: float = 1e-10,
+                 max_it: int = 5000):
+    """Quasi-Newton for the nonlinear eigenproblem (Sec. 4.4 eqs. system_qusi, system_normal).
+
+    U0 is normalised first (<U0, U0> = 1). Each step: lambda_n and F (eig_residual);
+    stop when ||F|| / |lambda_n| <= tol; beta_n = (max + min)/2 of 3 b U^2 + V, minus
+    lambda_n (lam counts in f, so A_h here is the difference operator alone and the
+    shift is lam + mid-range - lambda_n = beta_n as computed); U~ = U - (A_h + beta_n I)^{-1} F;
+    then U = U~ / ||U~||.
+    Returns (U, lambda_n, history, converged); history[i] has rel, lambda and beta of U_i."""
+    n, dim = U0.shape[0], U0.ndim
+    m = mass_weights(n, dim, h, bc)
+    S, S_inv, lam1d = eig_1d(n, h, bc)
+    U = np.array(U0, dtype=np.float64, copy=True)
+    U = U / math.sqrt(float(np.sum(m * U * U)))
+    history = []
+    for it in range(max_it + 1):
+        F, lam_n = eig_residual(U, h, bc, lam, b, V)
+        rel = math.sqrt(float(np.sum(m * F * F))) / abs(lam_n)
+        d = jacobian_diag(U, b, V) + lam
+        beta_n = 0.5 * (float(d.max()) + float(d.min())) - lam_n
+        history.append({"rel": rel, "lambda": lam_n, "beta": beta_n})
+        if rel <= tol:
+            return U, lam_n, history, True
+        if not math.isfinite(rel) or it == max_it:
+            break
+        Ut = U - fast_diag_solve(F, S, S_inv, lam1d, beta_n)
+        U = Ut / math.sqrt(float(np.sum(m * Ut * Ut)))
+    return U, lam_n, history, False
+
+
+def newton_eig_dense(U0, lam0: float, h: float, bc: str, lam: float = 0.0, b: float = 1.0, V=None,
+                     tol: float = 1e-13, max_it: int = 50):
+    """Newton's method on the bordered system A U + f(U) - lambda U = 0, (<U, U> - 1)/2 = 0
+    for the unknowns (U, lambda), dense (tiny grids)."""
+    n, dim = U0.shape[0], U0.ndim
+    A = dense_operator(n, dim, h, bc, lam)
+    mv = mass_weights(n, dim, h, bc).ravel()
+    Vv = np.zeros(U0.size) if V is None else V.ravel()
+    u = np.array(U0, dtype=np.float64).ravel()
+    lm = float(lam0)
+    N = u.size
+    for _ in range(max_it):
+        F1 = A @ u + b * u ** 3 + Vv * u - lm * u
+        F2 = 0.5 * (float(np.sum(mv * u * u)) - 1.0)
+        if math.sqrt(float(np.sum(F1 * F1)) + F2 * F2) <= tol * abs(lm) * math.sqrt(N):
+            break
+        J = np.zeros((N + 1, N + 1))
+        J[:N, :N] = A + np.diag(3.0 * b * u * u + Vv - lm)
+        J[:N, N] = -u
+        J[N, :N] = mv * u
+        step = np.linalg.solve(J, np.concatenate([F1, [F2]]))
+        u = u - step[:N]
+        lm = lm - step[N]
+    return u.reshape(U0.shape), lm

@@ -157,3 +157,112 @@ def test_ex1_converges_at_second_order():
         assert ok
         errs.append(float(np.max(np.abs(U - u))))
     assert 3.3 < errs[0] / errs[1] < 4.7
+
+
+# ---------------------------------------------------------------------------------------------
+# nonlinear eigenproblem (Sec. 4.4)
+# ---------------------------------------------------------------------------------------------
+def _eig_grid(n, bc, L=16.0):
+    h = ob.mesh_width(n, bc, L)
+    x = -L / 2 + (h * np.arange(1, n + 1) if bc == "dirichlet" else h * np.arange(n))
+    return h, x
+
+
+def _start(x, L=16.0):
+    g = np.cos(math.pi * x / L)
+    return g[None, None, :] * g[None, :, None] * g[:, None, None]
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+def test_eig_linear_separable_ground_state(bc):
+    """b = 0 with a separable potential: the eigenproblem separates, so the ground state is the
+    product of the 1-D ground states of H + diag(v_a) (from a general dense eigensolver) and
+    lambda is the sum of their eigenvalues."""
+    n = 12
+    h, x = _eig_grid(n, bc)
+    # harmonic wells: simple, well-separated 1-D ground states (a nearly degenerate pair would
+    # leave the eigenvector undetermined)
+    tabs = np.stack([0.3 * x * x, 0.5 * x * x, 0.2 * (x - 1.0) ** 2])
+    V = ob.potential(tabs, 3, n)
+    U, lam, hist, ok = ob.qn_eig_solve(_start(x), h, bc, b=0.0, V=V, tol=1e-11, max_it=20000)
+    assert ok
+    lam_ref, vecs = 0.0, []
+    for a in range(3):
+        ev, W = np.linalg.eig(ob.fd_matrix_1d(n, h, bc) + np.diag(tabs[a]))
+        k = int(np.argmin(ev.real))
+        lam_ref += float(ev[k].real)
+        vecs.append(np.real(W[:, k]))
+    assert lam == pytest.approx(lam_ref, rel=1e-10)
+    Uref = vecs[0][None, None, :] * vecs[1][None, :, None] * vecs[2][:, None, None]
+    m = ob.mass_weights(n, 3, h, bc)
+    Uref = Uref / math.sqrt(float(np.sum(m * Uref * Uref)))
+    Uref = Uref * np.sign(np.sum(Uref * U))
+    assert np.abs(U - Uref).max() <= 1e-8 * np.abs(Uref).max()
+
+
+def test_eig_hellmann_feynman():
+    """d lambda / d b at b = 0 equals <U0^3, U0> = sum m U0^4 for the normalised linear ground
+    state U0 (first-order perturbation of the Rayleigh quotient)."""
+    n, bc = 10, "dirichlet"
+    h, x = _eig_grid(n, bc)
+    V = ob.potential(np.stack([0.3 * x * x, 0.5 * x * x, 0.2 * (x - 1.0) ** 2]), 3, n)
+    U0, lam0, _, ok0 = ob.qn_eig_solve(_start(x), h, bc, b=0.0, V=V, tol=1e-12, max_it=20000)
+    db = 1e-3
+    _, lam1, _, ok1 = ob.qn_eig_solve(U0, h, bc, b=db, V=V, tol=1e-12, max_it=20000)
+    assert ok0 and ok1
+    m = ob.mass_weights(n, 3, h, bc)
+    slope = float(np.sum(m * U0 ** 4))
+    assert (lam1 - lam0) / db == pytest.approx(slope, rel=2e-3)
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+def test_eig_limit_solves_bordered_system(bc):
+    """The quasi-Newton limit is a solution of A U + b U^3 + V U = lambda U, <U, U> = 1:
+    dense Newton on that bordered system, started off it, converges back to it."""
+    n = 5
+    h, x = _eig_grid(n, bc)
+    V = ob.potential(I.ex1_potential_1d(x), 3, n)
+    U, lam, hist, ok = ob.qn_eig_solve(_start(x), h, bc, b=1600.0, V=V, tol=1e-12, max_it=20000)
+    assert ok
+    Un, lamn = ob.newton_eig_dense(U * (1 + 0.01 * I.random_field(U.shape, 4)), lam * 1.01, h, bc, b=1600.0, V=V)
+    assert lamn == pytest.approx(lam, rel=1e-11)
+    assert np.abs(Un - U).max() <= 1e-9 * np.abs(U).max()
+
+
+def test_eig_residual_is_mass_orthogonal():
+    """With the Rayleigh quotient in the mass-weighted product, F is M-orthogonal to U for
+    every U (<F, U>_M = <A U + f, U>_M - lambda <U, U>_M = 0); with Neumann data the face
+    weights matter: the unweighted product would leave a visible <F, U>_M."""
+    n, bc = 7, "neumann"
+    h, x = _eig_grid(n, bc)
+    V = ob.potential(0.4 * x * x, 3, n)
+    U = 1.0 + I.random_field((n, n, n), 8)
+    F, lam = ob.eig_residual(U, h, bc, 0.3, 50.0, V)
+    m = ob.mass_weights(n, 3, h, bc)
+    scale = math.sqrt(float(np.sum(m * F * F)) * float(np.sum(m * U * U)))
+    assert abs(float(np.sum(m * F * U))) <= 1e-13 * scale
+    lam_flat = float(np.sum((F + lam * U) * U)) / float(np.sum(U * U))
+    assert abs(lam_flat - lam) > 1e-6 * abs(lam)
+
+
+def test_eig_linear_rate_is_second_eigenvalue_ratio():
+    """b = 0: near the limit, U_{k+1} is proportional to T U_k with
+    T = (A_h + c - lambda)^{-1} (c - V), c = (max V + min V)/2 (beta_n + lambda_n = c). U* is
+    T's eigenvector with eigenvalue 1, so the observed rate of rel is the largest |mu| of T
+    over the other eigenvectors. This pins the sign and size of beta_n."""
+    n, bc = 6, "dirichlet"
+    h, x = _eig_grid(n, bc, L=6.0)
+    V = ob.potential(np.stack([3.0 * x * x, 4.0 * x * x, 2.0 * (x - 0.5) ** 2]), 3, n)
+    U, lam, hist, ok = ob.qn_eig_solve(_start(x, L=6.0), h, bc, b=0.0, V=V, tol=1e-13, max_it=20000)
+    assert ok
+    c = 0.5 * (V.max() + V.min())
+    A = ob.dense_operator(n, 3, h, bc)
+    T = np.linalg.solve(A + (c - lam) * np.eye(n ** 3), np.diag(c - V.ravel()))
+    mu = np.sort(np.abs(np.linalg.eigvals(T)))[::-1]
+    assert abs(mu[0] - 1.0) < 1e-8
+    rel = np.array([e["rel"] for e in hist])
+    k1 = len(rel) - 3
+    k0 = max(k1 - 30, 1)
+    rate = (rel[k1] / rel[k0]) ** (1.0 / (k1 - k0))
+    assert 0.2 < mu[1] < 1.0
+    assert rate == pytest.approx(mu[1], rel=0.03)
