@@ -95,6 +95,7 @@ typedef struct qn_stats {
     double fu_max;    /* largest entry */
     double beta;      /* beta_n applied to this iterate (paper rule or fixed) */
     double rel;       /* res_norm / f_norm */
+    double lambda;    /* qn_eig_solve: the Rayleigh quotient lambda_n of this iterate; else 0 */
 } qn_stats;
 
 typedef struct qn_opts {
@@ -332,6 +333,26 @@ int qn_interp3d_f32(const double *src, int m_from, float *dst, int m_to, int B, 
 int qn_solve_warm(qn_ctx *ctx, qn_net *net, double *U, const double *f, int n, double in_scale,
                   double out_scale, const qn_opts *opts, qn_result *res, int *used_warm, void *stream);
 
+/* ---- nonlinear eigenproblem (Sec. 4.4; Sec. 6.3 Example 2) ------------------------------
+ * Finds u and lambda with -Lap u + f(u) = lambda u, ||u|| = 1, f(u) = lam u + b u^3 + V u
+ * (the context's boundary data, lam, b and potential). Iteration (eqs. system_qusi,
+ * system_normal):
+ *   lambda_n = <A_h U + f(U), U> / <U, U>,   F = A_h U + f(U) - lambda_n U,
+ *   beta_n = (max + min)/2 of diag(lam + 3 b U^2 + V) - lambda_n (or opts->beta_value),
+ *   U~ = U - step (A_h + beta_n I)^{-1} F  (A_h the difference operator alone),
+ *   U = U~ / ||U~||,
+ * stopping when ||F|| / |lambda_n| <= opts->tol. <V, W> = h^dim sum w V W, w the product
+ * of the 1-D trapezoid weights (1/2 at Neumann face nodes, else 1).
+ * U: device, n^dim doubles: in = start (normalised by the call), out = last iterate, with
+ * ||U|| = 1. opts: host, NULL = tol 1e-10, max_it 4096, paper beta, step 1, sync_every 8.
+ * lambda: host, may be NULL: lambda_n of the returned iterate. history (host, may be NULL):
+ * per iterate res_norm = ||F||, f_norm = |lambda_n| ||U||, fu_min / fu_max = extremes of
+ * lam + 3 b U^2 + V, beta = beta_n, rel, lambda = lambda_n. With opts->graph every group of
+ * sync_every iterations is replayed from a CUDA graph. BF16X3 contexts allocate n^dim
+ * doubles on the first call. Synchronises `stream`. Returns res->status. */
+int qn_eig_solve(qn_ctx *ctx, double *U, const qn_opts *opts, qn_result *res, double *lambda,
+                 qn_stats *history, int history_len, void *stream);
+
 /* ---- measurement ------------------------------------------------------------- */
 typedef struct qn_profile {
     long long launches;       /* kernels launched that did work since qn_profile_enable
@@ -355,6 +376,8 @@ typedef struct qn_profile {
     int split_products;       /* 1: the last shifted inverse used the reflection-split mode
                                  products (3-D split solve, n+ padding a multiple of 128):
                                  half the tensor work of the dense products */
+    int normalize_launches;   /* qn_eig_solve: the norm and scale kernels of the normalisation */
+    double normalize_ms;
 } qn_profile;
 
 /* on != 0: from now on record a pair of CUDA events around every kernel

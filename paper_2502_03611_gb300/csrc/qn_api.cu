@@ -106,10 +106,12 @@ struct qn_ctx {
     // pairs with lam added to the last axis (k_residual_tiled / mirror); nullptr: V = 0
     double *pot64;
     float2 *pot2;
+    double *eig_r0;       // eigen solves, BF16X3: A_h U + f(U) between the two residual passes
+    int g_kind;           // graph contents: 0 quasi-Newton iterations, 1 eigen iterations
 };
 
 enum ProfKind { PK_RESIDUAL = 0, PK_FINALIZE = 1, PK_MP_STORE = 2, PK_MP_DIVIDE = 3, PK_MP_LAST = 4,
-                PK_SPLIT = 5, PK_RESIDUAL_TILED = 6, PK_COUNT = 7 };
+                PK_SPLIT = 5, PK_RESIDUAL_TILED = 6, PK_NORMALIZE = 7, PK_COUNT = 8 };
 
 // Begin/end a timed launch. With profiling off these only count launches.
 static long prof_begin(qn_ctx *c, int kind, cudaStream_t s) {
@@ -222,6 +224,7 @@ static void ctx_free(qn_ctx *c) {
     cudaFree(c->lam32_split);
     cudaFree(c->pot64);
     cudaFree(c->pot2);
+    cudaFree(c->eig_r0);
     for (int b = 0; b < 2; ++b) {
         cudaFree(c->w64[b]);
         cudaFree(c->bhi[b]);
@@ -673,8 +676,11 @@ static int enqueue_iteration(qn_ctx *c, double *U, const double *f, double step,
 // Capture `chunk` steady-state iterations (third iteration on: the residual
 // takes its fixed-point exponent from the previous iterate, no preparation
 // passes) into a CUDA graph on a private stream, once per (U, f, step, chunk).
-static int ensure_iteration_graph(qn_ctx *c, double *U, const double *f, double step, int chunk) {
-    if (c->gexec && c->g_U == U && c->g_f == f && c->g_step == step && c->g_chunk == chunk) return QN_OK;
+static int enqueue_eig_iteration(qn_ctx *c, double *U, double step, cudaStream_t s);
+
+static int ensure_iteration_graph(qn_ctx *c, double *U, const double *f, double step, int chunk, int kind = 0) {
+    if (c->gexec && c->g_U == U && c->g_f == f && c->g_step == step && c->g_chunk == chunk && c->g_kind == kind)
+        return QN_OK;
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
@@ -686,7 +692,8 @@ static int ensure_iteration_graph(qn_ctx *c, double *U, const double *f, double 
     int rc = QN_OK;
     for (int k = 0; k < chunk && rc == QN_OK; ++k) {
         c->cur_iter = 2 + k;
-        rc = enqueue_iteration(c, U, f, step, c->cap_stream);
+        rc = (kind == 1) ? enqueue_eig_iteration(c, U, step, c->cap_stream)
+                         : enqueue_iteration(c, U, f, step, c->cap_stream);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
@@ -708,6 +715,7 @@ static int ensure_iteration_graph(qn_ctx *c, double *U, const double *f, double 
     c->g_f = f;
     c->g_step = step;
     c->g_chunk = chunk;
+    c->g_kind = kind;
     return QN_OK;
 }
 
@@ -1019,5 +1027,139 @@ extern "C" int qn_profile_read(qn_ctx *c, qn_profile *out) {
     out->mp_divide_ms = ms[PK_MP_DIVIDE];
     out->mp_last_launches = cnt[PK_MP_LAST];
     out->mp_last_ms = ms[PK_MP_LAST];
+    out->normalize_launches = cnt[PK_NORMALIZE];
+    out->normalize_ms = ms[PK_NORMALIZE];
     return QN_OK;
+}
+
+// ---- nonlinear eigenproblem (Sec. 4.4) ----------------------------------------------------------
+// One iteration (qn_eig.cu): Rayleigh pass, lambda_n / beta_n, F = r0 - lambda_n U into
+// the inverse's input, stop test, the shifted inverse with the update, normalisation.
+static int enqueue_eig_iteration(qn_ctx *c, double *U, double step, cudaStream_t s) {
+    const double hd = pow(c->h, c->dim);
+    const int grid = c->nparts;
+    const bool fp64 = (c->prob.precision == QN_PREC_FP64);
+    double *r0 = fp64 ? c->w64[1] : c->eig_r0;   // w64[1] is free until the first mode product
+    const bool mirror = !fp64 && c->split;
+    long pr = prof_begin(c, PK_RESIDUAL, s);
+    int rc = launch_eig_rayleigh(U, r0, c->n, c->dim, c->prob.bc, c->inv_h2, c->prob.lam, c->prob.b, c->pot64,
+                                 c->partials, grid, c->st, s);
+    prof_end(c, pr, s);
+    if (rc) return rc;
+    pr = prof_begin(c, PK_FINALIZE, s);
+    rc = launch_eig_finalize1(c->partials, grid, hd, c->st, s);
+    prof_end(c, pr, s);
+    if (rc) return rc;
+    pr = prof_begin(c, PK_RESIDUAL, s);
+    rc = launch_eig_residual2(U, r0, c->n, c->P, c->dim, c->prob.bc, hd, fp64 ? c->w64[0] : nullptr,
+                              fp64 ? nullptr : c->bhi[0], fp64 ? nullptr : c->blo[0], mirror, c->partials, grid,
+                              c->st, s);
+    prof_end(c, pr, s);
+    if (rc) return rc;
+    pr = prof_begin(c, PK_FINALIZE, s);
+    rc = launch_finalize(c->partials, grid, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 1, 1, 2, s);
+    prof_end(c, pr, s);
+    if (rc) return rc;
+    rc = enqueue_inverse(c, nullptr, U, true, step, s, mirror);
+    if (rc) return rc;
+    pr = prof_begin(c, PK_NORMALIZE, s);
+    rc = launch_eig_normalize(U, c->n, c->dim, c->prob.bc, hd, c->partials, grid, c->st, s);
+    prof_end(c, pr, s);
+    c->launches += 1;   // two kernels
+    return rc;
+}
+
+extern "C" int qn_eig_solve(qn_ctx *c, double *U, const qn_opts *opts, qn_result *res, double *lambda,
+                            qn_stats *history, int history_len, void *stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (bad_ptr(U)) {
+        set_error("qn_eig_solve: null U");
+        return QN_EINVAL;
+    }
+    qn_opts o;
+    if (opts) {
+        o = *opts;
+    } else {
+        o.tol = 1e-10;
+        o.max_it = kHistCap - 1;
+        o.beta_mode = QN_BETA_PAPER;
+        o.beta_value = 0.0;
+        o.step = 1.0;
+        o.sync_every = 8;
+        o.graph = 0;
+    }
+    if (!(o.tol >= 0.0) || o.max_it < 0 || o.max_it > kHistCap - 1 || !isfinite(o.step) ||
+        (o.beta_mode != QN_BETA_PAPER && o.beta_mode != QN_BETA_FIXED) ||
+        (o.beta_mode == QN_BETA_FIXED && !isfinite(o.beta_value))) {
+        set_error("qn_eig_solve: invalid options");
+        return QN_EINVAL;
+    }
+    if (o.sync_every < 1) o.sync_every = 1;
+    if (history_len < 0 || (history_len > 0 && history == nullptr)) {
+        set_error("qn_eig_solve: invalid history buffer");
+        return QN_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->prob.precision == QN_PREC_BF16X3 && !c->eig_r0)
+        QN_CUDA(cudaMalloc(&c->eig_r0, sizeof(double) * (size_t)c->N));
+    rc = reset_state(c, o.tol, o.max_it, o.beta_mode, o.beta_value, s);
+    if (rc) return rc;
+    const size_t first_rec = c->prof_used;
+    const long long launches0 = c->launches;
+    // the start is normalised first (<U_0, U_0> = 1)
+    c->cur_iter = -1;
+    const long pr = prof_begin(c, PK_NORMALIZE, s);
+    rc = launch_eig_normalize(U, c->n, c->dim, c->prob.bc, pow(c->h, c->dim), c->partials, c->nparts, c->st, s);
+    prof_end(c, pr, s);
+    if (rc) return rc;
+    DevState h;
+    memset(&h, 0, sizeof(h));
+    int enqueued = 0;
+    const bool use_graph = o.graph != 0 && !c->prof_on;
+    while (!h.done && enqueued <= o.max_it) {
+        if (use_graph && enqueued + o.sync_every <= o.max_it + 1) {
+            rc = ensure_iteration_graph(c, U, nullptr, o.step, o.sync_every, 1);
+            if (rc) return rc;
+            QN_CUDA(cudaGraphLaunch(c->gexec, s));
+            enqueued += o.sync_every;
+        } else {
+            for (int k = 0; k < o.sync_every && enqueued <= o.max_it; ++k, ++enqueued) {
+                c->cur_iter = enqueued;
+                rc = enqueue_eig_iteration(c, U, o.step, s);
+                if (rc) return rc;
+            }
+        }
+        rc = read_state(c, &h, s);
+        if (rc) return rc;
+    }
+    if (!h.done) {
+        set_error("qn_eig_solve: internal iteration accounting error");
+        return QN_ECUDA;
+    }
+    const int its = h.it;
+    const int status = h.status;
+    for (size_t i = first_rec; i < c->prof_used; ++i) {
+        qn_ctx::ProfRec &r = (*c->prof)[i];
+        const bool after_update = (r.kind >= PK_MP_STORE && r.kind <= PK_MP_LAST) || r.kind == PK_NORMALIZE;
+        if ((after_update && r.iter >= its) || (!after_update && r.iter > its)) r.valid = 0;
+    }
+    // per evaluated iterate 2 residual passes + 2 finalisers; per update 2 dim products and
+    // 2 normalisation kernels; 2 for normalising the start
+    c->launches = launches0 + 4LL * (its + 1) + (2LL * c->dim + 2) * its + 2;
+    qn_stats last;
+    QN_CUDA(cudaMemcpy(&last, c->hist + its, sizeof(qn_stats), cudaMemcpyDeviceToHost));
+    if (history && history_len > 0) {
+        const int cnt = (its + 1) < history_len ? (its + 1) : history_len;
+        QN_CUDA(cudaMemcpy(history, c->hist, sizeof(qn_stats) * cnt, cudaMemcpyDeviceToHost));
+    }
+    if (res) {
+        res->iterations = its;
+        res->status = status;
+        res->rel = last.rel;
+    }
+    if (lambda) *lambda = last.lambda;
+    if (status == QN_ENOTCONV) set_error("qn_eig_solve: max_it reached (rel %.3e)", last.rel);
+    if (status == QN_EDIVERGED) set_error("qn_eig_solve: diverged (rel %.3e)", last.rel);
+    return status;
 }

@@ -404,7 +404,8 @@ __global__ void k_umax_finish(DevState *st) {
 __global__ void __launch_bounds__(256) k_finalize(const double *partials, int nparts, DevState *st,
                                                   qn_stats *hist, int hist_cap, double b,
                                                   double lam, int update_state, int use_saved_fnorm,
-                                                  int pot) {
+                                                  int mode) {
+    const bool pot = (mode == 1), eig = (mode == 2);
     if (update_state && *(volatile int *)&st->done) return;
     Red4 acc{0.0, 0.0, INFINITY, 0.0};
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
@@ -426,8 +427,9 @@ __global__ void __launch_bounds__(256) k_finalize(const double *partials, int np
     }
     // extremes of diag(N_h)_U: 3 b U^2 from those of U^2, or taken directly with a potential
     const double fa = pot ? acc.mn : 3.0 * b * acc.mn, fb = pot ? acc.mx : 3.0 * b * acc.mx;
-    const double fu_min = fmin(fa, fb), fu_max = fmax(fa, fb);
-    const double beta = (st->beta_mode == QN_BETA_FIXED) ? st->beta_value : 0.5 * (fu_min + fu_max);
+    const double fu_min = eig ? st->eig_fu_min : fmin(fa, fb), fu_max = eig ? st->eig_fu_max : fmax(fa, fb);
+    const double beta = eig ? st->beta
+                            : (st->beta_mode == QN_BETA_FIXED) ? st->beta_value : 0.5 * (fu_min + fu_max);
     double rel;
     if (fn > 0.0)
         rel = res / fn;
@@ -442,6 +444,7 @@ __global__ void __launch_bounds__(256) k_finalize(const double *partials, int np
         s.fu_max = fu_max;
         s.beta = beta;
         s.rel = rel;
+        s.lambda = eig ? st->eig_lambda : 0.0;
         hist[it] = s;
     }
     if (!update_state) return;
@@ -451,11 +454,13 @@ __global__ void __launch_bounds__(256) k_finalize(const double *partials, int np
     if (pot) {
         st->fx_e = fx_exponent(st->umax_scan, st);
         st->umax_scan = 0ull;
-    } else {
+    } else if (!eig) {
         st->fx_e = (acc.mx < INFINITY) ? fx_exponent((unsigned long long)__double_as_longlong(sqrt(acc.mx)), st) : 0;
     }
-    st->beta = beta;
-    st->shift = lam + beta;
+    if (!eig) {
+        st->beta = beta;
+        st->shift = lam + beta;
+    }
     if (rel <= st->tol) {
         st->status = QN_OK;
         st->done = 1;
@@ -1427,9 +1432,9 @@ int launch_umax(const double *U, long long N, DevState *st, int grid, cudaStream
 
 int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *hist,
                         int hist_cap, double b, double lam, int update_state, int use_saved_fnorm,
-                        int pot, cudaStream_t s) {
+                        int mode, cudaStream_t s) {
     k_finalize<<<1, 256, 0, s>>>(partials, nparts, st, hist, hist_cap, b, lam, update_state,
-                                 use_saved_fnorm, pot);
+                                 use_saved_fnorm, mode);
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }
@@ -1449,7 +1454,7 @@ namespace {
 
 constexpr int kNoAllocMaxBlocks = 1024;               // reduction blocks per call
 constexpr int kNoAllocStateDoubles = 16;              // DevState (<= 128 B)
-constexpr int kNoAllocStatsDoubles = 8;               // one qn_stats (48 B)
+constexpr int kNoAllocStatsDoubles = 8;               // one qn_stats (56 B)
 constexpr int kNoAllocDoubles = 4 * kNoAllocMaxBlocks + kNoAllocStateDoubles + kNoAllocStatsDoubles;
 static_assert(sizeof(DevState) <= kNoAllocStateDoubles * sizeof(double), "DevState too large");
 static_assert(sizeof(qn_stats) <= kNoAllocStatsDoubles * sizeof(double), "qn_stats too large");

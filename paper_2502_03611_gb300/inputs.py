@@ -281,3 +281,34 @@ def ex2d1_problem(n: int):
     u = np.cos(2.0 * math.pi * x)[:, None] * np.cos(math.pi * x)[None, :]
     f = (5.0 * math.pi ** 2 + 1.0) * u + u ** 3
     return u, f, 2.0 / (n - 1)
+
+
+# ---------------------------------------------------------------------------
+# Nonlinear eigenproblem: the three-dimensional Example 2 of Sec. 6.3
+# ---------------------------------------------------------------------------
+EX2_ALPHA = 1600.0
+EX2_LENGTH = 16.0
+
+
+def ex2_problem(n: int):
+    """Data of -Lap u + 1600 u^3 + V u = lambda u on (-8,8)^3, u = 0 on the boundary
+    (Sec. 6.3, Example 2), V as in Example 1, on n interior nodes per axis.
+    Returns (v, h, x): the 1-D potential table, h = 16/(n+1) and the nodes."""
+    h = EX2_LENGTH / (n + 1)
+    x = -0.5 * EX2_LENGTH + h * np.arange(1, n + 1, dtype=np.float64)
+    return ex1_potential_1d(x), h, x
+
+
+def ex2_start(n: int, seed: int = 0, eps: float = 0.1, degree: int = 4) -> np.ndarray:
+    """Start of the eigen iteration: g(x) g(y) g(z) (1 + eps p), g(t) = cos(pi t / 16) (the box's
+    ground state, zero on the boundary) and p a random polynomial of degree `degree` per axis
+    in (x/8, y/8, z/8) with U(-1,1) coefficients from SplitMix64(seed), normalised by its
+    maximum over the nodes (the paper's perturbation, Sec. 6.3). Not normalised."""
+    _, _, x = ex2_problem(n)
+    m = degree + 1
+    c = random_field((m, m, m), seed, -1.0, 1.0)
+    Vp = np.vander(x / (0.5 * EX2_LENGTH), m, increasing=True)
+    q = np.einsum("kji,zk,yj,xi->zyx", c, Vp, Vp, Vp, optimize=True)
+    g = np.cos(math.pi * x / EX2_LENGTH)
+    G = g[None, None, :] * g[None, :, None] * g[:, None, None]
+    return G * (1.0 + eps * q / float(np.max(np.abs(q))))

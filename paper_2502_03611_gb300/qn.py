@@ -44,7 +44,7 @@ class QnProblem(ctypes.Structure):
 class QnStats(ctypes.Structure):
     _fields_ = [("res_norm", ctypes.c_double), ("f_norm", ctypes.c_double),
                 ("fu_min", ctypes.c_double), ("fu_max", ctypes.c_double),
-                ("beta", ctypes.c_double), ("rel", ctypes.c_double)]
+                ("beta", ctypes.c_double), ("rel", ctypes.c_double), ("lambda", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,7 +69,8 @@ class QnProfile(ctypes.Structure):
                 ("mp_divide_launches", ctypes.c_int), ("mp_divide_ms", ctypes.c_double),
                 ("mp_last_launches", ctypes.c_int), ("mp_last_ms", ctypes.c_double),
                 ("residual_tiled_launches", ctypes.c_int), ("residual_tiled_ms", ctypes.c_double),
-                ("split_products", ctypes.c_int)]
+                ("split_products", ctypes.c_int),
+                ("normalize_launches", ctypes.c_int), ("normalize_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -146,6 +147,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                          ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult),
                                          ctypes.POINTER(ctypes.c_int), P]),
         "qn_profile_read": (ctypes.c_int, [P, ctypes.POINTER(QnProfile)]),
+        "qn_eig_solve": (ctypes.c_int, [P, P, ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(QnStats), ctypes.c_int, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -292,6 +295,22 @@ def qn_solve(ctx: QnContext, U, f, tol=1e-10, max_it=200, beta=None, step=1.0, s
         _check(rc, allowed=(QN_OK, QN_ENOTCONV, QN_EDIVERGED))
     out = {"iterations": res.iterations, "status": res.status, "rel": res.rel, "rc": rc}
     n_h = min(res.iterations + 1, history_len) if rc in (QN_OK, QN_ENOTCONV, QN_EDIVERGED) else 0
+    return out, [hist[i].as_dict() for i in range(n_h)] if hist is not None else []
+
+
+def qn_eig_solve(ctx: QnContext, U, tol=1e-10, max_it=4096, beta=None, step=1.0, sync_every=8,
+                 history_len=0, stream=None, graph=False):
+    """Nonlinear eigenproblem; U (device) holds the start and receives the normalised
+    eigenfunction. Returns (result dict with "lambda", list of per-iterate stats dicts)."""
+    opts = make_opts(tol, max_it, beta, step, sync_every, graph)
+    res = QnResult()
+    lam = ctypes.c_double()
+    hist = (QnStats * history_len)() if history_len > 0 else None
+    rc = load_library().qn_eig_solve(ctx.handle, _dptr(U, ctx.numel, "U"), ctypes.byref(opts), ctypes.byref(res),
+                                     ctypes.byref(lam), hist, history_len, _stream_ptr(stream))
+    _check(rc, allowed=(QN_OK, QN_ENOTCONV, QN_EDIVERGED))
+    out = {"iterations": res.iterations, "status": res.status, "rel": res.rel, "lambda": lam.value, "rc": rc}
+    n_h = min(res.iterations + 1, history_len)
     return out, [hist[i].as_dict() for i in range(n_h)] if hist is not None else []
 
 
