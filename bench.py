@@ -280,7 +280,7 @@ def run_reference(a):
         return
     if a.workload == "ex2":
         print(json.dumps({"impl": "reference", "unavailable": "the oracle's eigen solve needs ~10^3 iterations of "
-                          "minutes each at 200^3; the ours line carries a timed one-iteration oracle sample "
+                          "seconds each at 200^3 (about an hour); the ours line carries a timed one-iteration oracle sample "
                           "(cpu_baseline) instead"}), flush=True)
         return
     _, f_small = manufactured_problem(127, 3, seed=a.seed)
