@@ -383,16 +383,17 @@ def main_ex2(a):
     its = [r["iterations"] for r in results]
     P = ((n + 63) // 64) * 64
     nres = max(prof["residual_launches"], 1)
-    # the two residual passes: U 8 + r0 8 B/pt, then U 8 + r0 8 B/pt + the hi/lo planes 4 B per padded point
-    res_bytes = 0.5 * (16.0 * N) + 0.5 * (16.0 * N + 4.0 * P ** 3)
+    # the two residual passes (average per launch): pass 1 reads U~ and writes lin (16 B/pt);
+    # pass 2 reads U~ and lin, writes U (24 B/pt) and the hi/lo planes (4 B per padded point)
+    res_bytes = 0.5 * (16.0 * N) + 0.5 * (24.0 * N + 4.0 * P ** 3)
     res_ms = prof["residual_ms"] / nres
     mp_ms = prof["modeprod_ms"] / max(prof["modeprod_launches"], 1)
     st_ms = prof["mp_store_ms"] / max(prof["mp_store_launches"], 1)
     split = bool(prof["split_products"])
     st_bytes = 8.0 * P ** 3
-    tot = prof["residual_ms"] + prof["modeprod_ms"] + prof["finalize_ms"] + prof["normalize_ms"]
+    tot = prof["residual_ms"] + prof["modeprod_ms"] + prof["finalize_ms"]
     kernels = {
-        "residual_passes": {"kernel": "k_eig_rayleigh + k_eig_residual2", "launches": prof["residual_launches"],
+        "residual_passes": {"kernel": "k_eig_pass1 + k_eig_pass2", "launches": prof["residual_launches"],
                             "avg_launch_ms": round(res_ms, 4), "bytes_per_launch": res_bytes,
                             "achieved_gbs": round(res_bytes / (res_ms * 1e-3) / 1e9, 1),
                             "frac_hbm": round(res_bytes / (res_ms * 1e-3) / 1e9 / hbm, 4),
@@ -403,9 +404,6 @@ def main_ex2(a):
         "finalize": {"launches": prof["finalize_launches"],
                      "avg_launch_ms": round(prof["finalize_ms"] / max(prof["finalize_launches"], 1), 4),
                      "share": round(prof["finalize_ms"] / tot, 4) if tot else None},
-        "normalize": {"kernel": "k_eig_sumsq + k_eig_scale", "launches": prof["normalize_launches"],
-                      "avg_launch_ms": round(prof["normalize_ms"] / max(prof["normalize_launches"], 1), 4),
-                      "share": round(prof["normalize_ms"] / tot, 4) if tot else None},
     }
     if prof["modeprod_ms"] >= prof["residual_ms"]:
         gbs = st_bytes / (st_ms * 1e-3) / 1e9
@@ -415,7 +413,7 @@ def main_ex2(a):
                     "avg_launch_ms": round(st_ms, 4), "launches": prof["mp_store_launches"]}
     else:
         gbs = res_bytes / (res_ms * 1e-3) / 1e9
-        roofline = {"kernel": "k_eig_rayleigh + k_eig_residual2", "bound": "hbm", "achieved": round(gbs, 1),
+        roofline = {"kernel": "k_eig_pass1 + k_eig_pass2", "bound": "hbm", "achieved": round(gbs, 1),
                     "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4), "traffic": None,
                     "peak_source": f"HBM copy bandwidth ({peak_src})", "bytes_per_launch_algorithmic": res_bytes,
                     "avg_launch_ms": round(res_ms, 4), "launches": prof["residual_launches"]}

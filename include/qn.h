@@ -343,8 +343,8 @@ int qn_solve_warm(qn_ctx *ctx, qn_net *net, double *U, const double *f, int n, d
  *   U = U~ / ||U~||,
  * stopping when ||F|| / |lambda_n| <= opts->tol. <V, W> = h^dim sum w V W, w the product
  * of the 1-D trapezoid weights (1/2 at Neumann face nodes, else 1).
- * U: device, n^dim doubles: in = start (normalised by the call), out = last iterate, with
- * ||U|| = 1. opts: host, NULL = tol 1e-10, max_it 4096, paper beta, step 1, sync_every 8.
+ * U: device, n^dim doubles: in = start (any nonzero scale; each iteration normalises the
+ * iterate it evaluates), out = the last evaluated iterate, with ||U|| = 1. opts: host, NULL = tol 1e-10, max_it 4096, paper beta, step 1, sync_every 8.
  * lambda: host, may be NULL: lambda_n of the returned iterate. history (host, may be NULL):
  * per iterate res_norm = ||F||, f_norm = |lambda_n| ||U||, fu_min / fu_max = extremes of
  * lam + 3 b U^2 + V, beta = beta_n, rel, lambda = lambda_n. With opts->graph every group of
@@ -376,8 +376,6 @@ typedef struct qn_profile {
     int split_products;       /* 1: the last shifted inverse used the reflection-split mode
                                  products (3-D split solve, n+ padding a multiple of 128):
                                  half the tensor work of the dense products */
-    int normalize_launches;   /* qn_eig_solve: the norm and scale kernels of the normalisation */
-    double normalize_ms;
 } qn_profile;
 
 /* on != 0: from now on record a pair of CUDA events around every kernel

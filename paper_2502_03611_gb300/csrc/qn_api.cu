@@ -111,7 +111,7 @@ struct qn_ctx {
 };
 
 enum ProfKind { PK_RESIDUAL = 0, PK_FINALIZE = 1, PK_MP_STORE = 2, PK_MP_DIVIDE = 3, PK_MP_LAST = 4,
-                PK_SPLIT = 5, PK_RESIDUAL_TILED = 6, PK_NORMALIZE = 7, PK_COUNT = 8 };
+                PK_SPLIT = 5, PK_RESIDUAL_TILED = 6, PK_COUNT = 7 };
 
 // Begin/end a timed launch. With profiling off these only count launches.
 static long prof_begin(qn_ctx *c, int kind, cudaStream_t s) {
@@ -1027,23 +1027,22 @@ extern "C" int qn_profile_read(qn_ctx *c, qn_profile *out) {
     out->mp_divide_ms = ms[PK_MP_DIVIDE];
     out->mp_last_launches = cnt[PK_MP_LAST];
     out->mp_last_ms = ms[PK_MP_LAST];
-    out->normalize_launches = cnt[PK_NORMALIZE];
-    out->normalize_ms = ms[PK_NORMALIZE];
     return QN_OK;
 }
 
 // ---- nonlinear eigenproblem (Sec. 4.4) ----------------------------------------------------------
-// One iteration (qn_eig.cu): Rayleigh pass, lambda_n / beta_n, F = r0 - lambda_n U into
-// the inverse's input, stop test, the shifted inverse with the update, normalisation.
+// One iteration (qn_eig.cu): pass 1 (A U~ + (lam + V) U~ and the Rayleigh sums), lambda_n and
+// the normalisation factor, pass 2 (U = s U~, F into the inverse's input, beta's extremes), stop
+// test and beta_n, the shifted inverse with the update.
 static int enqueue_eig_iteration(qn_ctx *c, double *U, double step, cudaStream_t s) {
     const double hd = pow(c->h, c->dim);
     const int grid = c->nparts;
     const bool fp64 = (c->prob.precision == QN_PREC_FP64);
-    double *r0 = fp64 ? c->w64[1] : c->eig_r0;   // w64[1] is free until the first mode product
+    double *lin = fp64 ? c->w64[1] : c->eig_r0;   // w64[1] is free until the first mode product
     const bool mirror = !fp64 && c->split;
     long pr = prof_begin(c, PK_RESIDUAL, s);
-    int rc = launch_eig_rayleigh(U, r0, c->n, c->dim, c->prob.bc, c->inv_h2, c->prob.lam, c->prob.b, c->pot64,
-                                 c->partials, grid, c->st, s);
+    int rc = launch_eig_pass1(U, lin, c->n, c->dim, c->prob.bc, c->inv_h2, c->prob.lam, c->prob.b, c->pot64,
+                              c->partials, grid, c->st, s);
     prof_end(c, pr, s);
     if (rc) return rc;
     pr = prof_begin(c, PK_FINALIZE, s);
@@ -1051,22 +1050,16 @@ static int enqueue_eig_iteration(qn_ctx *c, double *U, double step, cudaStream_t
     prof_end(c, pr, s);
     if (rc) return rc;
     pr = prof_begin(c, PK_RESIDUAL, s);
-    rc = launch_eig_residual2(U, r0, c->n, c->P, c->dim, c->prob.bc, hd, fp64 ? c->w64[0] : nullptr,
-                              fp64 ? nullptr : c->bhi[0], fp64 ? nullptr : c->blo[0], mirror, c->partials, grid,
-                              c->st, s);
+    rc = launch_eig_pass2(U, lin, c->n, c->P, c->dim, c->prob.bc, hd, c->prob.lam, c->prob.b, c->pot64,
+                          fp64 ? c->w64[0] : nullptr, fp64 ? nullptr : c->bhi[0], fp64 ? nullptr : c->blo[0],
+                          mirror, c->partials, grid, c->st, s);
     prof_end(c, pr, s);
     if (rc) return rc;
     pr = prof_begin(c, PK_FINALIZE, s);
     rc = launch_finalize(c->partials, grid, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 1, 1, 2, s);
     prof_end(c, pr, s);
     if (rc) return rc;
-    rc = enqueue_inverse(c, nullptr, U, true, step, s, mirror);
-    if (rc) return rc;
-    pr = prof_begin(c, PK_NORMALIZE, s);
-    rc = launch_eig_normalize(U, c->n, c->dim, c->prob.bc, hd, c->partials, grid, c->st, s);
-    prof_end(c, pr, s);
-    c->launches += 1;   // two kernels
-    return rc;
+    return enqueue_inverse(c, nullptr, U, true, step, s, mirror);
 }
 
 extern "C" int qn_eig_solve(qn_ctx *c, double *U, const qn_opts *opts, qn_result *res, double *lambda,
@@ -1107,12 +1100,6 @@ extern "C" int qn_eig_solve(qn_ctx *c, double *U, const qn_opts *opts, qn_result
     if (rc) return rc;
     const size_t first_rec = c->prof_used;
     const long long launches0 = c->launches;
-    // the start is normalised first (<U_0, U_0> = 1)
-    c->cur_iter = -1;
-    const long pr = prof_begin(c, PK_NORMALIZE, s);
-    rc = launch_eig_normalize(U, c->n, c->dim, c->prob.bc, pow(c->h, c->dim), c->partials, c->nparts, c->st, s);
-    prof_end(c, pr, s);
-    if (rc) return rc;
     DevState h;
     memset(&h, 0, sizeof(h));
     int enqueued = 0;
@@ -1141,12 +1128,11 @@ extern "C" int qn_eig_solve(qn_ctx *c, double *U, const qn_opts *opts, qn_result
     const int status = h.status;
     for (size_t i = first_rec; i < c->prof_used; ++i) {
         qn_ctx::ProfRec &r = (*c->prof)[i];
-        const bool after_update = (r.kind >= PK_MP_STORE && r.kind <= PK_MP_LAST) || r.kind == PK_NORMALIZE;
-        if ((after_update && r.iter >= its) || (!after_update && r.iter > its)) r.valid = 0;
+        const bool mp = r.kind >= PK_MP_STORE && r.kind <= PK_MP_LAST;
+        if ((mp && r.iter >= its) || (!mp && r.iter > its)) r.valid = 0;
     }
-    // per evaluated iterate 2 residual passes + 2 finalisers; per update 2 dim products and
-    // 2 normalisation kernels; 2 for normalising the start
-    c->launches = launches0 + 4LL * (its + 1) + (2LL * c->dim + 2) * its + 2;
+    // per evaluated iterate 2 residual passes + 2 finalisers; per update 2 dim products
+    c->launches = launches0 + 4LL * (its + 1) + 2LL * c->dim * its;
     qn_stats last;
     QN_CUDA(cudaMemcpy(&last, c->hist + its, sizeof(qn_stats), cudaMemcpyDeviceToHost));
     if (history && history_len > 0) {

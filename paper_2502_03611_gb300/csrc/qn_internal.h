@@ -36,8 +36,7 @@ struct DevState {
     double npts;     // number of unknowns (for RMS(f))
     unsigned long long umax_scan;   // max|U| bit pattern from a scan pass (k_prep_split, k_umax)
     double eig_lambda;   // eigen solves: Rayleigh quotient lambda_n of the current iterate
-    double eig_fu_min;   //   and the extremes of lam + 3 b U^2 + V
-    double eig_fu_max;
+    double eig_scale;    //   and the normalisation factor 1/||U~|| applied to it
 };
 
 // Residual kernel outputs.
@@ -122,23 +121,22 @@ int launch_residual_mirror(const ResidualArgs &a, int max_grid, int zchunk, int 
 int launch_umax(const double *U, long long N, DevState *st, int grid, cudaStream_t s);
 // mode 0: the partial records hold min / max U^2. 1 (a potential is present): min / max of
 // 3 b U^2 + V, and the fixed-point exponent comes from DevState::umax_scan. 2 (eigen solve):
-// only sum F^2 is read; beta_n, the shift and the extremes were set by k_eig_finalize1.
+// min / max of lam + 3 b U^2 + V; beta_n = mid-range - lambda_n is the whole shift.
 int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *hist,
                     int hist_cap, double b, double lam, int update_state, int use_saved_fnorm,
                     int mode, cudaStream_t s);
 
 // ---- nonlinear eigenproblem (qn_eig.cu) ------------------------------------------------
 // hd = h^dim (the lumped mass without the trapezoid weights); partials: 4 doubles per block.
-int launch_eig_rayleigh(const double *U, double *r0, int n, int dim, int bc, double inv_h2, double lam, double b,
-                        const double *pot, double *partials, int grid, const DevState *st, cudaStream_t s);
+// U arrives unnormalised; pass 2 writes it back normalised (DevState::eig_scale).
+int launch_eig_pass1(const double *U, double *lin, int n, int dim, int bc, double inv_h2, double lam, double b,
+                     const double *pot, double *partials, int grid, const DevState *st, cudaStream_t s);
 int launch_eig_finalize1(const double *partials, int nparts, double hd, DevState *st, cudaStream_t s);
 // exactly one of R64 (FP64 output) or Rhi/Rlo (split planes; mirror: reflection-split order)
-int launch_eig_residual2(const double *U, const double *r0, int n, int P, int dim, int bc, double hd, double *R64,
-                         __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, bool mirror, double *partials, int grid,
-                         const DevState *st, cudaStream_t s);
-// U /= ||U|| (two launches: per-block sums, then the scale)
-int launch_eig_normalize(double *U, int n, int dim, int bc, double hd, double *partials, int grid,
-                         const DevState *st, cudaStream_t s);
+int launch_eig_pass2(double *U, const double *lin, int n, int P, int dim, int bc, double hd, double lam, double b,
+                     const double *pot, double *R64, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, bool mirror,
+                     double *partials, int grid, const DevState *st, cudaStream_t s);
+
 int launch_split_pad(const double *r, int n, int P, int dim, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
                      int grid, cudaStream_t s);
 int launch_modeprod_f64(const double *A, const double *B, double *out, const GemmShape &g,

@@ -426,10 +426,11 @@ __global__ void __launch_bounds__(256) k_finalize(const double *partials, int np
         st->r2_exp = k < -120 ? -120 : (k > 120 ? 120 : k);
     }
     // extremes of diag(N_h)_U: 3 b U^2 from those of U^2, or taken directly with a potential
-    const double fa = pot ? acc.mn : 3.0 * b * acc.mn, fb = pot ? acc.mx : 3.0 * b * acc.mx;
-    const double fu_min = eig ? st->eig_fu_min : fmin(fa, fb), fu_max = eig ? st->eig_fu_max : fmax(fa, fb);
-    const double beta = eig ? st->beta
-                            : (st->beta_mode == QN_BETA_FIXED) ? st->beta_value : 0.5 * (fu_min + fu_max);
+    const double fa = (pot || eig) ? acc.mn : 3.0 * b * acc.mn, fb = (pot || eig) ? acc.mx : 3.0 * b * acc.mx;
+    const double fu_min = fmin(fa, fb), fu_max = fmax(fa, fb);
+    // eigen solves: (N_h)_U = diag(lam + 3 b U^2 + V) - lambda_n (extremes from pass 2)
+    const double beta = (st->beta_mode == QN_BETA_FIXED) ? st->beta_value
+                                                         : 0.5 * (fu_min + fu_max) - (eig ? st->eig_lambda : 0.0);
     double rel;
     if (fn > 0.0)
         rel = res / fn;
@@ -457,10 +458,8 @@ __global__ void __launch_bounds__(256) k_finalize(const double *partials, int np
     } else if (!eig) {
         st->fx_e = (acc.mx < INFINITY) ? fx_exponent((unsigned long long)__double_as_longlong(sqrt(acc.mx)), st) : 0;
     }
-    if (!eig) {
-        st->beta = beta;
-        st->shift = lam + beta;
-    }
+    st->beta = beta;
+    st->shift = eig ? beta : lam + beta;   // eigen solves: lam is part of f, not of A_h
     if (rel <= st->tol) {
         st->status = QN_OK;
         st->done = 1;

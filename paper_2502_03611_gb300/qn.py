@@ -69,8 +69,7 @@ class QnProfile(ctypes.Structure):
                 ("mp_divide_launches", ctypes.c_int), ("mp_divide_ms", ctypes.c_double),
                 ("mp_last_launches", ctypes.c_int), ("mp_last_ms", ctypes.c_double),
                 ("residual_tiled_launches", ctypes.c_int), ("residual_tiled_ms", ctypes.c_double),
-                ("split_products", ctypes.c_int),
-                ("normalize_launches", ctypes.c_int), ("normalize_ms", ctypes.c_double)]
+                ("split_products", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -72,9 +72,10 @@ def test_eig_example2_matches_oracle(qn, n, prec):
     _check(res, Ug, lam_o, Uo, len(ho) - 1, prec)
     m = ob.mass_weights(n, 3, h, "dirichlet")
     assert float(np.sum(m * Ug * Ug)) == pytest.approx(1.0, rel=1e-12)
-    # the first iterate (same start) matches the oracle's lambda_0 and beta_0
+    # the first iterate (same start) matches the oracle's lambda_0 and beta_0 (beta from the
+    # FP32 extremes of lam + 3 b U^2 + V: it only chooses the shift)
     assert hist[0]["lambda"] == pytest.approx(ho[0]["lambda"], rel=1e-12)
-    assert hist[0]["beta"] == pytest.approx(ho[0]["beta"], rel=1e-11)
+    assert hist[0]["beta"] == pytest.approx(ho[0]["beta"], rel=1e-6)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
