@@ -86,6 +86,11 @@ typedef struct qn_problem {
     const double *potential_host;   /* NULL (V = 0) or host array of dim*n doubles: the
                          1-D tables v_x[n], v_y[n](, v_z[n]) of V = v_x + v_y (+ v_z) at the
                          nodes, x first. Copied by qn_ctx_create; the caller keeps it. */
+    int sem_k;        /* 0: finite differences. 1..16: Q^k spectral elements (Sec. 3.1) on E
+                         equal elements, n = E k - 1 (Dirichlet) or E k + 1 (Neumann) nodes per
+                         axis at the Gauss-Lobatto points (qn_setup_1d_sem gives them); the
+                         residual applies H = M^{-1} S along every axis (FP64), the inverse uses
+                         its numerical eigenpairs. f and the potential are nodal values. */
 } qn_problem;
 
 typedef struct qn_stats {
@@ -143,6 +148,19 @@ const char *qn_last_error(void);
  * S, S_inv: caller-owned host buffers of n*n doubles, row-major (S[j*n+k]).
  * lam: caller-owned host buffer of n doubles. Any output may be NULL. */
 int qn_setup_1d_eig(int n, double h, int bc, double *S, double *S_inv, double *lam);
+
+/* 1-D Q^k spectral element matrices (Sec. 3.1 eqs. S_x, M_x, final-system-3d; Sec. 4.2).
+ * Host-only, FP64. E = (n+1)/k (Dirichlet) or (n-1)/k (Neumann) equal elements of
+ * [0, length]; Lagrange bases at the k+1 Gauss-Lobatto points, Gauss-Lobatto quadrature
+ * (diagonal mass M), assembled stiffness S, Dirichlet keeping the interior nodes.
+ *   H = M^{-1} S (n x n), and H = S diag(lam) S^{-1} from the symmetric
+ *   M^{-1/2} S M^{-1/2} = Q diag(lam) Q^T: S = M^{-1/2} Q, S_inv = Q^T M^{1/2};
+ *   nodes: the node coordinates on [0, length].
+ * 1 <= k <= 16, length > 0, n + 1 (Dirichlet) or n - 1 (Neumann) a positive multiple of k
+ * (QN_EINVAL otherwise). Outputs are caller-owned host buffers (n*n or n doubles,
+ * row-major), any of which may be NULL. */
+int qn_setup_1d_sem(int n, int k, double length, int bc, double *H, double *S, double *S_inv,
+                    double *lam, double *nodes);
 
 /* Create a context for one problem shape on the current CUDA device: uploads
  * S, S^{-1} and the eigenvalues (and their BF16 hi/lo splits for

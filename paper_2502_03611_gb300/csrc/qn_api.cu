@@ -17,6 +17,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -108,6 +109,11 @@ struct qn_ctx {
     float2 *pot2;
     double *eig_r0;       // eigen solves, BF16X3: A_h U + f(U) between the two residual passes
     int g_kind;           // graph contents: 0 quasi-Newton iterations, 1 eigen iterations
+    double lam_min;       // smallest eigenvalue of the 1-D matrix H
+    // spectral elements (prob.sem_k > 0): banded H on the device (k_residual_sem)
+    int *hc0, *hlen;
+    double *hval;
+    int hbw;
 };
 
 enum ProfKind { PK_RESIDUAL = 0, PK_FINALIZE = 1, PK_MP_STORE = 2, PK_MP_DIVIDE = 3, PK_MP_LAST = 4,
@@ -225,6 +231,9 @@ static void ctx_free(qn_ctx *c) {
     cudaFree(c->pot64);
     cudaFree(c->pot2);
     cudaFree(c->eig_r0);
+    cudaFree(c->hc0);
+    cudaFree(c->hlen);
+    cudaFree(c->hval);
     for (int b = 0; b < 2; ++b) {
         cudaFree(c->w64[b]);
         cudaFree(c->bhi[b]);
@@ -278,6 +287,10 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
     const int nmin = (p->bc == QN_BC_NEUMANN) ? 2 : 1;
     if (p->n < nmin || p->n > 1024) {
         set_error("qn_ctx_create: n must be in [%d, 1024] (got %d)", nmin, p->n);
+        return QN_EINVAL;
+    }
+    if (p->sem_k < 0 || p->sem_k > 16) {
+        set_error("qn_ctx_create: sem_k must be 0 (finite differences) or 1..16 (got %d)", p->sem_k);
         return QN_EINVAL;
     }
     if (!(p->length >= 0.0) || !isfinite(p->length)) {
@@ -334,20 +347,61 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
         c->N *= c->n;
         c->NP *= c->P;
     }
-    {
-        const double L = (p->length > 0.0) ? p->length : 1.0;
-        c->h = (p->bc == QN_BC_NEUMANN) ? L / (c->n - 1) : L / (c->n + 1);
+    const double Ldom = (p->length > 0.0) ? p->length : 1.0;
+    if (p->sem_k > 0) {   // element width
+        c->h = Ldom * p->sem_k / ((p->bc == QN_BC_NEUMANN) ? c->n - 1 : c->n + 1);
+    } else {
+        c->h = (p->bc == QN_BC_NEUMANN) ? Ldom / (c->n - 1) : Ldom / (c->n + 1);
     }
     c->prob.potential_host = nullptr;   // not retained
     c->inv_h2 = 1.0 / (c->h * c->h);
     const int n = c->n, P = c->P;
 
     std::vector<double> S((size_t)n * n), Si((size_t)n * n), lam(n);
-    int rc = qn_setup_1d_eig(n, c->h, p->bc, S.data(), Si.data(), lam.data());
-    if (rc != QN_OK) {
-        ctx_free(c);
-        return rc;
+    int rc;
+    if (p->sem_k > 0) {
+        std::vector<double> Hm, nodes;
+        rc = sem_setup(n, p->sem_k, Ldom, p->bc, Hm, S, Si, lam, nodes);
+        if (rc != QN_OK) {
+            ctx_free(c);
+            return rc;
+        }
+        // band of H = M^{-1} S: first and last nonzero column of every row (<= 2k+1 wide)
+        const int bw = 2 * p->sem_k + 1;
+        std::vector<int> c0(n), len(n);
+        std::vector<double> hv((size_t)n * bw, 0.0);
+        for (int i = 0; i < n; ++i) {
+            int lo = n, hi = -1;
+            for (int j = 0; j < n; ++j)
+                if (Hm[(size_t)i * n + j] != 0.0) {
+                    lo = std::min(lo, j);
+                    hi = std::max(hi, j);
+                }
+            if (hi < lo) lo = hi = i;
+            if (hi - lo + 1 > bw) {
+                set_error("qn_ctx_create: spectral element matrix wider than its band");
+                ctx_free(c);
+                return QN_ECUDA;
+            }
+            c0[i] = lo;
+            len[i] = hi - lo + 1;
+            for (int j = lo; j <= hi; ++j) hv[(size_t)i * bw + (j - lo)] = Hm[(size_t)i * n + j];
+        }
+        c->hbw = bw;
+        CK(cudaMalloc(&c->hc0, sizeof(int) * n));
+        CK(cudaMalloc(&c->hlen, sizeof(int) * n));
+        CK(cudaMalloc(&c->hval, sizeof(double) * (size_t)n * bw));
+        CK(cudaMemcpy(c->hc0, c0.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->hlen, len.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->hval, hv.data(), sizeof(double) * (size_t)n * bw, cudaMemcpyHostToDevice));
+    } else {
+        rc = qn_setup_1d_eig(n, c->h, p->bc, S.data(), Si.data(), lam.data());
+        if (rc != QN_OK) {
+            ctx_free(c);
+            return rc;
+        }
     }
+    c->lam_min = lam[0];
     CK(cudaMalloc(&c->S64, sizeof(double) * n * n));
     CK(cudaMalloc(&c->Si64, sizeof(double) * n * n));
     CK(cudaMalloc(&c->lam64, sizeof(double) * n));
@@ -424,7 +478,7 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
         // the float-pair residual needs lam, b and 1/h^2 well inside the FP32 range
         const bool pair_ok = fabs(p->lam) < 0x1p40 && fabs(p->b) < 0x1p20 && c->inv_h2 < 0x1p24 &&
                              vmax < 0x1p40;
-        if (c->dim == 3 && pair_ok) {
+        if (c->dim == 3 && pair_ok && p->sem_k == 0) {   // (the FP64-free residual is the FD stencil's)
             CK(cudaMalloc(&c->fdf, sizeof(float2) * (size_t)c->NP));
         } else {
             c->res_tiled = 0;
@@ -569,6 +623,10 @@ static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double 
     a.pot = c->pot64;
     a.pot2 = c->pot2;
     a.umax_scan = &c->st->umax_scan;
+    a.hc0 = c->hc0;
+    a.hlen = c->hlen;
+    a.hval = c->hval;
+    a.hbw = c->hbw;
     // 3-D split solve: the residual without FP64 arithmetic (k_residual_tiled)
     // in every iteration. It needs the FP32-pair copy of f and a fixed-point
     // exponent from max|U|: iteration 0 prepares both in one pass over f and
@@ -772,9 +830,7 @@ extern "C" int qn_fast_diag_solve(qn_ctx *c, const double *r, double *V, double 
         return QN_EINVAL;
     }
     // smallest eigenvalue of sum_a H_a is dim * lambda_1 (0 for Neumann data: constants)
-    const double l1 = (c->prob.bc == QN_BC_NEUMANN)
-                          ? 0.0
-                          : 4.0 / (c->h * c->h) * pow(sin(0.5 * 3.14159265358979323846 / (c->n + 1)), 2);
+    const double l1 = (c->prob.bc == QN_BC_NEUMANN) ? 0.0 : c->lam_min;
     if (!(shift > -c->dim * l1)) {
         set_error("qn_fast_diag_solve: shift %.6g makes the operator singular or indefinite", shift);
         return QN_EINVAL;
@@ -825,7 +881,7 @@ extern "C" int qn_step(qn_ctx *c, double *U, const double *f, double beta, qn_st
 bool qn::ctx_split_precision(const qn_ctx *c) { return c != nullptr && c->prob.precision == QN_PREC_BF16X3; }
 
 bool qn::ctx_unit_dirichlet(const qn_ctx *c) {
-    return c != nullptr && c->prob.bc == QN_BC_DIRICHLET && c->pot64 == nullptr &&
+    return c != nullptr && c->prob.bc == QN_BC_DIRICHLET && c->pot64 == nullptr && c->prob.sem_k == 0 &&
            fabs(c->h * (c->n + 1) - 1.0) < 1e-12;
 }
 
@@ -1069,6 +1125,10 @@ extern "C" int qn_eig_solve(qn_ctx *c, double *U, const qn_opts *opts, qn_result
     if (bad_ptr(U)) {
         set_error("qn_eig_solve: null U");
         return QN_EINVAL;
+    }
+    if (c->prob.sem_k > 0) {
+        set_error("qn_eig_solve: finite-difference contexts only");
+        return QN_EUNSUPPORTED;
     }
     qn_opts o;
     if (opts) {

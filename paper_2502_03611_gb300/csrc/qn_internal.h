@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/qn.h"
 
 namespace qn {
@@ -68,6 +70,12 @@ struct ResidualArgs {
     const float2 *pot2;        // the same tables as FP32 pairs (hi, lo), lam added to the last
                                // axis' table: [dim][n] (k_residual_tiled / k_residual_mirror)
     unsigned long long *umax_scan;   // DevState::umax_scan (atomicMax of |U| bit patterns)
+    // spectral elements (k_residual_sem): banded H = M^{-1} S, row i = hlen[i] values from
+    // column hc0[i], stored with row stride hbw; hval == nullptr: finite differences
+    const int *hc0;
+    const int *hlen;
+    const double *hval;
+    int hbw;
 };
 
 // Epilogue selector shared by both mode-product kernels.
@@ -106,6 +114,8 @@ struct GemmShape {
 
 // ---- launchers (implemented in the .cu files) ---------------------------------
 int launch_residual(const ResidualArgs &a, int grid, cudaStream_t s);
+// spectral elements (qn_sem.cu): the per-node residual with the banded H
+int launch_residual_sem(const ResidualArgs &a, int grid, cudaStream_t s);
 // 3-D split solve, iterations >= 2: no FP64 arithmetic per point (k_residual_tiled).
 // Uses at most max_grid blocks; the number of partial records written goes to *grid_used.
 int launch_residual_tiled(const ResidualArgs &a, int max_grid, int zchunk, int *grid_used, cudaStream_t s);
@@ -201,6 +211,9 @@ bool tc_supported(int device);
 int solve_internal(::qn_ctx *c, double *U, const double *f, const qn_opts *opts, qn_result *res,
                    qn_stats *history, int history_len, void *stream, const double *u0_sq, int *used_warm);
 bool ctx_split_precision(const ::qn_ctx *c);
+// host setup of the Q^k spectral element matrices (qn_sem.cu); see qn_setup_1d_sem
+int sem_setup(int n, int k, double length, int bc, std::vector<double> &H, std::vector<double> &S,
+              std::vector<double> &Si, std::vector<double> &lam, std::vector<double> &nodes);
 // Dirichlet data on the unit cube and no potential (the learned warm start's setting)
 bool ctx_unit_dirichlet(const ::qn_ctx *c);
 

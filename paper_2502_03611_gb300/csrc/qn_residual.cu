@@ -1298,6 +1298,7 @@ static void launch_res2(const ResidualArgs &a, int grid, cudaStream_t s) {
 }
 
 int launch_residual(const ResidualArgs &a, int grid, cudaStream_t s) {
+    if (a.hval != nullptr) return launch_residual_sem(a, grid, s);
     const bool split = a.Rhi != nullptr;
     if (a.dim == 3) {
         if (split)

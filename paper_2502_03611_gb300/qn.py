@@ -38,7 +38,8 @@ PRECISIONS = {"fp64": QN_PREC_FP64, "bf16x3": QN_PREC_BF16X3}
 class QnProblem(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("bc", ctypes.c_int),
                 ("precision", ctypes.c_int), ("lam", ctypes.c_double), ("b", ctypes.c_double),
-                ("length", ctypes.c_double), ("potential_host", ctypes.POINTER(ctypes.c_double))]
+                ("length", ctypes.c_double), ("potential_host", ctypes.POINTER(ctypes.c_double)),
+                ("sem_k", ctypes.c_int)]
 
 
 class QnStats(ctypes.Structure):
@@ -112,6 +113,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "qn_version": (ctypes.c_int, []),
         "qn_last_error": (ctypes.c_char_p, []),
         "qn_setup_1d_eig": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, D, D, D]),
+        "qn_setup_1d_sem": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, D, D, D, D, D]),
         "qn_ctx_create": (ctypes.c_int, [ctypes.POINTER(QnProblem), ctypes.POINTER(P)]),
         "qn_ctx_destroy": (ctypes.c_int, [P]),
         "qn_residual": (ctypes.c_int, [P, P, P, P, ctypes.POINTER(QnStats), P]),
@@ -205,7 +207,8 @@ class QnContext:
     """Owns a qn_ctx (qn_ctx_create / qn_ctx_destroy)."""
 
     def __init__(self, dim: int, n: int, precision: str | int = "fp64", lam: float = 0.0,
-                 b: float = 1.0, bc: str | int = QN_BC_DIRICHLET, length: float = 0.0, potential=None):
+                 b: float = 1.0, bc: str | int = QN_BC_DIRICHLET, length: float = 0.0, potential=None,
+                 sem_k: int = 0):
         """potential: None, or the 1-D tables of V = v_x + v_y (+ v_z) at the nodes, an array
         of shape (n,) (the same table on every axis) or (dim, n) (x first)."""
         lib = load_library()
@@ -218,7 +221,7 @@ class QnContext:
             if pot.shape != (dim, n):
                 raise ValueError(f"potential tables must have shape ({n},) or ({dim}, {n})")
         ptr = pot.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if pot is not None else None
-        self.problem = QnProblem(dim, n, bcv, prec, lam, b, length, ptr)
+        self.problem = QnProblem(dim, n, bcv, prec, lam, b, length, ptr, sem_k)
         self.dim, self.n, self.precision, self.bc = dim, n, prec, bcv
         self.numel = n ** dim
         h = ctypes.c_void_p()
@@ -248,8 +251,22 @@ class QnContext:
 
 
 def qn_ctx_create(dim, n, precision="fp64", lam=0.0, b=1.0, bc=QN_BC_DIRICHLET, length=0.0,
-                  potential=None) -> QnContext:
-    return QnContext(dim, n, precision, lam, b, bc, length, potential)
+                  potential=None, sem_k=0) -> QnContext:
+    return QnContext(dim, n, precision, lam, b, bc, length, potential, sem_k)
+
+
+def qn_setup_1d_sem(n: int, k: int, length: float = 1.0, bc: int = QN_BC_DIRICHLET):
+    """Host Q^k spectral element matrices; returns numpy (H, S, S_inv, lam, nodes)."""
+    lib = load_library()
+    H = np.empty((n, n))
+    S = np.empty((n, n))
+    Si = np.empty((n, n))
+    lam = np.empty(n)
+    x = np.empty(n)
+    D = ctypes.POINTER(ctypes.c_double)
+    _check(lib.qn_setup_1d_sem(n, k, length, bc, H.ctypes.data_as(D), S.ctypes.data_as(D), Si.ctypes.data_as(D),
+                               lam.ctypes.data_as(D), x.ctypes.data_as(D)))
+    return H, S, Si, lam, x
 
 
 def qn_ctx_destroy(ctx: QnContext):

@@ -113,3 +113,35 @@ def test_ctx_create_validates_before_cuda(lib):
     assert lib.qn_residual(None, None, None, None, None, None) == qn.QN_EINVAL
     assert lib.qn_solve(None, None, None, None, None, None, 0, None) == qn.QN_EINVAL
     assert lib.qn_ctx_destroy(None) == qn.QN_OK
+
+
+@pytest.mark.parametrize("n,k,bc", [(9, 1, 0), (15, 2, 0), (33, 4, 1), (59, 3, 0), (63, 8, 0), (41, 5, 1)])
+def test_setup_1d_sem_matches_oracle(lib, n, k, bc):
+    """The library's Q^k matrices (its own Gauss-Lobatto rule, assembly and symmetric
+    eigensolver) against the oracle's (numpy Legendre roots, eigh)."""
+    from oracle import qn_oracle_sem as so
+    from paper_2502_03611_gb300 import qn
+    L = 2.5
+    H, S, Si, lam, x = qn.qn_setup_1d_sem(n, k, L, bc)
+    bcs = "dirichlet" if bc == 0 else "neumann"
+    So, Sio, lamo, Ho = so.eig_1d(n, k, L, bcs)
+    _, _, xo = so.assemble_1d(n, k, L, bcs)
+    assert np.abs(x - xo).max() < 1e-14 * L
+    assert np.abs(H - Ho).max() <= 1e-11 * np.abs(Ho).max()
+    assert np.abs(lam - lamo).max() <= 1e-11 * np.abs(lamo).max()
+    assert np.abs(Si @ S - np.eye(n)).max() < 1e-11
+    assert np.abs(H @ S - S * lam[None, :]).max() < 1e-11 * np.abs(lam).max()
+
+
+def test_setup_1d_sem_large_and_rejects_bad_sizes(lib):
+    import time
+    from paper_2502_03611_gb300 import qn
+    t0 = time.time()
+    H, S, Si, lam, x = qn.qn_setup_1d_sem(511, 4, 1.0, 0)
+    assert time.time() - t0 < 60
+    assert np.all(np.diff(lam) >= 0) and lam[0] > 0
+    assert np.abs(H @ S - S * lam[None, :]).max() < 1e-10 * lam.max()
+    assert np.abs(Si @ S - np.eye(511)).max() < 1e-10
+    assert lib.qn_setup_1d_sem(10, 4, 1.0, 0, None, None, None, None, None) == qn.QN_EINVAL   # 11 % 4 != 0
+    assert lib.qn_setup_1d_sem(9, 0, 1.0, 0, None, None, None, None, None) == qn.QN_EINVAL
+    assert lib.qn_setup_1d_sem(9, 2, -1.0, 0, None, None, None, None, None) == qn.QN_EINVAL
