@@ -18,6 +18,9 @@ instead: -Lap u + 10 u + 10 u^3 + V u = f on (-1,1)^3 with zero normal
 derivative, V = sum of 100 sin^2(pi t/4) + t^2 over the axes, n = 200 nodes per
 axis by default (400, 800: the paper's other mesh sizes), started from the
 exact solution plus 0.1 times a random normalised polynomial.
+--workload sem times -Lap u + u^3 = f on (0,1)^3 discretised by Q^k spectral
+elements (Sec. 3.1; --sem-k, default 4) on n = 255 Gauss-Lobatto nodes per axis
+(64 elements), zero start, u* = sin(pi x) sin(pi y) sin(pi z) at the nodes.
 --workload ex2 times the nonlinear eigenproblem of the paper's Sec. 6.3
 Example 2 (qn_eig_solve): -Lap u + 1600 u^3 + V u = lambda u on (-8,8)^3,
 u = 0 on the boundary, n = 200 interior nodes per axis by default.
@@ -57,7 +60,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dirichlet", choices=["dirichlet", "ex1", "ex2"])
+    ap.add_argument("--workload", default="dirichlet", choices=["dirichlet", "ex1", "ex2", "sem"])
+    ap.add_argument("--sem-k", type=int, default=4, help="element degree of --workload sem")
     ap.add_argument("--n", type=int, default=None, help="nodes per axis (default 511, ex1: 200)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
@@ -70,7 +74,7 @@ def parse():
     if a.quick:
         a.no_fp64 = a.no_cpu = a.no_e2e = a.no_batched = True
     if a.n is None:
-        a.n = 511 if a.workload == "dirichlet" else 200
+        a.n = {"dirichlet": 511, "sem": 255}.get(a.workload, 200)
     return a
 
 
@@ -515,7 +519,18 @@ def main():
     seed = a.seed + rank
     peaks, peak_src = load_peaks()
     ex1 = a.workload == "ex1"
-    if ex1:
+    sem = a.workload == "sem"
+    if sem:
+        # nodes from the library's own setup (a user's workflow); f in closed form
+        xs = qn.qn_setup_1d_sem(n, a.sem_k, 1.0, qn.QN_BC_DIRICHLET)[4]
+        g = np.sin(math.pi * xs)
+        u_np = g[None, None, :] * g[None, :, None] * g[:, None, None]
+        f_np = 3.0 * math.pi ** 2 * u_np + u_np ** 3
+        U0_np = None
+        ctx_kw = dict(sem_k=a.sem_k)
+        max_it = 100
+        del u_np
+    elif ex1:
         # Sec. 6.3, Example 1: start = exact solution + 0.1 * normalised random polynomial
         u_np, f_np, v_np, _ = I.ex1_problem(n)
         U0_np = np.ascontiguousarray((u_np + I.ex1_perturbation(n, seed, 0.1)).reshape(-1))
@@ -752,11 +767,11 @@ def main():
         del ctx64, A, B
 
     batched = None
-    if not a.no_batched and a.precision == "bf16x3" and not ex1:
+    if not a.no_batched and a.precision == "bf16x3" and not ex1 and not sem:
         batched = run_batched(qn)
 
     cpu = None
-    if not a.no_cpu and rank == 0 and world == 1:
+    if not a.no_cpu and rank == 0 and world == 1 and not sem:
         if ex1:
             ms_cpu, det = cpu_oracle_baseline_ex1(n, a.seed)
             small = "33^3, same kind of start"
@@ -768,7 +783,25 @@ def main():
                           f"({det['per_iteration_s']:.2f} s) x {det['iterations_assumed']} iterations "
                           f"(oracle count at {small})")}
 
-    if rank == 0 and ex1:
+    if rank == 0 and sem:
+        line = {
+            "metric": "time to rel. residual 1e-10, 3-D Q^k spectral elements at n^3 nodes", "value": round(ms_max, 3),
+            "unit": "ms", "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_max, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3+f64" if a.precision == "bf16x3" else "f64",
+            "data": "synthetic (closed-form source of u* = sin(pi x) sin(pi y) sin(pi z) at the nodes)",
+            "config": {"workload": f"3-D -Lap u + u^3 = f on (0,1)^3, Q^{a.sem_k} spectral elements (Gauss-Lobatto, "
+                                   f"lumped mass), {n}^3 nodes, Dirichlet 0, tol 1e-10, zero start",
+                       "n": n, "sem_k": a.sem_k, "dim": 3, "precision": a.precision,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": f"inputs {'larger' if 8 * N > 129e6 else 'smaller'} than L2 ({8 * N / 1e9:.2f} GB)",
+                       "launch": "iterations >= 2 replayed from a CUDA graph (qn_opts.graph)"},
+            "iterations": iters[0] if len(set(iters)) == 1 else iters, "final_rel": max(rels), "converged": ok,
+            "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
+            "e2e": e2e, "plain_fp64": plain, "cpu_baseline": None, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    elif rank == 0 and ex1:
         paper = PAPER_EX1.get(n)
         line = {
             "metric": METRIC_EX1, "value": round(ms_max, 3), "unit": "ms", "n_gpus": world,

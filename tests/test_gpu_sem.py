@@ -85,7 +85,7 @@ def test_sem_fast_diag_matches_oracle(qn, dim, n, k, bc, prec):
     assert np.abs(host(V).reshape(want.shape) - want).max() <= tol * np.abs(want).max()
 
 
-@pytest.mark.parametrize("dim,n,k,bc,prec", [(2, 31, 2, "dirichlet", "fp64"), (2, 63, 4, "neumann", "bf16x3"),
+@pytest.mark.parametrize("dim,n,k,bc,prec", [(2, 31, 2, "dirichlet", "fp64"), (2, 65, 4, "neumann", "bf16x3"),
                                              (3, 15, 2, "dirichlet", "fp64"), (3, 23, 3, "dirichlet", "bf16x3"),
                                              (3, 33, 4, "neumann", "fp64"), (3, 33, 4, "neumann", "bf16x3")])
 def test_sem_solve_matches_oracle(qn, dim, n, k, bc, prec):
