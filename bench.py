@@ -78,6 +78,22 @@ def parse():
     return a
 
 
+def rank_seed(base_seed: int, rank: int) -> int:
+    """Replicas: every rank solves its own seed (the solve has no data-parallel split)."""
+    return base_seed + rank
+
+
+def max_over_ranks(value: float, world: int, device="cuda") -> float:
+    """The slowest rank's time (all-reduce MAX over the process group); value as is for one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -338,7 +354,7 @@ def main_ex2(a):
     from paper_2502_03611_gb300 import qn
     from paper_2502_03611_gb300 import inputs as I
     n = a.n
-    seed = a.seed + rank
+    seed = rank_seed(a.seed, rank)
     peaks, peak_src = load_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
     v, h, _ = I.ex2_problem(n)
@@ -380,10 +396,7 @@ def main_ex2(a):
     torch.cuda.synchronize()
     prof = qn.qn_profile_read(ctx)
     qn.qn_profile_enable(ctx, False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world)
     its = [r["iterations"] for r in results]
     P = ((n + 63) // 64) * 64
     nres = max(prof["residual_launches"], 1)
@@ -516,7 +529,7 @@ def main():
     from paper_2502_03611_gb300 import inputs as I
 
     n = a.n
-    seed = a.seed + rank
+    seed = rank_seed(a.seed, rank)
     peaks, peak_src = load_peaks()
     ex1 = a.workload == "ex1"
     sem = a.workload == "sem"
@@ -596,10 +609,7 @@ def main():
     prof = qn.qn_profile_read(ctx)
     qn.qn_profile_enable(ctx, False)
     ms_per_step = elapsed_ms / max(a.steps, 1)
-    t = torch.tensor([ms_per_step], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms_per_step, world)
     iters = [r["iterations"] for r in results]
     rels = [r["rel"] for r in results]
     ok = all(r["status"] == 0 for r in results)
