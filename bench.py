@@ -234,6 +234,39 @@ def cpu_oracle_baseline_ex1(n: int, seed: int, iters_timed: int = 1):
     return per_it * its * 1e3, {"per_iteration_s": per_it, "iterations_assumed": its, "cores": cores}
 
 
+def sem_oracle_sample(n: int, k: int, iters_timed: int = 1):
+    """The SEM oracle timed on the host cores: iters_timed quasi-Newton iterations of
+    -Lap u + u^3 = f with Q^k elements at n^3 nodes, times the oracle's iteration count on
+    the same problem at 31^3 nodes (k = 4: 8 elements per axis). Returns (ms per solve, details)."""
+    import numpy as np
+    from oracle import qn_oracle_sem as so
+    from oracle.qn_oracle import fast_diag_solve
+
+    def problem(m):
+        _, _, x = so.assemble_1d(m, k, 1.0, "dirichlet")
+        g = np.sin(math.pi * x)
+        u = g[None, None, :] * g[None, :, None] * g[:, None, None]
+        return 3.0 * math.pi ** 2 * u + u ** 3
+
+    small = 8 * k - 1
+    _, h_small, _ = so.qn_solve(problem(small), k, 1.0, "dirichlet")
+    its = len(h_small) - 1
+    f = problem(n)
+    S_e, S_inv, lam1d, H = so.eig_1d(n, k, 1.0, "dirichlet")
+    U = np.zeros_like(f)
+    times = []
+    for _ in range(iters_timed):
+        t0 = time.perf_counter()
+        r = so.residual(U, f, H)
+        d = 3.0 * U * U
+        U = U - fast_diag_solve(r, S_e, S_inv, lam1d, 0.5 * (d.max() + d.min()))
+        times.append(time.perf_counter() - t0)
+    per_it = statistics.mean(times)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return per_it * its * 1e3, {"per_iteration_s": per_it, "iterations_assumed": its, "cores": cores,
+                                "small": small}
+
+
 def run_batched(qn, seed=0, count=256, reps=3):
     """Batched coupled 2-D systems: 256 instances, n uniform on {63,127,255,511},
     alpha ~ U[0,1], D ~ U[0.1,10]; tiles from the project autotuner per size.
@@ -297,6 +330,22 @@ def run_reference(a):
     n = a.n
     if a.workload == "ex1":
         run_reference_ex1(a)
+        return
+    if a.workload == "sem":
+        value, det = sem_oracle_sample(n, a.sem_k, iters_timed=max(1, min(a.steps, 3)))
+        print(json.dumps({
+            "impl": "reference", "metric": "time to rel. residual 1e-10, 3-D Q^k spectral elements at n^3 nodes",
+            "value": round(value, 3), "unit": "ms", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": round(value, 3), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (closed-form source at the nodes)",
+            "config": {"workload": f"3-D -Lap u + u^3 = f, Q^{a.sem_k} spectral elements, {n}^3 nodes, Dirichlet 0",
+                       "n": n, "sem_k": a.sem_k, "dim": 3, "precision": "fp64 (CPU oracle)", "parallelism": "none"},
+            "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": det["cores"], "kind": "oracle",
+                             "sample": f"{max(1, min(a.steps, 3))} oracle iterations at {n}^3 "
+                                       f"({det['per_iteration_s']:.2f} s each) x {det['iterations_assumed']} "
+                                       f"iterations (oracle count at {det['small']}^3)"},
+            "e2e": {"value": round(value, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+            flush=True)
         return
     if a.workload == "ex2":
         print(json.dumps({"impl": "reference", "unavailable": "the oracle's eigen solve needs ~10^3 iterations of "
@@ -781,7 +830,13 @@ def main():
         batched = run_batched(qn)
 
     cpu = None
-    if not a.no_cpu and rank == 0 and world == 1 and not sem:
+    if not a.no_cpu and rank == 0 and world == 1 and sem:
+        ms_cpu, det = sem_oracle_sample(n, a.sem_k)
+        cpu = {"value": round(ms_cpu, 1), "unit": "ms", "cores": det["cores"], "kind": "oracle",
+               "sample": (f"1 quasi-Newton iteration of the FP64 numpy SEM oracle at {n}^3 nodes "
+                          f"({det['per_iteration_s']:.2f} s) x {det['iterations_assumed']} iterations "
+                          f"(oracle count at {det['small']}^3 nodes)")}
+    elif not a.no_cpu and rank == 0 and world == 1:
         if ex1:
             ms_cpu, det = cpu_oracle_baseline_ex1(n, a.seed)
             small = "33^3, same kind of start"
@@ -808,7 +863,7 @@ def main():
                        "launch": "iterations >= 2 replayed from a CUDA graph (qn_opts.graph)"},
             "iterations": iters[0] if len(set(iters)) == 1 else iters, "final_rel": max(rels), "converged": ok,
             "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
-            "e2e": e2e, "plain_fp64": plain, "cpu_baseline": None, "clocks": clocks,
+            "e2e": e2e, "plain_fp64": plain, "cpu_baseline": cpu, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     elif rank == 0 and ex1:
