@@ -108,6 +108,8 @@ struct qn_ctx {
     double *pot64;
     float2 *pot2;
     double *eig_r0;       // eigen solves, BF16X3: A_h U + f(U) between the two residual passes
+    double *eig_vrow;     // eigen solves with a potential: lam + v_y (+ v_z) per (y, z) row
+    float *eig_pot32;     //   and the potential tables in FP32
     int g_kind;           // graph contents: 0 quasi-Newton iterations, 1 eigen iterations
     double lam_min;       // smallest eigenvalue of the 1-D matrix H
     // spectral elements (prob.sem_k > 0): banded H on the device (k_residual_sem)
@@ -231,6 +233,8 @@ static void ctx_free(qn_ctx *c) {
     cudaFree(c->pot64);
     cudaFree(c->pot2);
     cudaFree(c->eig_r0);
+    cudaFree(c->eig_vrow);
+    cudaFree(c->eig_pot32);
     cudaFree(c->hc0);
     cudaFree(c->hlen);
     cudaFree(c->hval);
@@ -1098,7 +1102,7 @@ static int enqueue_eig_iteration(qn_ctx *c, double *U, double step, cudaStream_t
     const bool mirror = !fp64 && c->split;
     long pr = prof_begin(c, PK_RESIDUAL, s);
     int rc = launch_eig_pass1(U, lin, c->n, c->dim, c->prob.bc, c->inv_h2, c->prob.lam, c->prob.b, c->pot64,
-                              c->partials, grid, c->st, s);
+                              c->eig_vrow, c->partials, grid, c->st, s);
     prof_end(c, pr, s);
     if (rc) return rc;
     pr = prof_begin(c, PK_FINALIZE, s);
@@ -1106,7 +1110,7 @@ static int enqueue_eig_iteration(qn_ctx *c, double *U, double step, cudaStream_t
     prof_end(c, pr, s);
     if (rc) return rc;
     pr = prof_begin(c, PK_RESIDUAL, s);
-    rc = launch_eig_pass2(U, lin, c->n, c->P, c->dim, c->prob.bc, hd, c->prob.lam, c->prob.b, c->pot64,
+    rc = launch_eig_pass2(U, lin, c->n, c->P, c->dim, c->prob.bc, hd, (float)c->prob.lam, c->prob.b, c->eig_pot32,
                           fp64 ? c->w64[0] : nullptr, fp64 ? nullptr : c->bhi[0], fp64 ? nullptr : c->blo[0],
                           mirror, c->partials, grid, c->st, s);
     prof_end(c, pr, s);
@@ -1156,6 +1160,24 @@ extern "C" int qn_eig_solve(qn_ctx *c, double *U, const qn_opts *opts, qn_result
     cudaStream_t s = (cudaStream_t)stream;
     if (c->prob.precision == QN_PREC_BF16X3 && !c->eig_r0)
         QN_CUDA(cudaMalloc(&c->eig_r0, sizeof(double) * (size_t)c->N));
+    if (c->pot64 != nullptr && !c->eig_vrow) {
+        // per (y, z) row: lam + v_y + v_z; and FP32 copies of the tables (beta's extremes)
+        const int n = c->n, dn = c->dim * n;
+        std::vector<double> pt(dn);
+        QN_CUDA(cudaMemcpy(pt.data(), c->pot64, sizeof(double) * dn, cudaMemcpyDeviceToHost));
+        const size_t rows = (c->dim == 3) ? (size_t)n * n : (size_t)n;
+        std::vector<double> vr(rows);
+        for (size_t r = 0; r < rows; ++r) {
+            const int y = (int)(r % n), z = (int)(r / n);
+            vr[r] = c->prob.lam + pt[n + y] + ((c->dim == 3) ? pt[2 * n + z] : 0.0);
+        }
+        std::vector<float> p32(dn);
+        for (int i = 0; i < dn; ++i) p32[i] = (float)pt[i];
+        QN_CUDA(cudaMalloc(&c->eig_vrow, sizeof(double) * rows));
+        QN_CUDA(cudaMalloc(&c->eig_pot32, sizeof(float) * dn));
+        QN_CUDA(cudaMemcpy(c->eig_vrow, vr.data(), sizeof(double) * rows, cudaMemcpyHostToDevice));
+        QN_CUDA(cudaMemcpy(c->eig_pot32, p32.data(), sizeof(float) * dn, cudaMemcpyHostToDevice));
+    }
     rc = reset_state(c, o.tol, o.max_it, o.beta_mode, o.beta_value, s);
     if (rc) return rc;
     const size_t first_rec = c->prof_used;

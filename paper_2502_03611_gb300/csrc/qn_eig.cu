@@ -110,19 +110,23 @@ __device__ __forceinline__ void node_xyz(long long c, int n, int &x, int &y, int
 
 // lin = A_h U + (lam + V) U at every node (U unnormalised), with the per-block
 // sums of w U lin, b w U^4 and w U^2.
+// vrow: with a potential, lam + v_y(y) (+ v_z(z)) per (y, z) row (n^(DIM-1) entries), so a
+// node adds only v_x(x); without one, nullptr (the coefficient is lam).
 template <int DIM, bool NEU>
 __global__ void __launch_bounds__(256) k_eig_pass1(const double *__restrict__ U, double *__restrict__ lin, int n,
                                                    double inv_h2, double lam, double b,
-                                                   const double *__restrict__ pot, double *__restrict__ partials,
-                                                   const DevState *st) {
+                                                   const double *__restrict__ pot, const double *__restrict__ vrow,
+                                                   double *__restrict__ partials, const DevState *st) {
     if (state_done(st)) return;
     const long long nn = (long long)n * n;
     const long long N = (DIM == 3) ? nn * n : nn;
     Sum4 acc{0.0, 0.0, 0.0, 0.0};   // a: sum w u lin, b: sum w u^4, mn: sum w u^2
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += stride) {
-        int x, y, z;
-        node_xyz<DIM>(c, n, x, y, z);
+        const long long row = c / n;   // (z, y) row
+        const int x = (int)(c - row * n);
+        const int y = (DIM == 3) ? (int)(row % n) : (int)row;
+        const int z = (DIM == 3) ? (int)(row / n) : 0;
         const double u = __ldg(U + c);
         double nbv[2 * DIM];
         nbv[0] = (x > 0) ? __ldg(U + c - 1) : (NEU ? __ldg(U + c + 1) : 0.0);
@@ -134,11 +138,7 @@ __global__ void __launch_bounds__(256) k_eig_pass1(const double *__restrict__ U,
             nbv[5] = (z < n - 1) ? __ldg(U + c + nn) : (NEU ? __ldg(U + c - nn) : 0.0);
         }
         const double lap = stencil_fixed<DIM>(u, nbv);          // exact 2 DIM u - sum(nb)
-        double cv = lam;
-        if (pot != nullptr) {
-            cv += __ldg(pot + x) + __ldg(pot + n + y);
-            if (DIM == 3) cv += __ldg(pot + 2 * n + z);
-        }
+        const double cv = (pot != nullptr) ? __ldg(vrow + row) + __ldg(pot + x) : lam;
         const double lv = fma(lap, inv_h2, cv * u);
         lin[c] = lv;
         const double wu = NEU ? tw<NEU>(x, n) * tw<NEU>(y, n) * ((DIM == 3) ? tw<NEU>(z, n) : 1.0) * u : u;
@@ -177,23 +177,24 @@ __global__ void __launch_bounds__(256) k_eig_finalize1(const double *partials, i
 }
 
 // One node of pass 2: U = s U~ written back; returns F = s lin + b U^3 - lambda_n U;
-// accumulates w F^2 and the extremes of lam + 3 b U^2 + V (FP32: they only set beta_n).
+// accumulates w F^2 and the extremes of lam + 3 b U^2 + V (FP32, from the FP32 potential
+// tables pot32: they only set beta_n).
 template <int DIM, bool NEU>
 __device__ __forceinline__ double eig_point(double *__restrict__ U, const double *__restrict__ lin, long long c,
-                                            int x, int y, int z, int n, double sc, double lam_n, double lam, double b,
-                                            const double *__restrict__ pot, double &sff, float &dmn, float &dmx) {
+                                            int x, int y, int z, int n, double sc, double lam_n, float lamf, double b,
+                                            const float *__restrict__ pot32, double &sff, float &dmn, float &dmx) {
     const double u = sc * U[c];
     U[c] = u;
     const double u2 = u * u;
     const double F = fma(sc, __ldg(lin + c), fma(b * u2, u, -lam_n * u));
     const double w = NEU ? tw<NEU>(x, n) * tw<NEU>(y, n) * ((DIM == 3) ? tw<NEU>(z, n) : 1.0) : 1.0;
     sff = fma(w * F, F, sff);
-    float cv = (float)lam;
-    if (pot != nullptr) {
-        cv += (float)(__ldg(pot + x) + __ldg(pot + n + y));
-        if (DIM == 3) cv += (float)__ldg(pot + 2 * n + z);
+    float cv = lamf;
+    if (pot32 != nullptr) {
+        cv += __ldg(pot32 + x) + __ldg(pot32 + n + y);
+        if (DIM == 3) cv += __ldg(pot32 + 2 * n + z);
     }
-    const float d = __fmaf_rn(3.0f * (float)b, (float)u2, cv);
+    const float d = __fmaf_rn(3.0f * (float)b, d2f_rn(u2), cv);
     dmn = fminf(dmn, d);
     dmx = fmaxf(dmx, d);
     return F;
@@ -206,8 +207,8 @@ __device__ __forceinline__ double eig_point(double *__restrict__ U, const double
 // y, z folded).
 template <int DIM, int OUT, bool NEU>
 __global__ void __launch_bounds__(256) k_eig_pass2(double *__restrict__ U, const double *__restrict__ lin, int n,
-                                                   int P, double hd, double lam, double b,
-                                                   const double *__restrict__ pot, double *__restrict__ R64,
+                                                   int P, double hd, float lam, double b,
+                                                   const float *__restrict__ pot, double *__restrict__ R64,
                                                    __nv_bfloat16 *__restrict__ Rhi, __nv_bfloat16 *__restrict__ Rlo,
                                                    double *__restrict__ partials, const DevState *st) {
     if (state_done(st)) return;
@@ -285,20 +286,26 @@ __global__ void __launch_bounds__(256) k_eig_pass2(double *__restrict__ U, const
 
 template <int DIM>
 static void pass1_dim(const double *U, double *lin, int n, bool neu, double inv_h2, double lam, double b,
-                      const double *pot, double *partials, int grid, const DevState *st, cudaStream_t s) {
+                      const double *pot, const double *vrow, double *partials, int grid, const DevState *st,
+                      cudaStream_t s) {
     if (neu)
-        k_eig_pass1<DIM, true><<<grid, 256, 0, s>>>(U, lin, n, inv_h2, lam, b, pot, partials, st);
+        k_eig_pass1<DIM, true><<<grid, 256, 0, s>>>(U, lin, n, inv_h2, lam, b, pot, vrow, partials, st);
     else
-        k_eig_pass1<DIM, false><<<grid, 256, 0, s>>>(U, lin, n, inv_h2, lam, b, pot, partials, st);
+        k_eig_pass1<DIM, false><<<grid, 256, 0, s>>>(U, lin, n, inv_h2, lam, b, pot, vrow, partials, st);
 }
 
 int launch_eig_pass1(const double *U, double *lin, int n, int dim, int bc, double inv_h2, double lam, double b,
-                     const double *pot, double *partials, int grid, const DevState *st, cudaStream_t s) {
+                     const double *pot, const double *vrow, double *partials, int grid, const DevState *st,
+                     cudaStream_t s) {
     const bool neu = (bc == QN_BC_NEUMANN);
+    if (pot != nullptr && vrow == nullptr) {
+        set_error("launch_eig_pass1: a potential needs its per-row table");
+        return QN_EINVAL;
+    }
     if (dim == 3)
-        pass1_dim<3>(U, lin, n, neu, inv_h2, lam, b, pot, partials, grid, st, s);
+        pass1_dim<3>(U, lin, n, neu, inv_h2, lam, b, pot, vrow, partials, grid, st, s);
     else
-        pass1_dim<2>(U, lin, n, neu, inv_h2, lam, b, pot, partials, grid, st, s);
+        pass1_dim<2>(U, lin, n, neu, inv_h2, lam, b, pot, vrow, partials, grid, st, s);
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }
@@ -310,8 +317,8 @@ int launch_eig_finalize1(const double *partials, int nparts, double hd, DevState
 }
 
 template <int DIM, int OUT>
-static void pass2_t(double *U, const double *lin, int n, int P, bool neu, double hd, double lam, double b,
-                    const double *pot, double *R64, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, double *partials,
+static void pass2_t(double *U, const double *lin, int n, int P, bool neu, double hd, float lam, double b,
+                    const float *pot, double *R64, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, double *partials,
                     int grid, const DevState *st, cudaStream_t s) {
     if (neu)
         k_eig_pass2<DIM, OUT, true><<<grid, 256, 0, s>>>(U, lin, n, P, hd, lam, b, pot, R64, Rhi, Rlo, partials, st);
@@ -319,8 +326,8 @@ static void pass2_t(double *U, const double *lin, int n, int P, bool neu, double
         k_eig_pass2<DIM, OUT, false><<<grid, 256, 0, s>>>(U, lin, n, P, hd, lam, b, pot, R64, Rhi, Rlo, partials, st);
 }
 
-int launch_eig_pass2(double *U, const double *lin, int n, int P, int dim, int bc, double hd, double lam, double b,
-                     const double *pot, double *R64, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, bool mirror,
+int launch_eig_pass2(double *U, const double *lin, int n, int P, int dim, int bc, double hd, float lam, double b,
+                     const float *pot, double *R64, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, bool mirror,
                      double *partials, int grid, const DevState *st, cudaStream_t s) {
     const bool neu = (bc == QN_BC_NEUMANN);
     if (R64 != nullptr) {

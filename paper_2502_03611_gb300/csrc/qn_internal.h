@@ -139,12 +139,15 @@ int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *
 // ---- nonlinear eigenproblem (qn_eig.cu) ------------------------------------------------
 // hd = h^dim (the lumped mass without the trapezoid weights); partials: 4 doubles per block.
 // U arrives unnormalised; pass 2 writes it back normalised (DevState::eig_scale).
+// vrow: lam + v_y (+ v_z) per (y, z) row when a potential is present (else nullptr)
 int launch_eig_pass1(const double *U, double *lin, int n, int dim, int bc, double inv_h2, double lam, double b,
-                     const double *pot, double *partials, int grid, const DevState *st, cudaStream_t s);
+                     const double *pot, const double *vrow, double *partials, int grid, const DevState *st,
+                     cudaStream_t s);
 int launch_eig_finalize1(const double *partials, int nparts, double hd, DevState *st, cudaStream_t s);
 // exactly one of R64 (FP64 output) or Rhi/Rlo (split planes; mirror: reflection-split order)
-int launch_eig_pass2(double *U, const double *lin, int n, int P, int dim, int bc, double hd, double lam, double b,
-                     const double *pot, double *R64, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, bool mirror,
+// pot32: the potential tables in FP32 (for beta's extremes only), or nullptr
+int launch_eig_pass2(double *U, const double *lin, int n, int P, int dim, int bc, double hd, float lam, double b,
+                     const float *pot32, double *R64, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, bool mirror,
                      double *partials, int grid, const DevState *st, cudaStream_t s);
 
 int launch_split_pad(const double *r, int n, int P, int dim, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
