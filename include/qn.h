@@ -63,6 +63,10 @@ extern "C" {
 #define QN_BC_NEUMANN   1   /* zero normal derivative by ghost points, face nodes are unknowns
                                (Sec. 3.2, Neumann rows with alpha_3 = 0; a nonzero flux only
                                adds a constant to f at the face nodes, so pass it in f) */
+#define QN_BC_ROBIN     2   /* alpha_1 du/dn + beta_1 u = 0 by the same ghost points:
+                               u_{-1} = u_1 - 2 h kappa u_0, kappa = beta_1/alpha_1 =
+                               qn_problem.robin_kappa >= 0 (the face term belongs to A_h);
+                               finite differences, per-node residual kernel */
 
 #define QN_PREC_FP64   0    /* mode products in FP64 on the FP64 pipe */
 #define QN_PREC_BF16X3 1    /* mode products on tcgen05 tensor cores as
@@ -91,6 +95,7 @@ typedef struct qn_problem {
                          axis at the Gauss-Lobatto points (qn_setup_1d_sem gives them); the
                          residual applies H = M^{-1} S along every axis (FP64), the inverse uses
                          its numerical eigenpairs. f and the potential are nodal values. */
+    double robin_kappa;   /* QN_BC_ROBIN: kappa = beta_1 / alpha_1 >= 0 (ignored otherwise) */
 } qn_problem;
 
 typedef struct qn_stats {
@@ -148,6 +153,13 @@ const char *qn_last_error(void);
  * S, S_inv: caller-owned host buffers of n*n doubles, row-major (S[j*n+k]).
  * lam: caller-owned host buffer of n doubles. Any output may be NULL. */
 int qn_setup_1d_eig(int n, double h, int bc, double *S, double *S_inv, double *lam);
+
+/* 1-D Robin matrix (Sec. 3.2 ghost points with alpha_1 du/dn + beta_1 u = 0): the Neumann
+ * matrix with face diagonals (2 + 2 h kappa)/h^2, n >= 2 nodes including both faces,
+ * kappa >= 0. H = S diag(lam) S^{-1} from the symmetric W^{1/2} H W^{-1/2} = Q diag(lam) Q^T
+ * (W = diag(1/2, 1, .., 1, 1/2)): S = W^{-1/2} Q, S_inv = Q^T W^{1/2}, lam ascending.
+ * Host-only, FP64, outputs as qn_setup_1d_eig (any may be NULL). */
+int qn_setup_1d_robin(int n, double h, double kappa, double *S, double *S_inv, double *lam);
 
 /* 1-D Q^k spectral element matrices (Sec. 3.1 eqs. S_x, M_x, final-system-3d; Sec. 4.2).
  * Host-only, FP64. E = (n+1)/k (Dirichlet) or (n-1)/k (Neumann) equal elements of

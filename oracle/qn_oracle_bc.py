@@ -22,6 +22,10 @@ systems):
   (1/h^2) tridiag(-1, 2, -1) with its first row (2, -2, 0, ..) and last row
   (.., 0, -2, 2) / h^2. With a zero flux the source term gets no boundary
   correction (the paper's alpha_3 = 0).
+* Robin rows (the same ghost construction with alpha_1 du/dn + beta_1 u = 0,
+  kappa = beta_1 / alpha_1 >= 0): the ghost value is u_{-1} = u_1 - 2 h kappa u_0,
+  so the face rows become ((2 + 2 h kappa), -2) / h^2; the face term belongs to
+  A_h (not to N_h, so beta_n does not see it).
 * Its diagonalisation, Sec. 4.2: H is not symmetric, but W H is, with
   W = diag(1/2, 1, .., 1, 1/2) (the trapezoid weights). So
   W^{1/2} H W^{-1/2} = Q Lambda Q^T with Q orthogonal, and
@@ -69,10 +73,10 @@ __all__ = ["mesh_width", "fd_matrix_1d", "eig_1d", "apply_operator", "potential"
 
 def mesh_width(n: int, bc: str, length: float = 1.0) -> float:
     """h for n unknowns per axis: length/(n+1) (Dirichlet, interior nodes) or
-    length/(n-1) (Neumann, both faces included, n >= 2)."""
+    length/(n-1) (Neumann and Robin, both faces included, n >= 2)."""
     if bc == "dirichlet":
         return length / (n + 1)
-    if bc == "neumann":
+    if bc in ("neumann", "robin"):
         if n < 2:
             raise ValueError("Neumann data needs n >= 2 nodes per axis")
         return length / (n - 1)
@@ -82,26 +86,30 @@ def mesh_width(n: int, bc: str, length: float = 1.0) -> float:
 def trapezoid_weights(n: int, bc: str) -> np.ndarray:
     """W: ones, with 1/2 at the two face nodes for Neumann data."""
     w = np.ones(n)
-    if bc == "neumann":
+    if bc in ("neumann", "robin"):
         w[0] = w[-1] = 0.5
     return w
 
 
-def fd_matrix_1d(n: int, h: float, bc: str) -> np.ndarray:
+def fd_matrix_1d(n: int, h: float, bc: str, kappa: float = 0.0) -> np.ndarray:
     """The 1-D second-difference matrix (Sec. 3.2): Dirichlet tridiag(-1, 2, -1)/h^2
-    on the interior nodes; Neumann the same with the ghost rows (2, -2) and (-2, 2)."""
+    on the interior nodes; Neumann the same with the ghost rows (2, -2) and (-2, 2);
+    Robin with the face diagonals 2 + 2 h kappa."""
     H = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
-    if bc == "neumann":
+    if bc in ("neumann", "robin"):
         H[0, 1] = -2.0
         H[n - 1, n - 2] = -2.0
+    if bc == "robin":
+        H[0, 0] += 2.0 * h * kappa
+        H[n - 1, n - 1] += 2.0 * h * kappa
     return H / (h * h)
 
 
-def eig_1d(n: int, h: float, bc: str):
+def eig_1d(n: int, h: float, bc: str, kappa: float = 0.0):
     """(S, S_inv, lam) with H = S diag(lam) S^{-1}, lam ascending (Sec. 4.2).
 
     W^{1/2} H W^{-1/2} is symmetric (W the trapezoid weights; W = I for Dirichlet)."""
-    H = fd_matrix_1d(n, h, bc)
+    H = fd_matrix_1d(n, h, bc, kappa)
     sw = np.sqrt(trapezoid_weights(n, bc))
     Hs = (sw[:, None] * H) / sw[None, :]
     Hs = 0.5 * (Hs + Hs.T)                   # exact symmetry (the two halves agree to rounding)
@@ -111,11 +119,12 @@ def eig_1d(n: int, h: float, bc: str):
     return S, S_inv, lam
 
 
-def apply_operator(U: np.ndarray, h: float, bc: str) -> np.ndarray:
+def apply_operator(U: np.ndarray, h: float, bc: str, kappa: float = 0.0) -> np.ndarray:
     """sum over axes of (2 u_i - u_{i-1} - u_{i+1}) / h^2 (eq. fdm-discrete); the
-    value past a face is 0 (Dirichlet) or the ghost value u_{-1} = u_1,
-    u_n = u_{n-2} (Neumann), i.e. an even reflection about the face node."""
-    mode = "reflect" if bc == "neumann" else "constant"
+    value past a face is 0 (Dirichlet), the ghost value u_{-1} = u_1,
+    u_n = u_{n-2} (Neumann: an even reflection about the face node), or that value
+    minus 2 h kappa u_face (Robin)."""
+    mode = "reflect" if bc in ("neumann", "robin") else "constant"
     n = U.shape[0]
     out = np.zeros_like(U)
     for axis in range(U.ndim):
@@ -125,6 +134,11 @@ def apply_operator(U: np.ndarray, h: float, bc: str) -> np.ndarray:
         lo[axis] = slice(0, n)
         hi[axis] = slice(2, n + 2)
         out += (2.0 * U - P[tuple(lo)] - P[tuple(hi)]) / (h * h)
+        if bc == "robin":   # the ghost's -2 h kappa u_face term, at both faces of this axis
+            for face in (0, n - 1):
+                sl = [slice(None)] * U.ndim
+                sl[axis] = face
+                out[tuple(sl)] += (2.0 * kappa / h) * U[tuple(sl)]
     return out
 
 
@@ -143,9 +157,9 @@ def potential(v, dim: int, n: int) -> np.ndarray:
     return V
 
 
-def residual(U, f, h: float, bc: str, lam: float = 0.0, b: float = 1.0, V=None) -> np.ndarray:
+def residual(U, f, h: float, bc: str, lam: float = 0.0, b: float = 1.0, V=None, kappa: float = 0.0) -> np.ndarray:
     """F(U) = A_h vec(U) + N_h(U): apply_operator + lam U + b U^3 + V U - f."""
-    r = apply_operator(U, h, bc) + lam * U + b * U ** 3 - f
+    r = apply_operator(U, h, bc, kappa) + lam * U + b * U ** 3 - f
     if V is not None:
         r = r + V * U
     return r
@@ -173,18 +187,18 @@ def qn_step(U, f, h: float, bc: str, eig=None, lam: float = 0.0, b: float = 1.0,
 
 
 def qn_solve(f, h: float, bc: str, U0=None, tol: float = 1e-10, max_it: int = 500,
-             lam: float = 0.0, b: float = 1.0, V=None, beta=None, step: float = 1.0):
+             lam: float = 0.0, b: float = 1.0, V=None, beta=None, step: float = 1.0, kappa: float = 0.0):
     """Iterate eq. identity-method until ||F(U)||_2 / ||f||_2 <= tol.
 
     Returns (U, history, converged) as qn_oracle.qn_solve; history entries hold
     rel, res, beta, fu_min and fu_max (the extremes of 3 b U^2 + V)."""
     n = f.shape[0]
-    S, S_inv, lam1d = eig_1d(n, h, bc)
+    S, S_inv, lam1d = eig_1d(n, h, bc, kappa)
     U = np.zeros_like(f) if U0 is None else np.array(U0, dtype=np.float64, copy=True)
     fnorm = float(np.linalg.norm(f.ravel()))
     history = []
     for it in range(max_it + 1):
-        r = residual(U, f, h, bc, lam, b, V)
+        r = residual(U, f, h, bc, lam, b, V, kappa)
         rnorm = float(np.linalg.norm(r.ravel()))
         rel = rnorm / fnorm
         d = jacobian_diag(U, b, V)
@@ -199,10 +213,10 @@ def qn_solve(f, h: float, bc: str, U0=None, tol: float = 1e-10, max_it: int = 50
     return U, history, False
 
 
-def dense_operator(n: int, dim: int, h: float, bc: str, lam: float = 0.0) -> np.ndarray:
+def dense_operator(n: int, dim: int, h: float, bc: str, lam: float = 0.0, kappa: float = 0.0) -> np.ndarray:
     """A_h = sum_a I..H_a..I + lam I as an explicit matrix (Kronecker products of
     fd_matrix_1d, eq. A_definition), acting on the C-order ravel (x fastest)."""
-    H = fd_matrix_1d(n, h, bc)
+    H = fd_matrix_1d(n, h, bc, kappa)
     I = np.eye(n)
     if dim == 2:
         A = np.kron(I, H) + np.kron(H, I)

@@ -284,11 +284,15 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
         set_error("qn_ctx_create: dim must be 2 or 3 (got %d)", p->dim);
         return QN_EINVAL;
     }
-    if (p->bc != QN_BC_DIRICHLET && p->bc != QN_BC_NEUMANN) {
+    if (p->bc != QN_BC_DIRICHLET && p->bc != QN_BC_NEUMANN && p->bc != QN_BC_ROBIN) {
         set_error("qn_ctx_create: unknown boundary condition %d", p->bc);
         return QN_EINVAL;
     }
-    const int nmin = (p->bc == QN_BC_NEUMANN) ? 2 : 1;
+    if (p->bc == QN_BC_ROBIN && (!(p->robin_kappa >= 0.0) || !isfinite(p->robin_kappa) || p->sem_k != 0)) {
+        set_error("qn_ctx_create: QN_BC_ROBIN needs a finite robin_kappa >= 0 and finite differences");
+        return QN_EINVAL;
+    }
+    const int nmin = (p->bc == QN_BC_DIRICHLET) ? 1 : 2;
     if (p->n < nmin || p->n > 1024) {
         set_error("qn_ctx_create: n must be in [%d, 1024] (got %d)", nmin, p->n);
         return QN_EINVAL;
@@ -355,7 +359,7 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
     if (p->sem_k > 0) {   // element width
         c->h = Ldom * p->sem_k / ((p->bc == QN_BC_NEUMANN) ? c->n - 1 : c->n + 1);
     } else {
-        c->h = (p->bc == QN_BC_NEUMANN) ? Ldom / (c->n - 1) : Ldom / (c->n + 1);
+        c->h = (p->bc == QN_BC_DIRICHLET) ? Ldom / (c->n + 1) : Ldom / (c->n - 1);
     }
     c->prob.potential_host = nullptr;   // not retained
     c->inv_h2 = 1.0 / (c->h * c->h);
@@ -398,6 +402,12 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
         CK(cudaMemcpy(c->hc0, c0.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(c->hlen, len.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(c->hval, hv.data(), sizeof(double) * (size_t)n * bw, cudaMemcpyHostToDevice));
+    } else if (p->bc == QN_BC_ROBIN) {
+        rc = qn_setup_1d_robin(n, c->h, p->robin_kappa, S.data(), Si.data(), lam.data());
+        if (rc != QN_OK) {
+            ctx_free(c);
+            return rc;
+        }
     } else {
         rc = qn_setup_1d_eig(n, c->h, p->bc, S.data(), Si.data(), lam.data());
         if (rc != QN_OK) {
@@ -482,7 +492,8 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
         // the float-pair residual needs lam, b and 1/h^2 well inside the FP32 range
         const bool pair_ok = fabs(p->lam) < 0x1p40 && fabs(p->b) < 0x1p20 && c->inv_h2 < 0x1p24 &&
                              vmax < 0x1p40;
-        if (c->dim == 3 && pair_ok && p->sem_k == 0) {   // (the FP64-free residual is the FD stencil's)
+        // (the FP64-free residual is the Dirichlet / Neumann FD stencil's)
+        if (c->dim == 3 && pair_ok && p->sem_k == 0 && p->bc != QN_BC_ROBIN) {
             CK(cudaMalloc(&c->fdf, sizeof(float2) * (size_t)c->NP));
         } else {
             c->res_tiled = 0;
@@ -627,6 +638,7 @@ static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double 
     a.pot = c->pot64;
     a.pot2 = c->pot2;
     a.umax_scan = &c->st->umax_scan;
+    a.robin = (c->prob.bc == QN_BC_ROBIN) ? 2.0 * c->prob.robin_kappa / c->h : 0.0;
     a.hc0 = c->hc0;
     a.hlen = c->hlen;
     a.hval = c->hval;
@@ -834,7 +846,7 @@ extern "C" int qn_fast_diag_solve(qn_ctx *c, const double *r, double *V, double 
         return QN_EINVAL;
     }
     // smallest eigenvalue of sum_a H_a is dim * lambda_1 (0 for Neumann data: constants)
-    const double l1 = (c->prob.bc == QN_BC_NEUMANN) ? 0.0 : c->lam_min;
+    const double l1 = (c->prob.bc == QN_BC_NEUMANN) ? 0.0 : fmax(c->lam_min, 0.0);
     if (!(shift > -c->dim * l1)) {
         set_error("qn_fast_diag_solve: shift %.6g makes the operator singular or indefinite", shift);
         return QN_EINVAL;
@@ -1130,8 +1142,8 @@ extern "C" int qn_eig_solve(qn_ctx *c, double *U, const qn_opts *opts, qn_result
         set_error("qn_eig_solve: null U");
         return QN_EINVAL;
     }
-    if (c->prob.sem_k > 0) {
-        set_error("qn_eig_solve: finite-difference contexts only");
+    if (c->prob.sem_k > 0 || c->prob.bc == QN_BC_ROBIN) {
+        set_error("qn_eig_solve: finite differences with Dirichlet or Neumann data only");
         return QN_EUNSUPPORTED;
     }
     qn_opts o;

@@ -76,6 +76,7 @@ struct ResidualArgs {
     const int *hlen;
     const double *hval;
     int hbw;
+    double robin;              // QN_BC_ROBIN: 2 kappa / h, added times u once per face a node lies on
 };
 
 // Epilogue selector shared by both mode-product kernels.
@@ -214,6 +215,9 @@ bool tc_supported(int device);
 int solve_internal(::qn_ctx *c, double *U, const double *f, const qn_opts *opts, qn_result *res,
                    qn_stats *history, int history_len, void *stream, const double *u0_sq, int *used_warm);
 bool ctx_split_precision(const ::qn_ctx *c);
+// Symmetric eigen-decomposition on the host (qn_sem.cu): A (row-major n x n) is replaced by
+// Q with A = Q diag(d) Q^T, d ascending; false if the QL iteration does not converge.
+bool symmetric_eigen(int n, std::vector<double> &A, std::vector<double> &d);
 // host setup of the Q^k spectral element matrices (qn_sem.cu); see qn_setup_1d_sem
 int sem_setup(int n, int k, double length, int bc, std::vector<double> &H, std::vector<double> &S,
               std::vector<double> &Si, std::vector<double> &lam, std::vector<double> &nodes);

@@ -145,9 +145,10 @@ __device__ __forceinline__ void residual_sweep(const ResidualArgs &a, ResAcc &s)
     const double *__restrict__ U = a.U;
     const double *__restrict__ f = a.f;
     const long long nn = (long long)n * n;
-    // Neumann faces: the missing neighbour is the ghost value, i.e. the
-    // neighbour on the other side (n >= 2 is guaranteed for Neumann data)
-    const bool neu = (a.bc == QN_BC_NEUMANN);
+    // Neumann and Robin faces: the missing neighbour is the ghost value, i.e. the
+    // neighbour on the other side (n >= 2 is guaranteed for these data); Robin adds
+    // -2 h kappa u to the ghost, i.e. (2 kappa / h) u per face to the residual
+    const bool neu = (a.bc == QN_BC_NEUMANN || a.bc == QN_BC_ROBIN);
     for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
         const int y = (DIM == 3) ? (int)(row % P) : (int)row;
         const int z = (DIM == 3) ? (int)(row / P) : 0;
@@ -197,6 +198,11 @@ __device__ __forceinline__ void residual_sweep(const ResidualArgs &a, ResAcc &s)
                     s.dmx = fmax(s.dmx, d);
                 }
                 r = fma(lap, a.inv_h2, t);
+                if (a.robin != 0.0) {
+                    int faces = (x == 0) + (x == n - 1) + (y == 0) + (y == n - 1);
+                    if (DIM == 3) faces += (z == 0) + (z == n - 1);
+                    r = fma(a.robin * faces, u, r);
+                }
                 const unsigned long long ab = abs_bits(u);
                 s.amin = ab < s.amin ? ab : s.amin;
                 s.amax = ab > s.amax ? ab : s.amax;

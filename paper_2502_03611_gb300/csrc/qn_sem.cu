@@ -75,121 +75,6 @@ void gauss_lobatto(int k, std::vector<double> &x, std::vector<double> &w) {
     }
 }
 
-// Symmetric eigen-decomposition A = Q diag(d) Q^T (A overwritten with Q, row-major n x n),
-// eigenvalues ascending. Returns false if the QL iteration does not converge.
-bool symmetric_eigen(int n, std::vector<double> &A, std::vector<double> &d) {
-    std::vector<double> Q((size_t)n * n, 0.0), e(n, 0.0), v(n), p(n);
-    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
-    auto a = [&](int i, int j) -> double & { return A[(size_t)i * n + j]; };
-    // Householder: for column c, reflect rows c+1.. so that A[c+2.., c] = 0
-    for (int c = 0; c + 2 < n; ++c) {
-        const int m = n - c - 1;   // length of the reflected part
-        double nrm = 0.0;
-        for (int i = 0; i < m; ++i) nrm += a(c + 1 + i, c) * a(c + 1 + i, c);
-        nrm = sqrt(nrm);
-        if (nrm == 0.0) continue;
-        const double x0 = a(c + 1, c);
-        const double alpha = (x0 >= 0.0) ? -nrm : nrm;
-        for (int i = 0; i < m; ++i) v[i] = a(c + 1 + i, c);
-        v[0] -= alpha;
-        double vn = 0.0;
-        for (int i = 0; i < m; ++i) vn += v[i] * v[i];
-        if (vn == 0.0) continue;
-        const double inv = 1.0 / vn;
-        // A <- P A P with P = I - 2 v v^T / (v^T v) on rows/cols c+1..: p = A v, K = v^T p / vn,
-        // q = 2 (p - K v) / vn, A <- A - v q^T - q v^T (symmetric rank-2 update)
-        for (int i = 0; i < n; ++i) {
-            double s = 0.0;
-            for (int j = 0; j < m; ++j) s += a(i, c + 1 + j) * v[j];
-            p[i] = s;
-        }
-        double K = 0.0;
-        for (int j = 0; j < m; ++j) K += v[j] * p[c + 1 + j];
-        K *= inv;
-        std::vector<double> q(n, 0.0);
-        for (int i = 0; i < n; ++i) {
-            const double vi = (i > c) ? v[i - c - 1] : 0.0;
-            q[i] = 2.0 * inv * (p[i] - K * vi);
-        }
-        for (int i = 0; i < n; ++i) {
-            const double vi = (i > c) ? v[i - c - 1] : 0.0;
-            for (int j = 0; j < n; ++j) {
-                const double vj = (j > c) ? v[j - c - 1] : 0.0;
-                a(i, j) -= vi * q[j] + q[i] * vj;
-            }
-        }
-        // Q <- Q P
-        for (int i = 0; i < n; ++i) {
-            double s = 0.0;
-            for (int j = 0; j < m; ++j) s += Q[(size_t)i * n + c + 1 + j] * v[j];
-            s *= 2.0 * inv;
-            for (int j = 0; j < m; ++j) Q[(size_t)i * n + c + 1 + j] -= s * v[j];
-        }
-    }
-    d.assign(n, 0.0);
-    for (int i = 0; i < n; ++i) d[i] = a(i, i);
-    for (int i = 0; i + 1 < n; ++i) e[i] = a(i + 1, i);
-    e[n - 1] = 0.0;
-    // implicit QL on the tridiagonal (d, e), rotations accumulated into Q's columns
-    for (int l = 0; l < n; ++l) {
-        int iter = 0;
-        for (;;) {
-            int m = l;
-            for (; m < n - 1; ++m) {
-                const double dd = fabs(d[m]) + fabs(d[m + 1]);
-                if (fabs(e[m]) + dd == dd) break;   // negligible next to its diagonal neighbours
-            }
-            if (m == l) break;
-            if (++iter > 60) return false;
-            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = hypot(g, 1.0);
-            g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
-            double s = 1.0, c = 1.0, pp = 0.0;
-            bool split_early = false;
-            for (int i = m - 1; i >= l; --i) {
-                double f = s * e[i];
-                const double b = c * e[i];
-                r = hypot(f, g);
-                e[i + 1] = r;
-                if (r == 0.0) {   // the rotation decouples: deflate and iterate again
-                    d[i + 1] -= pp;
-                    e[m] = 0.0;
-                    split_early = true;
-                    break;
-                }
-                s = f / r;
-                c = g / r;
-                g = d[i + 1] - pp;
-                r = (d[i] - g) * s + 2.0 * c * b;
-                pp = s * r;
-                d[i + 1] = g + pp;
-                g = c * r - b;
-                for (int row = 0; row < n; ++row) {
-                    double *qr = &Q[(size_t)row * n];
-                    f = qr[i + 1];
-                    qr[i + 1] = s * qr[i] + c * f;
-                    qr[i] = c * qr[i] - s * f;
-                }
-            }
-            if (split_early) continue;
-            d[l] -= pp;
-            e[l] = g;
-            e[m] = 0.0;
-        }
-    }
-    // ascending order
-    std::vector<int> ord(n);
-    for (int i = 0; i < n; ++i) ord[i] = i;
-    std::sort(ord.begin(), ord.end(), [&](int x, int y) { return d[x] < d[y]; });
-    std::vector<double> d2(n);
-    for (int j = 0; j < n; ++j) {
-        d2[j] = d[ord[j]];
-        for (int i = 0; i < n; ++i) A[(size_t)i * n + j] = Q[(size_t)i * n + ord[j]];
-    }
-    d = d2;
-    return true;
-}
-
 // ---- device: the banded SEM residual ------------------------------------------------------
 struct Red4s {
     double r2, f2, mn, mx;
@@ -333,6 +218,121 @@ void launch_sem_dim(const ResidualArgs &a, int grid, cudaStream_t s) {
 
 }  // namespace
 
+// Symmetric eigen-decomposition A = Q diag(d) Q^T (A overwritten with Q, row-major n x n),
+// eigenvalues ascending. Returns false if the QL iteration does not converge.
+bool symmetric_eigen(int n, std::vector<double> &A, std::vector<double> &d) {
+    std::vector<double> Q((size_t)n * n, 0.0), e(n, 0.0), v(n), p(n);
+    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+    auto a = [&](int i, int j) -> double & { return A[(size_t)i * n + j]; };
+    // Householder: for column c, reflect rows c+1.. so that A[c+2.., c] = 0
+    for (int c = 0; c + 2 < n; ++c) {
+        const int m = n - c - 1;   // length of the reflected part
+        double nrm = 0.0;
+        for (int i = 0; i < m; ++i) nrm += a(c + 1 + i, c) * a(c + 1 + i, c);
+        nrm = sqrt(nrm);
+        if (nrm == 0.0) continue;
+        const double x0 = a(c + 1, c);
+        const double alpha = (x0 >= 0.0) ? -nrm : nrm;
+        for (int i = 0; i < m; ++i) v[i] = a(c + 1 + i, c);
+        v[0] -= alpha;
+        double vn = 0.0;
+        for (int i = 0; i < m; ++i) vn += v[i] * v[i];
+        if (vn == 0.0) continue;
+        const double inv = 1.0 / vn;
+        // A <- P A P with P = I - 2 v v^T / (v^T v) on rows/cols c+1..: p = A v, K = v^T p / vn,
+        // q = 2 (p - K v) / vn, A <- A - v q^T - q v^T (symmetric rank-2 update)
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < m; ++j) s += a(i, c + 1 + j) * v[j];
+            p[i] = s;
+        }
+        double K = 0.0;
+        for (int j = 0; j < m; ++j) K += v[j] * p[c + 1 + j];
+        K *= inv;
+        std::vector<double> q(n, 0.0);
+        for (int i = 0; i < n; ++i) {
+            const double vi = (i > c) ? v[i - c - 1] : 0.0;
+            q[i] = 2.0 * inv * (p[i] - K * vi);
+        }
+        for (int i = 0; i < n; ++i) {
+            const double vi = (i > c) ? v[i - c - 1] : 0.0;
+            for (int j = 0; j < n; ++j) {
+                const double vj = (j > c) ? v[j - c - 1] : 0.0;
+                a(i, j) -= vi * q[j] + q[i] * vj;
+            }
+        }
+        // Q <- Q P
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < m; ++j) s += Q[(size_t)i * n + c + 1 + j] * v[j];
+            s *= 2.0 * inv;
+            for (int j = 0; j < m; ++j) Q[(size_t)i * n + c + 1 + j] -= s * v[j];
+        }
+    }
+    d.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) d[i] = a(i, i);
+    for (int i = 0; i + 1 < n; ++i) e[i] = a(i + 1, i);
+    e[n - 1] = 0.0;
+    // implicit QL on the tridiagonal (d, e), rotations accumulated into Q's columns
+    for (int l = 0; l < n; ++l) {
+        int iter = 0;
+        for (;;) {
+            int m = l;
+            for (; m < n - 1; ++m) {
+                const double dd = fabs(d[m]) + fabs(d[m + 1]);
+                if (fabs(e[m]) + dd == dd) break;   // negligible next to its diagonal neighbours
+            }
+            if (m == l) break;
+            if (++iter > 60) return false;
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = hypot(g, 1.0);
+            g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
+            double s = 1.0, c = 1.0, pp = 0.0;
+            bool split_early = false;
+            for (int i = m - 1; i >= l; --i) {
+                double f = s * e[i];
+                const double b = c * e[i];
+                r = hypot(f, g);
+                e[i + 1] = r;
+                if (r == 0.0) {   // the rotation decouples: deflate and iterate again
+                    d[i + 1] -= pp;
+                    e[m] = 0.0;
+                    split_early = true;
+                    break;
+                }
+                s = f / r;
+                c = g / r;
+                g = d[i + 1] - pp;
+                r = (d[i] - g) * s + 2.0 * c * b;
+                pp = s * r;
+                d[i + 1] = g + pp;
+                g = c * r - b;
+                for (int row = 0; row < n; ++row) {
+                    double *qr = &Q[(size_t)row * n];
+                    f = qr[i + 1];
+                    qr[i + 1] = s * qr[i] + c * f;
+                    qr[i] = c * qr[i] - s * f;
+                }
+            }
+            if (split_early) continue;
+            d[l] -= pp;
+            e[l] = g;
+            e[m] = 0.0;
+        }
+    }
+    // ascending order
+    std::vector<int> ord(n);
+    for (int i = 0; i < n; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int x, int y) { return d[x] < d[y]; });
+    std::vector<double> d2(n);
+    for (int j = 0; j < n; ++j) {
+        d2[j] = d[ord[j]];
+        for (int i = 0; i < n; ++i) A[(size_t)i * n + j] = Q[(size_t)i * n + ord[j]];
+    }
+    d = d2;
+    return true;
+}
+
 int launch_residual_sem(const ResidualArgs &a, int grid, cudaStream_t s) {
     const bool split = a.Rhi != nullptr;
     if (a.dim == 3) {
@@ -428,6 +428,40 @@ int sem_setup(int n, int k, double length, int bc, std::vector<double> &H, std::
 }
 
 }  // namespace qn
+
+extern "C" int qn_setup_1d_robin(int n, double h, double kappa, double *S, double *S_inv, double *lam) {
+    if (n < 2 || n > 65536 || !(h > 0.0) || !isfinite(h) || !(kappa >= 0.0) || !isfinite(kappa)) {
+        qn::set_error("qn_setup_1d_robin: need n >= 2, h > 0 and a finite kappa >= 0");
+        return QN_EINVAL;
+    }
+    // W^{1/2} H W^{-1/2}: tridiagonal, symmetric; off-diagonals -1/h^2 inside, -sqrt(2)/h^2 at
+    // the faces (W^{1/2} (-2) W^{-1/2} with w = 1/2 on the face and 1 next to it)
+    std::vector<double> A((size_t)n * n, 0.0), lamv;
+    const double ih2 = 1.0 / (h * h);
+    for (int i = 0; i < n; ++i) A[(size_t)i * n + i] = 2.0 * ih2;
+    A[0] += 2.0 * kappa / h;
+    A[(size_t)(n - 1) * n + n - 1] += 2.0 * kappa / h;
+    for (int i = 0; i + 1 < n; ++i) {
+        const bool face = (i == 0 || i + 1 == n - 1);
+        const double off = face ? -sqrt(2.0) * ih2 : -ih2;
+        A[(size_t)i * n + i + 1] = A[(size_t)(i + 1) * n + i] = off;
+    }
+    if (n == 2) A[1] = A[2] = -2.0 * ih2;   // both nodes are faces: W = I/2, the -2 entries stay
+    if (!qn::symmetric_eigen(n, A, lamv)) {
+        qn::set_error("qn_setup_1d_robin: the eigenvalue iteration did not converge");
+        return QN_ECUDA;
+    }
+    for (int j = 0; j < n; ++j) {
+        const double sw = (j == 0 || j == n - 1) ? sqrt(0.5) : 1.0;   // sqrt(w_j)
+        for (int k = 0; k < n; ++k) {
+            const double q = A[(size_t)j * n + k];
+            if (S) S[(size_t)j * n + k] = q / sw;
+            if (S_inv) S_inv[(size_t)k * n + j] = q * sw;
+        }
+    }
+    if (lam) memcpy(lam, lamv.data(), sizeof(double) * n);
+    return QN_OK;
+}
 
 extern "C" int qn_setup_1d_sem(int n, int k, double length, int bc, double *H, double *S, double *S_inv,
                                double *lam, double *nodes) {

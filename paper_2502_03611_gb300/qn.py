@@ -26,7 +26,8 @@ QN_EUNSUPPORTED = -7
 
 QN_BC_DIRICHLET = 0
 QN_BC_NEUMANN = 1
-BCS = {"dirichlet": QN_BC_DIRICHLET, "neumann": QN_BC_NEUMANN}
+QN_BC_ROBIN = 2
+BCS = {"dirichlet": QN_BC_DIRICHLET, "neumann": QN_BC_NEUMANN, "robin": QN_BC_ROBIN}
 QN_PREC_FP64 = 0
 QN_PREC_BF16X3 = 1
 QN_BETA_PAPER = 0
@@ -39,7 +40,7 @@ class QnProblem(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("bc", ctypes.c_int),
                 ("precision", ctypes.c_int), ("lam", ctypes.c_double), ("b", ctypes.c_double),
                 ("length", ctypes.c_double), ("potential_host", ctypes.POINTER(ctypes.c_double)),
-                ("sem_k", ctypes.c_int)]
+                ("sem_k", ctypes.c_int), ("robin_kappa", ctypes.c_double)]
 
 
 class QnStats(ctypes.Structure):
@@ -113,6 +114,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "qn_version": (ctypes.c_int, []),
         "qn_last_error": (ctypes.c_char_p, []),
         "qn_setup_1d_eig": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, D, D, D]),
+        "qn_setup_1d_robin": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, D, D, D]),
         "qn_setup_1d_sem": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, D, D, D, D, D]),
         "qn_ctx_create": (ctypes.c_int, [ctypes.POINTER(QnProblem), ctypes.POINTER(P)]),
         "qn_ctx_destroy": (ctypes.c_int, [P]),
@@ -208,7 +210,7 @@ class QnContext:
 
     def __init__(self, dim: int, n: int, precision: str | int = "fp64", lam: float = 0.0,
                  b: float = 1.0, bc: str | int = QN_BC_DIRICHLET, length: float = 0.0, potential=None,
-                 sem_k: int = 0):
+                 sem_k: int = 0, robin_kappa: float = 0.0):
         """potential: None, or the 1-D tables of V = v_x + v_y (+ v_z) at the nodes, an array
         of shape (n,) (the same table on every axis) or (dim, n) (x first)."""
         lib = load_library()
@@ -221,7 +223,7 @@ class QnContext:
             if pot.shape != (dim, n):
                 raise ValueError(f"potential tables must have shape ({n},) or ({dim}, {n})")
         ptr = pot.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if pot is not None else None
-        self.problem = QnProblem(dim, n, bcv, prec, lam, b, length, ptr, sem_k)
+        self.problem = QnProblem(dim, n, bcv, prec, lam, b, length, ptr, sem_k, robin_kappa)
         self.dim, self.n, self.precision, self.bc = dim, n, prec, bcv
         self.numel = n ** dim
         h = ctypes.c_void_p()
@@ -253,6 +255,17 @@ class QnContext:
 def qn_ctx_create(dim, n, precision="fp64", lam=0.0, b=1.0, bc=QN_BC_DIRICHLET, length=0.0,
                   potential=None, sem_k=0) -> QnContext:
     return QnContext(dim, n, precision, lam, b, bc, length, potential, sem_k)
+
+
+def qn_setup_1d_robin(n: int, h: float, kappa: float):
+    """Host Robin diagonalisation; returns numpy (S, S_inv, lam)."""
+    lib = load_library()
+    S = np.empty((n, n))
+    Si = np.empty((n, n))
+    lam = np.empty(n)
+    D = ctypes.POINTER(ctypes.c_double)
+    _check(lib.qn_setup_1d_robin(n, h, kappa, S.ctypes.data_as(D), Si.ctypes.data_as(D), lam.ctypes.data_as(D)))
+    return S, Si, lam
 
 
 def qn_setup_1d_sem(n: int, k: int, length: float = 1.0, bc: int = QN_BC_DIRICHLET):

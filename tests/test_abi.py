@@ -145,3 +145,16 @@ def test_setup_1d_sem_large_and_rejects_bad_sizes(lib):
     assert lib.qn_setup_1d_sem(10, 4, 1.0, 0, None, None, None, None, None) == qn.QN_EINVAL   # 11 % 4 != 0
     assert lib.qn_setup_1d_sem(9, 0, 1.0, 0, None, None, None, None, None) == qn.QN_EINVAL
     assert lib.qn_setup_1d_sem(9, 2, -1.0, 0, None, None, None, None, None) == qn.QN_EINVAL
+
+
+@pytest.mark.parametrize("n,kappa", [(2, 1.0), (3, 0.0), (9, 2.5), (40, 0.3)])
+def test_setup_1d_robin_matches_oracle(lib, n, kappa):
+    from oracle import qn_oracle_bc as ob
+    from paper_2502_03611_gb300 import qn
+    h = ob.mesh_width(n, "robin", 2.0)
+    S, Si, lam = qn.qn_setup_1d_robin(n, h, kappa)
+    _, _, lamo = ob.eig_1d(n, h, "robin", kappa)
+    assert np.abs(lam - lamo).max() <= 1e-11 * np.abs(lamo).max()
+    H = ob.fd_matrix_1d(n, h, "robin", kappa)
+    assert np.abs(H @ S - S * lam[None, :]).max() < 1e-11 * np.abs(lam).max()
+    assert np.abs(Si @ S - np.eye(n)).max() < 1e-12

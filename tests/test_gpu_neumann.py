@@ -334,3 +334,49 @@ def test_warm_start_rejects_neumann(qn):
     with pytest.raises(qn.QnError) as e:
         qn.qn_solve_warm(ctx, net, U, f)
     assert e.value.code == qn.QN_EUNSUPPORTED
+
+
+# --------------------------------------------------------------------------------------------
+# Robin faces: alpha_1 du/dn + beta_1 u = 0, kappa = beta_1 / alpha_1 (per-node residual path)
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,n", [(2, 2), (2, 40), (3, 3), (3, 33)])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_robin_residual_and_inverse_match_oracle(qn, dim, n, prec):
+    import torch
+    kappa, L = 1.7, 2.0
+    U = I.random_field((n,) * dim, seed=n + 11)
+    f = I.random_field((n,) * dim, seed=n + 12) * 30.0
+    ctx = qn.QnContext(dim, n, prec, lam=0.4, b=1.2, bc="robin", length=L, robin_kappa=kappa)
+    R = torch.empty(n ** dim, dtype=torch.float64, device="cuda")
+    st = qn.qn_residual(ctx, dev(U).reshape(-1), dev(f).reshape(-1), R)
+    h = ob.mesh_width(n, "robin", L)
+    want = ob.residual(U, f, h, "robin", 0.4, 1.2, None, kappa)
+    scale = np.abs(want).max() + (4 * dim / h ** 2 + 2 * dim * kappa / h) * np.abs(U).max()
+    assert np.abs(host(R).reshape(want.shape) - want).max() <= 1e-13 * scale
+    assert st["beta"] == pytest.approx(ob.beta_rule(U, 1.2), rel=1e-13)    # no face term in beta
+    V = torch.empty(n ** dim, dtype=torch.float64, device="cuda")
+    qn.qn_fast_diag_solve(ctx, dev(f).reshape(-1), V, 0.7)
+    torch.cuda.synchronize()
+    S, Si, lam = ob.eig_1d(n, h, "robin", kappa)
+    wantv = qo.fast_diag_solve(f, S, Si, lam, 0.7)
+    tol = 1e-11 if prec == "fp64" else 3e-4
+    assert np.abs(host(V).reshape(wantv.shape) - wantv).max() <= tol * np.abs(wantv).max()
+
+
+@pytest.mark.parametrize("dim,n,prec", [(2, 50, "fp64"), (2, 64, "bf16x3"), (3, 17, "fp64"), (3, 33, "bf16x3"),
+                                        (3, 65, "bf16x3")])
+def test_robin_solve_matches_oracle(qn, dim, n, prec):
+    import torch
+    kappa, L = 2.5, 2.0
+    h = ob.mesh_width(n, "robin", L)
+    f = 20.0 + 10.0 * I.random_field((n,) * dim, seed=3 * n)
+    ctx = qn.QnContext(dim, n, prec, lam=1.0, b=1.0, bc="robin", length=L, robin_kappa=kappa)
+    U = torch.zeros(n ** dim, dtype=torch.float64, device="cuda")
+    res, hist = qn.qn_solve(ctx, U, dev(f).reshape(-1), tol=1e-10, max_it=200, history_len=201)
+    Uo, ho, ok = ob.qn_solve(f, h, "robin", lam=1.0, b=1.0, kappa=kappa, tol=1e-10)
+    assert ok and res["status"] == 0 and res["rel"] <= 1e-10
+    Ug = host(U).reshape(f.shape)
+    rel = np.linalg.norm(ob.residual(Ug, f, h, "robin", 1.0, 1.0, None, kappa)) / np.linalg.norm(f)
+    assert rel <= 1.05e-10
+    assert np.abs(Ug - Uo).max() <= 1e-9 * np.abs(Uo).max()
+    assert abs(res["iterations"] - (len(ho) - 1)) <= (1 if prec == "fp64" else 2)

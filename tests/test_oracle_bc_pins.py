@@ -266,3 +266,72 @@ def test_eig_linear_rate_is_second_eigenvalue_ratio():
     rate = (rel[k1] / rel[k0]) ** (1.0 / (k1 - k0))
     assert 0.2 < mu[1] < 1.0
     assert rate == pytest.approx(mu[1], rel=0.03)
+
+
+# ---------------------------------------------------------------------------------------------
+# Robin faces (ghost points with alpha_1 du/dn + beta_1 u = 0, kappa = beta_1 / alpha_1)
+# ---------------------------------------------------------------------------------------------
+def test_robin_rows_taylor_consistency():
+    """u = cos(w (x - 1/2)) on [0, 1] satisfies -u'(0) + kappa u(0) = 0 = u'(1) + kappa u(1) for
+    kappa = w tan(w/2), and -u'' = w^2 u. Taylor expansion of the ghost-point face row with the
+    exact Robin data leaves -u'' - (h/3) u3(0) + O(h^2), u3 the third derivative: the face error
+    must match that term (a wrong kappa or face row leaves an O(1) error); the interior rows are
+    second order."""
+    w = 2.0
+    kappa = w * math.tan(w / 2)
+    u3_0 = w ** 3 * math.sin(-0.5 * w)                 # third derivative of cos(w (x - 1/2)) at 0
+    interior = []
+    for n in (33, 65):
+        h = ob.mesh_width(n, "robin", 1.0)
+        x = h * np.arange(n)
+        u = np.cos(w * (x - 0.5))
+        e = ob.fd_matrix_1d(n, h, "robin", kappa) @ u - w * w * u
+        lead = -(h / 3.0) * u3_0
+        assert abs(e[0] - lead) < 0.1 * abs(lead) and abs(e[-1] - lead) < 0.1 * abs(lead)
+        interior.append(np.max(np.abs(e[1:-1])))
+    assert 3.5 < interior[0] / interior[1] < 4.5
+
+
+def test_robin_limits_and_spectrum():
+    """kappa = 0 is Neumann; the spectrum (general eigensolver on the matrix itself) is real and
+    positive for kappa > 0 and increases with kappa towards the Dirichlet spectrum."""
+    n, L = 12, 2.0
+    h = ob.mesh_width(n, "robin", L)
+    np.testing.assert_allclose(ob.fd_matrix_1d(n, h, "robin", 0.0), ob.fd_matrix_1d(n, h, "neumann"))
+    prev = None
+    for kappa in (0.5, 2.0, 8.0):
+        ev = np.sort(np.linalg.eigvals(ob.fd_matrix_1d(n, h, "robin", kappa)).real)
+        _, _, lam = ob.eig_1d(n, h, "robin", kappa)
+        np.testing.assert_allclose(lam, ev, rtol=1e-10)
+        assert lam[0] > 0 and (prev is None or lam[0] > prev)
+        prev = lam[0]
+
+
+@pytest.mark.parametrize("dim,n", [(2, 7), (3, 5)])
+def test_robin_stencil_and_inverse_match_dense(dim, n):
+    kappa, h = 1.7, ob.mesh_width(n, "robin", 2.0)
+    U = I.random_field((n,) * dim, 4)
+    A = ob.dense_operator(n, dim, h, "robin", 0.0, kappa)
+    np.testing.assert_allclose(ob.apply_operator(U, h, "robin", kappa).ravel(), A @ U.ravel(), atol=1e-11 / h ** 2)
+    S, Si, lam = ob.eig_1d(n, h, "robin", kappa)
+    v = qo.fast_diag_solve(U, S, Si, lam, 0.3)
+    np.testing.assert_allclose(v.ravel(), np.linalg.solve(A + 0.3 * np.eye(n ** dim), U.ravel()), rtol=1e-10,
+                               atol=1e-13)
+
+
+def test_robin_face_term_is_not_in_beta():
+    """The Robin face term belongs to A_h: beta_n is the mid-range of 3 b U^2 (+ V) alone, and
+    the quasi-Newton limit solves the discrete system (dense Newton)."""
+    n, kappa = 5, 2.5
+    h = ob.mesh_width(n, "robin", 1.0)
+    f = 20.0 * I.random_field((n, n, n), 6)
+    U, hist, ok = ob.qn_solve(f, h, "robin", lam=0.5, b=3.0, kappa=kappa, tol=1e-13, max_it=2000)
+    assert ok
+    d = 3.0 * 3.0 * np.zeros_like(f)
+    assert hist[0]["beta"] == 0.0 == 0.5 * (d.max() + d.min())
+    A = ob.dense_operator(n, 3, h, "robin", 0.5, kappa)
+    u = np.zeros(f.size)
+    for _ in range(40):
+        F = A @ u + 3.0 * u ** 3 - f.ravel()
+        u = u - np.linalg.solve(A + np.diag(9.0 * u * u), F)
+    np.testing.assert_allclose(U.ravel(), u, atol=1e-11 * np.abs(u).max())
