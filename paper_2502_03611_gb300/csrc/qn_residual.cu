@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "qn_internal.h"
+#include "qn_df.cuh"
 #include "qn_numeric.cuh"
 
 namespace qn {
@@ -98,37 +99,8 @@ __device__ unsigned long long block_max_u64(unsigned long long v) {
 // with one of the two loops (a warp-uniform branch around the whole loop, so
 // neither variant is predicated into the other).
 // KIND 0: lam u + b u^3 (general); 1: lam = 0; 2: lam = 0 and b = 1;
-// 3: (lam + V) u + b u^3 with the separable potential V.
-// f as an unevaluated pair of floats hi + lo (48 significant bits), the form
-// k_residual_tiled reads; |f| >= 2^100 (or inf/nan) marks the copy unusable.
-static __device__ __noinline__ void flag_fbad(int *flag) {
-    if (flag != nullptr) atomicOr(flag, 1);
-}
-
-static __device__ __noinline__ float2 f_pair_slow(double fv) {
-    const float fh = __double2float_rn(fv);
-    return make_float2(fh, __double2float_rn(fv - (double)fh));
-}
-
-// hi = f rounded to FP32, lo = (f - hi) rounded to FP32. The difference is
-// taken exactly on the integer significands (|f| - |hi| has at most 29
-// significant bits), so no FP64 operation is spent; tiny, huge and
-// non-finite f take the FP64 route.
-__device__ __forceinline__ float2 f_pair(double fv, int *flag) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(fv);
-    const int ex = (int)((b >> 52) & 0x7FF);
-    if (ex >= 1023 + 100) flag_fbad(flag);
-    if (ex < 1075 - 126 || ex >= 1023 + 100) return f_pair_slow(fv);
-    const float fh = d2f_rn(fv);
-    const unsigned int fb = __float_as_uint(fh);
-    const int ef = (int)((fb >> 23) & 0xFFu);
-    const long long hu = (long long)((fb & 0x7FFFFFu) | 0x800000u) << (ef - ex + 925);   // 29, or 30 after a carry
-    const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
-    float lo = __fmul_rn(__int2float_rn((int)(m - hu)), __int_as_float((ex - 1075 + 127) << 23));
-    if (b >> 63) lo = -lo;
-    return make_float2(fh, lo);
-}
-
+// 3: (lam + V) u + b u^3 with the separable potential V. The float-pair copy of f
+// that k_residual_tiled reads comes from f_pair (qn_df.cuh).
 struct ResAcc {
     double r2, f2;
     float kr2, kc;
@@ -514,55 +486,7 @@ constexpr int kTX = 64, kTY = 16, kTThreads = 256;
 constexpr int kSRow = 68;                                 // int64 per shared row; x = -1..64 at columns 1..66
 constexpr int kSRows = kTY + 2;
 constexpr int kHaloPerWarp = (2 * kTX + 2 * kTY) / 8;    // 160 halo points, 20 per warp
-constexpr int kFxG = 5;                                   // guard bits below the ulp of exponent E
 static_assert(kTThreads == 8 * 32 && kTY == 2 * 8 && kTX == 2 * 32, "tile / thread mapping");
-
-// Signed fixed-point value of the double with bit pattern b, in units of
-// 2^(E - 1075 - kFxG); `bad` is set when its exponent exceeds E.
-__device__ __forceinline__ long long fx_of(unsigned long long b, int E, unsigned &bad) {
-    const int ex = (int)((unsigned int)(b >> 52) & 0x7FFu);
-    bad |= (unsigned)(ex > E);
-    int sh = E - ex;
-    sh = sh < 0 ? 0 : (sh > 63 ? 63 : sh);
-    const unsigned long long m = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << kFxG;
-    const unsigned long long v = (ex == 0) ? 0ull : (m >> sh);
-    const unsigned long long sg = (unsigned long long)((long long)b >> 63);   // 0 or all ones
-    return (long long)((v ^ sg) - sg);
-}
-
-// Exact int -> float for |c| < 2^22 (the FP32 add of 1.5 * 2^23 trick, read backwards).
-__device__ __forceinline__ float small_i2f(int c) {
-    return __fsub_rn(__int_as_float(0x4B400000 + c), 12582912.0f);
-}
-
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// Fixed-point value v (|v| < 2^62) times the power of two `scale`, as a float pair.
-__device__ __forceinline__ void fx_to_pair(long long v, float scale, float &hi, float &lo) {
-    const int c2 = (int)(v >> 42);                                   // signed, |c2| <= 2^20
-    const int c1 = (int)((unsigned long long)v >> 21) & 0x1FFFFF;
-    const int c0 = (int)v & 0x1FFFFF;
-    const float f2 = __fmaf_rn(__int_as_float(0x4B400000 + c2), 0x1p42f, -0x1.8p65f);   // c2 * 2^42, exact
-    const float f1 = __fmaf_rn(__int_as_float(0x4B400000 + c1), 0x1p21f, -0x1.8p44f);   // c1 * 2^21, exact
-    const float f0 = small_i2f(c0);
-    float s, e;
-    two_sum(f2, f1, s, e);
-    hi = __fmul_rn(s, scale);
-    lo = __fmul_rn(__fadd_rn(e, f0), scale);
-}
-
-// (a + b) for two float pairs, renormalised.
-__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
-    float s, e;
-    two_sum(a.x, b.x, s, e);
-    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
-    const float hi = __fadd_rn(s, e);
-    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
-}
 
 // r = lap/h^2 + lam u + b u^3 - f in float pairs, rounded to FP32. KIND 3:
 // (lh, ll) is the point's lam + V, and d receives 3 b u^2 + V (FP32, V = vf).
