@@ -110,6 +110,8 @@ struct qn_ctx {
     double *eig_r0;       // eigen solves, BF16X3: A_h U + f(U) between the two residual passes
     double *eig_vrow;     // eigen solves with a potential: lam + v_y (+ v_z) per (y, z) row
     float *eig_pot32;     //   and the potential tables in FP32
+    float2 *eig_vrow2;    //   the per-row table and the x table as FP32 pairs (float-pair passes)
+    float2 *eig_potx2;
     int g_kind;           // graph contents: 0 quasi-Newton iterations, 1 eigen iterations
     double lam_min;       // smallest eigenvalue of the 1-D matrix H
     // spectral elements (prob.sem_k > 0): banded H on the device (k_residual_sem)
@@ -235,6 +237,8 @@ static void ctx_free(qn_ctx *c) {
     cudaFree(c->eig_r0);
     cudaFree(c->eig_vrow);
     cudaFree(c->eig_pot32);
+    cudaFree(c->eig_vrow2);
+    cudaFree(c->eig_potx2);
     cudaFree(c->hc0);
     cudaFree(c->hlen);
     cudaFree(c->hval);
@@ -1105,16 +1109,21 @@ extern "C" int qn_profile_read(qn_ctx *c, qn_profile *out) {
 // ---- nonlinear eigenproblem (Sec. 4.4) ----------------------------------------------------------
 // One iteration (qn_eig.cu): pass 1 (A U~ + (lam + V) U~ and the Rayleigh sums), lambda_n and
 // the normalisation factor, pass 2 (U = s U~, F into the inverse's input, beta's extremes), stop
-// test and beta_n, the shifted inverse with the update.
+// test and beta_n, the shifted inverse with the update. In split precision the passes run in
+// float pairs from iteration 1 on (their fixed-point exponent comes from the previous iterate).
 static int enqueue_eig_iteration(qn_ctx *c, double *U, double step, cudaStream_t s) {
     const double hd = pow(c->h, c->dim);
     const int grid = c->nparts;
     const bool fp64 = (c->prob.precision == QN_PREC_FP64);
+    const bool df = !fp64 && c->cur_iter >= 1;
     double *lin = fp64 ? c->w64[1] : c->eig_r0;   // w64[1] is free until the first mode product
+    float2 *lin2 = reinterpret_cast<float2 *>(c->eig_r0);   // the same 8 bytes per node, as a pair
     const bool mirror = !fp64 && c->split;
     long pr = prof_begin(c, PK_RESIDUAL, s);
-    int rc = launch_eig_pass1(U, lin, c->n, c->dim, c->prob.bc, c->inv_h2, c->prob.lam, c->prob.b, c->pot64,
-                              c->eig_vrow, c->partials, grid, c->st, s);
+    int rc = df ? launch_eig_pass1_df(U, lin2, c->n, c->dim, c->prob.bc, c->inv_h2, c->prob.lam, c->prob.b, c->pot64,
+                                      c->eig_vrow, c->eig_potx2, c->eig_vrow2, c->partials, grid, c->st, s)
+                : launch_eig_pass1(U, lin, c->n, c->dim, c->prob.bc, c->inv_h2, c->prob.lam, c->prob.b, c->pot64,
+                                   c->eig_vrow, c->partials, grid, c->st, s);
     prof_end(c, pr, s);
     if (rc) return rc;
     pr = prof_begin(c, PK_FINALIZE, s);
@@ -1122,9 +1131,13 @@ static int enqueue_eig_iteration(qn_ctx *c, double *U, double step, cudaStream_t
     prof_end(c, pr, s);
     if (rc) return rc;
     pr = prof_begin(c, PK_RESIDUAL, s);
-    rc = launch_eig_pass2(U, lin, c->n, c->P, c->dim, c->prob.bc, hd, (float)c->prob.lam, c->prob.b, c->eig_pot32,
-                          fp64 ? c->w64[0] : nullptr, fp64 ? nullptr : c->bhi[0], fp64 ? nullptr : c->blo[0],
-                          mirror, c->partials, grid, c->st, s);
+    if (df)
+        rc = launch_eig_pass2_df(U, lin2, c->n, c->P, c->dim, c->prob.bc, hd, (float)c->prob.lam, c->prob.b,
+                                 c->eig_pot32, c->bhi[0], c->blo[0], mirror, c->partials, grid, c->st, s);
+    else
+        rc = launch_eig_pass2(U, lin, c->n, c->P, c->dim, c->prob.bc, hd, (float)c->prob.lam, c->prob.b,
+                              c->eig_pot32, fp64 ? c->w64[0] : nullptr, fp64 ? nullptr : c->bhi[0],
+                              fp64 ? nullptr : c->blo[0], mirror, c->partials, grid, c->st, s);
     prof_end(c, pr, s);
     if (rc) return rc;
     pr = prof_begin(c, PK_FINALIZE, s);
@@ -1185,6 +1198,19 @@ extern "C" int qn_eig_solve(qn_ctx *c, double *U, const qn_opts *opts, qn_result
         }
         std::vector<float> p32(dn);
         for (int i = 0; i < dn; ++i) p32[i] = (float)pt[i];
+        std::vector<float2> vr2(rows), px2(n);
+        for (size_t r = 0; r < rows; ++r) {
+            const float hi = (float)vr[r];
+            vr2[r] = make_float2(hi, (float)(vr[r] - (double)hi));
+        }
+        for (int i = 0; i < n; ++i) {
+            const float hi = (float)pt[i];
+            px2[i] = make_float2(hi, (float)(pt[i] - (double)hi));
+        }
+        QN_CUDA(cudaMalloc(&c->eig_vrow2, sizeof(float2) * rows));
+        QN_CUDA(cudaMalloc(&c->eig_potx2, sizeof(float2) * n));
+        QN_CUDA(cudaMemcpy(c->eig_vrow2, vr2.data(), sizeof(float2) * rows, cudaMemcpyHostToDevice));
+        QN_CUDA(cudaMemcpy(c->eig_potx2, px2.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
         QN_CUDA(cudaMalloc(&c->eig_vrow, sizeof(double) * rows));
         QN_CUDA(cudaMalloc(&c->eig_pot32, sizeof(float) * dn));
         QN_CUDA(cudaMemcpy(c->eig_vrow, vr.data(), sizeof(double) * rows, cudaMemcpyHostToDevice));
@@ -1199,7 +1225,7 @@ extern "C" int qn_eig_solve(qn_ctx *c, double *U, const qn_opts *opts, qn_result
     int enqueued = 0;
     const bool use_graph = o.graph != 0 && !c->prof_on;
     while (!h.done && enqueued <= o.max_it) {
-        if (use_graph && enqueued + o.sync_every <= o.max_it + 1) {
+        if (use_graph && enqueued >= 1 && enqueued + o.sync_every <= o.max_it + 1) {
             rc = ensure_iteration_graph(c, U, nullptr, o.step, o.sync_every, 1);
             if (rc) return rc;
             QN_CUDA(cudaGraphLaunch(c->gexec, s));

@@ -25,6 +25,7 @@
 // the same as plain launches).
 #include <math.h>
 
+#include "qn_df.cuh"
 #include "qn_internal.h"
 #include "qn_numeric.cuh"
 
@@ -182,9 +183,12 @@ __global__ void __launch_bounds__(256) k_eig_finalize1(const double *partials, i
 template <int DIM, bool NEU>
 __device__ __forceinline__ double eig_point(double *__restrict__ U, const double *__restrict__ lin, long long c,
                                             int x, int y, int z, int n, double sc, double lam_n, float lamf, double b,
-                                            const float *__restrict__ pot32, double &sff, float &dmn, float &dmx) {
+                                            const float *__restrict__ pot32, double &sff, float &dmn, float &dmx,
+                                            unsigned long long &umax) {
     const double u = sc * U[c];
     U[c] = u;
+    const unsigned long long ab = abs_bits(u);
+    umax = ab > umax ? ab : umax;
     const double u2 = u * u;
     const double F = fma(sc, __ldg(lin + c), fma(b * u2, u, -lam_n * u));
     const double w = NEU ? tw<NEU>(x, n) * tw<NEU>(y, n) * ((DIM == 3) ? tw<NEU>(z, n) : 1.0) : 1.0;
@@ -210,11 +214,13 @@ __global__ void __launch_bounds__(256) k_eig_pass2(double *__restrict__ U, const
                                                    int P, double hd, float lam, double b,
                                                    const float *__restrict__ pot, double *__restrict__ R64,
                                                    __nv_bfloat16 *__restrict__ Rhi, __nv_bfloat16 *__restrict__ Rlo,
-                                                   double *__restrict__ partials, const DevState *st) {
+                                                   double *__restrict__ partials, const DevState *st,
+                                                   unsigned long long *umax_out) {
     if (state_done(st)) return;
     const double sc = st->eig_scale, lam_n = st->eig_lambda;
     double sff = 0.0;
     float dmn = INFINITY, dmx = -INFINITY;
+    unsigned long long umax = 0ull;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (OUT == 0) {
@@ -222,7 +228,7 @@ __global__ void __launch_bounds__(256) k_eig_pass2(double *__restrict__ U, const
         for (long long c = t0; c < N; c += stride) {
             int x, y, z;
             node_xyz<DIM>(c, n, x, y, z);
-            R64[c] = eig_point<DIM, NEU>(U, lin, c, x, y, z, n, sc, lam_n, lam, b, pot, sff, dmn, dmx);
+            R64[c] = eig_point<DIM, NEU>(U, lin, c, x, y, z, n, sc, lam_n, lam, b, pot, sff, dmn, dmx, umax);
         }
     } else if (OUT == 1) {
         const long long NP = (DIM == 3) ? (long long)P * P * P : (long long)P * P;
@@ -234,7 +240,7 @@ __global__ void __launch_bounds__(256) k_eig_pass2(double *__restrict__ U, const
             float f = 0.0f;
             if (x < n && y < n && z < n) {
                 const long long c = ((long long)z * n + y) * n + x;
-                f = d2f_rn(eig_point<DIM, NEU>(U, lin, c, x, y, z, n, sc, lam_n, lam, b, pot, sff, dmn, dmx));
+                f = d2f_rn(eig_point<DIM, NEU>(U, lin, c, x, y, z, n, sc, lam_n, lam, b, pot, sff, dmn, dmx, umax));
             }
             const __nv_bfloat16 hi = __float2bfloat16_rn(f);
             Rhi[o] = hi;
@@ -254,11 +260,11 @@ __global__ void __launch_bounds__(256) k_eig_pass2(double *__restrict__ U, const
                 const int y = (ry & 1) ? n - 1 - (ry >> 1) : (ry >> 1);
                 const int z = (rz & 1) ? n - 1 - (rz >> 1) : (rz >> 1);
                 const long long cb = ((long long)z * n + y) * n;
-                fa = d2f_rn(eig_point<DIM, NEU>(U, lin, cb + i, i, y, z, n, sc, lam_n, lam, b, pot, sff, dmn, dmx));
+                fa = d2f_rn(eig_point<DIM, NEU>(U, lin, cb + i, i, y, z, n, sc, lam_n, lam, b, pot, sff, dmn, dmx, umax));
                 if (i < nanti) {
                     const int j = n - 1 - i;
                     const float f2 =
-                        d2f_rn(eig_point<DIM, NEU>(U, lin, cb + j, j, y, z, n, sc, lam_n, lam, b, pot, sff, dmn, dmx));
+                        d2f_rn(eig_point<DIM, NEU>(U, lin, cb + j, j, y, z, n, sc, lam_n, lam, b, pot, sff, dmn, dmx, umax));
                     fb = __fsub_rn(fa, f2);
                     fa = __fadd_rn(fa, f2);
                 }
@@ -274,6 +280,256 @@ __global__ void __launch_bounds__(256) k_eig_pass2(double *__restrict__ U, const
     Sum4 acc{hd * sff, 0.0, (double)dmn, (double)dmx};
     acc = block_sum4(acc);
     if (threadIdx.x == 0) {
+        double *p = partials + 4ll * blockIdx.x;
+        p[0] = acc.a;
+        p[1] = 0.0;
+        p[2] = acc.mn;
+        p[3] = acc.mx;
+    }
+    if (umax_out != nullptr) {   // max|U| of the normalised iterate (fixed-point exponent of the next pass 1)
+        unsigned long long m = umax;
+        __shared__ unsigned long long shm2[8];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+            m = v > m ? v : m;
+        }
+        if ((threadIdx.x & 31) == 0) shm2[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = shm2[i] > m ? shm2[i] : m;
+            atomicMax(umax_out, m);
+        }
+    }
+}
+
+// ---- float-pair forms of the two passes (iterations >= 1) ------------------------------------
+// The same arithmetic with no FP64 operation per node in pass 1 and one (U = s U~) in
+// pass 2: the stencil 2 DIM u - sum(nb) is an exact int64 sum of fixed-point values in units
+// of 2^(E - 1075 - kFxG), E from max|U| of the previous iterate (DevState::fx_e, set by the
+// stop-test finaliser from pass 2's block maxima); everything else is in float pairs
+// (~48 significant bits). A node whose stencil reads a value beyond E takes the FP64 path.
+
+// a * b for float pairs, renormalised.
+__device__ __forceinline__ float2 pair_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    const float hi = __fadd_rn(p, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, p)));
+}
+
+__device__ __forceinline__ float2 pair_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ double pair_to_double(float2 a) { return (double)a.x + (double)a.y; }
+
+// FP64 path of one pass-1 node (values beyond the fixed-point range): lin and u as pairs.
+template <int DIM, bool NEU>
+static __device__ __noinline__ float2 pass1_node_exact(const double *U, long long c, int x, int y, int z, int n,
+                                                       double inv_h2, double cv, float2 &up) {
+    const long long nn = (long long)n * n;
+    const double u = U[c];
+    double nbv[2 * DIM];
+    nbv[0] = (x > 0) ? U[c - 1] : (NEU ? U[c + 1] : 0.0);
+    nbv[1] = (x < n - 1) ? U[c + 1] : (NEU ? U[c - 1] : 0.0);
+    nbv[2] = (y > 0) ? U[c - n] : (NEU ? U[c + n] : 0.0);
+    nbv[3] = (y < n - 1) ? U[c + n] : (NEU ? U[c - n] : 0.0);
+    if (DIM == 3) {
+        nbv[4] = (z > 0) ? U[c - nn] : (NEU ? U[c + nn] : 0.0);
+        nbv[5] = (z < n - 1) ? U[c + nn] : (NEU ? U[c - nn] : 0.0);
+    }
+    const double lv = fma(stencil_fixed<DIM>(u, nbv), inv_h2, cv * u);
+    up = f_pair_slow(u);
+    return f_pair_slow(lv);
+}
+
+// vrow2 / pot2: lam + v_y (+ v_z) per row and v_x per column as float pairs (nullptr: no
+// potential, the coefficient is lam2).
+template <int DIM, bool NEU>
+__global__ void __launch_bounds__(256) k_eig_pass1_df(const double *__restrict__ U, float2 *__restrict__ lin, int n,
+                                                      double inv_h2, double lam, float2 lam2, double b,
+                                                      const double *__restrict__ pot, const double *__restrict__ vrow,
+                                                      const float2 *__restrict__ pot2, const float2 *__restrict__ vrow2,
+                                                      double *__restrict__ partials, const DevState *st) {
+    if (state_done(st)) return;
+    const int E = st->fx_e;
+    const float scale = __int_as_float(E != 0 ? ((E - 1075 - kFxG + 127) << 23) : 0);
+    const float ih = __double2float_rn(inv_h2), il = __double2float_rn(inv_h2 - (double)ih);
+    const float2 ih2 = make_float2(ih, il);
+    const unsigned long long *Ub = reinterpret_cast<const unsigned long long *>(U);
+    const long long nn = (long long)n * n;
+    const long long N = (DIM == 3) ? nn * n : nn;
+    float2 e1 = make_float2(0.f, 0.f), e4 = e1, q = e1;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += stride) {
+        const long long row = c / n;
+        const int x = (int)(c - row * n);
+        const int y = (DIM == 3) ? (int)(row % n) : (int)row;
+        const int z = (DIM == 3) ? (int)(row / n) : 0;
+        unsigned long long bn[2 * DIM];
+        const unsigned long long bu = __ldg(Ub + c);
+        bn[0] = (x > 0) ? __ldg(Ub + c - 1) : (NEU ? __ldg(Ub + c + 1) : 0ull);
+        bn[1] = (x < n - 1) ? __ldg(Ub + c + 1) : (NEU ? __ldg(Ub + c - 1) : 0ull);
+        bn[2] = (y > 0) ? __ldg(Ub + c - n) : (NEU ? __ldg(Ub + c + n) : 0ull);
+        bn[3] = (y < n - 1) ? __ldg(Ub + c + n) : (NEU ? __ldg(Ub + c - n) : 0ull);
+        if (DIM == 3) {
+            bn[4] = (z > 0) ? __ldg(Ub + c - nn) : (NEU ? __ldg(Ub + c + nn) : 0ull);
+            bn[5] = (z < n - 1) ? __ldg(Ub + c + nn) : (NEU ? __ldg(Ub + c - nn) : 0ull);
+        }
+        unsigned bad = (E == 0) ? 1u : 0u;
+        const long long fu = fx_of(bu, E, bad);
+        unsigned long long snb = 0ull;
+#pragma unroll
+        for (int i = 0; i < 2 * DIM; ++i) snb += (unsigned long long)fx_of(bn[i], E, bad);
+        float2 lv, up;
+        if (!bad) {
+            const long long lapfx = (long long)((unsigned long long)(2 * DIM) * (unsigned long long)fu - snb);
+            float lh, ll, uh, ul;
+            fx_to_pair(lapfx, scale, lh, ll);
+            fx_to_pair(fu, scale, uh, ul);
+            up = make_float2(uh, ul);
+            const float2 cv = (pot != nullptr) ? pair_add(__ldg(vrow2 + row), __ldg(pot2 + x)) : lam2;
+            lv = pair_add(pair_mul(make_float2(lh, ll), ih2), pair_mul(cv, up));
+        } else {
+            const double cv = (pot != nullptr) ? __ldg(vrow + row) + __ldg(pot + x) : lam;
+            lv = pass1_node_exact<DIM, NEU>(U, c, x, y, z, n, inv_h2, cv, up);
+        }
+        lin[c] = lv;
+        float2 wu = up;
+        if (NEU) {   // trapezoid weights are powers of two: exact on both halves
+            const float w = (float)(tw<NEU>(x, n) * tw<NEU>(y, n) * ((DIM == 3) ? tw<NEU>(z, n) : 1.0));
+            wu = make_float2(wu.x * w, wu.y * w);
+        }
+        const float2 wu2 = pair_mul(wu, up);
+        e1 = pair_add(e1, pair_mul(wu, lv));
+        e4 = pair_add(e4, pair_mul(wu2, pair_mul(up, up)));
+        q = pair_add(q, wu2);
+    }
+    Sum4 acc{pair_to_double(e1), pair_to_double(e4), pair_to_double(q), 0.0};
+    acc = block_sum3(acc);
+    if (threadIdx.x == 0) {
+        double *p = partials + 4ll * blockIdx.x;
+        p[0] = acc.a;
+        p[1] = b * acc.b;
+        p[2] = acc.mn;
+        p[3] = 0.0;
+    }
+}
+
+// One node of pass 2 in float pairs; U = s U~ written back (the one FP64 multiply).
+template <int DIM, bool NEU>
+__device__ __forceinline__ float eig_point_df(double *__restrict__ U, const float2 *__restrict__ lin, long long c,
+                                              int x, int y, int z, int n, double sc, float2 sc2, float2 lamn2,
+                                              float2 b2, float lamf, float b3f, const float *__restrict__ pot32,
+                                              float &sk, float &kc, float &dmn, float &dmx,
+                                              unsigned long long &umax) {
+    const double u = sc * U[c];
+    U[c] = u;
+    const unsigned long long ab = abs_bits(u);
+    umax = ab > umax ? ab : umax;
+    const float2 up = f_pair(u, nullptr);
+    const float2 u2 = pair_mul(up, up);
+    const float2 bu3 = pair_mul(b2, pair_mul(u2, up));
+    const float2 F = pair_add(pair_add(pair_mul(sc2, __ldg(lin + c)), bu3), pair_neg(pair_mul(lamn2, up)));
+    const float Ff = __fadd_rn(F.x, F.y);
+    float wF = Ff;
+    if (NEU) wF = Ff * (float)(tw<NEU>(x, n) * tw<NEU>(y, n) * ((DIM == 3) ? tw<NEU>(z, n) : 1.0));
+    const float yk = __fsub_rn(__fmul_rn(wF, Ff), kc);   // Kahan sum of w F^2
+    const float tk = __fadd_rn(sk, yk);
+    kc = __fsub_rn(__fsub_rn(tk, sk), yk);
+    sk = tk;
+    float cv = lamf;
+    if (pot32 != nullptr) {
+        cv += __ldg(pot32 + x) + __ldg(pot32 + n + y);
+        if (DIM == 3) cv += __ldg(pot32 + 2 * n + z);
+    }
+    const float d = __fmaf_rn(b3f, u2.x, cv);
+    dmn = fminf(dmn, d);
+    dmx = fmaxf(dmx, d);
+    return Ff;
+}
+
+__device__ __forceinline__ float2 pair_of(double v) {
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
+template <int DIM, int OUT, bool NEU>
+__global__ void __launch_bounds__(256) k_eig_pass2_df(double *__restrict__ U, const float2 *__restrict__ lin, int n,
+                                                      int P, double hd, float lamf, double b,
+                                                      const float *__restrict__ pot32, __nv_bfloat16 *__restrict__ Rhi,
+                                                      __nv_bfloat16 *__restrict__ Rlo, double *__restrict__ partials,
+                                                      DevState *st) {
+    if (state_done(st)) return;
+    const double sc = st->eig_scale;
+    const float2 sc2 = pair_of(sc), lamn2 = pair_of(st->eig_lambda), b2 = pair_of(b);
+    const float b3f = (float)(3.0 * b);
+    float sk = 0.0f, kc = 0.0f, dmn = INFINITY, dmx = -INFINITY;
+    unsigned long long umax = 0ull;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (OUT == 1) {
+        const long long NP = (DIM == 3) ? (long long)P * P * P : (long long)P * P;
+        for (long long o = t0; o < NP; o += stride) {
+            const long long r = o / P;
+            const int x = (int)(o - r * P);
+            const int y = (DIM == 3) ? (int)(r % P) : (int)r;
+            const int z = (DIM == 3) ? (int)(r / P) : 0;
+            float f = 0.0f;
+            if (x < n && y < n && z < n) {
+                const long long c = ((long long)z * n + y) * n + x;
+                f = eig_point_df<DIM, NEU>(U, lin, c, x, y, z, n, sc, sc2, lamn2, b2, lamf, b3f, pot32, sk, kc, dmn,
+                                           dmx, umax);
+            }
+            const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+            Rhi[o] = hi;
+            Rlo[o] = __float2bfloat16_rn(f - __bfloat162float(hi));
+        }
+    } else {
+        const int H = P / 2, nsym = (n + 1) / 2, nanti = n / 2;
+        const long long items = (long long)P * P * H;
+        for (long long t = t0; t < items; t += stride) {
+            const long long row = t / H;
+            const int i = (int)(t - row * H);
+            const int ry = (int)(row % P), rz = (int)(row / P);
+            float fa = 0.0f, fb = 0.0f;
+            if (ry < n && rz < n && i < nsym) {
+                const int y = (ry & 1) ? n - 1 - (ry >> 1) : (ry >> 1);
+                const int z = (rz & 1) ? n - 1 - (rz >> 1) : (rz >> 1);
+                const long long cb = ((long long)z * n + y) * n;
+                fa = eig_point_df<DIM, NEU>(U, lin, cb + i, i, y, z, n, sc, sc2, lamn2, b2, lamf, b3f, pot32, sk, kc,
+                                            dmn, dmx, umax);
+                if (i < nanti) {
+                    const int j = n - 1 - i;
+                    const float f2 = eig_point_df<DIM, NEU>(U, lin, cb + j, j, y, z, n, sc, sc2, lamn2, b2, lamf, b3f,
+                                                            pot32, sk, kc, dmn, dmx, umax);
+                    fb = __fsub_rn(fa, f2);
+                    fa = __fadd_rn(fa, f2);
+                }
+            }
+            const long long o = row * P + i;
+            const __nv_bfloat16 ha = __float2bfloat16_rn(fa), hb = __float2bfloat16_rn(fb);
+            Rhi[o] = ha;
+            Rlo[o] = __float2bfloat16_rn(fa - __bfloat162float(ha));
+            Rhi[o + H] = hb;
+            Rlo[o + H] = __float2bfloat16_rn(fb - __bfloat162float(hb));
+        }
+    }
+    // max|U| of the iterate for the next pass 1's fixed-point exponent
+    __shared__ unsigned long long shm[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, umax, o);
+        umax = v > umax ? v : umax;
+    }
+    if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = umax;
+    Sum4 acc{hd * ((double)sk - (double)kc), 0.0, (double)dmn, (double)dmx};
+    acc = block_sum4(acc);   // (its __syncthreads also orders shm)
+    if (threadIdx.x == 0) {
+        unsigned long long m = 0ull;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = shm[i] > m ? shm[i] : m;
+        atomicMax(&st->umax_scan, m);
         double *p = partials + 4ll * blockIdx.x;
         p[0] = acc.a;
         p[1] = 0.0;
@@ -321,9 +577,11 @@ static void pass2_t(double *U, const double *lin, int n, int P, bool neu, double
                     const float *pot, double *R64, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, double *partials,
                     int grid, const DevState *st, cudaStream_t s) {
     if (neu)
-        k_eig_pass2<DIM, OUT, true><<<grid, 256, 0, s>>>(U, lin, n, P, hd, lam, b, pot, R64, Rhi, Rlo, partials, st);
+        k_eig_pass2<DIM, OUT, true><<<grid, 256, 0, s>>>(U, lin, n, P, hd, lam, b, pot, R64, Rhi, Rlo, partials, st,
+                                                          &const_cast<DevState *>(st)->umax_scan);
     else
-        k_eig_pass2<DIM, OUT, false><<<grid, 256, 0, s>>>(U, lin, n, P, hd, lam, b, pot, R64, Rhi, Rlo, partials, st);
+        k_eig_pass2<DIM, OUT, false><<<grid, 256, 0, s>>>(U, lin, n, P, hd, lam, b, pot, R64, Rhi, Rlo, partials, st,
+                                                           &const_cast<DevState *>(st)->umax_scan);
 }
 
 int launch_eig_pass2(double *U, const double *lin, int n, int P, int dim, int bc, double hd, float lam, double b,
@@ -345,6 +603,65 @@ int launch_eig_pass2(double *U, const double *lin, int n, int P, int dim, int bc
         pass2_t<3, 1>(U, lin, n, P, neu, hd, lam, b, pot, R64, Rhi, Rlo, partials, grid, st, s);
     } else {
         pass2_t<2, 1>(U, lin, n, P, neu, hd, lam, b, pot, R64, Rhi, Rlo, partials, grid, st, s);
+    }
+    QN_CUDA(cudaGetLastError());
+    return QN_OK;
+}
+
+template <int DIM>
+static void pass1_df_dim(const double *U, float2 *lin, int n, bool neu, double inv_h2, double lam, double b,
+                         const double *pot, const double *vrow, const float2 *pot2, const float2 *vrow2,
+                         double *partials, int grid, const DevState *st, cudaStream_t s) {
+    const float lh = (float)lam;
+    const float2 lam2 = make_float2(lh, (float)(lam - (double)lh));
+    if (neu)
+        k_eig_pass1_df<DIM, true><<<grid, 256, 0, s>>>(U, lin, n, inv_h2, lam, lam2, b, pot, vrow, pot2, vrow2,
+                                                       partials, st);
+    else
+        k_eig_pass1_df<DIM, false><<<grid, 256, 0, s>>>(U, lin, n, inv_h2, lam, lam2, b, pot, vrow, pot2, vrow2,
+                                                        partials, st);
+}
+
+int launch_eig_pass1_df(const double *U, float2 *lin, int n, int dim, int bc, double inv_h2, double lam, double b,
+                        const double *pot, const double *vrow, const float2 *pot2, const float2 *vrow2,
+                        double *partials, int grid, const DevState *st, cudaStream_t s) {
+    if (pot != nullptr && (vrow == nullptr || pot2 == nullptr || vrow2 == nullptr)) {
+        set_error("launch_eig_pass1_df: a potential needs its per-row and float-pair tables");
+        return QN_EINVAL;
+    }
+    const bool neu = (bc == QN_BC_NEUMANN);
+    if (dim == 3)
+        pass1_df_dim<3>(U, lin, n, neu, inv_h2, lam, b, pot, vrow, pot2, vrow2, partials, grid, st, s);
+    else
+        pass1_df_dim<2>(U, lin, n, neu, inv_h2, lam, b, pot, vrow, pot2, vrow2, partials, grid, st, s);
+    QN_CUDA(cudaGetLastError());
+    return QN_OK;
+}
+
+template <int DIM, int OUT>
+static void pass2_df_t(double *U, const float2 *lin, int n, int P, bool neu, double hd, float lam, double b,
+                       const float *pot32, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, double *partials, int grid,
+                       DevState *st, cudaStream_t s) {
+    if (neu)
+        k_eig_pass2_df<DIM, OUT, true><<<grid, 256, 0, s>>>(U, lin, n, P, hd, lam, b, pot32, Rhi, Rlo, partials, st);
+    else
+        k_eig_pass2_df<DIM, OUT, false><<<grid, 256, 0, s>>>(U, lin, n, P, hd, lam, b, pot32, Rhi, Rlo, partials, st);
+}
+
+int launch_eig_pass2_df(double *U, const float2 *lin, int n, int P, int dim, int bc, double hd, float lam, double b,
+                        const float *pot32, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, bool mirror, double *partials,
+                        int grid, DevState *st, cudaStream_t s) {
+    const bool neu = (bc == QN_BC_NEUMANN);
+    if (mirror) {
+        if (dim != 3 || P % 128 != 0) {
+            set_error("launch_eig_pass2_df: the reflection-split layout needs 3-D and P a multiple of 128");
+            return QN_EINVAL;
+        }
+        pass2_df_t<3, 2>(U, lin, n, P, neu, hd, lam, b, pot32, Rhi, Rlo, partials, grid, st, s);
+    } else if (dim == 3) {
+        pass2_df_t<3, 1>(U, lin, n, P, neu, hd, lam, b, pot32, Rhi, Rlo, partials, grid, st, s);
+    } else {
+        pass2_df_t<2, 1>(U, lin, n, P, neu, hd, lam, b, pot32, Rhi, Rlo, partials, grid, st, s);
     }
     QN_CUDA(cudaGetLastError());
     return QN_OK;

@@ -430,10 +430,10 @@ __global__ void __launch_bounds__(256) k_finalize(const double *partials, int np
     // exponent for the fixed-point stencil of the next residual, from max|U|
     // of this iterate (sqrt of max U^2 has at least max|U|'s exponent: the
     // rounding of u^2 can only carry it up)
-    if (pot) {
+    if (pot || eig) {   // max|U| gathered by the residual passes (atomicMax of bit patterns)
         st->fx_e = fx_exponent(st->umax_scan, st);
         st->umax_scan = 0ull;
-    } else if (!eig) {
+    } else {
         st->fx_e = (acc.mx < INFINITY) ? fx_exponent((unsigned long long)__double_as_longlong(sqrt(acc.mx)), st) : 0;
     }
     st->beta = beta;
