@@ -361,12 +361,15 @@ __global__ void __launch_bounds__(256) k_eig_pass1_df(const double *__restrict__
     const long long nn = (long long)n * n;
     const long long N = (DIM == 3) ? nn * n : nn;
     float2 e1 = make_float2(0.f, 0.f), e4 = e1, q = e1;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += stride) {
-        const long long row = c / n;
-        const int x = (int)(c - row * n);
-        const int y = (DIM == 3) ? (int)(row % n) : (int)row;
-        const int z = (DIM == 3) ? (int)(row / n) : 0;
+    // one warp per (y, z) row, lanes along x (one division per row, none per node)
+    const int lane = threadIdx.x & 31;
+    const int rows = (int)(N / n);
+    const int wstride = gridDim.x * (blockDim.x >> 5);
+    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
+      const int y = (DIM == 3) ? row % n : row;
+      const int z = (DIM == 3) ? row / n : 0;
+      for (int x = lane; x < n; x += 32) {
+        const long long c = (long long)row * n + x;
         unsigned long long bn[2 * DIM];
         const unsigned long long bu = __ldg(Ub + c);
         bn[0] = (x > 0) ? __ldg(Ub + c - 1) : (NEU ? __ldg(Ub + c + 1) : 0ull);
@@ -405,6 +408,7 @@ __global__ void __launch_bounds__(256) k_eig_pass1_df(const double *__restrict__
         e1 = pair_add(e1, pair_mul(wu, lv));
         e4 = pair_add(e4, pair_mul(wu2, pair_mul(up, up)));
         q = pair_add(q, wu2);
+      }
     }
     Sum4 acc{pair_to_double(e1), pair_to_double(e4), pair_to_double(q), 0.0};
     acc = block_sum3(acc);
@@ -467,15 +471,17 @@ __global__ void __launch_bounds__(256) k_eig_pass2_df(double *__restrict__ U, co
     const float b3f = (float)(3.0 * b);
     float sk = 0.0f, kc = 0.0f, dmn = INFINITY, dmx = -INFINITY;
     unsigned long long umax = 0ull;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // one warp per output row of the padded planes, lanes along its x axis
+    const int lane = threadIdx.x & 31;
+    const int wstride = gridDim.x * (blockDim.x >> 5);
+    const int w0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (OUT == 1) {
-        const long long NP = (DIM == 3) ? (long long)P * P * P : (long long)P * P;
-        for (long long o = t0; o < NP; o += stride) {
-            const long long r = o / P;
-            const int x = (int)(o - r * P);
-            const int y = (DIM == 3) ? (int)(r % P) : (int)r;
-            const int z = (DIM == 3) ? (int)(r / P) : 0;
+        const int rows = (DIM == 3) ? P * P : P;
+        for (int r = w0; r < rows; r += wstride) {
+          const int y = (DIM == 3) ? r % P : r;
+          const int z = (DIM == 3) ? r / P : 0;
+          for (int x = lane; x < P; x += 32) {
+            const long long o = (long long)r * P + x;
             float f = 0.0f;
             if (x < n && y < n && z < n) {
                 const long long c = ((long long)z * n + y) * n + x;
@@ -485,14 +491,13 @@ __global__ void __launch_bounds__(256) k_eig_pass2_df(double *__restrict__ U, co
             const __nv_bfloat16 hi = __float2bfloat16_rn(f);
             Rhi[o] = hi;
             Rlo[o] = __float2bfloat16_rn(f - __bfloat162float(hi));
+          }
         }
     } else {
         const int H = P / 2, nsym = (n + 1) / 2, nanti = n / 2;
-        const long long items = (long long)P * P * H;
-        for (long long t = t0; t < items; t += stride) {
-            const long long row = t / H;
-            const int i = (int)(t - row * H);
-            const int ry = (int)(row % P), rz = (int)(row / P);
+        for (int row = w0; row < P * P; row += wstride) {
+          const int ry = row % P, rz = row / P;
+          for (int i = lane; i < H; i += 32) {
             float fa = 0.0f, fb = 0.0f;
             if (ry < n && rz < n && i < nsym) {
                 const int y = (ry & 1) ? n - 1 - (ry >> 1) : (ry >> 1);
@@ -508,12 +513,13 @@ __global__ void __launch_bounds__(256) k_eig_pass2_df(double *__restrict__ U, co
                     fa = __fadd_rn(fa, f2);
                 }
             }
-            const long long o = row * P + i;
+            const long long o = (long long)row * P + i;
             const __nv_bfloat16 ha = __float2bfloat16_rn(fa), hb = __float2bfloat16_rn(fb);
             Rhi[o] = ha;
             Rlo[o] = __float2bfloat16_rn(fa - __bfloat162float(ha));
             Rhi[o + H] = hb;
             Rlo[o + H] = __float2bfloat16_rn(fb - __bfloat162float(hb));
+          }
         }
     }
     // max|U| of the iterate for the next pass 1's fixed-point exponent
