@@ -849,6 +849,33 @@ def main():
                           f"(oracle count at {small})")}
 
     if rank == 0 and sem:
+        # the SEM residual is bound by the FP64 pipe: algorithmic FP64 FLOP per launch = per node
+        # 2 x (band entries of H along each axis) + 9 for the nonlinear term and the norm, against
+        # a cuBLAS DGEMM measured here (no FP64 peak is in MEASURED_PEAKS)
+        Hm = qn.qn_setup_1d_sem(n, a.sem_k, 1.0, qn.QN_BC_DIRICHLET)[0]
+        avg_nnz = float(np.count_nonzero(Hm)) / n
+        flops_res = N * (2.0 * 3 * avg_nnz + 9.0)
+        res_ms = prof["residual_ms"] / max(prof["residual_launches"], 1)
+        A = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+        B = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            A @ B
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        g0.record(stream)
+        for _ in range(5):
+            A @ B
+        g1.record(stream)
+        torch.cuda.synchronize()
+        dgemm = 5 * 2 * 4096.0 ** 3 / (g0.elapsed_time(g1) * 1e-3) / 1e12
+        del A, B
+        ach = flops_res / (res_ms * 1e-3) / 1e12
+        roofline = {"kernel": "k_residual_sem", "bound": "fp64", "achieved": round(ach, 4), "peak": round(dgemm, 4),
+                    "unit": "TFLOP/s", "frac": round(ach / dgemm, 4), "traffic": None,
+                    "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (FP64 pipe)",
+                    "flops_per_launch_algorithmic": flops_res, "band_entries_per_row": round(avg_nnz, 3),
+                    "avg_launch_ms": round(res_ms, 4), "launches": prof["residual_launches"]}
         line = {
             "metric": "time to rel. residual 1e-10, 3-D Q^k spectral elements at n^3 nodes", "value": round(ms_max, 3),
             "unit": "ms", "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_max, 3),
