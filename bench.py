@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dirichlet", choices=["dirichlet", "ex1", "ex2", "sem"])
+    ap.add_argument("--workload", default="dirichlet", choices=["dirichlet", "ex1", "ex2", "sem", "batched"])
     ap.add_argument("--sem-k", type=int, default=4, help="element degree of --workload sem")
     ap.add_argument("--n", type=int, default=None, help="nodes per axis (default 511, ex1: 200)")
     ap.add_argument("--seed", type=int, default=0)
@@ -552,6 +552,26 @@ def main_ex2(a):
         dist.destroy_process_group()
 
 
+def main_batched(a):
+    """--workload batched: the 256 coupled 2-D systems alone (the same measurement the default
+    line carries under "batched"), one JSON line."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2502_03611_gb300 import qn
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    b = run_batched(qn, seed=a.seed, reps=max(a.steps, 1))
+    clocks = sampler.stop()
+    line = {"metric": "instances/s, 256 coupled 2-D systems to rel. residual 1e-10", "value": b["instances_per_s"],
+            "unit": "instances/s", "n_gpus": 1, "steps": b["steps"], "warmup": 2, "ms_per_step": b["ms_per_batch"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f64",
+            "data": "synthetic (manufactured pairs, seed-drawn sizes and coefficients)",
+            "config": {"workload": b["workload"]}, "batched": b, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -559,6 +579,9 @@ def main():
         return
     if a.workload == "ex2":
         main_ex2(a)
+        return
+    if a.workload == "batched":
+        main_batched(a)
         return
     import numpy as np
     import torch
