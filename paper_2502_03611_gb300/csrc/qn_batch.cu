@@ -11,7 +11,8 @@
 //
 // One iteration of ALL instances is six launches:
 //   k_sys_residual   work items (instance, 8 rows) of every active instance:
-//                    both residuals (FP64, fixed-point stencil), their BF16
+//                    both residuals (iteration 0 in FP64, later ones on an
+//                    exact fixed-point stencil in float pairs), their BF16
 //                    hi/lo planes, and partial sums / eigenvalue extremes
 //   k_sys_finalize   one block per instance: norms, beta, stop test, and the
 //                    device time at which the instance converged
@@ -29,6 +30,7 @@
 #include <new>
 #include <vector>
 
+#include "qn_df.cuh"
 #include "qn_internal.h"
 #include "qn_numeric.cuh"
 #include "qn_ptx.cuh"
@@ -41,14 +43,19 @@ constexpr int kRowsPerItem = 8;
 struct SysInst {
     double *U, *V;
     const double *f1, *f2;
+    float2 *f1p, *f2p;                               // float-pair copies of f1, f2 (written on iteration 0)
     __nv_bfloat16 *ru_hi, *ru_lo, *rv_hi, *rv_lo;   // buffer 0 planes of both components
     double alpha, D, inv_h2;
+    float2 ih2, dh2, al2;                            // inv_h2, D inv_h2, alpha as float pairs
     int n, P, item_begin, item_count;
+    int df_ok;   // the coefficients are within the float-pair range (|alpha|, D inv_h2 < 2^60)
 };
 
 struct SysState {
     int done, status, it;
     int r2_exp;   // k: from the second iteration on, sum r^2 adds (float(r) 2^-k)^2 in FP32 (2^k ~ RMS(f))
+    int df;       // iterations >= 1 may take the fixed-point / float-pair residual
+    int fbad;     // |f| beyond the float-pair range somewhere
     double beta, f_norm, rel, res;
     unsigned long long t_done;
 };
@@ -113,6 +120,24 @@ __global__ void k_sys_init(SysState *st, int count, SysCtl *ctl, double tol, int
     }
 }
 
+// Eigenvalues of [[3u^2, alpha], [-alpha, 3v^2]] (real parts), FP32: running extremes.
+__device__ __forceinline__ void sys_extremes(float uf, float vf, float alpha_f, float &mxp, float &mnm) {
+    const float a = 3.0f * uf * uf, d = 3.0f * vf * vf;
+    const float disc = (a - d) * (a - d) - 4.0f * alpha_f * alpha_f;
+    const float sq = disc > 0.0f ? sqrtf(disc) : 0.0f;
+    mxp = fmaxf(mxp, 0.5f * (a + d + sq));
+    mnm = fminf(mnm, 0.5f * (a + d - sq));
+}
+
+// Kahan sum of (F_u 2^-k)^2 + (F_v 2^-k)^2 in FP32.
+__device__ __forceinline__ void sys_r2(float Fuf, float Fvf, float r2s, float &kr2, float &kc) {
+    const float fu = __fmul_rn(Fuf, r2s), fv = __fmul_rn(Fvf, r2s);
+    const float yk = fmaf(fu, fu, fmaf(fv, fv, -kc));
+    const float tk = kr2 + yk;
+    kc = (tk - kr2) - yk;
+    kr2 = tk;
+}
+
 // sum f^2 and r^2 in FP64 (first iteration only; out of line so that the FP64
 // operations are not predicated into every later iteration's loop)
 static __device__ __noinline__ double2 first_iteration_sums(double2 acc, double g1, double g2, double Fu,
@@ -120,73 +145,231 @@ static __device__ __noinline__ double2 first_iteration_sums(double2 acc, double 
     return make_double2(fma(g1, g1, fma(g2, g2, acc.x)), fma(Fu, Fu, fma(Fv, Fv, acc.y)));
 }
 
-__global__ void __launch_bounds__(256) k_sys_residual(const SysInst *__restrict__ inst,
-                                                      const SysItem *__restrict__ items,
-                                                      const SysState *__restrict__ st,
+// Both residuals of one node in FP64 (fixed-point stencil, exact up to its final rounding).
+__device__ __forceinline__ void sys_node_fp64(const double *__restrict__ U, const double *__restrict__ V,
+                                              const double *__restrict__ f1, const double *__restrict__ f2, int c,
+                                              int x, int y, int n, double alpha, double inv_h2, double Dh2,
+                                              double &u, double &v, double &g1, double &g2, double &Fu, double &Fv) {
+    u = __ldg(U + c);
+    v = __ldg(V + c);
+    double nu[4], nv[4];
+    nu[0] = x > 0 ? __ldg(U + c - 1) : 0.0;
+    nu[1] = x < n - 1 ? __ldg(U + c + 1) : 0.0;
+    nu[2] = y > 0 ? __ldg(U + c - n) : 0.0;
+    nu[3] = y < n - 1 ? __ldg(U + c + n) : 0.0;
+    nv[0] = x > 0 ? __ldg(V + c - 1) : 0.0;
+    nv[1] = x < n - 1 ? __ldg(V + c + 1) : 0.0;
+    nv[2] = y > 0 ? __ldg(V + c - n) : 0.0;
+    nv[3] = y < n - 1 ? __ldg(V + c + n) : 0.0;
+    g1 = __ldg(f1 + c);
+    g2 = __ldg(f2 + c);
+    const double lu = stencil_fixed<2>(u, nu);
+    const double lv = stencil_fixed<2>(v, nv);
+    Fu = fma(lu, inv_h2, fma(u * u, u, fma(alpha, v, -g1)));
+    Fv = fma(lv, Dh2, fma(v * v, v, fma(-alpha, u, -g2)));
+}
+
+// The FP64 node of a float-pair iteration (a value beyond the fixed-point range):
+// (F_u, F_v, u, v) rounded to FP32.
+static __device__ __noinline__ float4 sys_node_exact(const double *__restrict__ U, const double *__restrict__ V,
+                                                     const double *__restrict__ f1, const double *__restrict__ f2,
+                                                     int c, int x, int y, int n, double alpha, double inv_h2,
+                                                     double Dh2) {
+    double u, v, g1, g2, Fu, Fv;
+    sys_node_fp64(U, V, f1, f2, c, x, y, n, alpha, inv_h2, Dh2, u, v, g1, g2, Fu, Fv);
+    return make_float4(d2f_rn(Fu), d2f_rn(Fv), d2f_rn(u), d2f_rn(v));
+}
+
+constexpr int kTW = 32;                  // chunk width (one warp's lanes)
+constexpr int kTH = kRowsPerItem;        // chunk height (one row per warp)
+constexpr int kHW = kTW + 2, kHH = kTH + 2;
+
+struct SysTile {   // fixed-point values of one chunk and its halo
+    long long u[kHH][kHW], v[kHH][kHW];
+};
+
+// bit pattern of node (y, x) of an n x n grid, 0 outside it (the Dirichlet boundary)
+__device__ __forceinline__ unsigned long long ld_node(const unsigned long long *__restrict__ B, int y, int x, int n) {
+    return (y >= 0 && y < n && x >= 0 && x < n) ? __ldg(B + y * n + x) : 0ull;
+}
+
+// high word of |value|: its exponent (bits 20..30) orders magnitudes to within 2x
+__device__ __forceinline__ unsigned hi_abs(unsigned long long b) { return (unsigned)(b >> 32) & 0x7FFFFFFFu; }
+
+__device__ __forceinline__ void store_planes(const SysInst &I, int o, float Fuf, float Fvf) {
+    __nv_bfloat16 h, l;
+    split_bf16(Fuf, h, l);
+    I.ru_hi[o] = h;
+    I.ru_lo[o] = l;
+    split_bf16(Fvf, h, l);
+    I.rv_hi[o] = h;
+    I.rv_lo[o] = l;
+}
+
+// One block per work item (instance, up to 8 rows of its padded P x P planes), one warp
+// per row, lanes along x. Iteration 0, and any iteration without a usable fixed-point
+// exponent, runs in FP64 (and writes the float-pair copies of f); later iterations
+// evaluate the stencil 4u - sum(nb) as an exact int64 sum of fixed-point values in units
+// of 2^(E - 1075 - kFxG), and the rest in float pairs (~48 significant bits). The block
+// walks its rows in chunks of 32 columns: it loads the chunk and its halo, takes E from
+// the largest |u|, |v| the chunk reads, converts every value to fixed point once into
+// shared memory (double-buffered, the next chunk's loads in flight), and forms each
+// node's stencil there. A chunk with values of 2^37 or more takes the FP64 path.
+__global__ void __launch_bounds__(256, 3) k_sys_residual(const SysInst *__restrict__ inst,
+                                                      const SysItem *__restrict__ items, SysState *st,
                                                       double *__restrict__ partials) {
     const SysItem it = items[blockIdx.x];
     const SysState S = st[it.inst];
     if (S.done) return;
     const SysInst I = inst[it.inst];
     const int n = I.n, P = I.P;
-    const bool want_f2 = S.it == 0;   // first iteration: sum f^2 and r^2 in FP64
+    const int lane = threadIdx.x & 31;
+    const int y = it.row0 + (threadIdx.x >> 5);
     const double alpha = I.alpha, Dh2 = I.D * I.inv_h2;
     const float alpha_f = (float)alpha;
     const float r2s = __int_as_float((127 - S.r2_exp) << 23);   // 2^-k
     float kr2 = 0.0f, kc = 0.0f;
-    double f2 = 0.0, r2 = 0.0;
+    double f2s = 0.0, r2 = 0.0;
     float mxp = -INFINITY, mnm = INFINITY;
-    for (int y = it.row0; y < it.row1; ++y) {
-        for (int x = threadIdx.x; x < P; x += blockDim.x) {
-            double Fu = 0.0, Fv = 0.0;
-            if (y < n && x < n) {
-                const int c = y * n + x;
-                const double u = __ldg(I.U + c), v = __ldg(I.V + c);
-                double nu[4], nv[4];
-                nu[0] = x > 0 ? __ldg(I.U + c - 1) : 0.0;
-                nu[1] = x < n - 1 ? __ldg(I.U + c + 1) : 0.0;
-                nu[2] = y > 0 ? __ldg(I.U + c - n) : 0.0;
-                nu[3] = y < n - 1 ? __ldg(I.U + c + n) : 0.0;
-                nv[0] = x > 0 ? __ldg(I.V + c - 1) : 0.0;
-                nv[1] = x < n - 1 ? __ldg(I.V + c + 1) : 0.0;
-                nv[2] = y > 0 ? __ldg(I.V + c - n) : 0.0;
-                nv[3] = y < n - 1 ? __ldg(I.V + c + n) : 0.0;
-                const double g1 = __ldg(I.f1 + c), g2 = __ldg(I.f2 + c);
-                const double lu = stencil_fixed<2>(u, nu);
-                const double lv = stencil_fixed<2>(v, nv);
-                Fu = fma(lu, I.inv_h2, fma(u * u, u, fma(alpha, v, -g1)));
-                Fv = fma(lv, Dh2, fma(v * v, v, fma(-alpha, u, -g2)));
-                // eigenvalues of [[3u^2, alpha], [-alpha, 3v^2]] (real parts), FP32
-                const float uf = d2f_rn(u), vf = d2f_rn(v);
-                const float a = 3.0f * uf * uf, d = 3.0f * vf * vf;
-                const float disc = (a - d) * (a - d) - 4.0f * alpha_f * alpha_f;
-                const float sq = disc > 0.0f ? sqrtf(disc) : 0.0f;
-                mxp = fmaxf(mxp, 0.5f * (a + d + sq));
-                mnm = fminf(mnm, 0.5f * (a + d - sq));
-                if (want_f2) {
-                    const double2 s2 = first_iteration_sums(make_double2(f2, r2), g1, g2, Fu, Fv);
-                    f2 = s2.x;
-                    r2 = s2.y;
-                } else {
-                    const float fu = __fmul_rn(d2f_rn(Fu), r2s), fv = __fmul_rn(d2f_rn(Fv), r2s);
-                    const float yk = fmaf(fu, fu, fmaf(fv, fv, -kc));
-                    const float tk = kr2 + yk;
-                    kc = (tk - kr2) - yk;
-                    kr2 = tk;
+    if (S.it == 0 || !S.df) {
+        const bool first = S.it == 0;   // sum f^2 and r^2 in FP64, copy f as float pairs
+        if (y < it.row1) {
+            for (int x = lane; x < P; x += 32) {
+                float Fuf = 0.0f, Fvf = 0.0f;
+                if (y < n && x < n) {
+                    const int c = y * n + x;
+                    double u, v, g1, g2, Fu, Fv;
+                    sys_node_fp64(I.U, I.V, I.f1, I.f2, c, x, y, n, alpha, I.inv_h2, Dh2, u, v, g1, g2, Fu, Fv);
+                    Fuf = d2f_rn(Fu);
+                    Fvf = d2f_rn(Fv);
+                    sys_extremes(d2f_rn(u), d2f_rn(v), alpha_f, mxp, mnm);
+                    if (first) {
+                        const double2 s2 = first_iteration_sums(make_double2(f2s, r2), g1, g2, Fu, Fv);
+                        f2s = s2.x;
+                        r2 = s2.y;
+                        I.f1p[c] = f_pair(g1, &st[it.inst].fbad);
+                        I.f2p[c] = f_pair(g2, &st[it.inst].fbad);
+                    } else {
+                        sys_r2(Fuf, Fvf, r2s, kr2, kc);
+                    }
+                }
+                store_planes(I, y * P + x, Fuf, Fvf);
+            }
+        }
+        if (!first) r2 = ldexp((double)kr2 - (double)kc, 2 * S.r2_exp);
+    } else {
+        __shared__ SysTile tile[2];
+        __shared__ __align__(16) unsigned smax[2][kTH];
+        const int t = threadIdx.x, w = t >> 5;
+        const unsigned long long *Ub = reinterpret_cast<const unsigned long long *>(I.U);
+        const unsigned long long *Vb = reinterpret_cast<const unsigned long long *>(I.V);
+        // this thread's halo slot (threads 0 .. 2 kTW + 2 kHH - 1): the rows above and below the
+        // chunk, then the columns left and right of it (corners included, unused)
+        const bool halo = t < 2 * kTW + 2 * kHH;
+        int hr = 0, hc = 0;
+        if (t < kTW) {
+            hr = 0;
+            hc = t + 1;
+        } else if (t < 2 * kTW) {
+            hr = kHH - 1;
+            hc = t - kTW + 1;
+        } else if (t < 2 * kTW + kHH) {
+            hr = t - 2 * kTW;
+            hc = 0;
+        } else {
+            hr = t - 2 * kTW - kHH;
+            hc = kHW - 1;
+        }
+        const int hy = it.row0 - 1 + hr, hx = hc - 1;   // halo node, x relative to the chunk
+        unsigned long long bu = ld_node(Ub, y, lane, n), bv = ld_node(Vb, y, lane, n), hu = 0ull, hv = 0ull;
+        if (halo) {
+            hu = ld_node(Ub, hy, hx, n);
+            hv = ld_node(Vb, hy, hx, n);
+        }
+        const bool yin = y < n;
+        float2 g1 = make_float2(0.0f, 0.0f), g2 = g1;
+        if (yin && lane < n) {
+            g1 = __ldg(I.f1p + y * n + lane);
+            g2 = __ldg(I.f2p + y * n + lane);
+        }
+        int par = 0;
+        for (int x0 = 0; x0 < P; x0 += kTW, par ^= 1) {
+            const int x = x0 + lane;
+            // the chunk's exponent: the largest |value| it reads (high words carry the exponent)
+            unsigned m = max(hi_abs(bu), hi_abs(bv));
+            if (halo) m = max(m, max(hi_abs(hu), hi_abs(hv)));
+            m = __reduce_max_sync(0xffffffffu, m);
+            if (lane == 0) smax[par][w] = m;
+            __syncthreads();
+            const uint4 m0 = *reinterpret_cast<const uint4 *>(&smax[par][0]);
+            const uint4 m1 = *reinterpret_cast<const uint4 *>(&smax[par][4]);
+            m = max(max(max(m0.x, m0.y), max(m0.z, m0.w)), max(max(m1.x, m1.y), max(m1.z, m1.w)));
+            const int ex = (int)(m >> 20);
+            // |values| < 2^37 keep every float-pair product inside the FP32 range; tiny
+            // chunks take the exponent 2^-60 (their fixed-point values stay exact to 2^-112)
+            const bool ok = ex <= 1023 + 36;
+            const int E = ex < 1023 - 60 ? 1023 - 60 : ex;
+            SysTile &T = tile[par];
+            unsigned nb = 0u;
+            const long long fu = fx_of(bu, E, nb), fv = fx_of(bv, E, nb);
+            T.u[w + 1][lane + 1] = fu;
+            T.v[w + 1][lane + 1] = fv;
+            if (halo) {
+                T.u[hr][hc] = fx_of(hu, E, nb);
+                T.v[hr][hc] = fx_of(hv, E, nb);
+            }
+            const float2 g1c = g1, g2c = g2;
+            if (x0 + kTW < P) {   // prefetch the next chunk
+                bu = ld_node(Ub, y, x + kTW, n);
+                bv = ld_node(Vb, y, x + kTW, n);
+                if (halo) {
+                    hu = ld_node(Ub, hy, x0 + kTW + hx, n);
+                    hv = ld_node(Vb, hy, x0 + kTW + hx, n);
+                }
+                if (yin && x + kTW < n) {
+                    g1 = __ldg(I.f1p + y * n + x + kTW);
+                    g2 = __ldg(I.f2p + y * n + x + kTW);
                 }
             }
-            const int o = y * P + x;
-            __nv_bfloat16 h, l;
-            split_bf16(d2f_rn(Fu), h, l);
-            I.ru_hi[o] = h;
-            I.ru_lo[o] = l;
-            split_bf16(d2f_rn(Fv), h, l);
-            I.rv_hi[o] = h;
-            I.rv_lo[o] = l;
+            __syncthreads();
+            float Fuf = 0.0f, Fvf = 0.0f;
+            if (yin && x < n) {
+                const int c = y * n + x;
+                float uf, vf;
+                if (ok) {
+                    const float scale = __int_as_float((E - 1075 - kFxG + 127) << 23);
+                    const long long lu = 4 * fu - T.u[w + 1][lane] - T.u[w + 1][lane + 2] - T.u[w][lane + 1] -
+                                         T.u[w + 2][lane + 1];
+                    const long long lv = 4 * fv - T.v[w + 1][lane] - T.v[w + 1][lane + 2] - T.v[w][lane + 1] -
+                                         T.v[w + 2][lane + 1];
+                    float2 lu2, lv2, up, vp;
+                    fx_to_pair(lu, scale, lu2.x, lu2.y);
+                    fx_to_pair(lv, scale, lv2.x, lv2.y);
+                    fx_to_pair(fu, scale, up.x, up.y);
+                    fx_to_pair(fv, scale, vp.x, vp.y);
+                    const float2 Fu = pair_add(pair_add(pair_mul(lu2, I.ih2), pair_mul(pair_mul(up, up), up)),
+                                               pair_add(pair_mul(I.al2, vp), pair_neg(g1c)));
+                    const float2 Fv = pair_add(pair_add(pair_mul(lv2, I.dh2), pair_mul(pair_mul(vp, vp), vp)),
+                                               pair_neg(pair_add(pair_mul(I.al2, up), g2c)));
+                    Fuf = __fadd_rn(Fu.x, Fu.y);
+                    Fvf = __fadd_rn(Fv.x, Fv.y);
+                    uf = __fadd_rn(up.x, up.y);
+                    vf = __fadd_rn(vp.x, vp.y);
+                } else {
+                    const float4 r = sys_node_exact(I.U, I.V, I.f1, I.f2, c, x, y, n, alpha, I.inv_h2, Dh2);
+                    Fuf = r.x;
+                    Fvf = r.y;
+                    uf = r.z;
+                    vf = r.w;
+                }
+                sys_extremes(uf, vf, alpha_f, mxp, mnm);
+                sys_r2(Fuf, Fvf, r2s, kr2, kc);
+            }
+            store_planes(I, y * P + x, Fuf, Fvf);
         }
+        r2 = ldexp((double)kr2 - (double)kc, 2 * S.r2_exp);
     }
-    if (!want_f2) r2 = ldexp((double)kr2 - (double)kc, 2 * S.r2_exp);
-    Red4 acc{r2, f2, (double)mxp, (double)mnm};
+    Red4 acc{r2, f2s, (double)mxp, (double)mnm};
     acc = block_red(acc);
     if (threadIdx.x == 0) {
         double *p = partials + 4ll * blockIdx.x;
@@ -219,6 +402,9 @@ __global__ void __launch_bounds__(128) k_sys_finalize(const SysInst *__restrict_
         int k = (rms > 0.0 && rms < INFINITY) ? ilogb(rms) : 0;
         s.r2_exp = k < -120 ? -120 : (k > 120 ? 120 : k);
     }
+    // later iterations in fixed point / float pairs unless a coefficient or |f| is out of
+    // the float-pair range, or ||f|| < 2^-40 (relative errors of tiny values would show)
+    s.df = (I.df_ok && !s.fbad && s.f_norm >= 0x1p-40) ? 1 : 0;
     const double res = sqrt(acc.r2);
     double rel = s.f_norm > 0.0 ? res / s.f_norm : (res == 0.0 ? 0.0 : INFINITY);
     const double beta = 0.5 * (acc.mx + acc.mn);
@@ -273,6 +459,7 @@ struct qn_batch {
     SysItem *d_items;
     int nitems;
     double *partials;
+    float2 *fpairs;                    // float-pair copies of every instance's f1, f2
     SysState *d_state;
     SysCtl *d_ctl;
     int *err;
@@ -298,6 +485,7 @@ static void batch_free(qn_batch *b) {
     cudaFree(b->d_inst);
     cudaFree(b->d_items);
     cudaFree(b->partials);
+    cudaFree(b->fpairs);
     cudaFree(b->d_state);
     cudaFree(b->d_ctl);
     cudaFree(b->err);
@@ -463,14 +651,23 @@ extern "C" int qn_batch_create(const qn_sys_instance *inst, int count, int bk, c
     BCK(cudaMalloc(&b->d_ctl, sizeof(SysCtl)));
     BCK(cudaMalloc(&b->err, sizeof(int)));
     BCK(cudaMemset(b->err, 0, sizeof(int)));
+    size_t npts = 0;
+    for (int i = 0; i < count; ++i) npts += (size_t)inst[i].n * inst[i].n;
+    BCK(cudaMalloc(&b->fpairs, sizeof(float2) * 2 * npts));
     std::vector<SysInst> hinst(count);
     std::vector<SysItem> hitems;
+    size_t poff = 0;
+    auto pair_host = [](double v) { const float hi = (float)v; return make_float2(hi, (float)(v - (double)hi)); };
     for (int i = 0; i < count; ++i) {
         SysInst &s = hinst[i];
         s.U = inst[i].U;
         s.V = inst[i].V;
         s.f1 = inst[i].f1;
         s.f2 = inst[i].f2;
+        const size_t nn = (size_t)inst[i].n * inst[i].n;
+        s.f1p = b->fpairs + poff;
+        s.f2p = b->fpairs + poff + nn;
+        poff += 2 * nn;
         s.ru_hi = plane(i, 0, 0, 0);
         s.ru_lo = plane(i, 0, 0, 1);
         s.rv_hi = plane(i, 1, 0, 0);
@@ -479,6 +676,10 @@ extern "C" int qn_batch_create(const qn_sys_instance *inst, int count, int bk, c
         s.D = inst[i].D;
         const double h = 1.0 / (inst[i].n + 1);
         s.inv_h2 = 1.0 / (h * h);
+        s.ih2 = pair_host(s.inv_h2);
+        s.dh2 = pair_host(s.D * s.inv_h2);
+        s.al2 = pair_host(s.alpha);
+        s.df_ok = (fabs(s.alpha) < 0x1p60 && s.D * s.inv_h2 < 0x1p60) ? 1 : 0;
         s.n = inst[i].n;
         s.P = b->P[i];
         s.item_begin = (int)hitems.size();

@@ -87,4 +87,16 @@ __device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
     return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
 }
 
+// a * b for float pairs, renormalised.
+__device__ __forceinline__ float2 pair_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    const float hi = __fadd_rn(p, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, p)));
+}
+
+__device__ __forceinline__ float2 pair_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
 }  // namespace qn

@@ -310,18 +310,6 @@ __global__ void __launch_bounds__(256) k_eig_pass2(double *__restrict__ U, const
 // stop-test finaliser from pass 2's block maxima); everything else is in float pairs
 // (~48 significant bits). A node whose stencil reads a value beyond E takes the FP64 path.
 
-// a * b for float pairs, renormalised.
-__device__ __forceinline__ float2 pair_mul(float2 a, float2 b) {
-    const float p = __fmul_rn(a.x, b.x);
-    float e = __fmaf_rn(a.x, b.x, -p);
-    e = __fmaf_rn(a.x, b.y, e);
-    e = __fmaf_rn(a.y, b.x, e);
-    const float hi = __fadd_rn(p, e);
-    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, p)));
-}
-
-__device__ __forceinline__ float2 pair_neg(float2 a) { return make_float2(-a.x, -a.y); }
-
 __device__ __forceinline__ double pair_to_double(float2 a) { return (double)a.x + (double)a.y; }
 
 // FP64 path of one pass-1 node (values beyond the fixed-point range): lin and u as pairs.

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from paper_2502_03611_gb300.inputs import coupled_params, coupled_problem
+from paper_2502_03611_gb300.inputs import coupled_params, coupled_problem, random_field
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +35,7 @@ def make_instances(specs):
     return insts, truth
 
 
-def check_against_oracle(inst, f1, f2, res):
+def check_against_oracle(inst, f1, f2, res, check_iterations=True):
     n = inst["n"]
     Uo, Vo, ho, ok = O.qn_solve_system(f1, f2, inst["alpha"], inst["D"], tol=1e-10)
     assert ok
@@ -49,7 +49,8 @@ def check_against_oracle(inst, f1, f2, res):
     Fu, Fv = O.system_residual(Ug, Vg, f1, f2, inst["alpha"], inst["D"])
     rel = np.sqrt(np.sum(Fu ** 2) + np.sum(Fv ** 2)) / np.sqrt(np.sum(f1 ** 2) + np.sum(f2 ** 2))
     assert rel <= 1.05e-10
-    assert res["iterations"] <= len(ho) - 1 + 2
+    if check_iterations:
+        assert res["iterations"] <= len(ho) - 1 + 2
 
 
 def test_batch_mixed_sizes_match_oracle(qn):
@@ -139,3 +140,21 @@ def test_batch_tiny_source_scale(qn):
     for inst, (f1, f2), r in zip(insts, truth, res):
         assert r["iterations"] >= 1
         check_against_oracle(inst, f1, f2, r)
+
+
+def test_batch_fixed_point_range_fallback(qn):
+    """A start 1e-4 the size of the solution: the fixed-point exponent of the
+    first float-pair iteration comes from max|U_0|, so most of its nodes read
+    values beyond it and take the FP64 node path; later iterations are back on
+    the float-pair path. The solve still matches the oracle."""
+    import torch
+    specs = [(63, 0.5, 1.0, 41), (127, 0.9, 5.0, 42)]
+    insts, truth = make_instances(specs)
+    for k, inst in enumerate(insts):
+        n = inst["n"]
+        inst["U"].copy_(torch.from_numpy(1e-4 * random_field((n * n,), 100 + k)))
+        inst["V"].copy_(torch.from_numpy(1e-4 * random_field((n * n,), 200 + k)))
+    rc, res = qn.QnBatch(insts).solve()
+    assert rc == 0
+    for inst, (f1, f2), r in zip(insts, truth, res):
+        check_against_oracle(inst, f1, f2, r, check_iterations=False)
