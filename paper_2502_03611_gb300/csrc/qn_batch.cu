@@ -124,7 +124,7 @@ __global__ void k_sys_init(SysState *st, int count, SysCtl *ctl, double tol, int
 __device__ __forceinline__ void sys_extremes(float uf, float vf, float alpha_f, float &mxp, float &mnm) {
     const float a = 3.0f * uf * uf, d = 3.0f * vf * vf;
     const float disc = (a - d) * (a - d) - 4.0f * alpha_f * alpha_f;
-    const float sq = disc > 0.0f ? sqrtf(disc) : 0.0f;
+    const float sq = disc > 0.0f ? disc * rsqrtf(disc) : 0.0f;   // beta needs no more than FP32 accuracy
     mxp = fmaxf(mxp, 0.5f * (a + d + sq));
     mnm = fminf(mnm, 0.5f * (a + d - sq));
 }
@@ -183,6 +183,32 @@ static __device__ __noinline__ float4 sys_node_exact(const double *__restrict__ 
 constexpr int kTW = 32;                  // chunk width (one warp's lanes)
 constexpr int kTH = kRowsPerItem;        // chunk height (one row per warp)
 constexpr int kHW = kTW + 2, kHH = kTH + 2;
+
+// a * b for a float pair a and a float b (unnormalised pair result)
+__device__ __forceinline__ float2 pair_mul_f(float2 a, float b) {
+    const float p = __fmul_rn(a.x, b);
+    return make_float2(p, __fmaf_rn(a.y, b, __fmaf_rn(a.x, b, -p)));
+}
+
+// a^3 for a float pair a: hi^3 with its exact rounding errors, plus 3 hi^2 lo
+__device__ __forceinline__ float2 pair_cube(float2 a) {
+    const float s = __fmul_rn(a.x, a.x);
+    const float es = __fmaf_rn(a.x, a.x, -s);
+    const float c = __fmul_rn(s, a.x);
+    const float ec = __fmaf_rn(s, a.x, -c);
+    return make_float2(c, __fmaf_rn(3.0f * s, a.y, __fmaf_rn(es, a.x, ec)));
+}
+
+// t0 + t1 + t2 + t3 of float pairs, rounded to FP32: the high parts through a chain of
+// exact two-sums, every low part and rounding error added once at the end
+__device__ __forceinline__ float pair_sum4(float2 t0, float2 t1, float2 t2, float2 t3) {
+    float s, e0, e1, e2;
+    two_sum(t0.x, t1.x, s, e0);
+    two_sum(s, t2.x, s, e1);
+    two_sum(s, t3.x, s, e2);
+    const float lo = ((t0.y + t1.y) + (t2.y + t3.y)) + ((e0 + e1) + e2);
+    return __fadd_rn(s, lo);
+}
 
 struct SysTile {   // fixed-point values of one chunk and its halo
     long long u[kHH][kHW], v[kHH][kHW];
@@ -347,14 +373,11 @@ __global__ void __launch_bounds__(256, 3) k_sys_residual(const SysInst *__restri
                     fx_to_pair(lv, scale, lv2.x, lv2.y);
                     fx_to_pair(fu, scale, up.x, up.y);
                     fx_to_pair(fv, scale, vp.x, vp.y);
-                    const float2 Fu = pair_add(pair_add(pair_mul(lu2, I.ih2), pair_mul(pair_mul(up, up), up)),
-                                               pair_add(pair_mul(I.al2, vp), pair_neg(g1c)));
-                    const float2 Fv = pair_add(pair_add(pair_mul(lv2, I.dh2), pair_mul(pair_mul(vp, vp), vp)),
-                                               pair_neg(pair_add(pair_mul(I.al2, up), g2c)));
-                    Fuf = __fadd_rn(Fu.x, Fu.y);
-                    Fvf = __fadd_rn(Fv.x, Fv.y);
-                    uf = __fadd_rn(up.x, up.y);
-                    vf = __fadd_rn(vp.x, vp.y);
+                    // inv_h2 is (n + 1)^2 to FP64 rounding, an FP32 number (n <= 1024): its high part suffices
+                    Fuf = pair_sum4(pair_mul_f(lu2, I.ih2.x), pair_cube(up), pair_mul(I.al2, vp), pair_neg(g1c));
+                    Fvf = pair_sum4(pair_mul(lv2, I.dh2), pair_cube(vp), pair_neg(pair_mul(I.al2, up)), pair_neg(g2c));
+                    uf = up.x;
+                    vf = vp.x;
                 } else {
                     const float4 r = sys_node_exact(I.U, I.V, I.f1, I.f2, c, x, y, n, alpha, I.inv_h2, Dh2);
                     Fuf = r.x;

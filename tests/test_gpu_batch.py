@@ -143,10 +143,10 @@ def test_batch_tiny_source_scale(qn):
 
 
 def test_batch_fixed_point_range_fallback(qn):
-    """A start 1e-4 the size of the solution: the fixed-point exponent of the
-    first float-pair iteration comes from max|U_0|, so most of its nodes read
-    values beyond it and take the FP64 node path; later iterations are back on
-    the float-pair path. The solve still matches the oracle."""
+    """A start 1e-4 the size of the solution: the first float-pair iteration
+    reads values four orders of magnitude above those of iteration 0, so each
+    chunk's fixed-point exponent has to follow the iterate it reads (it is
+    taken per chunk, not carried over). The solve still matches the oracle."""
     import torch
     specs = [(63, 0.5, 1.0, 41), (127, 0.9, 5.0, 42)]
     insts, truth = make_instances(specs)
