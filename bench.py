@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end solve")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched coupled-systems measurement")
+    ap.add_argument("--tiles", default="auto",
+                    help="batched tiles: 'auto' (autotuner) or BK:BN63,BN127,BN255,BN511, e.g. 64:64,64,128,256")
     ap.add_argument("--quick", action="store_true", help="= --no-fp64 --no-cpu --no-e2e --no-batched")
     a = ap.parse_args()
     if a.quick:
@@ -267,17 +269,23 @@ def sem_oracle_sample(n: int, k: int, iters_timed: int = 1):
                                 "small": small}
 
 
-def run_batched(qn, seed=0, count=256, reps=3):
+def run_batched(qn, seed=0, count=256, reps=3, tiles="auto"):
     """Batched coupled 2-D systems: 256 instances, n uniform on {63,127,255,511},
-    alpha ~ U[0,1], D ~ U[0.1,10]; tiles from the project autotuner per size.
-    Returns instances/s and p50/p99 of the per-instance device time to convergence."""
+    alpha ~ U[0,1], D ~ U[0.1,10]; tiles from the project autotuner per size, or
+    given as BK:BN63,BN127,BN255,BN511. Returns instances/s and p50/p99 of the
+    per-instance device time to convergence."""
     import numpy as np
     import torch
     from paper_2502_03611_gb300.inputs import coupled_params, coupled_problem
     specs = [coupled_params(seed, i) + (seed * 1000 + i,) for i in range(count)]
     tuned = {}
-    for n in sorted({s[0] for s in specs}):
-        tuned[n] = qn.qn_autotune_tile(n, copies=16)
+    if tiles == "auto":
+        for n in sorted({s[0] for s in specs}):
+            tuned[n] = qn.qn_autotune_tile(n, copies=16)
+    else:
+        bk_s, bns = tiles.split(":")
+        for n, bn_s in zip((63, 127, 255, 511), bns.split(",")):
+            tuned[n] = (int(bk_s), int(bn_s), 0.0)
     # one K-tile per launch: the one tuned for the largest (costliest) size;
     # other sizes keep their tuned N-tile when it was tuned with that K-tile
     bk = tuned[max(tuned)][0]
@@ -562,7 +570,7 @@ def main_batched(a):
     from paper_2502_03611_gb300 import qn
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     sampler.start()
-    b = run_batched(qn, seed=a.seed, reps=max(a.steps, 1))
+    b = run_batched(qn, seed=a.seed, reps=max(a.steps, 1), tiles=a.tiles)
     clocks = sampler.stop()
     line = {"metric": "instances/s, 256 coupled 2-D systems to rel. residual 1e-10", "value": b["instances_per_s"],
             "unit": "instances/s", "n_gpus": 1, "steps": b["steps"], "warmup": 2, "ms_per_step": b["ms_per_batch"],

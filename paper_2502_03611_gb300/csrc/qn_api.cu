@@ -1120,14 +1120,15 @@ static int enqueue_eig_iteration(qn_ctx *c, double *U, double step, cudaStream_t
     float2 *lin2 = reinterpret_cast<float2 *>(c->eig_r0);   // the same 8 bytes per node, as a pair
     const bool mirror = !fp64 && c->split;
     long pr = prof_begin(c, PK_RESIDUAL, s);
+    int grid1 = grid;   // blocks (partial sums) of pass 1
     int rc = df ? launch_eig_pass1_df(U, lin2, c->n, c->dim, c->prob.bc, c->inv_h2, c->prob.lam, c->prob.b, c->pot64,
-                                      c->eig_vrow, c->eig_potx2, c->eig_vrow2, c->partials, grid, c->st, s)
+                                      c->eig_vrow, c->eig_potx2, c->eig_vrow2, c->partials, grid, &grid1, c->st, s)
                 : launch_eig_pass1(U, lin, c->n, c->dim, c->prob.bc, c->inv_h2, c->prob.lam, c->prob.b, c->pot64,
                                    c->eig_vrow, c->partials, grid, c->st, s);
     prof_end(c, pr, s);
     if (rc) return rc;
     pr = prof_begin(c, PK_FINALIZE, s);
-    rc = launch_eig_finalize1(c->partials, grid, hd, c->st, s);
+    rc = launch_eig_finalize1(c->partials, grid1, hd, c->st, s);
     prof_end(c, pr, s);
     if (rc) return rc;
     pr = prof_begin(c, PK_RESIDUAL, s);

@@ -409,6 +409,146 @@ __global__ void __launch_bounds__(256) k_eig_pass1_df(const double *__restrict__
     }
 }
 
+// ---- tiled pass 1 (3-D, float pairs) ------------------------------------------------------
+// The arithmetic of k_eig_pass1_df with each value converted to fixed point once: a block
+// owns a 32 x 8 (x, y) tile of a run of z planes, one warp per y row, and walks z. The
+// tile's plane z and its x / y halo sit in shared memory (double-buffered), the z - 1 and
+// z + 1 values of the thread's own column in registers; the next plane's loads are in
+// flight while the current one is evaluated. A node takes the FP64 path when a value of
+// plane z (anywhere in the tile: one block-wide flag) or of its own column at z - 1, z + 1
+// lies beyond the fixed-point exponent.
+constexpr int kP1W = 32, kP1H = 8;
+constexpr int kP1SW = kP1W + 2, kP1SH = kP1H + 2;
+constexpr int kP1Halo = 2 * kP1W + 2 * kP1H;   // 80 halo values per plane (no corners)
+
+__device__ __forceinline__ int ghost_of(int i, int n, bool neu) {
+    return neu ? (i == -1 ? 1 : (i == n ? n - 2 : i)) : i;
+}
+
+// bit pattern of node (z, y, x), the Neumann ghost rule applied, 0 off the grid (Dirichlet)
+template <bool NEU>
+__device__ __forceinline__ unsigned long long ld_node3(const unsigned long long *__restrict__ Ub, int z, int y,
+                                                       int x, int n) {
+    z = ghost_of(z, n, NEU);
+    y = ghost_of(y, n, NEU);
+    x = ghost_of(x, n, NEU);
+    const bool in = (unsigned)z < (unsigned)n && (unsigned)y < (unsigned)n && (unsigned)x < (unsigned)n;
+    return in ? __ldg(Ub + ((long long)z * n + y) * n + x) : 0ull;
+}
+
+template <bool NEU>
+__global__ void __launch_bounds__(256, 3) k_eig_pass1_tiled(const double *__restrict__ U, float2 *__restrict__ lin,
+                                                            int n, int zchunk, double inv_h2, double lam,
+                                                            float2 lam2, double b, const double *__restrict__ pot,
+                                                            const double *__restrict__ vrow,
+                                                            const float2 *__restrict__ pot2,
+                                                            const float2 *__restrict__ vrow2,
+                                                            double *__restrict__ partials, const DevState *st) {
+    if (state_done(st)) return;
+    __shared__ long long sp[2][kP1SH][kP1SW];
+    const int E = st->fx_e;
+    const float scale = __int_as_float(E != 0 ? ((E - 1075 - kFxG + 127) << 23) : 0);
+    const float ih = __double2float_rn(inv_h2), il = __double2float_rn(inv_h2 - (double)ih);
+    const float2 ih2 = make_float2(ih, il);
+    const unsigned long long *Ub = reinterpret_cast<const unsigned long long *>(U);
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    // this thread's halo slot: the rows above / below the tile, then the columns left / right
+    const bool halo = t < kP1Halo;
+    int hr, hc;
+    if (t < kP1W) {
+        hr = 0;
+        hc = t + 1;
+    } else if (t < 2 * kP1W) {
+        hr = kP1SH - 1;
+        hc = t - kP1W + 1;
+    } else if (t < 2 * kP1W + kP1H) {
+        hr = t - 2 * kP1W + 1;
+        hc = 0;
+    } else {
+        hr = t - 2 * kP1W - kP1H + 1;
+        hc = kP1SW - 1;
+    }
+    if (!halo) hr = hc = 0;
+    const int tiles_x = (n + kP1W - 1) / kP1W, tiles_y = (n + kP1H - 1) / kP1H;
+    const int nzc = (n + zchunk - 1) / zchunk;
+    const long long items = (long long)tiles_x * tiles_y * nzc;
+    float2 e1 = make_float2(0.f, 0.f), e4 = e1, q = e1;
+    for (long long item = blockIdx.x; item < items; item += gridDim.x) {
+        const int tx = (int)(item % tiles_x);
+        const long long rest = item / tiles_x;
+        const int ty = (int)(rest % tiles_y);
+        const int z0 = (int)(rest / tiles_y) * zchunk;
+        const int z1 = min(z0 + zchunk, n);
+        const int x = tx * kP1W + lane, y = ty * kP1H + w;
+        const int hx = tx * kP1W + hc - 1, hy = ty * kP1H + hr - 1;
+        const bool own = x < n && y < n;
+        unsigned bm = (E == 0) ? 1u : 0u, bc = bm, bh = bm;   // bad flags: own z-1, own z, plane z (local)
+        long long fmv = fx_of(ld_node3<NEU>(Ub, z0 - 1, y, x, n), E, bm);
+        long long fc = fx_of(ld_node3<NEU>(Ub, z0, y, x, n), E, bc);
+        sp[0][w + 1][lane + 1] = fc;
+        if (halo) sp[0][hr][hc] = fx_of(ld_node3<NEU>(Ub, z0, hy, hx, n), E, bh);
+        bh |= bc;
+        unsigned long long nO = ld_node3<NEU>(Ub, z0 + 1, y, x, n);
+        unsigned long long nH = halo ? ld_node3<NEU>(Ub, z0 + 1, hy, hx, n) : 0ull;
+        int buf = 0;
+        for (int z = z0; z < z1; ++z, buf ^= 1) {
+            const bool plane_bad = __syncthreads_or((int)bh) != 0;   // plane z is in sp[buf]
+            unsigned bp = (E == 0) ? 1u : 0u;
+            const long long fp = fx_of(nO, E, bp);
+            bh = bp;
+            sp[buf ^ 1][w + 1][lane + 1] = fp;
+            if (halo) sp[buf ^ 1][hr][hc] = fx_of(nH, E, bh);
+            if (z + 1 < z1) {   // prefetch plane z + 2
+                nO = ld_node3<NEU>(Ub, z + 2, y, x, n);
+                if (halo) nH = ld_node3<NEU>(Ub, z + 2, hy, hx, n);
+            }
+            if (own) {
+                const long long c = ((long long)z * n + y) * n + x;
+                float2 lv, up;
+                if (!(plane_bad || bm || bp)) {
+                    const long long lapfx = 6 * fc - sp[buf][w + 1][lane] - sp[buf][w + 1][lane + 2] -
+                                            sp[buf][w][lane + 1] - sp[buf][w + 2][lane + 1] - fmv - fp;
+                    float lh, ll, uh, ul;
+                    fx_to_pair(lapfx, scale, lh, ll);
+                    fx_to_pair(fc, scale, uh, ul);
+                    up = make_float2(uh, ul);
+                    const float2 cv = (pot != nullptr) ? pair_add(__ldg(vrow2 + (long long)z * n + y), __ldg(pot2 + x))
+                                                       : lam2;
+                    lv = pair_add(pair_mul(make_float2(lh, ll), ih2), pair_mul(cv, up));
+                } else {
+                    const double cv = (pot != nullptr) ? __ldg(vrow + (long long)z * n + y) + __ldg(pot + x) : lam;
+                    lv = pass1_node_exact<3, NEU>(U, c, x, y, z, n, inv_h2, cv, up);
+                }
+                lin[c] = lv;
+                float2 wu = up;
+                if (NEU) {   // trapezoid weights are powers of two: exact on both halves
+                    const float wt = ((x == 0 || x == n - 1) ? 0.5f : 1.0f) * ((y == 0 || y == n - 1) ? 0.5f : 1.0f) *
+                                     ((z == 0 || z == n - 1) ? 0.5f : 1.0f);
+                    wu = make_float2(wu.x * wt, wu.y * wt);
+                }
+                const float2 wu2 = pair_mul(wu, up);
+                e1 = pair_add(e1, pair_mul(wu, lv));
+                e4 = pair_add(e4, pair_mul(wu2, pair_mul(up, up)));
+                q = pair_add(q, wu2);
+            }
+            fmv = fc;
+            bm = bc;
+            fc = fp;
+            bc = bp;
+        }
+        __syncthreads();   // the next item's first plane reuses sp[0]
+    }
+    Sum4 acc{pair_to_double(e1), pair_to_double(e4), pair_to_double(q), 0.0};
+    acc = block_sum3(acc);
+    if (threadIdx.x == 0) {
+        double *p = partials + 4ll * blockIdx.x;
+        p[0] = acc.a;
+        p[1] = b * acc.b;
+        p[2] = acc.mn;
+        p[3] = 0.0;
+    }
+}
+
 // One node of pass 2 in float pairs; U = s U~ written back (the one FP64 multiply).
 template <int DIM, bool NEU>
 __device__ __forceinline__ float eig_point_df(double *__restrict__ U, const float2 *__restrict__ lin, long long c,
@@ -602,6 +742,25 @@ int launch_eig_pass2(double *U, const double *lin, int n, int P, int dim, int bc
     return QN_OK;
 }
 
+template <bool NEU>
+static int pass1_tiled(const double *U, float2 *lin, int n, double inv_h2, double lam, float2 lam2, double b,
+                       const double *pot, const double *vrow, const float2 *pot2, const float2 *vrow2,
+                       double *partials, int grid, int *used, const DevState *st, cudaStream_t s) {
+    int dev = 0, sms = 0, nb = 0;
+    QN_CUDA(cudaGetDevice(&dev));
+    QN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    QN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eig_pass1_tiled<NEU>, 256, 0));
+    const int zc = n < 400 ? 16 : 32;   // planes per work item (two more are read at its start)
+    const long long items = (long long)((n + kP1W - 1) / kP1W) * ((n + kP1H - 1) / kP1H) * ((n + zc - 1) / zc);
+    long long g = (long long)(nb > 0 ? nb : 1) * sms;   // one wave of resident blocks
+    if (g > grid) g = grid;
+    if (g > items) g = items;
+    k_eig_pass1_tiled<NEU><<<(int)g, 256, 0, s>>>(U, lin, n, zc, inv_h2, lam, lam2, b, pot, vrow, pot2, vrow2,
+                                                  partials, st);
+    *used = (int)g;
+    return QN_OK;
+}
+
 template <int DIM>
 static void pass1_df_dim(const double *U, float2 *lin, int n, bool neu, double inv_h2, double lam, double b,
                          const double *pot, const double *vrow, const float2 *pot2, const float2 *vrow2,
@@ -618,16 +777,24 @@ static void pass1_df_dim(const double *U, float2 *lin, int n, bool neu, double i
 
 int launch_eig_pass1_df(const double *U, float2 *lin, int n, int dim, int bc, double inv_h2, double lam, double b,
                         const double *pot, const double *vrow, const float2 *pot2, const float2 *vrow2,
-                        double *partials, int grid, const DevState *st, cudaStream_t s) {
+                        double *partials, int grid, int *used, const DevState *st, cudaStream_t s) {
     if (pot != nullptr && (vrow == nullptr || pot2 == nullptr || vrow2 == nullptr)) {
         set_error("launch_eig_pass1_df: a potential needs its per-row and float-pair tables");
         return QN_EINVAL;
     }
     const bool neu = (bc == QN_BC_NEUMANN);
-    if (dim == 3)
-        pass1_df_dim<3>(U, lin, n, neu, inv_h2, lam, b, pot, vrow, pot2, vrow2, partials, grid, st, s);
-    else
+    *used = grid;
+    if (dim == 3) {
+        const float lh = (float)lam;
+        const float2 lam2 = make_float2(lh, (float)(lam - (double)lh));
+        const int rc = neu ? pass1_tiled<true>(U, lin, n, inv_h2, lam, lam2, b, pot, vrow, pot2, vrow2, partials,
+                                               grid, used, st, s)
+                           : pass1_tiled<false>(U, lin, n, inv_h2, lam, lam2, b, pot, vrow, pot2, vrow2, partials,
+                                                grid, used, st, s);
+        if (rc) return rc;
+    } else {
         pass1_df_dim<2>(U, lin, n, neu, inv_h2, lam, b, pot, vrow, pot2, vrow2, partials, grid, st, s);
+    }
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }

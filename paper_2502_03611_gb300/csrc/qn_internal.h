@@ -147,10 +147,11 @@ int launch_eig_pass1(const double *U, double *lin, int n, int dim, int bc, doubl
 int launch_eig_finalize1(const double *partials, int nparts, double hd, DevState *st, cudaStream_t s);
 // Float-pair forms (split precision, iterations >= 1): lin as FP32 pairs; pot2 / vrow2 the
 // potential's per-column and per-row tables as pairs; the fixed-point exponent comes from
-// DevState::fx_e. Pass 2 writes planes only (natural or reflection-split order).
+// DevState::fx_e. Pass 2 writes planes only (natural or reflection-split order). Pass 1
+// launches at most `grid` blocks and returns in `used` how many (the partial sums to add).
 int launch_eig_pass1_df(const double *U, float2 *lin, int n, int dim, int bc, double inv_h2, double lam, double b,
                         const double *pot, const double *vrow, const float2 *pot2, const float2 *vrow2,
-                        double *partials, int grid, const DevState *st, cudaStream_t s);
+                        double *partials, int grid, int *used, const DevState *st, cudaStream_t s);
 int launch_eig_pass2_df(double *U, const float2 *lin, int n, int P, int dim, int bc, double hd, float lam, double b,
                         const float *pot32, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, bool mirror, double *partials,
                         int grid, DevState *st, cudaStream_t s);
