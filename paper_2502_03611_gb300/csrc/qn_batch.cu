@@ -45,7 +45,7 @@ struct SysInst {
     const double *f1, *f2;
     float2 *f1p, *f2p;                               // float-pair copies of f1, f2 (written on iteration 0)
     __nv_bfloat16 *ru_hi, *ru_lo, *rv_hi, *rv_lo;   // buffer 0 planes of both components
-    double alpha, D, inv_h2;
+    double alpha, D, inv_h2, Dh2;                    // Dh2 = D inv_h2
     float2 ih2, dh2, al2;                            // inv_h2, D inv_h2, alpha as float pairs
     int n, P, item_begin, item_count;
     int df_ok;   // the coefficients are within the float-pair range (|alpha|, D inv_h2 < 2^60)
@@ -120,13 +120,16 @@ __global__ void k_sys_init(SysState *st, int count, SysCtl *ctl, double tol, int
     }
 }
 
-// Eigenvalues of [[3u^2, alpha], [-alpha, 3v^2]] (real parts), FP32: running extremes.
-__device__ __forceinline__ void sys_extremes(float uf, float vf, float alpha_f, float &mxp, float &mnm) {
+// Eigenvalues of [[3u^2, alpha], [-alpha, 3v^2]] (real parts), FP32: running extremes. Both
+// are >= 0, so they are kept as bit patterns under integer max / min, which the block then
+// reduces with one warp instruction each; a rounding below zero is clamped to +0.
+__device__ __forceinline__ void sys_extremes(float uf, float vf, float alpha_f, unsigned &mxb, unsigned &mnb) {
     const float a = 3.0f * uf * uf, d = 3.0f * vf * vf;
     const float disc = (a - d) * (a - d) - 4.0f * alpha_f * alpha_f;
     const float sq = disc > 0.0f ? disc * rsqrtf(disc) : 0.0f;   // beta needs no more than FP32 accuracy
-    mxp = fmaxf(mxp, 0.5f * (a + d + sq));
-    mnm = fminf(mnm, 0.5f * (a + d - sq));
+    const int hi = __float_as_int(0.5f * (a + d + sq)), lo = __float_as_int(0.5f * (a + d - sq));
+    mxb = max(mxb, (unsigned)max(hi, 0));
+    mnb = min(mnb, (unsigned)max(lo, 0));
 }
 
 // Kahan sum of (F_u 2^-k)^2 + (F_v 2^-k)^2 in FP32.
@@ -232,6 +235,15 @@ __device__ __forceinline__ void store_planes(const SysInst &I, int o, float Fuf,
     I.rv_lo[o] = l;
 }
 
+// Warp sum of the FP32 Kahan sums (k, -c) as float pairs; lane 0 stores it in out[warp].
+__device__ __forceinline__ void warp_pair_sum(float k, float c, float2 *out, int lane) {
+    float2 ps = make_float2(k, -c);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        ps = pair_add(ps, make_float2(__shfl_xor_sync(0xffffffffu, ps.x, o), __shfl_xor_sync(0xffffffffu, ps.y, o)));
+    if (lane == 0) out[threadIdx.x >> 5] = ps;
+}
+
 // One block per work item (instance, up to 8 rows of its padded P x P planes), one warp
 // per row, lanes along x. Iteration 0, and any iteration without a usable fixed-point
 // exponent, runs in FP64 (and writes the float-pair copies of f); later iterations
@@ -251,14 +263,18 @@ __global__ void __launch_bounds__(256, 3) k_sys_residual(const SysInst *__restri
     const int n = I.n, P = I.P;
     const int lane = threadIdx.x & 31;
     const int y = it.row0 + (threadIdx.x >> 5);
-    const double alpha = I.alpha, Dh2 = I.D * I.inv_h2;
-    const float alpha_f = (float)alpha;
+    const double alpha = I.alpha, Dh2 = I.Dh2;
+    const float alpha_f = I.al2.x;
     const float r2s = __int_as_float((127 - S.r2_exp) << 23);   // 2^-k
     float kr2 = 0.0f, kc = 0.0f;
-    double f2s = 0.0, r2 = 0.0;
-    float mxp = -INFINITY, mnm = INFINITY;
+    // per-warp partial sums for the block's partials (written at the end of either path)
+    __shared__ double sd[2][kTH];
+    __shared__ float2 sf[kTH];
+    __shared__ unsigned sx[2][kTH];
+    unsigned mxb = 0u, mnb = 0x7F800000u;   // +0 and +inf
     if (S.it == 0 || !S.df) {
         const bool first = S.it == 0;   // sum f^2 and r^2 in FP64, copy f as float pairs
+        double f2s = 0.0, r2 = 0.0;
         if (y < it.row1) {
             for (int x = lane; x < P; x += 32) {
                 float Fuf = 0.0f, Fvf = 0.0f;
@@ -268,7 +284,7 @@ __global__ void __launch_bounds__(256, 3) k_sys_residual(const SysInst *__restri
                     sys_node_fp64(I.U, I.V, I.f1, I.f2, c, x, y, n, alpha, I.inv_h2, Dh2, u, v, g1, g2, Fu, Fv);
                     Fuf = d2f_rn(Fu);
                     Fvf = d2f_rn(Fv);
-                    sys_extremes(d2f_rn(u), d2f_rn(v), alpha_f, mxp, mnm);
+                    sys_extremes(d2f_rn(u), d2f_rn(v), alpha_f, mxb, mnb);
                     if (first) {
                         const double2 s2 = first_iteration_sums(make_double2(f2s, r2), g1, g2, Fu, Fv);
                         f2s = s2.x;
@@ -282,7 +298,19 @@ __global__ void __launch_bounds__(256, 3) k_sys_residual(const SysInst *__restri
                 store_planes(I, y * P + x, Fuf, Fvf);
             }
         }
-        if (!first) r2 = ldexp((double)kr2 - (double)kc, 2 * S.r2_exp);
+        if (first) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+                f2s += __shfl_xor_sync(0xffffffffu, f2s, o);
+            }
+            if (lane == 0) {
+                sd[0][threadIdx.x >> 5] = r2;
+                sd[1][threadIdx.x >> 5] = f2s;
+            }
+        } else {
+            warp_pair_sum(kr2, kc, sf, lane);
+        }
     } else {
         __shared__ SysTile tile[2];
         __shared__ __align__(16) unsigned smax[2][kTH];
@@ -385,21 +413,45 @@ __global__ void __launch_bounds__(256, 3) k_sys_residual(const SysInst *__restri
                     uf = r.z;
                     vf = r.w;
                 }
-                sys_extremes(uf, vf, alpha_f, mxp, mnm);
+                sys_extremes(uf, vf, alpha_f, mxb, mnb);
                 sys_r2(Fuf, Fvf, r2s, kr2, kc);
             }
             store_planes(I, y * P + x, Fuf, Fvf);
         }
-        r2 = ldexp((double)kr2 - (double)kc, 2 * S.r2_exp);
+        warp_pair_sum(kr2, kc, sf, lane);
     }
-    Red4 acc{r2, f2s, (double)mxp, (double)mnm};
-    acc = block_red(acc);
+    // Block partials. Iteration 0 sums f^2 and r^2 in FP64; later iterations add the FP32
+    // Kahan sums of (r 2^-k)^2 as float pairs and the extremes by integer max / min, so the
+    // FP64 pipe (16 cycles per warp instruction) only sees thread 0's last additions.
+    const bool first = S.it == 0;
+    mxb = __reduce_max_sync(0xffffffffu, mxb);
+    mnb = __reduce_min_sync(0xffffffffu, mnb);
+    if (lane == 0) {
+        sx[0][threadIdx.x >> 5] = mxb;
+        sx[1][threadIdx.x >> 5] = mnb;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        double a = 0.0, f = 0.0;
+        unsigned mx = 0u, mn = 0x7F800000u;
+        float2 ps = make_float2(0.0f, 0.0f);
+        for (int i = 0; i < kTH; ++i) {
+            if (first) {
+                a += sd[0][i];
+                f += sd[1][i];
+            } else {
+                ps = pair_add(ps, sf[i]);
+            }
+            mx = max(mx, sx[0][i]);
+            mn = min(mn, sx[1][i]);
+        }
+        if (!first)   // (hi + lo) 2^(2k); 2k in [-240, 240], a normal power of two
+            a = ((double)ps.x + (double)ps.y) * __longlong_as_double((long long)(1023 + 2 * S.r2_exp) << 52);
         double *p = partials + 4ll * blockIdx.x;
-        p[0] = acc.r2;
-        p[1] = acc.f2;
-        p[2] = acc.mx;
-        p[3] = acc.mn;
+        p[0] = a;
+        p[1] = f;
+        p[2] = (double)__uint_as_float(mx);
+        p[3] = (double)__uint_as_float(mn);
     }
 }
 
@@ -699,6 +751,7 @@ extern "C" int qn_batch_create(const qn_sys_instance *inst, int count, int bk, c
         s.D = inst[i].D;
         const double h = 1.0 / (inst[i].n + 1);
         s.inv_h2 = 1.0 / (h * h);
+        s.Dh2 = s.D * s.inv_h2;
         s.ih2 = pair_host(s.inv_h2);
         s.dh2 = pair_host(s.D * s.inv_h2);
         s.al2 = pair_host(s.alpha);
