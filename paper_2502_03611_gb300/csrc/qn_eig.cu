@@ -86,6 +86,58 @@ __device__ Sum4 block_sum3(Sum4 v) {
     return v;
 }
 
+// Block reduction of NS float-pair sums (and, with MM, an FP32 min / max) with no FP64 warp
+// instruction: GB300 issues those at about 16 cycles per warp, which for a few hundred
+// blocks per launch adds up. Thread 0 receives {s0, s1, s2 or min, max} in FP64.
+__device__ __forceinline__ float2 shfl_pair(float2 v, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
+template <int NS, bool MM>
+__device__ Sum4 block_pair_red(float2 s0, float2 s1, float2 s2, float mn, float mx) {
+    __shared__ float2 shs[3][32];
+    __shared__ float shm[2][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 = pair_add(s0, shfl_pair(s0, o));
+        if (NS > 1) s1 = pair_add(s1, shfl_pair(s1, o));
+        if (NS > 2) s2 = pair_add(s2, shfl_pair(s2, o));
+        if (MM) {
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        shs[0][w] = s0;
+        shs[1][w] = s1;
+        shs[2][w] = s2;
+        shm[0][w] = mn;
+        shm[1][w] = mx;
+    }
+    __syncthreads();
+    Sum4 r{0.0, 0.0, 0.0, 0.0};
+    if (threadIdx.x == 0) {
+        const float2 z = make_float2(0.0f, 0.0f);
+        float2 a = z, b = z, c = z;
+        float m0 = INFINITY, m1 = -INFINITY;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            a = pair_add(a, shs[0][i]);
+            if (NS > 1) b = pair_add(b, shs[1][i]);
+            if (NS > 2) c = pair_add(c, shs[2][i]);
+            if (MM) {
+                m0 = fminf(m0, shm[0][i]);
+                m1 = fmaxf(m1, shm[1][i]);
+            }
+        }
+        r.a = (double)a.x + (double)a.y;
+        r.b = (double)b.x + (double)b.y;
+        r.mn = (NS > 2) ? (double)c.x + (double)c.y : (double)m0;
+        r.mx = (double)m1;
+    }
+    return r;
+}
+
 __device__ __forceinline__ bool state_done(const DevState *st) { return *(volatile const int *)&st->done != 0; }
 
 // 1-D trapezoid weight of node i (the lumped mass without h).
@@ -171,9 +223,13 @@ __global__ void __launch_bounds__(256) k_eig_finalize1(const double *partials, i
     if (threadIdx.x != 0) return;
     const double E1 = acc.a, E4 = acc.b, Q = acc.mn;
     const double s2 = 1.0 / (hd * Q);                  // ||s U~||^2 = s^2 h^d Q = 1
-    st->eig_scale = sqrt(s2);
+    const double sc = sqrt(s2);
+    st->eig_scale = sc;
     const double lam_n = (E1 + s2 * E4) / Q;           // <A U + f(U), U> / <U, U> at U = s U~
     st->eig_lambda = lam_n;
+    const float sh = __double2float_rn(sc), lh = __double2float_rn(lam_n);
+    st->eig_scale2 = make_float2(sh, __double2float_rn(sc - (double)sh));
+    st->eig_lambda2 = make_float2(lh, __double2float_rn(lam_n - (double)lh));
     st->f_norm = fabs(lam_n);                          // |lambda_n| ||U||, ||U|| = 1
 }
 
@@ -538,8 +594,7 @@ __global__ void __launch_bounds__(256, 3) k_eig_pass1_tiled(const double *__rest
         }
         __syncthreads();   // the next item's first plane reuses sp[0]
     }
-    Sum4 acc{pair_to_double(e1), pair_to_double(e4), pair_to_double(q), 0.0};
-    acc = block_sum3(acc);
+    const Sum4 acc = block_pair_red<3, false>(e1, e4, q, 0.0f, 0.0f);
     if (threadIdx.x == 0) {
         double *p = partials + 4ll * blockIdx.x;
         p[0] = acc.a;
@@ -582,21 +637,15 @@ __device__ __forceinline__ float eig_point_df(double *__restrict__ U, const floa
     return Ff;
 }
 
-__device__ __forceinline__ float2 pair_of(double v) {
-    const float hi = __double2float_rn(v);
-    return make_float2(hi, __double2float_rn(v - (double)hi));
-}
-
 template <int DIM, int OUT, bool NEU>
 __global__ void __launch_bounds__(256) k_eig_pass2_df(double *__restrict__ U, const float2 *__restrict__ lin, int n,
-                                                      int P, double hd, float lamf, double b,
+                                                      int P, double hd, float lamf, float2 b2, float b3f,
                                                       const float *__restrict__ pot32, __nv_bfloat16 *__restrict__ Rhi,
                                                       __nv_bfloat16 *__restrict__ Rlo, double *__restrict__ partials,
                                                       DevState *st) {
     if (state_done(st)) return;
     const double sc = st->eig_scale;
-    const float2 sc2 = pair_of(sc), lamn2 = pair_of(st->eig_lambda), b2 = pair_of(b);
-    const float b3f = (float)(3.0 * b);
+    const float2 sc2 = st->eig_scale2, lamn2 = st->eig_lambda2;   // b2 = b, b3f = 3 b: from the host
     float sk = 0.0f, kc = 0.0f, dmn = INFINITY, dmx = -INFINITY;
     unsigned long long umax = 0ull;
     // one warp per output row of the padded planes, lanes along its x axis
@@ -658,8 +707,9 @@ __global__ void __launch_bounds__(256) k_eig_pass2_df(double *__restrict__ U, co
         umax = v > umax ? v : umax;
     }
     if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = umax;
-    Sum4 acc{hd * ((double)sk - (double)kc), 0.0, (double)dmn, (double)dmx};
-    acc = block_sum4(acc);   // (its __syncthreads also orders shm)
+    Sum4 acc = block_pair_red<1, true>(make_float2(sk, -kc), make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), dmn,
+                                       dmx);   // (its __syncthreads also orders shm)
+    acc.a *= hd;
     if (threadIdx.x == 0) {
         unsigned long long m = 0ull;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = shm[i] > m ? shm[i] : m;
@@ -803,10 +853,15 @@ template <int DIM, int OUT>
 static void pass2_df_t(double *U, const float2 *lin, int n, int P, bool neu, double hd, float lam, double b,
                        const float *pot32, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, double *partials, int grid,
                        DevState *st, cudaStream_t s) {
+    const float bh = (float)b;
+    const float2 b2 = make_float2(bh, (float)(b - (double)bh));
+    const float b3f = (float)(3.0 * b);
     if (neu)
-        k_eig_pass2_df<DIM, OUT, true><<<grid, 256, 0, s>>>(U, lin, n, P, hd, lam, b, pot32, Rhi, Rlo, partials, st);
+        k_eig_pass2_df<DIM, OUT, true><<<grid, 256, 0, s>>>(U, lin, n, P, hd, lam, b2, b3f, pot32, Rhi, Rlo, partials,
+                                                             st);
     else
-        k_eig_pass2_df<DIM, OUT, false><<<grid, 256, 0, s>>>(U, lin, n, P, hd, lam, b, pot32, Rhi, Rlo, partials, st);
+        k_eig_pass2_df<DIM, OUT, false><<<grid, 256, 0, s>>>(U, lin, n, P, hd, lam, b2, b3f, pot32, Rhi, Rlo, partials,
+                                                              st);
 }
 
 int launch_eig_pass2_df(double *U, const float2 *lin, int n, int P, int dim, int bc, double hd, float lam, double b,

@@ -39,6 +39,7 @@ struct DevState {
     unsigned long long umax_scan;   // max|U| bit pattern from a scan pass (k_prep_split, k_umax)
     double eig_lambda;   // eigen solves: Rayleigh quotient lambda_n of the current iterate
     double eig_scale;    //   and the normalisation factor 1/||U~|| applied to it
+    float2 eig_lambda2, eig_scale2;   // the same two as FP32 pairs (hi, lo)
 };
 
 // Residual kernel outputs.
