@@ -226,6 +226,14 @@ int qn_solve(qn_ctx *ctx, double *U, const double *f, const qn_opts *opts,
 int qn_solve_host(qn_ctx *ctx, double *U_host, const double *f_host, const qn_opts *opts,
                   qn_result *res, qn_stats *history, int history_len, void *stream);
 
+/* qn_solve_host from the zero start U_0 = 0 (the start of the paper's FD and SEM
+ * runs): only f_host is copied to the device; U_host is output only (its
+ * contents on entry are ignored) and receives the result. Same arguments, errors
+ * and synchronisation as qn_solve_host; the iterates and the result are those
+ * of qn_solve_host with U_host = 0. */
+int qn_solve_host_zero_start(qn_ctx *ctx, double *U_host, const double *f_host, const qn_opts *opts,
+                             qn_result *res, qn_stats *history, int history_len, void *stream);
+
 /* Allocation-free variant of qn_residual, for callers that cannot allocate
  * device memory where they need a residual: their device memory is owned in
  * full by another allocator or a fixed budget, or they run in a section that
@@ -250,7 +258,9 @@ int qn_residual_noalloc(int dim, int n, double lam, double b, const double *U, c
  * Many independent 2-D instances of
  *   -Lap u + u^3 + alpha v = f1,   -D Lap v + v^3 - alpha u = f2   (Dirichlet 0)
  * with uneven grid sizes, solved together. Each iteration evaluates both
- * residuals (FP64), takes one beta per instance as the midpoint of the extreme
+ * residuals (iteration 0 in FP64; later ones on an exact fixed-point stencil
+ * with float-pair arithmetic, ~48 significant bits, FP64 for any value of 2^37
+ * or more), takes one beta per instance as the midpoint of the extreme
  * eigenvalues of the 2x2 blocks [[3u^2, alpha], [-alpha, 3v^2]] over all nodes
  * (Sec. 4.3 eqs. eigen_quad, eigenvalues; real parts when the pair is complex),
  * and updates u -= (A_h + beta I)^{-1} F_u, v -= (D A_h + beta I)^{-1} F_v by

@@ -1036,12 +1036,14 @@ int qn::solve_internal(qn_ctx *c, double *U, const double *f, const qn_opts *opt
     return status;
 }
 
-extern "C" int qn_solve_host(qn_ctx *c, double *U_host, const double *f_host, const qn_opts *opts,
-                             qn_result *res, qn_stats *history, int history_len, void *stream) {
+// Host-array solve: f_host (and, unless zero_start, the start U_host) to context-owned
+// device buffers, the solve, the result back into U_host.
+static int solve_host(qn_ctx *c, double *U_host, const double *f_host, bool zero_start, const qn_opts *opts,
+                      qn_result *res, qn_stats *history, int history_len, void *stream, const char *who) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (bad_ptr(U_host) || bad_ptr(f_host)) {
-        set_error("qn_solve_host: null U_host or f_host");
+        set_error("%s: null U_host or f_host", who);
         return QN_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -1051,12 +1053,26 @@ extern "C" int qn_solve_host(qn_ctx *c, double *U_host, const double *f_host, co
         QN_CUDA(cudaMalloc(&c->df, bytes));
     }
     QN_CUDA(cudaMemcpyAsync(c->df, f_host, bytes, cudaMemcpyHostToDevice, s));
-    QN_CUDA(cudaMemcpyAsync(c->dU, U_host, bytes, cudaMemcpyHostToDevice, s));
+    if (zero_start)
+        QN_CUDA(cudaMemsetAsync(c->dU, 0, bytes, s));   // +0.0 is all-zero bits
+    else
+        QN_CUDA(cudaMemcpyAsync(c->dU, U_host, bytes, cudaMemcpyHostToDevice, s));
     rc = qn_solve(c, c->dU, c->df, opts, res, history, history_len, stream);
     if (rc != QN_OK && rc != QN_ENOTCONV && rc != QN_EDIVERGED) return rc;
     QN_CUDA(cudaMemcpyAsync(U_host, c->dU, bytes, cudaMemcpyDeviceToHost, s));
     QN_CUDA(cudaStreamSynchronize(s));
     return rc;
+}
+
+extern "C" int qn_solve_host(qn_ctx *c, double *U_host, const double *f_host, const qn_opts *opts,
+                             qn_result *res, qn_stats *history, int history_len, void *stream) {
+    return solve_host(c, U_host, f_host, false, opts, res, history, history_len, stream, "qn_solve_host");
+}
+
+extern "C" int qn_solve_host_zero_start(qn_ctx *c, double *U_host, const double *f_host, const qn_opts *opts,
+                                        qn_result *res, qn_stats *history, int history_len, void *stream) {
+    return solve_host(c, U_host, f_host, true, opts, res, history, history_len, stream,
+                      "qn_solve_host_zero_start");
 }
 
 extern "C" int qn_profile_enable(qn_ctx *c, int on) {

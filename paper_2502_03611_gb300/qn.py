@@ -123,6 +123,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "qn_step": (ctypes.c_int, [P, P, P, ctypes.c_double, ctypes.POINTER(QnStats), P]),
         "qn_solve": (ctypes.c_int, [P, P, P, ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult),
                                     ctypes.POINTER(QnStats), ctypes.c_int, P]),
+        "qn_solve_host_zero_start": (ctypes.c_int, [P, P, P, ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult),
+                                                    ctypes.POINTER(QnStats), ctypes.c_int, P]),
         "qn_solve_host": (ctypes.c_int, [P, P, P, ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult),
                                          ctypes.POINTER(QnStats), ctypes.c_int, P]),
         "qn_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
@@ -344,16 +346,19 @@ def qn_eig_solve(ctx: QnContext, U, tol=1e-10, max_it=4096, beta=None, step=1.0,
 
 
 def qn_solve_host(ctx: QnContext, U_host: np.ndarray, f_host: np.ndarray, tol=1e-10, max_it=200,
-                  beta=None, step=1.0, sync_every=2, stream=None, graph=False):
-    """Solve with host arrays (copies inside the call). U_host is updated in place."""
+                  beta=None, step=1.0, sync_every=2, stream=None, graph=False, zero_start=False):
+    """Solve with host arrays (copies inside the call). U_host is updated in place; with
+    zero_start the solve starts from U = 0 and U_host is output only (qn_solve_host_zero_start:
+    no copy of a start)."""
     for name, a in (("U_host", U_host), ("f_host", f_host)):
         if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != ctx.numel:
             raise ValueError(f"{name} must be a C-contiguous float64 array of {ctx.numel} values")
     opts = make_opts(tol, max_it, beta, step, sync_every, graph)
     res = QnResult()
-    rc = load_library().qn_solve_host(ctx.handle, ctypes.c_void_p(U_host.ctypes.data),
-                                      ctypes.c_void_p(f_host.ctypes.data), ctypes.byref(opts),
-                                      ctypes.byref(res), None, 0, _stream_ptr(stream))
+    lib = load_library()
+    fn = lib.qn_solve_host_zero_start if zero_start else lib.qn_solve_host
+    rc = fn(ctx.handle, ctypes.c_void_p(U_host.ctypes.data), ctypes.c_void_p(f_host.ctypes.data),
+            ctypes.byref(opts), ctypes.byref(res), None, 0, _stream_ptr(stream))
     _check(rc, allowed=(QN_OK, QN_ENOTCONV, QN_EDIVERGED))
     return {"iterations": res.iterations, "status": res.status, "rel": res.rel, "rc": rc}
 

@@ -299,6 +299,12 @@ def test_solve_host_arrays(qn):
     Uo, _, _ = O.qn_solve(f)
     assert res["status"] == 0
     assert np.abs(U.reshape(f.shape) - Uo).max() <= 1e-9 * np.abs(Uo).max()
+    # the zero-start entry point copies only f: same iterates, bit for bit; U_host's
+    # contents on entry are ignored
+    U2 = np.full(n ** 3, 7.5)
+    res2 = qn.qn_solve_host(ctx, U2, np.ascontiguousarray(f.reshape(-1)), zero_start=True)
+    assert res2["iterations"] == res["iterations"] and res2["status"] == 0
+    assert np.array_equal(U2, U)
 
 
 # --------------------------------------------------------------------------------------------
