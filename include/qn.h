@@ -254,6 +254,18 @@ int qn_solve_host_zero_start(qn_ctx *ctx, double *U_host, const double *f_host, 
 int qn_residual_noalloc(int dim, int n, double lam, double b, const double *U, const double *f,
                         double *R, qn_stats *st, void *stream);
 
+/* Test-only fault injection for the bounded device waits (no GPU fault, no hang):
+ * the next tensor-core mode-product launch in this process has the TMA producer
+ * of its block 0 skip its first stage, so that stage's barrier never completes.
+ * The MMA issuer and the epilogue give up after 2 s of %globaltimer, set
+ * QN_ETIMEOUT in the launch's error word and return; nothing is left in flight
+ * (no MMA was issued, the other stages' loads are drained), and the device and
+ * the context stay usable. The solve or product call that contains the launch
+ * returns QN_ETIMEOUT when it reads that word (qn_solve at its next convergence
+ * check). Only the one launch is affected (the request is taken atomically).
+ * Returns QN_OK, or QN_ECUDA without a device. */
+int qn_test_withhold_arrival(void);
+
 /* ---- batched coupled two-component systems (Sec. 4.3) ---------------------------
  * Many independent 2-D instances of
  *   -Lap u + u^3 + alpha v = f1,   -D Lap v + v^3 - alpha u = f2   (Dirichlet 0)

@@ -1075,6 +1075,8 @@ extern "C" int qn_solve_host_zero_start(qn_ctx *c, double *U_host, const double 
                       "qn_solve_host_zero_start");
 }
 
+extern "C" int qn_test_withhold_arrival(void) { return tc_test_withhold_arrival(); }
+
 extern "C" int qn_profile_enable(qn_ctx *c, int on) {
     int rc = check_ctx(c);
     if (rc) return rc;

@@ -208,6 +208,8 @@ bool tc_plan_has_split(const TcPlan *plan);
 // EPI_STORE_PQ / EPI_UPDATE_PQ (backward).
 int launch_modeprod_tc_split(TcPlan *plan, int src, int dst, Epi epi, const EpiArgs &e, cudaStream_t s);
 // Grouped launch over a device tile table (batched solves).
+// Test-only: the next k_modeprod_tc launch has block 0's producer withhold its first stage.
+int tc_test_withhold_arrival();
 int launch_modeprod_tc_grouped(const TcGroup *groups, const TcTile *tiles, int ntiles, int dim, int BK,
                                Epi epi, int *err, int grid, cudaStream_t s);
 // Encode a 2-D BF16 tensor map [outer][inner] with a (box_inner x box_outer) box.

@@ -76,6 +76,13 @@ constexpr uint32_t kTmemCols = 2 * BN_MAX;         // two accumulators of BN_MAX
 // rows wide, so their stages are 64 KB and three fit in shared memory
 __host__ __device__ constexpr int bn_slot(int mode) { return mode == 2 ? 128 : BN_MAX; }
 
+// Test-only fault injection (qn_test_withhold_arrival): when set, the TMA producer of
+// block 0 of the next launch takes it (atomically, so one launch is affected) and skips
+// its first stage, whose full barrier then never completes; the MMA issuer and the
+// epilogue give up after kTimeoutNs and report QN_ETIMEOUT. Nothing is left in flight:
+// no MMA was issued and the other stages' loads are drained.
+__device__ int g_tc_withhold = 0;
+
 // Wait for `parity` on `bar`; false on timeout or when another role aborted.
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort_flag,
                                          int *err) {
@@ -194,6 +201,7 @@ __global__ void __maxnreg__(104)
         int s = 0;
         uint32_t ph = 0;
         bool ok = true;
+        bool withhold = (blockIdx.x == 0) && atomicExch(&g_tc_withhold, 0) != 0;
         for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
             TcGroup G;
             int m0, n0;
@@ -217,13 +225,17 @@ __global__ void __maxnreg__(104)
                     by = (second ? Hh : 0) + n0;
                 }
                 const uint32_t st = base + (uint32_t)s * stage_bytes;
-                ptx::mbar_arrive_expect_tx(full_bar(s), tx_bytes);
-                ptx::tma_load_2d(st, G.a_hi, full_bar(s), ax, m0);
-                ptx::tma_load_2d(st + a_bytes, G.a_lo, full_bar(s), ax, m0);
-                ptx::tma_load_2d(st + 2 * a_bytes, G.b_hi, full_bar(s), bx, by);
-                ptx::tma_load_2d(st + 2 * a_bytes + b_bytes_max, G.b_lo, full_bar(s), bx, by);
-                armed_parity[s] = ph;
-                armed_mask |= 1u << s;
+                if (withhold) {   // test-only: this stage is never armed
+                    withhold = false;
+                } else {
+                    ptx::mbar_arrive_expect_tx(full_bar(s), tx_bytes);
+                    ptx::tma_load_2d(st, G.a_hi, full_bar(s), ax, m0);
+                    ptx::tma_load_2d(st + a_bytes, G.a_lo, full_bar(s), ax, m0);
+                    ptx::tma_load_2d(st + 2 * a_bytes, G.b_hi, full_bar(s), bx, by);
+                    ptx::tma_load_2d(st + 2 * a_bytes + b_bytes_max, G.b_lo, full_bar(s), bx, by);
+                    armed_parity[s] = ph;
+                    armed_mask |= 1u << s;
+                }
                 if (++s == stages) {
                     s = 0;
                     ph ^= 1u;
@@ -791,6 +803,12 @@ int launch_modeprod_tc(TcPlan *p, int src, int dst, bool forward, Epi epi, const
     g.ntile_n = p->ntile_n;
     g.ntiles = p->ntiles;
     return launch_any(p->BK, p->dim, epi, g, nullptr, nullptr, p->ntiles, p->stages, e.err, p->grid, s);
+}
+
+int tc_test_withhold_arrival() {
+    const int one = 1;
+    QN_CUDA(cudaMemcpyToSymbol(g_tc_withhold, &one, sizeof(int)));
+    return QN_OK;
 }
 
 int launch_modeprod_tc_grouped(const TcGroup *groups, const TcTile *tiles, int ntiles, int dim, int BK, Epi epi,

@@ -128,6 +128,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "qn_solve_host": (ctypes.c_int, [P, P, P, ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult),
                                          ctypes.POINTER(QnStats), ctypes.c_int, P]),
         "qn_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
+        "qn_test_withhold_arrival": (ctypes.c_int, []),
         "qn_residual_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                P, P, P, ctypes.POINTER(QnStats), P]),
         "qn_batch_create": (ctypes.c_int, [ctypes.POINTER(QnSysInstance), ctypes.c_int, ctypes.c_int,
@@ -361,6 +362,12 @@ def qn_solve_host(ctx: QnContext, U_host: np.ndarray, f_host: np.ndarray, tol=1e
             ctypes.byref(opts), ctypes.byref(res), None, 0, _stream_ptr(stream))
     _check(rc, allowed=(QN_OK, QN_ENOTCONV, QN_EDIVERGED))
     return {"iterations": res.iterations, "status": res.status, "rel": res.rel, "rc": rc}
+
+
+def qn_test_withhold_arrival():
+    """Test-only: the next tensor-core mode-product launch withholds one TMA arrival and its
+    waits give up after 2 s with QN_ETIMEOUT (bounded; no GPU fault)."""
+    _check(load_library().qn_test_withhold_arrival())
 
 
 def qn_profile_enable(ctx: QnContext, on: bool = True):
