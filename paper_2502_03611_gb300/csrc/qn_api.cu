@@ -61,6 +61,7 @@ struct qn_ctx {
     double *w64[2];
     __nv_bfloat16 *bhi[2], *blo[2];
     double *partials;
+    int partials_cap;     // records the partials buffer holds (>= nparts; eigen pass 2 may use more)
     int nparts;
     DevState *st;
     qn_stats *hist;
@@ -450,7 +451,8 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
 
     const int rows = (c->dim == 3) ? P * P : P;
     c->nparts = rows < 4 * c->num_sms ? rows : 4 * c->num_sms;
-    CK(cudaMalloc(&c->partials, sizeof(double) * 4 * c->nparts));
+    c->partials_cap = c->nparts > 8 * c->num_sms ? c->nparts : 8 * c->num_sms;
+    CK(cudaMalloc(&c->partials, sizeof(double) * 4 * c->partials_cap));
     CK(cudaMalloc(&c->st, sizeof(DevState)));
     CK(cudaMalloc(&c->hist, sizeof(qn_stats) * kHistCap));
     CK(cudaMalloc(&c->err, sizeof(int)));
@@ -1150,9 +1152,11 @@ static int enqueue_eig_iteration(qn_ctx *c, double *U, double step, cudaStream_t
     prof_end(c, pr, s);
     if (rc) return rc;
     pr = prof_begin(c, PK_RESIDUAL, s);
+    int grid2 = grid;   // blocks (partial sums) of pass 2
     if (df)
         rc = launch_eig_pass2_df(U, lin2, c->n, c->P, c->dim, c->prob.bc, hd, (float)c->prob.lam, c->prob.b,
-                                 c->eig_pot32, c->bhi[0], c->blo[0], mirror, c->partials, grid, c->st, s);
+                                 c->eig_pot32, c->bhi[0], c->blo[0], mirror, c->partials, c->partials_cap, &grid2,
+                                 c->st, s);
     else
         rc = launch_eig_pass2(U, lin, c->n, c->P, c->dim, c->prob.bc, hd, (float)c->prob.lam, c->prob.b,
                               c->eig_pot32, fp64 ? c->w64[0] : nullptr, fp64 ? nullptr : c->bhi[0],
@@ -1160,7 +1164,7 @@ static int enqueue_eig_iteration(qn_ctx *c, double *U, double step, cudaStream_t
     prof_end(c, pr, s);
     if (rc) return rc;
     pr = prof_begin(c, PK_FINALIZE, s);
-    rc = launch_finalize(c->partials, grid, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 1, 1, 2, s);
+    rc = launch_finalize(c->partials, grid2, c->st, c->hist, kHistCap, c->prob.b, c->prob.lam, 1, 1, 2, s);
     prof_end(c, pr, s);
     if (rc) return rc;
     return enqueue_inverse(c, nullptr, U, true, step, s, mirror);

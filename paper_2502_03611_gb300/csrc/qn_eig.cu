@@ -638,7 +638,7 @@ __device__ __forceinline__ float eig_point_df(double *__restrict__ U, const floa
 }
 
 template <int DIM, int OUT, bool NEU>
-__global__ void __launch_bounds__(256) k_eig_pass2_df(double *__restrict__ U, const float2 *__restrict__ lin, int n,
+__global__ void __launch_bounds__(256, NEU ? 4 : 5) k_eig_pass2_df(double *__restrict__ U, const float2 *__restrict__ lin, int n,
                                                       int P, double hd, float lamf, float2 b2, float b3f,
                                                       const float *__restrict__ pot32, __nv_bfloat16 *__restrict__ Rhi,
                                                       __nv_bfloat16 *__restrict__ Rlo, double *__restrict__ partials,
@@ -850,35 +850,52 @@ int launch_eig_pass1_df(const double *U, float2 *lin, int n, int dim, int bc, do
 }
 
 template <int DIM, int OUT>
-static void pass2_df_t(double *U, const float2 *lin, int n, int P, bool neu, double hd, float lam, double b,
-                       const float *pot32, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, double *partials, int grid,
-                       DevState *st, cudaStream_t s) {
+static int pass2_df_t(double *U, const float2 *lin, int n, int P, bool neu, double hd, float lam, double b,
+                      const float *pot32, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, double *partials, int grid,
+                      int *used, DevState *st, cudaStream_t s) {
     const float bh = (float)b;
     const float2 b2 = make_float2(bh, (float)(b - (double)bh));
     const float b3f = (float)(3.0 * b);
+    // one wave of resident blocks (5 per SM for the Dirichlet forms), at most `grid`
+    int dev = 0, sms = 0, nb = 0;
+    QN_CUDA(cudaGetDevice(&dev));
+    QN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (neu)
-        k_eig_pass2_df<DIM, OUT, true><<<grid, 256, 0, s>>>(U, lin, n, P, hd, lam, b2, b3f, pot32, Rhi, Rlo, partials,
-                                                             st);
+        QN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eig_pass2_df<DIM, OUT, true>, 256, 0));
     else
-        k_eig_pass2_df<DIM, OUT, false><<<grid, 256, 0, s>>>(U, lin, n, P, hd, lam, b2, b3f, pot32, Rhi, Rlo, partials,
-                                                              st);
+        QN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eig_pass2_df<DIM, OUT, false>, 256, 0));
+    const long long rows = (OUT == 2 || DIM == 3) ? (long long)P * P : P;   // one warp per output row
+    long long g = (long long)(nb > 0 ? nb : 1) * sms;
+    if (g > grid) g = grid;
+    if (g > (rows + 7) / 8) g = (rows + 7) / 8;
+    if (g < 1) g = 1;
+    if (neu)
+        k_eig_pass2_df<DIM, OUT, true><<<(int)g, 256, 0, s>>>(U, lin, n, P, hd, lam, b2, b3f, pot32, Rhi, Rlo,
+                                                                partials, st);
+    else
+        k_eig_pass2_df<DIM, OUT, false><<<(int)g, 256, 0, s>>>(U, lin, n, P, hd, lam, b2, b3f, pot32, Rhi, Rlo,
+                                                                 partials, st);
+    *used = (int)g;
+    return QN_OK;
 }
 
 int launch_eig_pass2_df(double *U, const float2 *lin, int n, int P, int dim, int bc, double hd, float lam, double b,
                         const float *pot32, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, bool mirror, double *partials,
-                        int grid, DevState *st, cudaStream_t s) {
+                        int grid, int *used, DevState *st, cudaStream_t s) {
     const bool neu = (bc == QN_BC_NEUMANN);
+    int rc;
     if (mirror) {
         if (dim != 3 || P % 128 != 0) {
             set_error("launch_eig_pass2_df: the reflection-split layout needs 3-D and P a multiple of 128");
             return QN_EINVAL;
         }
-        pass2_df_t<3, 2>(U, lin, n, P, neu, hd, lam, b, pot32, Rhi, Rlo, partials, grid, st, s);
+        rc = pass2_df_t<3, 2>(U, lin, n, P, neu, hd, lam, b, pot32, Rhi, Rlo, partials, grid, used, st, s);
     } else if (dim == 3) {
-        pass2_df_t<3, 1>(U, lin, n, P, neu, hd, lam, b, pot32, Rhi, Rlo, partials, grid, st, s);
+        rc = pass2_df_t<3, 1>(U, lin, n, P, neu, hd, lam, b, pot32, Rhi, Rlo, partials, grid, used, st, s);
     } else {
-        pass2_df_t<2, 1>(U, lin, n, P, neu, hd, lam, b, pot32, Rhi, Rlo, partials, grid, st, s);
+        rc = pass2_df_t<2, 1>(U, lin, n, P, neu, hd, lam, b, pot32, Rhi, Rlo, partials, grid, used, st, s);
     }
+    if (rc) return rc;
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }

@@ -155,7 +155,7 @@ int launch_eig_pass1_df(const double *U, float2 *lin, int n, int dim, int bc, do
                         double *partials, int grid, int *used, const DevState *st, cudaStream_t s);
 int launch_eig_pass2_df(double *U, const float2 *lin, int n, int P, int dim, int bc, double hd, float lam, double b,
                         const float *pot32, __nv_bfloat16 *Rhi, __nv_bfloat16 *Rlo, bool mirror, double *partials,
-                        int grid, DevState *st, cudaStream_t s);
+                        int grid, int *used, DevState *st, cudaStream_t s);   // grid: at most; used: launched
 // exactly one of R64 (FP64 output) or Rhi/Rlo (split planes; mirror: reflection-split order)
 // pot32: the potential tables in FP32 (for beta's extremes only), or nullptr
 int launch_eig_pass2(double *U, const double *lin, int n, int P, int dim, int bc, double hd, float lam, double b,
