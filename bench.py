@@ -39,6 +39,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -117,7 +118,8 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples (transient; the JSON line carries their summary)
+        self.path = os.path.join(tempfile.gettempdir(), f"qn_bench_clocks_rank{index}_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -159,6 +161,10 @@ class ClockSampler:
                 except ValueError:
                     continue
         # the samples of the timed region; the last earlier one if it was shorter than a period
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         skip = getattr(self, "skip", 0)
         rows = rows[skip:] if len(rows) > skip else rows[-1:]
         if not rows:
