@@ -159,7 +159,7 @@ static void split_host(double v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
     lo = __float2bfloat16_rn(f - __bfloat162float(hi));
 }
 
-extern "C" int qn_version(void) { return 10100; }
+extern "C" int qn_version(void) { return 10200; }
 
 extern "C" const char *qn_last_error(void) { return g_err; }
 
