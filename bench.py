@@ -2,8 +2,10 @@
 """Benchmark: time to relative residual 1e-10 for -Lap u + u^3 = f on the
 3-D 511^3 interior grid (Dirichlet 0, 7-point differences), quasi-Newton with
 the fast-diagonalisation inverse, mode products in BF16x3 split precision on
-the tensor cores, residual / update / stop test in FP64. Zero start,
-manufactured source (6x6x6 random sine modes, seed-drawn), synthetic data.
+the tensor cores. The residual of the split solve sums the stencil exactly in
+int64 fixed point and the rest in FP32 pairs (iteration 0 in FP64); U, the
+update and the stop test's denominator stay FP64. Zero start, manufactured
+source (6x6x6 random sine modes, seed-drawn), synthetic data.
 
 One step = one complete solve (every iteration: residual + reductions, beta_n
 and stop test, 3 forward mode products with the eigen-sum divide, 3 backward
@@ -72,10 +74,14 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched coupled-systems measurement")
     ap.add_argument("--tiles", default="auto",
                     help="batched tiles: 'auto' (autotuner) or BK:BN63,BN127,BN255,BN511, e.g. 64:64,64,128,256")
-    ap.add_argument("--quick", action="store_true", help="= --no-fp64 --no-cpu --no-e2e --no-batched")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 2-D 63^2 FP64, 3-D 255^3 FP64 and warm-start legs of the default line")
+    ap.add_argument("--no-warm", action="store_true", help="skip the warm-start leg (training takes ~100 s)")
+    ap.add_argument("--oracle-sample", default=None, choices=["c1", "c2"], help=argparse.SUPPRESS)
+    ap.add_argument("--quick", action="store_true", help="= --no-fp64 --no-cpu --no-e2e --no-batched --no-configs")
     a = ap.parse_args()
     if a.quick:
-        a.no_fp64 = a.no_cpu = a.no_e2e = a.no_batched = True
+        a.no_fp64 = a.no_cpu = a.no_e2e = a.no_batched = a.no_configs = True
     if a.n is None:
         a.n = {"dirichlet": 511, "sem": 255}.get(a.workload, 200)
     return a
@@ -194,30 +200,6 @@ def ncu_traffic(kernel_file: str):
     return d.get("dram_bytes_per_launch")
 
 
-def cpu_oracle_baseline(n: int, seed: int, iters_timed: int = 1):
-    """Time the FP64 oracle on the host cores: iters_timed quasi-Newton
-    iterations at n^3 (the full solve takes minutes), scaled by the iteration
-    count the oracle needs on the same problem family at 127^3 (the count is
-    mesh-independent, Sec. 6). Returns (ms per solve estimate, details)."""
-    import numpy as np
-    import oracle as O
-    from paper_2502_03611_gb300.inputs import manufactured_problem
-    _, f_small = manufactured_problem(127, 3, seed=seed)
-    _, h_small, _ = O.qn_solve(f_small)
-    its = len(h_small) - 1
-    _, f = manufactured_problem(n, 3, seed=seed)
-    eig = O.eig_1d(n)
-    U = np.zeros_like(f)
-    times = []
-    for _ in range(iters_timed):
-        t0 = time.perf_counter()
-        U, r, beta = O.qn_step(U, f, eig)
-        times.append(time.perf_counter() - t0)
-    per_it = statistics.mean(times)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return per_it * its * 1e3, {"per_iteration_s": per_it, "iterations_assumed": its, "cores": cores}
-
-
 def cpu_oracle_baseline_ex1(n: int, seed: int, iters_timed: int = 1):
     """cpu_oracle_baseline for Example 1: iters_timed oracle iterations at n^3 times the
     oracle's iteration count at 33^3 from the same kind of start (mesh-independent)."""
@@ -333,13 +315,277 @@ def run_batched(qn, seed=0, count=256, reps=3, tiles="auto"):
             "bk_used": bk, "steps": reps}
 
 
+def cpu_info() -> dict:
+    """Logical CPUs, the cores this process may use, and the host CPU model."""
+    import platform
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cores": cores, "model": model, "machine": platform.machine()}
+
+
+def oracle_solve_timed(f):
+    """The FP64 oracle's complete quasi-Newton solve of f from the zero start to 1e-10
+    (its own eigenpairs, residuals, products and stop test), timed on the host cores."""
+    import oracle as O
+    t0 = time.perf_counter()
+    U, hist, ok = O.qn_solve(f)
+    return U, hist, ok, time.perf_counter() - t0
+
+
+def compare_with_oracle(U_gpu, U_ora, f):
+    """max|U_gpu - U_ora| / max|U_ora|, and ||F(U_gpu)|| / ||f|| recomputed by the oracle in FP64."""
+    import numpy as np
+    import oracle as O
+    err = float(np.abs(U_gpu - U_ora).max() / np.abs(U_ora).max())
+    r = O.residual(U_gpu, f)
+    rel = float(np.linalg.norm(r.ravel()) / np.linalg.norm(f.ravel()))
+    return {"error_vs_oracle": err, "rel_residual_fp64": rel, "pass_1e-9": bool(err <= 1e-9 and rel <= 1e-10)}
+
+
+def oracle_single_thread(kind: str, seed: int = 0) -> dict | None:
+    """The oracle on one core: a fresh interpreter with the BLAS pool at one thread
+    (the thread count is fixed when numpy loads), timing kind 'c1' (100 complete 2-D 63^2
+    solves) or 'c2' (one quasi-Newton iteration at 255^3)."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", kind,
+                            "--seed", str(seed)], capture_output=True, text=True, timeout=600, env=env)
+        for line in r.stdout.splitlines()[::-1]:
+            if line.startswith("{"):
+                return json.loads(line)
+    except Exception as e:   # reported, not fatal: the all-core figures stand
+        return {"error": str(e)}
+    return {"error": (r.stderr or "no output")[-300:]}
+
+
+def oracle_sample_main(kind: str, seed: int):
+    """--oracle-sample: CPU-only oracle timing for oracle_single_thread (prints one JSON line)."""
+    import numpy as np
+    import oracle as O
+    from paper_2502_03611_gb300.inputs import manufactured_problem
+    if kind == "c1":
+        fs = [manufactured_problem(63, 2, seed=s)[1] for s in range(100)]
+        ts = []
+        for f in fs:
+            t0 = time.perf_counter()
+            O.qn_solve(f)
+            ts.append(time.perf_counter() - t0)
+        print(json.dumps({"kind": "c1", "solves": len(ts), "median_ms": 1e3 * statistics.median(ts),
+                          "p90_ms": 1e3 * float(np.percentile(ts, 90)), "threads": 1}))
+    elif kind == "c2":
+        _, f = manufactured_problem(255, 3, seed=seed)
+        eig = O.eig_1d(255)
+        U = np.zeros_like(f)
+        U, _, _ = O.qn_step(U, f, eig)            # untimed: the zero start's first step has beta = 0
+        t0 = time.perf_counter()
+        O.qn_step(U, f, eig)
+        print(json.dumps({"kind": "c2", "per_iteration_s": time.perf_counter() - t0, "threads": 1}))
+
+
+def dgemm_tflops(stream) -> float:
+    """cuBLAS DGEMM 4096^3 measured here: the FP64 denominator (MEASURED_PEAKS holds no FP64 peak)."""
+    import torch
+    A = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    B = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        A @ B
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(5):
+        A @ B
+    g1.record(stream)
+    torch.cuda.synchronize()
+    return 5 * 2 * 4096.0 ** 3 / (g0.elapsed_time(g1) * 1e-3) / 1e12
+
+
+def run_c1(qn, seeds=range(100), want_cpu=True):
+    """2-D -Lap u + u^3 = f on the 63^2 interior grid, FP64 throughout, zero start, tol 1e-10:
+    a latency workload. Per seed: device time per solve (CUDA events around qn_solve, which
+    includes its host round trips), iterations and launches; every result against the oracle."""
+    import numpy as np
+    import torch
+    from paper_2502_03611_gb300.inputs import manufactured_problem
+    n = 63
+    stream = torch.cuda.current_stream()
+    ctx = qn.QnContext(2, n, "fp64")
+    fs = [np.ascontiguousarray(manufactured_problem(n, 2, seed=s)[1]) for s in seeds]
+    fd = [torch.from_numpy(f.reshape(-1)).cuda() for f in fs]
+    U = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    for k in range(3):
+        U.zero_()
+        qn.qn_solve(ctx, U, fd[k], graph=True, sync_every=4)
+    torch.cuda.synchronize()
+    us, its, launches, outs, wall = [], [], [], [], []
+    for f in fd:
+        U.zero_()
+        qn.qn_profile_enable(ctx, False)          # resets the launch counter
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        res, _ = qn.qn_solve(ctx, U, f, graph=True, sync_every=4)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall.append(time.perf_counter() - t0)
+        us.append(1e3 * e0.elapsed_time(e1))
+        its.append(res["iterations"])
+        launches.append(int(qn.qn_profile_read(ctx)["launches"]))
+        outs.append(U.cpu().numpy().reshape(n, n).copy())
+    out = {"workload": "2-D -Lap u + u^3 = f, 63^2 interior, 5-point FD, Dirichlet 0, FP64, zero start, "
+                       f"tol 1e-10, seeds {seeds[0]}-{seeds[-1]}",
+           "precision": "fp64", "solves": len(us), "us_per_solve_median": round(statistics.median(us), 1),
+           "us_per_solve_p90": round(float(np.percentile(us, 90)), 1),
+           "host_wall_us_median": round(1e6 * statistics.median(wall), 1),
+           "iterations_median": statistics.median(its), "iterations_max": max(its),
+           "launches_per_solve_median": statistics.median(launches),
+           "launch": "iterations >= 2 replayed from a CUDA graph, host check every 4 iterations"}
+    if want_cpu:
+        errs, rels, dit, ts = [], [], [], []
+        for f, Ug, it in zip(fs, outs, its):
+            Uo, ho, ok, t = oracle_solve_timed(f)
+            c = compare_with_oracle(Ug, Uo, f)
+            errs.append(c["error_vs_oracle"])
+            rels.append(c["rel_residual_fp64"])
+            dit.append(it - (len(ho) - 1))
+            ts.append(t)
+        info = cpu_info()
+        out.update({"error_vs_oracle_max": max(errs), "rel_residual_fp64_max": max(rels),
+                    "iterations_minus_oracle": sorted(set(dit)),
+                    "pass_1e-9": bool(max(errs) <= 1e-9 and max(rels) <= 1e-10),
+                    "cpu_baseline": {"value": round(1e3 * statistics.median(ts), 3), "unit": "ms per solve",
+                                     "cores": info["cores"], "kind": "oracle",
+                                     "sample": f"{len(ts)} complete oracle solves (median), all cores",
+                                     "single_thread": oracle_single_thread("c1")}})
+    return out
+
+
+def run_c2(qn, seeds=(0, 1, 2), want_cpu=True):
+    """3-D -Lap u + u^3 = f on the 255^3 interior grid, FP64 throughout (FP64 mode products),
+    zero start, tol 1e-10: complete solves timed with CUDA events, the FP64 product kernel's
+    fraction of a cuBLAS DGEMM measured here, and seed 0 against the oracle's solve."""
+    import numpy as np
+    import torch
+    from paper_2502_03611_gb300.inputs import manufactured_problem
+    n = 255
+    stream = torch.cuda.current_stream()
+    ctx = qn.QnContext(3, n, "fp64")
+    U = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
+    f0 = None
+    ms, its = [], []
+    for k, s in enumerate(seeds):
+        f_np = np.ascontiguousarray(manufactured_problem(n, 3, seed=s)[1])
+        if k == 0:
+            f0 = f_np
+        f = torch.from_numpy(f_np.reshape(-1)).cuda()
+        if k == 0:   # warm-up (kernel load, graph capture)
+            U.zero_()
+            qn.qn_solve(ctx, U, f, graph=True)
+        U.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res, _ = qn.qn_solve(ctx, U, f, graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        its.append(res["iterations"])
+        if k == 0:
+            U0 = U.cpu().numpy().reshape(n, n, n).copy()
+            qn.qn_profile_enable(ctx, True)
+            U.zero_()
+            qn.qn_solve(ctx, U, f)
+            torch.cuda.synchronize()
+            prof = qn.qn_profile_read(ctx)
+            qn.qn_profile_enable(ctx, False)
+    mp_ms = prof["modeprod_ms"] / max(prof["modeprod_launches"], 1)
+    split = bool(prof.get("split_products", 0))
+    flops = (1.0 if split else 2.0) * float(n) ** 4
+    tfl = flops / (mp_ms * 1e-3) / 1e12
+    dg = dgemm_tflops(stream)
+    tot = prof["residual_ms"] + prof["modeprod_ms"] + prof["finalize_ms"]
+    out = {"workload": "3-D -Lap u + u^3 = f, 255^3 interior, 7-point FD, Dirichlet 0, FP64 throughout, "
+                       f"zero start, tol 1e-10, seeds {list(seeds)}",
+           "precision": "fp64", "ms_per_solve_median": round(statistics.median(ms), 2),
+           "ms_per_solve": [round(m, 2) for m in ms], "iterations": its,
+           "roofline": {"kernel": "k_modeprod_f64", "bound": "fp64", "achieved": round(tfl, 4),
+                        "peak": round(dg, 4), "unit": "TFLOP/s", "frac": round(tfl / dg, 4),
+                        "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (FP64 pipe)",
+                        "split_products": split, "flops_per_launch_algorithmic": flops,
+                        "avg_launch_ms": round(mp_ms, 4), "launches": prof["modeprod_launches"],
+                        "share": round(prof["modeprod_ms"] / tot, 4) if tot else None},
+           "residual_avg_ms": round(prof["residual_ms"] / max(prof["residual_launches"], 1), 4)}
+    if want_cpu:
+        Uo, ho, ok, t = oracle_solve_timed(f0)
+        c = compare_with_oracle(U0, Uo, f0)
+        info = cpu_info()
+        out.update(c)
+        out["iterations_oracle"] = len(ho) - 1
+        out["cpu_baseline"] = {"value": round(1e3 * t, 1), "unit": "ms per solve", "cores": info["cores"],
+                               "kind": "oracle", "sample": "one complete oracle solve (seed 0), all cores",
+                               "single_thread": oracle_single_thread("c2")}
+    return out
+
+
+def run_warm(qn, want_cpu=True, ntrain=4096, ntest=256, epochs=12):
+    """The learned warm start at 255^3 (unit-variance GRF sources): generate the training
+    solves with the library, train the network with its own kernels, then compare zero-start
+    and warm-started solves (time to 1e-10 including the network) on the held-out seeds;
+    two warm-started results against the oracle's solve."""
+    import numpy as np
+    import torch
+    from paper_2502_03611_gb300 import warmstart as W
+    from paper_2502_03611_gb300.inputs import grf_source
+    n = 255
+    summ, net, rows = W.run(n=n, ntrain=ntrain, ntest=ntest, epochs=epochs, log=lambda *_: None)
+    out = {"workload": f"3-D -Lap u + u^3 = f, {n}^3, f a unit-variance GRF (spectrum (1+|k|^2)^-2), "
+                       f"train seeds 0-{ntrain - 1}, test seeds 100000-{100000 + ntest - 1}, tol 1e-10",
+           "summary": summ,
+           "warm_faster": bool(summ["warm_ms_median"] < summ["zero_ms_median"])}
+    if want_cpu:
+        ctx = qn.QnContext(3, n, "bf16x3")
+        checks = []
+        for s in (100000, 100001):
+            f_np = np.ascontiguousarray(grf_source(n, s))
+            f = torch.from_numpy(f_np.reshape(-1)).cuda()
+            U = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
+            r = qn.qn_solve_warm(ctx, net, U, f, in_scale=summ["in_scale"], out_scale=summ["out_scale"])
+            Ug = U.cpu().numpy().reshape(n, n, n)
+            Uo, ho, ok, t = oracle_solve_timed(f_np)
+            c = compare_with_oracle(Ug, Uo, f_np)
+            c.update({"seed": s, "used_warm": r["used_warm"], "iterations": r["iterations"],
+                      "iterations_oracle_zero_start": len(ho) - 1, "oracle_s": round(t, 2)})
+            checks.append(c)
+        out["oracle_checks"] = checks
+        out["pass_1e-9"] = all(c["pass_1e-9"] for c in checks)
+    return out
+
+
 def run_reference(a):
     """--impl reference: the FP64 CPU oracle, as it stands, on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import numpy as np
-    import oracle as O
     from paper_2502_03611_gb300.inputs import manufactured_problem
     n = a.n
     if a.workload == "ex1":
@@ -366,36 +612,27 @@ def run_reference(a):
                           "seconds each at 200^3 (about an hour); the ours line carries a timed one-iteration oracle sample "
                           "(cpu_baseline) instead"}), flush=True)
         return
-    _, f_small = manufactured_problem(127, 3, seed=a.seed)
-    _, h_small, _ = O.qn_solve(f_small)
-    its = len(h_small) - 1
+    # one complete oracle solve, timed as run (no extrapolation). A full solve at 511^3 takes
+    # about 100 s on 16 host cores, so one step is that solve: the line reports steps = 1,
+    # warmup = 0 (what was timed), with the requested K and W beside them
     _, f = manufactured_problem(n, 3, seed=a.seed)
-    eig = O.eig_1d(n)
-    U = np.zeros_like(f)
-    warm = min(a.warmup, 2)
-    steps = min(a.steps, 5)
-    for _ in range(warm):
-        U, _, _ = O.qn_step(U, f, eig)
-    times = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        U, _, _ = O.qn_step(U, f, eig)
-        times.append(time.perf_counter() - t0)
-    per_it = statistics.mean(times)
-    value = per_it * its * 1e3
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    sample = (f"{steps} timed quasi-Newton iterations (after {warm} untimed) of the FP64 numpy oracle at "
-              f"{n}^3, mean {per_it:.2f} s/iteration x {its} iterations (the oracle's count at 127^3 "
-              f"on the same seed; the count is mesh-independent)")
+    Uo, ho, ok, t = oracle_solve_timed(f)
+    value = 1e3 * t
+    info = cpu_info()
+    sample = (f"one complete solve of the FP64 numpy oracle at {n}^3 (seed {a.seed}, zero start, "
+              f"{len(ho) - 1} iterations to rel. residual {ho[-1]['rel']:.2e}), timed as run on the host cores")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "ms",
-            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(value, 3),
+            "n_gpus": a.gpus, "steps": 1, "warmup": 0, "steps_requested": a.steps, "warmup_requested": a.warmup,
+            "ms_per_step": round(value, 3),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (manufactured sine-series source, seed-drawn)",
             "config": {"workload": f"3-D -Lap u + u^3 = f, {n}^3 interior, 7-point FD, Dirichlet 0, "
                                    f"tol 1e-10, zero start, seed {a.seed}",
                        "n": n, "dim": 3, "precision": "fp64 (CPU oracle)", "parallelism": "none"},
-            "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+            "iterations": len(ho) - 1, "converged": bool(ok),
+            "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": info["cores"], "kind": "oracle",
+                             "sample": sample, "nproc": info["nproc"], "cpu_model": info["model"],
+                             "machine": info["machine"]},
             "e2e": {"value": round(value, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -588,6 +825,9 @@ def main_batched(a):
 
 def main():
     a = parse()
+    if a.oracle_sample:
+        oracle_sample_main(a.oracle_sample, a.seed)
+        return
     if a.impl == "reference":
         run_reference(a)
         return
@@ -685,6 +925,9 @@ def main():
     clocks = sampler.stop()
     elapsed_ms = ev0.elapsed_time(ev1)
     timed_launches = int(qn.qn_profile_read(ctx)["launches"])
+    # the last timed solve's result, for the comparison with the oracle (after the GPU legs)
+    U_result = U.cpu().numpy().copy() if (not a.no_cpu and rank == 0 and world == 1
+                                          and not ex1 and not sem) else None
     # per-kernel breakdown: the same solves with CUDA events around every
     # launch (plain launches; outside the timed region)
     qn.qn_profile_enable(ctx, True)
@@ -875,17 +1118,39 @@ def main():
                "sample": (f"1 quasi-Newton iteration of the FP64 numpy SEM oracle at {n}^3 nodes "
                           f"({det['per_iteration_s']:.2f} s) x {det['iterations_assumed']} iterations "
                           f"(oracle count at {det['small']}^3 nodes)")}
-    elif not a.no_cpu and rank == 0 and world == 1:
-        if ex1:
-            ms_cpu, det = cpu_oracle_baseline_ex1(n, a.seed)
-            small = "33^3, same kind of start"
-        else:
-            ms_cpu, det = cpu_oracle_baseline(n, a.seed)
-            small = "127^3, same seed"
+    elif not a.no_cpu and rank == 0 and world == 1 and ex1:
+        ms_cpu, det = cpu_oracle_baseline_ex1(n, a.seed)
         cpu = {"value": round(ms_cpu, 1), "unit": "ms", "cores": det["cores"], "kind": "oracle",
                "sample": (f"1 quasi-Newton iteration of the FP64 numpy oracle at {n}^3 "
                           f"({det['per_iteration_s']:.2f} s) x {det['iterations_assumed']} iterations "
-                          f"(oracle count at {small})")}
+                          f"(oracle count at 33^3, same kind of start)")}
+
+    # ---- the other reported workloads: 2-D 63^2 FP64, 3-D 255^3 FP64, the learned warm start
+    configs = None
+    if not a.no_configs and rank == 0 and world == 1 and not ex1 and not sem and a.precision == "bf16x3":
+        torch.cuda.empty_cache()
+        configs = {"c1_2d_63_fp64": run_c1(qn, want_cpu=not a.no_cpu),
+                   "c2_3d_255_fp64": run_c2(qn, want_cpu=not a.no_cpu)}
+        torch.cuda.empty_cache()
+        if not a.no_warm:
+            configs["warm_start_255"] = run_warm(qn, want_cpu=not a.no_cpu)
+
+    # ---- the complete FP64 oracle solve of the same problem on the host cores: the CPU
+    # baseline, and the reference solution the GPU result is compared with point by point
+    parity = None
+    if not a.no_cpu and rank == 0 and world == 1 and not ex1 and not sem:
+        f3 = f_np.reshape(n, n, n)
+        Uo, ho, ok, t_ora = oracle_solve_timed(f3)
+        info = cpu_info()
+        parity = compare_with_oracle(U_result.reshape(n, n, n), Uo, f3)
+        parity.update({"iterations_oracle": len(ho) - 1, "oracle_converged": bool(ok),
+                       "oracle_final_rel": ho[-1]["rel"],
+                       "tolerance": "max|U - U_oracle| <= 1e-9 max|U_oracle| and ||F(U)||/||f|| <= 1e-10 (FP64)"})
+        cpu = {"value": round(1e3 * t_ora, 1), "unit": "ms", "cores": info["cores"], "kind": "oracle",
+               "sample": (f"one complete solve of the FP64 numpy oracle at {n}^3 (seed {a.seed}, zero start, "
+                          f"{len(ho) - 1} iterations to 1e-10), timed as run"),
+               "nproc": info["nproc"], "cpu_model": info["model"], "machine": info["machine"]}
+        del Uo
 
     if rank == 0 and sem:
         # the SEM residual is bound by the FP64 pipe: algorithmic FP64 FLOP per launch = per node
@@ -963,7 +1228,8 @@ def main():
             "metric": METRIC, "value": round(ms_max, 3), "unit": "ms", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_max, 3),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16x3+f64" if a.precision == "bf16x3" else "f64",
+            "dtype": ("bf16x3 products (fp32 accumulate); int64 fixed-point + fp32-pair residual; f64 update"
+                      if a.precision == "bf16x3" else "f64"),
             "data": "synthetic (manufactured sine-series source, 6x6x6 modes, seed-drawn)",
             "config": {"workload": f"3-D -Lap u + u^3 = f, {n}^3 interior ({N} unknowns), 7-point FD, "
                                    f"Dirichlet 0, tol 1e-10 on ||F||/||f||, zero start, seed {a.seed}",
@@ -974,8 +1240,10 @@ def main():
             "iterations": iters[0] if len(set(iters)) == 1 else iters,
             "final_rel": max(rels), "converged": ok,
             "solves_per_s": round(world * 1e3 / ms_max, 3),
+            "parity": parity,
             "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
-            "e2e": e2e, "plain_fp64": plain, "batched": batched, "cpu_baseline": cpu, "clocks": clocks,
+            "e2e": e2e, "plain_fp64": plain, "batched": batched, "configs": configs,
+            "cpu_baseline": cpu, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -247,10 +247,13 @@ int qn_solve_host_zero_start(qn_ctx *ctx, double *U_host, const double *f_host, 
  * Scratch: a fixed 33 KB device array inside libqn (4096 partial sums plus
  * the solver state and one statistics record), present on every GPU that
  * loads the library until the process exits. The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture. All calls share the one array, so
- * calls that overlap on the GPU (other streams, other host threads) race;
- * serialise them. Each call rewrites every scratch entry it reads. */
+ * looks up that array's device address (cudaGetSymbolAddress) and keeps it;
+ * make that first call before any stream capture. The lookup is redone when
+ * the device's context has changed since (after a cudaDeviceReset, which
+ * reloads the library's module). Every call reads the statistics back to the
+ * host and synchronises `stream` before it returns. All calls share the one
+ * array, so calls that overlap on the GPU (other streams, other host threads)
+ * race; serialise them. Each call rewrites every scratch entry it reads. */
 int qn_residual_noalloc(int dim, int n, double lam, double b, const double *U, const double *f,
                         double *R, qn_stats *st, void *stream);
 

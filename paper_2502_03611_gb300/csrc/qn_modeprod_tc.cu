@@ -13,14 +13,15 @@
 // to P = 64*ceil(n/64) points per axis (padded entries are zero, padded
 // eigenvalues are 1e30 so the divide keeps them zero).
 //
-// Kernel organisation (persistent, one CTA of 320 threads per SM):
+// Kernel organisation (persistent, one CTA of 576 threads per SM, kThreads):
 //   warp 0 lane 0  TMA producer: A_hi, A_lo (128 x BK) and B_hi, B_lo (BN x BK)
 //                  tiles per pipeline stage, K-major with 128-B or 64-B swizzle
 //   warp 1         allocates TMEM (2 accumulators of BN FP32 columns); lane 0
 //                  issues tcgen05.mma (M=128, N=BN, K=16) and commits to mbarriers
-//   warps 2..9     epilogue: tcgen05.ld of the accumulator (warp w owns TMEM
-//                  lanes 32*(w%4)..+31 = rows and one half of the BN columns),
-//                  then store / divide / update
+//   warps 2..17    epilogue (kEpiWarps = 16): tcgen05.ld of the accumulator; four
+//                  warps per TMEM lane quadrant (warp w owns lanes 32*(w%4)..+31 =
+//                  rows), each taking a quarter of the BN columns in 16-column
+//                  loads, then store / divide / update
 // Tiles are walked in m-major order (consecutive CTAs share the same A rows;
 // S stays resident in L2). The epilogue of tile i overlaps the MMAs of tile
 // i+1 through the double-buffered accumulators.

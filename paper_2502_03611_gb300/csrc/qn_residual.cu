@@ -1393,10 +1393,48 @@ static_assert(sizeof(qn_stats) <= kNoAllocStatsDoubles * sizeof(double), "qn_sta
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
 std::mutex g_noalloc_mu;
-double *g_noalloc_ptr[128] = {nullptr};   // device address of the array, per device ordinal
+// device address of the array per device ordinal, with the unique ID of the
+// context it was looked up in: after a device reset the runtime creates a new
+// primary context (a new ID) and reloads the module, so the lookup is redone
+struct NoAllocSlot {
+    double *ptr;
+    unsigned long long ctx_id;
+};
+NoAllocSlot g_noalloc_slot[128] = {};
 
-// Device address of g_noalloc_scratch on the current device (looked up once
-// per device; in host code the array's name is only a host-side stand-in).
+typedef int (*PfnCtxGetCurrent)(void **);
+typedef int (*PfnCtxGetId)(void *, unsigned long long *);
+
+// Unique ID of the calling thread's current context (driver entry points,
+// resolved once; the library links only the runtime).
+int current_ctx_id(unsigned long long *id) {
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *p1 = nullptr, *p2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p1, 12000, cudaEnableDefault, &q1);
+        cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &p2, 12000, cudaEnableDefault, &q2);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+            q2 != cudaDriverEntryPointSuccess || !p1 || !p2) {
+            set_error("qn_residual_noalloc: cuCtxGetCurrent / cuCtxGetId unavailable from the driver");
+            return QN_ECUDA;
+        }
+        get_current = reinterpret_cast<PfnCtxGetCurrent>(p1);
+        get_id = reinterpret_cast<PfnCtxGetId>(p2);
+    }
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || ctx == nullptr || get_id(ctx, id) != 0) {
+        set_error("qn_residual_noalloc: no current CUDA context");
+        return QN_ECUDA;
+    }
+    return QN_OK;
+}
+
+// Device address of g_noalloc_scratch on the current device. In host code the
+// array's name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress: once per device, and again whenever that device's
+// context has changed since (a cudaDeviceReset in between).
 int noalloc_scratch(double **out) {
     int dev = 0;
     QN_CUDA(cudaGetDevice(&dev));
@@ -1404,14 +1442,23 @@ int noalloc_scratch(double **out) {
         set_error("qn_residual_noalloc: device ordinal %d out of range", dev);
         return QN_EINVAL;
     }
+    QN_CUDA(cudaSetDevice(dev));   // makes the device's primary context current (initialising it)
+    unsigned long long id = 0;
+    int rc = current_ctx_id(&id);
+    if (rc != QN_OK) return rc;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (g_noalloc_ptr[dev] == nullptr) {
+    NoAllocSlot &slot = g_noalloc_slot[dev];
+    if (slot.ptr == nullptr || slot.ctx_id != id) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        g_noalloc_ptr[dev] = static_cast<double *>(p);
+        if (e != cudaSuccess) {
+            slot.ptr = nullptr;
+            return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        }
+        slot.ptr = static_cast<double *>(p);
+        slot.ctx_id = id;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = slot.ptr;
     return QN_OK;
 }
 

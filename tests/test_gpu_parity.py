@@ -176,26 +176,31 @@ def test_solve_3d_255_fp64_full_size(qn):
 
 
 def test_solve_3d_511_bf16x3_full_size(qn):
-    """The benchmark workload. The oracle's full solve at 511^3 is too slow for a
-    test, so the GPU result is judged by properties that hold at any size: the
-    oracle's FP64 residual of the GPU solution is <= 1e-10 ||f||, and since
-    F(U) - F(U_h) = (A_h + diag(b(U^2 + U U_h + U_h^2))) (U - U_h) with the
-    diagonal >= 0, ||U - U_h||_2 <= ||F(U)||_2 / lambda_min(A_h)."""
+    """The benchmark workload (511^3, BF16x3, the launch configuration the benchmark
+    times: graph replay of the steady-state iterations), against the oracle's own
+    complete FP64 solve, point by point: max|U_gpu - U_oracle| <= 1e-9 max|U_oracle|,
+    and the oracle's FP64 residual of the GPU solution <= 1e-10 ||f||."""
     import torch
     n = 511
     u, f = manufactured_problem(n, 3, seed=0)
     ctx = qn.QnContext(3, n, "bf16x3")
     U = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
-    res, hist = qn.qn_solve(ctx, U, dev(f).reshape(-1), tol=1e-10, max_it=60, history_len=61)
+    fd = dev(f).reshape(-1)
+    qn.qn_solve(ctx, U, fd, graph=True)          # warm-up: captures the iteration graph
+    U.zero_()
+    res, hist = qn.qn_solve(ctx, U, fd, tol=1e-10, max_it=60, history_len=61, graph=True)
     assert res["status"] == 0 and res["rel"] <= 1e-10
     Ug = host(U).reshape(f.shape)
-    del U
+    del U, fd, ctx
+    torch.cuda.empty_cache()
+    Uo, ho, ok = O.qn_solve(f)
+    assert ok
+    err = np.abs(Ug - Uo).max() / np.abs(Uo).max()
+    assert err <= 1e-9, err
     r = O.residual(Ug, f)
-    rnorm = np.linalg.norm(r)
-    assert rnorm <= 1.05e-10 * np.linalg.norm(f)
-    lam_min = 3 * 4.0 * (n + 1) ** 2 * math.sin(math.pi / (2 * (n + 1))) ** 2
-    rms_err_bound = rnorm / lam_min / math.sqrt(Ug.size)
-    assert rms_err_bound <= 1e-9 * np.abs(Ug).max()
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(f)
+    assert abs(res["iterations"] - (len(ho) - 1)) <= 1
+    del Uo, r
     # discretisation error against the manufactured solution decays as O(h^2):
     # halving h (255 -> 511 interior points) divides it by about 4
     err511 = np.abs(Ug - u).max()
@@ -206,9 +211,6 @@ def test_solve_3d_511_bf16x3_full_size(qn):
     assert r255["status"] == 0
     err255 = np.abs(host(U255).reshape(u255.shape) - u255).max()
     assert 3.6 < err255 / err511 < 4.4, (err255, err511)
-    # mesh-independent iteration count (the paper's Sec. 6 observation): same as at 127^3
-    _, ho_small, _ = O.qn_solve(manufactured_problem(127, 3, seed=0)[1])
-    assert abs(res["iterations"] - (len(ho_small) - 1)) <= 2
 
 
 def test_golden_2d_63(qn):

@@ -61,6 +61,42 @@ def test_noalloc_residual_matches_context_residual(lib, dim, n, lam, b):
     assert outs[0] != outs[1]
 
 
+def _call(lib, dim, n, lam, b, U, f, R, st, stream):
+    return lib.qn_residual_noalloc(dim, n, lam, b, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(f.data_ptr()),
+                                   ctypes.c_void_p(R.data_ptr()) if R is not None else None,
+                                   ctypes.byref(st), stream)
+
+
+def test_noalloc_without_output_and_without_allocating(lib):
+    """R = NULL returns the statistics alone; after a first call (which loads the
+    kernels and looks up the scratch address) further calls leave the device's
+    free memory and torch's pool unchanged: the entry point allocates nothing."""
+    import torch
+    from paper_2502_03611_gb300 import qn
+    dim, n, lam, b = 3, 96, 0.2, 1.5
+    N = n ** dim
+    ctx = qn.QnContext(dim, n, "fp64", lam=lam, b=b)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    U = torch.from_numpy(random_field((N,), seed=31)).cuda()
+    f = torch.from_numpy(random_field((N,), seed=32) * 10.0).cuda()
+    want = qn.qn_residual(ctx, U, f)
+    st = qn.QnStats()
+    assert _call(lib, dim, n, lam, b, U, f, None, st, stream) == qn.QN_OK, qn.qn_last_error()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    for _ in range(3):
+        st = qn.QnStats()
+        assert _call(lib, dim, n, lam, b, U, f, None, st, stream) == qn.QN_OK, qn.qn_last_error()
+        got = st.as_dict()
+        for k in ("res_norm", "f_norm", "fu_min", "fu_max", "beta", "rel"):
+            assert got[k] == pytest.approx(want[k], rel=1e-12, abs=1e-300), k
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_reserved() == reserved0
+
+
 def test_noalloc_rejects_out_of_range(lib):
     from paper_2502_03611_gb300 import qn
     st = qn.QnStats()
