@@ -234,6 +234,28 @@ int qn_solve_host(qn_ctx *ctx, double *U_host, const double *f_host, const qn_op
 int qn_solve_host_zero_start(qn_ctx *ctx, double *U_host, const double *f_host, const qn_opts *opts,
                              qn_result *res, qn_stats *history, int history_len, void *stream);
 
+/* A sequence of independent host-array solves with one context, pipelined: the
+ * inputs of problem i+1 are copied in and the result of problem i-1 copied out on
+ * two copy streams of the context while problem i is solved on `stream`, so that
+ * the host link works alongside the GPU (a serving loop). No counterpart in the
+ * paper (its solves start from device-resident data).
+ *   count >= 0 problems. U_host[i], f_host[i]: host arrays of n^dim doubles in the
+ *   context's layout; U_host[i] holds the start unless zero_start != 0 (then it is
+ *   output only), and receives the result. Distinct problems may share an f array,
+ *   and may share a U array when the later one is at least two positions on (the
+ *   copies out run in order). Page-locked arrays (cudaHostAlloc / cudaHostRegister)
+ *   let the copies overlap the solves; pageable ones work, with less overlap.
+ *   opts: as qn_solve (NULL for the defaults). results: count records, written for
+ *   every problem solved.
+ * Allocates two pairs of device buffers (4 n^dim doubles), two streams and six
+ * events on the first call; the context frees them. Synchronises `stream` and the
+ * copy streams before it returns. Returns QN_OK when every problem ran (each
+ * record's status says whether it converged: QN_OK, QN_ENOTCONV, QN_EDIVERGED),
+ * QN_EINVAL for bad arguments (before any copy), or the first hard error
+ * (QN_ECUDA, QN_ETIMEOUT, ...), after which the later problems are not solved. */
+int qn_solve_host_many(qn_ctx *ctx, int count, double *const *U_host, const double *const *f_host,
+                       int zero_start, const qn_opts *opts, qn_result *results, void *stream);
+
 /* Allocation-free variant of qn_residual, for callers that cannot allocate
  * device memory where they need a residual: their device memory is owned in
  * full by another allocator or a fixed budget, or they run in a section that

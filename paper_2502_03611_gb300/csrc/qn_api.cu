@@ -45,6 +45,8 @@ using namespace qn;
 
 static const int kHistCap = 4097;
 
+struct StateMirror;
+
 struct qn_ctx {
     qn_problem prob;
     int device;
@@ -96,12 +98,32 @@ struct qn_ctx {
     double g_step;
     int g_chunk;
     long long g_launches; // kernels per replay
+    // the previously used graph, kept so that two alternating (U, f) pairs (the
+    // ping-pong buffers of qn_solve_host_many) do not re-capture on every solve
+    struct GraphSlot {
+        cudaGraphExec_t exec;
+        double *U;
+        const double *f;
+        double step;
+        int chunk, kind;
+        long long launches;
+    } g_prev;
+    // the solver state read by the host: written by a kernel into mapped page-locked host
+    // memory, so that the solve loop issues no memory copies (copies would queue behind
+    // the large transfers of qn_solve_host_many on the copy engines)
+    StateMirror *mir_host, *mir_dev;
+    long long aux_launches;   // state-set / state-mirror kernels of the current solve
+    // qn_solve_host_many: two device (U, f) buffer pairs and the copy streams / events
+    double *hm_U[2], *hm_f[2];
+    cudaStream_t hm_h2d, hm_d2h;
+    cudaEvent_t hm_in_ready[2], hm_solved[2], hm_out_done[2];
     float *warm_dsq;      // device: ||U_1 - U_0||^2 of a warm-started solve's first iteration
     int warm_dsq_on;      // 1 while that iteration's products are enqueued
     // reflection-split mode products (3-D split solve, P a multiple of 128)
     int split;            // 1: the plan holds the split matrices and the solve loop uses them
     int split_layout;     // 1: the last residual wrote its planes in split / folded order
     int last_split;       // 1: the last shifted inverse used the split products
+    int f64_split;        // FP64 path: reflection-split FP64 products (FD Dirichlet / Neumann)
     __nv_bfloat16 *bf_hi, *bf_lo, *bb_hi, *bb_lo;   // [P][P/2] forward / backward matrices
     float *lam32_split;   // eigenvalues in split mode order (even modes, then odd), 1e30 padding
     // separable potential V = v_x + v_y (+ v_z): device tables [dim][n], FP64 and as FP32
@@ -120,6 +142,29 @@ struct qn_ctx {
     double *hval;
     int hbw;
 };
+
+struct StateMirror {
+    DevState st;
+    int err;        // the device error word (QN_ETIMEOUT), taken and cleared by the mirror kernel
+    int pad;
+    qn_stats last;  // hist[st.it]: the statistics of the iterate evaluated last
+};
+
+// The solver state from host parameters (one thread; no copy-engine transfer).
+__global__ void k_set_state(DevState *st, DevState v) {
+    if (threadIdx.x == 0) *st = v;
+}
+
+// State, error word and the last statistics record into mapped host memory.
+__global__ void k_mirror_state(const DevState *st, int *err, const qn_stats *hist, int hist_cap,
+                               StateMirror *out) {
+    if (threadIdx.x != 0) return;
+    const DevState v = *st;
+    out->st = v;
+    out->err = atomicExch(err, 0);
+    if (hist != nullptr && v.it >= 0 && v.it < hist_cap) out->last = hist[v.it];
+    __threadfence_system();
+}
 
 enum ProfKind { PK_RESIDUAL = 0, PK_FINALIZE = 1, PK_MP_STORE = 2, PK_MP_DIVIDE = 3, PK_MP_LAST = 4,
                 PK_SPLIT = 5, PK_RESIDUAL_TILED = 6, PK_COUNT = 7 };
@@ -251,9 +296,20 @@ static void ctx_free(qn_ctx *c) {
     cudaFree(c->partials);
     cudaFree(c->warm_dsq);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->g_prev.exec) cudaGraphExecDestroy(c->g_prev.exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(c->hm_U[b]);
+        cudaFree(c->hm_f[b]);
+        if (c->hm_in_ready[b]) cudaEventDestroy(c->hm_in_ready[b]);
+        if (c->hm_solved[b]) cudaEventDestroy(c->hm_solved[b]);
+        if (c->hm_out_done[b]) cudaEventDestroy(c->hm_out_done[b]);
+    }
+    if (c->hm_h2d) cudaStreamDestroy(c->hm_h2d);
+    if (c->hm_d2h) cudaStreamDestroy(c->hm_d2h);
     cudaFree(c->fdf);
     cudaFree(c->st);
+    if (c->mir_host) cudaFreeHost(c->mir_host);
     cudaFree(c->hist);
     cudaFree(c->err);
     cudaFree(c->dU);
@@ -454,12 +510,19 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
     c->partials_cap = c->nparts > 8 * c->num_sms ? c->nparts : 8 * c->num_sms;
     CK(cudaMalloc(&c->partials, sizeof(double) * 4 * c->partials_cap));
     CK(cudaMalloc(&c->st, sizeof(DevState)));
+    CK(cudaHostAlloc((void **)&c->mir_host, sizeof(StateMirror), cudaHostAllocMapped));
+    memset(c->mir_host, 0, sizeof(StateMirror));
+    CK(cudaHostGetDevicePointer((void **)&c->mir_dev, c->mir_host, 0));
     CK(cudaMalloc(&c->hist, sizeof(qn_stats) * kHistCap));
     CK(cudaMalloc(&c->err, sizeof(int)));
     CK(cudaMemset(c->err, 0, sizeof(int)));
 
     if (p->precision == QN_PREC_FP64) {
         for (int b = 0; b < 2; ++b) CK(cudaMalloc(&c->w64[b], sizeof(double) * c->N));
+        // the closed-form sine / cosine pairs have the reflection symmetry the split
+        // products use; the numerical (Robin, spectral-element) ones need not
+        const char *es = getenv("QN_SPLIT");
+        c->f64_split = (es ? (atoi(es) != 0) : true) && p->sem_k == 0 && p->bc != QN_BC_ROBIN;
     } else {
         if (!tc_supported(c->device)) {
             set_error("qn_ctx_create: QN_PREC_BF16X3 needs an sm_103 (tcgen05) device");
@@ -584,7 +647,9 @@ static int reset_state(qn_ctx *c, double tol, int max_it, int beta_mode, double 
     h.beta_value = beta_value;
     h.fx_headroom = c->res_fx_headroom;
     h.npts = (double)c->N;
-    QN_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    k_set_state<<<1, 32, 0, s>>>(c->st, h);
+    QN_CUDA(cudaGetLastError());
+    c->aux_launches += 1;
     return QN_OK;
 }
 
@@ -728,6 +793,8 @@ static int enqueue_inverse(qn_ctx *c, const double *r0, double *target, bool upd
             g.K = c->n;
             g.N = c->n;
             g.Mtot = (d == 3) ? c->n * c->n : c->n;
+            g.split = c->f64_split ? (forward ? 1 : 2) : 0;
+            c->last_split = c->f64_split;
             const double *A = (i == 0 && r0 != nullptr) ? r0 : c->w64[cur];
             const double *B = forward ? c->Si64 : c->S64;
             double *o = last ? target : c->w64[next];
@@ -761,10 +828,24 @@ static int enqueue_eig_iteration(qn_ctx *c, double *U, double step, cudaStream_t
 static int ensure_iteration_graph(qn_ctx *c, double *U, const double *f, double step, int chunk, int kind = 0) {
     if (c->gexec && c->g_U == U && c->g_f == f && c->g_step == step && c->g_chunk == chunk && c->g_kind == kind)
         return QN_OK;
-    if (c->gexec) {
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
+    qn_ctx::GraphSlot cur{c->gexec, c->g_U, c->g_f, c->g_step, c->g_chunk, c->g_kind, c->g_launches};
+    const qn_ctx::GraphSlot &pv = c->g_prev;
+    if (pv.exec && pv.U == U && pv.f == f && pv.step == step && pv.chunk == chunk && pv.kind == kind) {
+        // the previous graph matches: swap it in
+        c->gexec = pv.exec;
+        c->g_U = pv.U;
+        c->g_f = pv.f;
+        c->g_step = pv.step;
+        c->g_chunk = pv.chunk;
+        c->g_kind = pv.kind;
+        c->g_launches = pv.launches;
+        c->g_prev = cur;
+        return QN_OK;
     }
+    // capture a new one; the current one becomes the previous, the older one goes
+    if (c->g_prev.exec) cudaGraphExecDestroy(c->g_prev.exec);
+    c->g_prev = cur;
+    c->gexec = nullptr;
     if (!c->cap_stream) QN_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     const long long l0 = c->launches;
     const int it0 = c->cur_iter;
@@ -799,13 +880,16 @@ static int ensure_iteration_graph(qn_ctx *c, double *U, const double *f, double 
     return QN_OK;
 }
 
+// The state after the work queued so far on s: a kernel mirrors it into mapped host
+// memory, and the host waits for s alone.
 static int read_state(qn_ctx *c, DevState *h, cudaStream_t s) {
-    QN_CUDA(cudaMemcpyAsync(h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    k_mirror_state<<<1, 32, 0, s>>>(c->st, c->err, c->hist, kHistCap, c->mir_dev);
+    QN_CUDA(cudaGetLastError());
+    c->aux_launches += 1;
     QN_CUDA(cudaStreamSynchronize(s));
-    int err = 0;
-    QN_CUDA(cudaMemcpy(&err, c->err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err) {
-        QN_CUDA(cudaMemset(c->err, 0, sizeof(int)));
+    const volatile StateMirror *m = c->mir_host;
+    memcpy(h, const_cast<const StateMirror *>(m), sizeof(DevState));
+    if (m->err) {
         set_error("a device-side wait gave up (tensor-core pipeline timeout)");
         return QN_ETIMEOUT;
     }
@@ -944,6 +1028,7 @@ int qn::solve_internal(qn_ctx *c, double *U, const double *f, const qn_opts *opt
         return QN_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    c->aux_launches = 0;
     rc = reset_state(c, o.tol, o.max_it, o.beta_mode, o.beta_value, s);
     if (rc) return rc;
     DevState h;
@@ -1019,11 +1104,12 @@ int qn::solve_internal(qn_ctx *c, double *U, const double *f, const qn_opts *opt
         const bool mp = r.kind >= PK_MP_STORE && r.kind <= PK_MP_LAST;
         if ((mp && r.iter >= its) || (!mp && r.iter > its)) r.valid = 0;
     }
-    c->launches = launches0 + 2LL * (its + 1) + 2LL * c->dim * its;
+    c->launches = launches0 + 2LL * (its + 1) + 2LL * c->dim * its + c->aux_launches;
     if (c->prob.precision == QN_PREC_BF16X3 && c->fdf != nullptr && c->res_tiled)
         c->launches += 2 + (its >= 1 ? 2 : 0);   // preparation kernels of iterations 0 and 1
+    // the statistics of the final iterate came with the last state mirror
     qn_stats last;
-    QN_CUDA(cudaMemcpy(&last, c->hist + its, sizeof(qn_stats), cudaMemcpyDeviceToHost));
+    memcpy(&last, const_cast<const qn_stats *>(&((const volatile StateMirror *)c->mir_host)->last), sizeof(last));
     if (history && history_len > 0) {
         const int cnt = (its + 1) < history_len ? (its + 1) : history_len;
         QN_CUDA(cudaMemcpy(history, c->hist, sizeof(qn_stats) * cnt, cudaMemcpyDeviceToHost));
@@ -1075,6 +1161,84 @@ extern "C" int qn_solve_host_zero_start(qn_ctx *c, double *U_host, const double 
                                         qn_result *res, qn_stats *history, int history_len, void *stream) {
     return solve_host(c, U_host, f_host, true, opts, res, history, history_len, stream,
                       "qn_solve_host_zero_start");
+}
+
+// A sequence of host-array solves with one context: problem i+1 is copied in and
+// problem i-1 copied out on two copy streams while problem i is solved on `stream`,
+// through two pairs of context-owned device buffers.
+extern "C" int qn_solve_host_many(qn_ctx *c, int count, double *const *U_host, const double *const *f_host,
+                                  int zero_start, const qn_opts *opts, qn_result *results, void *stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (count < 0 || (count > 0 && (!U_host || !f_host || !results))) {
+        set_error("qn_solve_host_many: count < 0 or null arrays");
+        return QN_EINVAL;
+    }
+    for (int i = 0; i < count; ++i)
+        if (bad_ptr(U_host[i]) || bad_ptr(f_host[i])) {
+            set_error("qn_solve_host_many: null U_host[%d] or f_host[%d]", i, i);
+            return QN_EINVAL;
+        }
+    if (count == 0) return QN_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * (size_t)c->N;
+    for (int b = 0; b < 2; ++b) {
+        if (!c->hm_U[b]) {
+            QN_CUDA(cudaMalloc(&c->hm_U[b], bytes));
+            QN_CUDA(cudaMalloc(&c->hm_f[b], bytes));
+            QN_CUDA(cudaEventCreateWithFlags(&c->hm_in_ready[b], cudaEventDisableTiming));
+            QN_CUDA(cudaEventCreateWithFlags(&c->hm_solved[b], cudaEventDisableTiming));
+            QN_CUDA(cudaEventCreateWithFlags(&c->hm_out_done[b], cudaEventDisableTiming));
+        }
+    }
+    if (!c->hm_h2d) QN_CUDA(cudaStreamCreateWithFlags(&c->hm_h2d, cudaStreamNonBlocking));
+    if (!c->hm_d2h) QN_CUDA(cudaStreamCreateWithFlags(&c->hm_d2h, cudaStreamNonBlocking));
+    // inputs of problem i into buffer pair i & 1, once problem i - 2 has left it
+    auto enqueue_in = [&](int i) -> int {
+        const int b = i & 1;
+        if (i >= 2) QN_CUDA(cudaStreamWaitEvent(c->hm_h2d, c->hm_out_done[b], 0));
+        QN_CUDA(cudaMemcpyAsync(c->hm_f[b], f_host[i], bytes, cudaMemcpyHostToDevice, c->hm_h2d));
+        if (zero_start)
+            QN_CUDA(cudaMemsetAsync(c->hm_U[b], 0, bytes, c->hm_h2d));   // +0.0 is all-zero bits
+        else
+            QN_CUDA(cudaMemcpyAsync(c->hm_U[b], U_host[i], bytes, cudaMemcpyHostToDevice, c->hm_h2d));
+        QN_CUDA(cudaEventRecord(c->hm_in_ready[b], c->hm_h2d));
+        return QN_OK;
+    };
+    int err = enqueue_in(0);
+    for (int i = 0; i < count && err == QN_OK; ++i) {
+        const int b = i & 1;
+        if (i + 1 < count) {
+            err = enqueue_in(i + 1);
+            if (err != QN_OK) break;
+        }
+        cudaError_t ce = cudaStreamWaitEvent(s, c->hm_in_ready[b], 0);
+        if (ce != cudaSuccess) {
+            err = cuda_fail(ce, "cudaStreamWaitEvent (qn_solve_host_many)");
+            break;
+        }
+        rc = qn_solve(c, c->hm_U[b], c->hm_f[b], opts, &results[i], nullptr, 0, stream);
+        if (rc != QN_OK && rc != QN_ENOTCONV && rc != QN_EDIVERGED) {
+            err = rc;
+            break;
+        }
+        if ((ce = cudaEventRecord(c->hm_solved[b], s)) != cudaSuccess ||
+            (ce = cudaStreamWaitEvent(c->hm_d2h, c->hm_solved[b], 0)) != cudaSuccess ||
+            (ce = cudaMemcpyAsync(U_host[i], c->hm_U[b], bytes, cudaMemcpyDeviceToHost, c->hm_d2h)) != cudaSuccess ||
+            (ce = cudaEventRecord(c->hm_out_done[b], c->hm_d2h)) != cudaSuccess) {
+            err = cuda_fail(ce, "copy-out (qn_solve_host_many)");
+            break;
+        }
+    }
+    // every copy has landed (or been abandoned after an error) before the call returns
+    const cudaError_t e1 = cudaStreamSynchronize(c->hm_h2d);
+    const cudaError_t e2 = cudaStreamSynchronize(c->hm_d2h);
+    const cudaError_t e3 = cudaStreamSynchronize(s);
+    if (err != QN_OK) return err;
+    if (e1 != cudaSuccess) return cuda_fail(e1, "cudaStreamSynchronize (copy-in)");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamSynchronize (copy-out)");
+    if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamSynchronize (solve stream)");
+    return QN_OK;
 }
 
 extern "C" int qn_test_withhold_arrival(void) { return tc_test_withhold_arrival(); }
@@ -1239,6 +1403,7 @@ extern "C" int qn_eig_solve(qn_ctx *c, double *U, const qn_opts *opts, qn_result
         QN_CUDA(cudaMemcpy(c->eig_vrow, vr.data(), sizeof(double) * rows, cudaMemcpyHostToDevice));
         QN_CUDA(cudaMemcpy(c->eig_pot32, p32.data(), sizeof(float) * dn, cudaMemcpyHostToDevice));
     }
+    c->aux_launches = 0;
     rc = reset_state(c, o.tol, o.max_it, o.beta_mode, o.beta_value, s);
     if (rc) return rc;
     const size_t first_rec = c->prof_used;
@@ -1275,9 +1440,9 @@ extern "C" int qn_eig_solve(qn_ctx *c, double *U, const qn_opts *opts, qn_result
         if ((mp && r.iter >= its) || (!mp && r.iter > its)) r.valid = 0;
     }
     // per evaluated iterate 2 residual passes + 2 finalisers; per update 2 dim products
-    c->launches = launches0 + 4LL * (its + 1) + 2LL * c->dim * its;
+    c->launches = launches0 + 4LL * (its + 1) + 2LL * c->dim * its + c->aux_launches;
     qn_stats last;
-    QN_CUDA(cudaMemcpy(&last, c->hist + its, sizeof(qn_stats), cudaMemcpyDeviceToHost));
+    memcpy(&last, const_cast<const qn_stats *>(&((const volatile StateMirror *)c->mir_host)->last), sizeof(last));
     if (history && history_len > 0) {
         const int cnt = (its + 1) < history_len ? (its + 1) : history_len;
         QN_CUDA(cudaMemcpy(history, c->hist, sizeof(qn_stats) * cnt, cudaMemcpyDeviceToHost));

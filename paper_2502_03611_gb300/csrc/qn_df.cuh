@@ -41,14 +41,18 @@ __device__ __forceinline__ float2 f_pair(double fv, int *flag) {
 }
 
 // Signed fixed-point value of the double with bit pattern b, in units of
-// 2^(E - 1075 - kFxG); `bad` is set when its exponent exceeds E.
+// 2^(E - 1075 - kFxG); `bad` is set when its exponent exceeds E (the value
+// returned is then 0 and must not be used). Every usable exponent E is >= 64,
+// so zeros and subnormals (biased exponent 0) shift out entirely; the PTX
+// shift clamps amounts of 64 or more to 64 (result 0), which needs no clamp here.
 __device__ __forceinline__ long long fx_of(unsigned long long b, int E, unsigned &bad) {
-    const int ex = (int)((unsigned int)(b >> 52) & 0x7FFu);
+    const unsigned int bh = (unsigned int)(b >> 32);
+    const int ex = (int)((bh >> 20) & 0x7FFu);
     bad |= (unsigned)(ex > E);
-    int sh = E - ex;
-    sh = sh < 0 ? 0 : (sh > 63 ? 63 : sh);
+    const unsigned int sh = (unsigned int)(E - ex);
     const unsigned long long m = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << kFxG;
-    const unsigned long long v = (ex == 0) ? 0ull : (m >> sh);
+    unsigned long long v;
+    asm("shr.b64 %0, %1, %2;" : "=l"(v) : "l"(m), "r"(sh));
     const unsigned long long sg = (unsigned long long)((long long)b >> 63);   // 0 or all ones
     return (long long)((v ^ sg) - sg);
 }

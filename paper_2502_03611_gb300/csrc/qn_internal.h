@@ -112,6 +112,7 @@ struct GemmShape {
     int n;      // logical extent per axis
     int P;      // padded extent per axis (split path), = n for FP64
     int dim;
+    int split = 0;   // FP64 products: 0 dense, 1 forward / 2 backward reflection split
 };
 
 // ---- launchers (implemented in the .cu files) ---------------------------------

@@ -127,6 +127,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                                     ctypes.POINTER(QnStats), ctypes.c_int, P]),
         "qn_solve_host": (ctypes.c_int, [P, P, P, ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult),
                                          ctypes.POINTER(QnStats), ctypes.c_int, P]),
+        "qn_solve_host_many": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int,
+                                              ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult), P]),
         "qn_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
         "qn_test_withhold_arrival": (ctypes.c_int, []),
         "qn_residual_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -362,6 +364,28 @@ def qn_solve_host(ctx: QnContext, U_host: np.ndarray, f_host: np.ndarray, tol=1e
             ctypes.byref(opts), ctypes.byref(res), None, 0, _stream_ptr(stream))
     _check(rc, allowed=(QN_OK, QN_ENOTCONV, QN_EDIVERGED))
     return {"iterations": res.iterations, "status": res.status, "rel": res.rel, "rc": rc}
+
+
+def qn_solve_host_many(ctx: QnContext, U_hosts, f_hosts, tol=1e-10, max_it=200, beta=None, step=1.0,
+                       sync_every=2, stream=None, graph=False, zero_start=False):
+    """A sequence of host-array solves, copies overlapped with the neighbouring solves
+    (qn_solve_host_many). U_hosts[i], f_hosts[i]: C-contiguous float64 numpy arrays (the
+    same array may appear more than once, see the header). Returns one result dict per
+    problem."""
+    if len(U_hosts) != len(f_hosts):
+        raise ValueError("U_hosts and f_hosts must have the same length")
+    for name, arrs in (("U_hosts", U_hosts), ("f_hosts", f_hosts)):
+        for a in arrs:
+            if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != ctx.numel:
+                raise ValueError(f"{name} entries must be C-contiguous float64 arrays of {ctx.numel} values")
+    count = len(U_hosts)
+    Up = (ctypes.c_void_p * max(count, 1))(*[a.ctypes.data for a in U_hosts])
+    fp = (ctypes.c_void_p * max(count, 1))(*[a.ctypes.data for a in f_hosts])
+    res = (QnResult * max(count, 1))()
+    opts = make_opts(tol, max_it, beta, step, sync_every, graph)
+    _check(load_library().qn_solve_host_many(ctx.handle, count, Up, fp, 1 if zero_start else 0, ctypes.byref(opts),
+                                             res, _stream_ptr(stream)))
+    return [{"iterations": res[i].iterations, "status": res[i].status, "rel": res[i].rel} for i in range(count)]
 
 
 def qn_test_withhold_arrival():

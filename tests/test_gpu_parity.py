@@ -88,6 +88,34 @@ def test_fast_diag_solve_matches_oracle(qn, dim, n, prec, shift):
     assert err <= tol, err
 
 
+@pytest.mark.parametrize("dim,n", [(2, 130), (2, 257), (3, 64), (3, 65), (3, 127)])
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+def test_fp64_reflection_split_products(qn, monkeypatch, dim, n, bc):
+    """The FP64 products through the reflection symmetry of the FD eigenpairs (sums and
+    differences of mirror points, even / odd modes: half the FP64 work) give the
+    oracle's shifted inverse to 1e-12, like the dense FP64 products they replace."""
+    import torch
+    from oracle import qn_oracle_bc as ob
+    r = random_field((n,) * dim, seed=41 + n, lo=-10.0, hi=10.0)
+    h = 1.0 / (n + 1) if bc == "dirichlet" else ob.mesh_width(n, "neumann", 2.0)
+    S, Si, lam = O.eig_1d(n) if bc == "dirichlet" else ob.eig_1d(n, h, bc)
+    want = O.fast_diag_solve(r, S, Si, lam, 3.5)
+    outs = {}
+    for split in ("1", "0"):
+        monkeypatch.setenv("QN_SPLIT", split)
+        kw = {} if bc == "dirichlet" else dict(bc=bc, length=2.0)
+        ctx = qn.QnContext(dim, n, "fp64", **kw)
+        qn.qn_profile_enable(ctx, True)
+        V = torch.empty(n ** dim, dtype=torch.float64, device="cuda")
+        qn.qn_fast_diag_solve(ctx, dev(r).reshape(-1), V, 3.5)
+        torch.cuda.synchronize()
+        assert qn.qn_profile_read(ctx)["split_products"] == int(split)
+        outs[split] = host(V).reshape(want.shape)
+    for got in outs.values():
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    assert np.abs(outs["1"] - outs["0"]).max() <= 1e-12 * np.abs(want).max()
+
+
 # --------------------------------------------------------------------------------------------
 # one quasi-Newton step
 # --------------------------------------------------------------------------------------------
@@ -211,6 +239,32 @@ def test_solve_3d_511_bf16x3_full_size(qn):
     assert r255["status"] == 0
     err255 = np.abs(host(U255).reshape(u255.shape) - u255).max()
     assert 3.6 < err255 / err511 < 4.4, (err255, err511)
+
+
+@pytest.mark.parametrize("dim,n,prec,zero", [(3, 63, "bf16x3", True), (2, 63, "fp64", False),
+                                            (3, 130, "bf16x3", False)])
+def test_solve_host_many_matches_single_solves(qn, dim, n, prec, zero):
+    """qn_solve_host_many (copies overlapped with the neighbouring solves, two device
+    buffer pairs) gives each problem the result of its own qn_solve_host, bit for bit,
+    and the oracle's solution to 1e-9."""
+    import torch
+    ctx = qn.QnContext(dim, n, prec)
+    fs, starts = [], []
+    for seed in range(4):
+        u, f = manufactured_problem(n, dim, seed=10 + seed)
+        fs.append(torch.from_numpy(np.ascontiguousarray(f.reshape(-1))).pin_memory().numpy())
+        starts.append(np.zeros(n ** dim) if zero else np.ascontiguousarray((0.5 * u).reshape(-1)))
+    fs[3] = fs[1]                                         # two problems may share an input array
+    outs = [torch.from_numpy(s0.copy()).pin_memory().numpy() for s0 in starts]
+    res = qn.qn_solve_host_many(ctx, outs, fs, zero_start=zero, graph=True)
+    for i in range(4):
+        single = starts[i].copy()
+        r1 = qn.qn_solve_host(ctx, single, fs[i], zero_start=zero, graph=True)
+        assert res[i]["status"] == 0 and res[i]["iterations"] == r1["iterations"]
+        assert np.array_equal(outs[i], single)
+        f3 = fs[i].reshape((n,) * dim)
+        Uo, ho, ok = O.qn_solve(f3, U0=None if zero else starts[i].reshape(f3.shape))
+        assert ok and np.abs(outs[i].reshape(f3.shape) - Uo).max() <= 1e-9 * np.abs(Uo).max()
 
 
 def test_golden_2d_63(qn):
