@@ -305,8 +305,32 @@ def run_batched(qn, seed=0, count=256, reps=3, tiles="auto"):
             its += [r["iterations"] for r in res]
         ok = rc == 0 and all(r["status"] == 0 for r in res)
     ms = statistics.median(times)
+    # whole-solve averages over every launch of a batch (the solve is one graph of grouped
+    # launches, so there is no per-kernel timing here; the launch list is in profiles/):
+    # per instance and iteration, 2 components x 4 products of 2 n^3 algorithmic FLOP (3 P^3 x 2
+    # executed BF16 products each), and bytes: the residual reads u, v (16 B) and the f pairs
+    # (16 B) per node and writes 4 BF16 planes (8 B per padded point), each product reads and
+    # writes hi + lo planes (8 B per padded point), the two updates read and write U, V (32 B)
+    its_by = {}
+    for (n_i, _, _, _), r in zip(specs, res):
+        its_by.setdefault(n_i, []).append(r["iterations"])
+    flop = exe = byt = 0.0
+    for n_i, itl in its_by.items():
+        P_i = ((n_i + 63) // 64) * 64
+        it_sum = float(sum(itl))
+        flop += it_sum * 2 * 4 * 2.0 * n_i ** 3
+        exe += it_sum * 2 * 4 * 3 * 2.0 * P_i ** 3
+        byt += it_sum * (32.0 * n_i ** 2 + 8.0 * P_i ** 2 + 2 * 4 * 8.0 * P_i ** 2 + 32.0 * n_i ** 2)
+    peaks, _ = load_peaks()
+    t_s = ms * 1e-3
+    whole = {"kind": "whole-solve averages over all launches of a batch",
+             "tensor_tflops_algorithmic": round(flop / t_s / 1e12, 2),
+             "tensor_tflops_executed": round(exe / t_s / 1e12, 2),
+             "executed_frac_of_bf16_sustained": round(exe / t_s / 1e12 / float(peaks.get("bf16_tflops_sustained", 1700.0)), 4),
+             "hbm_gbs_algorithmic": round(byt / t_s / 1e9, 1),
+             "hbm_frac": round(byt / t_s / 1e9 / float(peaks.get("hbm_gbs", 6800.0)), 4)}
     return {"workload": f"{count} coupled 2-D systems, n uniform on {{63,127,255,511}}, alpha~U[0,1], "
-                        f"D~U[0.1,10], tol 1e-10, seed {seed}",
+                        f"D~U[0.1,10], tol 1e-10, seed {seed}", "roofline": whole,
             "instances_per_s": round(count / (ms * 1e-3), 1), "ms_per_batch": round(ms, 3),
             "p50_instance_ms": round(float(np.percentile(per_inst, 50)), 3),
             "p99_instance_ms": round(float(np.percentile(per_inst, 99)), 3),

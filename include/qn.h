@@ -341,7 +341,9 @@ int qn_batch_destroy(qn_batch *b);
 /* Project autotuner for the batched mode products: times the grouped
  * split-precision product over `copies` synthetic instances of size n for
  * each candidate (bk in {32, 64}) x (bn in {64, 128, 256}, bn <= P) and
- * returns the fastest. best_ms: mean time of one grouped launch (host). */
+ * returns the fastest. best_ms: mean time of one grouped launch (host). The
+ * result is kept for the process, per (device, n, copies): later calls with
+ * the same arguments return it without timing again. */
 int qn_autotune_tile(int n, int copies, int *best_bk, int *best_bn, double *best_ms);
 
 /* ---- learned warm start ---------------------------------------------------------

@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <new>
+#include <mutex>
 #include <vector>
 
 #include "qn_df.cuh"
@@ -943,10 +944,36 @@ extern "C" int qn_batch_solve(qn_batch *b, const qn_opts *opts, qn_sys_result *r
     return worst;
 }
 
+namespace {
+// qn_autotune_tile results of this process, per (device, n, copies)
+struct TuneKey {
+    int dev, n, copies;
+    bool operator==(const TuneKey &o) const { return dev == o.dev && n == o.n && copies == o.copies; }
+};
+struct TuneVal {
+    int bk, bn;
+    double ms;
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
+}  // namespace
+
 extern "C" int qn_autotune_tile(int n, int copies, int *best_bk, int *best_bn, double *best_ms) {
     if (n < 1 || n > 1024 || copies < 1 || copies > 4096 || !best_bk || !best_bn) {
         set_error("qn_autotune_tile: n in 1..1024, copies in 1..4096, non-null outputs");
         return QN_EINVAL;
+    }
+    int dev = 0;
+    QN_CUDA(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (const auto &e : g_tune_cache)
+            if (e.first == TuneKey{dev, n, copies}) {
+                *best_bk = e.second.bk;
+                *best_bn = e.second.bn;
+                if (best_ms) *best_ms = e.second.ms;
+                return QN_OK;
+            }
     }
     const int P = ((n + 63) / 64) * 64;
     double *zero = nullptr;
@@ -1017,5 +1044,9 @@ extern "C" int qn_autotune_tile(int n, int copies, int *best_bk, int *best_bn, d
     *best_bk = bbk;
     *best_bn = bbn;
     if (best_ms) *best_ms = best;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache.push_back({TuneKey{dev, n, copies}, TuneVal{bbk, bbn, best}});
+    }
     return QN_OK;
 }
