@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "qn_internal.h"
+#include "qn_numeric.cuh"
 
 namespace qn {
 namespace {
@@ -392,6 +393,263 @@ __global__ void __launch_bounds__(256) k_interp3d(const Tin *__restrict__ src, i
     }
 }
 
+// ---------------------------------------------------------------------------
+// Inference path (batch 1, qn_net_predict). The training forward keeps one kernel
+// per stage because the backward pass reads every intermediate; inference needs
+// none of them, so each block runs as three kernels:
+//   k_inf_analysis   the x and y analysis: every CTA reduces a chunk of rows of one
+//                    z plane to its (ky, kx) sums;
+//   k_inf_mix        one CTA per mode k: the z analysis of those sums (fixed order:
+//                    deterministic) and the mixing g = hh R_l;
+//   k_inf_pointwise  z_l = synthesis_xyz(g) + h_l W_l + b_l, h_{l+1} = gelu(z_l): the
+//                    z and y synthesis per CTA and row, the x synthesis per node, so
+//                    the FP32 spectral term is never stored; the last block projects
+//                    to the output channel directly (z_l itself is not stored).
+// The restriction is k_interp3d; the lift and the prolongation have their own
+// kernels (one warp per node / per fine row, no 64-bit division per element).
+constexpr int kInfRows = 16;   // rows of one z plane per CTA
+
+// h0[p][c] = f[p] wl[c] + bl[c], lane = c
+__global__ void __launch_bounds__(256) k_inf_lift(const float *__restrict__ f, const float *__restrict__ wl,
+                                                  const float *__restrict__ bl, __nv_bfloat16 *__restrict__ h,
+                                                  long long pts) {
+    const int lane = threadIdx.x & 31;
+    const float w = wl[lane], b = bl[lane];
+    for (long long p = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; p < pts;
+         p += ((long long)gridDim.x * blockDim.x) >> 5)
+        h[p * 32 + lane] = __float2bfloat16_rn(fmaf(f[p], w, b));
+}
+
+template <int M>
+__global__ void __launch_bounds__(256) k_inf_analysis(const __nv_bfloat16 *__restrict__ h, const float *__restrict__ Ba,
+                                                      int G, float *__restrict__ part) {
+    __shared__ float sBa[M * 256];        // Ba[k][j] = basis_a[k * G + j], G <= 256
+    __shared__ float sQ[M * M * 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int chunks = (G + kInfRows - 1) / kInfRows;
+    const int z = blockIdx.x / chunks, y0 = (blockIdx.x % chunks) * kInfRows;
+    const int y1 = min(y0 + kInfRows, G);
+    for (int t = threadIdx.x; t < M * G; t += blockDim.x) sBa[t] = Ba[t];
+    for (int t = threadIdx.x; t < M * M * 32; t += blockDim.x) sQ[t] = 0.0f;
+    __syncthreads();
+    float Q[M][M];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int b = 0; b < M; ++b) Q[a][b] = 0.0f;
+    for (int y = y0 + warp; y < y1; y += 8) {
+        const __nv_bfloat16 *row = h + (((long long)z * G + y) * G) * 32 + lane;
+        float t[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) t[k] = 0.0f;
+#pragma unroll 4
+        for (int x = 0; x < G; ++x) {
+            const float v = __bfloat162float(row[(long long)x * 32]);
+#pragma unroll
+            for (int k = 0; k < M; ++k) t[k] = fmaf(sBa[k * G + x], v, t[k]);
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            const float b = sBa[a * G + y];
+#pragma unroll
+            for (int k = 0; k < M; ++k) Q[a][k] = fmaf(b, t[k], Q[a][k]);
+        }
+    }
+    // the CTA's (ky, kx) sums of this z plane's rows (the 8 warps' in a fixed order)
+    for (int w = 0; w < 8; ++w) {
+        if (warp == w) {
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+#pragma unroll
+                for (int k = 0; k < M; ++k) sQ[(a * M + k) * 32 + lane] += Q[a][k];
+        }
+        __syncthreads();
+    }
+    float *pb = part + (long long)blockIdx.x * M * M * 32;
+    for (int t = threadIdx.x; t < M * M * 32; t += blockDim.x) pb[t] = sQ[t];
+}
+
+// hh[k][c] = sum_z Ba[kz][z] sum_chunks part[z][chunk][(ky, kx)][c] for one mode
+// k = (kz, ky, kx) per CTA (128 threads: 4 groups of z planes, fixed order), then
+// g[k][o] = sum_i hh[k][i] R[k][i][o].
+template <int M>
+__global__ void __launch_bounds__(128) k_inf_mix(const float *__restrict__ part, const float *__restrict__ Ba, int G,
+                                                 const float *__restrict__ R, float *__restrict__ hh,
+                                                 float *__restrict__ g) {
+    __shared__ float sacc[4][32];
+    const int k = blockIdx.x;
+    const int kz = k / (M * M), e = k % (M * M);
+    const int c = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int chunks = (G + kInfRows - 1) / kInfRows;
+    float acc = 0.0f;
+#pragma unroll 4
+    for (int zz = grp; zz < G; zz += 4) {
+        float sz = 0.0f;
+        for (int ch = 0; ch < chunks; ++ch) sz += __ldg(part + ((long long)(zz * chunks + ch) * M * M + e) * 32 + c);
+        acc = fmaf(__ldg(Ba + kz * G + zz), sz, acc);
+    }
+    sacc[grp][c] = acc;
+    __syncthreads();
+    if (grp != 0) return;
+    const float v = (sacc[0][c] + sacc[1][c]) + (sacc[2][c] + sacc[3][c]);
+    hh[(long long)k * 32 + c] = v;
+    sacc[0][c] = v;
+    __syncwarp();
+    const float *Rk = R + (long long)k * 32 * 32 + c;
+    float o = 0.0f;
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) o = fmaf(sacc[0][i], __ldg(Rk + i * 32), o);
+    g[(long long)k * 32 + c] = o;
+}
+
+template <int M, bool LAST>
+__global__ void __launch_bounds__(256) k_inf_pointwise(const __nv_bfloat16 *__restrict__ h, const float *__restrict__ Bs,
+                                                       int G, const float *__restrict__ g, const float *__restrict__ W,
+                                                       const float *__restrict__ bvec, __nv_bfloat16 *__restrict__ hnext,
+                                                       const float *__restrict__ wp, const float *__restrict__ bp,
+                                                       float *__restrict__ out) {
+    __shared__ float sBs[256 * M];        // Bs[j][k] = basis_s[j * M + k]
+    __shared__ float sgz[M * M * 32];     // g contracted over kz at this CTA's plane z
+    constexpr int U = LAST ? 2 : 4;       // nodes per step (the projection's reductions: two)
+    __shared__ __align__(16) float sh[8][U][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int chunks = (G + kInfRows - 1) / kInfRows;
+    const int z = blockIdx.x / chunks, y0 = (blockIdx.x % chunks) * kInfRows;
+    const int y1 = min(y0 + kInfRows, G);
+    for (int t = threadIdx.x; t < M * G; t += blockDim.x) sBs[t] = Bs[t];
+    __syncthreads();
+    for (int e = threadIdx.x; e < M * M * 32; e += blockDim.x) {
+        float a = 0.0f;
+#pragma unroll
+        for (int k = 0; k < M; ++k) a = fmaf(sBs[z * M + k], g[(long long)k * M * M * 32 + e], a);
+        sgz[e] = a;
+    }
+    float w[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) w[i] = __ldg(W + i * 32 + lane);
+    const float bo = bvec[lane];
+    const float wpl = LAST ? wp[lane] : 0.0f;
+    const float bpv = LAST ? bp[0] : 0.0f;
+    __syncthreads();
+    for (int y = y0 + warp; y < y1; y += 8) {
+        float t1r[M];   // z and y synthesis of this row, per kx
+#pragma unroll
+        for (int kx = 0; kx < M; ++kx) {
+            float a = 0.0f;
+#pragma unroll
+            for (int ky = 0; ky < M; ++ky) a = fmaf(sBs[y * M + ky], sgz[(ky * M + kx) * 32 + lane], a);
+            t1r[kx] = a;
+        }
+        const long long rowbase = ((long long)z * G + y) * G;
+        for (int x = 0; x < G; x += U) {   // U nodes per step
+            const long long p = rowbase + x;
+            float sv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool ok = x + u < G;
+                sh[warp][u][lane] = ok ? __bfloat162float(h[(p + u) * 32 + lane]) : 0.0f;
+                float a = bo;
+#pragma unroll
+                for (int kx = 0; kx < M; ++kx) a = fmaf(ok ? sBs[(x + u) * M + kx] : 0.0f, t1r[kx], a);
+                sv[u] = a;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float4 v = reinterpret_cast<const float4 *>(sh[warp][u])[q];
+                    sv[u] = fmaf(v.x, w[4 * q], sv[u]);
+                    sv[u] = fmaf(v.y, w[4 * q + 1], sv[u]);
+                    sv[u] = fmaf(v.z, w[4 * q + 2], sv[u]);
+                    sv[u] = fmaf(v.w, w[4 * q + 3], sv[u]);
+                }
+            }
+            __syncwarp();
+            if (LAST) {
+                // the U projections reduced over the channels together (independent shuffle chains)
+                float o[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) o[u] = sv[u] * wpl;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                    for (int u = 0; u < U; ++u) o[u] += __shfl_xor_sync(0xffffffffu, o[u], off);
+                if (lane == 0) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (x + u < G) out[p + u] = o[u] + bpv;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (x + u < G) hnext[(p + u) * 32 + lane] = __float2bfloat16_rn(gelu_f(sv[u]));
+            }
+        }
+    }
+}
+
+// U0 (mt^3, FP64) = scale * trilinear prolongation of src (mf^3, FP32) at the nodes
+// i/(mt+1), zero values on the boundary: one warp per fine row; the 1-D corner
+// indices and weights from integer arithmetic (i+1)(mf+1) = j (mt+1) + r, w = r/(mt+1).
+// With sq != nullptr it also adds sum U0^2 to *sq (FP32 per warp, one FP64 atomic per CTA).
+__global__ void __launch_bounds__(256) k_prolong_f32_f64(const float *__restrict__ src, int mf,
+                                                         double *__restrict__ dst, int mt, float scale,
+                                                         double *__restrict__ sq) {
+    __shared__ int sj[kInterpMax];
+    __shared__ float sw[kInterpMax];
+    __shared__ float ssq[8];
+    for (int i = threadIdx.x; i < mt; i += blockDim.x) {
+        const int num = (i + 1) * (mf + 1);
+        sj[i] = num / (mt + 1);   // 1-based left node; 0 and mf+1 are the zero boundary
+        sw[i] = (float)(num % (mt + 1)) / (float)(mt + 1);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long rows = (long long)mt * mt;
+    float wsq = 0.0f;
+    for (long long row = (long long)blockIdx.x * 8 + warp; row < rows; row += (long long)gridDim.x * 8) {
+        const int iz = (int)(row / mt), iy = (int)(row % mt);
+        const int jz = sj[iz], jy = sj[iy];
+        const float wz = sw[iz], wy = sw[iy];
+        float wr[4];
+        const float *ro[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int zz = jz + (c >> 1), yy = jy + (c & 1);
+            const bool ok = zz >= 1 && zz <= mf && yy >= 1 && yy <= mf;
+            wr[c] = ok ? ((c >> 1) ? wz : 1.0f - wz) * ((c & 1) ? wy : 1.0f - wy) : 0.0f;
+            ro[c] = src + (ok ? ((long long)(zz - 1) * mf + (yy - 1)) * mf : 0);
+        }
+        double *drow = dst + row * mt;
+        for (int ix = lane; ix < mt; ix += 32) {
+            const int jx = sj[ix];
+            const float wx = sw[ix];
+            const bool okl = jx >= 1, okr = jx + 1 <= mf;
+            float acc = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float vl = okl ? __ldg(ro[c] + jx - 1) : 0.0f;
+                const float vr = okr ? __ldg(ro[c] + jx) : 0.0f;
+                acc = fmaf(wr[c], fmaf(wx, vr - vl, vl), acc);
+            }
+            const float u = acc * scale;
+            wsq = fmaf(u, u, wsq);
+            drow[ix] = f2d_exact(u);
+        }
+    }
+    if (sq == nullptr) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wsq += __shfl_xor_sync(0xffffffffu, wsq, o);
+    if (lane == 0) ssq[warp] = wsq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += (double)ssq[w];
+        atomicAdd(sq, t);
+    }
+}
+
 // Grid for the kernels that end in per-block reductions (few blocks, many nodes each).
 inline int grid_reduce(long long n, int block = 256) {
     long long g = (n + block - 1) / block;
@@ -429,6 +687,8 @@ struct qn_net {
     std::vector<__nv_bfloat16 *> h, z;
     std::vector<float *> hh;
     float *t1, *t2, *sp, *g, *dg, *dhh, *out, *dout, *dh, *dz, *dh2, *fin, *tgt;
+    float *part;              // inference: per-CTA (ky, kx) sums of k_inf_analysis
+    double *wsq;              // warm-started solves: ||U_1 - U_0||^2, ||U_0||^2
     double *loss;
     long long step;
 };
@@ -458,6 +718,8 @@ static void net_free(qn_net *n) {
     cudaFree(n->fin);
     cudaFree(n->tgt);
     cudaFree(n->loss);
+    cudaFree(n->part);
+    cudaFree(n->wsq);
     delete n;
 }
 
@@ -539,6 +801,11 @@ extern "C" int qn_net_create(int G, int channels, int modes, int blocks, int max
     NCK(cudaMalloc(&n->fin, sizeof(float) * pts));
     NCK(cudaMalloc(&n->tgt, sizeof(float) * pts));
     NCK(cudaMalloc(&n->loss, sizeof(double)));
+    {
+        const long long chunks = (G + kInfRows - 1) / kInfRows;
+        NCK(cudaMalloc(&n->part, sizeof(float) * (size_t)(G * chunks * modes * modes * channels)));
+        NCK(cudaMalloc(&n->wsq, 2 * sizeof(double)));
+    }
     n->step = 0;
     *out = n;
     return QN_OK;
@@ -616,6 +883,42 @@ static int net_forward(qn_net *n, int B, cudaStream_t s) {
                                                  pts);
     QN_CUDA(cudaGetLastError());
     return QN_OK;
+}
+
+// Inference (batch 1) on n->fin, the result in n->out, through the fused kernels.
+template <int M>
+static int net_infer_t(qn_net *n, cudaStream_t s) {
+    const int G = n->G;
+    const long long pts = (long long)G * G * G;
+    const int grid = G * ((G + kInfRows - 1) / kInfRows);
+    k_inf_lift<<<grid_for(pts * 32), 256, 0, s>>>(n->fin, P_wl(n), P_bl(n), n->h[0], pts);
+    for (int l = 0; l < n->L; ++l) {
+        k_inf_analysis<M><<<grid, 256, 0, s>>>(n->h[l], n->basis_a, G, n->part);
+        k_inf_mix<M><<<M * M * M, 128, 0, s>>>(n->part, n->basis_a, G, n->params + off_R(n, l), n->hh[l], n->g);
+        if (l < n->L - 1)
+            k_inf_pointwise<M, false><<<grid, 256, 0, s>>>(n->h[l], n->basis_s, G, n->g, n->params + off_W(n, l),
+                                                           n->params + off_b(n, l), n->h[l + 1], nullptr, nullptr,
+                                                           nullptr);
+        else
+            k_inf_pointwise<M, true><<<grid, 256, 0, s>>>(n->h[l], n->basis_s, G, n->g, n->params + off_W(n, l),
+                                                          n->params + off_b(n, l), nullptr, n->params + off_wp(n),
+                                                          n->params + off_wp(n) + n->C, n->out);
+    }
+    QN_CUDA(cudaGetLastError());
+    return QN_OK;
+}
+
+static int net_infer(qn_net *n, cudaStream_t s) {
+    switch (n->M) {
+        case 2: return net_infer_t<2>(n, s);
+        case 3: return net_infer_t<3>(n, s);
+        case 4: return net_infer_t<4>(n, s);
+        case 5: return net_infer_t<5>(n, s);
+        case 6: return net_infer_t<6>(n, s);
+        case 7: return net_infer_t<7>(n, s);
+        case 8: return net_infer_t<8>(n, s);
+        default: return net_forward(n, 1, s);   // larger mode counts: the unfused kernels
+    }
 }
 
 // Backward pass after net_forward; gradients (overwritten) in n->grads.
@@ -752,20 +1055,25 @@ extern "C" int qn_interp3d_f32(const double *src, int m_from, float *dst, int m_
 
 // Warm start for one fine n^3 source: restrict f to the G^3 grid, run the
 // network, prolong its output to n^3 (times out_scale) into U0.
+// U0 = prolong(net(restrict(f))); with u0_sq != nullptr, *u0_sq += ||U0||^2.
+static int net_predict(qn_net *n, const double *f_fine, int nf, double in_scale, double out_scale, double *U0,
+                       double *u0_sq, cudaStream_t s) {
+    const int G = n->G;
+    k_interp3d<double, float><<<grid_for((long long)G * G * 256), 256, 0, s>>>(f_fine, nf, n->fin, G, 1, in_scale);
+    int rc = net_infer(n, s);
+    if (rc) return rc;
+    k_prolong_f32_f64<<<grid_for((long long)nf * nf * 32), 256, 0, s>>>(n->out, G, U0, nf, (float)out_scale, u0_sq);
+    QN_CUDA(cudaGetLastError());
+    return QN_OK;
+}
+
 extern "C" int qn_net_predict(qn_net *n, const double *f_fine, int nf, double in_scale, double out_scale, double *U0,
                               void *stream) {
     if (!n || !f_fine || !U0 || nf < 1 || nf > 2048) {
         set_error("qn_net_predict: invalid arguments");
         return QN_EINVAL;
     }
-    cudaStream_t s = (cudaStream_t)stream;
-    const int G = n->G;
-    k_interp3d<double, float><<<grid_for((long long)G * G * 256), 256, 0, s>>>(f_fine, nf, n->fin, G, 1, in_scale);
-    int rc = net_forward(n, 1, s);
-    if (rc) return rc;
-    k_interp3d<float, double><<<grid_for((long long)nf * nf * 256), 256, 0, s>>>(n->out, G, U0, nf, 1, out_scale);
-    QN_CUDA(cudaGetLastError());
-    return QN_OK;
+    return net_predict(n, f_fine, nf, in_scale, out_scale, U0, nullptr, (cudaStream_t)stream);
 }
 
 // sums[0] += sum (a - b)^2, sums[1] += sum b^2
@@ -806,19 +1114,16 @@ extern "C" int qn_solve_warm(qn_ctx *ctx, qn_net *net, double *U, const double *
     }
     cudaStream_t s = (cudaStream_t)stream;
     const long long N = (long long)n * n * n;
-    int rc = qn_net_predict(net, f, n, in_scale, out_scale, U, stream);
-    if (rc) return rc;
-    double *sums = nullptr;
-    QN_CUDA(cudaMallocAsync(&sums, 2 * sizeof(double), s));
+    double *sums = net->wsq;
     QN_CUDA(cudaMemsetAsync(sums, 0, 2 * sizeof(double), s));
+    // the prolongation also sums ||U_0||^2 into sums[1]
+    int rc = net_predict(net, f, n, in_scale, out_scale, U, sums + 1, s);
+    if (rc) return rc;
     if (ctx_split_precision(ctx)) {
         // one solve from U_0; its first iteration measures ||U_1 - U_0|| and
         // falls back to the zero start by itself (solve_internal)
-        k_diff_norms<<<grid_for(N), 256, 0, s>>>(U, U, N, sums);   // sums[1] = ||U_0||^2
-        QN_CUDA(cudaGetLastError());
         int used = 0;
         rc = solve_internal(ctx, U, f, opts, res, nullptr, 0, stream, sums + 1, &used);
-        cudaFreeAsync(sums, s);
         if (used_warm) *used_warm = used;
         return rc;
     }
@@ -830,6 +1135,7 @@ extern "C" int qn_solve_warm(qn_ctx *ctx, qn_net *net, double *U, const double *
     rc = qn_step(ctx, U, f, NAN, &st0, stream);          // U1 = U0 - delta
     bool warm = (rc == QN_OK) && isfinite(st0.res_norm);
     if (warm) {
+        QN_CUDA(cudaMemsetAsync(sums, 0, 2 * sizeof(double), s));
         k_diff_norms<<<grid_for(N), 256, 0, s>>>(U, U0, N, sums);
         double h[2] = {0.0, 0.0};
         QN_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -837,7 +1143,6 @@ extern "C" int qn_solve_warm(qn_ctx *ctx, qn_net *net, double *U, const double *
         warm = isfinite(h[0]) && isfinite(h[1]) && h[1] > 0.0 && h[0] < 0.25 * h[1];
     }
     cudaFreeAsync(U0, s);
-    cudaFreeAsync(sums, s);
     if (used_warm) *used_warm = warm ? 1 : 0;
     if (!warm) {
         QN_CUDA(cudaMemsetAsync(U, 0, sizeof(double) * N, s));

@@ -80,6 +80,42 @@ def test_forward_and_gradients_match_oracle(qn, G, M, L, B):
         o += sz
 
 
+@pytest.mark.parametrize("G,M,L,n", [(16, 4, 2, 31), (12, 6, 3, 47), (64, 6, 4, 255), (10, 2, 1, 21)])
+def test_fused_inference_matches_oracle_and_training_forward(qn, G, M, L, n):
+    """qn_net_predict runs the fused inference kernels (analysis and mode mixing in one
+    kernel, the synthesis with the pointwise path in another, the projection in the last
+    block, the prolongation): against the FP64 oracle's restriction, network and
+    prolongation at the BF16 tolerance, and against the unfused training forward on the
+    same restricted input."""
+    import torch
+    C = 32
+    net = qn.QnNet(G, M, L, max_batch=2)
+    p = (random_field((net.nparams,), 51) * 0.2).astype(np.float64)
+    p[:C] = random_field((C,), 52)
+    net.set_params(p.astype(np.float32))
+    pf = net.get_params().astype(np.float64)
+    f = random_field((n, n, n), 53)
+    fd = torch.from_numpy(f.reshape(-1)).cuda()
+    U0 = torch.empty(n ** 3, dtype=torch.float64, device="cuda")
+    in_scale, out_scale = 0.7, 1.3
+    for _ in range(2):   # twice: the second call reuses the network's buffers
+        net.predict(fd, n, U0, in_scale, out_scale)
+    got = U0.cpu().numpy().reshape(n, n, n)
+    Ar, Ap = NO.interp_matrix(n, G), NO.interp_matrix(G, n)
+    fc = np.einsum("pz,qy,rx,zyx->pqr", Ar, Ar, Ar, f, optimize=True) * in_scale
+    want_c, _ = NO.forward(pf, fc[None], C, M, L)
+    want = np.einsum("pz,qy,rx,zyx->pqr", Ap, Ap, Ap, np.asarray(want_c).reshape(G, G, G), optimize=True) * out_scale
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert rel < 3e-2, rel
+    fcd = torch.empty(G ** 3, dtype=torch.float32, device="cuda")
+    qn.qn_interp3d(fd, n, fcd, G, 1, in_scale)
+    out = torch.empty(G ** 3, dtype=torch.float32, device="cuda")
+    net.forward(fcd, out, 1)
+    unf = np.einsum("pz,qy,rx,zyx->pqr", Ap, Ap, Ap, out.cpu().numpy().astype(np.float64).reshape(G, G, G),
+                    optimize=True) * out_scale
+    assert np.linalg.norm(got - unf) / np.linalg.norm(unf) < 2e-2
+
+
 def test_training_reduces_loss_and_warm_start_solves(qn):
     import torch
     from paper_2502_03611_gb300 import warmstart as W
