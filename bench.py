@@ -1020,12 +1020,18 @@ def main():
     first_ms = (prof["residual_ms"] - prof["residual_tiled_ms"]) / max(first_n, 1)
     til_gbs = res_bytes / (til_ms * 1e-3) / 1e9 if til_n else None
     kernels = {
+        # achieved GB/s and the HBM fraction of the full evaluations (the tiled kernel's launches
+        # when there are any; the preparation launches move other bytes)
         "residual": {"avg_launch_ms": round(res_avg_ms, 4), "launches": prof["residual_launches"],
-                     "bytes_per_launch": res_bytes, "achieved_gbs": round(res_gbs, 1),
-                     "frac_hbm": round(res_gbs / hbm, 4), "share": None,
-                     # split 3-D solve: preparation passes of iterations 0 and 1 (FP32-pair copy
-                     # of f and ||f||; max|U_1|), else the per-point residual kernel
-                     "preparation_or_per_point": {"kernel": "k_prep_split / k_umax" if til_n else "k_residual",
+                     "bytes_per_launch": res_bytes,
+                     "achieved_gbs": round(til_gbs if til_n else res_gbs, 1),
+                     "frac_hbm": round((til_gbs if til_n else res_gbs) / hbm, 4), "share": None,
+                     # split 3-D solve: the preparation passes of iterations 0 and 1 (FP32-pair copy
+                     # of f, ||f||, the zero start's residual -f; max|U_1|) and the iteration-0
+                     # residual launch, which only writes its partial records after a zero start;
+                     # else the per-point residual kernel
+                     "preparation_or_per_point": {"kernel": ("k_prep_split / iteration-0 residual / k_umax"
+                                                             if til_n else "k_residual"),
                                                   "launches": first_n, "avg_launch_ms": round(first_ms, 4)},
                      "tiled": {"kernel": "k_residual_tiled", "launches": til_n,
                                           "avg_launch_ms": round(til_ms, 4),

@@ -727,8 +727,14 @@ static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double 
     c->split_layout = mirror ? 1 : 0;
     if (tiled && c->cur_iter <= 1) {
         const long pp = prof_begin(c, PK_RESIDUAL, s);
-        if (c->cur_iter == 0)
-            rc = launch_prep_split(U, f, c->n, c->P, c->fdf, c->partials, c->nparts, c->st, mirror, s);
+        if (c->cur_iter == 0) {
+            // without a potential the pass also writes the zero start's residual -f, and the
+            // residual below only writes its partial records when U_0 = 0
+            const bool zs = (c->pot64 == nullptr);
+            rc = launch_prep_split(U, f, c->n, c->P, c->fdf, zs ? a.Rhi : nullptr, zs ? a.Rlo : nullptr, c->partials,
+                                   c->nparts, c->st, mirror, s);
+            a.zero_start = zs ? c->st : nullptr;
+        }
         else
             rc = launch_umax(U, c->N, c->st, 2 * c->num_sms, s);
         prof_end(c, pp, s);
@@ -739,7 +745,9 @@ static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double 
         a.fast = 1;
         a.want_f2 = 0;
     }
-    const long pr = prof_begin(c, tiled ? PK_RESIDUAL_TILED : PK_RESIDUAL, s);
+    // the iteration-0 launch after the preparation pass (which skips its work for a zero
+    // start) is accounted with the preparation, so that the tiled kind covers full evaluations
+    const long pr = prof_begin(c, (tiled && a.zero_start == nullptr) ? PK_RESIDUAL_TILED : PK_RESIDUAL, s);
     if (mirror) {
         rc = launch_residual_mirror(a, c->nparts, c->res_zc, &c->res_parts, s);
     } else if (tiled) {

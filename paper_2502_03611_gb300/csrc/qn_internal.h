@@ -40,6 +40,7 @@ struct DevState {
     double eig_lambda;   // eigen solves: Rayleigh quotient lambda_n of the current iterate
     double eig_scale;    //   and the normalisation factor 1/||U~|| applied to it
     float2 eig_lambda2, eig_scale2;   // the same two as FP32 pairs (hi, lo)
+    int u0_zero;     // 1: the preparation pass found U_0 = 0 (and wrote the residual -f)
 };
 
 // Residual kernel outputs.
@@ -78,6 +79,9 @@ struct ResidualArgs {
     const double *hval;
     int hbw;
     double robin;              // QN_BC_ROBIN: 2 kappa / h, added times u once per face a node lies on
+    const DevState *zero_start;  // iteration 0 of a split solve (KIND 0-2): when the preparation pass
+                                 // found U_0 = 0 it already wrote the residual -f, so the tiled kernels
+                                 // only write their partial records (nullptr: always evaluate)
 };
 
 // Epilogue selector shared by both mode-product kernels.
@@ -126,7 +130,8 @@ int launch_residual_tiled(const ResidualArgs &a, int max_grid, int zchunk, int *
 // the fixed-point exponent from): iteration 0 -> the FP32-pair copy of f, sum
 // f^2 (DevState::f_norm, r2_exp) and max|U_0|; iteration 1 -> max|U_1|. Both
 // end by setting DevState::fx_e from the scanned max|U|.
-int launch_prep_split(const double *U, const double *f, int n, int P, float2 *fdf, double *partials,
+int launch_prep_split(const double *U, const double *f, int n, int P, float2 *fdf, __nv_bfloat16 *Rhi,
+                      __nv_bfloat16 *Rlo, double *partials,
                       int nparts, DevState *st, bool mirror, cudaStream_t s);
 // The same residual written in split order along x and folded order along y
 // and z, the input layout of the reflection-split mode products.

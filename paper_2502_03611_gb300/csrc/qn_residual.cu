@@ -252,9 +252,15 @@ __device__ __forceinline__ int fx_exponent(unsigned long long umax, const DevSta
 // the |f| range check and the max|U_0| bit pattern. MIRROR: the copy is laid
 // out for k_residual_mirror, entry (z, y, i < P/2) = (f(i), f(n-1-i)) as two
 // FP32 pairs (the second zero where n-1-i <= i); else (z, y, x) = f(x).
+// With Rhi != nullptr it also writes the residual of the zero start, r = -f
+// rounded to FP32 (what the tiled kernels compute at U = 0, bit for bit), into
+// the planes in their layout; the iteration-0 residual then skips its work
+// when the pass found U_0 = 0 (DevState::u0_zero), and overwrites the planes
+// otherwise.
 template <bool MIRROR>
 __global__ void __launch_bounds__(256) k_prep_split(const double *__restrict__ U, const double *__restrict__ f,
                                                     int n, int P, float2 *__restrict__ fdf,
+                                                    __nv_bfloat16 *__restrict__ Rhi, __nv_bfloat16 *__restrict__ Rlo,
                                                     double *__restrict__ partials, DevState *st) {
     const long long rows = (long long)P * P;
     const int H = P / 2, nsym = (n + 1) / 2, nanti = n / 2;
@@ -300,6 +306,18 @@ __global__ void __launch_bounds__(256) k_prep_split(const double *__restrict__ U
                         umax = ab > umax ? ab : umax;
                     }
                     f4[row * H + i] = make_float4(a.x, a.y, b.x, b.y);
+                    if (Rhi != nullptr) {
+                        // split order along x, folded rows (rows of the padding stay in place)
+                        const int y = (int)(row % P), z = (int)(row / P);
+                        const int Fy = (y >= n) ? y : (y < nsym ? 2 * y : 2 * (n - 1 - y) + 1);
+                        const int Fz = (z >= n) ? z : (z < nsym ? 2 * z : 2 * (n - 1 - z) + 1);
+                        const long long o = ((long long)Fz * P + Fy) * P;
+                        // (+ 0.0f: a zero f gives +0, as the residual's arithmetic does)
+                        const float ra = oka[g] ? __fadd_rn(-a.x, 0.0f) : 0.0f;
+                        const float rb = okb[g] ? __fadd_rn(-b.x, 0.0f) : 0.0f;
+                        split_bf16(__fadd_rn(ra, rb), Rhi[o + i], Rlo[o + i]);
+                        split_bf16(okb[g] ? __fsub_rn(ra, rb) : 0.0f, Rhi[o + H + i], Rlo[o + H + i]);
+                    }
                 }
             }
         }
@@ -319,6 +337,8 @@ __global__ void __launch_bounds__(256) k_prep_split(const double *__restrict__ U
                     umax = ab > umax ? ab : umax;
                 }
                 fdf[row * P + x] = fp;
+                if (Rhi != nullptr)
+                    split_bf16((row_ok && x < n) ? __fadd_rn(-fp.x, 0.0f) : 0.0f, Rhi[row * P + x], Rlo[row * P + x]);
             }
         }
     }
@@ -344,7 +364,24 @@ __global__ void __launch_bounds__(256) k_prep_split_finish(const double *partial
     const int k = (rms > 0.0 && rms < INFINITY) ? ilogb(rms) : 0;
     st->r2_exp = k < -120 ? -120 : (k > 120 ? 120 : k);
     st->fx_e = fx_exponent(st->umax_scan, st);
+    st->u0_zero = (st->umax_scan == 0ull) ? 1 : 0;
     st->umax_scan = 0ull;
+}
+
+// The iteration-0 residual of a zero start (the preparation pass wrote r = -f):
+// every CTA writes its partial record only, ||r||^2 = ||f||^2 in CTA 0 and
+// min / max U^2 = 0. True when it did so.
+__device__ __forceinline__ bool zero_start_partials(const ResidualArgs &a) {
+    if (a.zero_start == nullptr || !*(volatile const int *)&a.zero_start->u0_zero) return false;
+    if (threadIdx.x == 0) {
+        double *p = a.partials + 4ll * blockIdx.x;
+        const double fn = a.zero_start->f_norm;
+        p[0] = (blockIdx.x == 0) ? fn * fn : 0.0;
+        p[1] = 0.0;
+        p[2] = 0.0;
+        p[3] = 0.0;
+    }
+    return true;
 }
 
 // max|U| bit pattern of a dense array (iteration 1: the first update's result).
@@ -616,6 +653,7 @@ __device__ __forceinline__ void tile_partials(const ResidualArgs &a, float kr2, 
 template <int KIND>
 __global__ void __launch_bounds__(kTThreads, 2) k_residual_tiled(ResidualArgs a, int zchunk) {
     if (a.done != nullptr && *(volatile const int *)a.done) return;
+    if (KIND != 3 && zero_start_partials(a)) return;
     __shared__ __align__(16) long long spl[2][kSRows * kSRow];
     const int n = a.n, P = a.P;
     const int E = *a.fx_e;
@@ -898,6 +936,7 @@ __device__ __forceinline__ int fold_index(int i, int n, int nsym) {
 template <int KIND>
 __global__ void __launch_bounds__(kTThreads, 2) k_residual_mirror(ResidualArgs a, int zchunk) {
     if (a.done != nullptr && *(volatile const int *)a.done) return;
+    if (KIND != 3 && zero_start_partials(a)) return;
     __shared__ __align__(16) long long spl[2][kSRows * kSRow];
     const int n = a.n, P = a.P, H = a.P / 2;
     const int nsym = (n + 1) / 2, nanti = n / 2;
@@ -1339,12 +1378,12 @@ int launch_residual_tiled(const ResidualArgs &a, int max_grid, int zchunk, int *
     return launch_tiled_kind<2>(a, max_grid, zchunk, grid_used, s);
 }
 
-int launch_prep_split(const double *U, const double *f, int n, int P, float2 *fdf, double *partials,
-                      int nparts, DevState *st, bool mirror, cudaStream_t s) {
+int launch_prep_split(const double *U, const double *f, int n, int P, float2 *fdf, __nv_bfloat16 *Rhi,
+                      __nv_bfloat16 *Rlo, double *partials, int nparts, DevState *st, bool mirror, cudaStream_t s) {
     if (mirror)
-        k_prep_split<true><<<nparts, 256, 0, s>>>(U, f, n, P, fdf, partials, st);
+        k_prep_split<true><<<nparts, 256, 0, s>>>(U, f, n, P, fdf, Rhi, Rlo, partials, st);
     else
-        k_prep_split<false><<<nparts, 256, 0, s>>>(U, f, n, P, fdf, partials, st);
+        k_prep_split<false><<<nparts, 256, 0, s>>>(U, f, n, P, fdf, Rhi, Rlo, partials, st);
     QN_CUDA(cudaGetLastError());
     k_prep_split_finish<<<1, 256, 0, s>>>(partials, nparts, st);
     QN_CUDA(cudaGetLastError());
@@ -1383,7 +1422,7 @@ int launch_finalize(const double *partials, int nparts, DevState *st, qn_stats *
 namespace {
 
 constexpr int kNoAllocMaxBlocks = 1024;               // reduction blocks per call
-constexpr int kNoAllocStateDoubles = 16;              // DevState (<= 128 B)
+constexpr int kNoAllocStateDoubles = 20;              // DevState (<= 160 B)
 constexpr int kNoAllocStatsDoubles = 8;               // one qn_stats (56 B)
 constexpr int kNoAllocDoubles = 4 * kNoAllocMaxBlocks + kNoAllocStateDoubles + kNoAllocStatsDoubles;
 static_assert(sizeof(DevState) <= kNoAllocStateDoubles * sizeof(double), "DevState too large");
