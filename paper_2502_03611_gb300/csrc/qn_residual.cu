@@ -266,20 +266,29 @@ __global__ void __launch_bounds__(256) k_prep_split(const double *__restrict__ U
     const int H = P / 2, nsym = (n + 1) / 2, nanti = n / 2;
     double f2 = 0.0;
     unsigned long long umax = 0ull;
+    float s2h = 0.0f, s2l = 0.0f;   // sum f^2 as a float pair (MIRROR)
     if (MIRROR) {
         // four rows per step, their loads issued together (the pass is
-        // latency-bound with one row per step)
+        // latency-bound with one row per step); rows < P^2 <= 2^22: 32-bit index math
         constexpr int kRows = 4;
         float4 *f4 = reinterpret_cast<float4 *>(fdf);
-        for (long long row0 = blockIdx.x; row0 < rows; row0 += (long long)kRows * gridDim.x) {
+        const unsigned int urows = (unsigned int)rows, uP = (unsigned int)P;
+        for (unsigned int row0 = blockIdx.x; row0 < urows; row0 += (unsigned int)kRows * gridDim.x) {
+            int ys[kRows], zs[kRows];
+#pragma unroll
+            for (int g = 0; g < kRows; ++g) {
+                const unsigned int row = row0 + (unsigned int)g * gridDim.x;
+                zs[g] = (int)(row / uP);
+                ys[g] = (int)(row - (unsigned int)zs[g] * uP);
+            }
             for (int i = threadIdx.x; i < H; i += blockDim.x) {
                 double fa[kRows], fb[kRows], ua[kRows], ub[kRows];
                 bool oka[kRows], okb[kRows];
 #pragma unroll
                 for (int g = 0; g < kRows; ++g) {
-                    const long long row = row0 + (long long)g * gridDim.x;
-                    const int y = (int)(row % P), z = (int)(row / P);
-                    const bool row_ok = row < rows && (y < n) && (z < n);
+                    const unsigned int row = row0 + (unsigned int)g * gridDim.x;
+                    const int y = ys[g], z = zs[g];
+                    const bool row_ok = row < urows && (y < n) && (z < n);
                     const long long cbase = ((long long)z * n + y) * n;
                     oka[g] = row_ok && i < nsym;
                     okb[g] = row_ok && i < nanti;
@@ -290,25 +299,37 @@ __global__ void __launch_bounds__(256) k_prep_split(const double *__restrict__ U
                 }
 #pragma unroll
                 for (int g = 0; g < kRows; ++g) {
-                    const long long row = row0 + (long long)g * gridDim.x;
-                    if (row >= rows) break;
+                    const unsigned int row = row0 + (unsigned int)g * gridDim.x;
+                    if (row >= urows) break;
                     float2 a = make_float2(0.0f, 0.0f), b = a;
                     if (oka[g]) {
-                        f2 = fma(fa[g], fa[g], f2);
                         a = f_pair(fa[g], &st->fx_fbad);
                         const unsigned long long ab = abs_bits(ua[g]);
                         umax = ab > umax ? ab : umax;
                     }
                     if (okb[g]) {
-                        f2 = fma(fb[g], fb[g], f2);
                         b = f_pair(fb[g], &st->fx_fbad);
                         const unsigned long long ab = abs_bits(ub[g]);
                         umax = ab > umax ? ab : umax;
                     }
-                    f4[row * H + i] = make_float4(a.x, a.y, b.x, b.y);
+                    // f^2 = hi^2 + 2 hi lo (+ lo^2, below 2^-46 of it) as a float pair
+                    {
+                        float p = __fmul_rn(a.x, a.x), e = __fmaf_rn(a.x, a.x, -p);
+                        e = __fmaf_rn(__fadd_rn(a.x, a.x), a.y, e);
+                        const float q = __fmul_rn(b.x, b.x);
+                        float eq = __fmaf_rn(b.x, b.x, -q);
+                        eq = __fmaf_rn(__fadd_rn(b.x, b.x), b.y, eq);
+                        float t, te;
+                        two_sum(p, q, t, te);
+                        float s, se;
+                        two_sum(s2h, t, s, se);
+                        s2l = __fadd_rn(s2l, __fadd_rn(se, __fadd_rn(te, __fadd_rn(e, eq))));
+                        s2h = s;
+                    }
+                    f4[(long long)row * H + i] = make_float4(a.x, a.y, b.x, b.y);
                     if (Rhi != nullptr) {
                         // split order along x, folded rows (rows of the padding stay in place)
-                        const int y = (int)(row % P), z = (int)(row / P);
+                        const int y = ys[g], z = zs[g];
                         const int Fy = (y >= n) ? y : (y < nsym ? 2 * y : 2 * (n - 1 - y) + 1);
                         const int Fz = (z >= n) ? z : (z < nsym ? 2 * z : 2 * (n - 1 - z) + 1);
                         const long long o = ((long long)Fz * P + Fy) * P;
@@ -321,6 +342,7 @@ __global__ void __launch_bounds__(256) k_prep_split(const double *__restrict__ U
                 }
             }
         }
+        f2 = (double)s2h + (double)s2l;
     }
     for (long long row = blockIdx.x; !MIRROR && row < rows; row += gridDim.x) {
         const int y = (int)(row % P), z = (int)(row / P);
