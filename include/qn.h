@@ -73,6 +73,21 @@ extern "C" {
                                hi*hi + hi*lo + lo*hi BF16 products, FP32
                                accumulation; residual, beta, update and stop
                                test stay FP64 (outer loop = iterative refinement) */
+#define QN_PREC_BF16X6 2    /* QN_PREC_BF16X3 with the backward mode products as six
+                               BF16 products of three-level operands (x = x0 + x1 + x2,
+                               each level the BF16 rounding of what the previous ones
+                               leave): a0 b0 + a0 b1 + a1 b0 + a1 b1 + a0 b2 + a2 b0, FP32
+                               accumulation; the spectral coefficients and the backward
+                               intermediates are stored as three levels. The forward
+                               products stay three-term: their error is divided by the
+                               eigenvalue sums, while the backward products' error is
+                               spread over all modes and A_h amplifies it by up to its
+                               stiffness ratio, so it sets a BF16X3 correction's residual
+                               (about 2e-2 of ||F|| at 255^3, growing as n^2) and
+                               BF16X6 cuts it about 20-fold. 3-D finite differences with
+                               the reflection-split products only (Dirichlet or Neumann,
+                               P = 64 ceil(n/64) a multiple of 128); QN_EUNSUPPORTED
+                               otherwise. Two more padded n^3 x 2-byte buffers. */
 
 #define QN_BETA_PAPER 0     /* beta_n = (max + min)/2 of diag(3 b U^2 + V) (eq. identity-method) */
 #define QN_BETA_FIXED 1     /* beta_n = qn_opts.beta_value every iteration */
@@ -83,7 +98,7 @@ typedef struct qn_problem {
     int n;            /* unknowns per axis (same on every axis): Dirichlet 1..1024 interior
                          nodes, Neumann 2..1024 nodes with both faces */
     int bc;           /* QN_BC_DIRICHLET or QN_BC_NEUMANN */
-    int precision;    /* QN_PREC_FP64 or QN_PREC_BF16X3 */
+    int precision;    /* QN_PREC_FP64, QN_PREC_BF16X3 or QN_PREC_BF16X6 */
     double lam;       /* linear coefficient lam of -Lap u + lam u + b u^3 + V u = f */
     double b;         /* cubic coefficient b */
     double length;    /* side L of the cubic domain; 0 selects 1 (the unit cube) */
@@ -176,7 +191,7 @@ int qn_setup_1d_sem(int n, int k, double length, int bc, double *H, double *S, d
 
 /* Create a context for one problem shape on the current CUDA device: uploads
  * S, S^{-1} and the eigenvalues (and their BF16 hi/lo splits for
- * QN_PREC_BF16X3), allocates the working buffers (about 2 n^dim doubles for
+ * QN_PREC_BF16X3 / BF16X6), allocates the working buffers (about 2 n^dim doubles for
  * FP64, 2 padded n^dim x 4 bytes for BF16X3) and, for BF16X3, builds the TMA
  * tensor maps. QN_EUNSUPPORTED for BF16X3 on a device without sm_103a
  * tcgen05 support. *out is owned by the library until qn_ctx_destroy. */
@@ -218,6 +233,21 @@ int qn_step(qn_ctx *ctx, double *U, const double *f, double beta, qn_stats *st, 
  * Returns res->status (QN_OK when converged). */
 int qn_solve(qn_ctx *ctx, double *U, const double *f, const qn_opts *opts,
              qn_result *res, qn_stats *history, int history_len, void *stream);
+
+/* Precision escalation for the solves of a BF16X3 context. rate > 0: at every host
+ * check of qn_solve (every opts->sync_every iterations) the one-step contraction
+ * rho = rel_it / rel_{it-1} is compared with the quasi-Newton bound
+ * b = max|diag(N_h)_U - beta| / (lambda_min(A_h) + beta) at U_it (Sec. 5: the error of the
+ * simplified Jacobian); when rho > rate and rho > 2 b, the precision of the split products,
+ * not the nonlinearity, sets the rate, and the remaining iterations of that solve run the
+ * backward products at the six-product level of QN_PREC_BF16X6. rate = 0 (the default)
+ * turns it off. The first call with rate > 0 allocates the third BF16 level of the working
+ * buffers (two padded n^3 x 2-byte buffers); QN_ENOMEM if that fails. QN_EUNSUPPORTED
+ * unless the context is BF16X3 with the reflection-split products (the shapes
+ * QN_PREC_BF16X6 accepts); a BF16X6 context runs every iteration at that level and only
+ * records the rate. QN_EINVAL for a negative or non-finite rate. Does not synchronise.
+ * qn_profile.x6_from reports where the last solve switched. */
+int qn_set_escalation(qn_ctx *ctx, double rate);
 
 /* qn_solve with HOST arrays: copies f_host and U_host (initial iterate) to
  * context-owned device buffers, solves, copies the result back into U_host.
@@ -455,6 +485,9 @@ typedef struct qn_profile {
     int split_products;       /* 1: the last shifted inverse used the reflection-split mode
                                  products (3-D split solve, n+ padding a multiple of 128):
                                  half the tensor work of the dense products */
+    int x6_from;              /* the last qn_solve: the first iteration whose backward products
+                                 ran at the six-product level (0 in a QN_PREC_BF16X6 context,
+                                 the escalation point after qn_set_escalation), -1: none */
 } qn_profile;
 
 /* on != 0: from now on record a pair of CUDA events around every kernel

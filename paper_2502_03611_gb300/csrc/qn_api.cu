@@ -105,7 +105,7 @@ struct qn_ctx {
         double *U;
         const double *f;
         double step;
-        int chunk, kind;
+        int chunk, kind, x6;
         long long launches;
     } g_prev;
     // the solver state read by the host: written by a kernel into mapped page-locked host
@@ -125,6 +125,17 @@ struct qn_ctx {
     int last_split;       // 1: the last shifted inverse used the split products
     int f64_split;        // FP64 path: reflection-split FP64 products (FD Dirichlet / Neumann)
     __nv_bfloat16 *bf_hi, *bf_lo, *bb_hi, *bb_lo;   // [P][P/2] forward / backward matrices
+    // six-product backward level (QN_PREC_BF16X6): the third BF16 level of the two working
+    // buffers and of the backward matrix; x6 = 1 while the solves use it
+    __nv_bfloat16 *bl2[2], *bb_l2;
+    int x6;               // the level the products enqueued next use
+    int x6_base;          // 1: a QN_PREC_BF16X6 context (every solve starts with the level on)
+    // precision escalation of BF16X3 solves (qn_ctx_set_escalation): the observed one-step
+    // contraction above esc_rate and above twice the nonlinear bound switches the
+    // remaining iterations of the solve to the six-product level
+    double esc_rate;      // 0: off
+    int esc_at;           // first iteration of the last solve that ran at that level (-1: none)
+    int g_x6;             // the captured graph's level
     float *lam32_split;   // eigenvalues in split mode order (even modes, then odd), 1e30 padding
     // separable potential V = v_x + v_y (+ v_z): device tables [dim][n], FP64 and as FP32
     // pairs with lam added to the last axis (k_residual_tiled / mirror); nullptr: V = 0
@@ -147,7 +158,9 @@ struct StateMirror {
     DevState st;
     int err;        // the device error word (QN_ETIMEOUT), taken and cleared by the mirror kernel
     int pad;
-    qn_stats last;  // hist[st.it]: the statistics of the iterate evaluated last
+    qn_stats last;  // the statistics of the iterate evaluated last: hist[st.it] once the solve
+                    // is done, hist[st.it - 1] before (st.it then names the next iterate)
+    qn_stats prev;  // the record before `last` (unchanged when `last` is hist[0])
 };
 
 // The solver state from host parameters (one thread; no copy-engine transfer).
@@ -162,7 +175,9 @@ __global__ void k_mirror_state(const DevState *st, int *err, const qn_stats *his
     const DevState v = *st;
     out->st = v;
     out->err = atomicExch(err, 0);
-    if (hist != nullptr && v.it >= 0 && v.it < hist_cap) out->last = hist[v.it];
+    const int li = v.done ? v.it : v.it - 1;
+    if (hist != nullptr && li >= 0 && li < hist_cap) out->last = hist[li];
+    if (hist != nullptr && li >= 1 && li - 1 < hist_cap) out->prev = hist[li - 1];
     __threadfence_system();
 }
 
@@ -204,7 +219,13 @@ static void split_host(double v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
     lo = __float2bfloat16_rn(f - __bfloat162float(hi));
 }
 
-extern "C" int qn_version(void) { return 10200; }
+// The third level below split_host's two: what hi + lo leave of v, rounded to BF16.
+static __nv_bfloat16 split_host_l2(double v, __nv_bfloat16 hi, __nv_bfloat16 lo) {
+    const double r = v - (double)__bfloat162float(hi) - (double)__bfloat162float(lo);
+    return __float2bfloat16_rn((float)r);
+}
+
+extern "C" int qn_version(void) { return 10300; }
 
 extern "C" const char *qn_last_error(void) { return g_err; }
 
@@ -277,6 +298,9 @@ static void ctx_free(qn_ctx *c) {
     cudaFree(c->bf_lo);
     cudaFree(c->bb_hi);
     cudaFree(c->bb_lo);
+    cudaFree(c->bb_l2);
+    cudaFree(c->bl2[0]);
+    cudaFree(c->bl2[1]);
     cudaFree(c->lam32_split);
     cudaFree(c->pot64);
     cudaFree(c->pot2);
@@ -335,6 +359,23 @@ static void ctx_free(qn_ctx *c) {
         }                                         \
     } while (0)
 
+// The working buffers' third level and its tensor maps (once per context).
+static int ensure_x6(qn_ctx *c) {
+    if (c->bl2[0] != nullptr) return QN_OK;
+    if (!c->split || c->bb_l2 == nullptr) return QN_EUNSUPPORTED;
+    const size_t pb = sizeof(__nv_bfloat16) * (size_t)c->NP;
+    for (int b = 0; b < 2; ++b) {
+        if (cudaMalloc(&c->bl2[b], pb) != cudaSuccess) {
+            cudaFree(c->bl2[0]);
+            c->bl2[0] = nullptr;
+            set_error("ensure_x6: out of device memory for the third BF16 level");
+            return QN_ENOMEM;
+        }
+        QN_CUDA(cudaMemset(c->bl2[b], 0, pb));
+    }
+    return tc_plan_enable_x6(c->plan, c->bl2, c->bb_l2);
+}
+
 extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
     if (!p || !out) {
         set_error("qn_ctx_create: null argument");
@@ -373,7 +414,7 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
                 return QN_EINVAL;
             }
     }
-    if (p->precision != QN_PREC_FP64 && p->precision != QN_PREC_BF16X3) {
+    if (p->precision != QN_PREC_FP64 && p->precision != QN_PREC_BF16X3 && p->precision != QN_PREC_BF16X6) {
         set_error("qn_ctx_create: unknown precision %d", p->precision);
         return QN_EINVAL;
     }
@@ -385,6 +426,10 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
     if (!c) return QN_ENOMEM;
     memset(c, 0, sizeof(*c));
     c->prob = *p;
+    // BF16X6 is the BF16X3 path with the six-product backward level on: every
+    // other part of the context (residual, forward products, state) is the same
+    const bool want_x6 = (p->precision == QN_PREC_BF16X6);
+    if (want_x6) c->prob.precision = QN_PREC_BF16X3;
     c->prof = new (std::nothrow) std::vector<qn_ctx::ProfRec>();
     if (!c->prof) {
         delete c;
@@ -623,6 +668,35 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
                 ctx_free(c);
                 return rc;
             }
+            if (c->split) {
+                // third level of the backward matrix (after the hi / lo above; small, kept for
+                // qn_ctx_set_escalation too); the working buffers' level only for BF16X6
+                std::vector<__nv_bfloat16> bl2v((size_t)P * H);
+                for (size_t i = 0; i < bl2v.size(); ++i) {
+                    const int r = (int)(i / H), ii = (int)(i % H);
+                    const int j = (r < H) ? r : r - H;
+                    const int jmax = (r < H) ? nsym : nanti;
+                    const int k = (r < H) ? 2 * ii : 2 * ii + 1;
+                    const double v = (j < jmax && k < n) ? S[(size_t)j * n + k] : 0.0;
+                    bl2v[i] = split_host_l2(v, bh[i], blo[i]);
+                }
+                CK(cudaMalloc(&c->bb_l2, bb));
+                CK(cudaMemcpy(c->bb_l2, bl2v.data(), bb, cudaMemcpyHostToDevice));
+            }
+            if (c->split && want_x6) {
+                rc = ensure_x6(c);
+                if (rc != QN_OK) {
+                    ctx_free(c);
+                    return rc;
+                }
+                c->x6 = c->x6_base = 1;
+            }
+        }
+        if (want_x6 && !c->x6) {
+            set_error("qn_ctx_create: QN_PREC_BF16X6 needs the reflection-split products (3-D finite "
+                      "differences, Dirichlet or Neumann, padded size P = 64 ceil(n/64) a multiple of 128)");
+            ctx_free(c);
+            return QN_EUNSUPPORTED;
         }
     }
     *out = c;
@@ -776,7 +850,7 @@ static int enqueue_inverse(qn_ctx *c, const double *r0, double *target, bool upd
             const bool last = (i == 5);
             const int next = 1 - cur;
             const long pr = prof_begin(c, last ? PK_MP_LAST : (i == 2 ? PK_MP_DIVIDE : PK_MP_STORE), s);
-            const int rc = launch_modeprod_tc_split(c->plan, cur, last ? -1 : next, seq[i], e, s);
+            const int rc = launch_modeprod_tc_split(c->plan, cur, last ? -1 : next, seq[i], e, s, c->x6 && i >= 2);
             prof_end(c, pr, s);
             if (rc != QN_OK) return rc;
             cur = next;
@@ -834,11 +908,13 @@ static int enqueue_iteration(qn_ctx *c, double *U, const double *f, double step,
 static int enqueue_eig_iteration(qn_ctx *c, double *U, double step, cudaStream_t s);
 
 static int ensure_iteration_graph(qn_ctx *c, double *U, const double *f, double step, int chunk, int kind = 0) {
-    if (c->gexec && c->g_U == U && c->g_f == f && c->g_step == step && c->g_chunk == chunk && c->g_kind == kind)
+    if (c->gexec && c->g_U == U && c->g_f == f && c->g_step == step && c->g_chunk == chunk && c->g_kind == kind &&
+        c->g_x6 == c->x6)
         return QN_OK;
-    qn_ctx::GraphSlot cur{c->gexec, c->g_U, c->g_f, c->g_step, c->g_chunk, c->g_kind, c->g_launches};
+    qn_ctx::GraphSlot cur{c->gexec, c->g_U, c->g_f, c->g_step, c->g_chunk, c->g_kind, c->g_x6, c->g_launches};
     const qn_ctx::GraphSlot &pv = c->g_prev;
-    if (pv.exec && pv.U == U && pv.f == f && pv.step == step && pv.chunk == chunk && pv.kind == kind) {
+    if (pv.exec && pv.U == U && pv.f == f && pv.step == step && pv.chunk == chunk && pv.kind == kind &&
+        pv.x6 == c->x6) {
         // the previous graph matches: swap it in
         c->gexec = pv.exec;
         c->g_U = pv.U;
@@ -846,6 +922,7 @@ static int ensure_iteration_graph(qn_ctx *c, double *U, const double *f, double 
         c->g_step = pv.step;
         c->g_chunk = pv.chunk;
         c->g_kind = pv.kind;
+        c->g_x6 = pv.x6;
         c->g_launches = pv.launches;
         c->g_prev = cur;
         return QN_OK;
@@ -885,6 +962,7 @@ static int ensure_iteration_graph(qn_ctx *c, double *U, const double *f, double 
     c->g_step = step;
     c->g_chunk = chunk;
     c->g_kind = kind;
+    c->g_x6 = c->x6;
     return QN_OK;
 }
 
@@ -976,6 +1054,7 @@ extern "C" int qn_step(qn_ctx *c, double *U, const double *f, double beta, qn_st
     }
     cudaStream_t s = (cudaStream_t)stream;
     const bool paper = isnan(beta);
+    c->x6 = c->x6_base;
     rc = reset_state(c, -1.0, 1, paper ? QN_BETA_PAPER : QN_BETA_FIXED, paper ? 0.0 : beta, s);
     if (rc) return rc;
     c->cur_iter = 0;
@@ -997,6 +1076,42 @@ bool qn::ctx_split_precision(const qn_ctx *c) { return c != nullptr && c->prob.p
 bool qn::ctx_unit_dirichlet(const qn_ctx *c) {
     return c != nullptr && c->prob.bc == QN_BC_DIRICHLET && c->pot64 == nullptr && c->prob.sem_k == 0 &&
            fabs(c->h * (c->n + 1) - 1.0) < 1e-12;
+}
+
+// Precision escalation: the one-step contraction rel_it / rel_{it-1} of the residual
+// against the quasi-Newton bound max|(N_h)_U - beta| / (lambda_min(A_h) + beta) at U_it
+// (Sec. 5: the error of the simplified Jacobian). A contraction above esc_rate and above
+// twice that bound comes from the split products' precision, not from the nonlinearity.
+static bool escalation_due(const qn_ctx *c, int it) {
+    if (it < 1) return false;   // `it`: the iterate evaluated last (the mirror's `last`)
+    const volatile StateMirror *m = c->mir_host;
+    const double rel = m->last.rel, rel0 = m->prev.rel, beta = m->last.beta;
+    if (!(rel0 > 0.0) || !std::isfinite(rel)) return false;
+    const double rho = rel / rel0;
+    const double l1 = (c->prob.bc == QN_BC_NEUMANN) ? 0.0 : fmax(c->lam_min, 0.0);
+    const double den = c->dim * l1 + c->prob.lam + beta;
+    if (!(den > 0.0)) return false;
+    const double bound = fmax(fabs(m->last.fu_max - beta), fabs(m->last.fu_min - beta)) / den;
+    return rho > c->esc_rate && rho > 2.0 * bound;
+}
+
+extern "C" int qn_set_escalation(qn_ctx *c, double rate) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!(rate >= 0.0) || !std::isfinite(rate)) {
+        set_error("qn_set_escalation: rate must be finite and >= 0");
+        return QN_EINVAL;
+    }
+    if (rate > 0.0 && c->x6_base == 0) {
+        if (c->prob.precision != QN_PREC_BF16X3 || !c->split) {
+            set_error("qn_set_escalation: needs a BF16X3 context with the reflection-split products");
+            return QN_EUNSUPPORTED;
+        }
+        rc = ensure_x6(c);
+        if (rc) return rc;
+    }
+    c->esc_rate = rate;
+    return QN_OK;
 }
 
 extern "C" int qn_solve(qn_ctx *c, double *U, const double *f, const qn_opts *opts, qn_result *res,
@@ -1037,6 +1152,8 @@ int qn::solve_internal(qn_ctx *c, double *U, const double *f, const qn_opts *opt
     }
     cudaStream_t s = (cudaStream_t)stream;
     c->aux_launches = 0;
+    c->x6 = c->x6_base;
+    c->esc_at = c->x6_base ? 0 : -1;
     rc = reset_state(c, o.tol, o.max_it, o.beta_mode, o.beta_value, s);
     if (rc) return rc;
     DevState h;
@@ -1099,6 +1216,10 @@ int qn::solve_internal(qn_ctx *c, double *U, const double *f, const qn_opts *opt
         rc = read_state(c, &h, s);
         if (rc) return rc;
         if (h.done) break;
+        if (c->esc_rate > 0.0 && !c->x6 && escalation_due(c, h.it - 1)) {
+            c->x6 = 1;
+            c->esc_at = enqueued;
+        }
     }
     if (!h.done) {   // cannot happen: the finaliser stops at max_it
         set_error("qn_solve: internal iteration accounting error");
@@ -1285,6 +1406,7 @@ extern "C" int qn_profile_read(qn_ctx *c, qn_profile *out) {
     out->residual_tiled_launches = cnt[PK_RESIDUAL_TILED];
     out->residual_tiled_ms = ms[PK_RESIDUAL_TILED];
     out->split_products = c->last_split;
+    out->x6_from = c->esc_at;
     out->finalize_launches = cnt[PK_FINALIZE];
     out->finalize_ms = ms[PK_FINALIZE];
     out->modeprod_launches = cnt[PK_MP_STORE] + cnt[PK_MP_DIVIDE] + cnt[PK_MP_LAST];
@@ -1378,6 +1500,7 @@ extern "C" int qn_eig_solve(qn_ctx *c, double *U, const qn_opts *opts, qn_result
         return QN_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    c->x6 = c->x6_base;
     if (c->prob.precision == QN_PREC_BF16X3 && !c->eig_r0)
         QN_CUDA(cudaMalloc(&c->eig_r0, sizeof(double) * (size_t)c->N));
     if (c->pot64 != nullptr && !c->eig_vrow) {

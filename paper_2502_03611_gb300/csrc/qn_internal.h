@@ -179,7 +179,9 @@ int launch_modeprod_f64(const double *A, const double *B, double *out, const Gem
 // solve) or of many groups (batched solve: every instance and component).
 struct TcGroup {
     const CUtensorMap *a_hi, *a_lo, *b_hi, *b_lo;   // tensor maps in global memory (64-B aligned)
+    const CUtensorMap *a_l2, *b_l2;                   // third operand levels (six-product backward)
     __nv_bfloat16 *out_hi, *out_lo;                   // EPI_STORE / EPI_DIVIDE destination planes
+    __nv_bfloat16 *out_l2;                            // third output level (three-level outputs)
     double *U;                                        // EPI_UPDATE / EPI_DENSE target (dense n^dim)
     float *dsq;                                       // update epilogues: += sum (step * delta)^2 (nullptr: off)
     const float *lam32;                               // padded eigenvalues (P entries, 1e30 past n)
@@ -210,9 +212,16 @@ int launch_modeprod_tc(TcPlan *plan, int src, int dst, bool forward, Epi epi,
 int tc_plan_enable_split(TcPlan *plan, const __nv_bfloat16 *bf_hi, const __nv_bfloat16 *bf_lo,
                          const __nv_bfloat16 *bb_hi, const __nv_bfloat16 *bb_lo);
 bool tc_plan_has_split(const TcPlan *plan);
+// Six-product backward level of the reflection-split products: the third BF16
+// level of the two working buffers (P^3 each) and of the backward matrix
+// ([P][P/2]). Needs tc_plan_enable_split first.
+int tc_plan_enable_x6(TcPlan *plan, __nv_bfloat16 *bufs_l2[2], const __nv_bfloat16 *bb_l2);
 // One reflection-split product: EPI_STORE_BFLY / EPI_DIVIDE (forward) or
-// EPI_STORE_PQ / EPI_UPDATE_PQ (backward).
-int launch_modeprod_tc_split(TcPlan *plan, int src, int dst, Epi epi, const EpiArgs &e, cudaStream_t s);
+// EPI_STORE_PQ / EPI_UPDATE_PQ (backward). x6: the divide writes three BF16
+// levels and the backward products read three levels and form six products
+// (and write three levels); needs tc_plan_enable_x6.
+int launch_modeprod_tc_split(TcPlan *plan, int src, int dst, Epi epi, const EpiArgs &e, cudaStream_t s,
+                             bool x6 = false);
 // Grouped launch over a device tile table (batched solves).
 // Test-only: the next k_modeprod_tc launch has block 0's producer withhold its first stage.
 int tc_test_withhold_arrival();

@@ -46,6 +46,17 @@
 // next product contracts is the fast part of m, stored in folded order (j at
 // 2j, its mirror at 2j+1), so partners sit in adjacent TMEM lanes (one shuffle).
 //
+// Six-product backward level (template flag L3; the BF16X6 precision). The
+// error of a three-product correction is spread evenly over all modes, and A_h
+// amplifies it by up to its stiffness ratio lambda_max/lambda_min: the backward
+// products set the correction's residual, the forward products' error is
+// divided by the eigenvalue sums. With L3 the divide epilogue (MODE 1) writes
+// its output as three BF16 levels x = x0 + x1 + x2 (each the rounded remainder
+// of the previous), and the backward products (MODE 2) read three levels of A
+// and of B and accumulate the six products a0 b0 + a0 b1 + a1 b0 + a1 b1 +
+// a0 b2 + a2 b0 (every term down to 2^-16 of the leading one; FP32
+// accumulation), writing three levels again. The stages then hold six tiles.
+//
 // Every mbarrier wait is bounded (2 s of %globaltimer). On expiry the kernel
 // sets the device error flag, tells the other roles to stop, waits (bounded)
 // for its own outstanding TMA copies and MMAs, frees TMEM and returns.
@@ -114,6 +125,27 @@ __device__ __forceinline__ void split_store(float v, __nv_bfloat16 *hi, __nv_bfl
     lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
+// Three levels: each the BF16 rounding of what the previous levels leave (the
+// remainders are exact in FP32), 8 + 8 + 8 significant bits.
+__device__ __forceinline__ void split_store3(float v, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                                             __nv_bfloat16 *l2, int o) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    hi[o] = h;
+    lo[o] = m;
+    l2[o] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+// Store one output value as two or three levels.
+template <bool L3>
+__device__ __forceinline__ void store_lv(float v, const TcGroup &G, int o) {
+    if (L3)
+        split_store3(v, G.out_hi, G.out_lo, G.out_l2, o);
+    else
+        split_store(v, G.out_hi, G.out_lo, o);
+}
+
 // Group and tile origin of tile t: single-group launches enumerate the tiles
 // of `g0` (m-major); grouped launches read the tile table.
 __device__ __forceinline__ void tile_info(int t, const TcGroup &g0, const TcGroup *groups,
@@ -137,7 +169,7 @@ __device__ __forceinline__ bool group_done(const TcGroup &G) {
 // 576 threads x 104 registers (one CTA per SM; 112 exceeds the launch limit)
 static_assert(kThreads * 104 <= 65536, "register file");
 
-template <int BK, int EPI, int DIM, int MODE>
+template <int BK, int EPI, int DIM, int MODE, bool L3 = false>
 __global__ void __maxnreg__(104)
     k_modeprod_tc(const TcGroup g0, const TcGroup *__restrict__ groups, const TcTile *__restrict__ tiles,
                   const int ntiles, const int stages, int *err) {
@@ -148,7 +180,12 @@ __global__ void __maxnreg__(104)
     constexpr int kKSteps = BK / 16;
     constexpr uint32_t a_bytes = BM * kRowBytes;
     constexpr uint32_t b_bytes_max = bn_slot(MODE) * kRowBytes;
-    constexpr uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes_max;
+    // operand levels in shared memory: three for the six-product backward products
+    constexpr bool IN3 = L3 && MODE == 2;
+    constexpr uint32_t kLv = IN3 ? 3u : 2u;
+    constexpr uint32_t b_off = kLv * a_bytes;   // B levels follow the A levels
+    constexpr uint32_t stage_bytes = kLv * a_bytes + kLv * b_bytes_max;
+    static_assert(!L3 || (MODE == 1 && EPI == EPI_DIVIDE) || MODE == 2, "three levels: divide or backward");
 
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = ptx::smem_u32(smem_raw);
@@ -208,7 +245,7 @@ __global__ void __maxnreg__(104)
             int m0, n0;
             tile_info(t, g0, groups, tiles, G, m0, n0);
             if (group_done(G)) continue;
-            const uint32_t tx_bytes = 2 * a_bytes + 2u * (uint32_t)G.BN * kRowBytes;
+            const uint32_t tx_bytes = kLv * (a_bytes + (uint32_t)G.BN * kRowBytes);
             const int Hh = G.P >> 1, KBh = Hh / BK;
             const int KB = (MODE == 0) ? G.P / BK : (MODE == 1 ? KBh : 2 * KBh);
             for (int kb = 0; kb < KB; ++kb) {
@@ -232,8 +269,10 @@ __global__ void __maxnreg__(104)
                     ptx::mbar_arrive_expect_tx(full_bar(s), tx_bytes);
                     ptx::tma_load_2d(st, G.a_hi, full_bar(s), ax, m0);
                     ptx::tma_load_2d(st + a_bytes, G.a_lo, full_bar(s), ax, m0);
-                    ptx::tma_load_2d(st + 2 * a_bytes, G.b_hi, full_bar(s), bx, by);
-                    ptx::tma_load_2d(st + 2 * a_bytes + b_bytes_max, G.b_lo, full_bar(s), bx, by);
+                    if (IN3) ptx::tma_load_2d(st + 2 * a_bytes, G.a_l2, full_bar(s), ax, m0);
+                    ptx::tma_load_2d(st + b_off, G.b_hi, full_bar(s), bx, by);
+                    ptx::tma_load_2d(st + b_off + b_bytes_max, G.b_lo, full_bar(s), bx, by);
+                    if (IN3) ptx::tma_load_2d(st + b_off + 2 * b_bytes_max, G.b_l2, full_bar(s), bx, by);
                     armed_parity[s] = ph;
                     armed_mask |= 1u << s;
                 }
@@ -280,13 +319,21 @@ __global__ void __maxnreg__(104)
                     const uint32_t koff = (uint32_t)kk * 32u;
                     const uint64_t a_hi = ptx::smem_desc_kmajor(st + koff, kRowBytes, kLayout);
                     const uint64_t a_lo = ptx::smem_desc_kmajor(st + a_bytes + koff, kRowBytes, kLayout);
-                    const uint64_t b_hi = ptx::smem_desc_kmajor(st + 2 * a_bytes + koff, kRowBytes, kLayout);
+                    const uint64_t b_hi = ptx::smem_desc_kmajor(st + b_off + koff, kRowBytes, kLayout);
                     const uint64_t b_lo =
-                        ptx::smem_desc_kmajor(st + 2 * a_bytes + b_bytes_max + koff, kRowBytes, kLayout);
+                        ptx::smem_desc_kmajor(st + b_off + b_bytes_max + koff, kRowBytes, kLayout);
                     const uint32_t first = (kb0 == 0 && kk == 0) ? 0u : 1u;
                     ptx::mma_bf16(d_tmem, a_hi, b_hi, idesc, first);
                     ptx::mma_bf16(d_tmem, a_hi, b_lo, idesc, 1u);
                     ptx::mma_bf16(d_tmem, a_lo, b_hi, idesc, 1u);
+                    if (IN3) {
+                        const uint64_t a_l2 = ptx::smem_desc_kmajor(st + 2 * a_bytes + koff, kRowBytes, kLayout);
+                        const uint64_t b_l2 =
+                            ptx::smem_desc_kmajor(st + b_off + 2 * b_bytes_max + koff, kRowBytes, kLayout);
+                        ptx::mma_bf16(d_tmem, a_lo, b_lo, idesc, 1u);
+                        ptx::mma_bf16(d_tmem, a_hi, b_l2, idesc, 1u);
+                        ptx::mma_bf16(d_tmem, a_l2, b_hi, idesc, 1u);
+                    }
                 }
                 ptx::mma_commit(empty_bar(s));
                 if (++s == stages) {
@@ -386,10 +433,10 @@ __global__ void __maxnreg__(104)
                         const int j = j0 + i;
                         const float p = __uint_as_float(rp[i]), qv = __uint_as_float(rq[i]);
                         if (j < nanti) {
-                            split_store(p + qv, G.out_hi, G.out_lo, j * Mtot + m);
-                            split_store(p - qv, G.out_hi, G.out_lo, (n - 1 - j) * Mtot + m);
+                            store_lv<L3>(p + qv, G, j * Mtot + m);
+                            store_lv<L3>(p - qv, G, (n - 1 - j) * Mtot + m);
                         } else if (j < nsym) {
-                            split_store(p, G.out_hi, G.out_lo, j * Mtot + m);
+                            store_lv<L3>(p, G, j * Mtot + m);
                         }
                     }
                 }
@@ -446,7 +493,7 @@ __global__ void __maxnreg__(104)
                         const int k = k0 + i;
                         if (k < P) {
                             const float den = dscale * (__ldg(G.lam32 + k) + rowlam) + shift;
-                            split_store(__fdividef(__uint_as_float(r[i]), den), G.out_hi, G.out_lo, k * Mtot + m);
+                            store_lv<L3>(__fdividef(__uint_as_float(r[i]), den), G, k * Mtot + m);
                         }
                     }
                 } else if (EPI == EPI_UPDATE) {
@@ -521,10 +568,15 @@ struct TcPlan {
     int n, P, dim, Mtot, BN, ntile_n, ntiles, grid, stages, BK;
     int split, BN1, BN2, num_sms;   // reflection-split products: forward / backward tile widths
     size_t smem;
-    CUtensorMap *maps;   // device: a_hi[2], a_lo[2], s_hi, s_lo, si_hi, si_lo, bf_hi, bf_lo, bb_hi, bb_lo
+    int x6;              // tc_plan_enable_x6 done
+    CUtensorMap *maps;   // device: a_hi[2], a_lo[2], s_hi, s_lo, si_hi, si_lo, bf_hi, bf_lo, bb_hi, bb_lo,
+                         // a_l2[2], bb_l2 (kPlanMaps entries)
     __nv_bfloat16 *bufs_hi[2];
     __nv_bfloat16 *bufs_lo[2];
+    __nv_bfloat16 *bufs_l2[2];
 };
+
+constexpr int kPlanMaps = 16;
 
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -568,17 +620,18 @@ bool tc_supported(int device) {
     return p.major == 10 && p.minor == 3;
 }
 
-static size_t smem_bytes_mode(int BK, int stages, int mode) {
-    const size_t stage = (size_t)(2 * BM + 2 * bn_slot(mode)) * BK * 2;
+// levels: operand levels per stage (3 for the six-product backward products)
+static size_t smem_bytes_mode(int BK, int stages, int mode, int levels = 2) {
+    const size_t stage = (size_t)levels * (BM + bn_slot(mode)) * BK * 2;
     return 1024 + stage * stages + kCtrlBytes;
 }
 
 size_t tc_smem_bytes(int BK, int stages) { return smem_bytes_mode(BK, stages, 0); }
 
-static int stages_mode(int BK, int mode) {
+static int stages_mode(int BK, int mode, int levels = 2) {
     const size_t budget = 227 * 1024;
     int stages = kMaxStages;
-    while (stages > 2 && smem_bytes_mode(BK, stages, mode) > budget) --stages;
+    while (stages > 2 && smem_bytes_mode(BK, stages, mode, levels) > budget) --stages;
     return stages;
 }
 
@@ -613,7 +666,7 @@ int tc_plan_create(TcPlan **out, int n, int P, int dim, __nv_bfloat16 *bufs_hi[2
         free(p);
         return QN_ECUDA;
     }
-    CUtensorMap h[12];
+    CUtensorMap h[kPlanMaps];
     memset(h, 0, sizeof(h));
     int rc = QN_OK;
     for (int b = 0; b < 2 && rc == QN_OK; ++b) {
@@ -671,17 +724,35 @@ int tc_plan_enable_split(TcPlan *p, const __nv_bfloat16 *bf_hi, const __nv_bfloa
 
 bool tc_plan_has_split(const TcPlan *p) { return p != nullptr && p->split; }
 
+int tc_plan_enable_x6(TcPlan *p, __nv_bfloat16 *bufs_l2[2], const __nv_bfloat16 *bb_l2) {
+    if (!p->split) return QN_EUNSUPPORTED;
+    const int H = p->P / 2;
+    CUtensorMap h[3];
+    memset(h, 0, sizeof(h));
+    int rc = QN_OK;
+    for (int b = 0; b < 2 && rc == QN_OK; ++b) {
+        p->bufs_l2[b] = bufs_l2[b];
+        rc = tc_encode_2d(&h[b], bufs_l2[b], p->P, p->Mtot, p->BK, BM, p->BK);
+    }
+    if (rc == QN_OK) rc = tc_encode_2d(&h[2], bb_l2, H, p->P, p->BK, p->BN2, p->BK);
+    if (rc != QN_OK) return rc;
+    QN_CUDA(cudaMemcpy(p->maps + 12, h, sizeof(h), cudaMemcpyHostToDevice));
+    p->x6 = 1;
+    return QN_OK;
+}
+
 void tc_plan_destroy(TcPlan *plan) {
     if (!plan) return;
     cudaFree(plan->maps);
     free(plan);
 }
 
-template <int BK, int EPI, int DIM, int MODE = 0>
+template <int BK, int EPI, int DIM, int MODE = 0, bool L3 = false>
 static int launch_t(const TcGroup &g0, const TcGroup *groups, const TcTile *tiles, int ntiles, int stages,
                     int *err, int grid, cudaStream_t s) {
-    auto kern = k_modeprod_tc<BK, EPI, DIM, MODE>;
-    kern<<<grid, kThreads, smem_bytes_mode(BK, stages, MODE), s>>>(g0, groups, tiles, ntiles, stages, err);
+    auto kern = k_modeprod_tc<BK, EPI, DIM, MODE, L3>;
+    const int levels = (L3 && MODE == 2) ? 3 : 2;
+    kern<<<grid, kThreads, smem_bytes_mode(BK, stages, MODE, levels), s>>>(g0, groups, tiles, ntiles, stages, err);
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }
@@ -707,10 +778,10 @@ static int launch_any(int BK, int dim, Epi epi, const TcGroup &g0, const TcGroup
                     : launch_epi<32, 2>(epi, g0, groups, tiles, ntiles, stages, err, grid, s);
 }
 
-template <int BK, int EPI, int DIM, int MODE = 0>
+template <int BK, int EPI, int DIM, int MODE = 0, bool L3 = false>
 static int set_attr_one() {
-    QN_CUDA(cudaFuncSetAttribute(k_modeprod_tc<BK, EPI, DIM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 227 * 1024));
+    QN_CUDA(cudaFuncSetAttribute(k_modeprod_tc<BK, EPI, DIM, MODE, L3>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     return QN_OK;
 }
 
@@ -734,12 +805,19 @@ int tc_set_attributes() {
     if (rc == QN_OK) rc = set_attr_one<64, EPI_DIVIDE, 3, 1>();
     if (rc == QN_OK) rc = set_attr_one<64, EPI_STORE_PQ, 3, 2>();
     if (rc == QN_OK) rc = set_attr_one<64, EPI_UPDATE_PQ, 3, 2>();
+    if (rc == QN_OK) rc = set_attr_one<64, EPI_DIVIDE, 3, 1, true>();
+    if (rc == QN_OK) rc = set_attr_one<64, EPI_STORE_PQ, 3, 2, true>();
+    if (rc == QN_OK) rc = set_attr_one<64, EPI_UPDATE_PQ, 3, 2, true>();
     return rc;
 }
 
-int launch_modeprod_tc_split(TcPlan *p, int src, int dst, Epi epi, const EpiArgs &e, cudaStream_t s) {
+int launch_modeprod_tc_split(TcPlan *p, int src, int dst, Epi epi, const EpiArgs &e, cudaStream_t s, bool x6) {
     if (!p->split) {
         set_error("launch_modeprod_tc_split: the plan has no reflection-split matrices");
+        return QN_EINVAL;
+    }
+    if (x6 && !p->x6) {
+        set_error("launch_modeprod_tc_split: the plan has no six-product level");
         return QN_EINVAL;
     }
     const bool fwd = (epi == EPI_STORE_BFLY || epi == EPI_DIVIDE);
@@ -755,6 +833,11 @@ int launch_modeprod_tc_split(TcPlan *p, int src, int dst, Epi epi, const EpiArgs
     g.b_lo = p->maps + (fwd ? 9 : 11);
     g.out_hi = (dst >= 0) ? p->bufs_hi[dst] : nullptr;
     g.out_lo = (dst >= 0) ? p->bufs_lo[dst] : nullptr;
+    if (x6) {
+        g.a_l2 = p->maps + 12 + src;
+        g.b_l2 = p->maps + 14;
+        g.out_l2 = (dst >= 0) ? p->bufs_l2[dst] : nullptr;
+    }
     g.U = e.U;
     g.dsq = e.dsq;
     g.lam32 = e.lam32;
@@ -769,6 +852,18 @@ int launch_modeprod_tc_split(TcPlan *p, int src, int dst, Epi epi, const EpiArgs
     g.ntile_n = fwd ? p->P / p->BN1 : (p->P / 2) / p->BN2;
     g.ntiles = g.ntile_n * (p->Mtot / BM);
     const int grid = g.ntiles < p->num_sms ? g.ntiles : p->num_sms;
+    if (x6 && epi != EPI_STORE_BFLY) {
+        // the divide writes three levels; the backward products read and write three
+        const int st3 = stages_mode(64, 2, 3);
+        switch (epi) {
+            case EPI_DIVIDE:
+                return launch_t<64, EPI_DIVIDE, 3, 1, true>(g, nullptr, nullptr, g.ntiles, p->stages, e.err, grid, s);
+            case EPI_STORE_PQ:
+                return launch_t<64, EPI_STORE_PQ, 3, 2, true>(g, nullptr, nullptr, g.ntiles, st3, e.err, grid, s);
+            default:
+                return launch_t<64, EPI_UPDATE_PQ, 3, 2, true>(g, nullptr, nullptr, g.ntiles, st3, e.err, grid, s);
+        }
+    }
     switch (epi) {
         case EPI_STORE_BFLY:
             return launch_t<64, EPI_STORE_BFLY, 3, 1>(g, nullptr, nullptr, g.ntiles, p->stages, e.err, grid, s);
@@ -784,6 +879,7 @@ int launch_modeprod_tc_split(TcPlan *p, int src, int dst, Epi epi, const EpiArgs
 
 int launch_modeprod_tc(TcPlan *p, int src, int dst, bool forward, Epi epi, const EpiArgs &e, cudaStream_t s) {
     TcGroup g;
+    memset(&g, 0, sizeof(g));
     g.a_hi = p->maps + src;
     g.a_lo = p->maps + 2 + src;
     g.b_hi = p->maps + (forward ? 6 : 4);

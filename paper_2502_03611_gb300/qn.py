@@ -30,10 +30,11 @@ QN_BC_ROBIN = 2
 BCS = {"dirichlet": QN_BC_DIRICHLET, "neumann": QN_BC_NEUMANN, "robin": QN_BC_ROBIN}
 QN_PREC_FP64 = 0
 QN_PREC_BF16X3 = 1
+QN_PREC_BF16X6 = 2
 QN_BETA_PAPER = 0
 QN_BETA_FIXED = 1
 
-PRECISIONS = {"fp64": QN_PREC_FP64, "bf16x3": QN_PREC_BF16X3}
+PRECISIONS = {"fp64": QN_PREC_FP64, "bf16x3": QN_PREC_BF16X3, "bf16x6": QN_PREC_BF16X6}
 
 
 class QnProblem(ctypes.Structure):
@@ -71,7 +72,7 @@ class QnProfile(ctypes.Structure):
                 ("mp_divide_launches", ctypes.c_int), ("mp_divide_ms", ctypes.c_double),
                 ("mp_last_launches", ctypes.c_int), ("mp_last_ms", ctypes.c_double),
                 ("residual_tiled_launches", ctypes.c_int), ("residual_tiled_ms", ctypes.c_double),
-                ("split_products", ctypes.c_int)]
+                ("split_products", ctypes.c_int), ("x6_from", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -155,6 +156,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                          ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult),
                                          ctypes.POINTER(ctypes.c_int), P]),
         "qn_profile_read": (ctypes.c_int, [P, ctypes.POINTER(QnProfile)]),
+        "qn_set_escalation": (ctypes.c_int, [P, ctypes.c_double]),
         "qn_eig_solve": (ctypes.c_int, [P, P, ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(QnStats), ctypes.c_int, P]),
     }
@@ -392,6 +394,12 @@ def qn_test_withhold_arrival():
     """Test-only: the next tensor-core mode-product launch withholds one TMA arrival and its
     waits give up after 2 s with QN_ETIMEOUT (bounded; no GPU fault)."""
     _check(load_library().qn_test_withhold_arrival())
+
+
+def qn_set_escalation(ctx: QnContext, rate: float):
+    """BF16X3 solves switch their backward products to the six-product level when the
+    observed contraction exceeds `rate` and twice the quasi-Newton bound (0: off)."""
+    _check(load_library().qn_set_escalation(ctx.handle, float(rate)))
 
 
 def qn_profile_enable(ctx: QnContext, on: bool = True):

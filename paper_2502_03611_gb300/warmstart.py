@@ -157,9 +157,12 @@ def summarise(rows):
 
 
 def run(n=255, G=64, modes=6, blocks=4, ntrain=4096, ntest=256, scale=1.0, epochs=12, batch=8, lr=2e-3,
-        train_seed0=0, test_seed0=100000, log=print):
+        train_seed0=0, test_seed0=100000, log=print, precision="bf16x3", also=()):
+    """Generate the training solves and evaluate with a `precision` context; `also`: more
+    precisions whose zero / warm solves are evaluated on the same held-out seeds (their
+    summaries under summ["by_precision"])."""
     import torch
-    ctx = qn.QnContext(3, n, "bf16x3")
+    ctx = qn.QnContext(3, n, precision)
     t0 = time.time()
     f_c, u_c, its = generate(ctx, G, n, range(train_seed0, train_seed0 + ntrain), scale)
     t_gen = time.time() - t0
@@ -173,6 +176,14 @@ def run(n=255, G=64, modes=6, blocks=4, ntrain=4096, ntest=256, scale=1.0, epoch
     t_train = time.time() - t0
     rows = evaluate(ctx, net, n, range(test_seed0, test_seed0 + ntest), scale, in_scale, out_scale)
     summ = summarise(rows)
+    summ["precision"] = precision
+    by = {precision: summarise(rows)}
+    for p in also:
+        c2 = qn.QnContext(3, n, p)
+        by[p] = summarise(evaluate(c2, net, n, range(test_seed0, test_seed0 + ntest), scale, in_scale, out_scale))
+        c2.close()
+    if also:
+        summ["by_precision"] = by
     summ.update({"n": n, "G": G, "modes": modes, "blocks": blocks, "params": int(net.nparams),
                  "train_samples": ntrain, "epochs": epochs, "batch": batch, "scale": scale,
                  "train_solve_iterations_mean": statistics.mean(its), "data_gen_s": round(t_gen, 1),
@@ -195,10 +206,13 @@ def main():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--precision", default="bf16x3", choices=("bf16x3", "bf16x6"))
+    ap.add_argument("--also", nargs="*", default=[], choices=("bf16x3", "bf16x6"))
     a = ap.parse_args()
     import __graft_entry__
     __graft_entry__.build()
-    summ, _, rows = run(a.n, a.G, a.modes, a.blocks, a.train, a.test, a.scale, a.epochs, a.batch, a.lr)
+    summ, _, rows = run(a.n, a.G, a.modes, a.blocks, a.train, a.test, a.scale, a.epochs, a.batch, a.lr,
+                        precision=a.precision, also=tuple(a.also))
     if a.out:
         with open(a.out, "w") as fh:
             json.dump({"summary": summ, "rows": rows}, fh)

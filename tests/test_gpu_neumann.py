@@ -179,7 +179,7 @@ def _check_ex1(res, Ug, Uo, n):
 
 
 @pytest.mark.parametrize("n,prec", [(9, "fp64"), (17, "fp64"), (17, "bf16x3"), (33, "fp64"), (33, "bf16x3"),
-                                    (65, "bf16x3"), (70, "bf16x3")])
+                                    (65, "bf16x3"), (70, "bf16x3"), (65, "bf16x6"), (128, "bf16x6")])
 def test_solve_ex1_perturbed_start_matches_oracle(qn, n, prec):
     """The paper's start: the solution plus 0.1 p, p a normalised random cubic-free
     polynomial of degree 4 per axis. n = 65, 70: P = 128, reflection-split products
