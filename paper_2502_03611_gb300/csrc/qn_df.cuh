@@ -82,6 +82,37 @@ __device__ __forceinline__ void fx_to_pair(long long v, float scale, float &hi, 
     lo = __fmul_rn(__fadd_rn(e, f0), scale);
 }
 
+// Two-lane forms of the helpers above on the packed FP32x2 instructions of sm_100+
+// (one FFMA2 / FADD2 / FMUL2 does the operation for two values, with the rounding
+// of the scalar instruction, so the results equal the scalar ones bit for bit).
+__device__ __forceinline__ float2 f2_splat(float v) { return make_float2(v, v); }
+
+// a - b as one rounded FMA (b * -1 + a).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2_splat(-1.0f), a); }
+
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+    s = __fadd2_rn(a, b);
+    const float2 bb = sub2(s, a);
+    e = __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
+// fx_to_pair for two fixed-point values.
+__device__ __forceinline__ void fx_to_pair2(long long v0, long long v1, float scale, float2 &hi, float2 &lo) {
+    const int a2 = (int)(v0 >> 42), b2 = (int)(v1 >> 42);
+    const int a1 = (int)((unsigned long long)v0 >> 21) & 0x1FFFFF, b1 = (int)((unsigned long long)v1 >> 21) & 0x1FFFFF;
+    const int a0 = (int)v0 & 0x1FFFFF, b0 = (int)v1 & 0x1FFFFF;
+    const float2 f2 = __ffma2_rn(make_float2(__int_as_float(0x4B400000 + a2), __int_as_float(0x4B400000 + b2)),
+                                 f2_splat(0x1p42f), f2_splat(-0x1.8p65f));
+    const float2 f1 = __ffma2_rn(make_float2(__int_as_float(0x4B400000 + a1), __int_as_float(0x4B400000 + b1)),
+                                 f2_splat(0x1p21f), f2_splat(-0x1.8p44f));
+    const float2 f0 = __fadd2_rn(make_float2(__int_as_float(0x4B400000 + a0), __int_as_float(0x4B400000 + b0)),
+                                 f2_splat(-12582912.0f));
+    float2 s, e;
+    two_sum2(f2, f1, s, e);
+    hi = __fmul2_rn(s, f2_splat(scale));
+    lo = __fmul2_rn(__fadd2_rn(e, f0), f2_splat(scale));
+}
+
 // (a + b) for two float pairs, renormalised.
 __device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
     float s, e;

@@ -179,9 +179,7 @@ int launch_modeprod_f64(const double *A, const double *B, double *out, const Gem
 // solve) or of many groups (batched solve: every instance and component).
 struct TcGroup {
     const CUtensorMap *a_hi, *a_lo, *b_hi, *b_lo;   // tensor maps in global memory (64-B aligned)
-    const CUtensorMap *a_l2, *b_l2;                   // third operand levels (six-product backward)
     __nv_bfloat16 *out_hi, *out_lo;                   // EPI_STORE / EPI_DIVIDE destination planes
-    __nv_bfloat16 *out_l2;                            // third output level (three-level outputs)
     double *U;                                        // EPI_UPDATE / EPI_DENSE target (dense n^dim)
     float *dsq;                                       // update epilogues: += sum (step * delta)^2 (nullptr: off)
     const float *lam32;                               // padded eigenvalues (P entries, 1e30 past n)

@@ -137,11 +137,18 @@ __device__ __forceinline__ void split_store3(float v, __nv_bfloat16 *hi, __nv_bf
     l2[o] = __float2bfloat16_rn(r1 - __bfloat162float(m));
 }
 
+// The third levels of the six-product launches (single-group reflection-split products
+// only; a separate kernel argument, so the group records of every launch keep one layout).
+struct TcL3 {
+    const CUtensorMap *a_l2, *b_l2;   // third operand levels of A and B
+    __nv_bfloat16 *out_l2;            // third output level
+};
+
 // Store one output value as two or three levels.
 template <bool L3>
-__device__ __forceinline__ void store_lv(float v, const TcGroup &G, int o) {
+__device__ __forceinline__ void store_lv(float v, const TcGroup &G, const TcL3 &l3, int o) {
     if (L3)
-        split_store3(v, G.out_hi, G.out_lo, G.out_l2, o);
+        split_store3(v, G.out_hi, G.out_lo, l3.out_l2, o);
     else
         split_store(v, G.out_hi, G.out_lo, o);
 }
@@ -172,7 +179,7 @@ static_assert(kThreads * 104 <= 65536, "register file");
 template <int BK, int EPI, int DIM, int MODE, bool L3 = false>
 __global__ void __maxnreg__(104)
     k_modeprod_tc(const TcGroup g0, const TcGroup *__restrict__ groups, const TcTile *__restrict__ tiles,
-                  const int ntiles, const int stages, int *err) {
+                  const int ntiles, const int stages, int *err, const TcL3 l3) {
     if (groups == nullptr && group_done(g0)) return;
 
     constexpr uint32_t kRowBytes = BK * 2;                // one swizzle row per tile row
@@ -269,10 +276,10 @@ __global__ void __maxnreg__(104)
                     ptx::mbar_arrive_expect_tx(full_bar(s), tx_bytes);
                     ptx::tma_load_2d(st, G.a_hi, full_bar(s), ax, m0);
                     ptx::tma_load_2d(st + a_bytes, G.a_lo, full_bar(s), ax, m0);
-                    if (IN3) ptx::tma_load_2d(st + 2 * a_bytes, G.a_l2, full_bar(s), ax, m0);
+                    if (IN3) ptx::tma_load_2d(st + 2 * a_bytes, l3.a_l2, full_bar(s), ax, m0);
                     ptx::tma_load_2d(st + b_off, G.b_hi, full_bar(s), bx, by);
                     ptx::tma_load_2d(st + b_off + b_bytes_max, G.b_lo, full_bar(s), bx, by);
-                    if (IN3) ptx::tma_load_2d(st + b_off + 2 * b_bytes_max, G.b_l2, full_bar(s), bx, by);
+                    if (IN3) ptx::tma_load_2d(st + b_off + 2 * b_bytes_max, l3.b_l2, full_bar(s), bx, by);
                     armed_parity[s] = ph;
                     armed_mask |= 1u << s;
                 }
@@ -433,10 +440,10 @@ __global__ void __maxnreg__(104)
                         const int j = j0 + i;
                         const float p = __uint_as_float(rp[i]), qv = __uint_as_float(rq[i]);
                         if (j < nanti) {
-                            store_lv<L3>(p + qv, G, j * Mtot + m);
-                            store_lv<L3>(p - qv, G, (n - 1 - j) * Mtot + m);
+                            store_lv<L3>(p + qv, G, l3, j * Mtot + m);
+                            store_lv<L3>(p - qv, G, l3, (n - 1 - j) * Mtot + m);
                         } else if (j < nsym) {
-                            store_lv<L3>(p, G, j * Mtot + m);
+                            store_lv<L3>(p, G, l3, j * Mtot + m);
                         }
                     }
                 }
@@ -493,7 +500,7 @@ __global__ void __maxnreg__(104)
                         const int k = k0 + i;
                         if (k < P) {
                             const float den = dscale * (__ldg(G.lam32 + k) + rowlam) + shift;
-                            store_lv<L3>(__fdividef(__uint_as_float(r[i]), den), G, k * Mtot + m);
+                            store_lv<L3>(__fdividef(__uint_as_float(r[i]), den), G, l3, k * Mtot + m);
                         }
                     }
                 } else if (EPI == EPI_UPDATE) {
@@ -749,10 +756,11 @@ void tc_plan_destroy(TcPlan *plan) {
 
 template <int BK, int EPI, int DIM, int MODE = 0, bool L3 = false>
 static int launch_t(const TcGroup &g0, const TcGroup *groups, const TcTile *tiles, int ntiles, int stages,
-                    int *err, int grid, cudaStream_t s) {
+                    int *err, int grid, cudaStream_t s, const TcL3 &l3 = TcL3{nullptr, nullptr, nullptr}) {
     auto kern = k_modeprod_tc<BK, EPI, DIM, MODE, L3>;
     const int levels = (L3 && MODE == 2) ? 3 : 2;
-    kern<<<grid, kThreads, smem_bytes_mode(BK, stages, MODE, levels), s>>>(g0, groups, tiles, ntiles, stages, err);
+    kern<<<grid, kThreads, smem_bytes_mode(BK, stages, MODE, levels), s>>>(g0, groups, tiles, ntiles, stages, err,
+                                                                           l3);
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }
@@ -833,10 +841,11 @@ int launch_modeprod_tc_split(TcPlan *p, int src, int dst, Epi epi, const EpiArgs
     g.b_lo = p->maps + (fwd ? 9 : 11);
     g.out_hi = (dst >= 0) ? p->bufs_hi[dst] : nullptr;
     g.out_lo = (dst >= 0) ? p->bufs_lo[dst] : nullptr;
+    TcL3 l3{nullptr, nullptr, nullptr};
     if (x6) {
-        g.a_l2 = p->maps + 12 + src;
-        g.b_l2 = p->maps + 14;
-        g.out_l2 = (dst >= 0) ? p->bufs_l2[dst] : nullptr;
+        l3.a_l2 = p->maps + 12 + src;
+        l3.b_l2 = p->maps + 14;
+        l3.out_l2 = (dst >= 0) ? p->bufs_l2[dst] : nullptr;
     }
     g.U = e.U;
     g.dsq = e.dsq;
@@ -857,11 +866,14 @@ int launch_modeprod_tc_split(TcPlan *p, int src, int dst, Epi epi, const EpiArgs
         const int st3 = stages_mode(64, 2, 3);
         switch (epi) {
             case EPI_DIVIDE:
-                return launch_t<64, EPI_DIVIDE, 3, 1, true>(g, nullptr, nullptr, g.ntiles, p->stages, e.err, grid, s);
+                return launch_t<64, EPI_DIVIDE, 3, 1, true>(g, nullptr, nullptr, g.ntiles, p->stages, e.err, grid, s,
+                                                            l3);
             case EPI_STORE_PQ:
-                return launch_t<64, EPI_STORE_PQ, 3, 2, true>(g, nullptr, nullptr, g.ntiles, st3, e.err, grid, s);
+                return launch_t<64, EPI_STORE_PQ, 3, 2, true>(g, nullptr, nullptr, g.ntiles, st3, e.err, grid, s,
+                                                              l3);
             default:
-                return launch_t<64, EPI_UPDATE_PQ, 3, 2, true>(g, nullptr, nullptr, g.ntiles, st3, e.err, grid, s);
+                return launch_t<64, EPI_UPDATE_PQ, 3, 2, true>(g, nullptr, nullptr, g.ntiles, st3, e.err, grid, s,
+                                                               l3);
         }
     }
     switch (epi) {
