@@ -475,6 +475,30 @@ def run_c1(qn, seeds=range(100), want_cpu=True):
         its.append(res["iterations"])
         launches.append(int(qn.qn_profile_read(ctx)["launches"]))
         outs.append(U.cpu().numpy().reshape(n, n).copy())
+    # the same solves as separate launches per phase (residual, finaliser, four products),
+    # iterations >= 2 replayed from a CUDA graph: the context's other path, for comparison
+    os.environ["QN_SMALL"] = "0"
+    try:
+        ctx2 = qn.QnContext(2, n, "fp64")
+    finally:
+        del os.environ["QN_SMALL"]
+    for k in range(3):
+        U.zero_()
+        qn.qn_solve(ctx2, U, fd[k], graph=True, sync_every=4)
+    us2, launches2 = [], []
+    for f in fd[:20]:
+        U.zero_()
+        qn.qn_profile_enable(ctx2, False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        qn.qn_solve(ctx2, U, f, graph=True, sync_every=4)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us2.append(1e3 * e0.elapsed_time(e1))
+        launches2.append(int(qn.qn_profile_read(ctx2)["launches"]))
+    ctx2.close()
     out = {"workload": "2-D -Lap u + u^3 = f, 63^2 interior, 5-point FD, Dirichlet 0, FP64, zero start, "
                        f"tol 1e-10, seeds {seeds[0]}-{seeds[-1]}",
            "precision": "fp64", "solves": len(us), "us_per_solve_median": round(statistics.median(us), 1),
@@ -482,7 +506,13 @@ def run_c1(qn, seeds=range(100), want_cpu=True):
            "host_wall_us_median": round(1e6 * statistics.median(wall), 1),
            "iterations_median": statistics.median(its), "iterations_max": max(its),
            "launches_per_solve_median": statistics.median(launches),
-           "launch": "iterations >= 2 replayed from a CUDA graph, host check every 4 iterations"}
+           "launch": "the whole solve in one cooperative launch (grid barriers between the phases); "
+                     "launches counted with the state-set and state-mirror kernels",
+           "per_phase_launches": {"us_per_solve_median": round(statistics.median(us2), 1),
+                                  "launches_per_solve_median": statistics.median(launches2),
+                                  "solves": len(us2),
+                                  "launch": "residual, finaliser and four products per iteration; iterations "
+                                            ">= 2 replayed from a CUDA graph, host check every 4 iterations"}}
     if want_cpu:
         errs, rels, dit, ts = [], [], [], []
         for f, Ug, it in zip(fs, outs, its):

@@ -12,7 +12,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqn.so")
-SOURCES = ["qn_api.cu", "qn_residual.cu", "qn_modeprod_f64.cu", "qn_modeprod_tc.cu", "qn_batch.cu", "qn_net.cu", "qn_eig.cu", "qn_sem.cu"]
+SOURCES = ["qn_api.cu", "qn_residual.cu", "qn_modeprod_f64.cu", "qn_modeprod_tc.cu", "qn_batch.cu", "qn_net.cu", "qn_eig.cu", "qn_sem.cu", "qn_small.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"] + ARCH

@@ -136,6 +136,8 @@ struct qn_ctx {
     double esc_rate;      // 0: off
     int esc_at;           // first iteration of the last solve that ran at that level (-1: none)
     int g_x6;             // the captured graph's level
+    unsigned *small_bar;  // small 2-D FP64 solves: the persistent kernel's grid barrier words
+    int small_solve;      // 1: qn_solve runs the whole-solve persistent kernel (qn_small.cu)
     float *lam32_split;   // eigenvalues in split mode order (even modes, then odd), 1e30 padding
     // separable potential V = v_x + v_y (+ v_z): device tables [dim][n], FP64 and as FP32
     // pairs with lam added to the last axis (k_residual_tiled / mirror); nullptr: V = 0
@@ -299,6 +301,7 @@ static void ctx_free(qn_ctx *c) {
     cudaFree(c->bb_hi);
     cudaFree(c->bb_lo);
     cudaFree(c->bb_l2);
+    cudaFree(c->small_bar);
     cudaFree(c->bl2[0]);
     cudaFree(c->bl2[1]);
     cudaFree(c->lam32_split);
@@ -564,6 +567,15 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
 
     if (p->precision == QN_PREC_FP64) {
         for (int b = 0; b < 2; ++b) CK(cudaMalloc(&c->w64[b], sizeof(double) * c->N));
+        // small 2-D finite-difference problems without a potential: the whole solve in one
+        // persistent launch (launch latency dominates there)
+        const char *esm = getenv("QN_SMALL");
+        if ((esm ? atoi(esm) != 0 : true) && small_solve_supported(c->dim, c->n) && p->sem_k == 0 &&
+            (p->bc == QN_BC_DIRICHLET || p->bc == QN_BC_NEUMANN) && p->potential_host == nullptr) {
+            CK(cudaMalloc(&c->small_bar, 2 * sizeof(unsigned)));
+            CK(cudaMemset(c->small_bar, 0, 2 * sizeof(unsigned)));
+            c->small_solve = 1;
+        }
         // the closed-form sine / cosine pairs have the reflection symmetry the split
         // products use; the numerical (Robin, spectral-element) ones need not
         const char *es = getenv("QN_SPLIT");
@@ -1198,7 +1210,40 @@ int qn::solve_internal(qn_ctx *c, double *U, const double *f, const qn_opts *opt
         *used_warm = 0;
     }
     const bool use_graph = o.graph != 0 && !c->prof_on;
-    while (!h.done && enqueued <= o.max_it) {
+    const bool small = c->small_solve && u0_sq == nullptr && !c->prof_on;
+    if (small) {
+        SmallSolve q;
+        q.U = U;
+        q.f = f;
+        q.S = c->S64;
+        q.Si = c->Si64;
+        q.lam1 = c->lam64;
+        q.w0 = c->w64[0];
+        q.w1 = c->w64[1];
+        q.partials = c->partials;
+        q.partials_cap = c->partials_cap;
+        q.bar = c->small_bar;
+        q.st = c->st;
+        q.hist = c->hist;
+        q.hist_cap = kHistCap;
+        q.err = c->err;
+        q.n = c->n;
+        q.neumann = (c->prob.bc == QN_BC_NEUMANN) ? 1 : 0;
+        q.num_sms = c->num_sms;
+        q.inv_h2 = c->inv_h2;
+        q.lam = c->prob.lam;
+        q.b = c->prob.b;
+        q.tol = o.tol;
+        q.beta_value = o.beta_value;
+        q.step = o.step;
+        q.beta_fixed = (o.beta_mode == QN_BETA_FIXED) ? 1 : 0;
+        q.max_it = o.max_it;
+        rc = launch_small_solve(q, s);
+        if (rc) return rc;
+        rc = read_state(c, &h, s);
+        if (rc) return rc;
+    }
+    while (!small && !h.done && enqueued <= o.max_it) {
         if (use_graph && enqueued >= 2 && enqueued + o.sync_every <= o.max_it + 1) {
             // steady-state iterations (the same launches every time): replay
             rc = ensure_iteration_graph(c, U, f, o.step, o.sync_every);
@@ -1233,7 +1278,8 @@ int qn::solve_internal(qn_ctx *c, double *U, const double *f, const qn_opts *opt
         const bool mp = r.kind >= PK_MP_STORE && r.kind <= PK_MP_LAST;
         if ((mp && r.iter >= its) || (!mp && r.iter > its)) r.valid = 0;
     }
-    c->launches = launches0 + 2LL * (its + 1) + 2LL * c->dim * its + c->aux_launches;
+    c->launches = small ? launches0 + 1 + c->aux_launches
+                        : launches0 + 2LL * (its + 1) + 2LL * c->dim * its + c->aux_launches;
     if (c->prob.precision == QN_PREC_BF16X3 && c->fdf != nullptr && c->res_tiled)
         c->launches += 2 + (its >= 1 ? 2 : 0);   // preparation kernels of iterations 0 and 1
     // the statistics of the final iterate came with the last state mirror

@@ -220,6 +220,29 @@ int tc_plan_enable_x6(TcPlan *plan, __nv_bfloat16 *bufs_l2[2], const __nv_bfloat
 // (and write three levels); needs tc_plan_enable_x6.
 int launch_modeprod_tc_split(TcPlan *plan, int src, int dst, Epi epi, const EpiArgs &e, cudaStream_t s,
                              bool x6 = false);
+// ---- whole-solve persistent kernel for small 2-D FP64 problems (qn_small.cu) ----------
+constexpr int kSmallMaxN = 128;
+struct SmallSolve {
+    double *U;
+    const double *f;
+    const double *S, *Si, *lam1;   // n x n eigenvector matrices and the eigenvalues (device, FP64)
+    double *w0, *w1;               // two n^2 work arrays
+    double *partials;              // partials_cap records of 4 doubles
+    int partials_cap;
+    unsigned *bar;                 // 2 words (barrier counter, generation)
+    DevState *st;
+    qn_stats *hist;
+    int hist_cap;
+    int *err;
+    int n, neumann, num_sms;
+    double inv_h2, lam, b, tol, beta_value, step;
+    int beta_fixed, max_it;
+};
+int small_solve_supported(int dim, int n);
+// One cooperative launch that runs the whole solve; on return (asynchronous) st holds
+// it / status / done as the finaliser leaves them, hist the per-iterate statistics.
+int launch_small_solve(const SmallSolve &q, cudaStream_t s);
+
 // Grouped launch over a device tile table (batched solves).
 // Test-only: the next k_modeprod_tc launch has block 0's producer withhold its first stage.
 int tc_test_withhold_arrival();
