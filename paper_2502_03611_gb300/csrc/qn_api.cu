@@ -572,8 +572,8 @@ extern "C" int qn_ctx_create(const qn_problem *p, qn_ctx **out) {
         const char *esm = getenv("QN_SMALL");
         if ((esm ? atoi(esm) != 0 : true) && small_solve_supported(c->dim, c->n) && p->sem_k == 0 &&
             (p->bc == QN_BC_DIRICHLET || p->bc == QN_BC_NEUMANN) && p->potential_host == nullptr) {
-            CK(cudaMalloc(&c->small_bar, 2 * sizeof(unsigned)));
-            CK(cudaMemset(c->small_bar, 0, 2 * sizeof(unsigned)));
+            CK(cudaMalloc(&c->small_bar, kSmallBarWords * sizeof(unsigned)));
+            CK(cudaMemset(c->small_bar, 0, kSmallBarWords * sizeof(unsigned)));
             c->small_solve = 1;
         }
         // the closed-form sine / cosine pairs have the reflection symmetry the split

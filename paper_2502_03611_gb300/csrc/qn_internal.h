@@ -222,6 +222,7 @@ int launch_modeprod_tc_split(TcPlan *plan, int src, int dst, Epi epi, const EpiA
                              bool x6 = false);
 // ---- whole-solve persistent kernel for small 2-D FP64 problems (qn_small.cu) ----------
 constexpr int kSmallMaxN = 128;
+constexpr int kSmallBarWords = 64;   // the grid barrier's counter and generation words, apart
 struct SmallSolve {
     double *U;
     const double *f;
@@ -229,7 +230,7 @@ struct SmallSolve {
     double *w0, *w1;               // two n^2 work arrays
     double *partials;              // partials_cap records of 4 doubles
     int partials_cap;
-    unsigned *bar;                 // 2 words (barrier counter, generation)
+    unsigned *bar;                 // kSmallBarWords words (barrier counter, generation)
     DevState *st;
     qn_stats *hist;
     int hist_cap;

@@ -10,11 +10,11 @@
 // feeds (the matrix rows come from L1, where S and S^{-1} stay between iterations).
 //
 //   iteration k:  residual r = A_h U + lam U + b U^3 - f  (+ block partials of ||r||^2,
-//                 ||f||^2 at k = 0, min / max U^2)                         -> barrier
+//                 ||f||^2 at k = 0, min / max U^2), and on the same rows
+//                 P1  Y1[kx][y] = sum_x S^{-1}[kx][x] r[y][x]              -> barrier
 //                 every block reduces the partial records in the same order, so all
 //                 take the same stop decision and the same beta_n = (min + max)/2 of
 //                 3 b U^2; block 0 records the iterate's statistics
-//                 P1  Y1[kx][y] = sum_x S^{-1}[kx][x] r[y][x]              -> barrier
 //                 P2  Y2[ky][kx] = sum_y S^{-1}[ky][y] Y1[kx][y] / (lam_kx + lam_ky + lam + beta_n)
 //                                                                           -> barrier
 //                 P3  Y3[x][ky] = sum_kx S[x][kx] Y2[ky][kx]               -> barrier
@@ -37,6 +37,7 @@ namespace qn {
 namespace {
 
 constexpr int kSmallThreads = 128;
+constexpr int kBarGen = 32;   // the generation word, a 128-byte line away from the counter
 constexpr unsigned long long kSmallTimeoutNs = 2000000000ull;
 
 __device__ __forceinline__ unsigned long long small_timer() {
@@ -186,7 +187,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_small2d_fp64(SmallArgs a) {
             q[2] = q2;
             q[3] = q3;
         }
-        if (!small_barrier(a.bar, a.bar + 1, a.err)) return;
+        // P1  Y1[kx][y] = sum_x Si[kx][x] r[y][x] on the rows just evaluated (this block's
+        // own), before the barrier: it needs neither the norms nor beta
+        small_product<false>(a.Si, a.w0, a.w1, n, row, nullptr, 0.0);
+        if (!small_barrier(a.bar, a.bar + kBarGen, a.err)) return;
         // ---- every block: the same reduction, the same decision
         if (warp == 0) {
             double R = 0.0, F = 0.0, MN = INFINITY, MX = 0.0;
@@ -241,15 +245,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_small2d_fp64(SmallArgs a) {
         fn = sh_fn;
         if (sh_stop) break;
         const double shift = sh_beta;
-        // P1  Y1[kx][y] = sum_x Si[kx][x] r[y][x]
-        small_product<false>(a.Si, a.w0, a.w1, n, row, nullptr, 0.0);
-        if (!small_barrier(a.bar, a.bar + 1, a.err)) return;
         // P2  Y2[ky][kx] = sum_y Si[ky][y] Y1[kx][y] / (lam_kx + lam_ky + shift)
         small_product<true>(a.Si, a.w1, a.w0, n, row, a.lam1, shift);
-        if (!small_barrier(a.bar, a.bar + 1, a.err)) return;
+        if (!small_barrier(a.bar, a.bar + kBarGen, a.err)) return;
         // P3  Y3[x][ky] = sum_kx S[x][kx] Y2[ky][kx]
         small_product<false>(a.S, a.w0, a.w1, n, row, nullptr, 0.0);
-        if (!small_barrier(a.bar, a.bar + 1, a.err)) return;
+        if (!small_barrier(a.bar, a.bar + kBarGen, a.err)) return;
         // P4  delta[y][x] = sum_ky S[y][ky] Y3[x][ky], U -= step * delta
         for (int b = blockIdx.x; b < n; b += gridDim.x) {   // b = x (the input row)
             __syncthreads();
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_small2d_fp64(SmallArgs a) {
                 a.U[p] = (a.step == 1.0) ? u - d : fma(-a.step, d, u);
             }
         }
-        if (!small_barrier(a.bar, a.bar + 1, a.err)) return;
+        if (!small_barrier(a.bar, a.bar + kBarGen, a.err)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.st->it = it;
@@ -333,7 +334,7 @@ int launch_small_solve(const SmallSolve &q, cudaStream_t s) {
     a.step = q.step;
     a.beta_fixed = q.beta_fixed;
     a.max_it = q.max_it;
-    QN_CUDA(cudaMemsetAsync(q.bar, 0, 2 * sizeof(unsigned), s));
+    QN_CUDA(cudaMemsetAsync(q.bar, 0, kSmallBarWords * sizeof(unsigned), s));
     void *params[] = {&a};
     QN_CUDA(cudaLaunchCooperativeKernel((const void *)k_small2d_fp64, dim3(grid), dim3(kSmallThreads), params,
                                         sizeof(double) * q.n, s));
