@@ -700,7 +700,7 @@ int tc_plan_create(TcPlan **out, int n, int P, int dim, __nv_bfloat16 *bufs_hi[2
 int tc_plan_enable_split(TcPlan *p, const __nv_bfloat16 *bf_hi, const __nv_bfloat16 *bf_lo,
                          const __nv_bfloat16 *bb_hi, const __nv_bfloat16 *bb_lo) {
     const int H = p->P / 2;
-    if (p->dim != 3 || p->BK != 64 || p->P % 128 != 0) return QN_EUNSUPPORTED;
+    if (p->dim != 3 || p->P % 128 != 0) return QN_EUNSUPPORTED;
     // tile widths must divide H (a forward tile stays inside one half; the
     // backward tiles cover the H rows exactly) and give every epilogue warp a
     // whole number of TMEM chunks: BN1/kEpiParts a multiple of kChunk (16),
@@ -802,6 +802,18 @@ static int set_attr_dim() {
     return rc;
 }
 
+template <int BK>
+static int set_attr_split() {
+    int rc = set_attr_one<BK, EPI_STORE_BFLY, 3, 1>();
+    if (rc == QN_OK) rc = set_attr_one<BK, EPI_DIVIDE, 3, 1>();
+    if (rc == QN_OK) rc = set_attr_one<BK, EPI_STORE_PQ, 3, 2>();
+    if (rc == QN_OK) rc = set_attr_one<BK, EPI_UPDATE_PQ, 3, 2>();
+    if (rc == QN_OK) rc = set_attr_one<BK, EPI_DIVIDE, 3, 1, true>();
+    if (rc == QN_OK) rc = set_attr_one<BK, EPI_STORE_PQ, 3, 2, true>();
+    if (rc == QN_OK) rc = set_attr_one<BK, EPI_UPDATE_PQ, 3, 2, true>();
+    return rc;
+}
+
 // Opt every instantiation in to the large dynamic shared memory once (before
 // any launch, so that launches can be captured into CUDA graphs).
 int tc_set_attributes() {
@@ -809,14 +821,37 @@ int tc_set_attributes() {
     if (rc == QN_OK) rc = set_attr_dim<64, 3>();
     if (rc == QN_OK) rc = set_attr_dim<32, 2>();
     if (rc == QN_OK) rc = set_attr_dim<32, 3>();
-    if (rc == QN_OK) rc = set_attr_one<64, EPI_STORE_BFLY, 3, 1>();
-    if (rc == QN_OK) rc = set_attr_one<64, EPI_DIVIDE, 3, 1>();
-    if (rc == QN_OK) rc = set_attr_one<64, EPI_STORE_PQ, 3, 2>();
-    if (rc == QN_OK) rc = set_attr_one<64, EPI_UPDATE_PQ, 3, 2>();
-    if (rc == QN_OK) rc = set_attr_one<64, EPI_DIVIDE, 3, 1, true>();
-    if (rc == QN_OK) rc = set_attr_one<64, EPI_STORE_PQ, 3, 2, true>();
-    if (rc == QN_OK) rc = set_attr_one<64, EPI_UPDATE_PQ, 3, 2, true>();
+    if (rc == QN_OK) rc = set_attr_split<64>();
+    if (rc == QN_OK) rc = set_attr_split<32>();
     return rc;
+}
+
+template <int BK>
+static int split_launch(const TcPlan *p, const TcGroup &g, const TcL3 &l3, Epi epi, bool x6, int *err, int grid,
+                        cudaStream_t s) {
+    if (x6 && epi != EPI_STORE_BFLY) {
+        // the divide writes three levels; the backward products read and write three
+        const int st3 = stages_mode(BK, 2, 3);
+        switch (epi) {
+            case EPI_DIVIDE:
+                return launch_t<BK, EPI_DIVIDE, 3, 1, true>(g, nullptr, nullptr, g.ntiles, p->stages, err, grid, s, l3);
+            case EPI_STORE_PQ:
+                return launch_t<BK, EPI_STORE_PQ, 3, 2, true>(g, nullptr, nullptr, g.ntiles, st3, err, grid, s, l3);
+            default:
+                return launch_t<BK, EPI_UPDATE_PQ, 3, 2, true>(g, nullptr, nullptr, g.ntiles, st3, err, grid, s, l3);
+        }
+    }
+    const int st2 = stages_mode(BK, 2);
+    switch (epi) {
+        case EPI_STORE_BFLY:
+            return launch_t<BK, EPI_STORE_BFLY, 3, 1>(g, nullptr, nullptr, g.ntiles, p->stages, err, grid, s);
+        case EPI_DIVIDE:
+            return launch_t<BK, EPI_DIVIDE, 3, 1>(g, nullptr, nullptr, g.ntiles, p->stages, err, grid, s);
+        case EPI_STORE_PQ:
+            return launch_t<BK, EPI_STORE_PQ, 3, 2>(g, nullptr, nullptr, g.ntiles, st2, err, grid, s);
+        default:
+            return launch_t<BK, EPI_UPDATE_PQ, 3, 2>(g, nullptr, nullptr, g.ntiles, st2, err, grid, s);
+    }
 }
 
 int launch_modeprod_tc_split(TcPlan *p, int src, int dst, Epi epi, const EpiArgs &e, cudaStream_t s, bool x6) {
@@ -861,32 +896,8 @@ int launch_modeprod_tc_split(TcPlan *p, int src, int dst, Epi epi, const EpiArgs
     g.ntile_n = fwd ? p->P / p->BN1 : (p->P / 2) / p->BN2;
     g.ntiles = g.ntile_n * (p->Mtot / BM);
     const int grid = g.ntiles < p->num_sms ? g.ntiles : p->num_sms;
-    if (x6 && epi != EPI_STORE_BFLY) {
-        // the divide writes three levels; the backward products read and write three
-        const int st3 = stages_mode(64, 2, 3);
-        switch (epi) {
-            case EPI_DIVIDE:
-                return launch_t<64, EPI_DIVIDE, 3, 1, true>(g, nullptr, nullptr, g.ntiles, p->stages, e.err, grid, s,
-                                                            l3);
-            case EPI_STORE_PQ:
-                return launch_t<64, EPI_STORE_PQ, 3, 2, true>(g, nullptr, nullptr, g.ntiles, st3, e.err, grid, s,
-                                                              l3);
-            default:
-                return launch_t<64, EPI_UPDATE_PQ, 3, 2, true>(g, nullptr, nullptr, g.ntiles, st3, e.err, grid, s,
-                                                               l3);
-        }
-    }
-    switch (epi) {
-        case EPI_STORE_BFLY:
-            return launch_t<64, EPI_STORE_BFLY, 3, 1>(g, nullptr, nullptr, g.ntiles, p->stages, e.err, grid, s);
-        case EPI_DIVIDE:
-            return launch_t<64, EPI_DIVIDE, 3, 1>(g, nullptr, nullptr, g.ntiles, p->stages, e.err, grid, s);
-        case EPI_STORE_PQ:
-            return launch_t<64, EPI_STORE_PQ, 3, 2>(g, nullptr, nullptr, g.ntiles, stages_mode(64, 2), e.err, grid, s);
-        default:
-            return launch_t<64, EPI_UPDATE_PQ, 3, 2>(g, nullptr, nullptr, g.ntiles, stages_mode(64, 2), e.err, grid,
-                                                      s);
-    }
+    return p->BK == 64 ? split_launch<64>(p, g, l3, epi, x6, e.err, grid, s)
+                       : split_launch<32>(p, g, l3, epi, x6, e.err, grid, s);
 }
 
 int launch_modeprod_tc(TcPlan *p, int src, int dst, bool forward, Epi epi, const EpiArgs &e, cudaStream_t s) {
