@@ -226,3 +226,28 @@ def test_escalation_arguments(qn):
             qn.qn_set_escalation(c, 0.5)
         qn.qn_set_escalation(c, 0.0)   # off is always accepted
         c.close()
+
+
+def test_eigenproblem_at_six_products(qn):
+    """The nonlinear eigenproblem (Sec. 4.4, Example 2 of Sec. 6.3) runs its shifted inverse
+    through the same split products, so a BF16X6 context takes it at the six-product level:
+    lambda and U against the oracle as for BF16X3 (tests/test_gpu_eig.py)."""
+    import torch
+    from oracle import qn_oracle_bc as ob
+    n = 65
+    v, h, x = I.ex2_problem(n)
+    U0 = I.ex2_start(n, seed=1)
+    Uo, lam_o, ho, ok = ob.qn_eig_solve(U0, h, "dirichlet", b=I.EX2_ALPHA, V=ob.potential(v, 3, n))
+    assert ok
+    its = {}
+    for prec in ("bf16x6", "bf16x3"):
+        ctx = qn.QnContext(3, n, prec, lam=0.0, b=I.EX2_ALPHA, bc="dirichlet", length=I.EX2_LENGTH, potential=v)
+        U = dev(U0).reshape(-1).clone()
+        res, _ = qn.qn_eig_solve(ctx, U)
+        ctx.close()
+        assert res["status"] == 0 and res["rel"] <= 1e-10, res
+        assert res["lambda"] == pytest.approx(lam_o, rel=1e-9)
+        Ug = host(U).reshape(U0.shape)
+        assert np.abs(Ug - Uo).max() <= 1e-7 * np.abs(Uo).max()
+        its[prec] = res["iterations"]
+    assert its["bf16x6"] <= its["bf16x3"] + 2
