@@ -397,11 +397,14 @@ __global__ void __launch_bounds__(256, 3) k_sys_residual(const SysInst *__restri
                                          T.u[w + 2][lane + 1];
                     const long long lv = 4 * fv - T.v[w + 1][lane] - T.v[w + 1][lane + 2] - T.v[w][lane + 1] -
                                          T.v[w + 2][lane + 1];
-                    float2 lu2, lv2, up, vp;
-                    fx_to_pair(lu, scale, lu2.x, lu2.y);
-                    fx_to_pair(lv, scale, lv2.x, lv2.y);
-                    fx_to_pair(fu, scale, up.x, up.y);
-                    fx_to_pair(fv, scale, vp.x, vp.y);
+                    // both components' conversions in packed FP32x2 chains (the same results)
+                    float2 hi, lo, lu2, lv2, up, vp;
+                    fx_to_pair2(lu, lv, scale, hi, lo);
+                    lu2 = make_float2(hi.x, lo.x);
+                    lv2 = make_float2(hi.y, lo.y);
+                    fx_to_pair2(fu, fv, scale, hi, lo);
+                    up = make_float2(hi.x, lo.x);
+                    vp = make_float2(hi.y, lo.y);
                     // inv_h2 is (n + 1)^2 to FP64 rounding, an FP32 number (n <= 1024): its high part suffices
                     Fuf = pair_sum4(pair_mul_f(lu2, I.ih2.x), pair_cube(up), pair_mul(I.al2, vp), pair_neg(g1c));
                     Fvf = pair_sum4(pair_mul(lv2, I.dh2), pair_cube(vp), pair_neg(pair_mul(I.al2, up)), pair_neg(g2c));

@@ -432,9 +432,9 @@ __global__ void __launch_bounds__(256) k_eig_pass1_df(const double *__restrict__
         float2 lv, up;
         if (!bad) {
             const long long lapfx = (long long)((unsigned long long)(2 * DIM) * (unsigned long long)fu - snb);
-            float lh, ll, uh, ul;
-            fx_to_pair(lapfx, scale, lh, ll);
-            fx_to_pair(fu, scale, uh, ul);
+            float2 ph, pl;   // the stencil sum and u in one packed FP32x2 chain (the same results)
+            fx_to_pair2(lapfx, fu, scale, ph, pl);
+            const float lh = ph.x, ll = pl.x, uh = ph.y, ul = pl.y;
             up = make_float2(uh, ul);
             const float2 cv = (pot != nullptr) ? pair_add(__ldg(vrow2 + row), __ldg(pot2 + x)) : lam2;
             lv = pair_add(pair_mul(make_float2(lh, ll), ih2), pair_mul(cv, up));
@@ -564,9 +564,9 @@ __global__ void __launch_bounds__(256, 3) k_eig_pass1_tiled(const double *__rest
                 if (!(plane_bad || bm || bp)) {
                     const long long lapfx = 6 * fc - sp[buf][w + 1][lane] - sp[buf][w + 1][lane + 2] -
                                             sp[buf][w][lane + 1] - sp[buf][w + 2][lane + 1] - fmv - fp;
-                    float lh, ll, uh, ul;
-                    fx_to_pair(lapfx, scale, lh, ll);
-                    fx_to_pair(fc, scale, uh, ul);
+                    float2 ph, pl;   // the stencil sum and u in one packed FP32x2 chain (the same results)
+                    fx_to_pair2(lapfx, fc, scale, ph, pl);
+                    const float lh = ph.x, ll = pl.x, uh = ph.y, ul = pl.y;
                     up = make_float2(uh, ul);
                     const float2 cv = (pot != nullptr) ? pair_add(__ldg(vrow2 + (long long)z * n + y), __ldg(pot2 + x))
                                                        : lam2;
