@@ -56,7 +56,7 @@ extern "C" {
 #define QN_ENOTCONV     -4  /* max_it reached before the tolerance; U holds the last iterate */
 #define QN_EDIVERGED    -5  /* residual became non-finite or grew past 1e8 x ||f|| */
 #define QN_ETIMEOUT     -6  /* a device-side wait gave up (kernel returned early, no hang) */
-#define QN_EUNSUPPORTED -7  /* valid request this build does not implement */
+#define QN_EUNSUPPORTED -7  /* valid request the library does not implement */
 
 /* ---- enumerations -------------------------------------------------------- */
 #define QN_BC_DIRICHLET 0   /* homogeneous Dirichlet, interior unknowns only (Sec. 3.2) */
