@@ -1145,7 +1145,10 @@ def main():
         run_many(2)
         count = 6
         nb = 7
+        e2e_sampler = ClockSampler(local_rank)   # clocks and throttle reasons during the batches
+        e2e_sampler.start()
         batches = [run_many(count) for _ in range(nb)]
+        e2e_clocks = e2e_sampler.stop()
         res_m = [r for _, rs in batches for r in rs]
         in_order = [t / count for t, _ in batches]
         per_solve = sorted(in_order)
@@ -1184,7 +1187,7 @@ def main():
                "solves": nb * count, "batch_ms_per_solve": [round(t, 3) for t in in_order],
                "all_converged": all(r["status"] == 0 for r in res_m),
                "single_solve_ms": round(statistics.median(single), 3),
-               "single_solve_reps_ms": [round(t, 3) for t in single], "link": link,
+               "single_solve_reps_ms": [round(t, 3) for t in single], "link": link, "clocks": e2e_clocks,
                "host_numa_nodes": len([d for d in os.listdir("/sys/devices/system/node")
                                        if d.startswith("node")]) if os.path.isdir("/sys/devices/system/node") else None,
                "note": (f"qn_solve_host_many, {nb} batches of {count} solves from pinned host memory: per step the "
