@@ -1185,6 +1185,7 @@ def main():
         e2e = {"value": round(many_ms / count, 3), "unit": "ms",
                "h2d_bytes_per_step": (1 if zero else 2) * 8 * N, "d2h_bytes_per_step": 8 * N,
                "solves": nb * count, "batch_ms_per_solve": [round(t, 3) for t in in_order],
+               "best_batch_ms_per_solve": round(per_solve[0], 3),
                "all_converged": all(r["status"] == 0 for r in res_m),
                "single_solve_ms": round(statistics.median(single), 3),
                "single_solve_reps_ms": [round(t, 3) for t in single], "link": link, "clocks": e2e_clocks,
