@@ -1455,12 +1455,13 @@ int launch_residual_tiled(const ResidualArgs &a, int max_grid, int zchunk, int *
 
 int launch_prep_split(const double *U, const double *f, int n, int P, float2 *fdf, __nv_bfloat16 *Rhi,
                       __nv_bfloat16 *Rlo, double *partials, int nparts, DevState *st, bool mirror, cudaStream_t s) {
+    const int g = 2 * nparts;   // (the partials buffer holds 8 records per SM, nparts <= 4 per SM)
     if (mirror)
-        k_prep_split<true><<<nparts, 256, 0, s>>>(U, f, n, P, fdf, Rhi, Rlo, partials, st);
+        k_prep_split<true><<<g, 256, 0, s>>>(U, f, n, P, fdf, Rhi, Rlo, partials, st);
     else
-        k_prep_split<false><<<nparts, 256, 0, s>>>(U, f, n, P, fdf, Rhi, Rlo, partials, st);
+        k_prep_split<false><<<g, 256, 0, s>>>(U, f, n, P, fdf, Rhi, Rlo, partials, st);
     QN_CUDA(cudaGetLastError());
-    k_prep_split_finish<<<1, 256, 0, s>>>(partials, nparts, st);
+    k_prep_split_finish<<<1, 256, 0, s>>>(partials, g, st);
     QN_CUDA(cudaGetLastError());
     return QN_OK;
 }
