@@ -46,24 +46,33 @@ __device__ __forceinline__ unsigned long long small_timer() {
     return t;
 }
 
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Grid barrier: returns false when a wait gave up (or another block's had), after
-// recording QN_ETIMEOUT in *err.
+// recording QN_ETIMEOUT in *err. Thread 0 arrives with one acquire-release add on the
+// counter (after the block's barrier, it releases the block's writes); the last block
+// resets the counter and releases the generation word, which the others poll with
+// acquire loads.
 __device__ bool small_barrier(unsigned *count, unsigned *gen, int *err) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
-        const unsigned g = *(volatile unsigned *)gen;
-        __threadfence();
-        if (atomicAdd(count, 1u) == gridDim.x - 1) {
-            *(volatile unsigned *)count = 0u;
-            __threadfence();
-            atomicAdd(gen, 1u);
+        const unsigned g = ld_acquire(gen);
+        unsigned old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+        if (old == gridDim.x - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(count) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(gen) : "memory");
         } else {
             // the error word and the clock only every 64 polls
             const unsigned long long t0 = small_timer();
             unsigned polls = 0;
-            while (*(volatile unsigned *)gen == g) {
+            while (ld_acquire(gen) == g) {
                 if ((++polls & 63u) == 0 &&
                     (*(volatile int *)err != 0 || small_timer() - t0 > kSmallTimeoutNs)) {
                     atomicExch(err, QN_ETIMEOUT);
@@ -72,8 +81,6 @@ __device__ bool small_barrier(unsigned *count, unsigned *gen, int *err) {
                 }
             }
         }
-        __threadfence();
-        if (*(volatile int *)err != 0) ok = 0;
     }
     __syncthreads();
     return ok != 0;
