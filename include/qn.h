@@ -230,7 +230,11 @@ int qn_step(qn_ctx *ctx, double *U, const double *f, double beta, qn_stats *st, 
  * res (host, may be NULL): iteration count, status, final relative residual.
  * history (host, may be NULL): receives the statistics of iterates
  * U_0 .. U_iterations (history_len entries at most). Synchronises `stream`.
- * Returns res->status (QN_OK when converged). */
+ * 2-D FP64 finite-difference contexts with n <= 128 and no potential (Dirichlet or
+ * Neumann data) run the whole solve as one cooperative kernel that takes the stop
+ * decision on the device (opts->sync_every and opts->graph do not apply; the environment
+ * variable QN_SMALL=0 at context creation, or launch profiling, selects the per-phase
+ * launches). Returns res->status (QN_OK when converged). */
 int qn_solve(qn_ctx *ctx, double *U, const double *f, const qn_opts *opts,
              qn_result *res, qn_stats *history, int history_len, void *stream);
 
