@@ -78,10 +78,15 @@ def parse():
                     help="skip the 2-D 63^2 FP64, 3-D 255^3 FP64 and warm-start legs of the default line")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-start leg (training takes ~100 s)")
     ap.add_argument("--oracle-sample", default=None, choices=["c1", "c2"], help=argparse.SUPPRESS)
-    ap.add_argument("--quick", action="store_true", help="= --no-fp64 --no-cpu --no-e2e --no-batched --no-configs")
+    ap.add_argument("--no-f1", action="store_true",
+                    help="skip the timing of the residual fused into the first mode product")
+    ap.add_argument("--fused", action="store_true",
+                    help="run the main solves with the fused residual (qn_set_fused_residual)")
+    ap.add_argument("--quick", action="store_true",
+                    help="= --no-fp64 --no-cpu --no-e2e --no-batched --no-configs --no-f1")
     a = ap.parse_args()
     if a.quick:
-        a.no_fp64 = a.no_cpu = a.no_e2e = a.no_batched = a.no_configs = True
+        a.no_fp64 = a.no_cpu = a.no_e2e = a.no_batched = a.no_configs = a.no_f1 = True
     if a.n is None:
         a.n = {"dirichlet": 511, "sem": 255}.get(a.workload, 200)
     return a
@@ -421,6 +426,58 @@ def oracle_sample_main(kind: str, seed: int):
         t0 = time.perf_counter()
         O.qn_step(U, f, eig)
         print(json.dumps({"kind": "c2", "per_iteration_s": time.perf_counter() - t0, "threads": 1}))
+
+
+def run_fused(qn, n, f, U_sep, max_it, steps, warmup, stream, prof_sep, sep_ms, hbm):
+    """The same solves with the residual fused into the first forward mode product
+    (qn_set_fused_residual), timed like the line's value; the result against the separate
+    kernels' (the two paths compute the same iterates)."""
+    import torch
+    ctx = qn.QnContext(3, n, "bf16x3")
+    qn.qn_set_fused_residual(ctx, True)
+    U = torch.zeros_like(U_sep)
+    for _ in range(max(warmup, 1)):
+        U.zero_()
+        qn.qn_solve(ctx, U, f, max_it=max_it, graph=True)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    its = []
+    for _ in range(max(steps, 1)):
+        U.zero_()
+        res, _ = qn.qn_solve(ctx, U, f, max_it=max_it, graph=True)
+        its.append(res["iterations"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / max(steps, 1)
+    qn.qn_profile_enable(ctx, True)
+    for _ in range(min(max(steps, 1), 3)):
+        U.zero_()
+        qn.qn_solve(ctx, U, f, max_it=max_it)
+    torch.cuda.synchronize()
+    p = qn.qn_profile_read(ctx)
+    diff = float((U - U_sep).abs().max().item())
+    scale = float(U_sep.abs().max().item())
+    ctx.close()
+    P = ((n + 63) // 64) * 64
+    fz_ms = p["fused_ms"] / max(p["fused_launches"], 1)
+    sep_res = prof_sep["residual_tiled_ms"] / max(prof_sep["residual_tiled_launches"], 1)
+    sep_st = prof_sep["mp_store_ms"] / max(prof_sep["mp_store_launches"], 1)
+    # algorithmic bytes of a fused launch: U and f read (8 + 8 B per unknown), the first
+    # product's hi / lo output written (4 B per padded point); the residual planes of the
+    # separate kernels (4 B per padded point written, then read) do not exist
+    fz_bytes = 16.0 * n ** 3 + 4.0 * P ** 3
+    gbs = fz_bytes / (fz_ms * 1e-3) / 1e9
+    return {"kernel": "k_fused_res_fwd", "default": "off (qn_set_fused_residual)",
+            "ms_per_solve": round(ms, 3), "ms_per_solve_separate": round(sep_ms, 3),
+            "iterations": its[0] if len(set(its)) == 1 else its,
+            "fused_avg_launch_ms": round(fz_ms, 4), "fused_launches": p["fused_launches"],
+            "separate_residual_ms": round(sep_res, 4), "separate_first_product_ms": round(sep_st, 4),
+            "separate_sum_ms": round(sep_res + sep_st, 4),
+            "bytes_per_launch_algorithmic": fz_bytes, "achieved_gbs": round(gbs, 1),
+            "frac_hbm": round(gbs / hbm, 4),
+            "max_abs_diff_vs_separate": diff, "rel_diff_vs_separate": diff / scale if scale > 0 else None}
 
 
 def dgemm_tflops(stream) -> float:
@@ -958,6 +1015,8 @@ def main():
     U = torch.zeros(N, dtype=torch.float64, device="cuda")
     U0 = torch.from_numpy(U0_np).cuda() if ex1 else None
     ctx = qn.QnContext(3, n, a.precision, **ctx_kw)
+    if a.fused:
+        qn.qn_set_fused_residual(ctx, True)
 
     def reset_start():
         if U0 is None:
@@ -1115,6 +1174,11 @@ def main():
                     "avg_launch_ms": round(til_ms if til_n else res_avg_ms, 4),
                     "launches": til_n if til_n else prof["residual_launches"]}
     gpu_launches = timed_launches
+
+    # ---- the residual fused into the first forward mode product (off by default)
+    f1 = None
+    if not ex1 and not sem and a.precision == "bf16x3" and not a.no_f1 and not a.fused:
+        f1 = run_fused(qn, n, f, U.clone(), max_it, a.steps, a.warmup, stream, prof, ms_per_step, hbm)
 
     # ---- end to end through the public API with host buffers (copies inside the timed region)
     e2e = None
@@ -1386,7 +1450,7 @@ def main():
             "parity": parity,
             "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
             "e2e": e2e, "plain_fp64": plain, "batched": batched, "configs": configs,
-            "cpu_baseline": cpu, "clocks": clocks,
+            "f1_fused": f1, "cpu_baseline": cpu, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

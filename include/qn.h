@@ -253,6 +253,23 @@ int qn_solve(qn_ctx *ctx, double *U, const double *f, const qn_opts *opts,
  * qn_profile.x6_from reports where the last solve switched. */
 int qn_set_escalation(qn_ctx *ctx, double rate);
 
+/* The residual fused into the first mode product (the one-kernel form of the residual
+ * F(U) of Sec. 4 eq. F_u and the first forward mode product of the inverse, Sec. 4.1
+ * eq. fin_inverse). on != 0: from the second iteration of each qn_solve on, one kernel
+ * evaluates the residual inside the producer of the first forward reflection-split
+ * product, writing the product's shared-memory operand instead of the residual planes
+ * (no HBM round trip of the planes); on = 0 (the default) restores the separate residual
+ * kernel and product. The iterates are those of the separate kernels: the same fixed-point
+ * stencil, float-pair nonlinear term and products; only the FP32 summation order of
+ * ||F||^2 differs. QN_EUNSUPPORTED (on != 0) unless the context is a 3-D BF16X3 or
+ * BF16X6 finite-difference context with the reflection-split products, n <= 512,
+ * Dirichlet data and no potential. The first call with on != 0 encodes two tensor maps
+ * (a blocking copy to the device): call it outside a stream capture. Does not
+ * synchronise otherwise. qn_profile.fused_launches / fused_ms time the fused kernel.
+ * Off by default because it is slower than the separate kernels (its producer re-reads
+ * and re-converts the z-neighbours of every point). */
+int qn_set_fused_residual(qn_ctx *ctx, int on);
+
 /* qn_solve with HOST arrays: copies f_host and U_host (initial iterate) to
  * context-owned device buffers, solves, copies the result back into U_host.
  * U_host, f_host: host, n^dim doubles (pinned memory gives full copy speed).
@@ -492,6 +509,9 @@ typedef struct qn_profile {
     int x6_from;              /* the last qn_solve: the first iteration whose backward products
                                  ran at the six-product level (0 in a QN_PREC_BF16X6 context,
                                  the escalation point after qn_set_escalation), -1: none */
+    int fused_launches;       /* qn_set_fused_residual: the fused residual + first product
+                                 kernels (counted in neither residual_ nor modeprod_) */
+    double fused_ms;
 } qn_profile;
 
 /* on != 0: from now on record a pair of CUDA events around every kernel

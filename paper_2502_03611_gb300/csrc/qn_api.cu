@@ -105,7 +105,7 @@ struct qn_ctx {
         double *U;
         const double *f;
         double step;
-        int chunk, kind, x6;
+        int chunk, kind, x6, fused;
         long long launches;
     } g_prev;
     // the solver state read by the host: written by a kernel into mapped page-locked host
@@ -136,6 +136,11 @@ struct qn_ctx {
     double esc_rate;      // 0: off
     int esc_at;           // first iteration of the last solve that ran at that level (-1: none)
     int g_x6;             // the captured graph's level
+    // the residual fused into the first forward product (qn_set_fused_residual)
+    int fused;            // 1: iterations >= 1 of the 3-D split solve use k_fused_res_fwd
+    int fused_first;      // 1: the last residual launch also formed the first product
+    int fused_used;       // 1: the current solve has used the fused kernel
+    int g_fused;          // the captured graph's form
     unsigned *small_bar;  // small 2-D FP64 solves: the persistent kernel's grid barrier words
     int small_solve;      // 1: qn_solve runs the whole-solve persistent kernel (qn_small.cu)
     float *lam32_split;   // eigenvalues in split mode order (even modes, then odd), 1e30 padding
@@ -184,7 +189,7 @@ __global__ void k_mirror_state(const DevState *st, int *err, const qn_stats *his
 }
 
 enum ProfKind { PK_RESIDUAL = 0, PK_FINALIZE = 1, PK_MP_STORE = 2, PK_MP_DIVIDE = 3, PK_MP_LAST = 4,
-                PK_SPLIT = 5, PK_RESIDUAL_TILED = 6, PK_COUNT = 7 };
+                PK_SPLIT = 5, PK_RESIDUAL_TILED = 6, PK_FUSED = 7, PK_COUNT = 8 };
 
 // Begin/end a timed launch. With profiling off these only count launches.
 static long prof_begin(qn_ctx *c, int kind, cudaStream_t s) {
@@ -227,7 +232,7 @@ static __nv_bfloat16 split_host_l2(double v, __nv_bfloat16 hi, __nv_bfloat16 lo)
     return __float2bfloat16_rn((float)r);
 }
 
-extern "C" int qn_version(void) { return 10300; }
+extern "C" int qn_version(void) { return 10400; }
 
 extern "C" const char *qn_last_error(void) { return g_err; }
 
@@ -831,10 +836,20 @@ static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double 
         a.fast = 1;
         a.want_f2 = 0;
     }
+    // the residual fused into the first forward product: iterations >= 1 (iteration 0
+    // keeps the preparation pass and its zero-start shortcut), Dirichlet data, no potential
+    c->fused_first = 0;
+    const bool fz = mirror && c->fused && c->cur_iter >= 1 && a.pot == nullptr && a.bc == QN_BC_DIRICHLET;
     // the iteration-0 launch after the preparation pass (which skips its work for a zero
     // start) is accounted with the preparation, so that the tiled kind covers full evaluations
-    const long pr = prof_begin(c, (tiled && a.zero_start == nullptr) ? PK_RESIDUAL_TILED : PK_RESIDUAL, s);
-    if (mirror) {
+    const long pr = prof_begin(c, fz ? PK_FUSED : (tiled && a.zero_start == nullptr) ? PK_RESIDUAL_TILED : PK_RESIDUAL, s);
+    if (fz) {
+        FusedFwd ff;
+        rc = tc_plan_fused_args(c->plan, 1, c->err, &ff);
+        if (rc == QN_OK) rc = launch_fused_residual_fwd(a, ff, &c->res_parts, s);
+        c->fused_first = 1;
+        c->fused_used = 1;
+    } else if (mirror) {
         rc = launch_residual_mirror(a, c->nparts, c->res_zc, &c->res_parts, s);
     } else if (tiled) {
         rc = launch_residual_tiled(a, c->nparts, c->res_zc, &c->res_parts, s);
@@ -849,7 +864,7 @@ static int enqueue_residual(qn_ctx *c, const double *U, const double *f, double 
 // Shifted inverse of working buffer 0 (or of `r0` for the FP64 path), written
 // as U -= step*delta (update=true) or V = delta (update=false).
 static int enqueue_inverse(qn_ctx *c, const double *r0, double *target, bool update, double step,
-                           cudaStream_t s, bool split = false) {
+                           cudaStream_t s, bool split = false, bool skip_first = false) {
     const int d = c->dim;
     EpiArgs e = epi_args(c, target, step);
     c->last_split = (split && update) ? 1 : 0;
@@ -857,8 +872,9 @@ static int enqueue_inverse(qn_ctx *c, const double *r0, double *target, bool upd
         // reflection-split products on the split / folded planes of the residual
         e.lam32 = c->lam32_split;
         const Epi seq[6] = {EPI_STORE_BFLY, EPI_STORE_BFLY, EPI_DIVIDE, EPI_STORE_PQ, EPI_STORE_PQ, EPI_UPDATE_PQ};
-        int cur = 0;
-        for (int i = 0; i < 6; ++i) {
+        // skip_first: the fused residual kernel already wrote the first product to buffer 1
+        int cur = skip_first ? 1 : 0;
+        for (int i = skip_first ? 1 : 0; i < 6; ++i) {
             const bool last = (i == 5);
             const int next = 1 - cur;
             const long pr = prof_begin(c, last ? PK_MP_LAST : (i == 2 ? PK_MP_DIVIDE : PK_MP_STORE), s);
@@ -911,7 +927,7 @@ static int enqueue_iteration(qn_ctx *c, double *U, const double *f, double step,
                          c->res_saved_fnorm, c->pot64 != nullptr, s);
     prof_end(c, pr, s);
     if (rc) return rc;
-    return enqueue_inverse(c, nullptr, U, true, step, s, c->split_layout != 0);
+    return enqueue_inverse(c, nullptr, U, true, step, s, c->split_layout != 0, c->fused_first != 0);
 }
 
 // Capture `chunk` steady-state iterations (third iteration on: the residual
@@ -921,12 +937,13 @@ static int enqueue_eig_iteration(qn_ctx *c, double *U, double step, cudaStream_t
 
 static int ensure_iteration_graph(qn_ctx *c, double *U, const double *f, double step, int chunk, int kind = 0) {
     if (c->gexec && c->g_U == U && c->g_f == f && c->g_step == step && c->g_chunk == chunk && c->g_kind == kind &&
-        c->g_x6 == c->x6)
+        c->g_x6 == c->x6 && c->g_fused == c->fused)
         return QN_OK;
-    qn_ctx::GraphSlot cur{c->gexec, c->g_U, c->g_f, c->g_step, c->g_chunk, c->g_kind, c->g_x6, c->g_launches};
+    qn_ctx::GraphSlot cur{c->gexec, c->g_U, c->g_f, c->g_step, c->g_chunk, c->g_kind, c->g_x6, c->g_fused,
+                          c->g_launches};
     const qn_ctx::GraphSlot &pv = c->g_prev;
     if (pv.exec && pv.U == U && pv.f == f && pv.step == step && pv.chunk == chunk && pv.kind == kind &&
-        pv.x6 == c->x6) {
+        pv.x6 == c->x6 && pv.fused == c->fused) {
         // the previous graph matches: swap it in
         c->gexec = pv.exec;
         c->g_U = pv.U;
@@ -935,6 +952,7 @@ static int ensure_iteration_graph(qn_ctx *c, double *U, const double *f, double 
         c->g_chunk = pv.chunk;
         c->g_kind = pv.kind;
         c->g_x6 = pv.x6;
+        c->g_fused = pv.fused;
         c->g_launches = pv.launches;
         c->g_prev = cur;
         return QN_OK;
@@ -975,6 +993,7 @@ static int ensure_iteration_graph(qn_ctx *c, double *U, const double *f, double 
     c->g_chunk = chunk;
     c->g_kind = kind;
     c->g_x6 = c->x6;
+    c->g_fused = c->fused;
     return QN_OK;
 }
 
@@ -1126,6 +1145,24 @@ extern "C" int qn_set_escalation(qn_ctx *c, double rate) {
     return QN_OK;
 }
 
+extern "C" int qn_set_fused_residual(qn_ctx *c, int on) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (on) {
+        if (c->dim != 3 || c->prob.precision != QN_PREC_BF16X3 || !c->split || c->fdf == nullptr || !c->res_tiled ||
+            c->prob.bc != QN_BC_DIRICHLET || c->pot64 != nullptr || c->prob.sem_k > 0) {
+            set_error("qn_set_fused_residual: needs a 3-D BF16X3 / BF16X6 finite-difference context with the "
+                      "reflection-split products, Dirichlet data and no potential");
+            return QN_EUNSUPPORTED;
+        }
+        rc = tc_plan_enable_fused(c->plan);
+        if (rc == QN_EUNSUPPORTED) set_error("qn_set_fused_residual: the fused kernel takes P <= 512");
+        if (rc) return rc;
+    }
+    c->fused = on ? 1 : 0;
+    return QN_OK;
+}
+
 extern "C" int qn_solve(qn_ctx *c, double *U, const double *f, const qn_opts *opts, qn_result *res,
                         qn_stats *history, int history_len, void *stream) {
     return solve_internal(c, U, f, opts, res, history, history_len, stream, nullptr, nullptr);
@@ -1166,6 +1203,7 @@ int qn::solve_internal(qn_ctx *c, double *U, const double *f, const qn_opts *opt
     c->aux_launches = 0;
     c->x6 = c->x6_base;
     c->esc_at = c->x6_base ? 0 : -1;
+    c->fused_used = 0;
     rc = reset_state(c, o.tol, o.max_it, o.beta_mode, o.beta_value, s);
     if (rc) return rc;
     DevState h;
@@ -1282,6 +1320,8 @@ int qn::solve_internal(qn_ctx *c, double *U, const double *f, const qn_opts *opt
                         : launches0 + 2LL * (its + 1) + 2LL * c->dim * its + c->aux_launches;
     if (c->prob.precision == QN_PREC_BF16X3 && c->fdf != nullptr && c->res_tiled)
         c->launches += 2 + (its >= 1 ? 2 : 0);   // preparation kernels of iterations 0 and 1
+    // the fused residual of iterations 1 .. its - 1 also formed their first product
+    if (!small && c->fused_used && its >= 2) c->launches -= its - 1;
     // the statistics of the final iterate came with the last state mirror
     qn_stats last;
     memcpy(&last, const_cast<const qn_stats *>(&((const volatile StateMirror *)c->mir_host)->last), sizeof(last));
@@ -1463,6 +1503,8 @@ extern "C" int qn_profile_read(qn_ctx *c, qn_profile *out) {
     out->mp_divide_ms = ms[PK_MP_DIVIDE];
     out->mp_last_launches = cnt[PK_MP_LAST];
     out->mp_last_ms = ms[PK_MP_LAST];
+    out->fused_launches = cnt[PK_FUSED];
+    out->fused_ms = ms[PK_FUSED];
     return QN_OK;
 }
 

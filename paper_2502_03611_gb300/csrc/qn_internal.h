@@ -136,6 +136,26 @@ int launch_prep_split(const double *U, const double *f, int n, int P, float2 *fd
 // The same residual written in split order along x and folded order along y
 // and z, the input layout of the reflection-split mode products.
 int launch_residual_mirror(const ResidualArgs &a, int max_grid, int zchunk, int *grid_used, cudaStream_t s);
+// The residual fused into the first forward reflection-split mode product
+// (k_fused_res_fwd): what k_residual_mirror and the EPI_STORE_BFLY product that reads
+// its planes compute, in one launch. FusedFwd carries the product's side: the
+// forward matrix [P][H] as hi / lo tensor maps with 32 x H boxes and the 64-byte
+// swizzle, the output planes of the product and the device error word.
+struct FusedFwd {
+    const CUtensorMap *b_hi, *b_lo;
+    __nv_bfloat16 *out_hi, *out_lo;
+    int *err;
+    int num_sms;
+};
+struct TcPlan;
+int fused_set_attributes();
+int launch_fused_residual_fwd(const ResidualArgs &a, const FusedFwd &ff, int *grid_used, cudaStream_t s);
+// Encodes the fused kernel's maps of the plan's forward matrix (once; not during a
+// stream capture) and opts the kernel in to its shared memory. QN_EUNSUPPORTED
+// without reflection-split products or for P > 512.
+int tc_plan_enable_fused(TcPlan *p);
+// The FusedFwd of a plan prepared by tc_plan_enable_fused, writing working buffer dst.
+int tc_plan_fused_args(const TcPlan *p, int dst, int *err, FusedFwd *out);
 int launch_umax(const double *U, long long N, DevState *st, int grid, cudaStream_t s);
 // mode 0: the partial records hold min / max U^2. 1 (a potential is present): min / max of
 // 3 b U^2 + V, and the fixed-point exponent comes from DevState::umax_scan. 2 (eigen solve):

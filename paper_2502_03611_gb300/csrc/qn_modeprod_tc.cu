@@ -173,8 +173,12 @@ __device__ __forceinline__ bool group_done(const TcGroup &G) {
     return G.done != nullptr && *(volatile const int *)G.done;
 }
 
-// 576 threads x 104 registers (one CTA per SM; 112 exceeds the launch limit)
-static_assert(kThreads * 104 <= 65536, "register file");
+// 576 threads, one CTA per SM. The register file is split over the SM's four
+// sub-partitions of 16384 registers and 18 warps put five on two of them, so a thread may
+// hold at most 96 registers (five warps x 32 threads x 96 <= 16384; a 104-register kernel
+// of this block size is refused at launch). Every instantiation below compiles to at most
+// 96 under the cap of 104 (ptxas -v).
+static_assert(5 * 32 * 96 <= 16384 && (kThreads / 32 + 3) / 4 == 5, "register file");
 
 template <int BK, int EPI, int DIM, int MODE, bool L3 = false>
 __global__ void __maxnreg__(104)
@@ -576,14 +580,16 @@ struct TcPlan {
     int split, BN1, BN2, num_sms;   // reflection-split products: forward / backward tile widths
     size_t smem;
     int x6;              // tc_plan_enable_x6 done
+    int fused;           // tc_plan_enable_fused done
+    const __nv_bfloat16 *bf_hi, *bf_lo;   // the forward split matrix [P][P/2] (tc_plan_enable_split)
     CUtensorMap *maps;   // device: a_hi[2], a_lo[2], s_hi, s_lo, si_hi, si_lo, bf_hi, bf_lo, bb_hi, bb_lo,
-                         // a_l2[2], bb_l2 (kPlanMaps entries)
+                         // a_l2[2], bb_l2, and the fused kernel's bf_hi, bf_lo (kPlanMaps entries)
     __nv_bfloat16 *bufs_hi[2];
     __nv_bfloat16 *bufs_lo[2];
     __nv_bfloat16 *bufs_l2[2];
 };
 
-constexpr int kPlanMaps = 16;
+constexpr int kPlanMaps = 18;
 
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -725,7 +731,34 @@ int tc_plan_enable_split(TcPlan *p, const __nv_bfloat16 *bf_hi, const __nv_bfloa
     if (rc == QN_OK) rc = tc_encode_2d(&h[3], bb_lo, H, p->P, p->BK, p->BN2, p->BK);
     if (rc != QN_OK) return rc;
     QN_CUDA(cudaMemcpy(p->maps + 8, h, sizeof(h), cudaMemcpyHostToDevice));
+    p->bf_hi = bf_hi;
+    p->bf_lo = bf_lo;
     p->split = 1;
+    return QN_OK;
+}
+
+int tc_plan_enable_fused(TcPlan *p) {
+    if (p == nullptr || !p->split || p->P > 512) return QN_EUNSUPPORTED;
+    if (p->fused) return QN_OK;
+    const int H = p->P / 2;
+    CUtensorMap h[2];
+    int rc = tc_encode_2d(&h[0], p->bf_hi, H, p->P, 32, H, 32);
+    if (rc == QN_OK) rc = tc_encode_2d(&h[1], p->bf_lo, H, p->P, 32, H, 32);
+    if (rc == QN_OK) rc = fused_set_attributes();
+    if (rc != QN_OK) return rc;
+    QN_CUDA(cudaMemcpy(p->maps + 16, h, sizeof(h), cudaMemcpyHostToDevice));
+    p->fused = 1;
+    return QN_OK;
+}
+
+int tc_plan_fused_args(const TcPlan *p, int dst, int *err, FusedFwd *out) {
+    if (p == nullptr || !p->fused || dst < 0 || dst > 1) return QN_EUNSUPPORTED;
+    out->b_hi = p->maps + 16;
+    out->b_lo = p->maps + 17;
+    out->out_hi = p->bufs_hi[dst];
+    out->out_lo = p->bufs_lo[dst];
+    out->err = err;
+    out->num_sms = p->num_sms;
     return QN_OK;
 }
 

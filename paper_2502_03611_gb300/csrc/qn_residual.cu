@@ -21,6 +21,7 @@
 #include "qn_internal.h"
 #include "qn_df.cuh"
 #include "qn_numeric.cuh"
+#include "qn_ptx.cuh"
 
 namespace qn {
 
@@ -1279,6 +1280,448 @@ __global__ void __launch_bounds__(kTThreads, 2) k_residual_mirror(ResidualArgs a
     tile_partials<KIND>(a, kr2, kc, r2k, amin, amax, dmn, dmx);
 }
 
+// ---------------------------------------------------------------------------
+// k_fused_res_fwd: the residual of the split solve and the first forward
+// reflection-split mode product (the contraction of x, Sec. 4.1 eq.
+// fin_inverse, applied to F(U) of Sec. 4 eq. F_u) in one kernel. The residual
+// is formed in shared memory as the product's A operand, instead of being
+// written to HBM as split planes and read back by the product.
+//
+// A product tile is 128 rows m = (z_f, y_f) of one folded plane (64 spatial
+// rows y and their mirrors n-1-y) times the whole split x axis. One CTA takes
+// both halves of a tile (the sums a_j against the even modes, the differences
+// b_j against the odd modes: two accumulators of H FP32 columns, all 512 TMEM
+// columns), so every point's residual is formed once. Per pipeline stage
+// (32 positions j of the split axis):
+//   warp 0 lane 0   TMA of the B tiles: the even and odd rows of the forward
+//                   matrix [P][H], hi and lo, 32 x H each, 64-byte swizzle
+//   warp 1          allocates TMEM; lane 0 issues tcgen05.mma per half:
+//                   a_hi b_hi + a_hi b_lo + a_lo b_hi (FP32 accumulators)
+//   warps 2..17     the residual: warps 2..9 the even rows (y ascending),
+//                   10..17 the odd rows (the mirrors, y descending), eight
+//                   consecutive spatial rows per warp; lane l owns the points
+//                   x = j0 + l and n-1-j0-l. The fixed-point values march in y
+//                   (the rows above and below stay in registers, the loads of
+//                   the next row are issued one row ahead); x neighbours come
+//                   from the adjacent lanes by shuffles and the four strip ends
+//                   from one extra load; the z - 1 and z + 1 values are loaded
+//                   and converted per point. The arithmetic is that of
+//                   k_residual_mirror (exact int64 stencil, float-pair
+//                   nonlinear term, FP32 result; a row that touches a value
+//                   above the fixed-point range takes the exact per-point
+//                   path). Sums and differences are split into BF16 hi + lo
+//                   and stored in the swizzled layout a TMA load would write.
+//                   After a tile's last stage the same warps run the first
+//                   product's epilogue (the butterflies of y, as the
+//                   EPI_STORE_BFLY epilogue of k_modeprod_tc).
+// Dirichlet data without a potential (KIND 0-2); per-CTA partial records as
+// the other tiled residuals. Every mbarrier wait is bounded (2 s of
+// %globaltimer): on expiry the kernel sets the error word and the other roles
+// stop; the TMA producer waits (bounded) for its armed stages and the MMA
+// issuer for its last commit before TMEM is freed.
+// ---------------------------------------------------------------------------
+constexpr int kFzThreads = 576;
+constexpr int kFzWorkers = 16;
+constexpr uint32_t kFzATile = 128u * 64u;   // 128 rows x 32 BF16
+constexpr uint32_t kFzBTile = 256u * 64u;   // up to 256 rows x 32 BF16
+constexpr uint32_t kFzStage = 4u * kFzATile + 4u * kFzBTile;
+constexpr int kFzStages = 2;
+constexpr uint32_t kFzSmem = 1024u + kFzStages * kFzStage + 256u;
+constexpr unsigned long long kFzTimeoutNs = 2000000000ull;
+static_assert(kFzThreads == 64 + 32 * kFzWorkers, "roles");
+
+__device__ __forceinline__ bool fz_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err) {
+    if (ptx::mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = ptx::globaltimer();
+    while (true) {
+        if (ptx::mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (ptx::globaltimer() - t0 > kFzTimeoutNs) {
+            *abort_flag = 1;
+            atomicExch(err, QN_ETIMEOUT);
+            return false;
+        }
+    }
+}
+
+// Bounded wait that ignores the abort flag (draining after an abort).
+__device__ __forceinline__ void fz_drain(uint32_t bar, uint32_t parity) {
+    const unsigned long long t0 = ptx::globaltimer();
+    while (!ptx::mbar_try_wait(bar, parity))
+        if (ptx::globaltimer() - t0 > kFzTimeoutNs) return;
+}
+
+// Byte offset of element (row, col) of a 32-column BF16 tile in the 64-byte
+// swizzle (16-byte chunk c of row r at chunk c ^ ((r / 2) mod 4)): the layout
+// of a TMA load with CU_TENSOR_MAP_SWIZZLE_64B into a 512-byte aligned tile.
+__device__ __forceinline__ uint32_t sw64_off(int row, int col) {
+    return (uint32_t)row * 64u + (((((uint32_t)col) >> 3) ^ (((uint32_t)row >> 1) & 3u)) << 4) +
+           (((uint32_t)col & 7u) << 1);
+}
+
+__device__ __forceinline__ void st_shared_b16(uint32_t addr, __nv_bfloat16 v) {
+    asm volatile("st.shared.b16 [%0], %1;" ::"r"(addr), "h"(__bfloat16_as_ushort(v)) : "memory");
+}
+
+// Loads of one march row issued a row ahead: planes z - 1 and z + 1 at both
+// points, the strip-end value (lanes 0, 1, 30, 31) and the f pairs.
+struct FzAhead {
+    unsigned long long ml, mr, pl, pr, h;
+    float4 f;
+};
+
+// 96 registers: the limit for 18 warps per CTA (five of them share one of the SM's four
+// 16384-register sub-partitions)
+template <int KIND>
+__global__ void __maxnreg__(96) k_fused_res_fwd(ResidualArgs a, FusedFwd ff) {
+    static_assert(KIND >= 0 && KIND <= 2, "Dirichlet data without a potential");
+    if (a.done != nullptr && *(volatile const int *)a.done) return;
+    const int n = a.n, P = a.P, H = P / 2;
+    const int nsym = (n + 1) / 2, nanti = n / 2;
+    const long long Mtot = (long long)P * P;
+    const int ntiles = (int)(Mtot / 128);
+    const int KB = H / 32;
+
+    extern __shared__ uint8_t fz_raw[];
+    const uint32_t raw = ptx::smem_u32(fz_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t ctrl = base + (uint32_t)kFzStages * kFzStage;
+    auto full_bar = [&](int s) { return ctrl + 8u * (uint32_t)s; };
+    auto empty_bar = [&](int s) { return ctrl + 16u + 8u * (uint32_t)s; };
+    const uint32_t tfull_bar = ctrl + 32u, tempty_bar = ctrl + 40u, mma_done_bar = ctrl + 48u;
+    const uint32_t tmem_slot = ctrl + 56u;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(fz_raw + (ctrl + 60u - raw));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr unsigned kAll = 0xffffffffu;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kFzStages; ++s) {
+            ptx::mbar_init(full_bar(s), 1 + kFzWorkers);   // the TMA arrival + one per worker warp
+            ptx::mbar_init(empty_bar(s), 1);
+        }
+        ptx::mbar_init(tfull_bar, 1);
+        ptx::mbar_init(tempty_bar, kFzWorkers);
+        ptx::mbar_init(mma_done_bar, 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+        ptx::fence_proxy_async();
+        ptx::prefetch_tensormap(ff.b_hi);
+        ptx::prefetch_tensormap(ff.b_lo);
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(tmem_slot, 512);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t *>(fz_raw + (tmem_slot - raw));
+
+    // partial sums of the worker threads (the identity elsewhere)
+    float kr2 = 0.0f, kc = 0.0f;
+    unsigned long long amin = 0x7FFFFFFFFFFFFFFFull, amax = 0ull;
+    const int r2k = *a.r2_exp;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------ TMA of B ----------------------------------
+        uint32_t armed_parity[kFzStages];
+        uint32_t armed_mask = 0;
+        int s = 0;
+        uint32_t ph = 0;
+        bool ok = true;
+        const uint32_t tx = 4u * (uint32_t)H * 64u;
+        for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+            for (int kb = 0; kb < KB; ++kb) {
+                if (!fz_wait(empty_bar(s), ph ^ 1u, abort_flag, ff.err)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t sb = base + (uint32_t)s * kFzStage + 4u * kFzATile;
+                ptx::mbar_arrive_expect_tx(full_bar(s), tx);
+                ptx::tma_load_2d(sb, ff.b_hi, full_bar(s), kb * 32, 0);
+                ptx::tma_load_2d(sb + kFzBTile, ff.b_lo, full_bar(s), kb * 32, 0);
+                ptx::tma_load_2d(sb + 2u * kFzBTile, ff.b_hi, full_bar(s), kb * 32, H);
+                ptx::tma_load_2d(sb + 3u * kFzBTile, ff.b_lo, full_bar(s), kb * 32, H);
+                armed_parity[s] = ph;
+                armed_mask |= 1u << s;
+                if (++s == kFzStages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+        }
+        if (!ok) {
+            for (int i = 0; i < kFzStages; ++i)
+                if (armed_mask & (1u << i)) fz_drain(full_bar(i), armed_parity[i]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------ MMA issuer --------------------------------
+        int s = 0;
+        uint32_t ph = 0, aph = 0;
+        bool ok = true;
+        const uint32_t idesc = ptx::idesc_bf16_f32(128, (uint32_t)H);
+        for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+            if (!fz_wait(tempty_bar, aph ^ 1u, abort_flag, ff.err)) break;
+            ptx::tc_fence_after();
+            for (int kb = 0; kb < KB; ++kb) {
+                if (!fz_wait(full_bar(s), ph, abort_flag, ff.err)) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint32_t st = base + (uint32_t)s * kFzStage;
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const uint32_t ko = (uint32_t)kk * 32u;
+                    const uint64_t sa_hi = ptx::smem_desc_kmajor(st + ko, 64, 4);
+                    const uint64_t sa_lo = ptx::smem_desc_kmajor(st + kFzATile + ko, 64, 4);
+                    const uint64_t sd_hi = ptx::smem_desc_kmajor(st + 2u * kFzATile + ko, 64, 4);
+                    const uint64_t sd_lo = ptx::smem_desc_kmajor(st + 3u * kFzATile + ko, 64, 4);
+                    const uint32_t sb = st + 4u * kFzATile + ko;
+                    const uint64_t be_hi = ptx::smem_desc_kmajor(sb, 64, 4);
+                    const uint64_t be_lo = ptx::smem_desc_kmajor(sb + kFzBTile, 64, 4);
+                    const uint64_t bo_hi = ptx::smem_desc_kmajor(sb + 2u * kFzBTile, 64, 4);
+                    const uint64_t bo_lo = ptx::smem_desc_kmajor(sb + 3u * kFzBTile, 64, 4);
+                    const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+                    ptx::mma_bf16(tmem_base, sa_hi, be_hi, idesc, first);
+                    ptx::mma_bf16(tmem_base, sa_hi, be_lo, idesc, 1u);
+                    ptx::mma_bf16(tmem_base, sa_lo, be_hi, idesc, 1u);
+                    ptx::mma_bf16(tmem_base + (uint32_t)H, sd_hi, bo_hi, idesc, first);
+                    ptx::mma_bf16(tmem_base + (uint32_t)H, sd_hi, bo_lo, idesc, 1u);
+                    ptx::mma_bf16(tmem_base + (uint32_t)H, sd_lo, bo_hi, idesc, 1u);
+                }
+                ptx::mma_commit(empty_bar(s));
+                if (++s == kFzStages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+            if (!ok) break;
+            ptx::mma_commit(tfull_bar);
+            aph ^= 1u;
+        }
+        ptx::mma_commit(mma_done_bar);
+        fz_drain(mma_done_bar, 0);
+    } else if (warp >= 2) {
+        // ------------------------- residual workers / epilogue ---------------------
+        const int wk = warp - 2;
+        const int grp = wk >> 3, wi = wk & 7;   // grp 0: even rows, 1: odd rows (mirrors)
+        const int q = warp & 3, part = wk >> 2;  // epilogue: TMEM lane quadrant, column range
+        const int E = *a.fx_e;
+        const bool fx_ok = (E != 0);
+        const float scale = __int_as_float(fx_ok ? ((E - 1075 - kFxG + 127) << 23) : 0);
+        const float ih = __double2float_rn(a.inv_h2);
+        const float il = __double2float_rn(a.inv_h2 - (double)ih);
+        float bh = 1.0f, bl = 0.0f, lh = 0.0f, ll = 0.0f;
+        if (KIND != 2) {
+            bh = __double2float_rn(a.b);
+            bl = __double2float_rn(a.b - (double)bh);
+        }
+        if (KIND == 0) {
+            lh = __double2float_rn(a.lam);
+            ll = __double2float_rn(a.lam - (double)lh);
+        }
+        const float r2s = __int_as_float((127 - r2k) << 23);   // 2^-r2k
+        const long long nn = (long long)n * n;
+        const unsigned long long *Ub = reinterpret_cast<const unsigned long long *>(a.U);
+        const float4 *fdf4 = reinterpret_cast<const float4 *>(a.fdf);
+        int s = 0;
+        uint32_t ph = 0, aph = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+            const int m0 = t * 128;
+            const int zf = m0 / P, yf0 = m0 % P;
+            const int zi = zf >> 1;
+            const bool zval = (zf & 1) ? (zi < nanti) : (zi < nsym);
+            const int z = (zf & 1) ? n - 1 - zi : zi;
+            const int i0 = (yf0 >> 1) + 8 * wi;            // march row k: index i0 + k of its group
+            const int ybase = grp ? n - 1 - i0 : i0;       // spatial y of march row k: ybase + ydir k
+            const int ydir = grp ? -1 : 1;
+            const int own_lim = grp ? nanti : nsym;        // row k is a grid row iff i0 + k < own_lim
+            const unsigned long long *pz = Ub + (long long)(zval ? z : 0) * nn;
+            const bool zm_in = zval && z > 0, zp_in = zval && z + 1 < n;
+            for (int kb = 0; kb < KB; ++kb) {
+                const bool ready = fz_wait(empty_bar(s), ph ^ 1u, abort_flag, ff.err);
+                if (!__all_sync(kAll, ready)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t st = base + (uint32_t)s * kFzStage;
+                const int j0 = kb * 32;
+                const int xL = j0 + lane, xR = n - 1 - xL;   // 0 <= xR, xL < n (n > H)
+                const bool oL = xL < nsym, oR = xL < nanti;
+                // strip ends: lane 0 x = j0 - 1, lane 1 x = n - j0, lane 30 x = j0 + 32, lane 31 x = n - 33 - j0
+                const int hx = (lane == 0) ? j0 - 1 : (lane == 1) ? n - j0 : (lane == 30) ? j0 + 32 : (lane == 31) ? n - 33 - j0 : -1;
+                const bool hin = hx >= 0 && hx < n;
+                if (zval) {
+                    auto load_c = [&](int k, unsigned long long &vl, unsigned long long &vr) {
+                        const int y = ybase + ydir * k;
+                        const bool yin = y >= 0 && y < n;
+                        const unsigned long long *p = pz + (long long)(yin ? y : 0) * n;
+                        vl = yin ? __ldg(p + xL) : 0ull;
+                        vr = yin ? __ldg(p + xR) : 0ull;
+                    };
+                    auto load_ahead = [&](int k, FzAhead &L) {
+                        const int y = ybase + ydir * k;
+                        const bool yin = y >= 0 && y < n;
+                        const long long yo = (long long)(yin ? y : 0) * n;
+                        const unsigned long long *p = pz + yo;
+                        L.ml = (yin && zm_in) ? __ldg(p - nn + xL) : 0ull;
+                        L.mr = (yin && zm_in) ? __ldg(p - nn + xR) : 0ull;
+                        L.pl = (yin && zp_in) ? __ldg(p + nn + xL) : 0ull;
+                        L.pr = (yin && zp_in) ? __ldg(p + nn + xR) : 0ull;
+                        L.h = (yin && hin) ? __ldg(p + hx) : 0ull;
+                        L.f = yin ? __ldg(fdf4 + (((long long)z * P + y) * H + xL)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    };
+                    unsigned long long rl, rr, nxl, nxr;
+                    unsigned bp = 0, bc = 0;
+                    load_c(-1, rl, rr);
+                    long long pL = fx_of(rl, E, bp), pR = fx_of(rr, E, bp);
+                    load_c(0, rl, rr);
+                    long long cL = fx_of(rl, E, bc), cR = fx_of(rr, E, bc);
+                    unsigned long long cbl = rl, cbr = rr;   // bit patterns of the current row (min / max)
+                    load_c(1, nxl, nxr);
+                    FzAhead ah;
+                    load_ahead(0, ah);
+#pragma unroll 1
+                    for (int k = 0; k < 8; ++k) {
+                        unsigned bn = 0, bz = 0;
+                        const long long nL = fx_of(nxl, E, bn), nR = fx_of(nxr, E, bn);
+                        const unsigned long long nbl = nxl, nbr = nxr;
+                        const long long zmL = fx_of(ah.ml, E, bz), zmR = fx_of(ah.mr, E, bz);
+                        const long long zpL = fx_of(ah.pl, E, bz), zpR = fx_of(ah.pr, E, bz);
+                        const long long hv = fx_of(ah.h, E, bz);
+                        const float4 fq = ah.f;
+                        if (k + 2 <= 8) load_c(k + 2, nxl, nxr);
+                        if (k + 1 < 8) load_ahead(k + 1, ah);
+
+                        // x neighbours from the adjacent lanes, the strip ends from lanes 0, 1, 30, 31
+                        long long xLm = __shfl_up_sync(kAll, cL, 1), xLp = __shfl_down_sync(kAll, cL, 1);
+                        long long xRm = __shfl_down_sync(kAll, cR, 1), xRp = __shfl_up_sync(kAll, cR, 1);
+                        const long long hdn = __shfl_down_sync(kAll, hv, 1), hup = __shfl_up_sync(kAll, hv, 1);
+                        if (lane == 0) {
+                            xLm = hv;
+                            xRp = hdn;
+                        }
+                        if (lane == 31) {
+                            xLp = hup;
+                            xRm = hv;
+                        }
+                        const bool row_bad = __any_sync(kAll, (bp | bc | bn | bz) != 0u) || !fx_ok;
+                        const int y = ybase + ydir * k;
+                        const bool rown = (i0 + k) < own_lim;
+                        const bool vL = rown && oL, vR = rown && oR;
+                        float rL = 0.0f, rR = 0.0f;
+                        if (!row_bad) {
+                            typedef unsigned long long u64;
+                            // 6u - (x- + x+ + y- + y+ + z- + z+), exact (wrap-free: |sum| < 2^62)
+                            const long long lapL = (long long)(6ull * (u64)cL - ((((u64)xLm + (u64)xLp) + ((u64)pL + (u64)nL)) + ((u64)zmL + (u64)zpL)));
+                            const long long lapR = (long long)(6ull * (u64)cR - ((((u64)xRm + (u64)xRp) + ((u64)pR + (u64)nR)) + ((u64)zmR + (u64)zpR)));
+                            const float2 r01 = residual_pair2<KIND>(cL, cR, lapL, lapR, make_float2(fq.x, fq.z),
+                                                                    make_float2(fq.y, fq.w), scale, ih, il, bh, bl,
+                                                                    f2_splat(lh), f2_splat(ll));
+                            rL = r01.x;
+                            rR = r01.y;
+                        } else {
+                            if (vL) rL = residual_point_exact(a.U, a.f, n, xL, y, z, a.inv_h2, a.lam, a.b, a.bc, nullptr).x;
+                            if (vR) rR = residual_point_exact(a.U, a.f, n, xR, y, z, a.inv_h2, a.lam, a.b, a.bc, nullptr).x;
+                        }
+                        rL = vL ? rL : 0.0f;
+                        rR = vR ? rR : 0.0f;
+                        minmax_bits(cbl, vL, amin, amax);
+                        minmax_bits(cbr, vR, amin, amax);
+                        // sum (r 2^-k)^2 (FP32, Kahan)
+                        const float q0 = __fmul_rn(rL, r2s), q1 = __fmul_rn(rR, r2s);
+                        const float sq = __fmaf_rn(q0, q0, __fmul_rn(q1, q1));
+                        const float yk = __fsub_rn(sq, kc);
+                        const float tk = __fadd_rn(kr2, yk);
+                        kc = __fsub_rn(__fsub_rn(tk, kr2), yk);
+                        kr2 = tk;
+                        // the sum a_j and the difference b_j (none for the middle point of an odd n)
+                        __nv_bfloat16 a_h, a_l, d_h, d_l;
+                        split_bf16(__fadd_rn(rL, rR), a_h, a_l);
+                        split_bf16(vR ? __fsub_rn(rL, rR) : 0.0f, d_h, d_l);
+                        const uint32_t o = st + sw64_off(2 * (8 * wi + k) + grp, lane);
+                        st_shared_b16(o, a_h);
+                        st_shared_b16(o + kFzATile, a_l);
+                        st_shared_b16(o + 2u * kFzATile, d_h);
+                        st_shared_b16(o + 3u * kFzATile, d_l);
+                        pL = cL;
+                        pR = cR;
+                        cL = nL;
+                        cR = nR;
+                        bp = bc;
+                        bc = bn;
+                        cbl = nbl;
+                        cbr = nbr;
+                    }
+                } else {
+                    // a padding plane: zero rows
+                    const __nv_bfloat16 zb = __float2bfloat16_rn(0.0f);
+                    for (int k = 0; k < 8; ++k) {
+                        const uint32_t o = st + sw64_off(2 * (8 * wi + k) + grp, lane);
+                        st_shared_b16(o, zb);
+                        st_shared_b16(o + kFzATile, zb);
+                        st_shared_b16(o + 2u * kFzATile, zb);
+                        st_shared_b16(o + 3u * kFzATile, zb);
+                    }
+                }
+                // the generic-proxy stores become visible to the tensor core's async proxy
+                ptx::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(full_bar(s));
+                if (++s == kFzStages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+            if (!ok) break;
+            // ---- epilogue of the tile: butterflies of y into the next product's layout ----
+            const bool ready = fz_wait(tfull_bar, aph, abort_flag, ff.err);
+            if (!__all_sync(kAll, ready)) break;
+            ptx::tc_fence_after();
+            {
+                const int m = m0 + q * 32 + lane;
+                const int F = m % P, slow = m / P, i2 = F >> 1;
+                const bool odd = (F & 1) != 0;
+                const bool valid = odd ? (i2 < nanti) : (i2 < nsym);
+                const long long obase = (long long)slow * P + (odd ? H + i2 : i2);
+                const int cols = H / 2;   // 2H accumulator columns over four warps per quadrant
+                const int cbeg = part * cols;
+                for (int c = cbeg; c < cbeg + cols; c += 16) {
+                    uint32_t r[16];
+                    ptx::tmem_ld_32x32b_x16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)c, r);
+                    ptx::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const float v = __uint_as_float(r[i]);
+                        const float pv = __shfl_xor_sync(kAll, v, 1);
+                        const float o = valid ? (odd ? pv - v : v + pv) : 0.0f;
+                        __nv_bfloat16 oh, ol;
+                        split_bf16(o, oh, ol);
+                        const long long idx = (long long)(c + i) * Mtot + obase;
+                        ff.out_hi[idx] = oh;
+                        ff.out_lo[idx] = ol;
+                    }
+                }
+            }
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(tempty_bar);
+            aph ^= 1u;
+        }
+    }
+
+    tile_partials<KIND>(a, kr2, kc, r2k, amin, amax, INFINITY, -INFINITY);
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem_base, 512);
+    }
+}
+
 // Dense FP64 field -> FP32 -> BF16 hi/lo planes on the zero-padded P^dim grid.
 template <int DIM>
 __global__ void __launch_bounds__(256) k_split_pad(const double *__restrict__ r, int n, int P,
@@ -1433,6 +1876,35 @@ int launch_residual_mirror(const ResidualArgs &a, int max_grid, int zchunk, int 
     if (a.lam != 0.0) return launch_mirror_kind<0>(a, max_grid, zchunk, grid_used, s);
     if (a.b != 1.0) return launch_mirror_kind<1>(a, max_grid, zchunk, grid_used, s);
     return launch_mirror_kind<2>(a, max_grid, zchunk, grid_used, s);
+}
+
+int fused_set_attributes() {
+    QN_CUDA(cudaFuncSetAttribute(k_fused_res_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFzSmem));
+    QN_CUDA(cudaFuncSetAttribute(k_fused_res_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFzSmem));
+    QN_CUDA(cudaFuncSetAttribute(k_fused_res_fwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFzSmem));
+    return QN_OK;
+}
+
+int launch_fused_residual_fwd(const ResidualArgs &a, const FusedFwd &ff, int *grid_used, cudaStream_t s) {
+    const int H = a.P / 2;
+    if (a.dim != 3 || a.P % 128 != 0 || H > 256 || a.n <= H || a.fdf == nullptr || a.fx_e == nullptr ||
+        a.r2_exp == nullptr || a.pot != nullptr || a.bc != QN_BC_DIRICHLET || ff.b_hi == nullptr ||
+        ff.b_lo == nullptr || ff.out_hi == nullptr || ff.out_lo == nullptr || ff.err == nullptr || ff.num_sms < 1) {
+        set_error("launch_fused_residual_fwd: needs a 3-D split solve with P a multiple of 128, P <= 512, "
+                  "Dirichlet data, no potential, the f copy and the forward matrix maps");
+        return QN_EINVAL;
+    }
+    const int ntiles = (a.P / 128) * a.P;
+    const int grid = ntiles < ff.num_sms ? ntiles : ff.num_sms;
+    *grid_used = grid;
+    if (a.lam != 0.0)
+        k_fused_res_fwd<0><<<grid, kFzThreads, kFzSmem, s>>>(a, ff);
+    else if (a.b != 1.0)
+        k_fused_res_fwd<1><<<grid, kFzThreads, kFzSmem, s>>>(a, ff);
+    else
+        k_fused_res_fwd<2><<<grid, kFzThreads, kFzSmem, s>>>(a, ff);
+    QN_CUDA(cudaGetLastError());
+    return QN_OK;
 }
 
 int launch_residual_tiled(const ResidualArgs &a, int max_grid, int zchunk, int *grid_used, cudaStream_t s) {

@@ -72,7 +72,8 @@ class QnProfile(ctypes.Structure):
                 ("mp_divide_launches", ctypes.c_int), ("mp_divide_ms", ctypes.c_double),
                 ("mp_last_launches", ctypes.c_int), ("mp_last_ms", ctypes.c_double),
                 ("residual_tiled_launches", ctypes.c_int), ("residual_tiled_ms", ctypes.c_double),
-                ("split_products", ctypes.c_int), ("x6_from", ctypes.c_int)]
+                ("split_products", ctypes.c_int), ("x6_from", ctypes.c_int),
+                ("fused_launches", ctypes.c_int), ("fused_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -157,6 +158,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                          ctypes.POINTER(ctypes.c_int), P]),
         "qn_profile_read": (ctypes.c_int, [P, ctypes.POINTER(QnProfile)]),
         "qn_set_escalation": (ctypes.c_int, [P, ctypes.c_double]),
+        "qn_set_fused_residual": (ctypes.c_int, [P, ctypes.c_int]),
         "qn_eig_solve": (ctypes.c_int, [P, P, ctypes.POINTER(QnOpts), ctypes.POINTER(QnResult),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(QnStats), ctypes.c_int, P]),
     }
@@ -400,6 +402,12 @@ def qn_set_escalation(ctx: QnContext, rate: float):
     """BF16X3 solves switch their backward products to the six-product level when the
     observed contraction exceeds `rate` and twice the quasi-Newton bound (0: off)."""
     _check(load_library().qn_set_escalation(ctx.handle, float(rate)))
+
+
+def qn_set_fused_residual(ctx: QnContext, on: bool = True):
+    """Iterations >= 1 of the 3-D split solve evaluate the residual inside the first
+    forward mode product (one kernel) instead of the separate residual kernel."""
+    _check(load_library().qn_set_fused_residual(ctx.handle, 1 if on else 0))
 
 
 def qn_profile_enable(ctx: QnContext, on: bool = True):
