@@ -112,6 +112,9 @@ def test_ctx_create_validates_before_cuda(lib):
     assert lib.qn_ctx_create(None, ctypes.byref(h)) == qn.QN_EINVAL
     assert lib.qn_residual(None, None, None, None, None, None) == qn.QN_EINVAL
     assert lib.qn_solve(None, None, None, None, None, None, 0, None) == qn.QN_EINVAL
+    assert lib.qn_set_escalation(None, ctypes.c_double(1.0)) == qn.QN_EINVAL
+    assert lib.qn_set_fused_residual(None, 1) == qn.QN_EINVAL
+    assert lib.qn_set_fused_residual(None, 0) == qn.QN_EINVAL
     assert lib.qn_ctx_destroy(None) == qn.QN_OK
 
 
