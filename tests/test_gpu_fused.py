@@ -101,6 +101,21 @@ def test_fused_p384(qn):
     assert rel <= 1.05e-10, rel
 
 
+def test_fused_511_identical_to_separate(qn):
+    """The benchmark size (P = 512: split halves of 256, two accumulators of 256 columns, all
+    of TMEM): with graph replay as the benchmark runs it, the same iterations and the same U
+    bit for bit as the separate kernels, and the FP64 relative residual of U below 1.05e-10."""
+    n = 511
+    u, f = manufactured_problem(n, 3, seed=0)
+    fz = _solve(qn, n, f, True, graph=True)
+    sp = _solve(qn, n, f, False, graph=True)
+    assert fz[0]["status"] == 0 and fz[0]["iterations"] == sp[0]["iterations"]
+    assert np.array_equal(fz[2], sp[2])
+    assert fz[3]["fused_launches"] == fz[0]["iterations"]
+    rel = np.linalg.norm(O.residual(fz[2], f)) / np.linalg.norm(f)
+    assert rel <= 1.05e-10, rel
+
+
 @pytest.mark.parametrize("lam,b", [(2.5, 0.5), (-3.0, 2.0)])
 def test_fused_general_coefficients(qn, lam, b):
     """lam u + b u^3 with lam != 0 and b != 1 (the kernel's general forms)."""
