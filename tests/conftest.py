@@ -15,8 +15,8 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     # GPU tests are skipped (not failed) on a machine without CUDA so that
-    # `-m "not gpu"` and plain runs on CPU machines behave; on a GPU machine a
-    # missing library is a hard failure inside the tests themselves.
+    # `-m "not gpu"` and plain runs on CPU-only machines behave; on a machine with
+    # a GPU a missing library is a hard failure inside the tests themselves.
     try:
         import torch
         has_cuda = torch.cuda.is_available()
