@@ -1178,7 +1178,10 @@ def main():
     # ---- the residual fused into the first forward mode product (off by default)
     f1 = None
     if not ex1 and not sem and a.precision == "bf16x3" and not a.no_f1 and not a.fused:
-        f1 = run_fused(qn, n, f, U.clone(), max_it, a.steps, a.warmup, stream, prof, ms_per_step, hbm)
+        try:
+            f1 = run_fused(qn, n, f, U.clone(), max_it, a.steps, a.warmup, stream, prof, ms_per_step, hbm)
+        except qn.QnError as e:   # a library error of the optional form is reported, not fatal
+            f1 = {"kernel": "k_fused_res_fwd", "error": str(e)}
 
     # ---- end to end through the public API with host buffers (copies inside the timed region)
     e2e = None
