@@ -78,15 +78,15 @@ def parse():
                     help="skip the 2-D 63^2 FP64, 3-D 255^3 FP64 and warm-start legs of the default line")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-start leg (training takes ~100 s)")
     ap.add_argument("--oracle-sample", default=None, choices=["c1", "c2"], help=argparse.SUPPRESS)
-    ap.add_argument("--no-f1", action="store_true",
+    ap.add_argument("--no-fused-leg", action="store_true",
                     help="skip the timing of the residual fused into the first mode product")
     ap.add_argument("--fused", action="store_true",
                     help="run the main solves with the fused residual (qn_set_fused_residual)")
     ap.add_argument("--quick", action="store_true",
-                    help="= --no-fp64 --no-cpu --no-e2e --no-batched --no-configs --no-f1")
+                    help="= --no-fp64 --no-cpu --no-e2e --no-batched --no-configs --no-fused-leg")
     a = ap.parse_args()
     if a.quick:
-        a.no_fp64 = a.no_cpu = a.no_e2e = a.no_batched = a.no_configs = a.no_f1 = True
+        a.no_fp64 = a.no_cpu = a.no_e2e = a.no_batched = a.no_configs = a.no_fused_leg = True
     if a.n is None:
         a.n = {"dirichlet": 511, "sem": 255}.get(a.workload, 200)
     return a
@@ -1176,12 +1176,12 @@ def main():
     gpu_launches = timed_launches
 
     # ---- the residual fused into the first forward mode product (off by default)
-    f1 = None
-    if not ex1 and not sem and a.precision == "bf16x3" and not a.no_f1 and not a.fused:
+    fused = None
+    if not ex1 and not sem and a.precision == "bf16x3" and not a.no_fused_leg and not a.fused:
         try:
-            f1 = run_fused(qn, n, f, U.clone(), max_it, a.steps, a.warmup, stream, prof, ms_per_step, hbm)
+            fused = run_fused(qn, n, f, U.clone(), max_it, a.steps, a.warmup, stream, prof, ms_per_step, hbm)
         except qn.QnError as e:   # a library error of the optional form is reported, not fatal
-            f1 = {"kernel": "k_fused_res_fwd", "error": str(e)}
+            fused = {"kernel": "k_fused_res_fwd", "error": str(e)}
 
     # ---- end to end through the public API with host buffers (copies inside the timed region)
     e2e = None
@@ -1453,7 +1453,7 @@ def main():
             "parity": parity,
             "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
             "e2e": e2e, "plain_fp64": plain, "batched": batched, "configs": configs,
-            "f1_fused": f1, "cpu_baseline": cpu, "clocks": clocks,
+            "fused_residual": fused, "cpu_baseline": cpu, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
